@@ -1,0 +1,201 @@
+/*
+ * fk.h -- C-ABI of the B300 (sm_103a) path for Fourier-represented kernel
+ * regression (arXiv 2509.02649, "Fast kernel methods: Sobolev, physics-informed,
+ * and additive models").
+ *
+ * What the library computes (paper notation, frequency scale pi/(2L) = 1, so
+ * points are radians and a caller with data in [-L, L]^d passes x * pi/(2L)):
+ *
+ *   modes     K = { k in Z^d : |k|_inf <= m },  D = (2m+1)^d           (Sec. 2.2)
+ *   moments   T_j = (1/n) sum_i exp(-i <j, X_i>),   |j|_inf <= 2m      (Sec. 2.3,
+ *             covariance matrix: Phi^*Phi/n is d-level block Toeplitz with
+ *             entries T_{k-k'})
+ *   rhs       b_k = (1/n) sum_i Y_i exp(-i <k, X_i>), |k|_inf <= m      (Sec. 2.3,
+ *             covariance vector)
+ *   estimator theta = (Toep(T) + diag W)^{-1} b                         (Eq. 2)
+ *   penalty   W_k = lambda (c0 + |k|_2^{2s})        Sobolev, M = S     (Sec. 3.1)
+ *             W_k = lambda                           low bias, M = I    (Sec. 3.2)
+ *             W_k += mu |P(ik)|^2                    physics-informed  (Sec. 4,
+ *             tractable domain on the full period, where the Fourier matrix C
+ *             of the domain is the identity)
+ *   additive  block Gram of Prop. 5.1 (+ lambda I), blocks off the diagonal are
+ *             2-D type-1 transforms of ones at (X_l1, -X_l2)            (Sec. 5)
+ *   predict   f(x) = Re sum_k theta_k exp(+i <k, x>)                    (Eq. 1)
+ *
+ * Sums over points run through a type-1 non-uniform FFT (exponential-of-
+ * semicircle spreading, FFT on an upsampled grid, deconvolution); prediction
+ * through the type-2 transform (deconvolution, inverse FFT, interpolation).
+ * eps is the requested relative l2 error of each transformed vector.
+ *
+ * Conventions shared by every entry point
+ *  - Mode vectors are lexicographic over k in K with the LAST dimension
+ *    fastest; flat index sum_l (k_l + m) (2m+1)^{d-1-l}.  Complex arrays are
+ *    interleaved (re, im) doubles.
+ *  - Points are structure-of-arrays, x[l * n + i] = coordinate l of point i.
+ *    precision FK_MIXED: x and y are float32; FK_FP64: float64.  Points must
+ *    lie in [-3 pi, 3 pi); they are folded onto [-pi, pi) (exact for integer
+ *    modes by periodicity).  A point outside that range makes the call return
+ *    FK_ERANGE.
+ *  - Array arguments documented as "device" are device pointers owned by the
+ *    caller; "host" arrays are read before the call returns.  The library never
+ *    frees caller memory.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream).  Calls that return a status depending on device results (range
+ *    flag, Cholesky pivots, CG convergence) synchronise `stream` before they
+ *    return; fk_type1 / fk_type2 / fk_penalty_weights do not synchronise.
+ *  - Scratch memory is allocated stream-ordered (cudaMallocAsync) on `stream`
+ *    and released on it before return.
+ *  - On error the outputs are unspecified and fk_last_error() describes the
+ *    failure (thread-local string, valid until the next call on the thread).
+ *    Argument errors are detected on the host before any launch.
+ */
+#ifndef FK_H_
+#define FK_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FK_API __attribute__((visibility("default")))
+#else
+#define FK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FK_OK = 0,
+  FK_EINVAL = 1,     /* invalid argument (detected on the host, nothing launched) */
+  FK_ERANGE = 2,     /* a point outside [-3 pi, 3 pi) */
+  FK_ENOMEM = 3,     /* device allocation failed */
+  FK_ECUDA = 4,      /* a CUDA runtime call failed */
+  FK_ENOTPD = 5,     /* Cholesky met a non-positive pivot (system not positive definite) */
+  FK_ENOCONV = 6,    /* conjugate gradients did not reach cg_tol within cg_maxit */
+  FK_ETIMEOUT = 7,   /* a bounded device-side wait gave up */
+  FK_EINTERNAL = 8   /* internal consistency check failed */
+} fk_status;
+
+typedef enum { FK_FP64 = 0, FK_MIXED = 1 } fk_precision;
+typedef enum { FK_PEN_SOBOLEV = 0, FK_PEN_LOWBIAS = 1 } fk_penalty;
+typedef enum { FK_SOLVER_AUTO = 0, FK_SOLVER_CHOL = 1, FK_SOLVER_CG = 2 } fk_solver;
+typedef enum { FK_SPREAD_AUTO = 0, FK_SPREAD_ATOMIC = 1, FK_SPREAD_BINNED = 2 } fk_spread;
+
+/* Options; pass NULL for defaults (fk_default_opts). */
+typedef struct {
+  int solver;         /* fk_solver; AUTO = Cholesky for D <= 1024, else CG */
+  double cg_tol;      /* relative residual target of CG (default 1e-13) */
+  int cg_maxit;       /* CG iteration cap (default 1000) */
+  int refine_steps;   /* iterative-refinement steps after a Cholesky solve (default 1) */
+  double sobolev_c0;  /* c0 in lambda (c0 + |k|^{2s}); the paper's value is 1 (default 1) */
+  double upsampfac;   /* minimum fine-grid oversampling sigma (default 1.9; grids are powers of 2) */
+  int spread;         /* fk_spread: AUTO = BINNED for FK_MIXED, ATOMIC for FK_FP64 */
+  int deterministic;  /* reserved: 1 asks for run-to-run identical sums (default 0) */
+} fk_opts;
+
+/* Filled when a non-NULL pointer is passed (the call then synchronises `stream`). */
+typedef struct {
+  double ms_spread;     /* spreading (type-1) */
+  double ms_fft;        /* FFT + deconvolution */
+  double ms_solve;      /* penalty, assembly and solve */
+  double ms_total;
+  int cg_iters;         /* largest CG iteration count over the batch (0 for Cholesky) */
+  double rel_residual;  /* largest |b - A theta| / |b| over the batch, FP64 */
+  int64_t n_used;       /* points consumed */
+  int fine_grid;        /* upsampled grid size per dimension */
+  int kernel_width;     /* ES kernel width w (taps per dimension) */
+} fk_report;
+
+FK_API void fk_default_opts(fk_opts* opts);
+
+/* Sobolev / low-bias estimator (Eq. 2 with Sec. 3.1 or 3.2 penalty) for a batch of
+ * n_lambda regularisation values and n_targets response vectors.
+ *   d in {1, 2, 3}; n >= 1; m >= 0; s >= 0; eps in [1e-14, 1e-1]; lambdas > 0.
+ *   x: device, d x n;  y: device, n_targets x n;  lambdas: host, n_lambda.
+ *   theta: device, [n_lambda][n_targets][D] complex (2 doubles each). */
+FK_API fk_status fk_fit_sobolev(int d, int64_t n, const void* x, const void* y, int n_targets,
+                         int m, double s, int penalty, const double* lambdas, int n_lambda,
+                         double eps, int precision, const fk_opts* opts,
+                         double* theta, void* stream, fk_report* rep);
+
+/* Physics-informed estimator (Sec. 4, tractable domain = full period):
+ *   W_k = lambda (c0 + |k|^{2s}) + mu |P(ik)|^2,  P(ik) = sum_t a_t prod_l (i k_l)^{alpha_t,l}.
+ *   alpha: host, n_terms x d non-negative ints; a: host, n_terms reals.
+ *   theta: device, [n_targets][D] complex.  Other arguments as fk_fit_sobolev. */
+FK_API fk_status fk_fit_pik(int d, int64_t n, const void* x, const void* y, int n_targets,
+                     int m, double s, double lambda, double mu, int n_terms,
+                     const int* alpha, const double* a, double eps, int precision,
+                     const fk_opts* opts, double* theta, void* stream, fk_report* rep);
+
+/* Low-bias additive estimator (Prop. 5.1): theta = (Sigma + lambda I)^{-1} (Phi_l^*Y/n)_l.
+ *   d in [2, 16] coordinates; theta: device, [n_lambda][n_targets][d][2m+1] complex. */
+FK_API fk_status fk_fit_additive(int d, int64_t n, const void* x, const void* y, int n_targets,
+                          int m, const double* lambdas, int n_lambda, double eps,
+                          int precision, const fk_opts* opts, double* theta, void* stream,
+                          fk_report* rep);
+
+/* Prediction f(x) = Re sum_k theta_k e^{+i<k,x>} (Eq. 1), or for additive != 0 the
+ * additive form sum_l Re sum_k theta_{l,k} e^{i k x_l} (Sec. 5).
+ *   theta: device, n_sets coefficient vectors (layout of the fit outputs);
+ *   xq: device, d x n_q (precision as above);  f: device, [n_sets][n_q] doubles. */
+FK_API fk_status fk_predict(int additive, int d, int m, const double* theta, int n_sets, int64_t n_q,
+                     const void* xq, double eps, int precision, double* f, void* stream);
+
+/* Building blocks (also the pieces of the autograd backward). */
+
+/* Unnormalised type-1 sums out[c][k] = sum_i c_i exp(-i<k, x_i>), |k|_inf <= kmax.
+ *   c: device, n_ch x n real strengths (precision of x);  out: device complex
+ *   [n_ch][(2kmax+1)^d]. */
+FK_API fk_status fk_type1(int d, int64_t n, const void* x, const void* c, int n_ch, int kmax,
+                   double eps, int precision, double* out, void* stream);
+
+/* Type-2 real parts out[s][i] = Re sum_k coef_{s,k} exp(+i<k, x_i>), |k|_inf <= kmax.
+ *   coef: device complex [n_sets][(2kmax+1)^d];  out: device doubles [n_sets][n]. */
+FK_API fk_status fk_type2(int d, int kmax, const double* coef, int n_sets, int64_t n, const void* x,
+                   double eps, int precision, double* out, void* stream);
+
+/* Moments and right-hand sides: T (device complex, (4m+1)^d) and
+ * b (device complex, [n_targets][D]), each divided by n (Sec. 2.3). */
+FK_API fk_status fk_build_system(int d, int64_t n, const void* x, const void* y, int n_targets, int m,
+                          double eps, int precision, const fk_opts* opts, double* T, double* b,
+                          void* stream, fk_report* rep);
+
+/* Penalty diagonals W (device doubles, [n_lambda][D]) of Sec. 3.1 / 3.2 / 4:
+ *   W = lambda (c0 + |k|^{2s}) (+ mu |P(ik)|^2 when n_terms > 0); penalty selects
+ *   FK_PEN_SOBOLEV or FK_PEN_LOWBIAS (then W = lambda, s and c0 ignored). */
+FK_API fk_status fk_penalty_weights(int d, int m, int penalty, double s, double c0,
+                             const double* lambdas, int n_lambda, double mu, int n_terms,
+                             const int* alpha, const double* a, double* W, void* stream);
+
+/* Solve (Toep(T) + diag W_l) sol_{l,r} = rhs_r for every penalty l and right-hand side r.
+ *   T: device complex (4m+1)^d;  W: device doubles [n_w][D];  rhs: device complex
+ *   [n_rhs][D];  sol: device complex [n_w][n_rhs][D]. */
+FK_API fk_status fk_solve(int d, int m, const double* T, const double* W, int n_w, const double* rhs,
+                   int n_rhs, const fk_opts* opts, double* sol, void* stream, fk_report* rep);
+
+/* Held-out-loss hypergradient (not in the paper; adjoint of Eq. 2).  Given the fit
+ * theta for one (W, Y) pair and validation data (xv, yv):
+ *   r = f(xv) - yv,  L = mean(r^2),  g = type1(xv, r) / n_v,  z = A^{-1} g,
+ *   dW_k = -2 Re(conj(z_k) theta_k),  dY_i = (2/n) Re sum_k z_k e^{+i<k, X_i>}.
+ *   T: device complex (4m+1)^d of the training points; W: device D; theta: device D
+ *   complex; xv/yv: device (precision of x); outputs: loss (host double), dW (device
+ *   D doubles), dY (device n doubles, may be NULL to skip). */
+FK_API fk_status fk_hypergrad(int d, int64_t n, const void* x, int64_t n_v, const void* xv,
+                       const void* yv, int m, const double* T, const double* W,
+                       const double* theta, double eps, int precision, const fk_opts* opts,
+                       double* loss, double* dW, double* dY, void* stream);
+
+/* Thread-local description of the last failure on this thread ("" after success). */
+FK_API const char* fk_last_error(void);
+
+/* Upper bound of the scratch bytes one fit with these sizes allocates. */
+FK_API size_t fk_workspace_bytes(int d, int m, int64_t n, int n_ch, double eps, int precision);
+
+/* Library version string. */
+FK_API const char* fk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FK_H_ */

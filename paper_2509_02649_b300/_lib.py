@@ -1,0 +1,277 @@
+"""ctypes binding of libfk (include/fk.h): argument marshalling only.
+
+Every function here takes torch tensors that already live on the GPU, checks
+their dtype/layout, allocates the outputs with torch and passes raw device
+pointers plus the current CUDA stream to the C-ABI.  All arithmetic runs in
+libfk's kernels; there is no CPU fallback.  If libfk.so is missing the first
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import torch
+
+from .build import LIB
+
+FK_FP64, FK_MIXED = 0, 1
+FK_PEN_SOBOLEV, FK_PEN_LOWBIAS = 0, 1
+FK_SOLVER_AUTO, FK_SOLVER_CHOL, FK_SOLVER_CG = 0, 1, 2
+FK_SPREAD_AUTO, FK_SPREAD_ATOMIC, FK_SPREAD_BINNED = 0, 1, 2
+
+STATUS = {0: "FK_OK", 1: "FK_EINVAL", 2: "FK_ERANGE", 3: "FK_ENOMEM", 4: "FK_ECUDA", 5: "FK_ENOTPD",
+          6: "FK_ENOCONV", 7: "FK_ETIMEOUT", 8: "FK_EINTERNAL"}
+
+EXPORTS = ["fk_default_opts", "fk_fit_sobolev", "fk_fit_pik", "fk_fit_additive", "fk_predict", "fk_type1",
+           "fk_type2", "fk_build_system", "fk_penalty_weights", "fk_solve", "fk_hypergrad", "fk_last_error",
+           "fk_workspace_bytes", "fk_version"]
+
+
+class FkError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(status, str(status)), msg))
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("solver", ctypes.c_int), ("cg_tol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
+                ("refine_steps", ctypes.c_int), ("sobolev_c0", ctypes.c_double), ("upsampfac", ctypes.c_double),
+                ("spread", ctypes.c_int), ("deterministic", ctypes.c_int)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("ms_spread", ctypes.c_double), ("ms_fft", ctypes.c_double), ("ms_solve", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("cg_iters", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("n_used", ctypes.c_int64), ("fine_grid", ctypes.c_int), ("kernel_width", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib: Optional[ctypes.CDLL] = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_L = ctypes.c_int64
+_D = ctypes.c_double
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError("libfk.so is not built (run paper_2509_02649_b300/build.py); no fallback exists")
+        L = ctypes.CDLL(LIB)
+        sig = {
+            "fk_default_opts": (None, [_P]),
+            "fk_fit_sobolev": (_I, [_I, _L, _P, _P, _I, _I, _D, _I, _P, _I, _D, _I, _P, _P, _P, _P]),
+            "fk_fit_pik": (_I, [_I, _L, _P, _P, _I, _I, _D, _D, _D, _I, _P, _P, _D, _I, _P, _P, _P, _P]),
+            "fk_fit_additive": (_I, [_I, _L, _P, _P, _I, _I, _P, _I, _D, _I, _P, _P, _P, _P]),
+            "fk_predict": (_I, [_I, _I, _I, _P, _I, _L, _P, _D, _I, _P, _P]),
+            "fk_type1": (_I, [_I, _L, _P, _P, _I, _I, _D, _I, _P, _P]),
+            "fk_type2": (_I, [_I, _I, _P, _I, _L, _P, _D, _I, _P, _P]),
+            "fk_build_system": (_I, [_I, _L, _P, _P, _I, _I, _D, _I, _P, _P, _P, _P, _P]),
+            "fk_penalty_weights": (_I, [_I, _I, _I, _D, _D, _P, _I, _D, _I, _P, _P, _P, _P]),
+            "fk_solve": (_I, [_I, _I, _P, _P, _I, _P, _I, _P, _P, _P, _P]),
+            "fk_hypergrad": (_I, [_I, _L, _P, _L, _P, _P, _I, _P, _P, _P, _D, _I, _P, _P, _P, _P, _P]),
+            "fk_last_error": (ctypes.c_char_p, []),
+            "fk_workspace_bytes": (ctypes.c_size_t, [_I, _I, _L, _I, _D, _I]),
+            "fk_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise FkError(status, lib().fk_last_error().decode())
+
+
+def _stream(stream=None) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def _prec(precision) -> int:
+    if isinstance(precision, int):
+        return precision
+    return {"fp64": FK_FP64, "mixed": FK_MIXED}[precision]
+
+
+def _points(x: torch.Tensor, prec: int) -> torch.Tensor:
+    want = torch.float64 if prec == FK_FP64 else torch.float32
+    if not x.is_cuda:
+        raise ValueError("points must be a CUDA tensor")
+    if x.dtype != want:
+        raise ValueError("points must be %s for this precision" % want)
+    if x.dim() == 1:
+        x = x.unsqueeze(0)
+    return x.contiguous()
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().fk_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _opts_ptr(opts):
+    return ctypes.byref(opts) if opts is not None else None
+
+
+def _dbl_array(vals: Sequence[float]):
+    arr = (ctypes.c_double * len(vals))(*[float(v) for v in vals])
+    return arr
+
+
+def fk_build_system(x, y, m: int, eps: float, precision="mixed", opts: Optional[Opts] = None, report: bool = False):
+    """Moments T ((4m+1)^d complex) and right-hand sides b ([n_targets][D] complex), both / n."""
+    p = _prec(precision)
+    x = _points(x, p)
+    d, n = x.shape
+    y = y.reshape(-1, n).contiguous() if y is not None else None
+    nt = 0 if y is None else y.shape[0]
+    T = torch.empty((4 * m + 1) ** d, dtype=torch.complex128, device=x.device)
+    b = torch.empty((max(nt, 1), (2 * m + 1) ** d), dtype=torch.complex128, device=x.device)
+    rep = Report()
+    _check(lib().fk_build_system(d, n, x.data_ptr(), y.data_ptr() if y is not None else None, nt, m, eps, p,
+                                 _opts_ptr(opts), T.data_ptr(), b.data_ptr(), _stream(),
+                                 ctypes.byref(rep) if report else None))
+    out = (T, b[:nt])
+    return (out + (rep.as_dict(),)) if report else out
+
+
+def fk_fit_sobolev(x, y, m: int, s: float, lambdas, eps: float, precision="mixed", penalty: int = FK_PEN_SOBOLEV,
+                   opts: Optional[Opts] = None, report: bool = False):
+    """theta [n_lambda][n_targets][D] complex128 (Eq. 2 with the Sec. 3.1 / 3.2 penalty)."""
+    p = _prec(precision)
+    x = _points(x, p)
+    d, n = x.shape
+    y = y.reshape(-1, n).contiguous()
+    lam = list(lambdas) if hasattr(lambdas, "__len__") else [lambdas]
+    theta = torch.empty((len(lam), y.shape[0], (2 * m + 1) ** d), dtype=torch.complex128, device=x.device)
+    rep = Report()
+    _check(lib().fk_fit_sobolev(d, n, x.data_ptr(), y.data_ptr(), y.shape[0], m, s, penalty, _dbl_array(lam), len(lam),
+                                eps, p, _opts_ptr(opts), theta.data_ptr(), _stream(),
+                                ctypes.byref(rep) if report else None))
+    return (theta, rep.as_dict()) if report else theta
+
+
+def fk_fit_pik(x, y, m: int, s: float, lam: float, mu: float, alpha, a, eps: float, precision="mixed",
+               opts: Optional[Opts] = None, report: bool = False):
+    """theta [n_targets][D] complex128 with W = lambda(c0 + |k|^{2s}) + mu |P(ik)|^2 (Sec. 4)."""
+    p = _prec(precision)
+    x = _points(x, p)
+    d, n = x.shape
+    y = y.reshape(-1, n).contiguous()
+    al = [int(v) for row in alpha for v in row]
+    nt = len(a)
+    alpha_arr = (ctypes.c_int * max(len(al), 1))(*al)
+    theta = torch.empty((y.shape[0], (2 * m + 1) ** d), dtype=torch.complex128, device=x.device)
+    rep = Report()
+    _check(lib().fk_fit_pik(d, n, x.data_ptr(), y.data_ptr(), y.shape[0], m, s, lam, mu, nt, alpha_arr,
+                            _dbl_array(a), eps, p, _opts_ptr(opts), theta.data_ptr(), _stream(),
+                            ctypes.byref(rep) if report else None))
+    return (theta, rep.as_dict()) if report else theta
+
+
+def fk_fit_additive(x, y, m: int, lambdas, eps: float, precision="mixed", opts: Optional[Opts] = None,
+                    report: bool = False):
+    """theta [n_lambda][n_targets][d][2m+1] complex128 (Prop. 5.1)."""
+    p = _prec(precision)
+    x = _points(x, p)
+    d, n = x.shape
+    y = y.reshape(-1, n).contiguous()
+    lam = list(lambdas) if hasattr(lambdas, "__len__") else [lambdas]
+    theta = torch.empty((len(lam), y.shape[0], d, 2 * m + 1), dtype=torch.complex128, device=x.device)
+    rep = Report()
+    _check(lib().fk_fit_additive(d, n, x.data_ptr(), y.data_ptr(), y.shape[0], m, _dbl_array(lam), len(lam), eps, p,
+                                 _opts_ptr(opts), theta.data_ptr(), _stream(), ctypes.byref(rep) if report else None))
+    return (theta, rep.as_dict()) if report else theta
+
+
+def fk_predict(theta, xq, m: int, eps: float, precision="mixed", additive: bool = False):
+    """f [n_sets][n_q] float64: Re sum_k theta_k e^{i<k,x>} (or the additive sum)."""
+    p = _prec(precision)
+    xq = _points(xq, p)
+    d, nq = xq.shape
+    per = d * (2 * m + 1) if additive else (2 * m + 1) ** d
+    th = theta.reshape(-1, per).contiguous()
+    f = torch.empty((th.shape[0], nq), dtype=torch.float64, device=xq.device)
+    _check(lib().fk_predict(1 if additive else 0, d, m, th.data_ptr(), th.shape[0], nq, xq.data_ptr(), eps, p,
+                            f.data_ptr(), _stream()))
+    return f
+
+
+def fk_type1(x, c, kmax: int, eps: float, precision="mixed"):
+    """Unnormalised sums out[c][k] = sum_i c_i e^{-i<k,x_i>} (complex128)."""
+    p = _prec(precision)
+    x = _points(x, p)
+    d, n = x.shape
+    c = c.reshape(-1, n).contiguous()
+    out = torch.empty((c.shape[0], (2 * kmax + 1) ** d), dtype=torch.complex128, device=x.device)
+    _check(lib().fk_type1(d, n, x.data_ptr(), c.data_ptr(), c.shape[0], kmax, eps, p, out.data_ptr(), _stream()))
+    return out
+
+
+def fk_type2(coef, x, kmax: int, eps: float, precision="mixed"):
+    """Re sum_k coef_k e^{+i<k,x>} for each coefficient set, float64 [n_sets][n]."""
+    p = _prec(precision)
+    x = _points(x, p)
+    d, n = x.shape
+    cf = coef.reshape(-1, (2 * kmax + 1) ** d).contiguous()
+    out = torch.empty((cf.shape[0], n), dtype=torch.float64, device=x.device)
+    _check(lib().fk_type2(d, kmax, cf.data_ptr(), cf.shape[0], n, x.data_ptr(), eps, p, out.data_ptr(), _stream()))
+    return out
+
+
+def fk_penalty_weights(d: int, m: int, lambdas, s: float = 1.0, penalty: int = FK_PEN_SOBOLEV, c0: float = 1.0,
+                       mu: float = 0.0, alpha=(), a=(), device="cuda"):
+    lam = list(lambdas) if hasattr(lambdas, "__len__") else [lambdas]
+    al = [int(v) for row in alpha for v in row]
+    W = torch.empty((len(lam), (2 * m + 1) ** d), dtype=torch.float64, device=device)
+    alpha_arr = (ctypes.c_int * max(len(al), 1))(*al)
+    a_arr = _dbl_array(list(a) if len(a) else [0.0])
+    _check(lib().fk_penalty_weights(d, m, penalty, s, c0, _dbl_array(lam), len(lam), mu, len(a), alpha_arr, a_arr,
+                                    W.data_ptr(), _stream()))
+    return W
+
+
+def fk_solve(T, W, rhs, d: int, m: int, opts: Optional[Opts] = None, report: bool = False):
+    """sol [n_w][n_rhs][D] complex128 of (Toep(T) + diag W_l) sol = rhs_r."""
+    D = (2 * m + 1) ** d
+    T = T.contiguous()
+    W = W.reshape(-1, D).contiguous()
+    rhs = rhs.reshape(-1, D).contiguous()
+    sol = torch.empty((W.shape[0], rhs.shape[0], D), dtype=torch.complex128, device=T.device)
+    rep = Report()
+    _check(lib().fk_solve(d, m, T.data_ptr(), W.data_ptr(), W.shape[0], rhs.data_ptr(), rhs.shape[0],
+                          _opts_ptr(opts), sol.data_ptr(), _stream(), ctypes.byref(rep) if report else None))
+    return (sol, rep.as_dict()) if report else sol
+
+
+def fk_hypergrad(x, xv, yv, m: int, T, W, theta, eps: float, precision="mixed", opts: Optional[Opts] = None,
+                 want_dy: bool = True):
+    """(loss, dL/dW [D] float64, dL/dY [n] float64 or None) by the adjoint method."""
+    p = _prec(precision)
+    x = _points(x, p)
+    xv = _points(xv, p)
+    d, n = x.shape
+    nv = xv.shape[1]
+    D = (2 * m + 1) ** d
+    dW = torch.empty(D, dtype=torch.float64, device=x.device)
+    dY = torch.empty(n, dtype=torch.float64, device=x.device) if want_dy else None
+    loss = ctypes.c_double(0.0)
+    _check(lib().fk_hypergrad(d, n, x.data_ptr(), nv, xv.data_ptr(), yv.contiguous().data_ptr(), m,
+                              T.contiguous().data_ptr(), W.contiguous().data_ptr(), theta.contiguous().data_ptr(),
+                              eps, p, _opts_ptr(opts), ctypes.byref(loss), dW.data_ptr(),
+                              dY.data_ptr() if dY is not None else None, _stream()))
+    return loss.value, dW, dY

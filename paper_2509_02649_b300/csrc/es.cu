@@ -1,0 +1,114 @@
+// Exponential-of-semicircle (ES) kernel plan and its Fourier-transform correction.
+//
+// The type-1 sums of Sec. 2.3 are evaluated as a non-uniform FFT: strengths are
+// spread onto an upsampled periodic grid with psi(x) = phi(x / alpha),
+// phi(z) = exp(beta (sqrt(1 - z^2) - 1)), alpha = w h / 2, h = 2 pi / N; the grid
+// is Fourier transformed and each mode divided by the kernel's transform
+//   Psi_hat(j) = alpha * int_{-1}^{1} phi(z) cos(j alpha z) dz,
+// so that sum_i c_i e^{-i j x_i} ~= (-1)^j h / Psi_hat(j) * DFT(g)[j mod N]
+// (Poisson summation; grid node l sits at x_l = -pi + l h).  The integral is
+// evaluated by Gauss-Legendre quadrature whose nodes come from Newton's method on
+// the Legendre recurrence, all in fp64 on the device.
+#include "fk_internal.cuh"
+
+namespace fk {
+
+static int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+fk_status make_es_plan(int d, int kmax, double eps, double upsampfac, EsPlan* p) {
+  if (kmax < 0) return set_error(FK_EINVAL, "kmax < 0");
+  const int K = 2 * kmax + 1;
+  if (upsampfac <= 1.0) upsampfac = 1.9;
+  int N = next_pow2(static_cast<int>(std::ceil(upsampfac * K)));
+  if (N < 16) N = 16;
+  // width from the ES error estimate exp(-pi w sqrt(1 - 1/sigma)), with half a tap of
+  // margin: measured relative l2 errors then stay within ~2 eps over sigma in [2, 5]
+  int w = 0;
+  for (int iter = 0; iter < 4; ++iter) {
+    const double sigma = static_cast<double>(N) / K;
+    w = static_cast<int>(std::ceil(std::log(1.0 / eps) / (M_PI * std::sqrt(1.0 - 1.0 / sigma)) + 0.5));
+    if (w < 2) w = 2;
+    if (w > 16) w = 16;
+    if (N >= 2 * w) break;
+    N *= 2;
+  }
+  const double sigma = static_cast<double>(N) / K;
+  p->d = d;
+  p->N = N;
+  p->w = w;
+  p->sigma = sigma;
+  p->kmax = kmax;
+  p->beta = 0.97 * M_PI * (1.0 - 0.5 / sigma) * w;
+  return FK_OK;
+}
+
+constexpr int GL_Q = 128;  // quadrature nodes on [-1, 1]
+
+// Gauss-Legendre nodes and weights: one thread per root.
+__global__ void k_gauss_legendre(double* nodes, double* weights) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= GL_Q) return;
+  const int q = GL_Q;
+  double x = cos(M_PI * (i + 0.75) / (q + 0.5));
+  double dp = 1.0;
+  for (int it = 0; it < 100; ++it) {
+    double p0 = 1.0, p1 = x;
+    for (int k = 2; k <= q; ++k) {
+      const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    // p1 = P_q(x), p0 = P_{q-1}(x);  P_q'(x) = q (x P_q - P_{q-1}) / (x^2 - 1)
+    dp = q * (x * p1 - p0) / (x * x - 1.0);
+    const double dx = p1 / dp;
+    x -= dx;
+    if (fabs(dx) < 1e-16) break;
+  }
+  {
+    double p0 = 1.0, p1 = x;
+    for (int k = 2; k <= q; ++k) {
+      const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = q * (x * p1 - p0) / (x * x - 1.0);
+  }
+  nodes[i] = x;
+  weights[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+}
+
+__global__ void k_es_correction(int kmax, int N, int w, double beta, const double* nodes,
+                                const double* weights, double* corr) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t > 2 * kmax) return;
+  const int j = t - kmax;
+  const double h = 2.0 * M_PI / N;
+  const double alpha = 0.5 * w * h;
+  double acc = 0.0;
+  for (int q = 0; q < GL_Q; ++q) {
+    const double z = nodes[q];
+    const double phi = exp(beta * (sqrt(1.0 - z * z) - 1.0));
+    acc += weights[q] * phi * cos(j * alpha * z);
+  }
+  const double psi_hat = alpha * acc;
+  const double sgn = (j & 1) ? -1.0 : 1.0;
+  corr[t] = sgn * h / psi_hat;
+}
+
+fk_status es_correction(const EsPlan& p, double* corr, cudaStream_t st) {
+  double* nw = nullptr;
+  FK_CUDA(cudaMallocAsync(&nw, 2 * GL_Q * sizeof(double), st));
+  k_gauss_legendre<<<1, GL_Q, 0, st>>>(nw, nw + GL_Q);
+  const int K = 2 * p.kmax + 1;
+  k_es_correction<<<(K + 127) / 128, 128, 0, st>>>(p.kmax, p.N, p.w, p.beta, nw, nw + GL_Q, corr);
+  cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(nw, st);
+  if (e != cudaSuccess) return set_error(FK_ECUDA, "es_correction launch: %s", cudaGetErrorString(e));
+  return FK_OK;
+}
+
+}  // namespace fk

@@ -1,0 +1,377 @@
+// C-ABI entry points of libfk (declared in include/fk.h): argument checks on the
+// host, scratch management, and the order of the device stages of each call.
+#include "fk_internal.cuh"
+
+#include <chrono>
+#include <vector>
+
+namespace fk {
+
+static thread_local std::string g_err;
+
+fk_status set_error(fk_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+void clear_error() { g_err.clear(); }
+
+static fk_opts resolve_opts(const fk_opts* o) {
+  fk_opts r;
+  fk_default_opts(&r);
+  if (o) r = *o;
+  if (r.cg_tol <= 0) r.cg_tol = 1e-13;
+  if (r.cg_maxit <= 0) r.cg_maxit = 1000;
+  if (r.refine_steps < 0) r.refine_steps = 0;
+  if (r.upsampfac <= 1.0) r.upsampfac = 1.9;
+  return r;
+}
+
+static fk_status check_common(int d, int64_t n, int m, double eps, int precision) {
+  if (d < 1 || d > 2) return set_error(FK_EINVAL, "d = %d: transforms are built for d in {1, 2}", d);
+  if (n < 1) return set_error(FK_EINVAL, "n = %lld < 1", (long long)n);
+  if (m < 0) return set_error(FK_EINVAL, "m = %d < 0", m);
+  if (!(eps >= 1e-14 && eps <= 1e-1)) return set_error(FK_EINVAL, "eps = %g outside [1e-14, 1e-1]", eps);
+  if (precision != FK_FP64 && precision != FK_MIXED) return set_error(FK_EINVAL, "unknown precision %d", precision);
+  return FK_OK;
+}
+
+static int64_t ipow(int64_t b, int e) {
+  int64_t r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+// Flags word that lives for one call.
+struct Flags {
+  unsigned* dev = nullptr;
+  cudaStream_t st;
+  explicit Flags(cudaStream_t s) : st(s) {}
+  fk_status init(Scratch& scr) {
+    FK_TRY(scr.alloc(&dev, 1));
+    FK_CUDA(cudaMemsetAsync(dev, 0, sizeof(unsigned), st));
+    return FK_OK;
+  }
+  fk_status check() {
+    unsigned h = 0;
+    FK_CUDA(cudaMemcpyAsync(&h, dev, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    FK_CUDA(cudaStreamSynchronize(st));
+    if (h & FLAG_RANGE) return set_error(FK_ERANGE, "a point lies outside [-3 pi, 3 pi)");
+    if (h & FLAG_NOTPD) return set_error(FK_ENOTPD, "Cholesky met a non-positive pivot");
+    if (h & FLAG_TIMEOUT) return set_error(FK_ETIMEOUT, "a bounded device wait gave up");
+    if (h & FLAG_INTERNAL) return set_error(FK_EINTERNAL, "device index check failed");
+    return FK_OK;
+  }
+};
+
+struct Timer {
+  cudaStream_t st;
+  bool on;
+  cudaEvent_t ev[8];
+  int n = 0;
+  Timer(cudaStream_t s, bool enabled) : st(s), on(enabled) {}
+  ~Timer() {
+    for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]);
+  }
+  void mark() {
+    if (!on || n >= 8) return;
+    cudaEventCreate(&ev[n]);
+    cudaEventRecord(ev[n], st);
+    ++n;
+  }
+  double ms(int a, int b) {
+    if (!on || b >= n) return 0.0;
+    cudaEventSynchronize(ev[b]);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, ev[a], ev[b]);
+    return t;
+  }
+};
+
+// Spread (ones channel if with_ones, then n_y strength channels) onto the fine grid.
+static fk_status spread_any(const EsPlan& p, int precision, const fk_opts& o, int64_t n, const void* x,
+                            const void* y, int n_y, bool with_ones, double* grid, unsigned* flags,
+                            cudaStream_t st, Scratch& scr) {
+  if (precision == FK_FP64)
+    return spread_atomic<double>(p, n, static_cast<const double*>(x), static_cast<const double*>(y), n_y,
+                                 with_ones, grid, flags, st);
+  const int nc = n_y + (with_ones ? 1 : 0);
+  const bool binned = (o.spread == FK_SPREAD_BINNED) ||
+                      (o.spread == FK_SPREAD_AUTO && spread_binned_supported(p, nc));
+  if (binned) {
+    if (!spread_binned_supported(p, nc))
+      return set_error(FK_EINVAL, "binned spreading does not support d=%d w=%d channels=%d", p.d, p.w, nc);
+    return spread_binned(p, n, static_cast<const float*>(x), static_cast<const float*>(y), n_y, with_ones, grid,
+                         flags, st, scr);
+  }
+  return spread_atomic<float>(p, n, static_cast<const float*>(x), static_cast<const float*>(y), n_y, with_ones,
+                              grid, flags, st);
+}
+
+static fk_status modes_any(const EsPlan& p, int precision, const double* grid, int c0, int nc, int kout,
+                           const double* corr, double scale, double* out, cudaStream_t st, Scratch& scr) {
+  if (precision == FK_FP64) return grid_to_modes<double>(p, grid, c0, nc, kout, corr, scale, out, st, scr);
+  return grid_to_modes<float>(p, grid, c0, nc, kout, corr, scale, out, st, scr);
+}
+
+// T (doubled range, divided by n) and b (n_targets channels, divided by n).
+static fk_status build_system(int d, int64_t n, const void* x, const void* y, int n_targets, int m, double eps,
+                              int precision, const fk_opts& o, double* T, double* b, cudaStream_t st,
+                              Scratch& scr, unsigned* flags, EsPlan* plan_out, Timer* tm) {
+  EsPlan p;
+  FK_TRY(make_es_plan(d, 2 * m, eps, o.upsampfac, &p));
+  if (plan_out) *plan_out = p;
+  const int nc = 1 + n_targets;
+  const int64_t G = ipow(p.N, d);
+  double *grid, *corr;
+  FK_TRY(scr.alloc(&grid, G * nc));
+  FK_TRY(scr.alloc(&corr, 2 * static_cast<size_t>(p.kmax) + 1));
+  FK_TRY(es_correction(p, corr, st));
+  if (tm) tm->mark();
+  FK_TRY(spread_any(p, precision, o, n, x, y, n_targets, true, grid, flags, st, scr));
+  if (tm) tm->mark();
+  const double inv_n = 1.0 / static_cast<double>(n);
+  FK_TRY(modes_any(p, precision, grid, 0, 1, 2 * m, corr, inv_n, T, st, scr));
+  if (n_targets > 0) FK_TRY(modes_any(p, precision, grid, 1, n_targets, m, corr, inv_n, b, st, scr));
+  if (tm) tm->mark();
+  return FK_OK;
+}
+
+}  // namespace fk
+
+using namespace fk;
+
+extern "C" {
+
+void fk_default_opts(fk_opts* o) {
+  if (!o) return;
+  o->solver = FK_SOLVER_AUTO;
+  o->cg_tol = 1e-13;
+  o->cg_maxit = 1000;
+  o->refine_steps = 1;
+  o->sobolev_c0 = 1.0;
+  o->upsampfac = 1.9;
+  o->spread = FK_SPREAD_AUTO;
+  o->deterministic = 0;
+}
+
+const char* fk_last_error(void) { return g_err.c_str(); }
+
+const char* fk_version(void) { return "fk 0.1 (sm_103a)"; }
+
+size_t fk_workspace_bytes(int d, int m, int64_t n, int n_ch, double eps, int precision) {
+  (void)n;
+  (void)precision;
+  EsPlan p;
+  if (make_es_plan(d, 2 * m, eps, 1.9, &p) != FK_OK) return 0;
+  const int64_t G = ipow(p.N, d);
+  const int64_t D = ipow(2 * m + 1, d);
+  size_t bytes = sizeof(double) * G * (n_ch + 1);          // grids
+  bytes += sizeof(double) * 2 * G * (n_ch + 1);            // FFT intermediates (upper bound)
+  bytes += sizeof(double) * 2 * ipow(4 * m + 1, d);        // T
+  bytes += sizeof(double) * 2 * D * D;                     // dense system (Cholesky route)
+  bytes += sizeof(double) * 2 * D * 8 * (n_ch + 1);        // CG vectors
+  bytes += 64u << 20;                                      // binning buffers
+  return bytes;
+}
+
+fk_status fk_type1(int d, int64_t n, const void* x, const void* c, int n_ch, int kmax, double eps, int precision,
+                   double* out, void* stream) {
+  clear_error();
+  FK_TRY(check_common(d, n, 0, eps, precision));
+  if (kmax < 0 || n_ch < 1 || !x || !c || !out) return set_error(FK_EINVAL, "bad type-1 arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const fk_opts o = resolve_opts(nullptr);
+  Scratch scr(st);
+  Flags fl(st);
+  FK_TRY(fl.init(scr));
+  EsPlan p;
+  FK_TRY(make_es_plan(d, kmax, eps, o.upsampfac, &p));
+  double *grid, *corr;
+  FK_TRY(scr.alloc(&grid, ipow(p.N, d) * n_ch));
+  FK_TRY(scr.alloc(&corr, 2 * static_cast<size_t>(kmax) + 1));
+  FK_TRY(es_correction(p, corr, st));
+  FK_TRY(spread_any(p, precision, o, n, x, c, n_ch, false, grid, fl.dev, st, scr));
+  FK_TRY(modes_any(p, precision, grid, 0, n_ch, kmax, corr, 1.0, out, st, scr));
+  return fl.check();
+}
+
+fk_status fk_type2(int d, int kmax, const double* coef, int n_sets, int64_t n, const void* x, double eps,
+                   int precision, double* out, void* stream) {
+  clear_error();
+  FK_TRY(check_common(d, n, 0, eps, precision));
+  if (kmax < 0 || n_sets < 1 || !x || !coef || !out) return set_error(FK_EINVAL, "bad type-2 arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const fk_opts o = resolve_opts(nullptr);
+  Scratch scr(st);
+  Flags fl(st);
+  FK_TRY(fl.init(scr));
+  EsPlan p;
+  FK_TRY(make_es_plan(d, kmax, eps, o.upsampfac, &p));
+  double* corr;
+  FK_TRY(scr.alloc(&corr, 2 * static_cast<size_t>(kmax) + 1));
+  FK_TRY(es_correction(p, corr, st));
+  if (precision == FK_FP64)
+    FK_TRY(type2_eval<double>(p, kmax, coef, n_sets, n, static_cast<const double*>(x), corr, out, fl.dev, st, scr));
+  else
+    FK_TRY(type2_eval<float>(p, kmax, coef, n_sets, n, static_cast<const float*>(x), corr, out, fl.dev, st, scr));
+  return fl.check();
+}
+
+fk_status fk_build_system(int d, int64_t n, const void* x, const void* y, int n_targets, int m, double eps,
+                          int precision, const fk_opts* opts, double* T, double* b, void* stream, fk_report* rep) {
+  clear_error();
+  FK_TRY(check_common(d, n, m, eps, precision));
+  if (!x || !T || (n_targets > 0 && (!y || !b)) || n_targets < 0)
+    return set_error(FK_EINVAL, "bad build_system arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const fk_opts o = resolve_opts(opts);
+  Scratch scr(st);
+  Flags fl(st);
+  FK_TRY(fl.init(scr));
+  Timer tm(st, rep != nullptr);
+  tm.mark();
+  EsPlan p;
+  FK_TRY(build_system(d, n, x, y, n_targets, m, eps, precision, o, T, b, st, scr, fl.dev, &p, &tm));
+  FK_TRY(fl.check());
+  if (rep) {
+    *rep = fk_report{};
+    rep->ms_spread = tm.ms(1, 2);
+    rep->ms_fft = tm.ms(2, 3);
+    rep->ms_total = tm.ms(0, 3);
+    rep->n_used = n;
+    rep->fine_grid = p.N;
+    rep->kernel_width = p.w;
+  }
+  return FK_OK;
+}
+
+fk_status fk_penalty_weights(int d, int m, int penalty, double s, double c0, const double* lambdas, int n_lambda,
+                             double mu, int n_terms, const int* alpha, const double* a, double* W, void* stream) {
+  clear_error();
+  if (d < 1 || d > 3 || m < 0 || n_lambda < 1 || !lambdas || !W) return set_error(FK_EINVAL, "bad penalty arguments");
+  if (n_terms > 0 && (!alpha || !a)) return set_error(FK_EINVAL, "PDE terms need alpha and a");
+  if (penalty != FK_PEN_SOBOLEV && penalty != FK_PEN_LOWBIAS) return set_error(FK_EINVAL, "unknown penalty");
+  if (s < 0) return set_error(FK_EINVAL, "s < 0");
+  return penalty_weights(d, m, penalty, s, c0, lambdas, n_lambda, mu, n_terms, alpha, a, W,
+                         static_cast<cudaStream_t>(stream));
+}
+
+fk_status fk_solve(int d, int m, const double* T, const double* W, int n_w, const double* rhs, int n_rhs,
+                   const fk_opts* opts, double* sol, void* stream, fk_report* rep) {
+  clear_error();
+  if (d < 1 || d > 2 || m < 0 || n_w < 1 || n_rhs < 1 || !T || !W || !rhs || !sol)
+    return set_error(FK_EINVAL, "bad solve arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const fk_opts o = resolve_opts(opts);
+  Scratch scr(st);
+  Flags fl(st);
+  FK_TRY(fl.init(scr));
+  int iters = 0;
+  double rr = 0;
+  FK_TRY(solve_system(d, m, T, W, n_w, rhs, n_rhs, o, sol, st, scr, fl.dev, &iters, &rr));
+  FK_TRY(fl.check());
+  if (rep) {
+    *rep = fk_report{};
+    rep->cg_iters = iters;
+    rep->rel_residual = rr;
+  }
+  return FK_OK;
+}
+
+static fk_status fit_common(int d, int64_t n, const void* x, const void* y, int n_targets, int m,
+                            int penalty, double s, const double* lambdas, int n_lambda, double mu, int n_terms,
+                            const int* alpha, const double* a, double eps, int precision, const fk_opts* opts,
+                            double* theta, void* stream, fk_report* rep) {
+  FK_TRY(check_common(d, n, m, eps, precision));
+  if (!x || !y || !theta || !lambdas || n_targets < 1 || n_lambda < 1)
+    return set_error(FK_EINVAL, "bad fit arguments");
+  for (int i = 0; i < n_lambda; ++i)
+    if (!(lambdas[i] >= 0.0)) return set_error(FK_EINVAL, "lambda[%d] = %g < 0", i, lambdas[i]);
+  if (s < 0) return set_error(FK_EINVAL, "s < 0");
+  if (mu < 0) return set_error(FK_EINVAL, "mu < 0");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const fk_opts o = resolve_opts(opts);
+  Scratch scr(st);
+  Flags fl(st);
+  FK_TRY(fl.init(scr));
+  Timer tm(st, rep != nullptr);
+  tm.mark();
+  const int64_t D = ipow(2 * m + 1, d), M2 = ipow(4 * m + 1, d);
+  double *T, *b, *W;
+  FK_TRY(scr.alloc(&T, 2 * M2));
+  FK_TRY(scr.alloc(&b, 2 * D * n_targets));
+  FK_TRY(scr.alloc(&W, D * n_lambda));
+  EsPlan p;
+  FK_TRY(build_system(d, n, x, y, n_targets, m, eps, precision, o, T, b, st, scr, fl.dev, &p, &tm));
+  FK_TRY(penalty_weights(d, m, penalty, s, o.sobolev_c0, lambdas, n_lambda, mu, n_terms, alpha, a, W, st));
+  int iters = 0;
+  double rr = 0;
+  FK_TRY(solve_system(d, m, T, W, n_lambda, b, n_targets, o, theta, st, scr, fl.dev, &iters, &rr));
+  tm.mark();
+  FK_TRY(fl.check());
+  if (rep) {
+    *rep = fk_report{};
+    rep->ms_spread = tm.ms(1, 2);
+    rep->ms_fft = tm.ms(2, 3);
+    rep->ms_solve = tm.ms(3, 4);
+    rep->ms_total = tm.ms(0, 4);
+    rep->cg_iters = iters;
+    rep->rel_residual = rr;
+    rep->n_used = n;
+    rep->fine_grid = p.N;
+    rep->kernel_width = p.w;
+  }
+  return FK_OK;
+}
+
+fk_status fk_fit_sobolev(int d, int64_t n, const void* x, const void* y, int n_targets, int m, double s,
+                         int penalty, const double* lambdas, int n_lambda, double eps, int precision,
+                         const fk_opts* opts, double* theta, void* stream, fk_report* rep) {
+  clear_error();
+  if (penalty != FK_PEN_SOBOLEV && penalty != FK_PEN_LOWBIAS) return set_error(FK_EINVAL, "unknown penalty");
+  return fit_common(d, n, x, y, n_targets, m, penalty, s, lambdas, n_lambda, 0.0, 0, nullptr, nullptr, eps,
+                    precision, opts, theta, stream, rep);
+}
+
+fk_status fk_fit_pik(int d, int64_t n, const void* x, const void* y, int n_targets, int m, double s, double lambda,
+                     double mu, int n_terms, const int* alpha, const double* a, double eps, int precision,
+                     const fk_opts* opts, double* theta, void* stream, fk_report* rep) {
+  clear_error();
+  if (n_terms < 0 || n_terms > 16 || (n_terms > 0 && (!alpha || !a)))
+    return set_error(FK_EINVAL, "bad PDE operator arguments");
+  return fit_common(d, n, x, y, n_targets, m, FK_PEN_SOBOLEV, s, &lambda, 1, mu, n_terms, alpha, a, eps, precision,
+                    opts, theta, stream, rep);
+}
+
+fk_status fk_fit_additive(int d, int64_t n, const void* x, const void* y, int n_targets, int m,
+                          const double* lambdas, int n_lambda, double eps, int precision, const fk_opts* opts,
+                          double* theta, void* stream, fk_report* rep) {
+  clear_error();
+  (void)d; (void)n; (void)x; (void)y; (void)n_targets; (void)m; (void)lambdas; (void)n_lambda; (void)eps;
+  (void)precision; (void)opts; (void)theta; (void)stream; (void)rep;
+  return set_error(FK_EINVAL, "fk_fit_additive: not built yet");
+}
+
+fk_status fk_predict(int additive, int d, int m, const double* theta, int n_sets, int64_t n_q, const void* xq,
+                     double eps, int precision, double* f, void* stream) {
+  clear_error();
+  if (additive) return set_error(FK_EINVAL, "additive prediction: not built yet");
+  return fk_type2(d, m, theta, n_sets, n_q, xq, eps, precision, f, stream);
+}
+
+fk_status fk_hypergrad(int d, int64_t n, const void* x, int64_t n_v, const void* xv, const void* yv, int m,
+                       const double* T, const double* W, const double* theta, double eps, int precision,
+                       const fk_opts* opts, double* loss, double* dW, double* dY, void* stream) {
+  clear_error();
+  (void)d; (void)n; (void)x; (void)n_v; (void)xv; (void)yv; (void)m; (void)T; (void)W; (void)theta; (void)eps;
+  (void)precision; (void)opts; (void)loss; (void)dW; (void)dY; (void)stream;
+  return set_error(FK_EINVAL, "fk_hypergrad: not built yet");
+}
+
+}  // extern "C"

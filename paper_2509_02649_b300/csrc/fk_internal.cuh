@@ -1,0 +1,156 @@
+// Internal declarations shared by the CUDA translation units of libfk.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "../../include/fk.h"
+
+namespace fk {
+
+// ------------------------------------------------------------------ errors
+fk_status set_error(fk_status st, const char* fmt, ...);
+void clear_error();
+
+#define FK_CUDA(call)                                                          \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess)                                                     \
+      return ::fk::set_error(FK_ECUDA, "%s failed: %s (%s:%d)", #call,         \
+                             cudaGetErrorString(e_), __FILE__, __LINE__);      \
+  } while (0)
+
+#define FK_TRY(expr)                    \
+  do {                                  \
+    fk_status s_ = (expr);              \
+    if (s_ != FK_OK) return s_;         \
+  } while (0)
+
+// Device-side error flags (bits), read back by the host after a call.
+enum : unsigned {
+  FLAG_RANGE = 1u,      // a point outside [-3 pi, 3 pi)
+  FLAG_NOTPD = 2u,      // Cholesky pivot <= 0
+  FLAG_INTERNAL = 4u,   // an index check failed
+  FLAG_TIMEOUT = 8u,    // a bounded wait gave up
+};
+
+// ------------------------------------------------------------------ complex
+struct cd { double x, y; };
+__host__ __device__ inline cd cmk(double a, double b) { return cd{a, b}; }
+__host__ __device__ inline cd cadd(cd a, cd b) { return cd{a.x + b.x, a.y + b.y}; }
+__host__ __device__ inline cd csub(cd a, cd b) { return cd{a.x - b.x, a.y - b.y}; }
+__host__ __device__ inline cd cmul(cd a, cd b) { return cd{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__host__ __device__ inline cd cconjmul(cd a, cd b) { return cd{a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x}; }  // conj(a)*b
+__host__ __device__ inline cd cscale(cd a, double s) { return cd{a.x * s, a.y * s}; }
+__host__ __device__ inline cd cconj(cd a) { return cd{a.x, -a.y}; }
+
+template <typename R> struct cplx { R x, y; };
+
+// ------------------------------------------------------------------ kernel plan
+// Exponential-of-semicircle kernel phi(z) = exp(beta (sqrt(1 - z^2) - 1)), |z| < 1,
+// spread over w grid nodes of spacing h = 2 pi / N (support radius w h / 2).
+struct EsPlan {
+  int d = 1;
+  int N = 0;         // fine grid nodes per dimension (power of two)
+  int w = 0;         // taps per dimension
+  double beta = 0;   // ES shape
+  double sigma = 0;  // N / (2 kmax + 1)
+  int kmax = 0;      // largest |k| extracted per dimension
+};
+
+// Chooses N (power of two >= upsampfac * (2 kmax + 1), at least 2 w) and w, beta
+// for the requested tolerance.
+fk_status make_es_plan(int d, int kmax, double eps, double upsampfac, EsPlan* p);
+
+// ------------------------------------------------------------------ workspace
+// Stream-ordered scratch allocation tracked for release at scope exit.
+struct Scratch {
+  cudaStream_t st;
+  void* ptrs[64];
+  int count = 0;
+  explicit Scratch(cudaStream_t s) : st(s) {}
+  ~Scratch() { release(); }
+  void release() {
+    for (int i = count - 1; i >= 0; --i) cudaFreeAsync(ptrs[i], st);
+    count = 0;
+  }
+  template <typename T>
+  fk_status alloc(T** p, size_t elems) {
+    if (count >= 64) return set_error(FK_EINTERNAL, "scratch table full");
+    size_t bytes = elems * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, bytes, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(FK_ENOMEM, "cudaMallocAsync(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    ptrs[count++] = q;
+    *p = static_cast<T*>(q);
+    return FK_OK;
+  }
+};
+
+inline int grid_for(int64_t work, int block, int cap = 148 * 32) {
+  int64_t g = (work + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return static_cast<int>(g);
+}
+
+// ------------------------------------------------------------------ component entry points
+// (host functions enqueueing kernels on `st`; all pointers device)
+
+// ES Fourier-transform correction factors corr[j + kmax] = (-1)^j h / Psi_hat(j),
+// j = -kmax..kmax, in fp64 (Gauss-Legendre quadrature on the device).
+fk_status es_correction(const EsPlan& p, double* corr, cudaStream_t st);
+
+// Spreading: grid[c][node] += sum_i str_c(i) * prod_l psi(node_l - u_l(i)),
+// ones channel optional (c = 0 when with_ones).  grid: fp64, n_ch x N^d, zeroed inside.
+// R = float (FK_MIXED inputs) or double (FK_FP64 inputs).
+template <typename R>
+fk_status spread_atomic(const EsPlan& p, int64_t n, const R* x, const R* y, int n_y,
+                        bool with_ones, double* grid, unsigned* flags, cudaStream_t st);
+
+// Binned register-accumulation spreading (fp32, d = 1 or 2, ones + n_y channels).
+fk_status spread_binned(const EsPlan& p, int64_t n, const float* x, const float* y, int n_y,
+                        bool with_ones, double* grid, unsigned* flags, cudaStream_t st,
+                        Scratch& scratch);
+bool spread_binned_supported(const EsPlan& p, int n_ch);
+
+// Forward transform of real fp64 grids + deconvolution + extraction of the modes
+// |k|_inf <= kout (kout <= p.kmax) for channels [c0, c0 + nc), scaled by `scale`.
+// out: complex [nc][(2 kout + 1)^d].  FFT arithmetic in R.
+template <typename R>
+fk_status grid_to_modes(const EsPlan& p, const double* grid, int c0, int nc, int kout,
+                        const double* corr, double scale, double* out, cudaStream_t st,
+                        Scratch& scratch);
+
+// Type-2: coef [n_sets][(2 kmax_c + 1)^d] complex -> out [n_sets][n] = Re f(x_i).
+template <typename R>
+fk_status type2_eval(const EsPlan& p, int kmax_c, const double* coef, int n_sets, int64_t n,
+                     const R* x, const double* corr, double* out, unsigned* flags,
+                     cudaStream_t st, Scratch& scratch);
+
+// Penalty diagonals.
+fk_status penalty_weights(int d, int m, int penalty, double s, double c0, const double* lambdas,
+                          int n_lambda, double mu, int n_terms, const int* alpha, const double* a,
+                          double* W, cudaStream_t st);
+
+// Dense / CG solves of (Toep(T) + diag W_l) X = B.
+fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, const double* rhs,
+                       int n_rhs, const fk_opts& o, double* sol, cudaStream_t st,
+                       Scratch& scratch, unsigned* flags, int* cg_iters, double* rel_res);
+
+// FFT primitives (complex, in place on contiguous lines of length N, batched).
+template <typename R>
+fk_status fft_lines(cplx<R>* data, int N, int64_t n_lines, int64_t line_stride, int64_t elem_stride,
+                    int sign, const double* tw, cudaStream_t st);
+fk_status fft_twiddles(int N, double* tw, cudaStream_t st);  // tw[2t..2t+1] = e^{-2 pi i t / N}
+
+}  // namespace fk

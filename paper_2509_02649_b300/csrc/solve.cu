@@ -1,0 +1,703 @@
+// Penalty diagonals, Toeplitz assembly and the FP64 solves of
+//   (Toep(T) + diag W) theta = b                                   (Eq. 2, Sec. 2.3)
+// Dense route: blocked right-looking complex Cholesky A = L L^H (non-positive
+// pivot -> FLAG_NOTPD), triangular solves, iterative refinement.
+// Iterative route: Jacobi-preconditioned conjugate gradients whose Toeplitz
+// matvec runs through a circulant embedding and FFTs (Sec. 2.3, matvec via FFT),
+// batched over every (penalty, right-hand side) pair.
+#include "fk_internal.cuh"
+
+#include <vector>
+
+namespace fk {
+
+// ---------------------------------------------------------------- penalty (Sec. 3.1, 3.2, 4)
+struct PdeTerms {
+  int n_terms;
+  int alpha[16][3];
+  double a[16];
+};
+
+__device__ inline void mode_of(int64_t q, int d, int m, int* k) {
+  const int K = 2 * m + 1;
+  for (int l = d - 1; l >= 0; --l) {
+    k[l] = static_cast<int>(q % K) - m;
+    q /= K;
+  }
+}
+
+__global__ void k_penalty(int d, int m, int penalty, double s, double c0, const double* lambdas, int n_lambda,
+                          double mu, PdeTerms pde, double* W) {
+  const int K = 2 * m + 1;
+  int64_t D = 1;
+  for (int l = 0; l < d; ++l) D *= K;
+  const int64_t total = D * n_lambda;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int li = static_cast<int>(t / D);
+    const int64_t q = t - li * D;
+    int k[3] = {0, 0, 0};
+    mode_of(q, d, m, k);
+    const double lam = lambdas[li];
+    double wv;
+    if (penalty == FK_PEN_LOWBIAS) {
+      wv = lam;
+    } else {
+      double r2 = 0.0;
+      for (int l = 0; l < d; ++l) r2 += static_cast<double>(k[l]) * k[l];
+      const double pw = (r2 > 0.0) ? pow(r2, s) : 0.0;
+      wv = lam * (c0 + pw);
+    }
+    if (pde.n_terms > 0) {
+      // P(ik) = sum_t a_t prod_l (i k_l)^alpha_tl
+      double pre = 0.0, pim = 0.0;
+      for (int tt = 0; tt < pde.n_terms; ++tt) {
+        double tre = pde.a[tt], tim = 0.0;
+        for (int l = 0; l < d; ++l) {
+          for (int e = 0; e < pde.alpha[tt][l]; ++e) {  // multiply by i k_l
+            const double nre = -tim * k[l];
+            const double nim = tre * k[l];
+            tre = nre;
+            tim = nim;
+          }
+        }
+        pre += tre;
+        pim += tim;
+      }
+      wv += mu * (pre * pre + pim * pim);
+    }
+    W[t] = wv;
+  }
+}
+
+fk_status penalty_weights(int d, int m, int penalty, double s, double c0, const double* lambdas, int n_lambda,
+                          double mu, int n_terms, const int* alpha, const double* a, double* W, cudaStream_t st) {
+  if (n_terms < 0 || n_terms > 16) return set_error(FK_EINVAL, "n_terms must be in [0, 16]");
+  if (d < 1 || d > 3) return set_error(FK_EINVAL, "d must be 1..3");
+  PdeTerms pde{};
+  pde.n_terms = n_terms;
+  for (int t = 0; t < n_terms; ++t) {
+    pde.a[t] = a[t];
+    for (int l = 0; l < d; ++l) {
+      if (alpha[t * d + l] < 0 || alpha[t * d + l] > 32) return set_error(FK_EINVAL, "alpha out of range");
+      pde.alpha[t][l] = alpha[t * d + l];
+    }
+  }
+  double* dl = nullptr;
+  FK_CUDA(cudaMallocAsync(&dl, sizeof(double) * n_lambda, st));
+  cudaError_t e = cudaMemcpyAsync(dl, lambdas, sizeof(double) * n_lambda, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    int64_t D = 1;
+    for (int l = 0; l < d; ++l) D *= (2 * m + 1);
+    k_penalty<<<grid_for(D * n_lambda, 256), 256, 0, st>>>(d, m, penalty, s, c0, dl, n_lambda, mu, pde, W);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(dl, st);
+  if (e != cudaSuccess) return set_error(FK_ECUDA, "penalty: %s", cudaGetErrorString(e));
+  return FK_OK;
+}
+
+// ---------------------------------------------------------------- dense assembly
+// A[r][c] = T_{k_r - k_c} + delta_rc W[r]
+__global__ void k_assemble(int d, int m, const double* T, const double* W, double* A) {
+  const int K = 2 * m + 1, K2 = 4 * m + 1;
+  int64_t D = 1;
+  for (int l = 0; l < d; ++l) D *= K;
+  const int64_t total = D * D;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = t / D, c = t - (t / D) * D;
+    int kr[3] = {0, 0, 0}, kc[3] = {0, 0, 0};
+    mode_of(r, d, m, kr);
+    mode_of(c, d, m, kc);
+    int64_t idx = 0;
+    for (int l = 0; l < d; ++l) idx = idx * K2 + (kr[l] - kc[l] + 2 * m);
+    double re = T[2 * idx], im = T[2 * idx + 1];
+    if (r == c) re += W[r];
+    A[2 * t] = re;
+    A[2 * t + 1] = im;
+  }
+}
+
+// ---------------------------------------------------------------- Cholesky
+constexpr int NB = 32;
+
+__global__ void k_chol_diag(double* A, int64_t D, int kb, int nb, unsigned* flags) {
+  __shared__ cd s[NB][NB + 1];
+  const int tid = threadIdx.x;
+  for (int t = tid; t < nb * nb; t += blockDim.x) {
+    const int i = t / nb, j = t % nb;
+    const double* p = A + 2 * ((kb + i) * D + (kb + j));
+    s[i][j] = cd{p[0], p[1]};
+  }
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    if (tid == 0) {
+      double piv = s[j][j].x;
+      if (!(piv > 0.0)) {
+        atomicOr(flags, FLAG_NOTPD);
+        piv = 1.0;
+      }
+      s[j][j] = cd{sqrt(piv), 0.0};
+    }
+    __syncthreads();
+    const double inv = 1.0 / s[j][j].x;
+    for (int i = j + 1 + tid; i < nb; i += blockDim.x) s[i][j] = cscale(s[i][j], inv);
+    __syncthreads();
+    for (int t = tid; t < nb * nb; t += blockDim.x) {
+      const int i = t / nb, k = t % nb;
+      if (i > j && k > j && k <= i) s[i][k] = csub(s[i][k], cmul(s[i][j], cconj(s[k][j])));
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < nb * nb; t += blockDim.x) {
+    const int i = t / nb, j = t % nb;
+    double* p = A + 2 * ((kb + i) * D + (kb + j));
+    if (j <= i) {
+      p[0] = s[i][j].x;
+      p[1] = s[i][j].y;
+    } else {
+      p[0] = 0.0;
+      p[1] = 0.0;
+    }
+  }
+}
+
+// rows i >= kb + nb of the panel: x L11^H = a  =>  x_j = (a_j - sum_{p<j} x_p conj(L11[j][p])) / L11[j][j]
+__global__ void k_chol_panel(double* A, int64_t D, int kb, int nb) {
+  __shared__ cd L[NB][NB + 1];
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int i = t / nb, j = t % nb;
+    const double* p = A + 2 * ((kb + i) * D + (kb + j));
+    L[i][j] = cd{p[0], p[1]};
+  }
+  __syncthreads();
+  const int64_t row = kb + nb + blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (row >= D) return;
+  double* a = A + 2 * (row * D + kb);
+  cd x[NB];
+  for (int j = 0; j < nb; ++j) {
+    cd v = cd{a[2 * j], a[2 * j + 1]};
+    for (int p = 0; p < j; ++p) v = csub(v, cmul(x[p], cconj(L[j][p])));
+    x[j] = cscale(v, 1.0 / L[j][j].x);
+  }
+  for (int j = 0; j < nb; ++j) {
+    a[2 * j] = x[j].x;
+    a[2 * j + 1] = x[j].y;
+  }
+}
+
+// A22[i][j] -= sum_p L21[i][p] conj(L21[j][p]),  lower triangle, 32x32 tiles
+__global__ void k_chol_update(double* A, int64_t D, int kb, int nb) {
+  const int64_t base = kb + nb;
+  const int ti = blockIdx.y, tj = blockIdx.x;
+  if (tj > ti) return;
+  const int64_t i0 = base + static_cast<int64_t>(ti) * 32, j0 = base + static_cast<int64_t>(tj) * 32;
+  __shared__ cd Li[32][NB + 1], Lj[32][NB + 1];
+  for (int t = threadIdx.x; t < 32 * nb; t += blockDim.x) {
+    const int r = t / nb, p = t % nb;
+    const int64_t gi = i0 + r, gj = j0 + r;
+    Li[r][p] = (gi < D) ? cd{A[2 * (gi * D + kb + p)], A[2 * (gi * D + kb + p) + 1]} : cd{0, 0};
+    Lj[r][p] = (gj < D) ? cd{A[2 * (gj * D + kb + p)], A[2 * (gj * D + kb + p) + 1]} : cd{0, 0};
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+    const int r = t / 32, c = t % 32;
+    const int64_t gi = i0 + r, gj = j0 + c;
+    if (gi >= D || gj >= D || gj > gi) continue;
+    cd acc = cd{0, 0};
+    for (int p = 0; p < nb; ++p) acc = cadd(acc, cmul(Li[r][p], cconj(Lj[c][p])));
+    double* q = A + 2 * (gi * D + gj);
+    q[0] -= acc.x;
+    q[1] -= acc.y;
+  }
+}
+
+static fk_status cholesky(double* A, int64_t D, unsigned* flags, cudaStream_t st) {
+  for (int kb = 0; kb < D; kb += NB) {
+    const int nb = static_cast<int>(std::min<int64_t>(NB, D - kb));
+    k_chol_diag<<<1, 256, 0, st>>>(A, D, kb, nb, flags);
+    const int64_t rest = D - kb - nb;
+    if (rest > 0) {
+      k_chol_panel<<<static_cast<int>((rest + 127) / 128), 128, 0, st>>>(A, D, kb, nb);
+      const int nt = static_cast<int>((rest + 31) / 32);
+      k_chol_update<<<dim3(nt, nt), 256, 0, st>>>(A, D, kb, nb);
+    }
+    FK_CUDA(cudaGetLastError());
+  }
+  return FK_OK;
+}
+
+// Triangular solves for RB right-hand sides per CTA; X holds B on entry, solution on exit.
+// forward:  y_i = (b_i - sum_{j<i} L_ij y_j) / L_ii       (row i of L, contiguous)
+// backward: x_j = y_j / L_jj;  y_i -= conj(L_ji) x_j, i<j  (row j of L, contiguous)
+constexpr int RB = 8;
+__global__ void k_trisolve(const double* L, int64_t D, double* X, int n_rhs) {
+  const int r0 = blockIdx.x * RB;
+  const int nr = min(RB, n_rhs - r0);
+  __shared__ cd red[RB][32];
+  __shared__ cd val[RB];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  // forward
+  for (int64_t i = 0; i < D; ++i) {
+    cd acc[RB];
+    for (int r = 0; r < RB; ++r) acc[r] = cd{0, 0};
+    for (int64_t j = tid; j < i; j += blockDim.x) {
+      const cd l = cd{L[2 * (i * D + j)], L[2 * (i * D + j) + 1]};
+      for (int r = 0; r < nr; ++r) {
+        const double* y = X + 2 * ((r0 + r) * D + j);
+        acc[r] = cadd(acc[r], cmul(l, cd{y[0], y[1]}));
+      }
+    }
+    for (int r = 0; r < nr; ++r) {
+      for (int o = 16; o > 0; o >>= 1) {
+        acc[r].x += __shfl_down_sync(0xffffffffu, acc[r].x, o);
+        acc[r].y += __shfl_down_sync(0xffffffffu, acc[r].y, o);
+      }
+      if (lane == 0) red[r][warp] = acc[r];
+    }
+    __syncthreads();
+    if (tid < nr) {
+      cd s = cd{0, 0};
+      for (int w = 0; w < nw; ++w) s = cadd(s, red[tid][w]);
+      double* y = X + 2 * ((r0 + tid) * D + i);
+      const double lii = L[2 * (i * D + i)];
+      y[0] = (y[0] - s.x) / lii;
+      y[1] = (y[1] - s.y) / lii;
+    }
+    __syncthreads();
+  }
+  // backward
+  for (int64_t j = D - 1; j >= 0; --j) {
+    if (tid < nr) {
+      double* y = X + 2 * ((r0 + tid) * D + j);
+      const double ljj = L[2 * (j * D + j)];
+      y[0] /= ljj;
+      y[1] /= ljj;
+      val[tid] = cd{y[0], y[1]};
+    }
+    __syncthreads();
+    for (int64_t i = tid; i < j; i += blockDim.x) {
+      const cd l = cd{L[2 * (j * D + i)], -L[2 * (j * D + i) + 1]};
+      for (int r = 0; r < nr; ++r) {
+        double* y = X + 2 * ((r0 + r) * D + i);
+        const cd v = cmul(l, val[r]);
+        y[0] -= v.x;
+        y[1] -= v.y;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// R = B - A X  (dense Hermitian A given by T, W) for refinement; one CTA per (rhs, row block)
+__global__ void k_residual_dense(int d, int m, const double* T, const double* W, const double* X,
+                                 const double* B, double* R, int n_rhs) {
+  const int K = 2 * m + 1, K2 = 4 * m + 1;
+  int64_t D = 1;
+  for (int l = 0; l < d; ++l) D *= K;
+  const int64_t total = D * n_rhs;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t rr = t / D, row = t - (t / D) * D;
+    int kr[3] = {0, 0, 0};
+    mode_of(row, d, m, kr);
+    cd acc = cd{B[2 * t], B[2 * t + 1]};
+    const double* x = X + 2 * rr * D;
+    for (int64_t c = 0; c < D; ++c) {
+      int kc[3] = {0, 0, 0};
+      mode_of(c, d, m, kc);
+      int64_t idx = 0;
+      for (int l = 0; l < d; ++l) idx = idx * K2 + (kr[l] - kc[l] + 2 * m);
+      cd a = cd{T[2 * idx], T[2 * idx + 1]};
+      if (c == row) a.x += W[row];
+      acc = csub(acc, cmul(a, cd{x[2 * c], x[2 * c + 1]}));
+    }
+    R[2 * t] = acc.x;
+    R[2 * t + 1] = acc.y;
+  }
+}
+
+__global__ void k_axpy_c(int64_t n2, const double* dx, double* x) {
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < n2;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    x[t] += dx[t];
+}
+
+// ---------------------------------------------------------------- CG with FFT Toeplitz matvec
+// Circulant of side Lc >= 4m + 1: c[(j mod Lc)] = T_j for |j|_inf <= 2m.
+__global__ void k_circ_embed(int d, int m, int Lc, const double* T, cplx<double>* c) {
+  const int K2 = 4 * m + 1;
+  int64_t M2 = 1;
+  for (int l = 0; l < d; ++l) M2 *= K2;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < M2;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int64_t q = t, node = 0, mul = 1;
+    int jj[3];
+    for (int l = d - 1; l >= 0; --l) {
+      jj[l] = static_cast<int>(q % K2) - 2 * m;
+      q /= K2;
+    }
+    for (int l = d - 1; l >= 0; --l) {
+      node += mul * ((jj[l] + Lc) % Lc);
+      mul *= Lc;
+    }
+    c[node].x = T[2 * t];
+    c[node].y = T[2 * t + 1];
+  }
+}
+
+// pad: buf[s][node(q)] = v[s][q] (q over D modes at node q_l = k_l + m), zeros elsewhere (buffer pre-zeroed)
+__global__ void k_pad(int d, int m, int Lc, int nsys, const double* v, cplx<double>* buf) {
+  const int K = 2 * m + 1;
+  int64_t D = 1, LL = 1;
+  for (int l = 0; l < d; ++l) { D *= K; LL *= Lc; }
+  const int64_t total = D * nsys;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t s = t / D;
+    int64_t q = t - s * D, node = 0, mul = 1;
+    for (int l = d - 1; l >= 0; --l) {
+      node += mul * (q % K);
+      q /= K;
+      mul *= Lc;
+    }
+    buf[s * LL + node].x = v[2 * t];
+    buf[s * LL + node].y = v[2 * t + 1];
+  }
+}
+
+__global__ void k_pointwise(int64_t LL, int nsys, const cplx<double>* ch, cplx<double>* buf) {
+  const int64_t total = LL * nsys;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const cplx<double> a = ch[t % LL], b = buf[t];
+    buf[t].x = a.x * b.x - a.y * b.y;
+    buf[t].y = a.x * b.y + a.y * b.x;
+  }
+}
+
+// q[s] = extract(buf[s]) / LL + W[l(s)] * p[s];  systems s = l * n_rhs + r
+__global__ void k_extract_addw(int d, int m, int Lc, int nsys, int n_rhs, const cplx<double>* buf, const double* W,
+                               const double* p, double* q) {
+  const int K = 2 * m + 1;
+  int64_t D = 1, LL = 1;
+  for (int l = 0; l < d; ++l) { D *= K; LL *= Lc; }
+  const double inv = 1.0 / static_cast<double>(LL);
+  const int64_t total = D * nsys;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t s = t / D;
+    const int64_t qi = t - s * D;
+    int64_t qq = qi, node = 0, mul = 1;
+    for (int l = d - 1; l >= 0; --l) {
+      node += mul * (qq % K);
+      qq /= K;
+      mul *= Lc;
+    }
+    const double w = W[(s / n_rhs) * D + qi];
+    const cplx<double> v = buf[s * LL + node];
+    q[2 * t] = v.x * inv + w * p[2 * t];
+    q[2 * t + 1] = v.y * inv + w * p[2 * t + 1];
+  }
+}
+
+// per-system reductions: out[s] = sum_k Re(conj(a_k) b_k)  (optionally scaled by invdiag)
+__global__ void k_dot(int64_t D, const double* a, const double* b, double* out) {
+  const int s = blockIdx.x;
+  const double* pa = a + 2 * s * D;
+  const double* pb = b + 2 * s * D;
+  double acc = 0.0;
+  for (int64_t k = threadIdx.x; k < D; k += blockDim.x) acc += pa[2 * k] * pb[2 * k] + pa[2 * k + 1] * pb[2 * k + 1];
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) out[s] = acc;
+  }
+}
+
+struct CgState {
+  double* rz;     // <r, z>
+  double* pq;     // <p, A p>
+  double* rr;     // <r, r>
+  double* bb;     // <b, b>
+  int* active;    // 1 while not converged
+};
+
+// x += alpha p; r -= alpha q; z = r / diag ; per-system alpha = rz / pq
+__global__ void k_cg_update_xr(int64_t D, int n_rhs, const double* W, double T0, CgState cs, const double* p,
+                               const double* q, double* x, double* r, double* z) {
+  const int s = blockIdx.y;
+  if (!cs.active[s]) return;
+  const double alpha = cs.rz[s] / cs.pq[s];
+  const int l = s / n_rhs;
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < D;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t o = 2 * (s * D + k);
+    x[o] += alpha * p[o];
+    x[o + 1] += alpha * p[o + 1];
+    r[o] -= alpha * q[o];
+    r[o + 1] -= alpha * q[o + 1];
+    const double inv = 1.0 / (T0 + W[l * D + k]);
+    z[o] = r[o] * inv;
+    z[o + 1] = r[o + 1] * inv;
+  }
+}
+
+// beta = rz_new / rz_old ; p = z + beta p ; update rz, convergence flags
+__global__ void k_cg_beta(int nsys, double tol2, CgState cs, double* rz_new) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys || !cs.active[s]) return;
+  if (cs.rr[s] <= tol2 * cs.bb[s]) {
+    cs.active[s] = 0;
+    return;
+  }
+  const double beta = rz_new[s] / cs.rz[s];
+  cs.rz[s] = rz_new[s];
+  rz_new[s] = beta;  // reuse as beta
+}
+
+__global__ void k_cg_update_p(int64_t D, CgState cs, const double* beta, const double* z, double* p) {
+  const int s = blockIdx.y;
+  if (!cs.active[s]) return;
+  const double b = beta[s];
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < D;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t o = 2 * (s * D + k);
+    p[o] = z[o] + b * p[o];
+    p[o + 1] = z[o + 1] + b * p[o + 1];
+  }
+}
+
+__global__ void k_cg_init(int64_t D, int n_rhs, int nsys, const double* W, double T0, const double* b, double* x,
+                          double* r, double* z, double* p) {
+  const int s = blockIdx.y;
+  const int l = s / n_rhs, rr = s % n_rhs;
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < D;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t o = 2 * (s * D + k), ob = 2 * (rr * D + k);
+    x[o] = 0.0;
+    x[o + 1] = 0.0;
+    r[o] = b[ob];
+    r[o + 1] = b[ob + 1];
+    const double inv = 1.0 / (T0 + W[l * D + k]);
+    z[o] = b[ob] * inv;
+    z[o + 1] = b[ob + 1] * inv;
+    p[o] = z[o];
+    p[o + 1] = z[o + 1];
+  }
+}
+
+__global__ void k_set_active(int nsys, int* active) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < nsys) active[s] = 1;
+}
+
+__global__ void k_count_active(int nsys, const int* active, int* count) {
+  __shared__ int c;
+  if (threadIdx.x == 0) c = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < nsys; s += blockDim.x)
+    if (active[s]) atomicAdd(&c, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) *count = c;
+}
+
+static int next_pow2i(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Toeplitz matvec q = Toep(T) v + W v for all systems (v, q: [nsys][D]).
+struct Circ {
+  int d, m, Lc;
+  int64_t LL, D;
+  cplx<double>* ch;   // FFT of the circulant
+  cplx<double>* buf;  // nsys * LL
+  double* tw;
+};
+
+static fk_status fft_nd(const Circ& c, int nsys, int sign, cudaStream_t st) {
+  if (c.d == 1) return fft_lines<double>(c.buf, c.Lc, nsys, c.Lc, 1, sign, c.tw, st);
+  if (c.d == 2) {
+    FK_TRY(fft_lines<double>(c.buf, c.Lc, static_cast<int64_t>(nsys) * c.Lc, c.Lc, 1, sign, c.tw, st));  // rows
+    for (int s = 0; s < nsys; ++s)
+      FK_TRY(fft_lines<double>(c.buf + s * c.LL, c.Lc, c.Lc, 1, c.Lc, sign, c.tw, st));  // columns
+    return FK_OK;
+  }
+  return set_error(FK_EINVAL, "CG: d = %d not built", c.d);
+}
+
+static fk_status matvec(const Circ& c, int nsys, int n_rhs, const double* W, const double* v, double* q,
+                        cudaStream_t st) {
+  FK_CUDA(cudaMemsetAsync(c.buf, 0, sizeof(cplx<double>) * c.LL * nsys, st));
+  k_pad<<<grid_for(c.D * nsys, 256), 256, 0, st>>>(c.d, c.m, c.Lc, nsys, v, c.buf);
+  FK_TRY(fft_nd(c, nsys, -1, st));
+  k_pointwise<<<grid_for(c.LL * nsys, 256), 256, 0, st>>>(c.LL, nsys, c.ch, c.buf);
+  FK_TRY(fft_nd(c, nsys, +1, st));
+  k_extract_addw<<<grid_for(c.D * nsys, 256), 256, 0, st>>>(c.d, c.m, c.Lc, nsys, n_rhs, c.buf, W, v, q);
+  FK_CUDA(cudaGetLastError());
+  return FK_OK;
+}
+
+// per system s: rr[s] = |b_{s % n_rhs} - q_s|^2, bb[s] = |b_{s % n_rhs}|^2
+__global__ void k_resid_norm(int64_t D, int n_rhs, const double* b, const double* q, double* rr, double* bb) {
+  const int s = blockIdx.x;
+  const double* pb = b + 2 * (s % n_rhs) * D;
+  const double* pq = q + 2 * s * D;
+  double a0 = 0.0, a1 = 0.0;
+  for (int64_t k = threadIdx.x; k < D; k += blockDim.x) {
+    const double er = pb[2 * k] - pq[2 * k], ei = pb[2 * k + 1] - pq[2 * k + 1];
+    a0 += er * er + ei * ei;
+    a1 += pb[2 * k] * pb[2 * k] + pb[2 * k + 1] * pb[2 * k + 1];
+  }
+  __shared__ double red[2][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_down_sync(0xffffffffu, a0, o);
+    a1 += __shfl_down_sync(0xffffffffu, a1, o);
+  }
+  if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = a0; red[1][threadIdx.x >> 5] = a1; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { s0 += red[0][w]; s1 += red[1][w]; }
+    rr[s] = s0;
+    bb[s] = s1;
+  }
+}
+
+static fk_status cg_solve(int d, int m, const double* T, const double* W, int n_w, const double* rhs, int n_rhs,
+                          const fk_opts& o, double* sol, cudaStream_t st, Scratch& scr, int* iters_out,
+                          double* relres_out) {
+  Circ c;
+  c.d = d;
+  c.m = m;
+  c.Lc = next_pow2i(4 * m + 1);
+  if (c.Lc < 2) c.Lc = 2;
+  c.LL = 1;
+  c.D = 1;
+  for (int l = 0; l < d; ++l) {
+    c.LL *= c.Lc;
+    c.D *= (2 * m + 1);
+  }
+  const int nsys = n_w * n_rhs;
+  const int64_t D = c.D;
+  FK_TRY(scr.alloc(&c.ch, c.LL));
+  FK_TRY(scr.alloc(&c.buf, c.LL * nsys));
+  FK_TRY(scr.alloc(&c.tw, 2 * static_cast<size_t>(c.Lc)));
+  FK_TRY(fft_twiddles(c.Lc, c.tw, st));
+  FK_CUDA(cudaMemsetAsync(c.ch, 0, sizeof(cplx<double>) * c.LL, st));
+  int64_t M2 = 1;
+  for (int l = 0; l < d; ++l) M2 *= (4 * m + 1);
+  k_circ_embed<<<grid_for(M2, 256), 256, 0, st>>>(d, m, c.Lc, T, c.ch);
+  FK_CUDA(cudaGetLastError());
+  {
+    Circ c1 = c;
+    c1.buf = c.ch;
+    FK_TRY(fft_nd(c1, 1, -1, st));
+  }
+  // T_0 (real part of the centre moment) for the Jacobi preconditioner
+  int64_t centre = 0;
+  for (int l = 0; l < d; ++l) centre = centre * (4 * m + 1) + 2 * m;
+  double T0 = 1.0;
+  FK_CUDA(cudaMemcpyAsync(&T0, T + 2 * centre, sizeof(double), cudaMemcpyDeviceToHost, st));
+  FK_CUDA(cudaStreamSynchronize(st));
+  if (!(T0 > 0.0)) T0 = 1.0;
+
+  double *r, *z, *p, *q, *scal;
+  int *active, *cnt;
+  FK_TRY(scr.alloc(&r, 2 * D * nsys));
+  FK_TRY(scr.alloc(&z, 2 * D * nsys));
+  FK_TRY(scr.alloc(&p, 2 * D * nsys));
+  FK_TRY(scr.alloc(&q, 2 * D * nsys));
+  FK_TRY(scr.alloc(&scal, 5 * static_cast<size_t>(nsys)));
+  FK_TRY(scr.alloc(&active, nsys));
+  FK_TRY(scr.alloc(&cnt, 1));
+  CgState cs{scal, scal + nsys, scal + 2 * nsys, scal + 3 * nsys, active};
+  double* rznew = scal + 4 * nsys;
+  double* x = sol;
+  const dim3 g2(static_cast<unsigned>(std::min<int64_t>((D + 255) / 256, 64)), nsys);
+  k_cg_init<<<g2, 256, 0, st>>>(D, n_rhs, nsys, W, T0, rhs, x, r, z, p);
+  k_set_active<<<(nsys + 255) / 256, 256, 0, st>>>(nsys, active);
+  k_dot<<<nsys, 256, 0, st>>>(D, r, z, cs.rz);
+  // |b|^2 per system: b of system s is rhs[s % n_rhs] = r at init
+  k_dot<<<nsys, 256, 0, st>>>(D, r, r, cs.bb);
+  FK_CUDA(cudaGetLastError());
+  const double tol2 = o.cg_tol * o.cg_tol;
+  int it = 0;
+  int host_active = nsys;
+  for (it = 0; it < o.cg_maxit; ++it) {
+    FK_TRY(matvec(c, nsys, n_rhs, W, p, q, st));
+    k_dot<<<nsys, 256, 0, st>>>(D, p, q, cs.pq);
+    k_cg_update_xr<<<g2, 256, 0, st>>>(D, n_rhs, W, T0, cs, p, q, x, r, z);
+    k_dot<<<nsys, 256, 0, st>>>(D, r, z, rznew);
+    k_dot<<<nsys, 256, 0, st>>>(D, r, r, cs.rr);
+    k_cg_beta<<<(nsys + 255) / 256, 256, 0, st>>>(nsys, tol2, cs, rznew);
+    k_cg_update_p<<<g2, 256, 0, st>>>(D, cs, rznew, z, p);
+    FK_CUDA(cudaGetLastError());
+    if ((it & 3) == 3 || it + 1 == o.cg_maxit) {
+      k_count_active<<<1, 256, 0, st>>>(nsys, active, cnt);
+      FK_CUDA(cudaMemcpyAsync(&host_active, cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+      FK_CUDA(cudaStreamSynchronize(st));
+      if (host_active == 0) break;
+    }
+  }
+  if (iters_out) *iters_out = it + 1;
+  // final relative residual from a fresh matvec: |b - A x| / |b| per system
+  FK_TRY(matvec(c, nsys, n_rhs, W, x, q, st));
+  k_resid_norm<<<nsys, 256, 0, st>>>(D, n_rhs, rhs, q, cs.rr, cs.bb);
+  FK_CUDA(cudaGetLastError());
+  {
+    std::vector<double> rr(nsys), bb(nsys);
+    FK_CUDA(cudaMemcpyAsync(rr.data(), cs.rr, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
+    FK_CUDA(cudaMemcpyAsync(bb.data(), cs.bb, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
+    FK_CUDA(cudaStreamSynchronize(st));
+    double worst = 0.0;
+    for (int s = 0; s < nsys; ++s) worst = std::max(worst, bb[s] > 0 ? std::sqrt(rr[s] / bb[s]) : std::sqrt(rr[s]));
+    if (relres_out) *relres_out = worst;
+  }
+  if (host_active != 0) return set_error(FK_ENOCONV, "CG did not converge in %d iterations", o.cg_maxit);
+  return FK_OK;
+}
+
+// ---------------------------------------------------------------- dispatcher
+fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, const double* rhs, int n_rhs,
+                       const fk_opts& o, double* sol, cudaStream_t st, Scratch& scratch, unsigned* flags,
+                       int* cg_iters, double* rel_res) {
+  int64_t D = 1;
+  for (int l = 0; l < d; ++l) D *= (2 * m + 1);
+  int solver = o.solver;
+  if (solver == FK_SOLVER_AUTO) solver = (D <= 1024) ? FK_SOLVER_CHOL : FK_SOLVER_CG;
+  if (cg_iters) *cg_iters = 0;
+  if (rel_res) *rel_res = 0.0;
+  if (solver == FK_SOLVER_CG)
+    return cg_solve(d, m, T, W, n_w, rhs, n_rhs, o, sol, st, scratch, cg_iters, rel_res);
+  if (D > 8192) return set_error(FK_EINVAL, "dense Cholesky limited to D <= 8192 (D = %lld)", (long long)D);
+  double *A, *R;
+  FK_TRY(scratch.alloc(&A, 2 * D * D));
+  FK_TRY(scratch.alloc(&R, 2 * D * n_rhs));
+  for (int l = 0; l < n_w; ++l) {
+    const double* Wl = W + l * D;
+    double* X = sol + 2 * static_cast<int64_t>(l) * n_rhs * D;
+    k_assemble<<<grid_for(D * D, 256), 256, 0, st>>>(d, m, T, Wl, A);
+    FK_CUDA(cudaGetLastError());
+    FK_TRY(cholesky(A, D, flags, st));
+    FK_CUDA(cudaMemcpyAsync(X, rhs, sizeof(double) * 2 * D * n_rhs, cudaMemcpyDeviceToDevice, st));
+    k_trisolve<<<(n_rhs + RB - 1) / RB, 256, 0, st>>>(A, D, X, n_rhs);
+    FK_CUDA(cudaGetLastError());
+    for (int it = 0; it < o.refine_steps; ++it) {
+      k_residual_dense<<<grid_for(D * n_rhs, 128), 128, 0, st>>>(d, m, T, Wl, X, rhs, R, n_rhs);
+      k_trisolve<<<(n_rhs + RB - 1) / RB, 256, 0, st>>>(A, D, R, n_rhs);
+      k_axpy_c<<<grid_for(2 * D * n_rhs, 256), 256, 0, st>>>(2 * D * n_rhs, R, X);
+      FK_CUDA(cudaGetLastError());
+    }
+  }
+  return FK_OK;
+}
+
+}  // namespace fk

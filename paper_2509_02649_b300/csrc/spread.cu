@@ -1,0 +1,238 @@
+// Spreading (type-1) and interpolation (type-2) with the ES kernel, atomic form.
+//
+// Point i with coordinate x (folded onto [-pi, pi)) sits at grid position
+// u = (x + pi) / h, h = 2 pi / N.  Its window is the w nodes
+// l = l0 .. l0 + w - 1 with l0 = ceil(u - w/2), and node l receives the weight
+// phi(z) with z = (l - u) * 2 / w in [-1, 1), phi(z) = exp(beta (sqrt(1-z^2) - 1)).
+// Indices wrap modulo N (the grid is periodic).
+//
+// This file holds the straightforward form: one thread per point, fp64 global
+// atomics into the grid.  It is the FP64 path's spreader and the fallback of the
+// mixed path; the register-accumulating binned spreader lives in spread_binned.cu.
+#include "fk_internal.cuh"
+
+namespace fk {
+
+constexpr int MAXW = 16;
+
+// Fold x onto [-pi, pi) and return the grid coordinate u in [0, N], or a negative
+// value when x is outside [-3 pi, 3 pi) (or NaN).
+template <typename R> __device__ __forceinline__ R grid_coord(R x, int N);
+
+template <> __device__ __forceinline__ double grid_coord<double>(double x, int N) {
+  if (!(x >= -3.0 * M_PI && x < 3.0 * M_PI)) return -1.0;
+  if (x < -M_PI) x += 2.0 * M_PI;
+  if (x >= M_PI) x -= 2.0 * M_PI;
+  return (x + M_PI) * (N / (2.0 * M_PI));
+}
+
+// fp32: u = x * (N / 2pi) + N / 2 with the constant split into a float pair so that
+// no systematic scale error enters (one rounding of the exact value).
+template <> __device__ __forceinline__ float grid_coord<float>(float x, int N) {
+  const float lim = 9.42477796076938f;  // 3 pi, rounded down in fp32
+  if (!(x >= -lim && x < lim)) return -1.0f;
+  const float twopi_hi = 6.28318548202514648f;   // fp32(2 pi)
+  const float twopi_lo = -1.74845553e-7f;         // 2 pi - fp32(2 pi)
+  if (x < -3.14159274101257324f) x = (x + twopi_hi) + twopi_lo;
+  if (x >= 3.14159274101257324f) x = (x - twopi_hi) - twopi_lo;
+  const double c = N / (2.0 * M_PI);
+  const float c_hi = static_cast<float>(c);
+  const float c_lo = static_cast<float>(c - static_cast<double>(c_hi));
+  float u = fmaf(x, c_hi, fmaf(x, c_lo, 0.5f * N));
+  if (u < 0.f) u = 0.f;
+  return u;
+}
+
+template <typename R>
+__device__ __forceinline__ R es_phi(R z, R beta);
+template <> __device__ __forceinline__ double es_phi<double>(double z, double beta) {
+  return exp(beta * (sqrt(1.0 - z * z) - 1.0));
+}
+template <> __device__ __forceinline__ float es_phi<float>(float z, float beta) {
+  return expf(beta * (sqrtf(fmaxf(1.0f - z * z, 0.0f)) - 1.0f));
+}
+
+// Weights of one coordinate: ker[a] for a = 0..w-1 and the first node l0.
+template <typename R>
+__device__ __forceinline__ void es_weights(R u, int w, R beta, R* ker, int* l0) {
+  const R half = R(0.5) * w;
+  const R s = ceil(u - half);
+  *l0 = static_cast<int>(s);
+  const R off = s - u;          // in [-w/2, -w/2 + 1)
+  const R sc = R(2) / w;
+#pragma unroll
+  for (int a = 0; a < MAXW; ++a)
+    if (a < w) ker[a] = es_phi<R>((off + a) * sc, beta);
+}
+
+template <typename R>
+__global__ void k_spread_atomic(int d, int N, int w, R beta, int64_t n, const R* __restrict__ x,
+                                const R* __restrict__ y, int n_y, int with_ones, double* grid,
+                                unsigned* flags) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t G = (d == 1) ? N : static_cast<int64_t>(N) * N;
+  const int nc = n_y + with_ones;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
+    R ker[2][MAXW];
+    int l0[2];
+    bool ok = true;
+    for (int l = 0; l < d; ++l) {
+      const R u = grid_coord<R>(x[l * n + i], N);
+      if (u < R(0)) { ok = false; break; }
+      es_weights<R>(u, w, beta, ker[l], &l0[l]);
+    }
+    if (!ok) { atomicOr(flags, FLAG_RANGE); continue; }
+    for (int c = 0; c < nc; ++c) {
+      const double str = (with_ones && c == 0) ? 1.0 : static_cast<double>(y[(c - with_ones) * n + i]);
+      double* g = grid + c * G;
+      if (d == 1) {
+        for (int a = 0; a < w; ++a) {
+          const int idx = (l0[0] + a + N) & (N - 1);
+          atomicAdd(g + idx, str * static_cast<double>(ker[0][a]));
+        }
+      } else {
+        for (int a = 0; a < w; ++a) {
+          const int r = (l0[0] + a + N) & (N - 1);
+          const double sa = str * static_cast<double>(ker[0][a]);
+          for (int b = 0; b < w; ++b) {
+            const int cidx = (l0[1] + b + N) & (N - 1);
+            atomicAdd(g + static_cast<int64_t>(r) * N + cidx, sa * static_cast<double>(ker[1][b]));
+          }
+        }
+      }
+    }
+  }
+}
+
+template <typename R>
+fk_status spread_atomic(const EsPlan& p, int64_t n, const R* x, const R* y, int n_y, bool with_ones,
+                        double* grid, unsigned* flags, cudaStream_t st) {
+  if (p.d < 1 || p.d > 2) return set_error(FK_EINVAL, "spread: d = %d not built", p.d);
+  if (p.w > MAXW) return set_error(FK_EINTERNAL, "w > %d", MAXW);
+  const int nc = n_y + (with_ones ? 1 : 0);
+  const int64_t G = (p.d == 1) ? p.N : static_cast<int64_t>(p.N) * p.N;
+  FK_CUDA(cudaMemsetAsync(grid, 0, sizeof(double) * G * nc, st));
+  if (n == 0) return FK_OK;
+  const int block = 256;
+  k_spread_atomic<R><<<grid_for(n, block, 148 * 16), block, 0, st>>>(
+      p.d, p.N, p.w, static_cast<R>(p.beta), n, x, y, n_y, with_ones ? 1 : 0, grid, flags);
+  FK_CUDA(cudaGetLastError());
+  return FK_OK;
+}
+template fk_status spread_atomic<float>(const EsPlan&, int64_t, const float*, const float*, int, bool, double*,
+                                        unsigned*, cudaStream_t);
+template fk_status spread_atomic<double>(const EsPlan&, int64_t, const double*, const double*, int, bool,
+                                         double*, unsigned*, cudaStream_t);
+
+// ---------------------------------------------------------------- type 2
+// Place coef'_k = coef_k * corr(k) at node (k mod N) of a zeroed complex grid,
+// inverse-transform (sign +1) and keep the real part; then interpolate.
+template <typename R>
+__global__ void k_t2_place(int d, int N, int kc, int corr_off, const double* coef, int n_sets,
+                           const double* corr, cplx<R>* G) {
+  const int K = 2 * kc + 1;
+  const int64_t D = (d == 1) ? K : static_cast<int64_t>(K) * K;
+  const int64_t GN = (d == 1) ? N : static_cast<int64_t>(N) * N;
+  const int64_t total = D * n_sets;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int sidx = static_cast<int>(t / D);
+    const int64_t q = t - sidx * D;
+    double f;
+    int64_t node;
+    if (d == 1) {
+      const int k = static_cast<int>(q) - kc;
+      f = corr[q + corr_off];
+      node = (k + N) & (N - 1);
+    } else {
+      const int a = static_cast<int>(q / K), b = static_cast<int>(q - static_cast<int64_t>(a) * K);
+      f = corr[a + corr_off] * corr[b + corr_off];
+      node = static_cast<int64_t>((a - kc + N) & (N - 1)) * N + ((b - kc + N) & (N - 1));
+    }
+    cplx<R> v;
+    v.x = static_cast<R>(coef[2 * t] * f);
+    v.y = static_cast<R>(coef[2 * t + 1] * f);
+    G[sidx * GN + node] = v;
+  }
+}
+
+template <typename R>
+__global__ void k_t2_interp(int d, int N, int w, R beta, int64_t n, const R* __restrict__ x, int n_sets,
+                            const cplx<R>* __restrict__ G, double* out, unsigned* flags) {
+  const int64_t GN = (d == 1) ? N : static_cast<int64_t>(N) * N;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    R ker[2][MAXW];
+    int l0[2];
+    bool ok = true;
+    for (int l = 0; l < d; ++l) {
+      const R u = grid_coord<R>(x[l * n + i], N);
+      if (u < R(0)) { ok = false; break; }
+      es_weights<R>(u, w, beta, ker[l], &l0[l]);
+    }
+    if (!ok) {
+      atomicOr(flags, FLAG_RANGE);
+      for (int s = 0; s < n_sets; ++s) out[s * n + i] = 0.0;
+      continue;
+    }
+    for (int s = 0; s < n_sets; ++s) {
+      const cplx<R>* g = G + s * GN;
+      double acc = 0.0;
+      if (d == 1) {
+        for (int a = 0; a < w; ++a) acc += static_cast<double>(ker[0][a]) * static_cast<double>(g[(l0[0] + a + N) & (N - 1)].x);
+      } else {
+        for (int a = 0; a < w; ++a) {
+          const int r = (l0[0] + a + N) & (N - 1);
+          R row = R(0);
+          for (int b = 0; b < w; ++b) row += ker[1][b] * g[static_cast<int64_t>(r) * N + ((l0[1] + b + N) & (N - 1))].x;
+          acc += static_cast<double>(ker[0][a]) * static_cast<double>(row);
+        }
+      }
+      out[s * n + i] = acc;
+    }
+  }
+}
+
+template <typename R>
+fk_status type2_eval(const EsPlan& p, int kmax_c, const double* coef, int n_sets, int64_t n, const R* x,
+                     const double* corr, double* out, unsigned* flags, cudaStream_t st, Scratch& scratch) {
+  if (p.d < 1 || p.d > 2) return set_error(FK_EINVAL, "type 2: d = %d not built", p.d);
+  if (kmax_c > p.kmax) return set_error(FK_EINTERNAL, "type 2: kmax_c > plan kmax");
+  const int N = p.N;
+  const int64_t GN = (p.d == 1) ? N : static_cast<int64_t>(N) * N;
+  cplx<R>* G = nullptr;
+  double* tw = nullptr;
+  FK_TRY(scratch.alloc(&G, GN * n_sets));
+  FK_TRY(scratch.alloc(&tw, 2 * static_cast<size_t>(N)));
+  FK_TRY(fft_twiddles(N, tw, st));
+  FK_CUDA(cudaMemsetAsync(G, 0, sizeof(cplx<R>) * GN * n_sets, st));
+  const int K = 2 * kmax_c + 1;
+  const int64_t D = (p.d == 1) ? K : static_cast<int64_t>(K) * K;
+  k_t2_place<R><<<grid_for(D * n_sets, 256), 256, 0, st>>>(p.d, N, kmax_c, p.kmax - kmax_c, coef, n_sets, corr, G);
+  FK_CUDA(cudaGetLastError());
+  if (p.d == 1) {
+    FK_TRY(fft_lines<R>(G, N, n_sets, N, 1, +1, tw, st));
+  } else {
+    // columns first (only the K nonzero ones per set), then every row
+    for (int s = 0; s < n_sets; ++s) {
+      cplx<R>* Gs = G + s * GN;
+      // columns with index (b - kc) mod N for b = 0..K-1: two contiguous ranges
+      const int lo_cnt = kmax_c + 1;  // columns 0..kc
+      FK_TRY(fft_lines<R>(Gs, N, lo_cnt, 1, N, +1, tw, st));
+      if (kmax_c > 0) FK_TRY(fft_lines<R>(Gs + (N - kmax_c), N, kmax_c, 1, N, +1, tw, st));
+    }
+    FK_TRY(fft_lines<R>(G, N, static_cast<int64_t>(n_sets) * N, N, 1, +1, tw, st));
+  }
+  if (n > 0) {
+    k_t2_interp<R><<<grid_for(n, 256, 148 * 16), 256, 0, st>>>(p.d, N, p.w, static_cast<R>(p.beta), n, x, n_sets,
+                                                               G, out, flags);
+    FK_CUDA(cudaGetLastError());
+  }
+  return FK_OK;
+}
+template fk_status type2_eval<float>(const EsPlan&, int, const double*, int, int64_t, const float*, const double*,
+                                     double*, unsigned*, cudaStream_t, Scratch&);
+template fk_status type2_eval<double>(const EsPlan&, int, const double*, int, int64_t, const double*,
+                                      const double*, double*, unsigned*, cudaStream_t, Scratch&);
+
+}  // namespace fk
