@@ -1,0 +1,290 @@
+#!/usr/bin/env python
+"""Fit throughput of Fourier-represented kernel regression on one B300.
+
+Workload: 2-D Sobolev regression, n = 1e8 points X ~ U[-pi, pi)^2 (fp32),
+Y = exp(-|X|^2) + N(0, 0.05^2), m = 32 (65 x 65 modes, 129 x 129 moments),
+s = 2, lambda = 1e-6, NUFFT eps = 1e-6.  One step is one whole fit through the
+C-ABI (fk_fit_sobolev): type-1 spreading of the ones and Y channels, FFT and
+deconvolution to the moments T and right-hand side b, penalty assembly and the
+FP64 conjugate-gradient solve.  Inputs (1.2 GB) are larger than L2, so no flush
+runs between steps.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WL = dict(workload="2d-sobolev", d=2, n=100_000_000, m=32, s=2.0, lam=1e-6, eps=1e-6)
+METRIC = "fit points/s (NUFFT Gram+RHS+solve)"
+SM_COUNT = 148
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=WL["n"], help="points (default: the workload's 1e8)")
+    ap.add_argument("--spread", default="auto", choices=["auto", "atomic", "binned"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def host_cores():
+    try:
+        from threadpoolctl import threadpool_info
+        th = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if th:
+            return int(max(th))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs(n: int):
+    import synthetic as S
+    x, y = S.wl2_sobolev_2d(n, dtype=np.float32)
+    return np.ascontiguousarray(x), np.ascontiguousarray(y)
+
+
+def cpu_oracle_fit(x, y, m, s, lam):
+    import oracle as O
+    t0 = time.perf_counter()
+    th = O.fit(x.astype(np.float64), y.astype(np.float64), m, O.penalty_sobolev(2, m, lam, s))
+    return time.perf_counter() - t0, th
+
+
+def run_reference(args, rank):
+    """The CPU oracle as it stands, timed on this machine's host cores."""
+    if rank != 0:
+        return
+    n_o = 50_000
+    x, y = make_inputs(n_o)
+    for _ in range(args.warmup):
+        cpu_oracle_fit(x[:, :2000], y[:2000], WL["m"], WL["s"], WL["lam"])
+    times = [cpu_oracle_fit(x, y, WL["m"], WL["s"], WL["lam"])[0] for _ in range(args.steps)]
+    t = statistics.median(times)
+    v = n_o / t
+    cores = host_cores()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "points/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WL["workload"], "n": n_o, "d": 2, "m": WL["m"], "s": WL["s"], "lambda": WL["lam"],
+                       "eps": WL["eps"], "note": "oracle fit on a %d-point sample of the workload" % n_o},
+            "cpu_baseline": {"value": v, "unit": "points/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d points of the workload; direct sums + dense solve D=4225" % n_o},
+            "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import paper_2509_02649_b300 as fk
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    n, d, m, s, lam, eps = args.n, WL["d"], WL["m"], WL["s"], WL["lam"], WL["eps"]
+    x_np, y_np = make_inputs(n)
+    x_h = torch.from_numpy(x_np).pin_memory()
+    y_h = torch.from_numpy(y_np).pin_memory()
+    x = x_h.cuda()
+    y = y_h.cuda()
+    spread = {"auto": fk.FK_SPREAD_AUTO, "atomic": fk.FK_SPREAD_ATOMIC, "binned": fk.FK_SPREAD_BINNED}[args.spread]
+    opts = fk.default_opts(spread=spread)
+    st = torch.cuda.current_stream()
+
+    def step():
+        return fk.fk_fit_sobolev(x, y, m, s, [lam], eps, "mixed", opts=opts, report=True)
+
+    for _ in range(args.warmup):
+        theta, rep = step()
+    torch.cuda.synchronize()
+
+    reps = []
+    launches0 = fk.fk_launch_count()
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            theta, rep = step()
+            reps.append(rep)
+        e1.record(st)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    launches = fk.fk_launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * n * args.steps / (ms / 1e3)
+
+    # dominant kernel: the spreading stage, timed by CUDA events on the launching stream
+    ms_spread = statistics.mean(r["ms_spread"] for r in reps)
+    w = reps[-1]["kernel_width"]
+    C = 2
+    f_pt = (w ** d) * (2 * C + (d - 1))
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = f_pt * n / (ms_spread / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "kernel": "spreading stage", "flop_per_point": f_pt, "kernel_width": w,
+                "peak_basis": "148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (unit counts and max clock)" % sm_max,
+                "ms_spread": ms_spread, "ms_fft": statistics.mean(r["ms_fft"] for r in reps),
+                "ms_solve": statistics.mean(r["ms_solve"] for r in reps), "cg_iters": reps[-1]["cg_iters"],
+                "hbm_view": {"bytes_per_point": 12, "achieved_GBs": 12 * n / (ms_spread / 1e3) / 1e9,
+                             "peak_GBs": peaks.get("hbm_gbs"), "of": "measured"}}
+
+    line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WL["workload"], "n": n, "d": d, "m": m, "s": s, "lambda": lam, "eps": eps,
+                       "precision": "mixed (fp32 spread/FFT, fp64 assembly/solve)",
+                       "l2": "inputs (1.2 GB) larger than L2, no flush", "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "gpu_launches": launches, "roofline": roofline, "clocks": clk.summary()}
+
+    if rank == 0 and not args.no_e2e:
+        # end to end through the public call: pinned host inputs copied each step, theta read back
+        theta_h = torch.empty(theta.shape, dtype=theta.dtype).pin_memory()
+        torch.cuda.synchronize()
+        k = max(2, min(args.steps, 5))
+        ee0 = torch.cuda.Event(enable_timing=True)
+        ee1 = torch.cuda.Event(enable_timing=True)
+        ee0.record(st)
+        for _ in range(k):
+            x.copy_(x_h, non_blocking=True)
+            y.copy_(y_h, non_blocking=True)
+            th, _ = step()
+            theta_h.copy_(th, non_blocking=True)
+        ee1.record(st)
+        torch.cuda.synchronize()
+        ems = ee0.elapsed_time(ee1) / k
+        line["e2e"] = {"value": n / (ems / 1e3), "unit": "points/s", "h2d_bytes_per_step": 12 * n,
+                       "d2h_bytes_per_step": int(theta.numel() * 16), "ms_per_step": ems}
+
+    if rank == 0 and not args.no_fp64:
+        # the plain FP64 GPU path on the same points (fp64 copies) and the mixed result's error against it
+        x64 = x.double()
+        y64 = y.double()
+        fk.fk_fit_sobolev(x64, y64, m, s, [lam], eps, "fp64")
+        torch.cuda.synchronize()
+        k = 2
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(st)
+        for _ in range(k):
+            th64 = fk.fk_fit_sobolev(x64, y64, m, s, [lam], eps, "fp64")
+        f1.record(st)
+        torch.cuda.synchronize()
+        fms = f0.elapsed_time(f1) / k
+        err = float(torch.linalg.norm(theta - th64) / torch.linalg.norm(th64))
+        line["fp64_path"] = {"value": n / (fms / 1e3), "unit": "points/s", "ms_per_step": fms,
+                             "mixed_speedup": (n / (ms_step / 1e3)) / (n / (fms / 1e3)),
+                             "theta_rel_err_mixed_vs_fp64": err, "eps": eps}
+        del x64, y64
+
+    if rank == 0 and not args.no_cpu_baseline:
+        n_o = 50_000
+        t_cpu, _ = cpu_oracle_fit(x_np[:, :n_o], y_np[:n_o], m, s, lam)
+        line["cpu_baseline"] = {"value": n_o / t_cpu, "unit": "points/s", "cores": host_cores(), "kind": "oracle",
+                                "sample": "first %d points of the workload: direct sums + dense solve D=4225" % n_o}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -192,6 +192,10 @@ FK_API const char* fk_last_error(void);
 /* Upper bound of the scratch bytes one fit with these sizes allocates. */
 FK_API size_t fk_workspace_bytes(int d, int m, int64_t n, int n_ch, double eps, int precision);
 
+/* Number of CUDA kernels this library has launched in the process so far
+ * (monotonic; a caller takes differences around a region of interest). */
+FK_API int64_t fk_launch_count(void);
+
 /* Library version string. */
 FK_API const char* fk_version(void);
 

@@ -26,7 +26,7 @@ STATUS = {0: "FK_OK", 1: "FK_EINVAL", 2: "FK_ERANGE", 3: "FK_ENOMEM", 4: "FK_ECU
 
 EXPORTS = ["fk_default_opts", "fk_fit_sobolev", "fk_fit_pik", "fk_fit_additive", "fk_predict", "fk_type1",
            "fk_type2", "fk_build_system", "fk_penalty_weights", "fk_solve", "fk_hypergrad", "fk_last_error",
-           "fk_workspace_bytes", "fk_version"]
+           "fk_workspace_bytes", "fk_version", "fk_launch_count"]
 
 
 class FkError(RuntimeError):
@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
             "fk_last_error": (ctypes.c_char_p, []),
             "fk_workspace_bytes": (ctypes.c_size_t, [_I, _I, _L, _I, _D, _I]),
             "fk_version": (ctypes.c_char_p, []),
+            "fk_launch_count": (ctypes.c_int64, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -275,3 +276,8 @@ def fk_hypergrad(x, xv, yv, m: int, T, W, theta, eps: float, precision="mixed", 
                               eps, p, _opts_ptr(opts), ctypes.byref(loss), dW.data_ptr(),
                               dY.data_ptr() if dY is not None else None, _stream()))
     return loss.value, dW, dY
+
+
+def fk_launch_count() -> int:
+    """Kernels libfk has launched in this process so far."""
+    return int(lib().fk_launch_count())

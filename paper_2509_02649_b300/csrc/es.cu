@@ -102,9 +102,9 @@ __global__ void k_es_correction(int kmax, int N, int w, double beta, const doubl
 fk_status es_correction(const EsPlan& p, double* corr, cudaStream_t st) {
   double* nw = nullptr;
   FK_CUDA(cudaMallocAsync(&nw, 2 * GL_Q * sizeof(double), st));
-  k_gauss_legendre<<<1, GL_Q, 0, st>>>(nw, nw + GL_Q);
+  k_gauss_legendre<<<1, GL_Q, 0, st>>>(nw, nw + GL_Q); note_launch();
   const int K = 2 * p.kmax + 1;
-  k_es_correction<<<(K + 127) / 128, 128, 0, st>>>(p.kmax, p.N, p.w, p.beta, nw, nw + GL_Q, corr);
+  k_es_correction<<<(K + 127) / 128, 128, 0, st>>>(p.kmax, p.N, p.w, p.beta, nw, nw + GL_Q, corr); note_launch();
   cudaError_t e = cudaGetLastError();
   cudaFreeAsync(nw, st);
   if (e != cudaSuccess) return set_error(FK_ECUDA, "es_correction launch: %s", cudaGetErrorString(e));

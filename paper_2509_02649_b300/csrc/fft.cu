@@ -21,7 +21,7 @@ __global__ void k_twiddles(int N, double* tw) {
 }
 
 fk_status fft_twiddles(int N, double* tw, cudaStream_t st) {
-  k_twiddles<<<(N + 255) / 256, 256, 0, st>>>(N, tw);
+  k_twiddles<<<(N + 255) / 256, 256, 0, st>>>(N, tw); note_launch();
   FK_CUDA(cudaGetLastError());
   return FK_OK;
 }
@@ -91,7 +91,7 @@ fk_status fft_lines(cplx<R>* data, int N, int64_t n_lines, int64_t line_stride, 
   if (sm > 48 * 1024) FK_CUDA(cudaFuncSetAttribute(k_fft_lines<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   for (int64_t l0 = 0; l0 < n_lines; l0 += 65535) {
     const int nl = static_cast<int>(std::min<int64_t>(65535, n_lines - l0));
-    k_fft_lines<R><<<nl, 256, sm, st>>>(data + l0 * line_stride, N, ilog2(N), line_stride, elem_stride, sign, tw);
+    k_fft_lines<R><<<nl, 256, sm, st>>>(data + l0 * line_stride, N, ilog2(N), line_stride, elem_stride, sign, tw); note_launch();
     FK_CUDA(cudaGetLastError());
   }
   return FK_OK;
@@ -194,16 +194,16 @@ fk_status grid_to_modes(const EsPlan& p, const double* grid, int c0, int nc, int
   const int K = 2 * kout + 1;
   if (p.d == 1) {
     FK_TRY(set_smem<R>((const void*)k_t1_1d<R>, sm));
-    k_t1_1d<R><<<nc, 256, sm, st>>>(grid, N, logN, c0, kout, corr, corr_off, scale, tw, out);
+    k_t1_1d<R><<<nc, 256, sm, st>>>(grid, N, logN, c0, kout, corr, corr_off, scale, tw, out); note_launch();
     FK_CUDA(cudaGetLastError());
   } else if (p.d == 2) {
     cplx<R>* H = nullptr;
     FK_TRY(scratch.alloc(&H, static_cast<size_t>(nc) * N * K));
     FK_TRY(set_smem<R>((const void*)k_t1_2d_rows<R>, sm));
     FK_TRY(set_smem<R>((const void*)k_t1_2d_cols<R>, sm));
-    k_t1_2d_rows<R><<<nc * N, 256, sm, st>>>(grid, N, logN, c0, kout, tw, H);
+    k_t1_2d_rows<R><<<nc * N, 256, sm, st>>>(grid, N, logN, c0, kout, tw, H); note_launch();
     FK_CUDA(cudaGetLastError());
-    k_t1_2d_cols<R><<<nc * K, 256, sm, st>>>(H, N, logN, kout, corr, corr_off, scale, tw, out);
+    k_t1_2d_cols<R><<<nc * K, 256, sm, st>>>(H, N, logN, kout, corr, corr_off, scale, tw, out); note_launch();
     FK_CUDA(cudaGetLastError());
   } else {
     return set_error(FK_EINVAL, "d = %d transforms are not built", p.d);

@@ -2,12 +2,16 @@
 // host, scratch management, and the order of the device stages of each call.
 #include "fk_internal.cuh"
 
+#include <atomic>
 #include <chrono>
 #include <vector>
 
 namespace fk {
 
 static thread_local std::string g_err;
+static std::atomic<int64_t> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 fk_status set_error(fk_status st, const char* fmt, ...) {
   char buf[512];
@@ -163,6 +167,8 @@ void fk_default_opts(fk_opts* o) {
 const char* fk_last_error(void) { return g_err.c_str(); }
 
 const char* fk_version(void) { return "fk 0.1 (sm_103a)"; }
+
+int64_t fk_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 size_t fk_workspace_bytes(int d, int m, int64_t n, int n_ch, double eps, int precision) {
   (void)n;

@@ -16,6 +16,8 @@ namespace fk {
 // ------------------------------------------------------------------ errors
 fk_status set_error(fk_status st, const char* fmt, ...);
 void clear_error();
+// Process-wide count of kernels this library has launched (fk_launch_count).
+void note_launch();
 
 #define FK_CUDA(call)                                                          \
   do {                                                                         \

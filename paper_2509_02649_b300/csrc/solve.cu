@@ -89,7 +89,7 @@ fk_status penalty_weights(int d, int m, int penalty, double s, double c0, const 
   if (e == cudaSuccess) {
     int64_t D = 1;
     for (int l = 0; l < d; ++l) D *= (2 * m + 1);
-    k_penalty<<<grid_for(D * n_lambda, 256), 256, 0, st>>>(d, m, penalty, s, c0, dl, n_lambda, mu, pde, W);
+    k_penalty<<<grid_for(D * n_lambda, 256), 256, 0, st>>>(d, m, penalty, s, c0, dl, n_lambda, mu, pde, W); note_launch();
     e = cudaGetLastError();
   }
   cudaFreeAsync(dl, st);
@@ -216,12 +216,12 @@ __global__ void k_chol_update(double* A, int64_t D, int kb, int nb) {
 static fk_status cholesky(double* A, int64_t D, unsigned* flags, cudaStream_t st) {
   for (int kb = 0; kb < D; kb += NB) {
     const int nb = static_cast<int>(std::min<int64_t>(NB, D - kb));
-    k_chol_diag<<<1, 256, 0, st>>>(A, D, kb, nb, flags);
+    k_chol_diag<<<1, 256, 0, st>>>(A, D, kb, nb, flags); note_launch();
     const int64_t rest = D - kb - nb;
     if (rest > 0) {
-      k_chol_panel<<<static_cast<int>((rest + 127) / 128), 128, 0, st>>>(A, D, kb, nb);
+      k_chol_panel<<<static_cast<int>((rest + 127) / 128), 128, 0, st>>>(A, D, kb, nb); note_launch();
       const int nt = static_cast<int>((rest + 31) / 32);
-      k_chol_update<<<dim3(nt, nt), 256, 0, st>>>(A, D, kb, nb);
+      k_chol_update<<<dim3(nt, nt), 256, 0, st>>>(A, D, kb, nb); note_launch();
     }
     FK_CUDA(cudaGetLastError());
   }
@@ -536,11 +536,11 @@ static fk_status fft_nd(const Circ& c, int nsys, int sign, cudaStream_t st) {
 static fk_status matvec(const Circ& c, int nsys, int n_rhs, const double* W, const double* v, double* q,
                         cudaStream_t st) {
   FK_CUDA(cudaMemsetAsync(c.buf, 0, sizeof(cplx<double>) * c.LL * nsys, st));
-  k_pad<<<grid_for(c.D * nsys, 256), 256, 0, st>>>(c.d, c.m, c.Lc, nsys, v, c.buf);
+  k_pad<<<grid_for(c.D * nsys, 256), 256, 0, st>>>(c.d, c.m, c.Lc, nsys, v, c.buf); note_launch();
   FK_TRY(fft_nd(c, nsys, -1, st));
-  k_pointwise<<<grid_for(c.LL * nsys, 256), 256, 0, st>>>(c.LL, nsys, c.ch, c.buf);
+  k_pointwise<<<grid_for(c.LL * nsys, 256), 256, 0, st>>>(c.LL, nsys, c.ch, c.buf); note_launch();
   FK_TRY(fft_nd(c, nsys, +1, st));
-  k_extract_addw<<<grid_for(c.D * nsys, 256), 256, 0, st>>>(c.d, c.m, c.Lc, nsys, n_rhs, c.buf, W, v, q);
+  k_extract_addw<<<grid_for(c.D * nsys, 256), 256, 0, st>>>(c.d, c.m, c.Lc, nsys, n_rhs, c.buf, W, v, q); note_launch();
   FK_CUDA(cudaGetLastError());
   return FK_OK;
 }
@@ -594,7 +594,7 @@ static fk_status cg_solve(int d, int m, const double* T, const double* W, int n_
   FK_CUDA(cudaMemsetAsync(c.ch, 0, sizeof(cplx<double>) * c.LL, st));
   int64_t M2 = 1;
   for (int l = 0; l < d; ++l) M2 *= (4 * m + 1);
-  k_circ_embed<<<grid_for(M2, 256), 256, 0, st>>>(d, m, c.Lc, T, c.ch);
+  k_circ_embed<<<grid_for(M2, 256), 256, 0, st>>>(d, m, c.Lc, T, c.ch); note_launch();
   FK_CUDA(cudaGetLastError());
   {
     Circ c1 = c;
@@ -622,26 +622,26 @@ static fk_status cg_solve(int d, int m, const double* T, const double* W, int n_
   double* rznew = scal + 4 * nsys;
   double* x = sol;
   const dim3 g2(static_cast<unsigned>(std::min<int64_t>((D + 255) / 256, 64)), nsys);
-  k_cg_init<<<g2, 256, 0, st>>>(D, n_rhs, nsys, W, T0, rhs, x, r, z, p);
-  k_set_active<<<(nsys + 255) / 256, 256, 0, st>>>(nsys, active);
-  k_dot<<<nsys, 256, 0, st>>>(D, r, z, cs.rz);
+  k_cg_init<<<g2, 256, 0, st>>>(D, n_rhs, nsys, W, T0, rhs, x, r, z, p); note_launch();
+  k_set_active<<<(nsys + 255) / 256, 256, 0, st>>>(nsys, active); note_launch();
+  k_dot<<<nsys, 256, 0, st>>>(D, r, z, cs.rz); note_launch();
   // |b|^2 per system: b of system s is rhs[s % n_rhs] = r at init
-  k_dot<<<nsys, 256, 0, st>>>(D, r, r, cs.bb);
+  k_dot<<<nsys, 256, 0, st>>>(D, r, r, cs.bb); note_launch();
   FK_CUDA(cudaGetLastError());
   const double tol2 = o.cg_tol * o.cg_tol;
   int it = 0;
   int host_active = nsys;
   for (it = 0; it < o.cg_maxit; ++it) {
     FK_TRY(matvec(c, nsys, n_rhs, W, p, q, st));
-    k_dot<<<nsys, 256, 0, st>>>(D, p, q, cs.pq);
-    k_cg_update_xr<<<g2, 256, 0, st>>>(D, n_rhs, W, T0, cs, p, q, x, r, z);
-    k_dot<<<nsys, 256, 0, st>>>(D, r, z, rznew);
-    k_dot<<<nsys, 256, 0, st>>>(D, r, r, cs.rr);
-    k_cg_beta<<<(nsys + 255) / 256, 256, 0, st>>>(nsys, tol2, cs, rznew);
-    k_cg_update_p<<<g2, 256, 0, st>>>(D, cs, rznew, z, p);
+    k_dot<<<nsys, 256, 0, st>>>(D, p, q, cs.pq); note_launch();
+    k_cg_update_xr<<<g2, 256, 0, st>>>(D, n_rhs, W, T0, cs, p, q, x, r, z); note_launch();
+    k_dot<<<nsys, 256, 0, st>>>(D, r, z, rznew); note_launch();
+    k_dot<<<nsys, 256, 0, st>>>(D, r, r, cs.rr); note_launch();
+    k_cg_beta<<<(nsys + 255) / 256, 256, 0, st>>>(nsys, tol2, cs, rznew); note_launch();
+    k_cg_update_p<<<g2, 256, 0, st>>>(D, cs, rznew, z, p); note_launch();
     FK_CUDA(cudaGetLastError());
     if ((it & 3) == 3 || it + 1 == o.cg_maxit) {
-      k_count_active<<<1, 256, 0, st>>>(nsys, active, cnt);
+      k_count_active<<<1, 256, 0, st>>>(nsys, active, cnt); note_launch();
       FK_CUDA(cudaMemcpyAsync(&host_active, cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
       FK_CUDA(cudaStreamSynchronize(st));
       if (host_active == 0) break;
@@ -650,7 +650,7 @@ static fk_status cg_solve(int d, int m, const double* T, const double* W, int n_
   if (iters_out) *iters_out = it + 1;
   // final relative residual from a fresh matvec: |b - A x| / |b| per system
   FK_TRY(matvec(c, nsys, n_rhs, W, x, q, st));
-  k_resid_norm<<<nsys, 256, 0, st>>>(D, n_rhs, rhs, q, cs.rr, cs.bb);
+  k_resid_norm<<<nsys, 256, 0, st>>>(D, n_rhs, rhs, q, cs.rr, cs.bb); note_launch();
   FK_CUDA(cudaGetLastError());
   {
     std::vector<double> rr(nsys), bb(nsys);
@@ -684,16 +684,16 @@ fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, 
   for (int l = 0; l < n_w; ++l) {
     const double* Wl = W + l * D;
     double* X = sol + 2 * static_cast<int64_t>(l) * n_rhs * D;
-    k_assemble<<<grid_for(D * D, 256), 256, 0, st>>>(d, m, T, Wl, A);
+    k_assemble<<<grid_for(D * D, 256), 256, 0, st>>>(d, m, T, Wl, A); note_launch();
     FK_CUDA(cudaGetLastError());
     FK_TRY(cholesky(A, D, flags, st));
     FK_CUDA(cudaMemcpyAsync(X, rhs, sizeof(double) * 2 * D * n_rhs, cudaMemcpyDeviceToDevice, st));
-    k_trisolve<<<(n_rhs + RB - 1) / RB, 256, 0, st>>>(A, D, X, n_rhs);
+    k_trisolve<<<(n_rhs + RB - 1) / RB, 256, 0, st>>>(A, D, X, n_rhs); note_launch();
     FK_CUDA(cudaGetLastError());
     for (int it = 0; it < o.refine_steps; ++it) {
-      k_residual_dense<<<grid_for(D * n_rhs, 128), 128, 0, st>>>(d, m, T, Wl, X, rhs, R, n_rhs);
-      k_trisolve<<<(n_rhs + RB - 1) / RB, 256, 0, st>>>(A, D, R, n_rhs);
-      k_axpy_c<<<grid_for(2 * D * n_rhs, 256), 256, 0, st>>>(2 * D * n_rhs, R, X);
+      k_residual_dense<<<grid_for(D * n_rhs, 128), 128, 0, st>>>(d, m, T, Wl, X, rhs, R, n_rhs); note_launch();
+      k_trisolve<<<(n_rhs + RB - 1) / RB, 256, 0, st>>>(A, D, R, n_rhs); note_launch();
+      k_axpy_c<<<grid_for(2 * D * n_rhs, 256), 256, 0, st>>>(2 * D * n_rhs, R, X); note_launch();
       FK_CUDA(cudaGetLastError());
     }
   }

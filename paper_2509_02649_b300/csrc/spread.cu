@@ -115,7 +115,7 @@ fk_status spread_atomic(const EsPlan& p, int64_t n, const R* x, const R* y, int 
   if (n == 0) return FK_OK;
   const int block = 256;
   k_spread_atomic<R><<<grid_for(n, block, 148 * 16), block, 0, st>>>(
-      p.d, p.N, p.w, static_cast<R>(p.beta), n, x, y, n_y, with_ones ? 1 : 0, grid, flags);
+      p.d, p.N, p.w, static_cast<R>(p.beta), n, x, y, n_y, with_ones ? 1 : 0, grid, flags); note_launch();
   FK_CUDA(cudaGetLastError());
   return FK_OK;
 }
@@ -208,7 +208,7 @@ fk_status type2_eval(const EsPlan& p, int kmax_c, const double* coef, int n_sets
   FK_CUDA(cudaMemsetAsync(G, 0, sizeof(cplx<R>) * GN * n_sets, st));
   const int K = 2 * kmax_c + 1;
   const int64_t D = (p.d == 1) ? K : static_cast<int64_t>(K) * K;
-  k_t2_place<R><<<grid_for(D * n_sets, 256), 256, 0, st>>>(p.d, N, kmax_c, p.kmax - kmax_c, coef, n_sets, corr, G);
+  k_t2_place<R><<<grid_for(D * n_sets, 256), 256, 0, st>>>(p.d, N, kmax_c, p.kmax - kmax_c, coef, n_sets, corr, G); note_launch();
   FK_CUDA(cudaGetLastError());
   if (p.d == 1) {
     FK_TRY(fft_lines<R>(G, N, n_sets, N, 1, +1, tw, st));
@@ -225,7 +225,7 @@ fk_status type2_eval(const EsPlan& p, int kmax_c, const double* coef, int n_sets
   }
   if (n > 0) {
     k_t2_interp<R><<<grid_for(n, 256, 148 * 16), 256, 0, st>>>(p.d, N, p.w, static_cast<R>(p.beta), n, x, n_sets,
-                                                               G, out, flags);
+                                                               G, out, flags); note_launch();
     FK_CUDA(cudaGetLastError());
   }
   return FK_OK;
