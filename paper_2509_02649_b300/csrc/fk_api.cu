@@ -106,9 +106,9 @@ static fk_status spread_any(const EsPlan& p, int precision, const fk_opts& o, in
                                  with_ones, grid, flags, st);
   const int nc = n_y + (with_ones ? 1 : 0);
   const bool binned = (o.spread == FK_SPREAD_BINNED) ||
-                      (o.spread == FK_SPREAD_AUTO && spread_binned_supported(p, nc));
+                      (o.spread == FK_SPREAD_AUTO && spread_binned_supported(p, n_y, with_ones));
   if (binned) {
-    if (!spread_binned_supported(p, nc))
+    if (!spread_binned_supported(p, n_y, with_ones))
       return set_error(FK_EINVAL, "binned spreading does not support d=%d w=%d channels=%d", p.d, p.w, nc);
     return spread_binned(p, n, static_cast<const float*>(x), static_cast<const float*>(y), n_y, with_ones, grid,
                          flags, st, scr);

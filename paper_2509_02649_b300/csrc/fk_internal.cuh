@@ -119,11 +119,11 @@ template <typename R>
 fk_status spread_atomic(const EsPlan& p, int64_t n, const R* x, const R* y, int n_y,
                         bool with_ones, double* grid, unsigned* flags, cudaStream_t st);
 
-// Binned register-accumulation spreading (fp32, d = 1 or 2, ones + n_y channels).
+// Binned register-accumulation spreading (fp32, d = 2, ones and/or one strength channel).
 fk_status spread_binned(const EsPlan& p, int64_t n, const float* x, const float* y, int n_y,
                         bool with_ones, double* grid, unsigned* flags, cudaStream_t st,
                         Scratch& scratch);
-bool spread_binned_supported(const EsPlan& p, int n_ch);
+bool spread_binned_supported(const EsPlan& p, int n_y, bool with_ones);
 
 // Forward transform of real fp64 grids + deconvolution + extraction of the modes
 // |k|_inf <= kout (kout <= p.kmax) for channels [c0, c0 + nc), scaled by `scale`.

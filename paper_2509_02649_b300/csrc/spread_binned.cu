@@ -1,18 +1,666 @@
-// Binned register-accumulation spreading (placeholder until the kernel lands).
+// Binned spreading with register accumulation (mixed path, fp32 arithmetic, d = 2).
+//
+// The type-1 sums of Sec. 2.3 are spread onto the upsampled grid.  A point's window
+// starts at node l0 = ceil(u - w/2) in each dimension; points sharing that start
+// node (a "cell") touch exactly the same w x w nodes.  Lanes of the accumulation
+// kernel own cells and keep the cell's w x w partial sums in registers for the
+// whole call, so its hot loop is FFMA work on register operands: no atomics and no
+// shared-memory read-modify-write.  With the ones channel (moments T) and one
+// strength channel (right-hand side b) two lanes share a cell, one per channel;
+// each lane evaluates the ES weights of one coordinate and the pair swaps them
+// with one shuffle, so every weight is computed once.
+//
+// Four launches.  Owner o holds cells [o cpc, (o+1) cpc), cpc <= 448 (224 in pair
+// mode, so that each lane keeps its w x w window in registers without spilling).
+//   k_bin_count   (full occupancy) counts, per block of the input, the points whose
+//                 window-start cell belongs to each owner;
+//   k_bin_scan    turns the counts into per-(block, owner) offsets and per-owner totals,
+//                 each run padded to whole 128-byte lines (sentinel records) so that
+//                 the scattered record writes never share a line between blocks;
+//   k_bin_scatter (full occupancy) recomputes each point's cell and fractional
+//                 offsets and writes a 16-byte record {owner:local cell, f0, f1,
+//                 strength} at its owner's next free slot (shared-memory cursors);
+//   k_bin_accumulate (one CTA per owner) streams its owner's bucket with double-
+//                 buffered TMA bulk copies, links each round's records into per-cell
+//                 lists in shared memory, and lets each lane run over at most a quota
+//                 of its cell's points (the mean load plus half a standard deviation);
+//                 the excess of fuller cells is carried into the next round, which
+//                 keeps the warps' trip counts even.  At the end each lane adds its
+//                 register window into the fp64 grid.
 #include "fk_internal.cuh"
 
 namespace fk {
 
-bool spread_binned_supported(const EsPlan& p, int n_ch) {
-  (void)p;
-  (void)n_ch;
-  return false;
+namespace {
+
+constexpr int MAX_G = 511;  // owners (< partition block size, for the block-wide scans)
+constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+constexpr int CARRY = 2048;                      // records a CTA may defer to its next round
+constexpr int THREADS_ACC = 448;                 // accumulation CTA size (one CTA per SM)
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ float coord_f32(float x, int N, float c_hi, float c_lo) {
+  // fold onto [-pi, pi) and map to grid units u = x N / (2 pi) + N / 2 (one rounding)
+  const float lim = 9.42477796076938f;
+  if (!(x >= -lim && x < lim)) return -1.0f;
+  const float twopi_hi = 6.28318548202514648f, twopi_lo = -1.74845553e-7f;
+  if (x < -3.14159274101257324f) x = (x + twopi_hi) + twopi_lo;
+  if (x >= 3.14159274101257324f) x = (x - twopi_hi) - twopi_lo;
+  const float u = fmaf(x, c_hi, fmaf(x, c_lo, 0.5f * N));
+  return u < 0.f ? 0.f : u;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float v) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
+
+__device__ __forceinline__ float ex2_approx(float v) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
+
+// ES weights of one coordinate from its fractional offset f in (w/2 - 1, w/2]:
+// psi_a = 2^(bl (sqrt(1 - z_a^2) - 1)), bl = beta log2(e), z_a = (a - f) 2 / w.
+template <int W>
+__device__ __forceinline__ void es_taps(float f, float bl, float* out) {
+  const float sc = 2.0f / W;
+  const float z0 = -f * sc;
+#pragma unroll
+  for (int a = 0; a < W; ++a) {
+    const float z = fmaf(static_cast<float>(a), sc, z0);
+    const float t = fmaxf(fmaf(-z, z, 1.0f), 1e-30f);
+    out[a] = ex2_approx(fmaf(bl, t * rsqrt_approx(t), -bl));
+  }
+}
+
+__device__ __forceinline__ bool wait_counter(const int* ctr, int target, unsigned* flags) {
+  const long long t0 = clock64();
+  while (true) {
+    if (*reinterpret_cast<const volatile int*>(ctr) >= target) break;
+    if (clock64() - t0 > WAIT_CYCLES) {
+      atomicOr(flags, FLAG_TIMEOUT);
+      return false;
+    }
+    if (*reinterpret_cast<const volatile unsigned*>(flags) & FLAG_TIMEOUT) return false;
+    __nanosleep(64);
+  }
+  __threadfence();
+  return true;
+}
+
+// ---------------------------------------------------------------- async copies
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// returns false when the bounded wait gives up
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned* flags) {
+  const long long t0 = clock64();
+  while (true) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > WAIT_CYCLES) {
+      atomicOr(flags, FLAG_TIMEOUT);
+      return false;
+    }
+  }
+}
+// global -> shared bulk copy (TMA), completion counted in bytes on `bar`
+__device__ __forceinline__ void bulk_g2s(void* sdst, const void* gsrc, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(sdst)),
+      "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// one warp: exclusive scan of v[0..cnt) in place, returns the total (all lanes)
+__device__ __forceinline__ int warp_exclusive_scan(int* v, int cnt, int lane) {
+  int carry = 0;
+  for (int o0 = 0; o0 < cnt; o0 += 32) {
+    const int o = o0 + lane;
+    const int x = (o < cnt) ? v[o] : 0;
+    int incl = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += t;
+    }
+    if (o < cnt) v[o] = carry + incl - x;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  return carry;
+}
+
+constexpr int P_THREADS = 512;   // partition kernels
+constexpr int P_NWARPS = P_THREADS / 32;
+constexpr int P_TILE = 4096;     // points per partition block, at least
+constexpr int CAPR = 4096;       // records per accumulation round
+
+// cells per owner: one lane per cell, or two (one per channel) in pair mode
+template <bool PAIR>
+struct Cfg {
+  static constexpr int THREADS = THREADS_ACC;
+  static constexpr int CELLS = PAIR ? THREADS_ACC / 2 : THREADS_ACC;
+};
+
+struct PartArgs {
+  int N, W, G, cells_per;
+  int64_t n;
+  const float* x;
+  const float* y;
+  int has_y;
+  int vec_ok;       // x (both rows) and y 16-byte aligned: float4 loads
+  int nblk;         // partition blocks
+  int64_t range;    // points per partition block
+  int* cnt;         // [nblk][G]
+  int* off;         // [nblk][G] offset of the block's run inside its owner's bucket
+  int* tot;         // [G]
+  uint4* rec;       // [n] records, bucketed by owner
+  unsigned* flags;
+  float c_hi, c_lo;
+};
+
+// owner and packed key of one point; returns false for a point out of range
+__device__ __forceinline__ bool point_key(float x0, float x1, const PartArgs& A, float inv_cpc, float* f0, float* f1,
+                                          uint32_t* packed) {
+  const float u0 = coord_f32(x0, A.N, A.c_hi, A.c_lo);
+  const float u1 = coord_f32(x1, A.N, A.c_hi, A.c_lo);
+  if (!(u0 >= 0.f && u1 >= 0.f)) return false;
+  const float l0a = ceilf(u0 - 0.5f * A.W), l0b = ceilf(u1 - 0.5f * A.W);
+  const int N = A.N;
+  const int key = ((static_cast<int>(l0a) + N) & (N - 1)) * N + ((static_cast<int>(l0b) + N) & (N - 1));
+  int o = __float2int_rd(static_cast<float>(key) * inv_cpc);
+  if (o * A.cells_per > key) --o;
+  else if ((o + 1) * A.cells_per <= key) ++o;
+  *f0 = u0 - l0a;
+  *f1 = u1 - l0b;
+  *packed = (static_cast<uint32_t>(o) << 16) | static_cast<uint32_t>(key - o * A.cells_per);
+  return true;
+}
+
+__global__ void __launch_bounds__(P_THREADS) k_bin_count(PartArgs A) {
+  extern __shared__ int whist[];  // [P_NWARPS][G]
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int G = A.G;
+  const float inv_cpc = 1.0f / static_cast<float>(A.cells_per);
+  for (int o = tid; o < P_NWARPS * G; o += P_THREADS) whist[o] = 0;
+  __syncthreads();
+  const int64_t s = static_cast<int64_t>(blockIdx.x) * A.range;
+  const int64_t e = min(A.n, s + A.range);
+  int* wh = whist + warp * G;
+  auto one = [&](float a0, float a1) {
+    float f0, f1;
+    uint32_t k;
+    if (point_key(a0, a1, A, inv_cpc, &f0, &f1, &k)) atomicAdd(&wh[k >> 16], 1);
+    else atomicOr(A.flags, FLAG_RANGE);
+  };
+  if (A.vec_ok) {
+    // four points per thread and iteration (float4 loads keep more bytes in flight)
+    for (int64_t i = s + 4 * tid; i < e; i += 4 * P_THREADS) {
+      if (i + 3 < e) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(A.x + i));
+        const float4 c = __ldg(reinterpret_cast<const float4*>(A.x + A.n + i));
+        one(a.x, c.x);
+        one(a.y, c.y);
+        one(a.z, c.z);
+        one(a.w, c.w);
+      } else {
+        for (int64_t j = i; j < e; ++j) one(__ldg(A.x + j), __ldg(A.x + A.n + j));
+      }
+    }
+  } else {
+    for (int64_t i = s + tid; i < e; i += P_THREADS) one(__ldg(A.x + i), __ldg(A.x + A.n + i));
+  }
+  __syncthreads();
+  for (int o = tid; o < G; o += P_THREADS) {
+    int c = 0;
+    for (int w = 0; w < P_NWARPS; ++w) c += whist[w * G + o];
+    A.cnt[static_cast<size_t>(blockIdx.x) * G + o] = c;
+  }
+}
+
+// one CTA per owner: exclusive scan over partition blocks
+__global__ void k_bin_scan(PartArgs A) {
+  __shared__ int wsum[32];
+  const int o = blockIdx.x, G = A.G;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int carry = 0;
+  for (int b0 = 0; b0 < A.nblk; b0 += blockDim.x) {
+    const int bb = b0 + tid;
+    // runs are padded to whole 128-byte lines (8 records) so that no line is shared by
+    // two blocks' runs; the padding holds sentinel records
+    const int v = (bb < A.nblk) ? ((A.cnt[static_cast<size_t>(bb) * G + o] + 7) & ~7) : 0;
+    int incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int wpre = 0, total = 0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) {
+      if (w < warp) wpre += wsum[w];
+      total += wsum[w];
+    }
+    if (bb < A.nblk) A.off[static_cast<size_t>(bb) * G + o] = carry + wpre + incl - v;
+    carry += total;
+    __syncthreads();
+  }
+  if (tid == 0) A.tot[o] = carry;
+}
+
+// exclusive scan of tot[0..G) into base[0..G] by the whole block (G < blockDim.x);
+// every total is loaded once, in parallel.  wsum: 32 ints of shared scratch.
+__device__ __forceinline__ void owner_bases(const int* tot, int G, int* base, int* wsum) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int v = (tid < G) ? __ldg(tot + tid) : 0;
+  int incl = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += t;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  int pre = 0;
+  for (int w = 0; w < warp; ++w) pre += wsum[w];
+  if (tid <= G) base[tid] = pre + incl - v;
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(P_THREADS) k_bin_scatter(PartArgs A) {
+  extern __shared__ int cursor[];  // [G + 1]: global position of this block's next record per owner
+  __shared__ int wsum[32];
+  const int G = A.G;
+  const int tid = threadIdx.x;
+  const float inv_cpc = 1.0f / static_cast<float>(A.cells_per);
+  owner_bases(A.tot, G, cursor, wsum);
+  for (int o = tid; o < G; o += P_THREADS) cursor[o] += A.off[static_cast<size_t>(blockIdx.x) * G + o];
+  __syncthreads();
+  const int64_t s = static_cast<int64_t>(blockIdx.x) * A.range;
+  const int64_t e = min(A.n, s + A.range);
+  auto one = [&](float a0, float a1, float yy) {
+    float f0, f1;
+    uint32_t k;
+    if (!point_key(a0, a1, A, inv_cpc, &f0, &f1, &k)) return;
+    const int pos = atomicAdd(&cursor[k >> 16], 1);
+    A.rec[pos] = make_uint4(k, __float_as_uint(f0), __float_as_uint(f1), __float_as_uint(yy));
+  };
+  if (A.vec_ok) {
+    for (int64_t i = s + 4 * tid; i < e; i += 4 * P_THREADS) {
+      if (i + 3 < e) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(A.x + i));
+        const float4 c = __ldg(reinterpret_cast<const float4*>(A.x + A.n + i));
+        float4 yy = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (A.has_y) yy = __ldg(reinterpret_cast<const float4*>(A.y + i));
+        one(a.x, c.x, yy.x);
+        one(a.y, c.y, yy.y);
+        one(a.z, c.z, yy.z);
+        one(a.w, c.w, yy.w);
+      } else {
+        for (int64_t j = i; j < e; ++j) one(__ldg(A.x + j), __ldg(A.x + A.n + j), A.has_y ? __ldg(A.y + j) : 0.f);
+      }
+    }
+  } else {
+    for (int64_t i = s + tid; i < e; i += P_THREADS)
+      one(__ldg(A.x + i), __ldg(A.x + A.n + i), A.has_y ? __ldg(A.y + i) : 0.f);
+  }
+  __syncthreads();
+  // sentinel records fill each run up to its padded length
+  for (int o = tid; o < G; o += P_THREADS) {
+    const int c = A.cnt[static_cast<size_t>(blockIdx.x) * G + o];
+    for (int k = c; k < ((c + 7) & ~7); ++k) A.rec[cursor[o]++] = make_uint4(0xFFFFu, 0u, 0u, 0u);
+  }
+}
+
+struct AccArgs {
+  int N, G, cells_per, ncells;
+  float beta;
+  int with_ones;
+  const int* tot;   // [G]
+  const uint4* rec;
+  double* grid;
+  unsigned* flags;
+};
+
+struct AccLayout {
+  size_t stage, nxt, head, ccount, total;
+};
+__host__ __device__ inline AccLayout acc_layout(int cpc) {
+  AccLayout L{};
+  L.stage = 0;                                                      // [2][CARRY + CAPR] uint4
+  L.nxt = L.stage + sizeof(uint4) * 2 * (CARRY + CAPR);             // [CARRY + CAPR] u16
+  L.head = (L.nxt + sizeof(unsigned short) * (CARRY + CAPR) + 15) & ~static_cast<size_t>(15);  // [cpc] int
+  L.ccount = L.head + sizeof(int) * cpc;                            // [cpc] int
+  L.total = L.ccount + sizeof(int) * cpc;
+  return L;
+}
+
+template <int W, bool PAIR>
+__global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArgs A) {
+  constexpr int THREADS = Cfg<PAIR>::THREADS;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_base, s_count, s_ncarry, s_nleft, s_abort;
+  __shared__ __align__(8) uint64_t s_bar[2];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int b = blockIdx.x;
+  const int N = A.N;
+  const int cpc = A.cells_per;
+  const int cell = PAIR ? (tid >> 1) : tid;
+  const int ch = PAIR ? (tid & 1) : 0;
+  const unsigned pmask = 3u << (lane & 30);
+  const int my_first_cell = b * cpc;
+  const int my_ncells = max(0, min(cpc, A.ncells - my_first_cell));
+  const bool owns = cell < my_ncells;
+  const float bl = A.beta * 1.4426950408889634f;
+  const AccLayout L = acc_layout(cpc);
+  uint4* stage = reinterpret_cast<uint4*>(smem + L.stage);
+  unsigned short* nxt = reinterpret_cast<unsigned short*>(smem + L.nxt);
+  int* head = reinterpret_cast<int*>(smem + L.head);
+  int* ccount = reinterpret_cast<int*>(smem + L.ccount);
+
+  {
+    // bucket of this owner = [sum of earlier totals, + tot[b]): one load per thread
+    __shared__ int wsum[32];
+    int v = 0;
+    for (int o = tid; o < b; o += THREADS) v += __ldg(A.tot + o);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    if (lane == 0) wsum[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+      int sum = 0;
+      for (int w = 0; w < THREADS / 32; ++w) sum += wsum[w];
+      s_base = sum;
+      s_count = __ldg(A.tot + b);
+      s_ncarry = 0;
+      s_abort = 0;
+      mbar_init(&s_bar[0]);
+      mbar_init(&s_bar[1]);
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+  }
+  for (int i = tid; i < cpc; i += THREADS) {
+    head[i] = 0xFFFF;
+    ccount[i] = 0;
+  }
+  __syncthreads();
+  const int base = s_base, count = s_count;
+  const int nrounds = (count + CAPR - 1) / CAPR;
+  if (nrounds == 0) return;
+
+  float acc[W][W];
+#pragma unroll
+  for (int a = 0; a < W; ++a)
+#pragma unroll
+    for (int c = 0; c < W; ++c) acc[a][c] = 0.f;
+
+  auto issue = [&](int r) {
+    const int nr = min(CAPR, count - r * CAPR);
+    uint4* dst = stage + (r & 1) * (CARRY + CAPR) + CARRY;
+    fence_proxy_async();
+    mbar_arrive_expect(&s_bar[r & 1], static_cast<unsigned>(nr) * 16u);
+    bulk_g2s(dst, A.rec + base + static_cast<int64_t>(r) * CAPR, static_cast<unsigned>(nr) * 16u, &s_bar[r & 1]);
+  };
+  if (tid == 0) issue(0);
+
+  for (int r = 0; r < nrounds; ++r) {
+    const int buf = r & 1;
+    uint4* st = stage + buf * (CARRY + CAPR);
+    const int nr = min(CAPR, count - r * CAPR);
+    const int nc = s_ncarry;
+    if (!mbar_wait(&s_bar[buf], (r >> 1) & 1, A.flags)) s_abort = 1;
+    __syncthreads();
+    if (s_abort) return;
+    if (tid == 0) {
+      if (r + 1 < nrounds) issue(r + 1);
+      s_nleft = 0;
+    }
+    // records of this round: [CARRY - nc, CARRY + nr) of the buffer
+    const int lo = CARRY - nc, hi = CARRY + nr;
+    for (int idx = lo + tid; idx < hi; idx += THREADS) {
+      const int cl = static_cast<int>(st[idx].x & 0xFFFFu);
+      if (cl == 0xFFFF) continue;  // run padding
+      atomicAdd(&ccount[cl], 1);
+      nxt[idx] = static_cast<unsigned short>(atomicExch(&head[cl], idx));
+    }
+    const bool last = (r == nrounds - 1);
+    int q = 0x7FFFFFFF;
+    if (!last && my_ncells > 0) {
+      const float lam = static_cast<float>(hi - lo) / static_cast<float>(my_ncells);
+      q = static_cast<int>(ceilf(lam + 0.5f * sqrtf(lam)));
+    }
+    __syncthreads();
+    const int mine = owns ? ccount[cell] : 0;
+    if (ch == 0 && mine > q) atomicAdd(&s_nleft, mine - q);
+    __syncthreads();
+    if (s_nleft > CARRY) q = 0x7FFFFFFF;  // not enough room: process everything now
+    int ri = owns ? head[cell] : 0xFFFF;
+    if (owns) {
+      const int nproc = min(mine, q);
+      if (PAIR) {
+        // lane 0 of the pair: ones channel, window [a][b]; lane 1: strength channel,
+        // window transposed ([b][a]) because it holds the second coordinate's weights.
+        // Two records per iteration for independent work in flight.
+        int k = 0;
+        for (; k + 1 < nproc; k += 2) {
+          const uint4 ra = st[ri];
+          const int rj = nxt[ri];
+          const uint4 rb = st[rj];
+          ri = nxt[rj];
+          float ea[W], eb[W];
+          es_taps<W>(__uint_as_float(ch == 0 ? ra.y : ra.z), bl, ea);
+          es_taps<W>(__uint_as_float(ch == 0 ? rb.y : rb.z), bl, eb);
+          const float wa = (ch == 0) ? 1.0f : __uint_as_float(ra.w);
+          const float wb = (ch == 0) ? 1.0f : __uint_as_float(rb.w);
+#pragma unroll
+          for (int j = 0; j < W; ++j) {
+            const float ta = wa * __shfl_xor_sync(pmask, ea[j], 1);
+            const float tb = wb * __shfl_xor_sync(pmask, eb[j], 1);
+#pragma unroll
+            for (int i = 0; i < W; ++i) acc[i][j] = fmaf(eb[i], tb, fmaf(ea[i], ta, acc[i][j]));
+          }
+        }
+        if (k < nproc) {
+          const uint4 ra = st[ri];
+          ri = nxt[ri];
+          float ea[W];
+          es_taps<W>(__uint_as_float(ch == 0 ? ra.y : ra.z), bl, ea);
+          const float wa = (ch == 0) ? 1.0f : __uint_as_float(ra.w);
+#pragma unroll
+          for (int j = 0; j < W; ++j) {
+            const float ta = wa * __shfl_xor_sync(pmask, ea[j], 1);
+#pragma unroll
+            for (int i = 0; i < W; ++i) acc[i][j] = fmaf(ea[i], ta, acc[i][j]);
+          }
+        }
+      } else {
+        for (int k = 0; k < nproc; ++k) {
+          const uint4 rec = st[ri];
+          ri = nxt[ri];
+          float px[W], py[W];
+          es_taps<W>(__uint_as_float(rec.y), bl, px);
+          es_taps<W>(__uint_as_float(rec.z), bl, py);
+          const float sv = A.with_ones ? 1.0f : __uint_as_float(rec.w);
+#pragma unroll
+          for (int i = 0; i < W; ++i) {
+            const float pa = px[i] * sv;
+#pragma unroll
+            for (int j = 0; j < W; ++j) acc[i][j] = fmaf(pa, py[j], acc[i][j]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // deferred records go in front of the next buffer's TMA region
+    const int nleft = (q == 0x7FFFFFFF) ? 0 : s_nleft;
+    if (tid == 0) s_ncarry = 0;
+    __syncthreads();
+    if (owns && ch == 0 && mine > q) {
+      uint4* nst = stage + (buf ^ 1) * (CARRY + CAPR);
+      int dst = CARRY - nleft + atomicAdd(&s_ncarry, mine - q);
+      while (ri != 0xFFFF) {
+        nst[dst++] = st[ri];
+        ri = nxt[ri];
+      }
+    }
+    for (int i = tid; i < cpc; i += THREADS) {
+      head[i] = 0xFFFF;
+      ccount[i] = 0;
+    }
+    __syncthreads();
+  }
+  // flush the register window into the fp64 grid
+  if (!owns) return;
+  const int key = my_first_cell + cell;
+  const int64_t GN = static_cast<int64_t>(N) * N;
+  const int c0 = key / N;
+  const int c1 = key - c0 * N;
+  double* g = A.grid + (PAIR ? ch : 0) * GN;
+  const bool transposed = PAIR && ch == 1;
+#pragma unroll
+  for (int i = 0; i < W; ++i)
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      const int a = transposed ? j : i, bb = transposed ? i : j;
+      atomicAdd(g + static_cast<int64_t>((c0 + a) & (N - 1)) * N + ((c1 + bb) & (N - 1)),
+                static_cast<double>(acc[i][j]));
+    }
+}
+
+using KFn = void (*)(AccArgs);
+
+template <bool PAIR>
+KFn pick2d(int w) {
+  switch (w) {
+    case 4: return k_bin_accumulate<4, PAIR>;
+    case 5: return k_bin_accumulate<5, PAIR>;
+    case 6: return k_bin_accumulate<6, PAIR>;
+    case 7: return k_bin_accumulate<7, PAIR>;
+    case 8: return k_bin_accumulate<8, PAIR>;
+    default: return nullptr;
+  }
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return sms;
+}
+
+}  // namespace
+
+// owners: enough that each holds at most Cfg::CELLS cells, and at least one per SM
+static int owner_count(int64_t ncells, bool pair, int sms) {
+  const int cells = pair ? Cfg<true>::CELLS : Cfg<false>::CELLS;
+  int64_t G = (ncells + cells - 1) / cells;
+  if (G < sms) G = sms;
+  if (G > ncells) G = ncells;
+  return static_cast<int>(G);
+}
+
+bool spread_binned_supported(const EsPlan& p, int n_y, bool with_ones) {
+  const int nch = n_y + (with_ones ? 1 : 0);
+  if (p.d != 2 || nch < 1 || nch > 2 || n_y > 1 || p.w < 4 || p.w > 8) return false;
+  const int sms = sm_count();
+  if (sms <= 0) return false;
+  const int64_t ncells = static_cast<int64_t>(p.N) * p.N;
+  return owner_count(ncells, nch == 2, sms) <= MAX_G;
 }
 
 fk_status spread_binned(const EsPlan& p, int64_t n, const float* x, const float* y, int n_y, bool with_ones,
-                        double* grid, unsigned* flags, cudaStream_t st, Scratch& scratch) {
-  (void)p; (void)n; (void)x; (void)y; (void)n_y; (void)with_ones; (void)grid; (void)flags; (void)st; (void)scratch;
-  return set_error(FK_EINVAL, "binned spreading not built");
+                        double* grid, unsigned* flags, cudaStream_t st, Scratch& scr) {
+  if (!spread_binned_supported(p, n_y, with_ones)) return set_error(FK_EINVAL, "binned spreading: unsupported shape");
+  if (n >= (static_cast<int64_t>(1) << 31)) return set_error(FK_EINVAL, "binned spreading: n >= 2^31 per call");
+  const int nch = n_y + (with_ones ? 1 : 0);
+  const bool pair = (nch == 2);
+  const int64_t ncells = static_cast<int64_t>(p.N) * p.N;
+  const int G = owner_count(ncells, pair, sm_count());
+  const int cpc = static_cast<int>((ncells + G - 1) / G);
+  const double c = p.N / (2.0 * M_PI);
+
+  FK_CUDA(cudaMemsetAsync(grid, 0, sizeof(double) * ncells * nch, st));
+  if (n == 0) return FK_OK;
+
+  PartArgs P{};
+  P.N = p.N;
+  P.W = p.w;
+  P.G = G;
+  P.cells_per = cpc;
+  P.n = n;
+  P.x = x;
+  P.y = y;
+  P.has_y = n_y > 0 ? 1 : 0;
+  P.nblk = static_cast<int>(std::min<int64_t>((n + P_TILE - 1) / P_TILE, 4 * sm_count()));
+  P.range = ((n + P.nblk - 1) / P.nblk + 3) & ~static_cast<int64_t>(3);
+  P.vec_ok = ((reinterpret_cast<uintptr_t>(x) & 15) == 0 && (n & 3) == 0 &&
+              (n_y == 0 || (reinterpret_cast<uintptr_t>(y) & 15) == 0))
+                 ? 1
+                 : 0;
+  P.flags = flags;
+  P.c_hi = static_cast<float>(c);
+  P.c_lo = static_cast<float>(c - static_cast<double>(P.c_hi));
+  FK_TRY(scr.alloc(&P.cnt, static_cast<size_t>(P.nblk) * G));
+  FK_TRY(scr.alloc(&P.off, static_cast<size_t>(P.nblk) * G));
+  FK_TRY(scr.alloc(&P.tot, static_cast<size_t>(G)));
+  FK_TRY(scr.alloc(&P.rec, static_cast<size_t>(n) + static_cast<size_t>(P.nblk) * G * 7));  // + run padding
+
+  const size_t sm_count_k = sizeof(int) * P_NWARPS * G;
+  k_bin_count<<<P.nblk, P_THREADS, sm_count_k, st>>>(P); note_launch();
+  FK_CUDA(cudaGetLastError());
+  k_bin_scan<<<G, 256, 0, st>>>(P); note_launch();
+  FK_CUDA(cudaGetLastError());
+  const size_t sm_scatter = sizeof(int) * (G + 1);
+  k_bin_scatter<<<P.nblk, P_THREADS, sm_scatter, st>>>(P); note_launch();
+  FK_CUDA(cudaGetLastError());
+
+  AccArgs A{};
+  A.N = p.N;
+  A.G = G;
+  A.cells_per = cpc;
+  A.ncells = static_cast<int>(ncells);
+  A.beta = static_cast<float>(p.beta);
+  A.with_ones = with_ones ? 1 : 0;
+  A.tot = P.tot;
+  A.rec = P.rec;
+  A.grid = grid;
+  A.flags = flags;
+  const KFn fn = pair ? pick2d<true>(p.w) : pick2d<false>(p.w);
+  if (!fn) return set_error(FK_EINVAL, "binned spreading: w = %d not built", p.w);
+  const int threads = pair ? Cfg<true>::THREADS : Cfg<false>::THREADS;
+  const size_t sm = acc_layout(cpc).total;
+  FK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+  fn<<<G, threads, sm, st>>>(A); note_launch();
+  FK_CUDA(cudaGetLastError());
+  return FK_OK;
 }
 
 }  // namespace fk

@@ -219,3 +219,44 @@ def test_noiseless_recovery_is_exact_to_solve_precision():
     assert abs(th[m + 7] - 0.25) < 1e-10
     other = np.delete(th, [m - 7, m - 3, m + 3, m + 7])
     assert np.max(np.abs(other)) < 1e-10
+
+
+# ---------------------------------------------------------------- binned register-accumulating spreader
+@pytest.mark.parametrize("n", [1, 37, 5000, 1_300_001, 3_000_017])
+def test_binned_spreader_matches_oracle(n):
+    m, eps = 8, 1e-6
+    x, y = S.wl2_sobolev_2d(n, dtype=np.float32)
+    opts = fk.default_opts(spread=fk.FK_SPREAD_BINNED)
+    T, b = fk.fk_build_system(dev(x, torch.float32), dev(y, torch.float32), m, eps, "mixed", opts=opts)
+    To = O.moments(x.astype(np.float64), m)
+    bo = O.rhs(x.astype(np.float64), y.astype(np.float64), m)
+    assert rel(host(T), To) <= 10 * eps
+    assert rel(host(b)[0], bo) <= 10 * eps
+
+
+def test_binned_and_atomic_spreaders_agree_config2_grid():
+    # the workload's grid (m = 32: 129 x 129 moments, N = 256, w = 7) over several chunks
+    m, eps = 32, 1e-6
+    x, y = S.wl2_sobolev_2d(4_000_037, dtype=np.float32)
+    xd, yd = dev(x, torch.float32), dev(y, torch.float32)
+    Tb, bb = fk.fk_build_system(xd, yd, m, eps, "mixed", opts=fk.default_opts(spread=fk.FK_SPREAD_BINNED))
+    Ta, ba = fk.fk_build_system(xd, yd, m, eps, "mixed", opts=fk.default_opts(spread=fk.FK_SPREAD_ATOMIC))
+    assert rel(host(Tb), host(Ta)) < 1e-6
+    assert rel(host(bb), host(ba)) < 1e-6
+    # sampled moments against direct sums over all points
+    j = [(0, 1), (5, -7), (-64, 64), (33, 2)]
+    K = 4 * m + 1
+    Tg = host(Tb)
+    for j0, j1 in j:
+        want = np.mean(np.exp(-1j * (j0 * x[0].astype(np.float64) + j1 * x[1].astype(np.float64))))
+        assert abs(Tg[(j0 + 2 * m) * K + (j1 + 2 * m)] - want) < 1e-6
+
+
+def test_binned_rejects_out_of_range_points():
+    x = S.uniform_points(2000, 2, 32).astype(np.float32)
+    x[1, 1234] = 20.0
+    c = np.ones(2000, dtype=np.float32)
+    with pytest.raises(fk.FkError) as e:
+        fk.fk_build_system(dev(x, torch.float32), dev(c, torch.float32), 4, 1e-6, "mixed",
+                           opts=fk.default_opts(spread=fk.FK_SPREAD_BINNED))
+    assert e.value.name == "FK_ERANGE"
