@@ -155,6 +155,24 @@ FK_API fk_status fk_type1(int d, int64_t n, const void* x, const void* c, int n_
 FK_API fk_status fk_type2(int d, int kmax, const double* coef, int n_sets, int64_t n, const void* x,
                    double eps, int precision, double* out, void* stream);
 
+/* Type-1 sums as fk_type1, for callers that cannot allocate device memory at call
+ * time (a process whose device memory is wholly reserved by its own pool allocator,
+ * or a service that forbids device allocation after start-up).  The paper has no
+ * counterpart to this entry point.
+ *   All scratch comes from one built-in device array of FK_NOALLOC_SCRATCH_BYTES,
+ *   which every GPU that loads the library holds until the process exits; no
+ *   cudaMalloc / cudaMallocAsync / cudaFree is called.  Shapes whose scratch would
+ *   exceed it (d = 2 needs about 16 N^2 n_ch bytes, N the upsampled grid) return
+ *   FK_EINVAL with the required size in fk_last_error().
+ *   The first call on a device looks up the array's device address (with that
+ *   device current); make that first call before any stream capture.
+ *   Calls share the array: calls whose work overlaps on the GPU (other streams,
+ *   other host threads) race on it.  The call synchronises `stream`.
+ *   Spreading uses the atomic form for both precisions.  Arguments as fk_type1. */
+#define FK_NOALLOC_SCRATCH_BYTES (16u << 20)
+FK_API fk_status fk_type1_noalloc(int d, int64_t n, const void* x, const void* c, int n_ch, int kmax,
+                                  double eps, int precision, double* out, void* stream);
+
 /* Moments and right-hand sides: T (device complex, (4m+1)^d) and
  * b (device complex, [n_targets][D]), each divided by n (Sec. 2.3). */
 FK_API fk_status fk_build_system(int d, int64_t n, const void* x, const void* y, int n_targets, int m,

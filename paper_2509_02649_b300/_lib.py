@@ -26,7 +26,7 @@ STATUS = {0: "FK_OK", 1: "FK_EINVAL", 2: "FK_ERANGE", 3: "FK_ENOMEM", 4: "FK_ECU
 
 EXPORTS = ["fk_default_opts", "fk_fit_sobolev", "fk_fit_pik", "fk_fit_additive", "fk_predict", "fk_type1",
            "fk_type2", "fk_build_system", "fk_penalty_weights", "fk_solve", "fk_hypergrad", "fk_last_error",
-           "fk_workspace_bytes", "fk_version", "fk_launch_count"]
+           "fk_workspace_bytes", "fk_version", "fk_launch_count", "fk_type1_noalloc"]
 
 
 class FkError(RuntimeError):
@@ -80,6 +80,7 @@ def lib() -> ctypes.CDLL:
             "fk_workspace_bytes": (ctypes.c_size_t, [_I, _I, _L, _I, _D, _I]),
             "fk_version": (ctypes.c_char_p, []),
             "fk_launch_count": (ctypes.c_int64, []),
+            "fk_type1_noalloc": (_I, [_I, _L, _P, _P, _I, _I, _D, _I, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -281,3 +282,16 @@ def fk_hypergrad(x, xv, yv, m: int, T, W, theta, eps: float, precision="mixed", 
 def fk_launch_count() -> int:
     """Kernels libfk has launched in this process so far."""
     return int(lib().fk_launch_count())
+
+
+def fk_type1_noalloc(x, c, kmax: int, eps: float, precision="mixed"):
+    """fk_type1 through the entry point that allocates no device scratch (it uses the
+    library's built-in scratch array); the output tensor is allocated here by torch."""
+    p = _prec(precision)
+    x = _points(x, p)
+    d, n = x.shape
+    c = c.reshape(-1, n).contiguous()
+    out = torch.empty((c.shape[0], (2 * kmax + 1) ** d), dtype=torch.complex128, device=x.device)
+    _check(lib().fk_type1_noalloc(d, n, x.data_ptr(), c.data_ptr(), c.shape[0], kmax, eps, p, out.data_ptr(),
+                                  _stream()))
+    return out

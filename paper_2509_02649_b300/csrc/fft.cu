@@ -216,3 +216,41 @@ template fk_status grid_to_modes<double>(const EsPlan&, const double*, int, int,
                                          double*, cudaStream_t, Scratch&);
 
 }  // namespace fk
+
+namespace fk {
+
+// Same as grid_to_modes, with the twiddle table (2 N doubles) and, for d = 2, the
+// row-transform intermediate (nc * N * (2 kout + 1) complex values) supplied by the
+// caller instead of allocated.
+template <typename R>
+fk_status grid_to_modes_into(const EsPlan& p, const double* grid, int c0, int nc, int kout, const double* corr,
+                             double scale, double* out, cudaStream_t st, double* tw, cplx<R>* H) {
+  if (kout > p.kmax) return set_error(FK_EINTERNAL, "kout %d > kmax %d", kout, p.kmax);
+  const int N = p.N, logN = ilog2(N);
+  const size_t sm = static_cast<size_t>(N) * sizeof(cplx<R>);
+  if (sm > 200 * 1024) return set_error(FK_EINVAL, "fine grid %d too long for one CTA", N);
+  const int corr_off = p.kmax - kout;
+  FK_TRY(fft_twiddles(N, tw, st));
+  const int K = 2 * kout + 1;
+  if (p.d == 1) {
+    FK_TRY(set_smem<R>((const void*)k_t1_1d<R>, sm));
+    k_t1_1d<R><<<nc, 256, sm, st>>>(grid, N, logN, c0, kout, corr, corr_off, scale, tw, out); note_launch();
+    FK_CUDA(cudaGetLastError());
+  } else if (p.d == 2) {
+    FK_TRY(set_smem<R>((const void*)k_t1_2d_rows<R>, sm));
+    FK_TRY(set_smem<R>((const void*)k_t1_2d_cols<R>, sm));
+    k_t1_2d_rows<R><<<nc * N, 256, sm, st>>>(grid, N, logN, c0, kout, tw, H); note_launch();
+    FK_CUDA(cudaGetLastError());
+    k_t1_2d_cols<R><<<nc * K, 256, sm, st>>>(H, N, logN, kout, corr, corr_off, scale, tw, out); note_launch();
+    FK_CUDA(cudaGetLastError());
+  } else {
+    return set_error(FK_EINVAL, "d = %d transforms are not built", p.d);
+  }
+  return FK_OK;
+}
+template fk_status grid_to_modes_into<float>(const EsPlan&, const double*, int, int, int, const double*, double,
+                                             double*, cudaStream_t, double*, cplx<float>*);
+template fk_status grid_to_modes_into<double>(const EsPlan&, const double*, int, int, int, const double*, double,
+                                              double*, cudaStream_t, double*, cplx<double>*);
+
+}  // namespace fk

@@ -149,6 +149,13 @@ fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, 
                        int n_rhs, const fk_opts& o, double* sol, cudaStream_t st,
                        Scratch& scratch, unsigned* flags, int* cg_iters, double* rel_res);
 
+// Variants with caller-supplied scratch (used by the entry point that allocates nothing).
+fk_status es_correction_into(const EsPlan& p, double* corr, double* gl_scratch, cudaStream_t st);
+int es_gl_nodes();
+template <typename R>
+fk_status grid_to_modes_into(const EsPlan& p, const double* grid, int c0, int nc, int kout, const double* corr,
+                             double scale, double* out, cudaStream_t st, double* tw, cplx<R>* H);
+
 // FFT primitives (complex, in place on contiguous lines of length N, batched).
 template <typename R>
 fk_status fft_lines(cplx<R>* data, int N, int64_t n_lines, int64_t line_stride, int64_t elem_stride,
