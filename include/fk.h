@@ -204,6 +204,14 @@ FK_API fk_status fk_hypergrad(int d, int64_t n, const void* x, int64_t n_v, cons
                        const double* theta, double eps, int precision, const fk_opts* opts,
                        double* loss, double* dW, double* dY, void* stream);
 
+/* Chain rule from dL/dW (device, D doubles) to the penalty's parameters of
+ *   W_k = lambda (c0 + |k|^{2s}) + mu |P(ik)|^2   (Sec. 3.1 and Sec. 4):
+ *   out (host, 3 + n_terms doubles) = [dL/dlambda, dL/ds, dL/dmu, dL/da_0 .. dL/da_{n_terms-1}],
+ *   dL/ds summing dW_k lambda |k|^{2s} ln|k|^2 over k != 0.  Synchronises `stream`. */
+FK_API fk_status fk_penalty_grads(int d, int m, double s, double c0, double lambda, double mu, int n_terms,
+                                  const int* alpha, const double* a, const double* dW, double* out,
+                                  void* stream);
+
 /* Thread-local description of the last failure on this thread ("" after success). */
 FK_API const char* fk_last_error(void);
 

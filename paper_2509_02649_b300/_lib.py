@@ -26,7 +26,7 @@ STATUS = {0: "FK_OK", 1: "FK_EINVAL", 2: "FK_ERANGE", 3: "FK_ENOMEM", 4: "FK_ECU
 
 EXPORTS = ["fk_default_opts", "fk_fit_sobolev", "fk_fit_pik", "fk_fit_additive", "fk_predict", "fk_type1",
            "fk_type2", "fk_build_system", "fk_penalty_weights", "fk_solve", "fk_hypergrad", "fk_last_error",
-           "fk_workspace_bytes", "fk_version", "fk_launch_count", "fk_type1_noalloc"]
+           "fk_workspace_bytes", "fk_version", "fk_launch_count", "fk_type1_noalloc", "fk_penalty_grads"]
 
 
 class FkError(RuntimeError):
@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
             "fk_version": (ctypes.c_char_p, []),
             "fk_launch_count": (ctypes.c_int64, []),
             "fk_type1_noalloc": (_I, [_I, _L, _P, _P, _I, _I, _D, _I, _P, _P]),
+            "fk_penalty_grads": (_I, [_I, _I, _D, _D, _D, _D, _I, _P, _P, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -295,3 +296,14 @@ def fk_type1_noalloc(x, c, kmax: int, eps: float, precision="mixed"):
     _check(lib().fk_type1_noalloc(d, n, x.data_ptr(), c.data_ptr(), c.shape[0], kmax, eps, p, out.data_ptr(),
                                   _stream()))
     return out
+
+
+def fk_penalty_grads(d: int, m: int, dW, lam: float, s: float = 1.0, mu: float = 0.0, alpha=(), a=(), c0: float = 1.0):
+    """[dL/dlambda, dL/ds, dL/dmu, dL/da_0, ...] (host floats) from dL/dW (device)."""
+    al = [int(v) for row in alpha for v in row]
+    alpha_arr = (ctypes.c_int * max(len(al), 1))(*al)
+    a_arr = _dbl_array(list(a) if len(a) else [0.0])
+    out = (ctypes.c_double * (3 + len(a)))()
+    _check(lib().fk_penalty_grads(d, m, s, c0, lam, mu, len(a), alpha_arr, a_arr, dW.contiguous().data_ptr(), out,
+                                  _stream()))
+    return list(out)

@@ -371,13 +371,4 @@ fk_status fk_predict(int additive, int d, int m, const double* theta, int n_sets
   return fk_type2(d, m, theta, n_sets, n_q, xq, eps, precision, f, stream);
 }
 
-fk_status fk_hypergrad(int d, int64_t n, const void* x, int64_t n_v, const void* xv, const void* yv, int m,
-                       const double* T, const double* W, const double* theta, double eps, int precision,
-                       const fk_opts* opts, double* loss, double* dW, double* dY, void* stream) {
-  clear_error();
-  (void)d; (void)n; (void)x; (void)n_v; (void)xv; (void)yv; (void)m; (void)T; (void)W; (void)theta; (void)eps;
-  (void)precision; (void)opts; (void)loss; (void)dW; (void)dY; (void)stream;
-  return set_error(FK_EINVAL, "fk_hypergrad: not built yet");
-}
-
 }  // extern "C"
