@@ -1,0 +1,217 @@
+// Low-bias additive model (Prop. 5.1, Sec. 5): block Gram, right-hand side, solve and
+// additive prediction.
+//
+// Blocks of Sigma (each (2m+1) x (2m+1), k in -m..m):
+//   (l, l)    Toeplitz in the 1-D moments T^(l)_j = (1/n) sum_i e^{-i j X_il}, |j| <= 2m
+//   (l1, l2)  (1/n) sum_i e^{-i k1 X_il1} e^{+i k2 X_il2}: a 2-D type-1 transform of ones at
+//             the points (X_l1, -X_l2) (Sec. 5, Complexity); (l2, l1) is its conjugate
+//             transpose
+// right-hand side b_l[k] = (1/n) sum_i Y_i e^{-i k X_il}, and theta = (Sigma + lambda I)^{-1} b
+// by a dense FP64 Cholesky solve of size d(2m+1) with one refinement step.
+#include "fk_internal.cuh"
+
+namespace fk {
+namespace {
+
+template <typename R>
+__global__ void k_pair_points(int64_t n, const R* x, int l1, int l2, R* out) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    out[i] = x[l1 * n + i];
+    out[n + i] = -x[l2 * n + i];
+  }
+}
+
+// A[(l1,k1),(l2,k2)], row-major, D = d K, plus lambda on the diagonal
+__global__ void k_additive_gram(int d, int m, const double* T1, const double* Bp, double lambda, double* A) {
+  const int K = 2 * m + 1, M2 = 4 * m + 1;
+  const int64_t D = static_cast<int64_t>(d) * K;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < D * D;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t row = t / D, col = t - (t / D) * D;
+    const int l1 = static_cast<int>(row / K), k1 = static_cast<int>(row % K);
+    const int l2 = static_cast<int>(col / K), k2 = static_cast<int>(col % K);
+    double re, im;
+    if (l1 == l2) {
+      const int j = k1 - k2 + 2 * m;  // moment index of k1 - k2
+      re = T1[2 * (static_cast<int64_t>(l1) * M2 + j)];
+      im = T1[2 * (static_cast<int64_t>(l1) * M2 + j) + 1];
+      if (k1 == k2) re += lambda;
+    } else {
+      const int a = l1 < l2 ? l1 : l2, b = l1 < l2 ? l2 : l1;
+      const int64_t pair = static_cast<int64_t>(a) * d - static_cast<int64_t>(a) * (a + 1) / 2 + (b - a - 1);
+      const double* blk = Bp + 2 * pair * K * K;
+      if (l1 < l2) {
+        re = blk[2 * (static_cast<int64_t>(k1) * K + k2)];
+        im = blk[2 * (static_cast<int64_t>(k1) * K + k2) + 1];
+      } else {  // conjugate transpose of block (l2, l1)
+        re = blk[2 * (static_cast<int64_t>(k2) * K + k1)];
+        im = -blk[2 * (static_cast<int64_t>(k2) * K + k1) + 1];
+      }
+    }
+    A[2 * t] = re;
+    A[2 * t + 1] = im;
+  }
+}
+
+__global__ void k_add_into(int64_t n, const double* a, double* acc) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    acc[i] += a[i];
+}
+
+template <typename R>
+fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, int m, const double* lambdas,
+                            int n_lambda, double eps, int precision, const fk_opts& o, double* theta,
+                            cudaStream_t st, fk_report* rep) {
+  Scratch scr(st);
+  unsigned* flags;
+  FK_TRY(scr.alloc(&flags, 1));
+  FK_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned), st));
+  const int K = 2 * m + 1, M2 = 4 * m + 1;
+  const int64_t Dall = static_cast<int64_t>(d) * K;
+  const int npairs = d * (d - 1) / 2;
+  cudaEvent_t ev[4];
+  for (int i = 0; i < 4; ++i) cudaEventCreate(&ev[i]);
+  cudaEventRecord(ev[0], st);
+
+  // 1-D moments and right-hand sides per coordinate
+  EsPlan p1;
+  FK_TRY(make_es_plan(1, 2 * m, eps, o.upsampfac, &p1));
+  double *corr1, *grid1, *T1, *bt, *rhs;
+  FK_TRY(scr.alloc(&corr1, 2 * static_cast<size_t>(p1.kmax) + 1));
+  FK_TRY(scr.alloc(&grid1, static_cast<size_t>(p1.N) * (1 + nt)));
+  FK_TRY(scr.alloc(&T1, 2 * static_cast<size_t>(d) * M2));
+  FK_TRY(scr.alloc(&bt, 2 * static_cast<size_t>(nt) * K));
+  FK_TRY(scr.alloc(&rhs, 2 * static_cast<size_t>(nt) * Dall));
+  FK_TRY(es_correction(p1, corr1, st));
+  const double inv_n = 1.0 / static_cast<double>(n);
+  for (int l = 0; l < d; ++l) {
+    Scratch inner(st);  // released (stream-ordered) after each coordinate
+    FK_TRY(spread_atomic<R>(p1, n, x + static_cast<int64_t>(l) * n, y, nt, true, grid1, flags, st));
+    if (precision == FK_FP64) {
+      FK_TRY(grid_to_modes<double>(p1, grid1, 0, 1, 2 * m, corr1, inv_n, T1 + 2 * static_cast<int64_t>(l) * M2, st, inner));
+      FK_TRY(grid_to_modes<double>(p1, grid1, 1, nt, m, corr1, inv_n, bt, st, inner));
+    } else {
+      FK_TRY(grid_to_modes<float>(p1, grid1, 0, 1, 2 * m, corr1, inv_n, T1 + 2 * static_cast<int64_t>(l) * M2, st, inner));
+      FK_TRY(grid_to_modes<float>(p1, grid1, 1, nt, m, corr1, inv_n, bt, st, inner));
+    }
+    // rhs[t][l K + k] = bt[t][k]
+    FK_CUDA(cudaMemcpy2DAsync(rhs + 2 * static_cast<int64_t>(l) * K, sizeof(double) * 2 * Dall, bt,
+                              sizeof(double) * 2 * K, sizeof(double) * 2 * K, nt, cudaMemcpyDeviceToDevice, st));
+  }
+  // 2-D blocks of ones at (X_l1, -X_l2)
+  EsPlan p2;
+  FK_TRY(make_es_plan(2, m, eps, o.upsampfac, &p2));
+  double *corr2, *grid2, *Bp;
+  R* pts;
+  FK_TRY(scr.alloc(&corr2, 2 * static_cast<size_t>(p2.kmax) + 1));
+  FK_TRY(scr.alloc(&grid2, static_cast<size_t>(p2.N) * p2.N));
+  FK_TRY(scr.alloc(&Bp, 2 * static_cast<size_t>(npairs > 0 ? npairs : 1) * K * K));
+  FK_TRY(scr.alloc(&pts, 2 * static_cast<size_t>(n)));
+  FK_TRY(es_correction(p2, corr2, st));
+  int pair = 0;
+  for (int l1 = 0; l1 < d; ++l1)
+    for (int l2 = l1 + 1; l2 < d; ++l2, ++pair) {
+      Scratch inner(st);  // released (stream-ordered) after each pair
+      k_pair_points<R><<<grid_for(n, 256), 256, 0, st>>>(n, x, l1, l2, pts); note_launch();
+      FK_CUDA(cudaGetLastError());
+      double* blk = Bp + 2 * static_cast<int64_t>(pair) * K * K;
+      if (precision == FK_FP64) {
+        FK_TRY(spread_atomic<double>(p2, n, reinterpret_cast<const double*>(pts), nullptr, 0, true, grid2, flags, st));
+        FK_TRY(grid_to_modes<double>(p2, grid2, 0, 1, m, corr2, inv_n, blk, st, inner));
+      } else {
+        const float* fp = reinterpret_cast<const float*>(pts);
+        if (o.spread != FK_SPREAD_ATOMIC && spread_binned_supported(p2, 0, true))
+          FK_TRY(spread_binned(p2, n, fp, nullptr, 0, true, grid2, flags, st, inner));
+        else
+          FK_TRY(spread_atomic<float>(p2, n, fp, nullptr, 0, true, grid2, flags, st));
+        FK_TRY(grid_to_modes<float>(p2, grid2, 0, 1, m, corr2, inv_n, blk, st, inner));
+      }
+    }
+  cudaEventRecord(ev[1], st);
+  // block Gram + lambda I, dense solve per lambda
+  double* A;
+  FK_TRY(scr.alloc(&A, 2 * Dall * Dall));
+  for (int li = 0; li < n_lambda; ++li) {
+    k_additive_gram<<<grid_for(Dall * Dall, 256), 256, 0, st>>>(d, m, T1, Bp, lambdas[li], A); note_launch();
+    FK_CUDA(cudaGetLastError());
+    double* X = theta + 2 * static_cast<int64_t>(li) * nt * Dall;
+    FK_CUDA(cudaMemcpyAsync(X, rhs, sizeof(double) * 2 * nt * Dall, cudaMemcpyDeviceToDevice, st));
+    Scratch inner(st);
+    FK_TRY(solve_dense(A, Dall, X, nt, o.refine_steps, st, inner, flags));
+  }
+  cudaEventRecord(ev[2], st);
+  unsigned h = 0;
+  FK_CUDA(cudaMemcpyAsync(&h, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  FK_CUDA(cudaStreamSynchronize(st));
+  if (rep) {
+    *rep = fk_report{};
+    float a = 0.f, b2 = 0.f;
+    cudaEventElapsedTime(&a, ev[0], ev[1]);
+    cudaEventElapsedTime(&b2, ev[1], ev[2]);
+    rep->ms_spread = a;
+    rep->ms_solve = b2;
+    rep->ms_total = a + b2;
+    rep->n_used = n;
+    rep->fine_grid = p2.N;
+    rep->kernel_width = p2.w;
+  }
+  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  if (h & FLAG_RANGE) return set_error(FK_ERANGE, "a point lies outside [-3 pi, 3 pi)");
+  if (h & FLAG_NOTPD) return set_error(FK_ENOTPD, "Cholesky met a non-positive pivot");
+  if (h) return set_error(FK_EINTERNAL, "device flag 0x%x", h);
+  return FK_OK;
+}
+
+template <typename R>
+fk_status predict_additive_impl(int d, int m, const double* theta, int n_sets, int64_t nq, const R* xq, double eps,
+                                double* f, cudaStream_t st) {
+  Scratch scr(st);
+  unsigned* flags;
+  FK_TRY(scr.alloc(&flags, 1));
+  FK_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned), st));
+  const int K = 2 * m + 1;
+  EsPlan p;
+  FK_TRY(make_es_plan(1, m, eps, 1.9, &p));
+  double *corr, *coef, *part;
+  FK_TRY(scr.alloc(&corr, 2 * static_cast<size_t>(m) + 1));
+  FK_TRY(scr.alloc(&coef, 2 * static_cast<size_t>(n_sets) * K));
+  FK_TRY(scr.alloc(&part, static_cast<size_t>(n_sets) * nq));
+  FK_TRY(es_correction(p, corr, st));
+  FK_CUDA(cudaMemsetAsync(f, 0, sizeof(double) * n_sets * nq, st));
+  for (int l = 0; l < d; ++l) {
+    FK_CUDA(cudaMemcpy2DAsync(coef, sizeof(double) * 2 * K, theta + 2 * static_cast<int64_t>(l) * K,
+                              sizeof(double) * 2 * d * K, sizeof(double) * 2 * K, n_sets, cudaMemcpyDeviceToDevice, st));
+    FK_TRY(type2_eval<R>(p, m, coef, n_sets, nq, xq + static_cast<int64_t>(l) * nq, corr, part, flags, st, scr));
+    k_add_into<<<grid_for(static_cast<int64_t>(n_sets) * nq, 256), 256, 0, st>>>(static_cast<int64_t>(n_sets) * nq,
+                                                                                   part, f); note_launch();
+    FK_CUDA(cudaGetLastError());
+  }
+  unsigned h = 0;
+  FK_CUDA(cudaMemcpyAsync(&h, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  FK_CUDA(cudaStreamSynchronize(st));
+  if (h & FLAG_RANGE) return set_error(FK_ERANGE, "a point lies outside [-3 pi, 3 pi)");
+  return FK_OK;
+}
+
+}  // namespace
+
+fk_status fit_additive(int d, int64_t n, const void* x, const void* y, int nt, int m, const double* lambdas,
+                       int n_lambda, double eps, int precision, const fk_opts& o, double* theta, cudaStream_t st,
+                       fk_report* rep) {
+  if (precision == FK_FP64)
+    return fit_additive_impl<double>(d, n, static_cast<const double*>(x), static_cast<const double*>(y), nt, m, lambdas,
+                                     n_lambda, eps, precision, o, theta, st, rep);
+  return fit_additive_impl<float>(d, n, static_cast<const float*>(x), static_cast<const float*>(y), nt, m, lambdas,
+                                  n_lambda, eps, precision, o, theta, st, rep);
+}
+
+fk_status predict_additive(int d, int m, const double* theta, int n_sets, int64_t nq, const void* xq, double eps,
+                           int precision, double* f, cudaStream_t st) {
+  if (precision == FK_FP64)
+    return predict_additive_impl<double>(d, m, theta, n_sets, nq, static_cast<const double*>(xq), eps, f, st);
+  return predict_additive_impl<float>(d, m, theta, n_sets, nq, static_cast<const float*>(xq), eps, f, st);
+}
+
+}  // namespace fk

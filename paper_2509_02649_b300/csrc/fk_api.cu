@@ -359,15 +359,29 @@ fk_status fk_fit_additive(int d, int64_t n, const void* x, const void* y, int n_
                           const double* lambdas, int n_lambda, double eps, int precision, const fk_opts* opts,
                           double* theta, void* stream, fk_report* rep) {
   clear_error();
-  (void)d; (void)n; (void)x; (void)y; (void)n_targets; (void)m; (void)lambdas; (void)n_lambda; (void)eps;
-  (void)precision; (void)opts; (void)theta; (void)stream; (void)rep;
-  return set_error(FK_EINVAL, "fk_fit_additive: not built yet");
+  if (d < 2 || d > 16) return set_error(FK_EINVAL, "additive model: d = %d outside [2, 16]", d);
+  if (n < 1) return set_error(FK_EINVAL, "n = %lld < 1", (long long)n);
+  if (m < 0) return set_error(FK_EINVAL, "m = %d < 0", m);
+  if (!(eps >= 1e-14 && eps <= 1e-1)) return set_error(FK_EINVAL, "eps = %g outside [1e-14, 1e-1]", eps);
+  if (precision != FK_FP64 && precision != FK_MIXED) return set_error(FK_EINVAL, "unknown precision %d", precision);
+  if (!x || !y || !theta || !lambdas || n_targets < 1 || n_lambda < 1) return set_error(FK_EINVAL, "bad fit arguments");
+  for (int i = 0; i < n_lambda; ++i)
+    if (!(lambdas[i] > 0.0)) return set_error(FK_EINVAL, "lambda[%d] = %g must be > 0 (Sigma is singular)", i, lambdas[i]);
+  if (static_cast<int64_t>(d) * (2 * m + 1) > 8192) return set_error(FK_EINVAL, "d (2m + 1) > 8192");
+  return fit_additive(d, n, x, y, n_targets, m, lambdas, n_lambda, eps, precision, resolve_opts(opts), theta,
+                      static_cast<cudaStream_t>(stream), rep);
 }
 
 fk_status fk_predict(int additive, int d, int m, const double* theta, int n_sets, int64_t n_q, const void* xq,
                      double eps, int precision, double* f, void* stream) {
   clear_error();
-  if (additive) return set_error(FK_EINVAL, "additive prediction: not built yet");
+  if (additive) {
+    if (d < 2 || d > 16 || m < 0 || n_sets < 1 || n_q < 1 || !theta || !xq || !f)
+      return set_error(FK_EINVAL, "bad additive prediction arguments");
+    if (!(eps >= 1e-14 && eps <= 1e-1)) return set_error(FK_EINVAL, "eps = %g outside [1e-14, 1e-1]", eps);
+    if (precision != FK_FP64 && precision != FK_MIXED) return set_error(FK_EINVAL, "unknown precision %d", precision);
+    return predict_additive(d, m, theta, n_sets, n_q, xq, eps, precision, f, static_cast<cudaStream_t>(stream));
+  }
   return fk_type2(d, m, theta, n_sets, n_q, xq, eps, precision, f, stream);
 }
 

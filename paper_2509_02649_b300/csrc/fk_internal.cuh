@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <string>
+#include <vector>
 
 #include "../../include/fk.h"
 
@@ -73,17 +74,17 @@ fk_status make_es_plan(int d, int kmax, double eps, double upsampfac, EsPlan* p)
 // Stream-ordered scratch allocation tracked for release at scope exit.
 struct Scratch {
   cudaStream_t st;
-  void* ptrs[64];
-  int count = 0;
+  std::vector<void*> ptrs;
   explicit Scratch(cudaStream_t s) : st(s) {}
   ~Scratch() { release(); }
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
   void release() {
-    for (int i = count - 1; i >= 0; --i) cudaFreeAsync(ptrs[i], st);
-    count = 0;
+    for (size_t i = ptrs.size(); i-- > 0;) cudaFreeAsync(ptrs[i], st);
+    ptrs.clear();
   }
   template <typename T>
   fk_status alloc(T** p, size_t elems) {
-    if (count >= 64) return set_error(FK_EINTERNAL, "scratch table full");
     size_t bytes = elems * sizeof(T);
     if (bytes == 0) bytes = 16;
     void* q = nullptr;
@@ -92,7 +93,7 @@ struct Scratch {
       cudaGetLastError();
       return set_error(FK_ENOMEM, "cudaMallocAsync(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
     }
-    ptrs[count++] = q;
+    ptrs.push_back(q);
     *p = static_cast<T*>(q);
     return FK_OK;
   }
@@ -155,6 +156,17 @@ int es_gl_nodes();
 template <typename R>
 fk_status grid_to_modes_into(const EsPlan& p, const double* grid, int c0, int nc, int kout, const double* corr,
                              double scale, double* out, cudaStream_t st, double* tw, cplx<R>* H);
+
+// Dense Hermitian positive definite solve (A row-major complex, kept); X: B in, solution out.
+fk_status solve_dense(const double* A, int64_t D, double* X, int n_rhs, int refine, cudaStream_t st, Scratch& scr,
+                      unsigned* flags);
+
+// Additive model (Prop. 5.1): theta [n_lambda][nt][d][2m+1]; prediction f [n_sets][nq].
+fk_status fit_additive(int d, int64_t n, const void* x, const void* y, int nt, int m, const double* lambdas,
+                       int n_lambda, double eps, int precision, const fk_opts& o, double* theta, cudaStream_t st,
+                       fk_report* rep);
+fk_status predict_additive(int d, int m, const double* theta, int n_sets, int64_t nq, const void* xq, double eps,
+                           int precision, double* f, cudaStream_t st);
 
 // FFT primitives (complex, in place on contiguous lines of length N, batched).
 template <typename R>

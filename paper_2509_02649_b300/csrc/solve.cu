@@ -701,3 +701,45 @@ fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, 
 }
 
 }  // namespace fk
+
+namespace fk {
+
+// R = B - A X for a dense row-major complex A (D x D); X, B, R: [n_rhs][D]
+__global__ void k_dense_residual(const double* A, int64_t D, const double* X, const double* B, double* R, int n_rhs) {
+  const int64_t total = D * n_rhs;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t rr = t / D, row = t - (t / D) * D;
+    const double* a = A + 2 * row * D;
+    const double* x = X + 2 * rr * D;
+    cd acc = cd{B[2 * t], B[2 * t + 1]};
+    for (int64_t c = 0; c < D; ++c) acc = csub(acc, cmul(cd{a[2 * c], a[2 * c + 1]}, cd{x[2 * c], x[2 * c + 1]}));
+    R[2 * t] = acc.x;
+    R[2 * t + 1] = acc.y;
+  }
+}
+
+// Solve A X = B for a dense Hermitian positive definite A (row-major complex, unchanged):
+// Cholesky of a copy, triangular solves, `refine` steps of iterative refinement against A.
+// X holds B on entry and the solution on exit.
+fk_status solve_dense(const double* A, int64_t D, double* X, int n_rhs, int refine, cudaStream_t st, Scratch& scr,
+                      unsigned* flags) {
+  double *L, *B, *R;
+  FK_TRY(scr.alloc(&L, 2 * D * D));
+  FK_TRY(scr.alloc(&B, 2 * D * n_rhs));
+  FK_TRY(scr.alloc(&R, 2 * D * n_rhs));
+  FK_CUDA(cudaMemcpyAsync(L, A, sizeof(double) * 2 * D * D, cudaMemcpyDeviceToDevice, st));
+  FK_CUDA(cudaMemcpyAsync(B, X, sizeof(double) * 2 * D * n_rhs, cudaMemcpyDeviceToDevice, st));
+  FK_TRY(cholesky(L, D, flags, st));
+  k_trisolve<<<(n_rhs + RB - 1) / RB, 256, 0, st>>>(L, D, X, n_rhs); note_launch();
+  FK_CUDA(cudaGetLastError());
+  for (int it = 0; it < refine; ++it) {
+    k_dense_residual<<<grid_for(D * n_rhs, 128), 128, 0, st>>>(A, D, X, B, R, n_rhs); note_launch();
+    k_trisolve<<<(n_rhs + RB - 1) / RB, 256, 0, st>>>(L, D, R, n_rhs); note_launch();
+    k_axpy_c<<<grid_for(2 * D * n_rhs, 256), 256, 0, st>>>(2 * D * n_rhs, R, X); note_launch();
+    FK_CUDA(cudaGetLastError());
+  }
+  return FK_OK;
+}
+
+}  // namespace fk
