@@ -209,7 +209,9 @@ def main():
     ms_step = ms / args.steps
     value = world * n * args.steps / (ms / 1e3)
 
-    # dominant kernel: the spreading stage, timed by CUDA events on the launching stream
+    # dominant kernel: the register-accumulation spreading kernel, timed by CUDA events
+    # recorded on its own stream inside the library (fk_report.ms_kernel)
+    ms_kernel = statistics.mean(r["ms_kernel"] for r in reps)
     ms_spread = statistics.mean(r["ms_spread"] for r in reps)
     w = reps[-1]["kernel_width"]
     C = 2
@@ -217,14 +219,17 @@ def main():
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2032.0)
     peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    achieved = f_pt * n / (ms_spread / 1e3) / 1e12
+    achieved = f_pt * n / (ms_kernel / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": None,
-                "kernel": "spreading stage", "flop_per_point": f_pt, "kernel_width": w,
-                "peak_basis": "148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (unit counts and max clock)" % sm_max,
-                "ms_spread": ms_spread, "ms_fft": statistics.mean(r["ms_fft"] for r in reps),
-                "ms_solve": statistics.mean(r["ms_solve"] for r in reps), "cg_iters": reps[-1]["cg_iters"],
-                "hbm_view": {"bytes_per_point": 12, "achieved_GBs": 12 * n / (ms_spread / 1e3) / 1e9,
+                "kernel": "k_bin_accumulate (register-accumulation spreading)",
+                "flop_per_point": f_pt, "kernel_width": w, "ms_kernel": ms_kernel,
+                "peak_basis": "of derived peak: 148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % sm_max,
+                "stage": {"ms_spread_all_kernels": ms_spread,
+                          "achieved_TFLOPs": f_pt * n / (ms_spread / 1e3) / 1e12,
+                          "ms_fft": statistics.mean(r["ms_fft"] for r in reps),
+                          "ms_solve": statistics.mean(r["ms_solve"] for r in reps), "cg_iters": reps[-1]["cg_iters"]},
+                "hbm_view": {"bytes_per_point_input": 12, "achieved_GBs": 12 * n / (ms_spread / 1e3) / 1e9,
                              "peak_GBs": peaks.get("hbm_gbs"), "of": "measured"}}
 
     line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,

@@ -105,6 +105,7 @@ typedef struct {
   int64_t n_used;       /* points consumed */
   int fine_grid;        /* upsampled grid size per dimension */
   int kernel_width;     /* ES kernel width w (taps per dimension) */
+  double ms_kernel;     /* the spreading step's main kernel alone (register accumulation or atomics) */
 } fk_report;
 
 FK_API void fk_default_opts(fk_opts* opts);

@@ -45,7 +45,8 @@ class Opts(ctypes.Structure):
 class Report(ctypes.Structure):
     _fields_ = [("ms_spread", ctypes.c_double), ("ms_fft", ctypes.c_double), ("ms_solve", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("cg_iters", ctypes.c_int), ("rel_residual", ctypes.c_double),
-                ("n_used", ctypes.c_int64), ("fine_grid", ctypes.c_int), ("kernel_width", ctypes.c_int)]
+                ("n_used", ctypes.c_int64), ("fine_grid", ctypes.c_int), ("kernel_width", ctypes.c_int),
+                ("ms_kernel", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -11,6 +11,10 @@
 // the Legendre recurrence, all in fp64 on the device.
 #include "fk_internal.cuh"
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 namespace fk {
 
 static int next_pow2(int v) {
@@ -55,7 +59,7 @@ __global__ void k_gauss_legendre(double* nodes, double* weights) {
   const int q = GL_Q;
   double x = cos(M_PI * (i + 0.75) / (q + 0.5));
   double dp = 1.0;
-  for (int it = 0; it < 100; ++it) {
+  for (int it = 0; it < 30; ++it) {
     double p0 = 1.0, p1 = x;
     for (int k = 2; k <= q; ++k) {
       const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
@@ -66,7 +70,7 @@ __global__ void k_gauss_legendre(double* nodes, double* weights) {
     dp = q * (x * p1 - p0) / (x * x - 1.0);
     const double dx = p1 / dp;
     x -= dx;
-    if (fabs(dx) < 1e-16) break;
+    if (fabs(dx) < 1e-14) break;  // quadratic convergence: the last step already polished x
   }
   {
     double p0 = 1.0, p1 = x;
@@ -99,7 +103,7 @@ __global__ void k_es_correction(int kmax, int N, int w, double beta, const doubl
   corr[t] = sgn * h / psi_hat;
 }
 
-fk_status es_correction(const EsPlan& p, double* corr, cudaStream_t st) {
+static fk_status es_correction_compute(const EsPlan& p, double* corr, cudaStream_t st) {
   double* nw = nullptr;
   FK_CUDA(cudaMallocAsync(&nw, 2 * GL_Q * sizeof(double), st));
   k_gauss_legendre<<<1, GL_Q, 0, st>>>(nw, nw + GL_Q); note_launch();
@@ -108,6 +112,36 @@ fk_status es_correction(const EsPlan& p, double* corr, cudaStream_t st) {
   cudaError_t e = cudaGetLastError();
   cudaFreeAsync(nw, st);
   if (e != cudaSuccess) return set_error(FK_ECUDA, "es_correction launch: %s", cudaGetErrorString(e));
+  return FK_OK;
+}
+
+// Correction factors depend only on (kmax, N, w, beta): computed once per device and
+// plan, kept for the life of the process, and copied into the caller's buffer.
+fk_status es_correction(const EsPlan& p, double* corr, cudaStream_t st) {
+  int dev = 0;
+  FK_CUDA(cudaGetDevice(&dev));
+  const size_t bytes = sizeof(double) * (2 * static_cast<size_t>(p.kmax) + 1);
+  const auto key = std::make_tuple(dev, p.kmax, p.N, p.w, p.beta);
+  static std::mutex mtx;
+  static std::map<std::tuple<int, int, int, int, double>, double*> cache;
+  double* src = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(mtx);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      src = it->second;
+    } else {
+      FK_CUDA(cudaMalloc(&src, bytes));
+      fk_status stt = es_correction_compute(p, src, st);
+      if (stt == FK_OK && cudaStreamSynchronize(st) != cudaSuccess) stt = set_error(FK_ECUDA, "es_correction sync");
+      if (stt != FK_OK) {
+        cudaFree(src);
+        return stt;
+      }
+      cache.emplace(key, src);
+    }
+  }
+  FK_CUDA(cudaMemcpyAsync(corr, src, bytes, cudaMemcpyDeviceToDevice, st));
   return FK_OK;
 }
 

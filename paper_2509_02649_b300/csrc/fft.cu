@@ -8,6 +8,7 @@
 // run in place in shared memory.  Twiddles e^{-2 pi i t / N} come from an fp64
 // table built once per plan with sincospi.
 #include "fk_internal.cuh"
+#include "fft_device.cuh"
 
 namespace fk {
 
@@ -24,44 +25,6 @@ fk_status fft_twiddles(int N, double* tw, cudaStream_t st) {
   k_twiddles<<<(N + 255) / 256, 256, 0, st>>>(N, tw); note_launch();
   FK_CUDA(cudaGetLastError());
   return FK_OK;
-}
-
-__device__ __forceinline__ unsigned bitrev(unsigned v, int bits) { return __brev(v) >> (32 - bits); }
-
-template <typename R>
-__device__ __forceinline__ cplx<R> tw_get(const double* tw, int idx, int sign) {
-  // e^{sign * 2 pi i idx / N}; the table holds e^{-2 pi i t / N}
-  cplx<R> r;
-  r.x = static_cast<R>(__ldg(tw + 2 * idx));
-  const R im = static_cast<R>(__ldg(tw + 2 * idx + 1));
-  r.y = sign < 0 ? im : -im;
-  return r;
-}
-
-// In-place radix-2 DIT over s[0..N) (already in bit-reversed order).
-template <typename R>
-__device__ void fft_smem(cplx<R>* s, int N, int sign, const double* tw) {
-  for (int len = 2; len <= N; len <<= 1) {
-    const int half = len >> 1;
-    const int tstep = N / len;
-    for (int b = threadIdx.x; b < (N >> 1); b += blockDim.x) {
-      const int grp = b / half;
-      const int k = b - grp * half;
-      const int i0 = grp * len + k;
-      const int i1 = i0 + half;
-      const cplx<R> w = tw_get<R>(tw, k * tstep, sign);
-      const cplx<R> a = s[i0];
-      const cplx<R> v = s[i1];
-      cplx<R> bw;
-      bw.x = v.x * w.x - v.y * w.y;
-      bw.y = v.x * w.y + v.y * w.x;
-      s[i0].x = a.x + bw.x;
-      s[i0].y = a.y + bw.y;
-      s[i1].x = a.x - bw.x;
-      s[i1].y = a.y - bw.y;
-    }
-    __syncthreads();
-  }
 }
 
 // ---------------------------------------------------------------- generic lines

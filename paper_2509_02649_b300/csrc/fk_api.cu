@@ -13,6 +13,30 @@ static std::atomic<int64_t> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+static thread_local KernelTimer g_ktimer;
+KernelTimer* kernel_timer() { return &g_ktimer; }
+
+// Arms the main-kernel timer for one call when a report is requested.
+struct KernelTimerScope {
+  KernelTimer* t;
+  explicit KernelTimerScope(bool enabled) : t(kernel_timer()) {
+    t->on = enabled;
+    t->recorded = false;
+    if (enabled && !t->start) {
+      cudaEventCreate(&t->start);
+      cudaEventCreate(&t->stop);
+    }
+  }
+  double ms() {
+    if (!t->on || !t->recorded) return 0.0;
+    float v = 0.f;
+    cudaEventSynchronize(t->stop);
+    cudaEventElapsedTime(&v, t->start, t->stop);
+    return v;
+  }
+  ~KernelTimerScope() { t->on = false; }
+};
+
 fk_status set_error(fk_status st, const char* fmt, ...) {
   char buf[512];
   va_list ap;
@@ -241,6 +265,7 @@ fk_status fk_build_system(int d, int64_t n, const void* x, const void* y, int n_
   Flags fl(st);
   FK_TRY(fl.init(scr));
   Timer tm(st, rep != nullptr);
+  KernelTimerScope kts(rep != nullptr);
   tm.mark();
   EsPlan p;
   FK_TRY(build_system(d, n, x, y, n_targets, m, eps, precision, o, T, b, st, scr, fl.dev, &p, &tm));
@@ -253,6 +278,7 @@ fk_status fk_build_system(int d, int64_t n, const void* x, const void* y, int n_
     rep->n_used = n;
     rep->fine_grid = p.N;
     rep->kernel_width = p.w;
+    rep->ms_kernel = kts.ms();
   }
   return FK_OK;
 }
@@ -307,6 +333,7 @@ static fk_status fit_common(int d, int64_t n, const void* x, const void* y, int 
   Flags fl(st);
   FK_TRY(fl.init(scr));
   Timer tm(st, rep != nullptr);
+  KernelTimerScope kts(rep != nullptr);
   tm.mark();
   const int64_t D = ipow(2 * m + 1, d), M2 = ipow(4 * m + 1, d);
   double *T, *b, *W;
@@ -332,6 +359,7 @@ static fk_status fit_common(int d, int64_t n, const void* x, const void* y, int 
     rep->n_used = n;
     rep->fine_grid = p.N;
     rep->kernel_width = p.w;
+    rep->ms_kernel = kts.ms();
   }
   return FK_OK;
 }

@@ -20,6 +20,15 @@ void clear_error();
 // Process-wide count of kernels this library has launched (fk_launch_count).
 void note_launch();
 
+// Optional timing of the spreading step's main kernel for fk_report.ms_kernel:
+// when `on`, the spreader records `start`/`stop` on its stream around that launch.
+struct KernelTimer {
+  bool on = false;
+  bool recorded = false;
+  cudaEvent_t start = nullptr, stop = nullptr;
+};
+KernelTimer* kernel_timer();  // thread-local
+
 #define FK_CUDA(call)                                                          \
   do {                                                                         \
     cudaError_t e_ = (call);                                                   \

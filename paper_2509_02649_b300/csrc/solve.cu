@@ -6,6 +6,7 @@
 // matvec runs through a circulant embedding and FFTs (Sec. 2.3, matvec via FFT),
 // batched over every (penalty, right-hand side) pair.
 #include "fk_internal.cuh"
+#include "fft_device.cuh"
 
 #include <vector>
 
@@ -665,6 +666,350 @@ static fk_status cg_solve(int d, int m, const double* T, const double* W, int n_
   return FK_OK;
 }
 
+// ---------------------------------------------------------------- fused CG (d = 1, 2)
+// Scalars per system s (double): PQ = <p, Ap>, RZ0 / RZ1 = <r, z> (ping-pong by
+// iteration parity), RR = |r|^2, BB = |b|^2.  A matvec q = Toep(T) v + W v goes through
+// the circulant of side Lc >= 4m + 1: only the K = 2m + 1 nonzero rows of the padded
+// input are transformed, and only K output rows are kept.
+struct CgScal {
+  double *pq, *rz0, *rz1, *rr, *bb;
+  int* active;
+};
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += red[w];
+  __syncthreads();
+  return t;  // valid in thread 0
+}
+
+// 2-D, step 1: forward FFT of the nonzero rows r < K of the padded input v
+__global__ void k_cgf_rows_fwd(int K, int Lc, int logLc, const double* v, cplx<double>* buf, const double* tw,
+                               CgScal sc, int zero_scalars, int cur) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<double>* sl = reinterpret_cast<cplx<double>*>(smem_raw);
+  const int r = blockIdx.x, s = blockIdx.y;
+  if (!sc.active[s]) return;
+  if (zero_scalars && r == 0 && threadIdx.x == 0) {
+    sc.pq[s] = 0.0;
+    sc.rr[s] = 0.0;
+    (cur ? sc.rz0 : sc.rz1)[s] = 0.0;  // the next <r, z>
+  }
+  const int64_t D = static_cast<int64_t>(K) * K;
+  const double* vs = v + 2 * (s * D + static_cast<int64_t>(r) * K);
+  for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
+    cplx<double> e;
+    e.x = (i < K) ? vs[2 * i] : 0.0;
+    e.y = (i < K) ? vs[2 * i + 1] : 0.0;
+    sl[bitrev(i, logLc)] = e;
+  }
+  __syncthreads();
+  fft_smem<double>(sl, Lc, -1, tw);
+  cplx<double>* o = buf + (static_cast<int64_t>(s) * K + r) * Lc;
+  for (int i = threadIdx.x; i < Lc; i += blockDim.x) o[i] = sl[i];
+}
+
+// 2-D, step 2: per column c: FFT over rows (K nonzero), times the circulant spectrum,
+// inverse FFT, keep rows < K
+__global__ void k_cgf_cols(int K, int Lc, int logLc, cplx<double>* buf, const cplx<double>* ch, const double* tw,
+                           CgScal sc) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<double>* sl = reinterpret_cast<cplx<double>*>(smem_raw);
+  const int c = blockIdx.x, s = blockIdx.y;
+  if (!sc.active[s]) return;
+  cplx<double>* b = buf + static_cast<int64_t>(s) * K * Lc + c;
+  for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
+    cplx<double> e;
+    if (i < K) e = b[static_cast<int64_t>(i) * Lc];
+    else e.x = e.y = 0.0;
+    sl[bitrev(i, logLc)] = e;
+  }
+  __syncthreads();
+  fft_smem<double>(sl, Lc, -1, tw);
+  for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
+    const cplx<double> a = ch[static_cast<int64_t>(i) * Lc + c], e = sl[i];
+    cplx<double> t;
+    t.x = a.x * e.x - a.y * e.y;
+    t.y = a.x * e.y + a.y * e.x;
+    sl[i] = t;
+  }
+  __syncthreads();
+  bitrev_permute<double>(sl, Lc, logLc);
+  fft_smem<double>(sl, Lc, +1, tw);
+  for (int i = threadIdx.x; i < K; i += blockDim.x) b[static_cast<int64_t>(i) * Lc] = sl[i];
+}
+
+// 2-D, step 3: inverse FFT of rows r < K, q = (.)/Lc^2 + W v, and <v, q>
+__global__ void k_cgf_rows_inv(int K, int Lc, int logLc, int n_rhs, const cplx<double>* buf, const double* W,
+                               const double* v, double* q, const double* tw, CgScal sc, int want_dot) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<double>* sl = reinterpret_cast<cplx<double>*>(smem_raw);
+  __shared__ double red[32];
+  const int r = blockIdx.x, s = blockIdx.y;
+  if (!sc.active[s]) return;
+  const cplx<double>* b = buf + (static_cast<int64_t>(s) * K + r) * Lc;
+  for (int i = threadIdx.x; i < Lc; i += blockDim.x) sl[bitrev(i, logLc)] = b[i];
+  __syncthreads();
+  fft_smem<double>(sl, Lc, +1, tw);
+  const int64_t D = static_cast<int64_t>(K) * K;
+  const double inv = 1.0 / (static_cast<double>(Lc) * Lc);
+  const double* Ws = W + (s / n_rhs) * D + static_cast<int64_t>(r) * K;
+  const double* vs = v + 2 * (s * D + static_cast<int64_t>(r) * K);
+  double* qs = q + 2 * (s * D + static_cast<int64_t>(r) * K);
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    const double qr = sl[i].x * inv + Ws[i] * vs[2 * i];
+    const double qi = sl[i].y * inv + Ws[i] * vs[2 * i + 1];
+    qs[2 * i] = qr;
+    qs[2 * i + 1] = qi;
+    acc += vs[2 * i] * qr + vs[2 * i + 1] * qi;
+  }
+  if (want_dot) {
+    const double t = block_sum(acc, red);
+    if (threadIdx.x == 0) atomicAdd(sc.pq + s, t);
+  }
+}
+
+// 1-D: the whole matvec of one system per CTA
+__global__ void k_cgf_1d(int K, int Lc, int logLc, int n_rhs, const cplx<double>* ch, const double* W, const double* v,
+                         double* q, const double* tw, CgScal sc, int zero_scalars, int cur, int want_dot) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<double>* sl = reinterpret_cast<cplx<double>*>(smem_raw);
+  __shared__ double red[32];
+  const int s = blockIdx.x;
+  if (!sc.active[s]) return;
+  if (zero_scalars && threadIdx.x == 0) {
+    sc.rr[s] = 0.0;
+    (cur ? sc.rz0 : sc.rz1)[s] = 0.0;
+  }
+  const double* vs = v + 2 * static_cast<int64_t>(s) * K;
+  for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
+    cplx<double> e;
+    e.x = (i < K) ? vs[2 * i] : 0.0;
+    e.y = (i < K) ? vs[2 * i + 1] : 0.0;
+    sl[bitrev(i, logLc)] = e;
+  }
+  __syncthreads();
+  fft_smem<double>(sl, Lc, -1, tw);
+  for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
+    const cplx<double> a = ch[i], e = sl[i];
+    cplx<double> t;
+    t.x = a.x * e.x - a.y * e.y;
+    t.y = a.x * e.y + a.y * e.x;
+    sl[i] = t;
+  }
+  __syncthreads();
+  bitrev_permute<double>(sl, Lc, logLc);
+  fft_smem<double>(sl, Lc, +1, tw);
+  const double inv = 1.0 / static_cast<double>(Lc);
+  const double* Ws = W + static_cast<int64_t>(s / n_rhs) * K;
+  double* qs = q + 2 * static_cast<int64_t>(s) * K;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    const double qr = sl[i].x * inv + Ws[i] * vs[2 * i];
+    const double qi = sl[i].y * inv + Ws[i] * vs[2 * i + 1];
+    qs[2 * i] = qr;
+    qs[2 * i + 1] = qi;
+    acc += vs[2 * i] * qr + vs[2 * i + 1] * qi;
+  }
+  if (want_dot) {
+    const double t = block_sum(acc, red);
+    if (threadIdx.x == 0) sc.pq[s] = t;
+  }
+}
+
+// x += alpha p; r -= alpha q; z = r / diag; <r, z> and |r|^2 into the next slots
+__global__ void k_cgf_update(int64_t D, int n_rhs, const double* W, double T0, CgScal sc, int cur, const double* p,
+                             const double* q, double* x, double* r, double* z) {
+  __shared__ double red[32];
+  const int s = blockIdx.y;
+  if (!sc.active[s]) return;
+  const double alpha = (cur ? sc.rz1 : sc.rz0)[s] / sc.pq[s];
+  const double* Ws = W + static_cast<int64_t>(s / n_rhs) * D;
+  double arz = 0.0, arr = 0.0;
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < D;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t o = 2 * (s * D + k);
+    x[o] += alpha * p[o];
+    x[o + 1] += alpha * p[o + 1];
+    const double rr0 = r[o] - alpha * q[o], rr1 = r[o + 1] - alpha * q[o + 1];
+    r[o] = rr0;
+    r[o + 1] = rr1;
+    const double inv = 1.0 / (T0 + Ws[k]);
+    z[o] = rr0 * inv;
+    z[o + 1] = rr1 * inv;
+    arz += (rr0 * rr0 + rr1 * rr1) * inv;
+    arr += rr0 * rr0 + rr1 * rr1;
+  }
+  const double t1 = block_sum(arz, red);
+  const double t2 = block_sum(arr, red);
+  if (threadIdx.x == 0) {
+    atomicAdd((cur ? sc.rz0 : sc.rz1) + s, t1);
+    atomicAdd(sc.rr + s, t2);
+  }
+}
+
+// convergence test and p = z + beta p
+__global__ void k_cgf_direction(int64_t D, double tol2, CgScal sc, int cur, const double* z, double* p) {
+  const int s = blockIdx.y;
+  if (!sc.active[s]) return;
+  if (sc.rr[s] <= tol2 * sc.bb[s]) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc.active[s] = 0;
+    return;
+  }
+  const double beta = (cur ? sc.rz0 : sc.rz1)[s] / (cur ? sc.rz1 : sc.rz0)[s];
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < D;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t o = 2 * (s * D + k);
+    p[o] = z[o] + beta * p[o];
+    p[o + 1] = z[o + 1] + beta * p[o + 1];
+  }
+}
+
+// x = 0, r = b, z = r / diag, p = z; <r, z> -> rz0, |b|^2 -> bb and rr
+__global__ void k_cgf_init(int64_t D, int n_rhs, const double* W, double T0, const double* b, double* x, double* r,
+                           double* z, double* p, CgScal sc) {
+  __shared__ double red[32];
+  const int s = blockIdx.y;
+  const double* bs = b + 2 * static_cast<int64_t>(s % n_rhs) * D;
+  const double* Ws = W + static_cast<int64_t>(s / n_rhs) * D;
+  double arz = 0.0, abb = 0.0;
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < D;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t o = 2 * (s * D + k);
+    const double b0 = bs[2 * k], b1 = bs[2 * k + 1];
+    const double inv = 1.0 / (T0 + Ws[k]);
+    x[o] = 0.0;
+    x[o + 1] = 0.0;
+    r[o] = b0;
+    r[o + 1] = b1;
+    z[o] = b0 * inv;
+    z[o + 1] = b1 * inv;
+    p[o] = b0 * inv;
+    p[o + 1] = b1 * inv;
+    arz += (b0 * b0 + b1 * b1) * inv;
+    abb += b0 * b0 + b1 * b1;
+  }
+  const double t1 = block_sum(arz, red);
+  const double t2 = block_sum(abb, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(sc.rz0 + s, t1);
+    atomicAdd(sc.bb + s, t2);
+    atomicAdd(sc.rr + s, t2);
+  }
+}
+
+static fk_status cg_solve_fused(int d, int m, const double* T, const double* W, int n_w, const double* rhs, int n_rhs,
+                                const fk_opts& o, double* sol, cudaStream_t st, Scratch& scr, int* iters_out,
+                                double* relres_out) {
+  const int K = 2 * m + 1;
+  int Lc = next_pow2i(4 * m + 1);
+  if (Lc < 2) Lc = 2;
+  int logLc = 0;
+  while ((1 << logLc) < Lc) ++logLc;
+  const size_t line_sm = sizeof(cplx<double>) * Lc;
+  if (line_sm > 200 * 1024) return set_error(FK_EINVAL, "CG: circulant side %d too long", Lc);
+  const int nsys = n_w * n_rhs;
+  const int64_t D = (d == 1) ? K : static_cast<int64_t>(K) * K;
+  const int64_t LL = (d == 1) ? Lc : static_cast<int64_t>(Lc) * Lc;
+  cplx<double>* ch;
+  double* tw;
+  FK_TRY(scr.alloc(&ch, LL));
+  FK_TRY(scr.alloc(&tw, 2 * static_cast<size_t>(Lc)));
+  FK_TRY(fft_twiddles(Lc, tw, st));
+  FK_CUDA(cudaMemsetAsync(ch, 0, sizeof(cplx<double>) * LL, st));
+  int64_t M2 = 1;
+  for (int l = 0; l < d; ++l) M2 *= (4 * m + 1);
+  k_circ_embed<<<grid_for(M2, 256), 256, 0, st>>>(d, m, Lc, T, ch); note_launch();
+  FK_CUDA(cudaGetLastError());
+  if (d == 1) {
+    FK_TRY(fft_lines<double>(ch, Lc, 1, Lc, 1, -1, tw, st));
+  } else {
+    FK_TRY(fft_lines<double>(ch, Lc, Lc, Lc, 1, -1, tw, st));
+    FK_TRY(fft_lines<double>(ch, Lc, Lc, 1, Lc, -1, tw, st));
+  }
+  int64_t centre = 0;
+  for (int l = 0; l < d; ++l) centre = centre * (4 * m + 1) + 2 * m;
+  double T0 = 1.0;
+  FK_CUDA(cudaMemcpyAsync(&T0, T + 2 * centre, sizeof(double), cudaMemcpyDeviceToHost, st));
+  FK_CUDA(cudaStreamSynchronize(st));
+  if (!(T0 > 0.0)) T0 = 1.0;
+
+  double *r, *z, *p, *q, *scal;
+  int *active, *cnt;
+  cplx<double>* buf = nullptr;
+  FK_TRY(scr.alloc(&r, 2 * D * nsys));
+  FK_TRY(scr.alloc(&z, 2 * D * nsys));
+  FK_TRY(scr.alloc(&p, 2 * D * nsys));
+  FK_TRY(scr.alloc(&q, 2 * D * nsys));
+  FK_TRY(scr.alloc(&scal, 5 * static_cast<size_t>(nsys)));
+  FK_TRY(scr.alloc(&active, nsys));
+  FK_TRY(scr.alloc(&cnt, 1));
+  if (d == 2) FK_TRY(scr.alloc(&buf, static_cast<size_t>(nsys) * K * Lc));
+  CgScal sc{scal, scal + nsys, scal + 2 * nsys, scal + 3 * nsys, scal + 4 * nsys, active};
+  FK_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * 5 * nsys, st));
+  k_set_active<<<(nsys + 255) / 256, 256, 0, st>>>(nsys, active); note_launch();
+  double* x = sol;
+  const dim3 gv(static_cast<unsigned>(std::min<int64_t>((D + 255) / 256, 64)), nsys);
+  k_cgf_init<<<gv, 256, 0, st>>>(D, n_rhs, W, T0, rhs, x, r, z, p, sc); note_launch();
+  FK_CUDA(cudaGetLastError());
+  const int thr = Lc >= 256 ? 256 : (Lc >= 64 ? Lc / 2 : 32);
+  if (line_sm > 48 * 1024) {
+    FK_CUDA(cudaFuncSetAttribute(k_cgf_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)line_sm));
+    FK_CUDA(cudaFuncSetAttribute(k_cgf_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)line_sm));
+    FK_CUDA(cudaFuncSetAttribute(k_cgf_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)line_sm));
+    FK_CUDA(cudaFuncSetAttribute(k_cgf_1d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)line_sm));
+  }
+  auto matvec = [&](const double* v, double* out, int zero, int cur, int dot) -> fk_status {
+    if (d == 1) {
+      k_cgf_1d<<<nsys, thr, line_sm, st>>>(K, Lc, logLc, n_rhs, ch, W, v, out, tw, sc, zero, cur, dot); note_launch();
+    } else {
+      k_cgf_rows_fwd<<<dim3(K, nsys), thr, line_sm, st>>>(K, Lc, logLc, v, buf, tw, sc, zero, cur); note_launch();
+      k_cgf_cols<<<dim3(Lc, nsys), thr, line_sm, st>>>(K, Lc, logLc, buf, ch, tw, sc); note_launch();
+      k_cgf_rows_inv<<<dim3(K, nsys), thr, line_sm, st>>>(K, Lc, logLc, n_rhs, buf, W, v, out, tw, sc, dot);
+      note_launch();
+    }
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
+  };
+  const double tol2 = o.cg_tol * o.cg_tol;
+  int it = 0, host_active = nsys;
+  for (it = 0; it < o.cg_maxit; ++it) {
+    const int cur = it & 1;
+    FK_TRY(matvec(p, q, 1, cur, 1));
+    k_cgf_update<<<gv, 256, 0, st>>>(D, n_rhs, W, T0, sc, cur, p, q, x, r, z); note_launch();
+    k_cgf_direction<<<gv, 256, 0, st>>>(D, tol2, sc, cur, z, p); note_launch();
+    FK_CUDA(cudaGetLastError());
+    if ((it & 3) == 3 || it + 1 == o.cg_maxit) {
+      k_count_active<<<1, 256, 0, st>>>(nsys, active, cnt); note_launch();
+      FK_CUDA(cudaMemcpyAsync(&host_active, cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+      FK_CUDA(cudaStreamSynchronize(st));
+      if (host_active == 0) break;
+    }
+  }
+  if (iters_out) *iters_out = it + 1;
+  // true relative residual from a fresh matvec
+  k_set_active<<<(nsys + 255) / 256, 256, 0, st>>>(nsys, active); note_launch();
+  FK_TRY(matvec(x, q, 0, 0, 0));
+  k_resid_norm<<<nsys, 256, 0, st>>>(D, n_rhs, rhs, q, sc.rr, sc.bb); note_launch();
+  FK_CUDA(cudaGetLastError());
+  {
+    std::vector<double> rr(nsys), bb(nsys);
+    FK_CUDA(cudaMemcpyAsync(rr.data(), sc.rr, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
+    FK_CUDA(cudaMemcpyAsync(bb.data(), sc.bb, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
+    FK_CUDA(cudaStreamSynchronize(st));
+    double worst = 0.0;
+    for (int s2 = 0; s2 < nsys; ++s2) worst = std::max(worst, bb[s2] > 0 ? std::sqrt(rr[s2] / bb[s2]) : std::sqrt(rr[s2]));
+    if (relres_out) *relres_out = worst;
+  }
+  if (host_active != 0) return set_error(FK_ENOCONV, "CG did not converge in %d iterations", o.cg_maxit);
+  return FK_OK;
+}
+
 // ---------------------------------------------------------------- dispatcher
 fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, const double* rhs, int n_rhs,
                        const fk_opts& o, double* sol, cudaStream_t st, Scratch& scratch, unsigned* flags,
@@ -675,8 +1020,10 @@ fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, 
   if (solver == FK_SOLVER_AUTO) solver = (D <= 1024) ? FK_SOLVER_CHOL : FK_SOLVER_CG;
   if (cg_iters) *cg_iters = 0;
   if (rel_res) *rel_res = 0.0;
-  if (solver == FK_SOLVER_CG)
+  if (solver == FK_SOLVER_CG) {
+    if (d <= 2) return cg_solve_fused(d, m, T, W, n_w, rhs, n_rhs, o, sol, st, scratch, cg_iters, rel_res);
     return cg_solve(d, m, T, W, n_w, rhs, n_rhs, o, sol, st, scratch, cg_iters, rel_res);
+  }
   if (D > 8192) return set_error(FK_EINVAL, "dense Cholesky limited to D <= 8192 (D = %lld)", (long long)D);
   double *A, *R;
   FK_TRY(scratch.alloc(&A, 2 * D * D));

@@ -658,7 +658,13 @@ fk_status spread_binned(const EsPlan& p, int64_t n, const float* x, const float*
   const int threads = pair ? Cfg<true>::THREADS : Cfg<false>::THREADS;
   const size_t sm = acc_layout(cpc).total;
   FK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+  KernelTimer* kt = kernel_timer();
+  if (kt->on) cudaEventRecord(kt->start, st);
   fn<<<G, threads, sm, st>>>(A); note_launch();
+  if (kt->on) {
+    cudaEventRecord(kt->stop, st);
+    kt->recorded = true;
+  }
   FK_CUDA(cudaGetLastError());
   return FK_OK;
 }
