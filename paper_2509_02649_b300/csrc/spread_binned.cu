@@ -17,9 +17,10 @@
 //   k_bin_scan    turns the counts into per-(block, owner) offsets and per-owner totals,
 //                 each run padded to whole 128-byte lines (sentinel records) so that
 //                 the scattered record writes never share a line between blocks;
-//   k_bin_scatter (full occupancy) recomputes each point's cell and fractional
-//                 offsets and writes a 16-byte record {owner:local cell, f0, f1,
-//                 strength} at its owner's next free slot (shared-memory cursors);
+//   k_bin_scatter (one block per SM) recomputes each point's cell and fractional
+//                 offsets, sorts a tile by owner in shared memory and writes 16-byte
+//                 records {owner:local cell, f0, f1, strength} into per-owner buckets
+//                 as long contiguous runs (coalesced stores);
 //   k_bin_accumulate (one CTA per owner) streams its owner's bucket with double-
 //                 buffered TMA bulk copies, links each round's records into per-cell
 //                 lists in shared memory, and lets each lane run over at most a quota
@@ -157,7 +158,7 @@ __device__ __forceinline__ int warp_exclusive_scan(int* v, int cnt, int lane) {
   return carry;
 }
 
-constexpr int P_THREADS = 512;   // partition kernels
+constexpr int P_THREADS = 1024;  // count kernel
 constexpr int P_NWARPS = P_THREADS / 32;
 constexpr int P_TILE = 4096;     // points per partition block, at least
 constexpr int CAPR = 4096;       // records per accumulation round
@@ -295,46 +296,104 @@ __device__ __forceinline__ void owner_bases(const int* tot, int G, int* base, in
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(P_THREADS) k_bin_scatter(PartArgs A) {
-  extern __shared__ int cursor[];  // [G + 1]: global position of this block's next record per owner
+// Scatter in tiles of S_TILE points per block (one block per SM): the tile is sorted
+// by owner in shared memory and copied out with coalesced stores, so each owner's run
+// from a tile (S_TILE / G records on average) lands as one contiguous write; scattered
+// 16-byte writes would run at a small fraction of the write bandwidth.
+constexpr int S_THREADS = 1024;
+constexpr int S_TILE = 12288;
+
+__global__ void __launch_bounds__(S_THREADS, 1) k_bin_scatter(PartArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int wsum[32];
   const int G = A.G;
+  uint4* sorted = reinterpret_cast<uint4*>(smem);                          // [S_TILE]
+  unsigned short* own = reinterpret_cast<unsigned short*>(sorted + S_TILE); // [S_TILE] owner per point
+  int* cursor = reinterpret_cast<int*>(own + S_TILE);                      // [G + 1] global run positions
+  int* tcnt = cursor + (G + 1);                                            // [G + 1] tile counts -> offsets
+  int* tcur = tcnt + (G + 1);                                              // [G] fill cursors inside the tile
   const int tid = threadIdx.x;
   const float inv_cpc = 1.0f / static_cast<float>(A.cells_per);
   owner_bases(A.tot, G, cursor, wsum);
-  for (int o = tid; o < G; o += P_THREADS) cursor[o] += A.off[static_cast<size_t>(blockIdx.x) * G + o];
-  __syncthreads();
-  const int64_t s = static_cast<int64_t>(blockIdx.x) * A.range;
-  const int64_t e = min(A.n, s + A.range);
-  auto one = [&](float a0, float a1, float yy) {
-    float f0, f1;
-    uint32_t k;
-    if (!point_key(a0, a1, A, inv_cpc, &f0, &f1, &k)) return;
-    const int pos = atomicAdd(&cursor[k >> 16], 1);
-    A.rec[pos] = make_uint4(k, __float_as_uint(f0), __float_as_uint(f1), __float_as_uint(yy));
-  };
-  if (A.vec_ok) {
-    for (int64_t i = s + 4 * tid; i < e; i += 4 * P_THREADS) {
-      if (i + 3 < e) {
-        const float4 a = __ldg(reinterpret_cast<const float4*>(A.x + i));
-        const float4 c = __ldg(reinterpret_cast<const float4*>(A.x + A.n + i));
-        float4 yy = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (A.has_y) yy = __ldg(reinterpret_cast<const float4*>(A.y + i));
-        one(a.x, c.x, yy.x);
-        one(a.y, c.y, yy.y);
-        one(a.z, c.z, yy.z);
-        one(a.w, c.w, yy.w);
-      } else {
-        for (int64_t j = i; j < e; ++j) one(__ldg(A.x + j), __ldg(A.x + A.n + j), A.has_y ? __ldg(A.y + j) : 0.f);
+  for (int o = tid; o < G; o += S_THREADS) cursor[o] += A.off[static_cast<size_t>(blockIdx.x) * G + o];
+  const int64_t s0 = static_cast<int64_t>(blockIdx.x) * A.range;
+  const int64_t e0 = min(A.n, s0 + A.range);
+  for (int64_t t0 = s0; t0 < e0; t0 += S_TILE) {
+    const int cnt = (e0 - t0 < S_TILE) ? static_cast<int>(e0 - t0) : S_TILE;
+    for (int o = tid; o <= G; o += S_THREADS) tcnt[o] = 0;
+    __syncthreads();
+    // pass 1: owners and tile histogram
+    auto own_of = [&](int i, float a0, float a1) {
+      float f0, f1;
+      uint32_t k;
+      unsigned short o = 0xFFFF;
+      if (point_key(a0, a1, A, inv_cpc, &f0, &f1, &k)) {
+        o = static_cast<unsigned short>(k >> 16);
+        atomicAdd(&tcnt[o], 1);
+      }
+      own[i] = o;
+    };
+    if (A.vec_ok) {
+      for (int i = 4 * tid; i < cnt; i += 4 * S_THREADS) {
+        if (i + 3 < cnt) {
+          const float4 a = __ldg(reinterpret_cast<const float4*>(A.x + t0 + i));
+          const float4 c = __ldg(reinterpret_cast<const float4*>(A.x + A.n + t0 + i));
+          own_of(i, a.x, c.x);
+          own_of(i + 1, a.y, c.y);
+          own_of(i + 2, a.z, c.z);
+          own_of(i + 3, a.w, c.w);
+        } else {
+          for (int j = i; j < cnt; ++j) own_of(j, __ldg(A.x + t0 + j), __ldg(A.x + A.n + t0 + j));
+        }
+      }
+    } else {
+      for (int i = tid; i < cnt; i += S_THREADS) own_of(i, __ldg(A.x + t0 + i), __ldg(A.x + A.n + t0 + i));
+    }
+    __syncthreads();
+    if (tid < 32) {  // exclusive scan of the tile counts (one warp)
+      int carry = 0;
+      for (int o0 = 0; o0 <= G; o0 += 32) {
+        const int o = o0 + tid;
+        const int v = (o < G) ? tcnt[o] : 0;
+        int incl = v;
+#pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, dd);
+          if (tid >= dd) incl += t;
+        }
+        if (o <= G) tcnt[o] = carry + incl - v;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
       }
     }
-  } else {
-    for (int64_t i = s + tid; i < e; i += P_THREADS)
-      one(__ldg(A.x + i), __ldg(A.x + A.n + i), A.has_y ? __ldg(A.y + i) : 0.f);
+    __syncthreads();
+    for (int o = tid; o < G; o += S_THREADS) tcur[o] = tcnt[o];
+    __syncthreads();
+    // pass 2: records straight into their sorted slots (inputs re-read, now from L2)
+    for (int i = tid; i < cnt; i += S_THREADS) {
+      const unsigned short o = own[i];
+      if (o == 0xFFFF) continue;
+      float f0, f1;
+      uint32_t k;
+      point_key(__ldg(A.x + t0 + i), __ldg(A.x + A.n + t0 + i), A, inv_cpc, &f0, &f1, &k);
+      const int pos = atomicAdd(&tcur[o], 1);
+      sorted[pos] = make_uint4(k, __float_as_uint(f0), __float_as_uint(f1),
+                               A.has_y ? __float_as_uint(__ldg(A.y + t0 + i)) : 0u);
+    }
+    __syncthreads();
+    // coalesced copy-out: record j belongs to owner o = its high bits; its global slot is
+    // the owner's cursor plus its rank inside the owner's run of this tile
+    const int valid = tcnt[G];
+    for (int j = tid; j < valid; j += S_THREADS) {
+      const uint4 r = sorted[j];
+      const int o = static_cast<int>(r.x >> 16);
+      A.rec[cursor[o] + (j - tcnt[o])] = r;
+    }
+    __syncthreads();
+    for (int o = tid; o < G; o += S_THREADS) cursor[o] += tcnt[o + 1] - tcnt[o];
+    __syncthreads();
   }
-  __syncthreads();
   // sentinel records fill each run up to its padded length
-  for (int o = tid; o < G; o += P_THREADS) {
+  for (int o = tid; o < G; o += S_THREADS) {
     const int c = A.cnt[static_cast<size_t>(blockIdx.x) * G + o];
     for (int k = c; k < ((c + 7) & ~7); ++k) A.rec[cursor[o]++] = make_uint4(0xFFFFu, 0u, 0u, 0u);
   }
@@ -619,7 +678,8 @@ fk_status spread_binned(const EsPlan& p, int64_t n, const float* x, const float*
   P.x = x;
   P.y = y;
   P.has_y = n_y > 0 ? 1 : 0;
-  P.nblk = static_cast<int>(std::min<int64_t>((n + P_TILE - 1) / P_TILE, 4 * sm_count()));
+  // one partition block per SM; count and scatter use the same block ranges
+  P.nblk = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + P_TILE - 1) / P_TILE, sm_count())));
   P.range = ((n + P.nblk - 1) / P.nblk + 3) & ~static_cast<int64_t>(3);
   P.vec_ok = ((reinterpret_cast<uintptr_t>(x) & 15) == 0 && (n & 3) == 0 &&
               (n_y == 0 || (reinterpret_cast<uintptr_t>(y) & 15) == 0))
@@ -638,8 +698,9 @@ fk_status spread_binned(const EsPlan& p, int64_t n, const float* x, const float*
   FK_CUDA(cudaGetLastError());
   k_bin_scan<<<G, 256, 0, st>>>(P); note_launch();
   FK_CUDA(cudaGetLastError());
-  const size_t sm_scatter = sizeof(int) * (G + 1);
-  k_bin_scatter<<<P.nblk, P_THREADS, sm_scatter, st>>>(P); note_launch();
+  const size_t sm_scatter = sizeof(uint4) * S_TILE + sizeof(unsigned short) * S_TILE + sizeof(int) * (3 * G + 2);
+  FK_CUDA(cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm_scatter)));
+  k_bin_scatter<<<P.nblk, S_THREADS, sm_scatter, st>>>(P); note_launch();
   FK_CUDA(cudaGetLastError());
 
   AccArgs A{};
