@@ -30,6 +30,7 @@ WL = dict(workload="2d-sobolev", d=2, n=100_000_000, m=32, s=2.0, lam=1e-6, eps=
 METRIC = "fit points/s (NUFFT Gram+RHS+solve)"
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
+ACC_DRAM_BYTES_PER_POINT = (323.824896e6 + 4.352e6) / 2e7  # k_bin_accumulate, 2-D, w = 7
 
 
 def parse():
@@ -220,8 +221,12 @@ def main():
     sm_max = peaks.get("sm_max_mhz", 2032.0)
     peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = f_pt * n / (ms_kernel / 1e3) / 1e12
+    # DRAM bytes of one k_bin_accumulate launch: ncu capture of this kernel at n = 2e7
+    # (dram__bytes_read.sum 323.8 MB + dram__bytes_write.sum 4.35 MB), scaled by points
+    # (the reads are the 16-byte partition records, the writes the grid flush)
+    traffic = ACC_DRAM_BYTES_PER_POINT * n if (d == 2 and w == 7) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None,
+                "frac": achieved / peak_tflops, "traffic": traffic,
                 "kernel": "k_bin_accumulate (register-accumulation spreading)",
                 "flop_per_point": f_pt, "kernel_width": w, "ms_kernel": ms_kernel,
                 "peak_basis": "of derived peak: 148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % sm_max,
@@ -237,7 +242,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WL["workload"], "n": n, "d": d, "m": m, "s": s, "lambda": lam, "eps": eps,
                        "precision": "mixed (fp32 spread/FFT, fp64 assembly/solve)",
-                       "l2": "inputs (1.2 GB) larger than L2, no flush", "parallelism": "replicas" if world > 1 else "1 GPU"},
+                       "l2": "inputs (%.1f GB) larger than L2, no flush" % (12 * n / 1e9), "parallelism": "replicas" if world > 1 else "1 GPU"},
             "gpu_launches": launches, "roofline": roofline, "clocks": clk.summary()}
 
     if rank == 0 and not args.no_e2e:
