@@ -80,7 +80,11 @@ typedef enum {
 typedef enum { FK_FP64 = 0, FK_MIXED = 1 } fk_precision;
 typedef enum { FK_PEN_SOBOLEV = 0, FK_PEN_LOWBIAS = 1 } fk_penalty;
 typedef enum { FK_SOLVER_AUTO = 0, FK_SOLVER_CHOL = 1, FK_SOLVER_CG = 2 } fk_solver;
-typedef enum { FK_SPREAD_AUTO = 0, FK_SPREAD_ATOMIC = 1, FK_SPREAD_BINNED = 2 } fk_spread;
+/* Spreading methods of the mixed path: ATOMIC = fp64 global atomics per tap; BINNED =
+   2-D partition + register accumulation (d = 2, ones and/or one strength channel);
+   FIXED = 1-D integer fixed-point sums in shared memory (d = 1, any channel count,
+   bitwise reproducible). */
+typedef enum { FK_SPREAD_AUTO = 0, FK_SPREAD_ATOMIC = 1, FK_SPREAD_BINNED = 2, FK_SPREAD_FIXED = 3 } fk_spread;
 
 /* Options; pass NULL for defaults (fk_default_opts). */
 typedef struct {
@@ -90,7 +94,8 @@ typedef struct {
   int refine_steps;   /* iterative-refinement steps after a Cholesky solve (default 1) */
   double sobolev_c0;  /* c0 in lambda (c0 + |k|^{2s}); the paper's value is 1 (default 1) */
   double upsampfac;   /* minimum fine-grid oversampling sigma (default 1.9; grids are powers of 2) */
-  int spread;         /* fk_spread: AUTO = BINNED for FK_MIXED, ATOMIC for FK_FP64 */
+  int spread;         /* fk_spread: AUTO = BINNED (d = 2) or FIXED (d = 1) for FK_MIXED where the
+                         shape allows, else ATOMIC; FK_FP64 always spreads with ATOMIC */
   int deterministic;  /* reserved: 1 asks for run-to-run identical sums (default 0) */
 } fk_opts;
 
@@ -173,6 +178,43 @@ FK_API fk_status fk_type2(int d, int kmax, const double* coef, int n_sets, int64
 #define FK_NOALLOC_SCRATCH_BYTES (16u << 20)
 FK_API fk_status fk_type1_noalloc(int d, int64_t n, const void* x, const void* c, int n_ch, int kmax,
                                   double eps, int precision, double* out, void* stream);
+
+/* Streaming sums.  T_j and b_k (Sec. 2.3) are sums over points, so a sample larger
+ * than device memory (the 1-D sweep of 1e10 points) is added chunk by chunk onto
+ * upsampled grids held by an accumulator; transform, penalty and solve run once.
+ *   fk_accum_create: d in {1, 2}, m, n_targets in [0, 1024], eps and precision as in
+ *     fk_fit_sobolev; allocates the grids ((1 + n_targets) N^d doubles) with cudaMalloc.
+ *   fk_accum_add: adds n points (x: device d x n, y: device n_targets x n, precision as
+ *     created).  y_absmax (device, n_targets float bit patterns of max|y_t| over this
+ *     chunk, e.g. from fk_generate_sweep_1d) may be NULL; it sets the fixed-point scale
+ *     of the 1-D mixed spreader, which otherwise reads y once more to find it.
+ *     Asynchronous: inputs must stay valid until `stream` passes the call.
+ *     Range errors surface at the next fk_accum_system / fk_accum_fit_sobolev.
+ *   fk_accum_system: T (device complex (4m+1)^d) and b (device complex [n_targets][D]),
+ *     each divided by the total point count; either may be NULL.  Synchronises.
+ *   fk_accum_fit_sobolev: theta [n_lambda][n_targets][D] as fk_fit_sobolev.
+ *   fk_accum_reset: clears the sums.  fk_accum_destroy: frees (NULL is allowed).
+ * One accumulator is not safe for concurrent use from several host threads. */
+typedef struct fk_accum fk_accum;
+FK_API fk_status fk_accum_create(int d, int m, int n_targets, double eps, int precision,
+                                 const fk_opts* opts, fk_accum** out, void* stream);
+FK_API fk_status fk_accum_add(fk_accum* acc, int64_t n, const void* x, const void* y,
+                              const unsigned* y_absmax, void* stream);
+FK_API fk_status fk_accum_system(fk_accum* acc, double* T, double* b, int64_t* n_total, void* stream);
+FK_API fk_status fk_accum_fit_sobolev(fk_accum* acc, double s, int penalty, const double* lambdas,
+                                      int n_lambda, double* theta, void* stream, fk_report* rep);
+FK_API fk_status fk_accum_reset(fk_accum* acc, void* stream);
+FK_API fk_status fk_accum_destroy(fk_accum* acc);
+
+/* Synthetic 1-D sweep sample generated on the device (the paper's experiments are on
+ * synthetic data; this one is too large to pass from the host).  Points first ..
+ * first + n - 1 of the sample keyed by (seed, workload):
+ *   X_i ~ Uniform(-pi, pi) (fp32), Y_ti = sign(X_i)|X_i|^0.7 + 0.2 z_ti, z ~ N(0, 1),
+ * drawn with Philox4x32-10 counters so that any chunk can be made on its own.
+ *   first: multiple of 4;  x: device float[n];  y: device float[n_targets][n];
+ *   y_absmax: device unsigned[n_targets] (max |Y_t| of the chunk as float bits) or NULL. */
+FK_API fk_status fk_generate_sweep_1d(uint64_t seed, int workload, int64_t first, int64_t n, int n_targets,
+                                      float* x, float* y, unsigned* y_absmax, void* stream);
 
 /* Moments and right-hand sides: T (device complex, (4m+1)^d) and
  * b (device complex, [n_targets][D]), each divided by n (Sec. 2.3). */

@@ -19,14 +19,16 @@ from .build import LIB
 FK_FP64, FK_MIXED = 0, 1
 FK_PEN_SOBOLEV, FK_PEN_LOWBIAS = 0, 1
 FK_SOLVER_AUTO, FK_SOLVER_CHOL, FK_SOLVER_CG = 0, 1, 2
-FK_SPREAD_AUTO, FK_SPREAD_ATOMIC, FK_SPREAD_BINNED = 0, 1, 2
+FK_SPREAD_AUTO, FK_SPREAD_ATOMIC, FK_SPREAD_BINNED, FK_SPREAD_FIXED = 0, 1, 2, 3
 
 STATUS = {0: "FK_OK", 1: "FK_EINVAL", 2: "FK_ERANGE", 3: "FK_ENOMEM", 4: "FK_ECUDA", 5: "FK_ENOTPD",
           6: "FK_ENOCONV", 7: "FK_ETIMEOUT", 8: "FK_EINTERNAL"}
 
 EXPORTS = ["fk_default_opts", "fk_fit_sobolev", "fk_fit_pik", "fk_fit_additive", "fk_predict", "fk_type1",
            "fk_type2", "fk_build_system", "fk_penalty_weights", "fk_solve", "fk_hypergrad", "fk_last_error",
-           "fk_workspace_bytes", "fk_version", "fk_launch_count", "fk_type1_noalloc", "fk_penalty_grads"]
+           "fk_workspace_bytes", "fk_version", "fk_launch_count", "fk_type1_noalloc", "fk_penalty_grads",
+           "fk_accum_create", "fk_accum_add", "fk_accum_system", "fk_accum_fit_sobolev", "fk_accum_reset",
+           "fk_accum_destroy", "fk_generate_sweep_1d"]
 
 
 class FkError(RuntimeError):
@@ -83,6 +85,13 @@ def lib() -> ctypes.CDLL:
             "fk_launch_count": (ctypes.c_int64, []),
             "fk_type1_noalloc": (_I, [_I, _L, _P, _P, _I, _I, _D, _I, _P, _P]),
             "fk_penalty_grads": (_I, [_I, _I, _D, _D, _D, _D, _I, _P, _P, _P, _P, _P]),
+            "fk_accum_create": (_I, [_I, _I, _I, _D, _I, _P, ctypes.POINTER(_P), _P]),
+            "fk_accum_add": (_I, [_P, _L, _P, _P, _P, _P]),
+            "fk_accum_system": (_I, [_P, _P, _P, ctypes.POINTER(_L), _P]),
+            "fk_accum_fit_sobolev": (_I, [_P, _D, _I, _P, _I, _P, _P, _P]),
+            "fk_accum_reset": (_I, [_P, _P]),
+            "fk_accum_destroy": (_I, [_P]),
+            "fk_generate_sweep_1d": (_I, [ctypes.c_uint64, _I, _L, _L, _I, _P, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -308,3 +317,86 @@ def fk_penalty_grads(d: int, m: int, dW, lam: float, s: float = 1.0, mu: float =
     _check(lib().fk_penalty_grads(d, m, s, c0, lam, mu, len(a), alpha_arr, a_arr, dW.contiguous().data_ptr(), out,
                                   _stream()))
     return list(out)
+
+
+class Accumulator:
+    """Streaming sums of T and b over chunks of points (fk_accum_*): add chunks with
+    add(), then system() or fit_sobolev().  The device grids are freed by close()."""
+
+    def __init__(self, d: int, m: int, n_targets: int, eps: float, precision="mixed",
+                 opts: Optional[Opts] = None, device=None):
+        self.d, self.m, self.nt = d, m, n_targets
+        self.prec = _prec(precision)
+        self.device = torch.device("cuda") if device is None else torch.device(device)
+        h = _P()
+        _check(lib().fk_accum_create(d, m, n_targets, eps, self.prec, _opts_ptr(opts), ctypes.byref(h), _stream()))
+        self._h = h
+        self._keep = []  # chunk tensors kept alive until the next synchronising call
+
+    def add(self, x, y=None, y_absmax=None):
+        x = _points(x, self.prec)
+        n = x.shape[1]
+        if x.shape[0] != self.d:
+            raise ValueError("points have %d coordinates, accumulator %d" % (x.shape[0], self.d))
+        if self.nt:
+            y = y.reshape(self.nt, n).contiguous()
+        if y_absmax is not None and y_absmax.dtype != torch.int32:
+            raise ValueError("y_absmax must be the int32 bit patterns written by generate_sweep_1d")
+        _check(lib().fk_accum_add(self._h, n, x.data_ptr(), y.data_ptr() if self.nt else None,
+                                  y_absmax.data_ptr() if y_absmax is not None else None, _stream()))
+        self._keep.append((x, y, y_absmax))
+
+    def system(self):
+        T = torch.empty((4 * self.m + 1) ** self.d, dtype=torch.complex128, device=self.device)
+        b = torch.empty((max(self.nt, 1), (2 * self.m + 1) ** self.d), dtype=torch.complex128, device=self.device)
+        nt = _L()
+        _check(lib().fk_accum_system(self._h, T.data_ptr(), b.data_ptr() if self.nt else None, ctypes.byref(nt),
+                                     _stream()))
+        self._keep.clear()
+        return T, b[:self.nt], int(nt.value)
+
+    def fit_sobolev(self, s: float, lambdas, penalty: int = FK_PEN_SOBOLEV, report: bool = False):
+        lam = list(lambdas) if hasattr(lambdas, "__len__") else [lambdas]
+        theta = torch.empty((len(lam), self.nt, (2 * self.m + 1) ** self.d), dtype=torch.complex128,
+                            device=self.device)
+        rep = Report()
+        _check(lib().fk_accum_fit_sobolev(self._h, s, penalty, _dbl_array(lam), len(lam), theta.data_ptr(), _stream(),
+                                          ctypes.byref(rep) if report else None))
+        self._keep.clear()
+        return (theta, rep.as_dict()) if report else theta
+
+    def reset(self):
+        _check(lib().fk_accum_reset(self._h, _stream()))
+
+    def close(self):
+        if self._h:
+            torch.cuda.current_stream().synchronize()
+            _check(lib().fk_accum_destroy(self._h))
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def generate_sweep_1d(first: int, n: int, n_targets: int = 16, seed: int = 20250902, workload: int = 5,
+                      out=None, device=None):
+    """Points first .. first + n - 1 of the counter-based 1-D sweep sample (device):
+    returns x (1, n) float32, y (n_targets, n) float32 and max|y_t| as int32 float bits."""
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    if out is None:
+        x = torch.empty((1, n), dtype=torch.float32, device=dev)
+        y = torch.empty((n_targets, n), dtype=torch.float32, device=dev)
+        amax = torch.empty(max(n_targets, 1), dtype=torch.int32, device=dev)
+    else:
+        x, y, amax = out
+        if not (x.is_contiguous() and y.is_contiguous() and x.numel() == n and y.shape == (n_targets, n)
+                and x.dtype == torch.float32 and y.dtype == torch.float32 and amax.dtype == torch.int32
+                and amax.numel() >= n_targets):
+            raise ValueError("out must be contiguous float32 x (1, n), y (n_targets, n) and int32 amax")
+    _check(lib().fk_generate_sweep_1d(seed, workload, first, n, n_targets, x.data_ptr(), y.data_ptr(),
+                                      amax.data_ptr(), _stream()))
+    return x, y, amax

@@ -86,9 +86,19 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
   FK_TRY(scr.alloc(&rhs, 2 * static_cast<size_t>(nt) * Dall));
   FK_TRY(es_correction(p1, corr1, st));
   const double inv_n = 1.0 / static_cast<double>(n);
+  const bool fixed1d = (precision == FK_MIXED) && o.spread != FK_SPREAD_ATOMIC && spread1d_fixed_supported(p1, nt, true);
+  unsigned* amax = nullptr;
+  if (fixed1d) {
+    FK_TRY(scr.alloc(&amax, static_cast<size_t>(nt)));
+    FK_TRY(absmax_channels(n, reinterpret_cast<const float*>(y), nt, amax, st));
+  }
   for (int l = 0; l < d; ++l) {
     Scratch inner(st);  // released (stream-ordered) after each coordinate
-    FK_TRY(spread_atomic<R>(p1, n, x + static_cast<int64_t>(l) * n, y, nt, true, grid1, flags, st));
+    if (fixed1d)
+      FK_TRY(spread1d_fixed(p1, n, reinterpret_cast<const float*>(x + static_cast<int64_t>(l) * n),
+                            reinterpret_cast<const float*>(y), nt, true, amax, grid1, false, flags, st, inner));
+    else
+      FK_TRY(spread_atomic<R>(p1, n, x + static_cast<int64_t>(l) * n, y, nt, true, grid1, flags, st));
     if (precision == FK_FP64) {
       FK_TRY(grid_to_modes<double>(p1, grid1, 0, 1, 2 * m, corr1, inv_n, T1 + 2 * static_cast<int64_t>(l) * M2, st, inner));
       FK_TRY(grid_to_modes<double>(p1, grid1, 1, nt, m, corr1, inv_n, bt, st, inner));

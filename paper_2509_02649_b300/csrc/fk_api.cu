@@ -129,6 +129,14 @@ static fk_status spread_any(const EsPlan& p, int precision, const fk_opts& o, in
     return spread_atomic<double>(p, n, static_cast<const double*>(x), static_cast<const double*>(y), n_y,
                                  with_ones, grid, flags, st);
   const int nc = n_y + (with_ones ? 1 : 0);
+  if (p.d == 1 && (o.spread == FK_SPREAD_FIXED ||
+                   (o.spread == FK_SPREAD_AUTO && spread1d_fixed_supported(p, n_y, with_ones)))) {
+    if (!spread1d_fixed_supported(p, n_y, with_ones))
+      return set_error(FK_EINVAL, "fixed-point spreading does not support N=%d w=%d channels=%d", p.N, p.w, nc);
+    return spread1d_fixed(p, n, static_cast<const float*>(x), static_cast<const float*>(y), n_y, with_ones, nullptr,
+                          grid, false, flags, st, scr);
+  }
+  if (o.spread == FK_SPREAD_FIXED) return set_error(FK_EINVAL, "fixed-point spreading is built for d = 1");
   const bool binned = (o.spread == FK_SPREAD_BINNED) ||
                       (o.spread == FK_SPREAD_AUTO && spread_binned_supported(p, n_y, with_ones));
   if (binned) {
@@ -411,6 +419,195 @@ fk_status fk_predict(int additive, int d, int m, const double* theta, int n_sets
     return predict_additive(d, m, theta, n_sets, n_q, xq, eps, precision, f, static_cast<cudaStream_t>(stream));
   }
   return fk_type2(d, m, theta, n_sets, n_q, xq, eps, precision, f, stream);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- streaming sums
+// The moments T_j and right-hand sides b_k of Sec. 2.3 are sums over points, so a
+// sample larger than device memory is spread chunk by chunk onto fine grids that
+// live between calls; the transform, penalty and solve then run once.
+struct fk_accum {
+  int d = 1, m = 0, nt = 0, precision = FK_MIXED;
+  double eps = 1e-6;
+  fk_opts o{};
+  fk::EsPlan p;
+  int64_t n_total = 0;
+  double* grid = nullptr;    // [1 + nt][N^d], fp64
+  double* corr = nullptr;    // [2 kmax + 1]
+  unsigned* flags = nullptr;
+  int device = 0;
+};
+
+namespace fk {
+
+__global__ void k_add_grid(int64_t total, const double* src, double* dst) {
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    dst[t] += src[t];
+}
+
+static fk_status accum_flags(fk_accum* a, cudaStream_t st) {
+  unsigned h = 0;
+  FK_CUDA(cudaMemcpyAsync(&h, a->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  FK_CUDA(cudaStreamSynchronize(st));
+  if (h & FLAG_RANGE) return set_error(FK_ERANGE, "a point lies outside [-3 pi, 3 pi)");
+  if (h & FLAG_TIMEOUT) return set_error(FK_ETIMEOUT, "a bounded device wait gave up");
+  if (h) return set_error(FK_EINTERNAL, "device flag 0x%x", h);
+  return FK_OK;
+}
+
+}  // namespace fk
+
+extern "C" {
+
+fk_status fk_accum_create(int d, int m, int n_targets, double eps, int precision, const fk_opts* opts,
+                          fk_accum** out, void* stream) {
+  clear_error();
+  if (!out) return set_error(FK_EINVAL, "null output handle");
+  *out = nullptr;
+  FK_TRY(check_common(d, 1, m, eps, precision));
+  if (n_targets < 0 || n_targets > 1024) return set_error(FK_EINVAL, "n_targets = %d outside [0, 1024]", n_targets);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  fk_accum* a = new fk_accum();
+  a->d = d;
+  a->m = m;
+  a->nt = n_targets;
+  a->precision = precision;
+  a->eps = eps;
+  a->o = resolve_opts(opts);
+  cudaGetDevice(&a->device);
+  fk_status rc = make_es_plan(d, 2 * m, eps, a->o.upsampfac, &a->p);
+  const int64_t G = ipow(a->p.N, d) * (1 + n_targets);
+  if (rc == FK_OK && cudaMalloc(&a->grid, sizeof(double) * G) != cudaSuccess)
+    rc = set_error(FK_ENOMEM, "accumulator grids (%lld doubles)", (long long)G);
+  if (rc == FK_OK && cudaMalloc(&a->corr, sizeof(double) * (2 * static_cast<size_t>(a->p.kmax) + 1)) != cudaSuccess)
+    rc = set_error(FK_ENOMEM, "correction factors");
+  if (rc == FK_OK && cudaMalloc(&a->flags, sizeof(unsigned)) != cudaSuccess) rc = set_error(FK_ENOMEM, "flags");
+  if (rc == FK_OK) rc = es_correction(a->p, a->corr, st);
+  if (rc == FK_OK && cudaMemsetAsync(a->grid, 0, sizeof(double) * G, st) != cudaSuccess)
+    rc = set_error(FK_ECUDA, "memset");
+  if (rc == FK_OK && cudaMemsetAsync(a->flags, 0, sizeof(unsigned), st) != cudaSuccess)
+    rc = set_error(FK_ECUDA, "memset");
+  if (rc != FK_OK) {
+    cudaGetLastError();
+    cudaFree(a->grid);
+    cudaFree(a->corr);
+    cudaFree(a->flags);
+    delete a;
+    return rc;
+  }
+  *out = a;
+  return FK_OK;
+}
+
+fk_status fk_accum_add(fk_accum* a, int64_t n, const void* x, const void* y, const unsigned* y_absmax, void* stream) {
+  clear_error();
+  if (!a) return set_error(FK_EINVAL, "null accumulator");
+  if (n < 0) return set_error(FK_EINVAL, "n = %lld < 0", (long long)n);
+  if (n == 0) return FK_OK;
+  if (!x || (a->nt > 0 && !y)) return set_error(FK_EINVAL, "null points or targets");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Scratch scr(st);
+  const EsPlan& p = a->p;
+  if (a->precision == FK_MIXED && a->d == 1 && a->o.spread != FK_SPREAD_ATOMIC &&
+      spread1d_fixed_supported(p, a->nt, true)) {
+    FK_TRY(spread1d_fixed(p, n, static_cast<const float*>(x), static_cast<const float*>(y), a->nt, true, y_absmax,
+                          a->grid, true, a->flags, st, scr));
+  } else {
+    const int64_t G = ipow(p.N, a->d) * (1 + a->nt);
+    double* tmp;
+    FK_TRY(scr.alloc(&tmp, G));
+    FK_TRY(spread_any(p, a->precision, a->o, n, x, y, a->nt, true, tmp, a->flags, st, scr));
+    k_add_grid<<<grid_for(G, 256), 256, 0, st>>>(G, tmp, a->grid); note_launch();
+    FK_CUDA(cudaGetLastError());
+  }
+  a->n_total += n;
+  return FK_OK;
+}
+
+fk_status fk_accum_system(fk_accum* a, double* T, double* b, int64_t* n_total, void* stream) {
+  clear_error();
+  if (!a) return set_error(FK_EINVAL, "null accumulator");
+  if (a->n_total < 1) return set_error(FK_EINVAL, "no points added");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Scratch scr(st);
+  const double inv_n = 1.0 / static_cast<double>(a->n_total);
+  if (T) FK_TRY(modes_any(a->p, a->precision, a->grid, 0, 1, 2 * a->m, a->corr, inv_n, T, st, scr));
+  if (b && a->nt > 0) FK_TRY(modes_any(a->p, a->precision, a->grid, 1, a->nt, a->m, a->corr, inv_n, b, st, scr));
+  if (n_total) *n_total = a->n_total;
+  return accum_flags(a, st);
+}
+
+fk_status fk_accum_fit_sobolev(fk_accum* a, double s, int penalty, const double* lambdas, int n_lambda,
+                               double* theta, void* stream, fk_report* rep) {
+  clear_error();
+  if (!a || !theta || !lambdas || n_lambda < 1 || a->nt < 1) return set_error(FK_EINVAL, "bad accumulator fit arguments");
+  if (penalty != FK_PEN_SOBOLEV && penalty != FK_PEN_LOWBIAS) return set_error(FK_EINVAL, "unknown penalty");
+  if (s < 0) return set_error(FK_EINVAL, "s < 0");
+  for (int i = 0; i < n_lambda; ++i)
+    if (!(lambdas[i] >= 0.0)) return set_error(FK_EINVAL, "lambda[%d] = %g < 0", i, lambdas[i]);
+  if (a->n_total < 1) return set_error(FK_EINVAL, "no points added");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Scratch scr(st);
+  Flags fl(st);
+  FK_TRY(fl.init(scr));
+  Timer tm(st, rep != nullptr);
+  tm.mark();
+  const int d = a->d, m = a->m;
+  const int64_t D = ipow(2 * m + 1, d), M2 = ipow(4 * m + 1, d);
+  double *T, *b, *W;
+  FK_TRY(scr.alloc(&T, 2 * M2));
+  FK_TRY(scr.alloc(&b, 2 * D * a->nt));
+  FK_TRY(scr.alloc(&W, D * n_lambda));
+  const double inv_n = 1.0 / static_cast<double>(a->n_total);
+  FK_TRY(modes_any(a->p, a->precision, a->grid, 0, 1, 2 * m, a->corr, inv_n, T, st, scr));
+  FK_TRY(modes_any(a->p, a->precision, a->grid, 1, a->nt, m, a->corr, inv_n, b, st, scr));
+  tm.mark();
+  FK_TRY(penalty_weights(d, m, penalty, s, a->o.sobolev_c0, lambdas, n_lambda, 0.0, 0, nullptr, nullptr, W, st));
+  int iters = 0;
+  double rr = 0;
+  FK_TRY(solve_system(d, m, T, W, n_lambda, b, a->nt, a->o, theta, st, scr, fl.dev, &iters, &rr));
+  tm.mark();
+  FK_TRY(fl.check());
+  FK_TRY(accum_flags(a, st));
+  if (rep) {
+    *rep = fk_report{};
+    rep->ms_fft = tm.ms(0, 1);
+    rep->ms_solve = tm.ms(1, 2);
+    rep->ms_total = tm.ms(0, 2);
+    rep->cg_iters = iters;
+    rep->rel_residual = rr;
+    rep->n_used = a->n_total;
+    rep->fine_grid = a->p.N;
+    rep->kernel_width = a->p.w;
+  }
+  return FK_OK;
+}
+
+fk_status fk_accum_reset(fk_accum* a, void* stream) {
+  clear_error();
+  if (!a) return set_error(FK_EINVAL, "null accumulator");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t G = ipow(a->p.N, a->d) * (1 + a->nt);
+  FK_CUDA(cudaMemsetAsync(a->grid, 0, sizeof(double) * G, st));
+  FK_CUDA(cudaMemsetAsync(a->flags, 0, sizeof(unsigned), st));
+  a->n_total = 0;
+  return FK_OK;
+}
+
+fk_status fk_accum_destroy(fk_accum* a) {
+  clear_error();
+  if (!a) return FK_OK;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != a->device) cudaSetDevice(a->device);
+  cudaFree(a->grid);
+  cudaFree(a->corr);
+  cudaFree(a->flags);
+  if (cur != a->device) cudaSetDevice(cur);
+  delete a;
+  return FK_OK;
 }
 
 }  // extern "C"

@@ -108,6 +108,8 @@ struct Scratch {
   }
 };
 
+int sm_count();  // multiprocessors of the current device (0 on error)
+
 inline int grid_for(int64_t work, int block, int cap = 148 * 32) {
   int64_t g = (work + block - 1) / block;
   if (g < 1) g = 1;
@@ -134,6 +136,16 @@ fk_status spread_binned(const EsPlan& p, int64_t n, const float* x, const float*
                         bool with_ones, double* grid, unsigned* flags, cudaStream_t st,
                         Scratch& scratch);
 bool spread_binned_supported(const EsPlan& p, int n_y, bool with_ones);
+
+// 1-D fixed-point shared-memory spreading (fp32 inputs, any channel count).  y_absmax:
+// device array of max|y_c| bit patterns for the n_y strength channels, or null to
+// compute it here.  accumulate: add into grid instead of overwriting it.
+bool spread1d_fixed_supported(const EsPlan& p, int n_y, bool with_ones);
+fk_status spread1d_fixed(const EsPlan& p, int64_t n, const float* x, const float* y, int n_y, bool with_ones,
+                         const unsigned* y_absmax, double* grid, bool accumulate, unsigned* flags, cudaStream_t st,
+                         Scratch& scratch);
+// amax[c] = bit pattern of max_i |y[c][i]| (amax zeroed here first)
+fk_status absmax_channels(int64_t n, const float* y, int n_y, unsigned* amax, cudaStream_t st);
 
 // Forward transform of real fp64 grids + deconvolution + extraction of the modes
 // |k|_inf <= kout (kout <= p.kmax) for channels [c0, c0 + nc), scaled by `scale`.

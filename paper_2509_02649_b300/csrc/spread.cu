@@ -1,46 +1,41 @@
 // Spreading (type-1) and interpolation (type-2) with the ES kernel, atomic form.
 //
-// Point i with coordinate x (folded onto [-pi, pi)) sits at grid position
-// u = (x + pi) / h, h = 2 pi / N.  Its window is the w nodes
-// l = l0 .. l0 + w - 1 with l0 = ceil(u - w/2), and node l receives the weight
-// phi(z) with z = (l - u) * 2 / w in [-1, 1), phi(z) = exp(beta (sqrt(1-z^2) - 1)).
-// Indices wrap modulo N (the grid is periodic).
+// Point i with coordinate x sits at grid position u = (x + pi) / h, h = 2 pi / N.
+// Its window is the w nodes l = l0 .. l0 + w - 1 with l0 = ceil(u - w/2), and node l
+// receives the weight phi(z) with z = (l - u) * 2 / w in [-1, 1),
+// phi(z) = exp(beta (sqrt(1-z^2) - 1)).  Indices wrap modulo N (the grid is periodic);
+// window.cuh computes l0 and the offset u - l0.
 //
 // This file holds the straightforward form: one thread per point, fp64 global
 // atomics into the grid.  It is the FP64 path's spreader and the fallback of the
 // mixed path; the register-accumulating binned spreader lives in spread_binned.cu.
 #include "fk_internal.cuh"
+#include "window.cuh"
 
 namespace fk {
 
 constexpr int MAXW = 16;
 
-// Fold x onto [-pi, pi) and return the grid coordinate u in [0, N], or a negative
-// value when x is outside [-3 pi, 3 pi) (or NaN).
-template <typename R> __device__ __forceinline__ R grid_coord(R x, int N);
+// Window start l0 and offset f of one coordinate (window.cuh); false outside [-3 pi, 3 pi).
+template <typename R> struct Win;
+template <> struct Win<double> {
+  int N, W;
+  __device__ __forceinline__ bool operator()(double x, int* l0, double* f) const { return window_f64(x, N, W, l0, f); }
+};
+template <> struct Win<float> {
+  int N, W;
+  float c_hi, c_lo;
+  __device__ __forceinline__ bool operator()(float x, int* l0, float* f) const {
+    return window_f32(x, N, c_hi, c_lo, W, l0, f);
+  }
+};
 
-template <> __device__ __forceinline__ double grid_coord<double>(double x, int N) {
-  if (!(x >= -3.0 * M_PI && x < 3.0 * M_PI)) return -1.0;
-  if (x < -M_PI) x += 2.0 * M_PI;
-  if (x >= M_PI) x -= 2.0 * M_PI;
-  return (x + M_PI) * (N / (2.0 * M_PI));
-}
-
-// fp32: u = x * (N / 2pi) + N / 2 with the constant split into a float pair so that
-// no systematic scale error enters (one rounding of the exact value).
-template <> __device__ __forceinline__ float grid_coord<float>(float x, int N) {
-  const float lim = 9.42477796076938f;  // 3 pi, rounded down in fp32
-  if (!(x >= -lim && x < lim)) return -1.0f;
-  const float twopi_hi = 6.28318548202514648f;   // fp32(2 pi)
-  const float twopi_lo = -1.74845553e-7f;         // 2 pi - fp32(2 pi)
-  if (x < -3.14159274101257324f) x = (x + twopi_hi) + twopi_lo;
-  if (x >= 3.14159274101257324f) x = (x - twopi_hi) - twopi_lo;
-  const double c = N / (2.0 * M_PI);
-  const float c_hi = static_cast<float>(c);
-  const float c_lo = static_cast<float>(c - static_cast<double>(c_hi));
-  float u = fmaf(x, c_hi, fmaf(x, c_lo, 0.5f * N));
-  if (u < 0.f) u = 0.f;
-  return u;
+template <typename R>
+Win<R> make_win(int N, int W);
+template <> Win<double> make_win<double>(int N, int W) { return Win<double>{N, W}; }
+template <> Win<float> make_win<float>(int N, int W) {
+  const CoordConst c = coord_const(N);
+  return Win<float>{N, W, c.hi, c.lo};
 }
 
 template <typename R>
@@ -52,23 +47,20 @@ template <> __device__ __forceinline__ float es_phi<float>(float z, float beta) 
   return expf(beta * (sqrtf(fmaxf(1.0f - z * z, 0.0f)) - 1.0f));
 }
 
-// Weights of one coordinate: ker[a] for a = 0..w-1 and the first node l0.
+// Weights ker[a] = psi((a - f) 2 / w), a = 0..w-1.
 template <typename R>
-__device__ __forceinline__ void es_weights(R u, int w, R beta, R* ker, int* l0) {
-  const R half = R(0.5) * w;
-  const R s = ceil(u - half);
-  *l0 = static_cast<int>(s);
-  const R off = s - u;          // in [-w/2, -w/2 + 1)
+__device__ __forceinline__ void es_weights(R f, int w, R beta, R* ker) {
   const R sc = R(2) / w;
 #pragma unroll
   for (int a = 0; a < MAXW; ++a)
-    if (a < w) ker[a] = es_phi<R>((off + a) * sc, beta);
+    if (a < w) ker[a] = es_phi<R>((a - f) * sc, beta);
 }
 
 template <typename R>
-__global__ void k_spread_atomic(int d, int N, int w, R beta, int64_t n, const R* __restrict__ x,
+__global__ void k_spread_atomic(int d, Win<R> win, R beta, int64_t n, const R* __restrict__ x,
                                 const R* __restrict__ y, int n_y, int with_ones, double* grid,
                                 unsigned* flags) {
+  const int N = win.N, w = win.W;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t G = (d == 1) ? N : static_cast<int64_t>(N) * N;
   const int nc = n_y + with_ones;
@@ -77,9 +69,9 @@ __global__ void k_spread_atomic(int d, int N, int w, R beta, int64_t n, const R*
     int l0[2];
     bool ok = true;
     for (int l = 0; l < d; ++l) {
-      const R u = grid_coord<R>(x[l * n + i], N);
-      if (u < R(0)) { ok = false; break; }
-      es_weights<R>(u, w, beta, ker[l], &l0[l]);
+      R f;
+      if (!win(x[l * n + i], &l0[l], &f)) { ok = false; break; }
+      es_weights<R>(f, w, beta, ker[l]);
     }
     if (!ok) { atomicOr(flags, FLAG_RANGE); continue; }
     for (int c = 0; c < nc; ++c) {
@@ -87,15 +79,15 @@ __global__ void k_spread_atomic(int d, int N, int w, R beta, int64_t n, const R*
       double* g = grid + c * G;
       if (d == 1) {
         for (int a = 0; a < w; ++a) {
-          const int idx = (l0[0] + a + N) & (N - 1);
+          const int idx = wrap_node(l0[0] + a, N);
           atomicAdd(g + idx, str * static_cast<double>(ker[0][a]));
         }
       } else {
         for (int a = 0; a < w; ++a) {
-          const int r = (l0[0] + a + N) & (N - 1);
+          const int r = wrap_node(l0[0] + a, N);
           const double sa = str * static_cast<double>(ker[0][a]);
           for (int b = 0; b < w; ++b) {
-            const int cidx = (l0[1] + b + N) & (N - 1);
+            const int cidx = wrap_node(l0[1] + b, N);
             atomicAdd(g + static_cast<int64_t>(r) * N + cidx, sa * static_cast<double>(ker[1][b]));
           }
         }
@@ -117,7 +109,7 @@ fk_status spread_atomic(const EsPlan& p, int64_t n, const R* x, const R* y, int 
   KernelTimer* kt = kernel_timer();
   if (kt->on) cudaEventRecord(kt->start, st);
   k_spread_atomic<R><<<grid_for(n, block, 148 * 16), block, 0, st>>>(
-      p.d, p.N, p.w, static_cast<R>(p.beta), n, x, y, n_y, with_ones ? 1 : 0, grid, flags); note_launch();
+      p.d, make_win<R>(p.N, p.w), static_cast<R>(p.beta), n, x, y, n_y, with_ones ? 1 : 0, grid, flags); note_launch();
   if (kt->on) {
     cudaEventRecord(kt->stop, st);
     kt->recorded = true;
@@ -163,8 +155,9 @@ __global__ void k_t2_place(int d, int N, int kc, int corr_off, const double* coe
 }
 
 template <typename R>
-__global__ void k_t2_interp(int d, int N, int w, R beta, int64_t n, const R* __restrict__ x, int n_sets,
+__global__ void k_t2_interp(int d, Win<R> win, R beta, int64_t n, const R* __restrict__ x, int n_sets,
                             const cplx<R>* __restrict__ G, double* out, unsigned* flags) {
+  const int N = win.N, w = win.W;
   const int64_t GN = (d == 1) ? N : static_cast<int64_t>(N) * N;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -172,9 +165,9 @@ __global__ void k_t2_interp(int d, int N, int w, R beta, int64_t n, const R* __r
     int l0[2];
     bool ok = true;
     for (int l = 0; l < d; ++l) {
-      const R u = grid_coord<R>(x[l * n + i], N);
-      if (u < R(0)) { ok = false; break; }
-      es_weights<R>(u, w, beta, ker[l], &l0[l]);
+      R f;
+      if (!win(x[l * n + i], &l0[l], &f)) { ok = false; break; }
+      es_weights<R>(f, w, beta, ker[l]);
     }
     if (!ok) {
       atomicOr(flags, FLAG_RANGE);
@@ -185,12 +178,12 @@ __global__ void k_t2_interp(int d, int N, int w, R beta, int64_t n, const R* __r
       const cplx<R>* g = G + s * GN;
       double acc = 0.0;
       if (d == 1) {
-        for (int a = 0; a < w; ++a) acc += static_cast<double>(ker[0][a]) * static_cast<double>(g[(l0[0] + a + N) & (N - 1)].x);
+        for (int a = 0; a < w; ++a) acc += static_cast<double>(ker[0][a]) * static_cast<double>(g[wrap_node(l0[0] + a, N)].x);
       } else {
         for (int a = 0; a < w; ++a) {
-          const int r = (l0[0] + a + N) & (N - 1);
+          const int r = wrap_node(l0[0] + a, N);
           R row = R(0);
-          for (int b = 0; b < w; ++b) row += ker[1][b] * g[static_cast<int64_t>(r) * N + ((l0[1] + b + N) & (N - 1))].x;
+          for (int b = 0; b < w; ++b) row += ker[1][b] * g[static_cast<int64_t>(r) * N + (wrap_node(l0[1] + b, N))].x;
           acc += static_cast<double>(ker[0][a]) * static_cast<double>(row);
         }
       }
@@ -230,7 +223,7 @@ fk_status type2_eval(const EsPlan& p, int kmax_c, const double* coef, int n_sets
     FK_TRY(fft_lines<R>(G, N, static_cast<int64_t>(n_sets) * N, N, 1, +1, tw, st));
   }
   if (n > 0) {
-    k_t2_interp<R><<<grid_for(n, 256, 148 * 16), 256, 0, st>>>(p.d, N, p.w, static_cast<R>(p.beta), n, x, n_sets,
+    k_t2_interp<R><<<grid_for(n, 256, 148 * 16), 256, 0, st>>>(p.d, make_win<R>(N, p.w), static_cast<R>(p.beta), n, x, n_sets,
                                                                G, out, flags); note_launch();
     FK_CUDA(cudaGetLastError());
   }

@@ -1,0 +1,387 @@
+// One-dimensional spreading of many channels with integer (fixed-point) sums in
+// shared memory (mixed path, fp32 inputs).
+//
+// The 1-D fine grids are short (N <= 8192 at the mode counts of §3 sweeps), so a
+// CTA can hold whole grids of several channels in shared memory; points are taken
+// in input order and every window tap is one shared-memory atomic.  On this part
+// 32-bit integer shared atomics are native while fp32 and 64-bit ones are compare-
+// and-swap loops, so each contribution psi_a * y is rounded to a fixed-point
+// integer q = round(psi_a * y * S) and added as a 64-bit integer held in two 32-bit
+// words: the low word takes an atomic add whose returned old value gives the carry,
+// and the high word is touched only on a carry or a borrow (rare).
+//
+// Scale: per channel S = 2^(21 - e) with max|y| <= 2^e (ones: e = 1), so every
+// |q| <= 2^21 and q is formed with one FFMA against the constant 1.5 * 2^23 (the
+// product psi_a * (y S) is exact inside the FMA and rounded once to an integer).
+// The rounding error of a contribution is at most 2^-22 max|y|; it does not grow
+// with the accumulated magnitude, unlike an fp32 running sum.  Integer sums do not
+// depend on the order of the additions, so the result is bitwise reproducible.
+//
+// Layout: channel groups of at most `cmax` channels share a CTA (cmax N 8 bytes of
+// shared memory); the CTAs of a group split the points into contiguous ranges; at
+// the end each CTA adds its integer grids into a global int64 accumulator, which a
+// last kernel scales back into the fp64 grid.
+#include "fk_internal.cuh"
+#include "window.cuh"
+
+namespace fk {
+
+namespace {
+
+constexpr int MAXGRP = 64;                      // channel groups per call
+constexpr int CG = 4;                           // channels per CTA at most
+constexpr int HALO = 16;                        // padding nodes after each grid (>= max W - 1)
+constexpr int THREADS = 1024;
+constexpr size_t SMEM_BUDGET = 220 * 1024;      // bytes of integer grids per CTA
+constexpr float MAGIC = 12582912.0f;            // 1.5 * 2^23
+constexpr int MAGIC_BITS = 0x4B400000;
+
+struct Fx1dArgs {
+  int64_t n;
+  const float* x;
+  const float* y;     // [n_y][n]
+  int n_y;
+  int with_ones;
+  int N;
+  float c_hi, c_lo;   // N / (2 pi) as a float pair
+  float bl;           // beta log2(e)
+  int ngrp;
+  int grp_c0[MAXGRP];  // first channel of each group (channel 0 = ones when with_ones)
+  int grp_nc[MAXGRP];
+  int grp_b0[MAXGRP + 1];  // first CTA of each group; grp_b0[ngrp] = total CTAs
+  int vec;                 // x and every y row 16-byte aligned (four points per load)
+  const unsigned* amax;    // [n_y] bit patterns of max |y_c| (non-negative floats)
+  unsigned long long* acc; // [nc][N] int64 accumulators
+  unsigned* flags;
+};
+
+__device__ __forceinline__ float rsqrt_ap(float v) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
+
+__device__ __forceinline__ float ex2_ap(float v) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
+
+// hi-word change of one low-word add: qsign + carry out of (old + q), where qsign is
+// the sign extension (0 or -1) of q
+__device__ __forceinline__ int carry_delta(unsigned old, unsigned q, int qsign) {
+  unsigned nw;
+  int dh;
+  asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, 0;" : "=r"(nw), "=r"(dh) : "r"(old), "r"(q), "r"(qsign));
+  return dh;
+}
+
+// exponent e with |v| <= 2^e for the channel scale (v = 0 gives e = 0)
+__device__ __forceinline__ int scale_exp(float v) {
+  int e = 0;
+  frexpf(v, &e);
+  return e;
+}
+
+template <int W>
+__global__ void __launch_bounds__(THREADS) k_spread1d_fx(Fx1dArgs A) {
+  extern __shared__ unsigned smem_fx[];
+  const int b = blockIdx.x;
+  int g = 0;
+  while (g + 1 < A.ngrp && A.grp_b0[g + 1] <= b) ++g;
+  const int c0 = A.grp_c0[g], nc = A.grp_nc[g];
+  const int nblk = A.grp_b0[g + 1] - A.grp_b0[g];
+  const int lb = b - A.grp_b0[g];
+  const int N = A.N;
+  // [nc][N + HALO] low and high words: a window starting at node b < N ends before
+  // N + HALO, and the halo is added into nodes 0 .. HALO - 1 at the end
+  const int stride = N + HALO;
+  unsigned* lo = smem_fx;
+  int* hi = reinterpret_cast<int*>(smem_fx + nc * stride);
+  for (int i = threadIdx.x; i < 2 * nc * stride; i += blockDim.x) smem_fx[i] = 0u;
+
+  // per-channel scales
+  float S[CG];
+#pragma unroll
+  for (int c = 0; c < CG; ++c) {
+    S[c] = 0.f;
+    if (c < nc) {
+      const int ch = c0 + c;
+      const float m = (A.with_ones && ch == 0) ? 1.0f : __uint_as_float(A.amax[ch - A.with_ones]);
+      S[c] = ldexpf(1.0f, 21 - scale_exp(m));
+    }
+  }
+  __syncthreads();
+
+  const float sc = 2.0f / W;
+  // one point: window, W weights, then per channel W low-word adds in flight before
+  // the (rare) carries are settled
+  auto one = [&](float xv, const float* yv) {
+    int l0;
+    float f;
+    if (!window_f32(xv, N, A.c_hi, A.c_lo, W, &l0, &f)) {
+      atomicOr(A.flags, FLAG_RANGE);
+      return;
+    }
+    float psi[W];
+    const float z0 = -f * sc;
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+      const float z = fmaf(static_cast<float>(a), sc, z0);
+      const float t = fmaxf(fmaf(-z, z, 1.0f), 1e-30f);
+      psi[a] = ex2_ap(fmaf(A.bl, t * rsqrt_ap(t), -A.bl));
+    }
+    const int b = wrap_node(l0, N);
+#pragma unroll
+    for (int c = 0; c < CG; ++c) {
+      if (c >= nc) break;
+      const float v = yv[c] * S[c];
+      unsigned* lc = lo + c * stride + b;
+      unsigned old[W];
+#pragma unroll
+      for (int a = 0; a < W; ++a) {
+        const int q = __float_as_int(fmaf(psi[a], v, MAGIC)) - MAGIC_BITS;
+        old[a] = atomicAdd(lc + a, static_cast<unsigned>(q));
+      }
+      // high-word change per tap: sign extension of q plus the carry out of the
+      // low-word add; nonzero only when the low word wraps (rare)
+      int any = 0;
+#pragma unroll
+      for (int a = 0; a < W; ++a) {
+        const int q = __float_as_int(fmaf(psi[a], v, MAGIC)) - MAGIC_BITS;
+        any |= carry_delta(old[a], static_cast<unsigned>(q), q >> 31);
+      }
+      if (any) {
+        int* hc = hi + c * stride + b;
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+          const int q = __float_as_int(fmaf(psi[a], v, MAGIC)) - MAGIC_BITS;
+          const int dh = carry_delta(old[a], static_cast<unsigned>(q), q >> 31);
+          if (dh) atomicAdd(hc + a, dh);
+        }
+      }
+    }
+  };
+  // strength of channel c at point i (ones channel: 1)
+  const float* yrow[CG];
+#pragma unroll
+  for (int c = 0; c < CG; ++c) {
+    const int ch = c0 + c;
+    yrow[c] = (c < nc && !(A.with_ones && ch == 0)) ? A.y + static_cast<int64_t>(ch - A.with_ones) * A.n : nullptr;
+  }
+
+  const int64_t per = ((A.n + nblk - 1) / nblk + 3) & ~static_cast<int64_t>(3);
+  const int64_t s0 = static_cast<int64_t>(lb) * per;
+  const int64_t s1 = min(A.n, s0 + per);
+  if (A.vec) {
+    // four consecutive points per thread: one 16-byte load per array, all issued
+    // before the first point is processed
+    for (int64_t i = s0 + 4 * static_cast<int64_t>(threadIdx.x); i < s1; i += 4 * static_cast<int64_t>(blockDim.x)) {
+      if (i + 3 < s1) {
+        const float4 xq = __ldg(reinterpret_cast<const float4*>(A.x + i));
+        float4 yq[CG];
+#pragma unroll
+        for (int c = 0; c < CG; ++c)
+          yq[c] = yrow[c] ? __ldg(reinterpret_cast<const float4*>(yrow[c] + i)) : make_float4(1.f, 1.f, 1.f, 1.f);
+        float yv[CG];
+#pragma unroll
+        for (int c = 0; c < CG; ++c) yv[c] = yq[c].x;
+        one(xq.x, yv);
+#pragma unroll
+        for (int c = 0; c < CG; ++c) yv[c] = yq[c].y;
+        one(xq.y, yv);
+#pragma unroll
+        for (int c = 0; c < CG; ++c) yv[c] = yq[c].z;
+        one(xq.z, yv);
+#pragma unroll
+        for (int c = 0; c < CG; ++c) yv[c] = yq[c].w;
+        one(xq.w, yv);
+      } else {
+        for (int64_t j2 = i; j2 < s1; ++j2) {
+          float yv[CG];
+#pragma unroll
+          for (int c = 0; c < CG; ++c) yv[c] = yrow[c] ? yrow[c][j2] : 1.0f;
+          one(A.x[j2], yv);
+        }
+      }
+    }
+  } else {
+    for (int64_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+      float yv[CG];
+#pragma unroll
+      for (int c = 0; c < CG; ++c) yv[c] = yrow[c] ? yrow[c][i] : 1.0f;
+      one(A.x[i], yv);
+    }
+  }
+  __syncthreads();
+  // add the CTA's integer grids (halo folded onto nodes 0 .. HALO - 1) into the
+  // global accumulators
+  for (int t = threadIdx.x; t < nc * stride; t += blockDim.x) {
+    const long long v = (static_cast<long long>(hi[t]) << 32) + static_cast<long long>(lo[t]);
+    if (v != 0) {
+      const int c = t / stride, node = (t - c * stride) & (N - 1);
+      atomicAdd(A.acc + static_cast<int64_t>(c0 + c) * N + node, static_cast<unsigned long long>(v));
+    }
+  }
+}
+
+// max |y_c| per channel as float bit patterns (non-negative floats order like their bits)
+__global__ void k_absmax(int64_t n, const float* __restrict__ y, int n_y, unsigned* amax) {
+  const int c = blockIdx.y;
+  const float* yc = y + static_cast<int64_t>(c) * n;
+  float m = 0.f;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float a = fabsf(yc[i]);
+    m = (a > m) ? a : m;  // NaN inputs are left out
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(amax + c, __float_as_uint(m));
+}
+
+// grid[c][node] (+)= acc[c][node] / S_c
+__global__ void k_fx_to_grid(int64_t total, int N, int with_ones, const unsigned* amax,
+                             const unsigned long long* acc, double* grid, int accumulate) {
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int ch = static_cast<int>(t / N);
+    const float m = (with_ones && ch == 0) ? 1.0f : __uint_as_float(amax[ch - with_ones]);
+    const double inv = ldexp(1.0, scale_exp(m) - 21);
+    const double v = static_cast<double>(static_cast<long long>(acc[t])) * inv;
+    grid[t] = accumulate ? grid[t] + v : v;
+  }
+}
+
+using FxFn = void (*)(Fx1dArgs);
+
+template <int W>
+FxFn fx_fn() {
+  return k_spread1d_fx<W>;
+}
+
+FxFn pick_fx(int w) {
+  switch (w) {
+    case 2: return fx_fn<2>();
+    case 3: return fx_fn<3>();
+    case 4: return fx_fn<4>();
+    case 5: return fx_fn<5>();
+    case 6: return fx_fn<6>();
+    case 7: return fx_fn<7>();
+    case 8: return fx_fn<8>();
+    case 9: return fx_fn<9>();
+    case 10: return fx_fn<10>();
+    case 11: return fx_fn<11>();
+    case 12: return fx_fn<12>();
+    case 13: return fx_fn<13>();
+    case 14: return fx_fn<14>();
+    case 15: return fx_fn<15>();
+    case 16: return fx_fn<16>();
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+fk_status absmax_channels(int64_t n, const float* y, int n_y, unsigned* amax, cudaStream_t st) {
+  if (n_y < 1) return FK_OK;
+  if (n_y > 65535) return set_error(FK_EINVAL, "absmax: %d channels", n_y);
+  FK_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned) * n_y, st));
+  if (n == 0) return FK_OK;
+  k_absmax<<<dim3(grid_for(n, 256, 148 * 8), n_y), 256, 0, st>>>(n, y, n_y, amax); note_launch();
+  FK_CUDA(cudaGetLastError());
+  return FK_OK;
+}
+
+bool spread1d_fixed_supported(const EsPlan& p, int n_y, bool with_ones) {
+  const int nc = n_y + (with_ones ? 1 : 0);
+  if (p.d != 1 || nc < 1 || p.w < 2 || p.w > 16) return false;
+  const int64_t cmax = static_cast<int64_t>(SMEM_BUDGET / (8 * static_cast<size_t>(p.N + HALO)));
+  if (cmax < 1) return false;
+  const int64_t c = std::min<int64_t>(cmax, CG);
+  return (nc + c - 1) / c <= MAXGRP;
+}
+
+fk_status spread1d_fixed(const EsPlan& p, int64_t n, const float* x, const float* y, int n_y, bool with_ones,
+                         const unsigned* y_absmax, double* grid, bool accumulate, unsigned* flags, cudaStream_t st,
+                         Scratch& scr) {
+  if (!spread1d_fixed_supported(p, n_y, with_ones))
+    return set_error(FK_EINVAL, "1-D fixed-point spreading: unsupported shape (N = %d, w = %d)", p.N, p.w);
+  const int nc = n_y + (with_ones ? 1 : 0);
+  const int N = p.N;
+  if (!accumulate) FK_CUDA(cudaMemsetAsync(grid, 0, sizeof(double) * N * nc, st));
+  if (n == 0) return FK_OK;
+
+  const int cmax = static_cast<int>(std::min<size_t>(CG, SMEM_BUDGET / (8 * static_cast<size_t>(N + HALO))));
+  const int ngrp = (nc + cmax - 1) / cmax;
+  Fx1dArgs A{};
+  A.n = n;
+  A.x = x;
+  A.y = y;
+  A.n_y = n_y;
+  A.with_ones = with_ones ? 1 : 0;
+  A.N = N;
+  const CoordConst cc = coord_const(N);
+  A.c_hi = cc.hi;
+  A.c_lo = cc.lo;
+  A.bl = static_cast<float>(p.beta * 1.4426950408889634);
+  A.ngrp = ngrp;
+  A.flags = flags;
+  A.vec = ((reinterpret_cast<uintptr_t>(x) & 15) == 0 && (n & 3) == 0 &&
+           (n_y == 0 || (reinterpret_cast<uintptr_t>(y) & 15) == 0)) ? 1 : 0;
+  // balanced groups: sizes differ by at most one channel
+  int c = 0;
+  size_t smem_max = 0;
+  for (int g = 0; g < ngrp; ++g) {
+    const int sz = nc / ngrp + (g < nc % ngrp ? 1 : 0);
+    A.grp_c0[g] = c;
+    A.grp_nc[g] = sz;
+    c += sz;
+    smem_max = std::max(smem_max, sizeof(unsigned) * 2 * static_cast<size_t>(sz) * (N + HALO));
+  }
+  // CTAs: as many as fit on the device at once, shared out by channel count, and no
+  // more than one per 4096 points (each CTA zeroes and flushes whole grids)
+  const int sms = std::max(1, sm_count());
+  const int per_sm = std::max(1, std::min<int>(2, static_cast<int>((228 * 1024) / (smem_max + 1024))));
+  const int64_t total_ctas = static_cast<int64_t>(sms) * per_sm;
+  const int64_t by_n = std::max<int64_t>(1, (n + 4095) / 4096);
+  A.grp_b0[0] = 0;
+  for (int g = 0; g < ngrp; ++g) {
+    int64_t k = (total_ctas * A.grp_nc[g] + nc - 1) / nc;
+    k = std::max<int64_t>(1, std::min(k, by_n));
+    A.grp_b0[g + 1] = A.grp_b0[g] + static_cast<int>(k);
+  }
+  const int nblocks = A.grp_b0[ngrp];
+
+  unsigned* amax = nullptr;
+  if (n_y > 0) {
+    if (y_absmax) {
+      amax = const_cast<unsigned*>(y_absmax);
+    } else {
+      FK_TRY(scr.alloc(&amax, static_cast<size_t>(n_y)));
+      FK_TRY(absmax_channels(n, y, n_y, amax, st));
+    }
+  }
+  A.amax = amax;
+  FK_TRY(scr.alloc(&A.acc, static_cast<size_t>(nc) * N));
+  FK_CUDA(cudaMemsetAsync(A.acc, 0, sizeof(unsigned long long) * nc * N, st));
+
+  const FxFn fn = pick_fx(p.w);
+  if (!fn) return set_error(FK_EINVAL, "1-D fixed-point spreading: w = %d not built", p.w);
+  FK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_max)));
+  KernelTimer* kt = kernel_timer();
+  if (kt->on) cudaEventRecord(kt->start, st);
+  fn<<<nblocks, THREADS, smem_max, st>>>(A); note_launch();
+  if (kt->on) {
+    cudaEventRecord(kt->stop, st);
+    kt->recorded = true;
+  }
+  FK_CUDA(cudaGetLastError());
+  const int64_t total = static_cast<int64_t>(nc) * N;
+  k_fx_to_grid<<<grid_for(total, 256), 256, 0, st>>>(total, N, A.with_ones, amax, A.acc, grid, accumulate ? 1 : 0);
+  note_launch();
+  FK_CUDA(cudaGetLastError());
+  return FK_OK;
+}
+
+}  // namespace fk

@@ -29,6 +29,7 @@
 //                 keeps the warps' trip counts even.  At the end each lane adds its
 //                 register window into the fp64 grid.
 #include "fk_internal.cuh"
+#include "window.cuh"
 
 namespace fk {
 
@@ -41,17 +42,6 @@ constexpr int THREADS_ACC = 448;                 // accumulation CTA size (one C
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ float coord_f32(float x, int N, float c_hi, float c_lo) {
-  // fold onto [-pi, pi) and map to grid units u = x N / (2 pi) + N / 2 (one rounding)
-  const float lim = 9.42477796076938f;
-  if (!(x >= -lim && x < lim)) return -1.0f;
-  const float twopi_hi = 6.28318548202514648f, twopi_lo = -1.74845553e-7f;
-  if (x < -3.14159274101257324f) x = (x + twopi_hi) + twopi_lo;
-  if (x >= 3.14159274101257324f) x = (x - twopi_hi) - twopi_lo;
-  const float u = fmaf(x, c_hi, fmaf(x, c_lo, 0.5f * N));
-  return u < 0.f ? 0.f : u;
 }
 
 __device__ __forceinline__ float rsqrt_approx(float v) {
@@ -190,17 +180,14 @@ struct PartArgs {
 // owner and packed key of one point; returns false for a point out of range
 __device__ __forceinline__ bool point_key(float x0, float x1, const PartArgs& A, float inv_cpc, float* f0, float* f1,
                                           uint32_t* packed) {
-  const float u0 = coord_f32(x0, A.N, A.c_hi, A.c_lo);
-  const float u1 = coord_f32(x1, A.N, A.c_hi, A.c_lo);
-  if (!(u0 >= 0.f && u1 >= 0.f)) return false;
-  const float l0a = ceilf(u0 - 0.5f * A.W), l0b = ceilf(u1 - 0.5f * A.W);
+  int la, lb;
+  if (!window_f32(x0, A.N, A.c_hi, A.c_lo, A.W, &la, f0)) return false;
+  if (!window_f32(x1, A.N, A.c_hi, A.c_lo, A.W, &lb, f1)) return false;
   const int N = A.N;
-  const int key = ((static_cast<int>(l0a) + N) & (N - 1)) * N + ((static_cast<int>(l0b) + N) & (N - 1));
+  const int key = wrap_node(la, N) * N + wrap_node(lb, N);
   int o = __float2int_rd(static_cast<float>(key) * inv_cpc);
   if (o * A.cells_per > key) --o;
   else if ((o + 1) * A.cells_per <= key) ++o;
-  *f0 = u0 - l0a;
-  *f1 = u1 - l0b;
   *packed = (static_cast<uint32_t>(o) << 16) | static_cast<uint32_t>(key - o * A.cells_per);
   return true;
 }
@@ -628,14 +615,14 @@ KFn pick2d(int w) {
   }
 }
 
+}  // namespace
+
 int sm_count() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   return sms;
 }
-
-}  // namespace
 
 // owners: enough that each holds at most Cfg::CELLS cells, and at least one per SM
 static int owner_count(int64_t ncells, bool pair, int sms) {

@@ -98,3 +98,82 @@ def bandlimited_2d(x: np.ndarray) -> np.ndarray:
     """Noiseless band-limited target 0.2 + cos(2 x1 + 3 x2) + 0.3 sin(x1 - 5 x2)
     at x (2, n)."""
     return 0.2 + np.cos(2 * x[0] + 3 * x[1]) + 0.3 * np.sin(x[0] - 5 * x[1])
+
+
+# ---------------------------------------------------------------- counter-based twin
+# The 1-D sweep at scale (workload 5, up to 1e10 points) is generated on the device
+# in chunks; this is the host twin of that generator, written from the published
+# definition of Philox4x32-10 (Salmon, Moraes, Dror and Shaw, "Parallel random
+# numbers: as easy as 1, 2, 3", SC 2011): two 32x32->64 multiplications per round
+# with multipliers 0xD2511F53 and 0xCD9E8D57, key schedule bumped by the Weyl
+# constants 0x9E3779B9 and 0xBB67AE85, ten rounds.
+#
+# Draws for point i (j = i // 4, r = i % 4), key (seed mod 2^32, workload):
+#   X_i:        word r of Philox(counter = (j mod 2^32, j div 2^32, 0, 0));
+#               u = (floor(word / 2^9) + 1/2) 2^-23 (exact in fp32) and
+#               X = fp32(u fp32(2 pi) - fp32(pi)) with one rounding.
+#   noise z_ti: words (2p, 2p + 1), p = r // 2, of Philox(counter = (.., .., 1 + t, 0))
+#               -> uniforms u1, u2 as above; Box-Muller radius sqrt(-2 ln u1) times
+#               cos(2 pi u2) for even r, sin(2 pi u2) for odd r.
+#   Y_ti = sign(X_i) |X_i|^0.7 + 0.2 z_ti.
+# The device computes the transcendental steps in fp32 with CUDA's libm, this twin
+# in fp64 rounded to fp32: X agrees bit for bit, Y to a few fp32 ulps.
+
+PHILOX_M = (0xD2511F53, 0xCD9E8D57)
+PHILOX_W = (0x9E3779B9, 0xBB67AE85)
+TWO_PI_F32 = np.float32(2.0 * np.pi)
+PI_F32 = np.float32(np.pi)
+
+
+def philox4x32_10(ctr: np.ndarray, key: tuple[int, int]) -> np.ndarray:
+    """Philox4x32-10 of counters ctr (4, m) uint32 under key (k0, k1); returns (4, m)."""
+    c = [np.asarray(ctr[i], dtype=np.uint64) for i in range(4)]
+    k0, k1 = np.uint64(key[0] & 0xFFFFFFFF), np.uint64(key[1] & 0xFFFFFFFF)
+    mask = np.uint64(0xFFFFFFFF)
+    m0, m1 = np.uint64(PHILOX_M[0]), np.uint64(PHILOX_M[1])
+    for rnd in range(10):
+        if rnd:
+            k0 = (k0 + np.uint64(PHILOX_W[0])) & mask
+            k1 = (k1 + np.uint64(PHILOX_W[1])) & mask
+        p0 = c[0] * m0
+        p1 = c[2] * m1
+        c = [((p1 >> np.uint64(32)) ^ c[1] ^ k0) & mask, p1 & mask,
+             ((p0 >> np.uint64(32)) ^ c[3] ^ k1) & mask, p0 & mask]
+    return np.stack(c).astype(np.uint32)
+
+
+def _unit_f32(words: np.ndarray) -> np.ndarray:
+    """(floor(w / 2^9) + 1/2) 2^-23 in (0, 1), exact in fp32."""
+    return ((words >> np.uint32(9)).astype(np.float64) + 0.5) * 2.0 ** -23
+
+
+def sweep_counter_points(first: int, n: int, n_targets: int = 16, seed: int = SEED,
+                         workload: int = 5):
+    """Points first .. first + n - 1 of the counter-based 1-D sweep workload.
+
+    Returns X (n,) float32 and Y (n_targets, n) float32."""
+    i = np.arange(first, first + n, dtype=np.uint64)
+    j = i >> np.uint64(2)
+    r = (i & np.uint64(3)).astype(np.int64)
+    jlo = (j & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    jhi = (j >> np.uint64(32)).astype(np.uint32)
+    key = (seed & 0xFFFFFFFF, workload)
+    zeros = np.zeros_like(jlo)
+    cols = np.arange(n)
+    w = philox4x32_10(np.stack([jlo, jhi, zeros, zeros]), key)
+    u = _unit_f32(w[r, cols])
+    x = (u * np.float64(TWO_PI_F32) - np.float64(PI_F32)).astype(np.float32)
+    xd = x.astype(np.float64)
+    fstar = (np.sign(xd) * np.abs(xd) ** 0.7).astype(np.float32)
+    y = np.empty((n_targets, n), dtype=np.float32)
+    pair = 2 * (r >> 1)
+    for t in range(n_targets):
+        wt = philox4x32_10(np.stack([jlo, jhi, np.full_like(jlo, 1 + t), zeros]), key)
+        u1 = _unit_f32(wt[pair, cols])
+        u2 = _unit_f32(wt[pair + 1, cols])
+        rad = np.sqrt(-2.0 * np.log(u1)).astype(np.float32).astype(np.float64)
+        ang = 2.0 * np.pi * u2
+        trig = np.where(r % 2 == 0, np.cos(ang), np.sin(ang)).astype(np.float32).astype(np.float64)
+        z = (rad * trig).astype(np.float32).astype(np.float64)
+        y[t] = (np.float64(np.float32(0.2)) * z + fstar.astype(np.float64)).astype(np.float32)
+    return x, y
