@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="2d-sobolev", choices=["2d-sobolev", "sweep-1d", "pik-heat", "additive-8d"],
+                    help="2d-sobolev is the headline line; the others time the other hot-path rows")
     return ap.parse_args()
 
 
@@ -150,6 +152,144 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def _dev_uniform(torch, n, d, seed):
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    return torch.rand((d, n), generator=g, device="cuda", dtype=torch.float32) * (2 * np.pi) - np.pi
+
+
+def _dev_normal(torch, n, seed):
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    return torch.randn(n, generator=g, device="cuda", dtype=torch.float32)
+
+
+def run_row(args, rank, local):
+    """Time one of the other hot-path rows on one GPU (inputs drawn on the device).
+
+    sweep-1d:    1e10 points (2^28-point chunks from the counter-based generator; the
+                 generation is outside the timed region), 17 channels on one 1-D grid,
+                 then the batched solve for 256 lambdas x 16 targets.
+    pik-heat:    n = 1e9 (t, x) points, heat prior, fit + held-out loss and its
+                 gradient (autograd) on 1e7 validation points.
+    additive-8d: n = 2e8 points in d = 8, m = 64: 8 1-D and 28 2-D transforms,
+                 block Gram and dense FP64 solve."""
+    import torch
+    import paper_2509_02649_b300 as fk
+    torch.cuda.set_device(local)
+    st = torch.cuda.current_stream()
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    p32 = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    W = args.workload
+    if W == "sweep-1d":
+        n_total, chunk, m, nt = 10_000_000_000, 1 << 28, 1000, 16
+        lams = list(np.logspace(-12, -2, 256))
+        x = torch.empty((1, chunk), dtype=torch.float32, device="cuda")
+        y = torch.empty((nt, chunk), dtype=torch.float32, device="cuda")
+        amax = torch.empty(nt, dtype=torch.int32, device="cuda")
+        acc = fk.Accumulator(1, m, nt, 1e-6, "mixed")
+
+        def step():
+            ev = []
+            first = 0
+            while first < n_total:
+                c = min(chunk, n_total - first)
+                xs, ys = (x, y) if c == chunk else (torch.empty((1, c), dtype=torch.float32, device="cuda"),
+                                                    torch.empty((nt, c), dtype=torch.float32, device="cuda"))
+                fk.generate_sweep_1d(first, c, nt, out=(xs, ys, amax))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                acc.add(xs, ys, amax)
+                e1.record(st)
+                ev.append((e0, e1))
+                first += c
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(st)
+            th = acc.fit_sobolev(1.0, lams)
+            f1.record(st)
+            torch.cuda.synchronize()
+            acc.reset()
+            ms_add = sum(a.elapsed_time(b) for a, b in ev)
+            return ms_add + f0.elapsed_time(f1), ms_add, th
+
+        n, f_pt = n_total, 7 * (2 * (1 + nt))
+        cfg = {"workload": W, "n": n_total, "d": 1, "m": m, "s": 1.0, "n_lambda": 256, "n_targets": nt, "eps": 1e-6,
+               "chunk": chunk, "timed": "spreading of every chunk + transform + batched solve; generation excluded"}
+        kern = "k_spread1d_fx (fixed-point shared-memory spreading, 17 channels)"
+    elif W == "pik-heat":
+        n, nv, m = 1_000_000_000, 10_000_000, 25
+        x = _dev_uniform(torch, n, 2, 11)
+        y = torch.exp(-0.1 * x[0]) * torch.sin(x[1]) + 0.1 * _dev_normal(torch, n, 12)
+        xv = _dev_uniform(torch, nv, 2, 13)
+        yv = torch.exp(-0.1 * xv[0]) * torch.sin(xv[1]) + 0.1 * _dev_normal(torch, nv, 14)
+        alpha = [[1, 0], [0, 2]]
+
+        def step():
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            lt = torch.tensor(1e-8, dtype=torch.float64, requires_grad=True)
+            mt = torch.tensor(1e-2, dtype=torch.float64, requires_grad=True)
+            at = torch.tensor([1.0, -0.1], dtype=torch.float64, requires_grad=True)
+            L = fk.heldout_loss(y, lt, torch.tensor(1.0, dtype=torch.float64), mt, at, x, xv, yv, m, alpha, 1e-6)
+            L.backward()
+            e1.record(st)
+            torch.cuda.synchronize()
+            _, rep = fk.fk_fit_pik(x, y, m, 1.0, 1e-8, 1e-2, alpha, [1.0, -0.1], 1e-6, "mixed", report=True)
+            return e0.elapsed_time(e1), rep["ms_kernel"], (L.item(), lt.grad.item(), mt.grad.item())
+
+        f_pt = 49 * (2 * 2 + 1)
+        cfg = {"workload": W, "n": n, "n_val": nv, "d": 2, "m": m, "s": 1.0, "lambda": 1e-8, "mu": 1e-2,
+               "operator": "d_t - 0.1 d_xx", "eps": 1e-6,
+               "timed": "fit + held-out loss + hypergradient (autograd forward and backward)"}
+        kern = "k_bin_accumulate (register-accumulation spreading, training fit)"
+    else:
+        n, d, m = 200_000_000, 8, 64
+        lam = n ** (-0.8)
+        x = _dev_uniform(torch, n, d, 41)
+        y = 0.1 * _dev_normal(torch, n, 42)
+        for j in range(d):
+            y += torch.sin((j + 1) * x[j]) / (j + 1)
+
+        def step():
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            th, rep = fk.fk_fit_additive(x, y, m, [lam], 1e-6, "mixed", report=True)
+            e1.record(st)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1), rep["ms_spread"], rep
+
+        f_pt = 8 * 7 * 3 + 28 * 49 * 3  # 8 1-D transforms (ones + y) and 28 2-D transforms of ones
+        cfg = {"workload": W, "n": n, "d": d, "m": m, "lambda": lam, "eps": 1e-6,
+               "timed": "8 1-D + 28 2-D type-1 transforms, block Gram, dense FP64 solve"}
+        kern = "all spreading kernels of the 36 transforms"
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    launches0 = fk.fk_launch_count()
+    res = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            res.append(step())
+    launches = (fk.fk_launch_count() - launches0) // max(1, args.steps)
+    ms = statistics.median(r[0] for r in res)
+    mk = statistics.median(r[1] for r in res)
+    achieved = f_pt * n / (mk / 1e3) / 1e12
+    line = {"metric": "fit points/s (" + W + ")", "value": n / (ms / 1e3), "unit": "points/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (drawn on the device)",
+            "config": cfg, "gpu_launches_per_step": launches,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": p32, "unit": "TFLOP/s", "frac": achieved / p32,
+                         "traffic": None, "kernel": kern, "flop_per_point": f_pt, "ms_kernel": mk,
+                         "peak_basis": "of derived peak: 148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % sm_max},
+            "clocks": clk.summary()}
+    if W == "pik-heat":
+        line["loss_and_grads"] = {"L": res[-1][2][0], "dL/dlambda": res[-1][2][1], "dL/dmu": res[-1][2][2]}
+    if W == "additive-8d":
+        line["report"] = res[-1][2]
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -157,6 +297,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload != "2d-sobolev":
+        run_row(args, rank, local)
         return
 
     import torch

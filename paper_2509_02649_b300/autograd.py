@@ -27,7 +27,9 @@ class HeldOutLoss(torch.autograd.Function):
         W = L.fk_penalty_weights(d, m, [lam_v], s=s_v, mu=mu_v, alpha=al, a=a_v, device=y.device)
         T, b = L.fk_build_system(x, y, m, eps, precision)
         theta = L.fk_solve(T, W, b, d, m)[0, 0]
-        loss, dW, dY = L.fk_hypergrad(x, xv, yv, m, T, W[0], theta, eps, precision)
+        # dL/dY (one type-2 pass over the training points and n doubles) only when asked
+        loss, dW, dY = L.fk_hypergrad(x, xv, yv, m, T, W[0], theta, eps, precision,
+                                      want_dy=bool(ctx.needs_input_grad[0]))
         g = L.fk_penalty_grads(d, m, dW, lam_v, s=s_v, mu=mu_v, alpha=al, a=a_v)
         ctx.save_for_backward(dY)
         ctx.pgrads = g
@@ -41,7 +43,7 @@ class HeldOutLoss(torch.autograd.Function):
         (dY,) = ctx.saved_tensors
         g = ctx.pgrads
         go = float(go)
-        gy = (go * dY).to(ctx.dtypes[0]).reshape(ctx.y_shape) if ctx.needs_input_grad[0] else None
+        gy = (go * dY).to(ctx.dtypes[0]).reshape(ctx.y_shape) if (ctx.needs_input_grad[0] and dY is not None) else None
         gl = torch.tensor(go * g[0], dtype=torch.float64)
         gs = torch.tensor(go * g[1], dtype=torch.float64)
         gm = torch.tensor(go * g[2], dtype=torch.float64)

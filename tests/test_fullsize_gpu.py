@@ -1,0 +1,150 @@
+"""Full-size runs of the physics-informed and additive workloads, checked through
+properties that hold at any size.
+
+With points uniform on the period the moments tend to T = I (delta_j0) and the
+right-hand side to the Fourier coefficients theta*_k of the target, so every fit is
+theta*_k / (1 + W_k) up to the sampling error O(sigma_Y / sqrt(n)) and the NUFFT
+error; theta* is known in closed form for both targets.  The hypergradients are
+checked against central finite differences of the same full-size loss.
+
+Inputs are drawn on the device with a seeded torch generator (the oracle is not
+involved, so nothing needs a host twin).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+fk = pytest.importorskip("paper_2509_02649_b300")
+
+ALPHA = [[1, 0], [0, 2]]  # P = d_t - c d_xx: terms d_t (coefficient 1) and d_xx (coefficient -c)
+
+
+def uniform(n, d, seed):
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    return torch.rand((d, n), generator=g, device="cuda", dtype=torch.float32) * (2 * math.pi) - math.pi
+
+
+def normal(n, seed, rows=1):
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    return torch.randn((rows, n), generator=g, device="cuda", dtype=torch.float32)
+
+
+def heat_data(n, seed):
+    x = uniform(n, 2, seed)
+    y = torch.exp(-0.1 * x[0]) * torch.sin(x[1]) + 0.1 * normal(n, seed + 1)[0]
+    return x, y
+
+
+def heat_theta_star(m):
+    """Fourier coefficients of exp(-0.1 t) sin(x) on [-pi, pi)^2, modes |k|_inf <= m,
+    lexicographic (t first).  (1/2pi) int exp(-0.1 t) e^{-ikt} dt = (-1)^k sinh(0.1 pi)
+    / (pi (0.1 + ik)); sin x has theta_{+1} = -i/2 and theta_{-1} = +i/2."""
+    k = np.arange(-m, m + 1)
+    at = ((-1.0) ** k) * math.sinh(0.1 * math.pi) / (math.pi * (0.1 + 1j * k))
+    sx = np.zeros(2 * m + 1, dtype=np.complex128)
+    sx[m + 1] = -0.5j
+    sx[m - 1] = 0.5j
+    return np.outer(at, sx).ravel()
+
+
+def pik_weights(m, lam, s, mu, c):
+    k = np.arange(-m, m + 1, dtype=np.float64)
+    kt, kx = np.meshgrid(k, k, indexing="ij")
+    kt, kx = kt.ravel(), kx.ravel()
+    r2 = kt ** 2 + kx ** 2
+    sob = 1.0 + np.where(r2 > 0, r2 ** s, 0.0)
+    P = 1j * kt + c * kx ** 2  # symbol of d_t - c d_xx on e^{i(kt t + kx x)}
+    return lam * sob + mu * np.abs(P) ** 2
+
+
+def test_pik_heat_full_size_closed_form():
+    n, m, lam, s, mu, c = 1_000_000_000, 25, 1e-8, 1.0, 1e-2, 0.1
+    x, y = heat_data(n, 11)
+    theta = fk.fk_fit_pik(x, y, m, s, lam, mu, ALPHA, [1.0, -c], 1e-6, "mixed")
+    th = theta.reshape(-1).cpu().numpy()
+    want = heat_theta_star(m) / (1.0 + pik_weights(m, lam, s, mu, c))
+    # sampling error ~ sqrt(Var(Y) / n) ~ 2e-5 in b; the fit cancels most of it
+    assert np.max(np.abs(th - want)) < 4e-5
+    D = (2 * m + 1) ** 2
+    assert np.max(np.abs(th[::-1] - np.conj(th))) < 1e-12  # Hermitian symmetry
+    assert th.shape == (D,)
+
+
+def test_pik_heat_full_size_hypergradient():
+    # Finite differences need a loss that resolves parameter steps of 1e-2 relative:
+    # the mixed path rounds theta to fp32 for prediction and its 2-D fp32 sums depend
+    # on the order points reach a cell, so the differences run on the FP64 path with
+    # one fixed (T, b) and only the penalty, solve and held-out loss re-evaluated.  The
+    # mixed autograd gradients (which rebuild T and b) must agree with them to 1e-3.
+    n, nv, m = 1_000_000_000, 10_000_000, 25
+    x, y = heat_data(n, 21)
+    xv, yv = heat_data(nv, 31)
+    params = dict(lam=1e-8, mu=1e-2, c=0.1)
+
+    lt = torch.tensor(params["lam"], dtype=torch.float64, requires_grad=True)
+    mt = torch.tensor(params["mu"], dtype=torch.float64, requires_grad=True)
+    at = torch.tensor([1.0, -params["c"]], dtype=torch.float64, requires_grad=True)
+    L = fk.heldout_loss(y, lt, torch.tensor(1.0, dtype=torch.float64), mt, at, x, xv, yv, m, ALPHA, 1e-6, "mixed")
+    L.backward()
+    grads = {"lam": lt.grad.item(), "mu": mt.grad.item(), "c": -at.grad[1].item()}
+    # the held-out MSE is close to the noise variance 0.01
+    assert 0.009 < L.item() < 0.012
+
+    x64, y64, xv64, yv64 = x.double(), y.double(), xv.double(), yv.double()
+    del x, y
+    T, b = fk.fk_build_system(x64, y64, m, 1e-9, "fp64")
+
+    def loss_at(lam, mu, c):
+        W = fk.fk_penalty_weights(2, m, [lam], s=1.0, mu=mu, alpha=ALPHA, a=[1.0, -c])
+        th = fk.fk_solve(T, W, b, 2, m)[0, 0]
+        return fk.fk_hypergrad(x64, xv64, yv64, m, T, W[0], th, 1e-9, "fp64", want_dy=False)
+
+    L0, dW, _ = loss_at(**params)
+    assert abs(L0 - L.item()) <= 1e-5 * L0
+    g = fk.fk_penalty_grads(2, m, dW, params["lam"], s=1.0, mu=params["mu"], alpha=ALPHA, a=[1.0, -params["c"]])
+    adj = {"lam": g[0], "mu": g[2], "c": -g[4]}
+
+    def fd(name, rel_step):
+        v = params[name]
+        h = rel_step * abs(v)
+        up = loss_at(**dict(params, **{name: v + h}))[0]
+        dn = loss_at(**dict(params, **{name: v - h}))[0]
+        return (up - dn) / (2 * h)
+
+    for name in ("lam", "mu", "c"):
+        f = fd(name, 1e-2)
+        assert abs(f - adj[name]) <= 1e-4 * abs(adj[name]), (name, f, adj[name])
+        assert abs(grads[name] - adj[name]) <= 1e-3 * abs(adj[name]), (name, grads[name], adj[name])
+
+
+def test_additive_full_size_closed_form():
+    n, d, m = 200_000_000, 8, 64
+    lam = n ** (-0.8)  # low-bias rate n^{-2s/(2s+1)} with s = 2
+    x = uniform(n, d, 41)
+    y = 0.1 * normal(n, 42)[0]
+    for j in range(d):
+        y += torch.sin((j + 1) * x[j]) / (j + 1)
+    theta = fk.fk_fit_additive(x, y, m, [lam], 1e-6, "mixed")
+    th = theta.reshape(d, 2 * m + 1).cpu().numpy()
+    want = np.zeros((d, 2 * m + 1), dtype=np.complex128)
+    for j in range(d):
+        want[j, m + j + 1] = -0.5j / (j + 1)
+        want[j, m - j - 1] = 0.5j / (j + 1)
+    want /= 1.0 + lam
+    nz = np.ones(2 * m + 1, dtype=bool)
+    nz[m] = False
+    # every non-intercept coefficient: sampling error ~ sqrt(Var(Y) / n) = 6e-5 at most
+    assert np.max(np.abs(th[:, nz] - want[:, nz])) < 3e-4
+    # intercepts: only their sum is determined well (it estimates the mean of Y, 0)
+    assert abs(th[:, m].sum()) < 3e-4
+    # the additive prediction at a few points against the target function
+    xq = uniform(4096, d, 43)
+    f = fk.fk_predict(theta, xq, m, 1e-6, "mixed", additive=True).reshape(-1).cpu().numpy()
+    fstar = sum(torch.sin((j + 1) * xq[j]) / (j + 1) for j in range(d)).cpu().numpy().astype(np.float64)
+    assert np.sqrt(np.mean((f - fstar) ** 2)) < 2e-3
