@@ -1011,6 +1011,10 @@ static fk_status cg_solve_fused(int d, int m, const double* T, const double* W, 
 }
 
 // ---------------------------------------------------------------- dispatcher
+fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, const double* rhs, int n_rhs,
+                              const fk_opts& o, double* sol, cudaStream_t st, Scratch& scr, unsigned* flags,
+                              int* iters_out, double* relres_out, bool* handled);
+
 fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, const double* rhs, int n_rhs,
                        const fk_opts& o, double* sol, cudaStream_t st, Scratch& scratch, unsigned* flags,
                        int* cg_iters, double* rel_res) {
@@ -1021,6 +1025,12 @@ fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, 
   if (cg_iters) *cg_iters = 0;
   if (rel_res) *rel_res = 0.0;
   if (solver == FK_SOLVER_CG) {
+    if (d == 2) {
+      bool handled = false;
+      const fk_status rc = cg_solve_persistent(m, T, W, n_w, rhs, n_rhs, o, sol, st, scratch, flags, cg_iters, rel_res,
+                                               &handled);
+      if (handled || rc != FK_OK) return rc;
+    }
     if (d <= 2) return cg_solve_fused(d, m, T, W, n_w, rhs, n_rhs, o, sol, st, scratch, cg_iters, rel_res);
     return cg_solve(d, m, T, W, n_w, rhs, n_rhs, o, sol, st, scratch, cg_iters, rel_res);
   }
@@ -1086,6 +1096,427 @@ fk_status solve_dense(const double* A, int64_t D, double* X, int n_rhs, int refi
     k_axpy_c<<<grid_for(2 * D * n_rhs, 256), 256, 0, st>>>(2 * D * n_rhs, R, X); note_launch();
     FK_CUDA(cudaGetLastError());
   }
+  return FK_OK;
+}
+
+}  // namespace fk
+
+namespace fk {
+
+// ---------------------------------------------------------------- CG in one cooperative launch
+// The fused CG above costs five dependent launches per iteration (2-D) and a host
+// round trip every four; at the workloads' sizes (D = 65^2, Lc = 256) each launch does
+// microseconds of work.  Here all iterations run in one cooperative launch whose CTAs
+// meet at a grid barrier between the phases of an iteration:
+//   P1 rows:    p = z + beta p (p = z at the first iteration) for one row of modes,
+//               zero-padded to Lc and transformed along the row;
+//   P2 columns: transform along the column, times the circulant spectrum, inverse;
+//   P3 rows:    inverse transform, q = (.) / Lc^2 + W p, and <p, q>;
+//   P4 update:  x += alpha p, r -= alpha q, z = r / diag, <r, z> and |r|^2.
+// Scalars that an iteration reads and the next one accumulates are kept in two copies
+// selected by the iteration's parity, so every CTA sees the same values within an
+// iteration without an extra barrier.  After convergence one more matvec of x gives
+// the true residual |b - A x|.  The barrier's wait is bounded (FK_ETIMEOUT).
+namespace {
+
+constexpr long long BAR_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+
+struct GridBar {
+  unsigned count, gen;
+};
+
+struct CgP {
+  int K, Lc, logLc, n_rhs, nsys, maxit;
+  int64_t D;
+  double tol2;
+  const double* T0p;  // &Re T_0
+  const cplx<double>* ch;
+  const double* W;
+  const double* b;
+  const double* tw;
+  double *x, *r, *z, *p, *q;
+  cplx<double>* buf;
+  double *rz, *rr, *pq, *bb, *rres;  // rz, rr: [2][nsys]
+  GridBar* bar;
+  unsigned* flags;
+  int* info;  // [0] iterations, [1] systems not converged
+};
+
+// all CTAs of the launch; false when the wait gave up (the caller returns)
+__device__ bool grid_sync(GridBar* gb, unsigned* flags) {
+  __shared__ int s_ok;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = atomicAdd(&gb->gen, 0u);
+    if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
+      atomicExch(&gb->count, 0u);
+      __threadfence();
+      atomicAdd(&gb->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*reinterpret_cast<volatile unsigned*>(&gb->gen) == g) {
+        if (*reinterpret_cast<volatile unsigned*>(flags) & FLAG_TIMEOUT) {
+          ok = 0;
+          break;
+        }
+        if (clock64() - t0 > BAR_WAIT_CYCLES) {
+          atomicOr(flags, FLAG_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ bool cg_active(const CgP& A, int it, int s) {
+  return __ldcg(A.rr + (it & 1) * A.nsys + s) > A.tol2 * __ldcg(A.bb + s);
+}
+
+__device__ __forceinline__ double block_sum_all(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += red[w];
+  __syncthreads();
+  return t;  // valid in thread 0
+}
+
+// P1 (final: the rows of x instead of the new direction)
+__device__ void cgp_rows_fwd(const CgP& A, cplx<double>* sl, int it, bool final_pass) {
+  const int K = A.K, Lc = A.Lc;
+  for (int item = blockIdx.x; item < A.nsys * K; item += gridDim.x) {
+    const int s = item / K, row = item - s * K;
+    if (!final_pass && !cg_active(A, it, s)) continue;
+    const int64_t o = 2 * (s * A.D + static_cast<int64_t>(row) * K);
+    double beta = 0.0;
+    if (!final_pass && it > 0)
+      beta = __ldcg(A.rz + (it & 1) * A.nsys + s) / __ldcg(A.rz + ((it + 1) & 1) * A.nsys + s);
+    for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
+      cplx<double> e;
+      e.x = e.y = 0.0;
+      if (i < K) {
+        if (final_pass) {
+          e.x = __ldcg(A.x + o + 2 * i);
+          e.y = __ldcg(A.x + o + 2 * i + 1);
+        } else {
+          e.x = __ldcg(A.z + o + 2 * i);
+          e.y = __ldcg(A.z + o + 2 * i + 1);
+          if (it > 0) {
+            e.x += beta * __ldcg(A.p + o + 2 * i);
+            e.y += beta * __ldcg(A.p + o + 2 * i + 1);
+          }
+          A.p[o + 2 * i] = e.x;
+          A.p[o + 2 * i + 1] = e.y;
+        }
+      }
+      sl[bitrev(i, A.logLc)] = e;
+    }
+    __syncthreads();
+    fft_smem<double>(sl, Lc, -1, A.tw);
+    cplx<double>* ob = A.buf + (static_cast<int64_t>(s) * K + row) * Lc;
+    for (int i = threadIdx.x; i < Lc; i += blockDim.x) ob[i] = sl[i];
+    if (!final_pass && row == 0 && threadIdx.x == 0) A.pq[s] = 0.0;
+    __syncthreads();
+  }
+}
+
+// P2
+__device__ void cgp_cols(const CgP& A, cplx<double>* sl, int it, bool final_pass) {
+  const int K = A.K, Lc = A.Lc;
+  for (int item = blockIdx.x; item < A.nsys * Lc; item += gridDim.x) {
+    const int s = item / Lc, c = item - s * Lc;
+    if (!final_pass && c == 0 && threadIdx.x == 0) {
+      // next iteration's accumulators; a finished system carries its values over so
+      // that it stays finished
+      const bool act = cg_active(A, it, s);
+      const int cur = (it & 1) * A.nsys + s, nxt = ((it + 1) & 1) * A.nsys + s;
+      A.rz[nxt] = act ? 0.0 : __ldcg(A.rz + cur);
+      A.rr[nxt] = act ? 0.0 : __ldcg(A.rr + cur);
+    }
+    if (!final_pass && !cg_active(A, it, s)) continue;
+    cplx<double>* bcol = A.buf + static_cast<int64_t>(s) * K * Lc + c;
+    for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
+      cplx<double> e;
+      e.x = e.y = 0.0;
+      if (i < K) {
+        const double2 v = __ldcg(reinterpret_cast<const double2*>(bcol + static_cast<int64_t>(i) * Lc));
+        e.x = v.x;
+        e.y = v.y;
+      }
+      sl[bitrev(i, A.logLc)] = e;
+    }
+    __syncthreads();
+    fft_smem<double>(sl, Lc, -1, A.tw);
+    for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
+      const cplx<double> a = A.ch[static_cast<int64_t>(i) * Lc + c], e = sl[i];
+      cplx<double> t;
+      t.x = a.x * e.x - a.y * e.y;
+      t.y = a.x * e.y + a.y * e.x;
+      sl[i] = t;
+    }
+    __syncthreads();
+    bitrev_permute<double>(sl, Lc, A.logLc);
+    fft_smem<double>(sl, Lc, +1, A.tw);
+    for (int i = threadIdx.x; i < K; i += blockDim.x) bcol[static_cast<int64_t>(i) * Lc] = sl[i];
+    __syncthreads();
+  }
+}
+
+// P3: q = A v for v = p (or x in the final pass) and <p, q>
+__device__ void cgp_rows_inv(const CgP& A, cplx<double>* sl, double* red, int it, bool final_pass) {
+  const int K = A.K, Lc = A.Lc;
+  const double inv = 1.0 / (static_cast<double>(Lc) * Lc);
+  for (int item = blockIdx.x; item < A.nsys * K; item += gridDim.x) {
+    const int s = item / K, row = item - s * K;
+    if (!final_pass && !cg_active(A, it, s)) continue;
+    const cplx<double>* bb = A.buf + (static_cast<int64_t>(s) * K + row) * Lc;
+    for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
+      const double2 v = __ldcg(reinterpret_cast<const double2*>(bb + i));
+      cplx<double> e;
+      e.x = v.x;
+      e.y = v.y;
+      sl[bitrev(i, A.logLc)] = e;
+    }
+    __syncthreads();
+    fft_smem<double>(sl, Lc, +1, A.tw);
+    const int64_t o = 2 * (s * A.D + static_cast<int64_t>(row) * K);
+    const double* Ws = A.W + static_cast<int64_t>(s / A.n_rhs) * A.D + static_cast<int64_t>(row) * K;
+    const double* v = final_pass ? A.x : A.p;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+      const double vr = __ldcg(v + o + 2 * i), vi = __ldcg(v + o + 2 * i + 1);
+      const double qr = sl[i].x * inv + Ws[i] * vr;
+      const double qi = sl[i].y * inv + Ws[i] * vi;
+      A.q[o + 2 * i] = qr;
+      A.q[o + 2 * i + 1] = qi;
+      acc += vr * qr + vi * qi;
+    }
+    if (!final_pass) {
+      const double t = block_sum_all(acc, red);
+      if (threadIdx.x == 0) atomicAdd(A.pq + s, t);
+    }
+    __syncthreads();
+  }
+}
+
+// P4 (final: |b - q|^2 into rres)
+__device__ void cgp_update(const CgP& A, double* red, int it, bool final_pass, double T0) {
+  const int64_t D = A.D;
+  const int chunk = 4 * blockDim.x;
+  const int nch = static_cast<int>((D + chunk - 1) / chunk);
+  for (int item = blockIdx.x; item < A.nsys * nch; item += gridDim.x) {
+    const int s = item / nch, cb = item - s * nch;
+    if (!final_pass && !cg_active(A, it, s)) continue;
+    const double* Ws = A.W + static_cast<int64_t>(s / A.n_rhs) * D;
+    const double* bs = A.b + 2 * static_cast<int64_t>(s % A.n_rhs) * D;
+    double a1 = 0.0, a2 = 0.0;
+    const double alpha = final_pass ? 0.0 : __ldcg(A.rz + (it & 1) * A.nsys + s) / __ldcg(A.pq + s);
+    for (int64_t k = static_cast<int64_t>(cb) * chunk + threadIdx.x; k < min(D, static_cast<int64_t>(cb + 1) * chunk);
+         k += blockDim.x) {
+      const int64_t o = 2 * (s * D + k);
+      const double q0 = __ldcg(A.q + o), q1 = __ldcg(A.q + o + 1);
+      if (final_pass) {
+        const double e0 = bs[2 * k] - q0, e1 = bs[2 * k + 1] - q1;
+        a1 += e0 * e0 + e1 * e1;
+        continue;
+      }
+      const double p0 = __ldcg(A.p + o), p1 = __ldcg(A.p + o + 1);
+      A.x[o] = __ldcg(A.x + o) + alpha * p0;
+      A.x[o + 1] = __ldcg(A.x + o + 1) + alpha * p1;
+      const double r0 = __ldcg(A.r + o) - alpha * q0, r1 = __ldcg(A.r + o + 1) - alpha * q1;
+      A.r[o] = r0;
+      A.r[o + 1] = r1;
+      const double id = 1.0 / (T0 + Ws[k]);
+      A.z[o] = r0 * id;
+      A.z[o + 1] = r1 * id;
+      a1 += (r0 * r0 + r1 * r1) * id;
+      a2 += r0 * r0 + r1 * r1;
+    }
+    const double t1 = block_sum_all(a1, red);
+    const double t2 = final_pass ? 0.0 : block_sum_all(a2, red);
+    if (threadIdx.x == 0) {
+      if (final_pass) {
+        atomicAdd(A.rres + s, t1);
+      } else {
+        atomicAdd(A.rz + ((it + 1) & 1) * A.nsys + s, t1);
+        atomicAdd(A.rr + ((it + 1) & 1) * A.nsys + s, t2);
+      }
+    }
+  }
+}
+
+// x = 0, r = b, z = b / diag; <r, z> -> rz[0], |b|^2 -> bb and rr[0]
+__device__ void cgp_init(const CgP& A, double* red, double T0) {
+  const int64_t D = A.D;
+  const int chunk = 4 * blockDim.x;
+  const int nch = static_cast<int>((D + chunk - 1) / chunk);
+  for (int item = blockIdx.x; item < A.nsys * nch; item += gridDim.x) {
+    const int s = item / nch, cb = item - s * nch;
+    const double* Ws = A.W + static_cast<int64_t>(s / A.n_rhs) * D;
+    const double* bs = A.b + 2 * static_cast<int64_t>(s % A.n_rhs) * D;
+    double a1 = 0.0, a2 = 0.0;
+    for (int64_t k = static_cast<int64_t>(cb) * chunk + threadIdx.x; k < min(D, static_cast<int64_t>(cb + 1) * chunk);
+         k += blockDim.x) {
+      const int64_t o = 2 * (s * D + k);
+      const double b0 = bs[2 * k], b1 = bs[2 * k + 1];
+      const double id = 1.0 / (T0 + Ws[k]);
+      A.x[o] = 0.0;
+      A.x[o + 1] = 0.0;
+      A.r[o] = b0;
+      A.r[o + 1] = b1;
+      A.z[o] = b0 * id;
+      A.z[o + 1] = b1 * id;
+      a1 += (b0 * b0 + b1 * b1) * id;
+      a2 += b0 * b0 + b1 * b1;
+    }
+    const double t1 = block_sum_all(a1, red);
+    const double t2 = block_sum_all(a2, red);
+    if (threadIdx.x == 0) {
+      atomicAdd(A.rz + s, t1);
+      atomicAdd(A.bb + s, t2);
+      atomicAdd(A.rr + s, t2);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_cg_persist2d(CgP A) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<double>* sl = reinterpret_cast<cplx<double>*>(smem_raw);
+  __shared__ double red[32];
+  double T0 = __ldg(A.T0p);
+  if (!(T0 > 0.0)) T0 = 1.0;
+  cgp_init(A, red, T0);
+  if (!grid_sync(A.bar, A.flags)) return;
+  int it = 0;
+  for (; it < A.maxit; ++it) {
+    bool any = false;
+    for (int s = 0; s < A.nsys && !any; ++s) any = cg_active(A, it, s);
+    if (!any) break;
+    cgp_rows_fwd(A, sl, it, false);
+    if (!grid_sync(A.bar, A.flags)) return;
+    cgp_cols(A, sl, it, false);
+    if (!grid_sync(A.bar, A.flags)) return;
+    cgp_rows_inv(A, sl, red, it, false);
+    if (!grid_sync(A.bar, A.flags)) return;
+    cgp_update(A, red, it, false, T0);
+    if (!grid_sync(A.bar, A.flags)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int left = 0;
+    for (int s = 0; s < A.nsys; ++s) left += cg_active(A, it, s) ? 1 : 0;
+    A.info[0] = it;
+    A.info[1] = left;
+  }
+  // true residual of the result
+  cgp_rows_fwd(A, sl, it, true);
+  if (!grid_sync(A.bar, A.flags)) return;
+  cgp_cols(A, sl, it, true);
+  if (!grid_sync(A.bar, A.flags)) return;
+  cgp_rows_inv(A, sl, red, it, true);
+  if (!grid_sync(A.bar, A.flags)) return;
+  cgp_update(A, red, it, true, T0);
+}
+
+}  // namespace
+
+fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, const double* rhs, int n_rhs,
+                              const fk_opts& o, double* sol, cudaStream_t st, Scratch& scr, unsigned* flags,
+                              int* iters_out, double* relres_out, bool* handled) {
+  *handled = false;
+  int dev = 0, coop = 0, sms = 0;
+  FK_CUDA(cudaGetDevice(&dev));
+  FK_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  FK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int K = 2 * m + 1;
+  int Lc = next_pow2i(4 * m + 1);
+  if (Lc < 2) Lc = 2;
+  int logLc = 0;
+  while ((1 << logLc) < Lc) ++logLc;
+  const size_t smem = sizeof(cplx<double>) * Lc;
+  if (!coop || smem > 48 * 1024) return FK_OK;  // not handled: the caller uses the multi-launch form
+  const int threads = 256;
+  int per_sm = 0;
+  FK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_persist2d, threads, smem));
+  if (per_sm < 1) return FK_OK;
+  const int nsys = n_w * n_rhs;
+  const int64_t D = static_cast<int64_t>(K) * K;
+  const int64_t want = std::max<int64_t>(static_cast<int64_t>(nsys) * Lc, 1);
+  const int nb = static_cast<int>(std::min<int64_t>(want, static_cast<int64_t>(std::min(per_sm, 2)) * sms));
+
+  CgP A{};
+  A.K = K;
+  A.Lc = Lc;
+  A.logLc = logLc;
+  A.n_rhs = n_rhs;
+  A.nsys = nsys;
+  A.maxit = o.cg_maxit;
+  A.D = D;
+  A.tol2 = o.cg_tol * o.cg_tol;
+  A.W = W;
+  A.b = rhs;
+  A.x = sol;
+  int64_t centre = 2 * static_cast<int64_t>(4 * m + 1) * m + 2 * m;  // index of T_(0,0)
+  A.T0p = T + 2 * centre;
+  cplx<double>* ch;
+  double* tw;
+  FK_TRY(scr.alloc(&ch, static_cast<int64_t>(Lc) * Lc));
+  FK_TRY(scr.alloc(&tw, 2 * static_cast<size_t>(Lc)));
+  FK_TRY(fft_twiddles(Lc, tw, st));
+  FK_CUDA(cudaMemsetAsync(ch, 0, sizeof(cplx<double>) * Lc * Lc, st));
+  const int64_t M2 = static_cast<int64_t>(4 * m + 1) * (4 * m + 1);
+  k_circ_embed<<<grid_for(M2, 256), 256, 0, st>>>(2, m, Lc, T, ch); note_launch();
+  FK_CUDA(cudaGetLastError());
+  FK_TRY(fft_lines<double>(ch, Lc, Lc, Lc, 1, -1, tw, st));
+  FK_TRY(fft_lines<double>(ch, Lc, Lc, 1, Lc, -1, tw, st));
+  A.ch = ch;
+  A.tw = tw;
+  FK_TRY(scr.alloc(&A.r, 2 * D * nsys));
+  FK_TRY(scr.alloc(&A.z, 2 * D * nsys));
+  FK_TRY(scr.alloc(&A.p, 2 * D * nsys));
+  FK_TRY(scr.alloc(&A.q, 2 * D * nsys));
+  FK_TRY(scr.alloc(&A.buf, static_cast<size_t>(nsys) * K * Lc));
+  double* scal;
+  FK_TRY(scr.alloc(&scal, 7 * static_cast<size_t>(nsys)));
+  FK_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * 7 * nsys, st));
+  A.rz = scal;
+  A.rr = scal + 2 * nsys;
+  A.pq = scal + 4 * nsys;
+  A.bb = scal + 5 * nsys;
+  A.rres = scal + 6 * nsys;
+  unsigned char* misc;
+  FK_TRY(scr.alloc(&misc, 64));
+  FK_CUDA(cudaMemsetAsync(misc, 0, 64, st));
+  A.bar = reinterpret_cast<GridBar*>(misc);
+  A.info = reinterpret_cast<int*>(misc + 32);
+  A.flags = flags;
+  void* args[] = {&A};
+  FK_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_cg_persist2d), dim3(nb), dim3(threads), args, smem,
+                                      st));
+  note_launch();
+  int info[2] = {0, 0};
+  std::vector<double> rres(nsys), bb(nsys);
+  FK_CUDA(cudaMemcpyAsync(info, A.info, sizeof(info), cudaMemcpyDeviceToHost, st));
+  FK_CUDA(cudaMemcpyAsync(rres.data(), A.rres, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
+  FK_CUDA(cudaMemcpyAsync(bb.data(), A.bb, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
+  FK_CUDA(cudaStreamSynchronize(st));
+  *handled = true;
+  unsigned fl = 0;
+  FK_CUDA(cudaMemcpy(&fl, flags, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (fl & FLAG_TIMEOUT) return set_error(FK_ETIMEOUT, "CG grid barrier gave up");
+  double worst = 0.0;
+  for (int s = 0; s < nsys; ++s) worst = std::max(worst, bb[s] > 0 ? std::sqrt(rres[s] / bb[s]) : std::sqrt(rres[s]));
+  if (iters_out) *iters_out = info[0];
+  if (relres_out) *relres_out = worst;
+  if (info[1] != 0) return set_error(FK_ENOCONV, "CG did not converge in %d iterations", o.cg_maxit);
   return FK_OK;
 }
 

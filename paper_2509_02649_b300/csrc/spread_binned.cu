@@ -386,6 +386,126 @@ __global__ void __launch_bounds__(S_THREADS, 1) k_bin_scatter(PartArgs A) {
   }
 }
 
+// Pipelined scatter for aligned inputs: the next tile's coordinates and strengths
+// arrive by TMA bulk copies while the current tile is sorted and written out; each
+// thread keeps its points' records in registers between the histogram and the
+// placement, so every key is computed once.
+constexpr int S2_THREADS = 1024;
+constexpr int S2_PER = 7;                       // points per thread per tile
+constexpr int S2_TILE = S2_THREADS * S2_PER;    // 7168
+
+struct S2Layout {
+  size_t stage, sorted, ints, bar, total;
+};
+__host__ __device__ inline S2Layout s2_layout(int G) {
+  S2Layout L;
+  L.stage = 0;                                             // float [3][S2_TILE]
+  L.sorted = L.stage + sizeof(float) * 3 * S2_TILE;        // uint4 [S2_TILE]
+  L.ints = L.sorted + sizeof(uint4) * S2_TILE;             // int [3 (G + 1)]
+  L.bar = (L.ints + sizeof(int) * 3 * (G + 1) + 15) & ~static_cast<size_t>(15);
+  L.total = L.bar + 16;
+  return L;
+}
+
+__global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter2(PartArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int wsum[32];
+  const int G = A.G;
+  const S2Layout L = s2_layout(G);
+  float* stage = reinterpret_cast<float*>(smem + L.stage);
+  uint4* sorted = reinterpret_cast<uint4*>(smem + L.sorted);
+  int* cursor = reinterpret_cast<int*>(smem + L.ints);  // [G + 1]
+  int* tcnt = cursor + (G + 1);                          // [G + 1]
+  int* tcur = tcnt + (G + 1);                            // [G + 1]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
+  const int tid = threadIdx.x;
+  const float inv_cpc = 1.0f / static_cast<float>(A.cells_per);
+  owner_bases(A.tot, G, cursor, wsum);
+  for (int o = tid; o < G; o += S2_THREADS) cursor[o] += A.off[static_cast<size_t>(blockIdx.x) * G + o];
+  const int64_t s0 = static_cast<int64_t>(blockIdx.x) * A.range;
+  const int64_t e0 = min(A.n, s0 + A.range);
+  if (tid == 0) {
+    mbar_init(bar);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int64_t t0) {  // one thread: bulk copies of tile t0
+    const int cnt = static_cast<int>(min(static_cast<int64_t>(S2_TILE), e0 - t0));
+    const unsigned bytes = static_cast<unsigned>(cnt) * 4u;
+    fence_proxy_async();
+    mbar_arrive_expect(bar, bytes * (A.has_y ? 3u : 2u));
+    bulk_g2s(stage, A.x + t0, bytes, bar);
+    bulk_g2s(stage + S2_TILE, A.x + A.n + t0, bytes, bar);
+    if (A.has_y) bulk_g2s(stage + 2 * S2_TILE, A.y + t0, bytes, bar);
+  };
+  if (tid == 0 && s0 < e0) issue(s0);
+  unsigned phase = 0;
+  for (int64_t t0 = s0; t0 < e0; t0 += S2_TILE) {
+    const int cnt = static_cast<int>(min(static_cast<int64_t>(S2_TILE), e0 - t0));
+    for (int o = tid; o <= G; o += S2_THREADS) tcnt[o] = 0;
+    if (!mbar_wait(bar, phase, A.flags)) return;
+    phase ^= 1u;
+    __syncthreads();
+    uint4 rec[S2_PER];
+#pragma unroll
+    for (int k = 0; k < S2_PER; ++k) {
+      const int i = k * S2_THREADS + tid;
+      rec[k].x = 0xFFFFFFFFu;
+      if (i < cnt) {
+        float f0, f1;
+        uint32_t key;
+        if (point_key(stage[i], stage[S2_TILE + i], A, inv_cpc, &f0, &f1, &key)) {
+          rec[k] = make_uint4(key, __float_as_uint(f0), __float_as_uint(f1),
+                              A.has_y ? __float_as_uint(stage[2 * S2_TILE + i]) : 0u);
+          atomicAdd(&tcnt[key >> 16], 1);
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && t0 + S2_TILE < e0) issue(t0 + S2_TILE);  // the stage is free again
+    if (tid < 32) {  // exclusive scan of the tile counts (one warp)
+      int carry = 0;
+      for (int o0 = 0; o0 <= G; o0 += 32) {
+        const int o = o0 + tid;
+        const int v = (o < G) ? tcnt[o] : 0;
+        int incl = v;
+#pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, dd);
+          if (tid >= dd) incl += t;
+        }
+        if (o <= G) {
+          tcnt[o] = carry + incl - v;
+          tcur[o] = carry + incl - v;
+        }
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < S2_PER; ++k) {
+      if (rec[k].x != 0xFFFFFFFFu) {
+        const int pos = atomicAdd(&tcur[rec[k].x >> 16], 1);
+        sorted[pos] = rec[k];
+      }
+    }
+    __syncthreads();
+    const int valid = tcnt[G];
+    for (int j = tid; j < valid; j += S2_THREADS) {
+      const uint4 r = sorted[j];
+      const int o = static_cast<int>(r.x >> 16);
+      A.rec[cursor[o] + (j - tcnt[o])] = r;
+    }
+    __syncthreads();
+    for (int o = tid; o < G; o += S2_THREADS) cursor[o] += tcnt[o + 1] - tcnt[o];
+    __syncthreads();
+  }
+  for (int o = tid; o < G; o += S2_THREADS) {
+    const int c = A.cnt[static_cast<size_t>(blockIdx.x) * G + o];
+    for (int k = c; k < ((c + 7) & ~7); ++k) A.rec[cursor[o]++] = make_uint4(0xFFFFu, 0u, 0u, 0u);
+  }
+}
+
 struct AccArgs {
   int N, G, cells_per, ncells;
   float beta;
@@ -685,9 +805,15 @@ fk_status spread_binned(const EsPlan& p, int64_t n, const float* x, const float*
   FK_CUDA(cudaGetLastError());
   k_bin_scan<<<G, 256, 0, st>>>(P); note_launch();
   FK_CUDA(cudaGetLastError());
-  const size_t sm_scatter = sizeof(uint4) * S_TILE + sizeof(unsigned short) * S_TILE + sizeof(int) * (3 * G + 2);
-  FK_CUDA(cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm_scatter)));
-  k_bin_scatter<<<P.nblk, S_THREADS, sm_scatter, st>>>(P); note_launch();
+  if (P.vec_ok) {
+    const size_t sm2 = s2_layout(G).total;
+    FK_CUDA(cudaFuncSetAttribute(k_bin_scatter2, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm2)));
+    k_bin_scatter2<<<P.nblk, S2_THREADS, sm2, st>>>(P); note_launch();
+  } else {
+    const size_t sm_scatter = sizeof(uint4) * S_TILE + sizeof(unsigned short) * S_TILE + sizeof(int) * (3 * G + 2);
+    FK_CUDA(cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm_scatter)));
+    k_bin_scatter<<<P.nblk, S_THREADS, sm_scatter, st>>>(P); note_launch();
+  }
   FK_CUDA(cudaGetLastError());
 
   AccArgs A{};
