@@ -36,8 +36,10 @@ ACC_DRAM_BYTES_PER_POINT = (323.824896e6 + 4.352e6) / 2e7  # k_bin_accumulate, 2
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    # a step takes a few ms: 100 steps make the timed region ~0.35 s, long enough that the
+    # nvidia-smi clock sampling running during it (each query stalls the GPU ~3 ms) costs ~2 %
+    ap.add_argument("--steps", type=int, default=None, help="default: 100 (2d-sobolev), 3 (sweep-1d), 20 (others)")
+    ap.add_argument("--warmup", type=int, default=None, help="default: 5 (2d-sobolev), 1 (sweep-1d), 3 (others)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=WL["n"], help="points (default: the workload's 1e8)")
     ap.add_argument("--spread", default="auto", choices=["auto", "atomic", "binned"])
@@ -46,7 +48,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="2d-sobolev", choices=["2d-sobolev", "sweep-1d", "pik-heat", "additive-8d"],
                     help="2d-sobolev is the headline line; the others time the other hot-path rows")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.steps is None:
+        a.steps = {"2d-sobolev": 100, "sweep-1d": 3}.get(a.workload, 20) if a.impl == "ours" else 10
+    if a.warmup is None:
+        a.warmup = {"2d-sobolev": 5, "sweep-1d": 1}.get(a.workload, 3)
+    return a
 
 
 def measured_peaks():

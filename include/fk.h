@@ -115,6 +115,13 @@ typedef struct {
 
 FK_API void fk_default_opts(fk_opts* opts);
 
+/* Workspace: every call takes its scratch from a library-owned stream-ordered memory
+ * pool of the current device (created at first use) that keeps freed blocks, so that
+ * repeated calls of the same shape reuse device memory.  fk_release_workspace returns
+ * the pool's unused memory of the current device to the system (synchronises the
+ * device). */
+FK_API fk_status fk_release_workspace(void);
+
 /* Sobolev / low-bias estimator (Eq. 2 with Sec. 3.1 or 3.2 penalty) for a batch of
  * n_lambda regularisation values and n_targets response vectors.
  *   d in {1, 2, 3}; n >= 1; m >= 0; s >= 0; eps in [1e-14, 1e-1]; lambdas > 0.

@@ -28,7 +28,7 @@ EXPORTS = ["fk_default_opts", "fk_fit_sobolev", "fk_fit_pik", "fk_fit_additive",
            "fk_type2", "fk_build_system", "fk_penalty_weights", "fk_solve", "fk_hypergrad", "fk_last_error",
            "fk_workspace_bytes", "fk_version", "fk_launch_count", "fk_type1_noalloc", "fk_penalty_grads",
            "fk_accum_create", "fk_accum_add", "fk_accum_system", "fk_accum_fit_sobolev", "fk_accum_reset",
-           "fk_accum_destroy", "fk_generate_sweep_1d"]
+           "fk_accum_destroy", "fk_generate_sweep_1d", "fk_release_workspace"]
 
 
 class FkError(RuntimeError):
@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
             "fk_accum_reset": (_I, [_P, _P]),
             "fk_accum_destroy": (_I, [_P]),
             "fk_generate_sweep_1d": (_I, [ctypes.c_uint64, _I, _L, _L, _I, _P, _P, _P, _P]),
+            "fk_release_workspace": (_I, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -400,3 +401,8 @@ def generate_sweep_1d(first: int, n: int, n_targets: int = 16, seed: int = 20250
     _check(lib().fk_generate_sweep_1d(seed, workload, first, n, n_targets, x.data_ptr(), y.data_ptr(),
                                       amax.data_ptr(), _stream()))
     return x, y, amax
+
+
+def fk_release_workspace():
+    """Return the library's unused workspace memory on the current device."""
+    _check(lib().fk_release_workspace())

@@ -3,6 +3,7 @@
 #include "fk_internal.cuh"
 
 #include <atomic>
+#include <mutex>
 #include <chrono>
 #include <vector>
 
@@ -36,6 +37,33 @@ struct KernelTimerScope {
   }
   ~KernelTimerScope() { t->on = false; }
 };
+
+static std::mutex g_pool_mutex;
+static cudaMemPool_t g_pools[64] = {};
+
+cudaMemPool_t workspace_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(g_pool_mutex);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = pool;
+  }
+  return g_pools[dev];
+}
 
 fk_status set_error(fk_status st, const char* fmt, ...) {
   char buf[512];
@@ -197,6 +225,15 @@ void fk_default_opts(fk_opts* o) {
 }
 
 const char* fk_last_error(void) { return g_err.c_str(); }
+
+fk_status fk_release_workspace(void) {
+  clear_error();
+  cudaMemPool_t pool = workspace_pool();
+  if (!pool) return set_error(FK_ECUDA, "no workspace pool on this device");
+  FK_CUDA(cudaDeviceSynchronize());
+  FK_CUDA(cudaMemPoolTrimTo(pool, 0));
+  return FK_OK;
+}
 
 const char* fk_version(void) { return "fk 0.1 (sm_103a)"; }
 

@@ -80,6 +80,11 @@ struct EsPlan {
 fk_status make_es_plan(int d, int kmax, double eps, double upsampfac, EsPlan* p);
 
 // ------------------------------------------------------------------ workspace
+// Library-owned stream-ordered memory pool of the current device.  It keeps freed
+// blocks (release threshold unlimited), so repeated calls reuse the same device
+// memory instead of mapping it again; fk_release_workspace() trims it.
+cudaMemPool_t workspace_pool();
+
 // Stream-ordered scratch allocation tracked for release at scope exit.
 struct Scratch {
   cudaStream_t st;
@@ -97,10 +102,11 @@ struct Scratch {
     size_t bytes = elems * sizeof(T);
     if (bytes == 0) bytes = 16;
     void* q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, bytes, st);
+    cudaMemPool_t pool = workspace_pool();
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(&q, bytes, pool, st) : cudaMallocAsync(&q, bytes, st);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      return set_error(FK_ENOMEM, "cudaMallocAsync(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+      return set_error(FK_ENOMEM, "stream-ordered allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
     }
     ptrs.push_back(q);
     *p = static_cast<T*>(q);

@@ -50,6 +50,12 @@ __device__ __forceinline__ float rsqrt_approx(float v) {
   return r;
 }
 
+__device__ __forceinline__ float sqrt_approx(float v) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
+
 __device__ __forceinline__ float ex2_approx(float v) {
   float r;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
@@ -65,8 +71,8 @@ __device__ __forceinline__ void es_taps(float f, float bl, float* out) {
 #pragma unroll
   for (int a = 0; a < W; ++a) {
     const float z = fmaf(static_cast<float>(a), sc, z0);
-    const float t = fmaxf(fmaf(-z, z, 1.0f), 1e-30f);
-    out[a] = ex2_approx(fmaf(bl, t * rsqrt_approx(t), -bl));
+    const float t = fmaxf(fmaf(-z, z, 1.0f), 0.0f);
+    out[a] = ex2_approx(fmaf(bl, sqrt_approx(t), -bl));
   }
 }
 
