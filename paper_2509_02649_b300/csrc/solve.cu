@@ -8,6 +8,8 @@
 #include "fk_internal.cuh"
 #include "fft_device.cuh"
 
+#include <map>
+#include <mutex>
 #include <vector>
 
 namespace fk {
@@ -1444,8 +1446,20 @@ fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, 
   const size_t smem = sizeof(cplx<double>) * Lc;
   if (!coop || smem > 48 * 1024) return FK_OK;  // not handled: the caller uses the multi-launch form
   const int threads = 256;
+  // resident CTAs per SM for this shared-memory size (cached per device)
+  static std::mutex occ_mu;
+  static std::map<std::pair<int, size_t>, int> occ_cache;
   int per_sm = 0;
-  FK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_persist2d, threads, smem));
+  {
+    std::lock_guard<std::mutex> lock(occ_mu);
+    auto it = occ_cache.find({dev, smem});
+    if (it != occ_cache.end()) {
+      per_sm = it->second;
+    } else {
+      FK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_persist2d, threads, smem));
+      occ_cache[{dev, smem}] = per_sm;
+    }
+  }
   if (per_sm < 1) return FK_OK;
   const int nsys = n_w * n_rhs;
   const int64_t D = static_cast<int64_t>(K) * K;
@@ -1503,14 +1517,14 @@ fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, 
                                       st));
   note_launch();
   int info[2] = {0, 0};
+  unsigned fl = 0;
   std::vector<double> rres(nsys), bb(nsys);
   FK_CUDA(cudaMemcpyAsync(info, A.info, sizeof(info), cudaMemcpyDeviceToHost, st));
   FK_CUDA(cudaMemcpyAsync(rres.data(), A.rres, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
   FK_CUDA(cudaMemcpyAsync(bb.data(), A.bb, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
+  FK_CUDA(cudaMemcpyAsync(&fl, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   FK_CUDA(cudaStreamSynchronize(st));
   *handled = true;
-  unsigned fl = 0;
-  FK_CUDA(cudaMemcpy(&fl, flags, sizeof(unsigned), cudaMemcpyDeviceToHost));
   if (fl & FLAG_TIMEOUT) return set_error(FK_ETIMEOUT, "CG grid barrier gave up");
   double worst = 0.0;
   for (int s = 0; s < nsys; ++s) worst = std::max(worst, bb[s] > 0 ? std::sqrt(rres[s] / bb[s]) : std::sqrt(rres[s]));

@@ -158,6 +158,7 @@ constexpr int P_THREADS = 1024;  // count kernel
 constexpr int P_NWARPS = P_THREADS / 32;
 constexpr int P_TILE = 4096;     // points per partition block, at least
 constexpr int CAPR = 4096;       // records per accumulation round
+constexpr int FLUSH_PTS = 2048;  // points per fp32 register run before an fp64 flush
 
 // cells per owner: one lane per cell, or two (one per channel) in pair mode
 template <bool PAIR>
@@ -178,10 +179,22 @@ struct PartArgs {
   int* cnt;         // [nblk][G]
   int* off;         // [nblk][G] offset of the block's run inside its owner's bucket
   int* tot;         // [G]
-  uint4* rec;       // [n] records, bucketed by owner
+  uint4* rec;       // records, bucketed by owner
   unsigned* flags;
   float c_hi, c_lo;
+  // one-pass partition: owner o's bucket is rec[o cap, (o + 1) cap), filled through
+  // atomic reservations on fill[o]; ovf is set when a bucket would overflow, and the
+  // exact kernels (count, scan, scatter) then run instead (guarded = 1: they return at
+  // once when ovf is clear)
+  int* fill;
+  int cap;
+  unsigned* ovf;
+  int guarded;
 };
+
+__device__ __forceinline__ bool skip_guarded(const PartArgs& A) {
+  return A.guarded && *reinterpret_cast<const volatile unsigned*>(A.ovf) == 0u;
+}
 
 // owner and packed key of one point; returns false for a point out of range
 __device__ __forceinline__ bool point_key(float x0, float x1, const PartArgs& A, float inv_cpc, float* f0, float* f1,
@@ -199,6 +212,7 @@ __device__ __forceinline__ bool point_key(float x0, float x1, const PartArgs& A,
 }
 
 __global__ void __launch_bounds__(P_THREADS) k_bin_count(PartArgs A) {
+  if (skip_guarded(A)) return;
   extern __shared__ int whist[];  // [P_NWARPS][G]
   const int tid = threadIdx.x, warp = tid >> 5;
   const int G = A.G;
@@ -241,6 +255,7 @@ __global__ void __launch_bounds__(P_THREADS) k_bin_count(PartArgs A) {
 
 // one CTA per owner: exclusive scan over partition blocks
 __global__ void k_bin_scan(PartArgs A) {
+  if (skip_guarded(A)) return;
   __shared__ int wsum[32];
   const int o = blockIdx.x, G = A.G;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -297,6 +312,7 @@ constexpr int S_THREADS = 1024;
 constexpr int S_TILE = 12288;
 
 __global__ void __launch_bounds__(S_THREADS, 1) k_bin_scatter(PartArgs A) {
+  if (skip_guarded(A)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int wsum[32];
   const int G = A.G;
@@ -414,6 +430,7 @@ __host__ __device__ inline S2Layout s2_layout(int G) {
 }
 
 __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter2(PartArgs A) {
+  if (skip_guarded(A)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int wsum[32];
   const int G = A.G;
@@ -512,6 +529,116 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter2(PartArgs A) {
   }
 }
 
+// One-pass scatter (no count pass): as k_bin_scatter2, but each tile reserves room
+// for its owner runs in fixed-capacity buckets with one global atomic per (tile,
+// owner).  A reservation that would pass the capacity writes nothing and sets ovf.
+__global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter1(PartArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int G = A.G;
+  const S2Layout L = s2_layout(G);
+  float* stage = reinterpret_cast<float*>(smem + L.stage);
+  uint4* sorted = reinterpret_cast<uint4*>(smem + L.sorted);
+  int* tpos = reinterpret_cast<int*>(smem + L.ints);  // [G + 1] reserved slot in the bucket, -1: none
+  int* tcnt = tpos + (G + 1);                          // [G + 1]
+  int* tcur = tcnt + (G + 1);                          // [G + 1]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
+  const int tid = threadIdx.x;
+  const float inv_cpc = 1.0f / static_cast<float>(A.cells_per);
+  const int64_t s0 = static_cast<int64_t>(blockIdx.x) * A.range;
+  const int64_t e0 = min(A.n, s0 + A.range);
+  if (tid == 0) {
+    mbar_init(bar);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int64_t t0) {
+    const int cnt = static_cast<int>(min(static_cast<int64_t>(S2_TILE), e0 - t0));
+    const unsigned bytes = static_cast<unsigned>(cnt) * 4u;
+    fence_proxy_async();
+    mbar_arrive_expect(bar, bytes * (A.has_y ? 3u : 2u));
+    bulk_g2s(stage, A.x + t0, bytes, bar);
+    bulk_g2s(stage + S2_TILE, A.x + A.n + t0, bytes, bar);
+    if (A.has_y) bulk_g2s(stage + 2 * S2_TILE, A.y + t0, bytes, bar);
+  };
+  if (tid == 0 && s0 < e0) issue(s0);
+  unsigned phase = 0;
+  for (int64_t t0 = s0; t0 < e0; t0 += S2_TILE) {
+    const int cnt = static_cast<int>(min(static_cast<int64_t>(S2_TILE), e0 - t0));
+    for (int o = tid; o <= G; o += S2_THREADS) tcnt[o] = 0;
+    if (!mbar_wait(bar, phase, A.flags)) return;
+    phase ^= 1u;
+    __syncthreads();
+    uint4 rec[S2_PER];
+#pragma unroll
+    for (int k = 0; k < S2_PER; ++k) {
+      const int i = k * S2_THREADS + tid;
+      rec[k].x = 0xFFFFFFFFu;
+      if (i < cnt) {
+        float f0, f1;
+        uint32_t key;
+        if (point_key(stage[i], stage[S2_TILE + i], A, inv_cpc, &f0, &f1, &key)) {
+          rec[k] = make_uint4(key, __float_as_uint(f0), __float_as_uint(f1),
+                              A.has_y ? __float_as_uint(stage[2 * S2_TILE + i]) : 0u);
+          atomicAdd(&tcnt[key >> 16], 1);
+        } else {
+          atomicOr(A.flags, FLAG_RANGE);
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && t0 + S2_TILE < e0) issue(t0 + S2_TILE);
+    // reservations in the buckets (one global atomic per owner present in the tile)
+    for (int o = tid; o < G; o += S2_THREADS) {
+      const int c = tcnt[o];
+      int pos = -1;
+      if (c > 0) {
+        pos = atomicAdd(A.fill + o, c);
+        if (pos + c > A.cap) {
+          atomicOr(A.ovf, 1u);
+          pos = -1;
+        }
+      }
+      tpos[o] = pos;
+    }
+    if (tid >= S2_THREADS - 32) {  // exclusive scan of the tile counts (last warp)
+      const int ln = tid - (S2_THREADS - 32);
+      int carry = 0;
+      for (int o0 = 0; o0 <= G; o0 += 32) {
+        const int o = o0 + ln;
+        const int v = (o < G) ? tcnt[o] : 0;
+        int incl = v;
+#pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, dd);
+          if (ln >= dd) incl += t;
+        }
+        if (o <= G) tcur[o] = carry + incl - v;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+      }
+    }
+    __syncthreads();
+    // tcnt becomes the run start inside the tile; tcur the fill cursor
+    for (int o = tid; o <= G; o += S2_THREADS) tcnt[o] = tcur[o];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < S2_PER; ++k) {
+      if (rec[k].x != 0xFFFFFFFFu) {
+        const int p2 = atomicAdd(&tcur[rec[k].x >> 16], 1);
+        sorted[p2] = rec[k];
+      }
+    }
+    __syncthreads();
+    const int valid = tcnt[G];
+    for (int j = tid; j < valid; j += S2_THREADS) {
+      const uint4 r = sorted[j];
+      const int o = static_cast<int>(r.x >> 16);
+      const int pos = tpos[o];
+      if (pos >= 0) A.rec[static_cast<int64_t>(o) * A.cap + pos + (j - tcnt[o])] = r;
+    }
+    __syncthreads();
+  }
+}
+
 struct AccArgs {
   int N, G, cells_per, ncells;
   float beta;
@@ -520,6 +647,12 @@ struct AccArgs {
   const uint4* rec;
   double* grid;
   unsigned* flags;
+  // mode 0: buckets from the exact partition (tot); 1: one-pass buckets (fill, cap),
+  // skipped when ovf is set; 2: exact buckets, run only when ovf is set
+  int mode;
+  const int* fill;
+  int cap;
+  const unsigned* ovf;
 };
 
 struct AccLayout {
@@ -558,7 +691,21 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
   int* head = reinterpret_cast<int*>(smem + L.head);
   int* ccount = reinterpret_cast<int*>(smem + L.ccount);
 
-  {
+  if (A.mode != 0) {
+    const bool ov = *reinterpret_cast<const volatile unsigned*>(A.ovf) != 0u;
+    if (ov != (A.mode == 2)) return;
+  }
+  if (A.mode == 1) {
+    if (tid == 0) {
+      s_base = b * A.cap;
+      s_count = min(__ldg(A.fill + b), A.cap);
+      s_ncarry = 0;
+      s_abort = 0;
+      mbar_init(&s_bar[0]);
+      mbar_init(&s_bar[1]);
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+  } else {
     // bucket of this owner = [sum of earlier totals, + tot[b]): one load per thread
     __shared__ int wsum[32];
     int v = 0;
@@ -593,6 +740,27 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
   for (int a = 0; a < W; ++a)
 #pragma unroll
     for (int c = 0; c < W; ++c) acc[a][c] = 0.f;
+  // the register window goes into the fp64 grid at the end, and also whenever FLUSH_PTS
+  // points have been added since the last flush, so that an fp32 running sum never
+  // spans more than that many points (crowded cells)
+  int since = 0;
+  auto flush = [&]() {
+    const int key = my_first_cell + cell;
+    const int64_t GN = static_cast<int64_t>(N) * N;
+    const int c0 = key / N;
+    const int c1 = key - c0 * N;
+    double* g = A.grid + (PAIR ? ch : 0) * GN;
+    const bool transposed = PAIR && ch == 1;
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        const int a = transposed ? j : i, bb = transposed ? i : j;
+        atomicAdd(g + static_cast<int64_t>((c0 + a) & (N - 1)) * N + ((c1 + bb) & (N - 1)),
+                  static_cast<double>(acc[i][j]));
+        acc[i][j] = 0.f;
+      }
+  };
 
   auto issue = [&](int r) {
     const int nr = min(CAPR, count - r * CAPR);
@@ -690,6 +858,13 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
         }
       }
     }
+    if (owns) {
+      since += min(mine, q);
+      if (since >= FLUSH_PTS) {
+        flush();
+        since = 0;
+      }
+    }
     __syncthreads();
     // deferred records go in front of the next buffer's TMA region
     const int nleft = (q == 0x7FFFFFFF) ? 0 : s_nleft;
@@ -710,21 +885,7 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
     __syncthreads();
   }
   // flush the register window into the fp64 grid
-  if (!owns) return;
-  const int key = my_first_cell + cell;
-  const int64_t GN = static_cast<int64_t>(N) * N;
-  const int c0 = key / N;
-  const int c1 = key - c0 * N;
-  double* g = A.grid + (PAIR ? ch : 0) * GN;
-  const bool transposed = PAIR && ch == 1;
-#pragma unroll
-  for (int i = 0; i < W; ++i)
-#pragma unroll
-    for (int j = 0; j < W; ++j) {
-      const int a = transposed ? j : i, bb = transposed ? i : j;
-      atomicAdd(g + static_cast<int64_t>((c0 + a) & (N - 1)) * N + ((c1 + bb) & (N - 1)),
-                static_cast<double>(acc[i][j]));
-    }
+  if (owns && since > 0) flush();
 }
 
 using KFn = void (*)(AccArgs);
@@ -804,23 +965,20 @@ fk_status spread_binned(const EsPlan& p, int64_t n, const float* x, const float*
   FK_TRY(scr.alloc(&P.cnt, static_cast<size_t>(P.nblk) * G));
   FK_TRY(scr.alloc(&P.off, static_cast<size_t>(P.nblk) * G));
   FK_TRY(scr.alloc(&P.tot, static_cast<size_t>(G)));
-  FK_TRY(scr.alloc(&P.rec, static_cast<size_t>(n) + static_cast<size_t>(P.nblk) * G * 7));  // + run padding
-
-  const size_t sm_count_k = sizeof(int) * P_NWARPS * G;
-  k_bin_count<<<P.nblk, P_THREADS, sm_count_k, st>>>(P); note_launch();
-  FK_CUDA(cudaGetLastError());
-  k_bin_scan<<<G, 256, 0, st>>>(P); note_launch();
-  FK_CUDA(cudaGetLastError());
-  if (P.vec_ok) {
-    const size_t sm2 = s2_layout(G).total;
-    FK_CUDA(cudaFuncSetAttribute(k_bin_scatter2, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm2)));
-    k_bin_scatter2<<<P.nblk, S2_THREADS, sm2, st>>>(P); note_launch();
-  } else {
-    const size_t sm_scatter = sizeof(uint4) * S_TILE + sizeof(unsigned short) * S_TILE + sizeof(int) * (3 * G + 2);
-    FK_CUDA(cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm_scatter)));
-    k_bin_scatter<<<P.nblk, S_THREADS, sm_scatter, st>>>(P); note_launch();
+  // one-pass bucket capacity: the mean load plus 2 % and 4096 records (a uniform
+  // sample's counts are within a few standard deviations, sqrt(n / G), of the mean)
+  const int64_t exact_len = n + static_cast<int64_t>(P.nblk) * G * 7;  // + run padding
+  const int64_t cap = ((n / G) + (n / G) / 50 + 4096 + 7) & ~static_cast<int64_t>(7);
+  const bool one_pass = P.vec_ok && cap * G < (static_cast<int64_t>(1) << 31);
+  FK_TRY(scr.alloc(&P.rec, static_cast<size_t>(one_pass ? std::max<int64_t>(exact_len, cap * G) : exact_len)));
+  unsigned* ovf = nullptr;
+  if (one_pass) {
+    FK_TRY(scr.alloc(&P.fill, static_cast<size_t>(G) + 1));
+    ovf = reinterpret_cast<unsigned*>(P.fill + G);
+    FK_CUDA(cudaMemsetAsync(P.fill, 0, sizeof(int) * (G + 1), st));
+    P.cap = static_cast<int>(cap);
+    P.ovf = ovf;
   }
-  FK_CUDA(cudaGetLastError());
 
   AccArgs A{};
   A.N = p.N;
@@ -833,15 +991,51 @@ fk_status spread_binned(const EsPlan& p, int64_t n, const float* x, const float*
   A.rec = P.rec;
   A.grid = grid;
   A.flags = flags;
+  A.fill = P.fill;
+  A.cap = P.cap;
+  A.ovf = ovf;
   const KFn fn = pair ? pick2d<true>(p.w) : pick2d<false>(p.w);
   if (!fn) return set_error(FK_EINVAL, "binned spreading: w = %d not built", p.w);
   const int threads = pair ? Cfg<true>::THREADS : Cfg<false>::THREADS;
   const size_t sm = acc_layout(cpc).total;
   FK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+  const size_t sm2 = s2_layout(G).total;
   KernelTimer* kt = kernel_timer();
-  if (kt->on) cudaEventRecord(kt->start, st);
+
+  if (one_pass) {
+    FK_CUDA(cudaFuncSetAttribute(k_bin_scatter1, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm2)));
+    k_bin_scatter1<<<P.nblk, S2_THREADS, sm2, st>>>(P); note_launch();
+    FK_CUDA(cudaGetLastError());
+    A.mode = 1;
+    if (kt->on) cudaEventRecord(kt->start, st);
+    fn<<<G, threads, sm, st>>>(A); note_launch();
+    if (kt->on) {
+      cudaEventRecord(kt->stop, st);
+      kt->recorded = true;
+    }
+    FK_CUDA(cudaGetLastError());
+    // exact partition, run only if a bucket overflowed (each kernel returns at once
+    // otherwise); no host round trip either way
+    P.guarded = 1;
+    A.mode = 2;
+  }
+  const size_t sm_count_k = sizeof(int) * P_NWARPS * G;
+  k_bin_count<<<P.nblk, P_THREADS, sm_count_k, st>>>(P); note_launch();
+  FK_CUDA(cudaGetLastError());
+  k_bin_scan<<<G, 256, 0, st>>>(P); note_launch();
+  FK_CUDA(cudaGetLastError());
+  if (P.vec_ok) {
+    FK_CUDA(cudaFuncSetAttribute(k_bin_scatter2, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm2)));
+    k_bin_scatter2<<<P.nblk, S2_THREADS, sm2, st>>>(P); note_launch();
+  } else {
+    const size_t sm_scatter = sizeof(uint4) * S_TILE + sizeof(unsigned short) * S_TILE + sizeof(int) * (3 * G + 2);
+    FK_CUDA(cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm_scatter)));
+    k_bin_scatter<<<P.nblk, S_THREADS, sm_scatter, st>>>(P); note_launch();
+  }
+  FK_CUDA(cudaGetLastError());
+  if (!one_pass && kt->on) cudaEventRecord(kt->start, st);
   fn<<<G, threads, sm, st>>>(A); note_launch();
-  if (kt->on) {
+  if (!one_pass && kt->on) {
     cudaEventRecord(kt->stop, st);
     kt->recorded = true;
   }

@@ -260,3 +260,20 @@ def test_binned_rejects_out_of_range_points():
         fk.fk_build_system(dev(x, torch.float32), dev(c, torch.float32), 4, 1e-6, "mixed",
                            opts=fk.default_opts(spread=fk.FK_SPREAD_BINNED))
     assert e.value.name == "FK_ERANGE"
+
+
+@pytest.mark.parametrize("n", [200_000, 1_000_003])
+def test_binned_spreader_clustered_points(n):
+    # points crowded into a few cells overflow the one-pass partition's buckets; the
+    # exact count-scan-scatter partition then takes over on the device
+    m, eps = 16, 1e-6
+    g = np.random.default_rng(99)
+    x = np.clip(g.normal(0.3, 0.02, size=(2, n)), -np.pi, np.pi - 1e-6).astype(np.float32)
+    x[:, : n // 10] = S.uniform_points(n // 10, 2, 33).astype(np.float32)  # and a uniform tenth
+    y = np.cos(x[0].astype(np.float64)).astype(np.float32)
+    T, b = fk.fk_build_system(dev(x, torch.float32), dev(y, torch.float32), m, eps, "mixed",
+                              opts=fk.default_opts(spread=fk.FK_SPREAD_BINNED))
+    To = O.moments(x.astype(np.float64), m)
+    bo = O.rhs(x.astype(np.float64), y.astype(np.float64), m)
+    assert rel(host(T), To) <= 10 * eps
+    assert rel(host(b)[0], bo) <= 10 * eps
