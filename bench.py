@@ -30,7 +30,7 @@ WL = dict(workload="2d-sobolev", d=2, n=100_000_000, m=32, s=2.0, lam=1e-6, eps=
 METRIC = "fit points/s (NUFFT Gram+RHS+solve)"
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
-ACC_DRAM_BYTES_PER_POINT = (323.824896e6 + 4.352e6) / 2e7  # k_bin_accumulate, 2-D, w = 7
+ACC_DRAM_BYTES_PER_POINT = (321.17632e6 + 3.851264e6) / 2e7  # k_bin_accumulate, 2-D, w = 7
 
 
 def parse():
@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=None, help="default: 100 (2d-sobolev), 3 (sweep-1d), 20 (others)")
     ap.add_argument("--warmup", type=int, default=None, help="default: 5 (2d-sobolev), 1 (sweep-1d), 3 (others)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=WL["n"], help="points (default: the workload's 1e8)")
+    ap.add_argument("--n", type=int, default=WL["n"],
+                    help="points (default: 1e8 for 2d-sobolev; sweep-1d: total points, default 1e10)")
     ap.add_argument("--spread", default="auto", choices=["auto", "atomic", "binned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -190,7 +191,8 @@ def run_row(args, rank, local):
     p32 = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     W = args.workload
     if W == "sweep-1d":
-        n_total, chunk, m, nt = 10_000_000_000, 1 << 28, 1000, 16
+        n_total = args.n if args.n != WL["n"] else 10_000_000_000
+        chunk, m, nt = min(1 << 28, (n_total + 3) // 4 * 4), 1000, 16
         lams = list(np.logspace(-12, -2, 256))
         x = torch.empty((1, chunk), dtype=torch.float32, device="cuda")
         y = torch.empty((nt, chunk), dtype=torch.float32, device="cuda")
@@ -372,7 +374,7 @@ def main():
     peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = f_pt * n / (ms_kernel / 1e3) / 1e12
     # DRAM bytes of one k_bin_accumulate launch: ncu capture of this kernel at n = 2e7
-    # (dram__bytes_read.sum 323.8 MB + dram__bytes_write.sum 4.35 MB), scaled by points
+    # (dram__bytes_read.sum 321.2 MB + dram__bytes_write.sum 3.85 MB), scaled by points
     # (the reads are the 16-byte partition records, the writes the grid flush)
     traffic = ACC_DRAM_BYTES_PER_POINT * n if (d == 2 and w == 7) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
