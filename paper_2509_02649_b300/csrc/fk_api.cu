@@ -125,18 +125,23 @@ struct Flags {
   }
 };
 
+// Stage timer of one call; its events are created once per host thread and reused.
 struct Timer {
   cudaStream_t st;
   bool on;
-  cudaEvent_t ev[8];
+  cudaEvent_t* ev;
   int n = 0;
-  Timer(cudaStream_t s, bool enabled) : st(s), on(enabled) {}
-  ~Timer() {
-    for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]);
+  Timer(cudaStream_t s, bool enabled) : st(s), on(enabled) {
+    static thread_local cudaEvent_t pool[8] = {};
+    static thread_local bool made = false;
+    if (on && !made) {
+      for (int i = 0; i < 8; ++i) cudaEventCreate(&pool[i]);
+      made = true;
+    }
+    ev = pool;
   }
   void mark() {
     if (!on || n >= 8) return;
-    cudaEventCreate(&ev[n]);
     cudaEventRecord(ev[n], st);
     ++n;
   }

@@ -423,8 +423,8 @@ __host__ __device__ inline S2Layout s2_layout(int G) {
   S2Layout L;
   L.stage = 0;                                             // float [3][S2_TILE]
   L.sorted = L.stage + sizeof(float) * 3 * S2_TILE;        // uint4 [S2_TILE]
-  L.ints = L.sorted + sizeof(uint4) * S2_TILE;             // int [3 (G + 1)]
-  L.bar = (L.ints + sizeof(int) * 3 * (G + 1) + 15) & ~static_cast<size_t>(15);
+  L.ints = L.sorted + sizeof(uint4) * S2_TILE;             // int [4 (G + 1)]
+  L.bar = (L.ints + sizeof(int) * 4 * (G + 1) + 15) & ~static_cast<size_t>(15);
   L.total = L.bar + 16;
   return L;
 }
@@ -539,8 +539,9 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter1(PartArgs A) {
   float* stage = reinterpret_cast<float*>(smem + L.stage);
   uint4* sorted = reinterpret_cast<uint4*>(smem + L.sorted);
   int* tpos = reinterpret_cast<int*>(smem + L.ints);  // [G + 1] reserved slot in the bucket, -1: none
-  int* tcnt = tpos + (G + 1);                          // [G + 1]
-  int* tcur = tcnt + (G + 1);                          // [G + 1]
+  int* tcnt = tpos + (G + 1);                          // [G + 1] counts of the tile
+  int* tcur = tcnt + (G + 1);                          // [G + 1] placement cursors
+  int* toff = tcur + (G + 1);                          // [G + 1] run starts inside the tile
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
   const int tid = threadIdx.x;
   const float inv_cpc = 1.0f / static_cast<float>(A.cells_per);
@@ -587,18 +588,13 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter1(PartArgs A) {
     }
     __syncthreads();
     if (tid == 0 && t0 + S2_TILE < e0) issue(t0 + S2_TILE);
-    // reservations in the buckets (one global atomic per owner present in the tile)
-    for (int o = tid; o < G; o += S2_THREADS) {
-      const int c = tcnt[o];
-      int pos = -1;
-      if (c > 0) {
-        pos = atomicAdd(A.fill + o, c);
-        if (pos + c > A.cap) {
-          atomicOr(A.ovf, 1u);
-          pos = -1;
-        }
-      }
-      tpos[o] = pos;
+    // reservations in the buckets, one global atomic per owner present in the tile;
+    // the returned slot is needed only for the copy-out, so the atomic's latency
+    // overlaps the scan and the placement
+    int my_c = 0, my_pos = -1;
+    if (tid < G) {
+      my_c = tcnt[tid];
+      if (my_c > 0) my_pos = atomicAdd(A.fill + tid, my_c);
     }
     if (tid >= S2_THREADS - 32) {  // exclusive scan of the tile counts (last warp)
       const int ln = tid - (S2_THREADS - 32);
@@ -612,13 +608,13 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter1(PartArgs A) {
           const int t = __shfl_up_sync(0xffffffffu, incl, dd);
           if (ln >= dd) incl += t;
         }
-        if (o <= G) tcur[o] = carry + incl - v;
+        if (o <= G) {
+          tcur[o] = carry + incl - v;
+          toff[o] = carry + incl - v;
+        }
         carry += __shfl_sync(0xffffffffu, incl, 31);
       }
     }
-    __syncthreads();
-    // tcnt becomes the run start inside the tile; tcur the fill cursor
-    for (int o = tid; o <= G; o += S2_THREADS) tcnt[o] = tcur[o];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < S2_PER; ++k) {
@@ -627,13 +623,20 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter1(PartArgs A) {
         sorted[p2] = rec[k];
       }
     }
+    if (tid < G) {
+      if (my_c > 0 && my_pos + my_c > A.cap) {
+        atomicOr(A.ovf, 1u);
+        my_pos = -1;
+      }
+      tpos[tid] = my_pos;
+    }
     __syncthreads();
-    const int valid = tcnt[G];
+    const int valid = toff[G];
     for (int j = tid; j < valid; j += S2_THREADS) {
       const uint4 r = sorted[j];
       const int o = static_cast<int>(r.x >> 16);
       const int pos = tpos[o];
-      if (pos >= 0) A.rec[static_cast<int64_t>(o) * A.cap + pos + (j - tcnt[o])] = r;
+      if (pos >= 0) A.rec[static_cast<int64_t>(o) * A.cap + pos + (j - toff[o])] = r;
     }
     __syncthreads();
   }
