@@ -114,28 +114,35 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
   EsPlan p2;
   FK_TRY(make_es_plan(2, m, eps, o.upsampfac, &p2));
   double *corr2, *grid2, *Bp;
-  R* pts;
+  R* pts = nullptr;
   FK_TRY(scr.alloc(&corr2, 2 * static_cast<size_t>(p2.kmax) + 1));
   FK_TRY(scr.alloc(&grid2, static_cast<size_t>(p2.N) * p2.N));
   FK_TRY(scr.alloc(&Bp, 2 * static_cast<size_t>(npairs > 0 ? npairs : 1) * K * K));
-  FK_TRY(scr.alloc(&pts, 2 * static_cast<size_t>(n)));
+  // mixed path: the partition reads X_l1 and X_l2 in place; otherwise the pair's
+  // points are gathered into (X_l1, -X_l2) rows first
+  const bool binned2 = precision == FK_MIXED && o.spread != FK_SPREAD_ATOMIC && spread_binned_supported(p2, 0, true);
+  if (!binned2) FK_TRY(scr.alloc(&pts, 2 * static_cast<size_t>(n)));
   FK_TRY(es_correction(p2, corr2, st));
   int pair = 0;
   for (int l1 = 0; l1 < d; ++l1)
     for (int l2 = l1 + 1; l2 < d; ++l2, ++pair) {
       Scratch inner(st);  // released (stream-ordered) after each pair
-      k_pair_points<R><<<grid_for(n, 256), 256, 0, st>>>(n, x, l1, l2, pts); note_launch();
-      FK_CUDA(cudaGetLastError());
+      if (!binned2) {
+        k_pair_points<R><<<grid_for(n, 256), 256, 0, st>>>(n, x, l1, l2, pts); note_launch();
+        FK_CUDA(cudaGetLastError());
+      }
       double* blk = Bp + 2 * static_cast<int64_t>(pair) * K * K;
       if (precision == FK_FP64) {
         FK_TRY(spread_atomic<double>(p2, n, reinterpret_cast<const double*>(pts), nullptr, 0, true, grid2, flags, st));
         FK_TRY(grid_to_modes<double>(p2, grid2, 0, 1, m, corr2, inv_n, blk, st, inner));
+      } else if (binned2) {
+        const float* xf = reinterpret_cast<const float*>(x);
+        FK_TRY(spread_binned_xy(p2, n, xf + static_cast<int64_t>(l1) * n, xf + static_cast<int64_t>(l2) * n, -1.0f,
+                                nullptr, 0, true, grid2, flags, st, inner));
+        FK_TRY(grid_to_modes<float>(p2, grid2, 0, 1, m, corr2, inv_n, blk, st, inner));
       } else {
         const float* fp = reinterpret_cast<const float*>(pts);
-        if (o.spread != FK_SPREAD_ATOMIC && spread_binned_supported(p2, 0, true))
-          FK_TRY(spread_binned(p2, n, fp, nullptr, 0, true, grid2, flags, st, inner));
-        else
-          FK_TRY(spread_atomic<float>(p2, n, fp, nullptr, 0, true, grid2, flags, st));
+        FK_TRY(spread_atomic<float>(p2, n, fp, nullptr, 0, true, grid2, flags, st));
         FK_TRY(grid_to_modes<float>(p2, grid2, 0, 1, m, corr2, inv_n, blk, st, inner));
       }
     }

@@ -142,6 +142,10 @@ fk_status spread_binned(const EsPlan& p, int64_t n, const float* x, const float*
                         bool with_ones, double* grid, unsigned* flags, cudaStream_t st,
                         Scratch& scratch);
 bool spread_binned_supported(const EsPlan& p, int n_y, bool with_ones);
+// As spread_binned with the two coordinates as separate rows, the second taken times s1.
+fk_status spread_binned_xy(const EsPlan& p, int64_t n, const float* x0, const float* x1, float s1, const float* y,
+                           int n_y, bool with_ones, double* grid, unsigned* flags, cudaStream_t st,
+                           Scratch& scratch);
 
 // 1-D fixed-point shared-memory spreading (fp32 inputs, any channel count).  y_absmax:
 // device array of max|y_c| bit patterns for the n_y strength channels, or null to

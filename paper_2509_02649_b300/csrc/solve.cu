@@ -294,6 +294,108 @@ __global__ void k_trisolve(const double* L, int64_t D, double* X, int n_rhs) {
 }
 
 // R = B - A X  (dense Hermitian A given by T, W) for refinement; one CTA per (rhs, row block)
+// Blocked triangular solves L L^H x = b for one right-hand side per CTA (blockIdx.x):
+// the vector lives in shared memory; each 32 x 32 diagonal block is staged in shared
+// memory and solved by one warp; the off-diagonal updates give every thread one row
+// (forward) or one column (backward) and 32 independent loads.  L: row-major complex
+// lower triangle (the Cholesky factor), X: B on entry, solution on exit.
+constexpr int TS_NB = 32;
+constexpr int TS_THREADS = 512;
+
+__global__ void __launch_bounds__(TS_THREADS) k_trisolve_blk(const double* __restrict__ L, int D, double* X) {
+  extern __shared__ __align__(16) unsigned char smem_ts[];
+  cd* ys = reinterpret_cast<cd*>(smem_ts);               // [D]
+  cd* dg = ys + D;                                       // [TS_NB][TS_NB + 1]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* xs = X + 2 * static_cast<int64_t>(blockIdx.x) * D;
+  for (int i = tid; i < D; i += TS_THREADS) ys[i] = cd{xs[2 * i], xs[2 * i + 1]};
+  auto Lat = [&](int r, int c) { return cd{__ldg(L + 2 * (static_cast<int64_t>(r) * D + c)),
+                                           __ldg(L + 2 * (static_cast<int64_t>(r) * D + c) + 1)}; };
+  auto stage_diag = [&](int kb, int nb) {
+    for (int t = tid; t < TS_NB * TS_NB; t += TS_THREADS) {
+      const int r = t / TS_NB, c = t - r * TS_NB;
+      dg[r * (TS_NB + 1) + c] = (r < nb && c <= r) ? Lat(kb + r, kb + c) : cd{0, 0};
+    }
+  };
+  __syncthreads();
+  // forward: L y = b
+  for (int kb = 0; kb < D; kb += TS_NB) {
+    const int nb = min(TS_NB, D - kb);
+    stage_diag(kb, nb);
+    __syncthreads();
+    if (warp == 0) {
+      for (int i = 0; i < nb; ++i) {
+        cd t = (lane < i) ? cmul(dg[i * (TS_NB + 1) + lane], ys[kb + lane]) : cd{0, 0};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+          t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+        }
+        if (lane == 0) {
+          const double lii = dg[i * (TS_NB + 1) + i].x;
+          ys[kb + i] = cd{(ys[kb + i].x - t.x) / lii, (ys[kb + i].y - t.y) / lii};
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int r = kb + nb + tid; r < D; r += TS_THREADS) {
+      cd acc = cd{0, 0};
+#pragma unroll 8
+      for (int j = 0; j < nb; ++j) acc = cadd(acc, cmul(Lat(r, kb + j), ys[kb + j]));
+      ys[r] = cd{ys[r].x - acc.x, ys[r].y - acc.y};
+    }
+    __syncthreads();
+  }
+  // backward: L^H x = y
+  const int nblocks = (D + TS_NB - 1) / TS_NB;
+  for (int bi = nblocks - 1; bi >= 0; --bi) {
+    const int kb = bi * TS_NB, nb = min(TS_NB, D - kb);
+    stage_diag(kb, nb);
+    __syncthreads();
+    if (warp == 0) {
+      for (int i = nb - 1; i >= 0; --i) {
+        // x_i = (y_i - sum_{j > i} conj(L[j][i]) x_j) / L[i][i]
+        cd t = (lane > i && lane < nb) ? cconjmul(dg[lane * (TS_NB + 1) + i], ys[kb + lane]) : cd{0, 0};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+          t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+        }
+        if (lane == 0) {
+          const double lii = dg[i * (TS_NB + 1) + i].x;
+          ys[kb + i] = cd{(ys[kb + i].x - t.x) / lii, (ys[kb + i].y - t.y) / lii};
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int c = tid; c < kb; c += TS_THREADS) {
+      cd acc = cd{0, 0};
+#pragma unroll 8
+      for (int j = 0; j < nb; ++j) acc = cadd(acc, cconjmul(Lat(kb + j, c), ys[kb + j]));
+      ys[c] = cd{ys[c].x - acc.x, ys[c].y - acc.y};
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < D; i += TS_THREADS) {
+    xs[2 * i] = ys[i].x;
+    xs[2 * i + 1] = ys[i].y;
+  }
+}
+
+static fk_status trisolve(const double* L, int64_t D, double* X, int n_rhs, cudaStream_t st) {
+  const size_t smem = sizeof(cd) * (static_cast<size_t>(D) + TS_NB * (TS_NB + 1));
+  if (smem <= 200 * 1024) {
+    FK_CUDA(cudaFuncSetAttribute(k_trisolve_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    k_trisolve_blk<<<n_rhs, TS_THREADS, smem, st>>>(L, static_cast<int>(D), X); note_launch();
+  } else {
+    k_trisolve<<<(n_rhs + RB - 1) / RB, 256, 0, st>>>(L, D, X, n_rhs); note_launch();
+  }
+  FK_CUDA(cudaGetLastError());
+  return FK_OK;
+}
+
 __global__ void k_residual_dense(int d, int m, const double* T, const double* W, const double* X,
                                  const double* B, double* R, int n_rhs) {
   const int K = 2 * m + 1, K2 = 4 * m + 1;
@@ -1047,11 +1149,11 @@ fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, 
     FK_CUDA(cudaGetLastError());
     FK_TRY(cholesky(A, D, flags, st));
     FK_CUDA(cudaMemcpyAsync(X, rhs, sizeof(double) * 2 * D * n_rhs, cudaMemcpyDeviceToDevice, st));
-    k_trisolve<<<(n_rhs + RB - 1) / RB, 256, 0, st>>>(A, D, X, n_rhs); note_launch();
+    FK_TRY(trisolve(A, D, X, n_rhs, st));
     FK_CUDA(cudaGetLastError());
     for (int it = 0; it < o.refine_steps; ++it) {
       k_residual_dense<<<grid_for(D * n_rhs, 128), 128, 0, st>>>(d, m, T, Wl, X, rhs, R, n_rhs); note_launch();
-      k_trisolve<<<(n_rhs + RB - 1) / RB, 256, 0, st>>>(A, D, R, n_rhs); note_launch();
+      FK_TRY(trisolve(A, D, R, n_rhs, st));
       k_axpy_c<<<grid_for(2 * D * n_rhs, 256), 256, 0, st>>>(2 * D * n_rhs, R, X); note_launch();
       FK_CUDA(cudaGetLastError());
     }
@@ -1090,11 +1192,11 @@ fk_status solve_dense(const double* A, int64_t D, double* X, int n_rhs, int refi
   FK_CUDA(cudaMemcpyAsync(L, A, sizeof(double) * 2 * D * D, cudaMemcpyDeviceToDevice, st));
   FK_CUDA(cudaMemcpyAsync(B, X, sizeof(double) * 2 * D * n_rhs, cudaMemcpyDeviceToDevice, st));
   FK_TRY(cholesky(L, D, flags, st));
-  k_trisolve<<<(n_rhs + RB - 1) / RB, 256, 0, st>>>(L, D, X, n_rhs); note_launch();
+  FK_TRY(trisolve(L, D, X, n_rhs, st));
   FK_CUDA(cudaGetLastError());
   for (int it = 0; it < refine; ++it) {
     k_dense_residual<<<grid_for(D * n_rhs, 128), 128, 0, st>>>(A, D, X, B, R, n_rhs); note_launch();
-    k_trisolve<<<(n_rhs + RB - 1) / RB, 256, 0, st>>>(L, D, R, n_rhs); note_launch();
+    FK_TRY(trisolve(L, D, R, n_rhs, st));
     k_axpy_c<<<grid_for(2 * D * n_rhs, 256), 256, 0, st>>>(2 * D * n_rhs, R, X); note_launch();
     FK_CUDA(cudaGetLastError());
   }

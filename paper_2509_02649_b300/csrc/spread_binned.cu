@@ -170,7 +170,9 @@ struct Cfg {
 struct PartArgs {
   int N, W, G, cells_per;
   int64_t n;
-  const float* x;
+  const float* x;    // first coordinate (row)
+  const float* x1;   // second coordinate (row), taken times s1 (the additive model's
+  float s1;          // pair transforms use (X_l1, -X_l2))
   const float* y;
   int has_y;
   int vec_ok;       // x (both rows) and y 16-byte aligned: float4 loads
@@ -201,7 +203,7 @@ __device__ __forceinline__ bool point_key(float x0, float x1, const PartArgs& A,
                                           uint32_t* packed) {
   int la, lb;
   if (!window_f32(x0, A.N, A.c_hi, A.c_lo, A.W, &la, f0)) return false;
-  if (!window_f32(x1, A.N, A.c_hi, A.c_lo, A.W, &lb, f1)) return false;
+  if (!window_f32(A.s1 * x1, A.N, A.c_hi, A.c_lo, A.W, &lb, f1)) return false;
   const int N = A.N;
   const int key = wrap_node(la, N) * N + wrap_node(lb, N);
   int o = __float2int_rd(static_cast<float>(key) * inv_cpc);
@@ -233,17 +235,17 @@ __global__ void __launch_bounds__(P_THREADS) k_bin_count(PartArgs A) {
     for (int64_t i = s + 4 * tid; i < e; i += 4 * P_THREADS) {
       if (i + 3 < e) {
         const float4 a = __ldg(reinterpret_cast<const float4*>(A.x + i));
-        const float4 c = __ldg(reinterpret_cast<const float4*>(A.x + A.n + i));
+        const float4 c = __ldg(reinterpret_cast<const float4*>(A.x1 + i));
         one(a.x, c.x);
         one(a.y, c.y);
         one(a.z, c.z);
         one(a.w, c.w);
       } else {
-        for (int64_t j = i; j < e; ++j) one(__ldg(A.x + j), __ldg(A.x + A.n + j));
+        for (int64_t j = i; j < e; ++j) one(__ldg(A.x + j), __ldg(A.x1 + j));
       }
     }
   } else {
-    for (int64_t i = s + tid; i < e; i += P_THREADS) one(__ldg(A.x + i), __ldg(A.x + A.n + i));
+    for (int64_t i = s + tid; i < e; i += P_THREADS) one(__ldg(A.x + i), __ldg(A.x1 + i));
   }
   __syncthreads();
   for (int o = tid; o < G; o += P_THREADS) {
@@ -346,17 +348,17 @@ __global__ void __launch_bounds__(S_THREADS, 1) k_bin_scatter(PartArgs A) {
       for (int i = 4 * tid; i < cnt; i += 4 * S_THREADS) {
         if (i + 3 < cnt) {
           const float4 a = __ldg(reinterpret_cast<const float4*>(A.x + t0 + i));
-          const float4 c = __ldg(reinterpret_cast<const float4*>(A.x + A.n + t0 + i));
+          const float4 c = __ldg(reinterpret_cast<const float4*>(A.x1 + t0 + i));
           own_of(i, a.x, c.x);
           own_of(i + 1, a.y, c.y);
           own_of(i + 2, a.z, c.z);
           own_of(i + 3, a.w, c.w);
         } else {
-          for (int j = i; j < cnt; ++j) own_of(j, __ldg(A.x + t0 + j), __ldg(A.x + A.n + t0 + j));
+          for (int j = i; j < cnt; ++j) own_of(j, __ldg(A.x + t0 + j), __ldg(A.x1 + t0 + j));
         }
       }
     } else {
-      for (int i = tid; i < cnt; i += S_THREADS) own_of(i, __ldg(A.x + t0 + i), __ldg(A.x + A.n + t0 + i));
+      for (int i = tid; i < cnt; i += S_THREADS) own_of(i, __ldg(A.x + t0 + i), __ldg(A.x1 + t0 + i));
     }
     __syncthreads();
     if (tid < 32) {  // exclusive scan of the tile counts (one warp)
@@ -383,7 +385,7 @@ __global__ void __launch_bounds__(S_THREADS, 1) k_bin_scatter(PartArgs A) {
       if (o == 0xFFFF) continue;
       float f0, f1;
       uint32_t k;
-      point_key(__ldg(A.x + t0 + i), __ldg(A.x + A.n + t0 + i), A, inv_cpc, &f0, &f1, &k);
+      point_key(__ldg(A.x + t0 + i), __ldg(A.x1 + t0 + i), A, inv_cpc, &f0, &f1, &k);
       const int pos = atomicAdd(&tcur[o], 1);
       sorted[pos] = make_uint4(k, __float_as_uint(f0), __float_as_uint(f1),
                                A.has_y ? __float_as_uint(__ldg(A.y + t0 + i)) : 0u);
@@ -458,7 +460,7 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter2(PartArgs A) {
     fence_proxy_async();
     mbar_arrive_expect(bar, bytes * (A.has_y ? 3u : 2u));
     bulk_g2s(stage, A.x + t0, bytes, bar);
-    bulk_g2s(stage + S2_TILE, A.x + A.n + t0, bytes, bar);
+    bulk_g2s(stage + S2_TILE, A.x1 + t0, bytes, bar);
     if (A.has_y) bulk_g2s(stage + 2 * S2_TILE, A.y + t0, bytes, bar);
   };
   if (tid == 0 && s0 < e0) issue(s0);
@@ -558,7 +560,7 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter1(PartArgs A) {
     fence_proxy_async();
     mbar_arrive_expect(bar, bytes * (A.has_y ? 3u : 2u));
     bulk_g2s(stage, A.x + t0, bytes, bar);
-    bulk_g2s(stage + S2_TILE, A.x + A.n + t0, bytes, bar);
+    bulk_g2s(stage + S2_TILE, A.x1 + t0, bytes, bar);
     if (A.has_y) bulk_g2s(stage + 2 * S2_TILE, A.y + t0, bytes, bar);
   };
   if (tid == 0 && s0 < e0) issue(s0);
@@ -934,6 +936,11 @@ bool spread_binned_supported(const EsPlan& p, int n_y, bool with_ones) {
 
 fk_status spread_binned(const EsPlan& p, int64_t n, const float* x, const float* y, int n_y, bool with_ones,
                         double* grid, unsigned* flags, cudaStream_t st, Scratch& scr) {
+  return spread_binned_xy(p, n, x, x + n, 1.0f, y, n_y, with_ones, grid, flags, st, scr);
+}
+
+fk_status spread_binned_xy(const EsPlan& p, int64_t n, const float* x, const float* x1, float s1, const float* y,
+                           int n_y, bool with_ones, double* grid, unsigned* flags, cudaStream_t st, Scratch& scr) {
   if (!spread_binned_supported(p, n_y, with_ones)) return set_error(FK_EINVAL, "binned spreading: unsupported shape");
   if (n >= (static_cast<int64_t>(1) << 31)) return set_error(FK_EINVAL, "binned spreading: n >= 2^31 per call");
   const int nch = n_y + (with_ones ? 1 : 0);
@@ -953,12 +960,15 @@ fk_status spread_binned(const EsPlan& p, int64_t n, const float* x, const float*
   P.cells_per = cpc;
   P.n = n;
   P.x = x;
+  P.x1 = x1;
+  P.s1 = s1;
   P.y = y;
   P.has_y = n_y > 0 ? 1 : 0;
   // one partition block per SM; count and scatter use the same block ranges
   P.nblk = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + P_TILE - 1) / P_TILE, sm_count())));
   P.range = ((n + P.nblk - 1) / P.nblk + 3) & ~static_cast<int64_t>(3);
-  P.vec_ok = ((reinterpret_cast<uintptr_t>(x) & 15) == 0 && (n & 3) == 0 &&
+  P.vec_ok = ((reinterpret_cast<uintptr_t>(x) & 15) == 0 && (reinterpret_cast<uintptr_t>(x1) & 15) == 0 &&
+              (n & 3) == 0 &&
               (n_y == 0 || (reinterpret_cast<uintptr_t>(y) & 15) == 0))
                  ? 1
                  : 0;
