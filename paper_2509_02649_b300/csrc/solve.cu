@@ -125,7 +125,7 @@ __global__ void k_assemble(int d, int m, const double* T, const double* W, doubl
 // ---------------------------------------------------------------- Cholesky
 constexpr int NB = 32;
 
-__global__ void k_chol_diag(double* A, int64_t D, int kb, int nb, unsigned* flags) {
+__global__ void k_chol_diag(double* A, int64_t D, int kb, int nb, unsigned* flags, double* Linv) {
   __shared__ cd s[NB][NB + 1];
   const int tid = threadIdx.x;
   for (int t = tid; t < nb * nb; t += blockDim.x) {
@@ -162,6 +162,34 @@ __global__ void k_chol_diag(double* A, int64_t D, int kb, int nb, unsigned* flag
     } else {
       p[0] = 0.0;
       p[1] = 0.0;
+    }
+  }
+  if (Linv) {
+    // inverse of the lower-triangular block by forward substitution L v = e_c, for the
+    // panel update as a product: 8 threads per column c share each step's inner sum
+    // (FP64 work spread over the whole CTA; this part's FP64 rate is low per warp)
+    __shared__ cd v[NB][NB + 1];
+    const int c = tid >> 3, sub = tid & 7;
+    for (int i = 0; i < nb; ++i) {
+      cd acc = cd{0.0, 0.0};
+      if (c < nb)
+        for (int p = c + sub; p < i; p += 8) acc = cadd(acc, cmul(s[i][p], v[p][c]));
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      if (c < nb && sub == 0) {
+        const cd rhs = (i == c) ? cd{1.0, 0.0} : cd{0.0, 0.0};
+        v[i][c] = (i < c) ? cd{0.0, 0.0} : cscale(csub(rhs, acc), 1.0 / s[i][i].x);
+      }
+      __syncthreads();
+    }
+    for (int t = tid; t < NB * NB; t += blockDim.x) {
+      const int i = t / NB, j = t % NB;
+      const cd val = (i < nb && j < nb) ? v[i][j] : cd{0.0, 0.0};
+      Linv[2 * t] = val.x;
+      Linv[2 * t + 1] = val.y;
     }
   }
 }
@@ -216,13 +244,45 @@ __global__ void k_chol_update(double* A, int64_t D, int kb, int nb) {
   }
 }
 
-static fk_status cholesky(double* A, int64_t D, unsigned* flags, cudaStream_t st) {
+// panel rows i >= kb + nb: L21 = A21 (L11^{-1})^H, i.e. x_j = sum_p a_p conj(Linv[j][p]);
+// one CTA per 32 rows, the 32 x 32 inverse and the row tile in shared memory
+constexpr int PANEL_ROWS = 8;  // rows per CTA: spreads the FP64 work over more SMs
+__global__ void k_chol_panel_mm(double* A, int64_t D, int kb, int nb, const double* Linv) {
+  __shared__ cd Li[NB][NB + 1], At[PANEL_ROWS][NB + 1];
+  const int64_t r0 = kb + nb + static_cast<int64_t>(blockIdx.x) * PANEL_ROWS;
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+    const int i = t / NB, j = t % NB;
+    Li[i][j] = cd{Linv[2 * t], Linv[2 * t + 1]};
+  }
+  for (int t = threadIdx.x; t < PANEL_ROWS * NB; t += blockDim.x) {
+    const int i = t / NB, j = t % NB;
+    const int64_t row = r0 + i;
+    At[i][j] = (row < D && j < nb) ? cd{A[2 * (row * D + kb + j)], A[2 * (row * D + kb + j) + 1]} : cd{0, 0};
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < PANEL_ROWS * NB; t += blockDim.x) {
+    const int r = t / NB, j = t % NB;
+    const int64_t row = r0 + r;
+    if (row >= D || j >= nb) continue;
+    cd acc = cd{0, 0};
+    for (int p = 0; p <= j; ++p) acc = cadd(acc, cmul(At[r][p], cconj(Li[j][p])));
+    A[2 * (row * D + kb + j)] = acc.x;
+    A[2 * (row * D + kb + j) + 1] = acc.y;
+  }
+}
+
+static fk_status cholesky(double* A, int64_t D, unsigned* flags, cudaStream_t st, double* linv) {
   for (int kb = 0; kb < D; kb += NB) {
     const int nb = static_cast<int>(std::min<int64_t>(NB, D - kb));
-    k_chol_diag<<<1, 256, 0, st>>>(A, D, kb, nb, flags); note_launch();
     const int64_t rest = D - kb - nb;
+    k_chol_diag<<<1, 256, 0, st>>>(A, D, kb, nb, flags, (rest > 0 && linv) ? linv : nullptr); note_launch();
     if (rest > 0) {
-      k_chol_panel<<<static_cast<int>((rest + 127) / 128), 128, 0, st>>>(A, D, kb, nb); note_launch();
+      if (linv) {
+        k_chol_panel_mm<<<static_cast<int>((rest + PANEL_ROWS - 1) / PANEL_ROWS), 256, 0, st>>>(A, D, kb, nb, linv);
+        note_launch();
+      } else {
+        k_chol_panel<<<static_cast<int>((rest + 127) / 128), 128, 0, st>>>(A, D, kb, nb); note_launch();
+      }
       const int nt = static_cast<int>((rest + 31) / 32);
       k_chol_update<<<dim3(nt, nt), 256, 0, st>>>(A, D, kb, nb); note_launch();
     }
@@ -384,7 +444,18 @@ __global__ void __launch_bounds__(TS_THREADS) k_trisolve_blk(const double* __res
   }
 }
 
-static fk_status trisolve(const double* L, int64_t D, double* X, int n_rhs, cudaStream_t st) {
+fk_status trisolve_coop(const double* L, int64_t D, double* X, int n_rhs, cudaStream_t st, Scratch& scr,
+                        unsigned* flags, bool* handled);
+
+// The cooperative form spreads the FP64 updates over every SM (this part's FP64 rate
+// makes one SM the bottleneck at D ~ 1000); the one-CTA blocked form is the fallback.
+static fk_status trisolve(const double* L, int64_t D, double* X, int n_rhs, cudaStream_t st, Scratch* scr = nullptr,
+                          unsigned* flags = nullptr) {
+  if (scr && flags) {
+    bool handled = false;
+    FK_TRY(trisolve_coop(L, D, X, n_rhs, st, *scr, flags, &handled));
+    if (handled) return FK_OK;
+  }
   const size_t smem = sizeof(cd) * (static_cast<size_t>(D) + TS_NB * (TS_NB + 1));
   if (smem <= 200 * 1024) {
     FK_CUDA(cudaFuncSetAttribute(k_trisolve_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
@@ -1147,13 +1218,15 @@ fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, 
     double* X = sol + 2 * static_cast<int64_t>(l) * n_rhs * D;
     k_assemble<<<grid_for(D * D, 256), 256, 0, st>>>(d, m, T, Wl, A); note_launch();
     FK_CUDA(cudaGetLastError());
-    FK_TRY(cholesky(A, D, flags, st));
+    double* linv;
+    FK_TRY(scratch.alloc(&linv, 2 * NB * NB));
+    FK_TRY(cholesky(A, D, flags, st, linv));
     FK_CUDA(cudaMemcpyAsync(X, rhs, sizeof(double) * 2 * D * n_rhs, cudaMemcpyDeviceToDevice, st));
-    FK_TRY(trisolve(A, D, X, n_rhs, st));
+    FK_TRY(trisolve(A, D, X, n_rhs, st, &scratch, flags));
     FK_CUDA(cudaGetLastError());
     for (int it = 0; it < o.refine_steps; ++it) {
       k_residual_dense<<<grid_for(D * n_rhs, 128), 128, 0, st>>>(d, m, T, Wl, X, rhs, R, n_rhs); note_launch();
-      FK_TRY(trisolve(A, D, R, n_rhs, st));
+      FK_TRY(trisolve(A, D, R, n_rhs, st, &scratch, flags));
       k_axpy_c<<<grid_for(2 * D * n_rhs, 256), 256, 0, st>>>(2 * D * n_rhs, R, X); note_launch();
       FK_CUDA(cudaGetLastError());
     }
@@ -1191,12 +1264,14 @@ fk_status solve_dense(const double* A, int64_t D, double* X, int n_rhs, int refi
   FK_TRY(scr.alloc(&R, 2 * D * n_rhs));
   FK_CUDA(cudaMemcpyAsync(L, A, sizeof(double) * 2 * D * D, cudaMemcpyDeviceToDevice, st));
   FK_CUDA(cudaMemcpyAsync(B, X, sizeof(double) * 2 * D * n_rhs, cudaMemcpyDeviceToDevice, st));
-  FK_TRY(cholesky(L, D, flags, st));
-  FK_TRY(trisolve(L, D, X, n_rhs, st));
+  double* linv;
+  FK_TRY(scr.alloc(&linv, 2 * NB * NB));
+  FK_TRY(cholesky(L, D, flags, st, linv));
+  FK_TRY(trisolve(L, D, X, n_rhs, st, &scr, flags));
   FK_CUDA(cudaGetLastError());
   for (int it = 0; it < refine; ++it) {
     k_dense_residual<<<grid_for(D * n_rhs, 128), 128, 0, st>>>(A, D, X, B, R, n_rhs); note_launch();
-    FK_TRY(trisolve(L, D, R, n_rhs, st));
+    FK_TRY(trisolve(L, D, R, n_rhs, st, &scr, flags));
     k_axpy_c<<<grid_for(2 * D * n_rhs, 256), 256, 0, st>>>(2 * D * n_rhs, R, X); note_launch();
     FK_CUDA(cudaGetLastError());
   }
@@ -1633,6 +1708,156 @@ fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, 
   if (iters_out) *iters_out = info[0];
   if (relres_out) *relres_out = worst;
   if (info[1] != 0) return set_error(FK_ENOCONV, "CG did not converge in %d iterations", o.cg_maxit);
+  return FK_OK;
+}
+
+}  // namespace fk
+
+namespace fk {
+namespace {
+
+// Triangular solves L L^H x = b for one right-hand side in one cooperative launch.
+// Forward: per 32-row block k, CTA 0 solves the diagonal block (its rows already
+// carry every earlier block's update), then after one grid barrier all CTAs subtract
+// block k's contribution from the rows below, CTA 0 taking block k + 1's rows first
+// so that it can solve that block while the others update the rest.  Backward is the
+// same on columns with conj(L)^T.  Updates of one row from different blocks are
+// separated by barriers; within a phase each row has one writer.
+struct TsP {
+  const double* L;
+  int D;
+  double* x;      // [D] complex, b in / solution out
+  GridBar* bar;
+  unsigned* flags;
+};
+
+// all threads of CTA 0: stage the diagonal block (independent loads in flight)
+__device__ void ts_stage(const TsP& A, int kb, int nb, cd* dg) {
+  for (int t = threadIdx.x; t < TS_NB * TS_NB; t += blockDim.x) {
+    const int r = t / TS_NB, c = t - r * TS_NB;
+    dg[r * (TS_NB + 1) + c] = (r < nb && c <= r)
+        ? cd{__ldg(A.L + 2 * (static_cast<int64_t>(kb + r) * A.D + kb + c)),
+             __ldg(A.L + 2 * (static_cast<int64_t>(kb + r) * A.D + kb + c) + 1)}
+        : cd{0, 0};
+  }
+}
+
+// one warp of CTA 0, after ts_stage and a CTA barrier
+__device__ void ts_diag(const TsP& A, int kb, int nb, bool fwd, cd* dg) {
+  const int lane = threadIdx.x & 31;
+  cd yv = (lane < nb) ? cd{__ldcg(A.x + 2 * (kb + lane)), __ldcg(A.x + 2 * (kb + lane) + 1)} : cd{0, 0};
+  for (int s = 0; s < nb; ++s) {
+    const int i = fwd ? s : nb - 1 - s;
+    cd t = cd{0, 0};
+    if (fwd && lane < i) t = cmul(dg[i * (TS_NB + 1) + lane], yv);
+    if (!fwd && lane > i && lane < nb) t = cconjmul(dg[lane * (TS_NB + 1) + i], yv);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+      t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+    }
+    if (lane == i) {
+      const double inv = 1.0 / dg[i * (TS_NB + 1) + i].x;
+      yv = cd{(yv.x - t.x) * inv, (yv.y - t.y) * inv};
+    }
+    __syncwarp();
+  }
+  if (lane < nb) {
+    A.x[2 * (kb + lane)] = yv.x;
+    A.x[2 * (kb + lane) + 1] = yv.y;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_trisolve_coop(TsP A) {
+  __shared__ cd dg[TS_NB * (TS_NB + 1)];
+  __shared__ cd yb[TS_NB];
+  const int D = A.D;
+  const int nblocks = (D + TS_NB - 1) / TS_NB;
+  const int64_t gth = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool fwd = (pass == 0);
+    // first diagonal block of the pass
+    if (blockIdx.x == 0) {
+      const int kb0 = fwd ? 0 : (nblocks - 1) * TS_NB, nb0 = fwd ? min(TS_NB, D) : D - (nblocks - 1) * TS_NB;
+      ts_stage(A, kb0, nb0, dg);
+      __syncthreads();
+      if (threadIdx.x < 32) ts_diag(A, kb0, nb0, fwd, dg);
+    }
+    if (!grid_sync(A.bar, A.flags)) return;
+    for (int s = 0; s < nblocks; ++s) {
+      const int bi = fwd ? s : nblocks - 1 - s;
+      const int kb = bi * TS_NB, nb = min(TS_NB, D - kb);
+      for (int j = threadIdx.x; j < nb; j += blockDim.x)
+        yb[j] = cd{__ldcg(A.x + 2 * (kb + j)), __ldcg(A.x + 2 * (kb + j) + 1)};
+      __syncthreads();
+      // rows (forward) or columns (backward) still to update: [lo, hi)
+      const int lo = fwd ? kb + nb : 0, hi = fwd ? D : kb;
+      const bool has_next = fwd ? (s + 1 < nblocks) : (bi > 0);
+      const int nkb = fwd ? kb + nb : kb - TS_NB;  // next block start
+      const int nnb = has_next ? min(TS_NB, D - nkb) : 0;
+      auto update = [&](int r) {
+        cd acc = cd{0, 0};
+        if (fwd) {
+#pragma unroll 8
+          for (int j = 0; j < nb; ++j)
+            acc = cadd(acc, cmul(cd{__ldg(A.L + 2 * (static_cast<int64_t>(r) * D + kb + j)),
+                                    __ldg(A.L + 2 * (static_cast<int64_t>(r) * D + kb + j) + 1)}, yb[j]));
+        } else {
+#pragma unroll 8
+          for (int j = 0; j < nb; ++j)
+            acc = cadd(acc, cconjmul(cd{__ldg(A.L + 2 * (static_cast<int64_t>(kb + j) * D + r)),
+                                        __ldg(A.L + 2 * (static_cast<int64_t>(kb + j) * D + r) + 1)}, yb[j]));
+        }
+        A.x[2 * r] = __ldcg(A.x + 2 * r) - acc.x;
+        A.x[2 * r + 1] = __ldcg(A.x + 2 * r + 1) - acc.y;
+      };
+      if (blockIdx.x == 0) {
+        // the next block's rows, then its diagonal solve
+        if (has_next) {
+          ts_stage(A, nkb, nnb, dg);
+          for (int r = nkb + threadIdx.x; r < nkb + nnb; r += blockDim.x) update(r);
+          __threadfence_block();
+          __syncthreads();
+          if (threadIdx.x < 32) ts_diag(A, nkb, nnb, fwd, dg);
+        }
+      } else {
+        // the rest, spread over CTAs 1 ..
+        const int64_t t = static_cast<int64_t>(blockIdx.x - 1) * blockDim.x + threadIdx.x;
+        const int64_t stride = gth - blockDim.x;
+        for (int64_t r = t; r < hi - lo; r += stride) {
+          const int rr = static_cast<int>(fwd ? lo + r : r);
+          if (has_next && rr >= nkb && rr < nkb + nnb) continue;  // CTA 0's rows
+          update(rr);
+        }
+      }
+      if (!grid_sync(A.bar, A.flags)) return;
+    }
+  }
+}
+
+}  // namespace
+
+// nullptr-free launcher: returns false in *handled when a cooperative launch is not possible
+fk_status trisolve_coop(const double* L, int64_t D, double* X, int n_rhs, cudaStream_t st, Scratch& scr,
+                        unsigned* flags, bool* handled) {
+  *handled = false;
+  int dev = 0, coop = 0, sms = 0;
+  FK_CUDA(cudaGetDevice(&dev));
+  FK_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  FK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (!coop || D < 2 * TS_NB || D > (1 << 30)) return FK_OK;
+  unsigned char* misc;
+  FK_TRY(scr.alloc(&misc, 16 * static_cast<size_t>(n_rhs)));
+  FK_CUDA(cudaMemsetAsync(misc, 0, 16 * static_cast<size_t>(n_rhs), st));
+  for (int r = 0; r < n_rhs; ++r) {
+    TsP A{L, static_cast<int>(D), X + 2 * static_cast<int64_t>(r) * D, reinterpret_cast<GridBar*>(misc + 16 * r),
+          flags};
+    void* args[] = {&A};
+    FK_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_trisolve_coop), dim3(sms), dim3(256), args, 0,
+                                        st));
+    note_launch();
+  }
+  *handled = true;
   return FK_OK;
 }
 
