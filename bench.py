@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--workload", default="2d-sobolev", choices=["2d-sobolev", "sweep-1d", "pik-heat", "additive-8d"],
                     help="2d-sobolev is the headline line; the others time the other hot-path rows")
     a = ap.parse_args()
@@ -384,7 +385,8 @@ def main():
     x = x_h.cuda()
     y = y_h.cuda()
     spread = {"auto": fk.FK_SPREAD_AUTO, "atomic": fk.FK_SPREAD_ATOMIC, "binned": fk.FK_SPREAD_BINNED}[args.spread]
-    opts = fk.default_opts(spread=spread)
+    # the first warm-up step times the spreader's tunable shapes and keeps the fastest
+    opts = fk.default_opts(spread=spread, autotune=0 if args.no_autotune else 1)
     st = torch.cuda.current_stream()
 
     def step():
@@ -452,7 +454,8 @@ def main():
             "config": {"workload": WL["workload"], "n": n, "d": d, "m": m, "s": s, "lambda": lam, "eps": eps,
                        "precision": "mixed (fp32 spread/FFT, fp64 assembly/solve)",
                        "l2": "inputs (%.1f GB) larger than L2, no flush" % (12 * n / 1e9), "parallelism": "replicas" if world > 1 else "1 GPU"},
-            "gpu_launches": launches, "roofline": roofline, "clocks": clk.summary()}
+            "gpu_launches": launches, "roofline": roofline, "clocks": clk.summary(),
+            "autotune": fk.fk_autotune_table().strip() or None}
 
     if rank == 0 and not args.no_e2e:
         # end to end through the public call: pinned host inputs copied each step, theta read back

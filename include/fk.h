@@ -97,6 +97,10 @@ typedef struct {
   int spread;         /* fk_spread: AUTO = BINNED (d = 2) or FIXED (d = 1) for FK_MIXED where the
                          shape allows, else ATOMIC; FK_FP64 always spreads with ATOMIC */
   int deterministic;  /* reserved: 1 asks for run-to-run identical sums (default 0) */
+  int autotune;       /* 1: the first call of a problem class times the kernels' tunable shapes
+                         (partition tile, cells per owner, round quota) on the call's own data,
+                         keeps the fastest in a process-wide table and uses it from then on;
+                         that first call runs the spreading several times (default 0) */
 } fk_opts;
 
 /* Filled when a non-NULL pointer is passed (the call then synchronises `stream`). */
@@ -121,6 +125,12 @@ FK_API void fk_default_opts(fk_opts* opts);
  * the pool's unused memory of the current device to the system (synchronises the
  * device). */
 FK_API fk_status fk_release_workspace(void);
+
+/* Autotuning table: fk_autotune_table writes one line per tuned problem class (device,
+ * kernel, class, the timings tried and the winner) into buf (at most cap bytes, NUL
+ * terminated) and returns the size it needs; fk_autotune_clear empties the table. */
+FK_API size_t fk_autotune_table(char* buf, size_t cap);
+FK_API void fk_autotune_clear(void);
 
 /* Sobolev / low-bias estimator (Eq. 2 with Sec. 3.1 or 3.2 penalty) for a batch of
  * n_lambda regularisation values and n_targets response vectors.

@@ -28,7 +28,8 @@ EXPORTS = ["fk_default_opts", "fk_fit_sobolev", "fk_fit_pik", "fk_fit_additive",
            "fk_type2", "fk_build_system", "fk_penalty_weights", "fk_solve", "fk_hypergrad", "fk_last_error",
            "fk_workspace_bytes", "fk_version", "fk_launch_count", "fk_type1_noalloc", "fk_penalty_grads",
            "fk_accum_create", "fk_accum_add", "fk_accum_system", "fk_accum_fit_sobolev", "fk_accum_reset",
-           "fk_accum_destroy", "fk_generate_sweep_1d", "fk_release_workspace"]
+           "fk_accum_destroy", "fk_generate_sweep_1d", "fk_release_workspace", "fk_autotune_table",
+           "fk_autotune_clear"]
 
 
 class FkError(RuntimeError):
@@ -41,7 +42,7 @@ class FkError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("cg_tol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
                 ("refine_steps", ctypes.c_int), ("sobolev_c0", ctypes.c_double), ("upsampfac", ctypes.c_double),
-                ("spread", ctypes.c_int), ("deterministic", ctypes.c_int)]
+                ("spread", ctypes.c_int), ("deterministic", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -93,6 +94,8 @@ def lib() -> ctypes.CDLL:
             "fk_accum_destroy": (_I, [_P]),
             "fk_generate_sweep_1d": (_I, [ctypes.c_uint64, _I, _L, _L, _I, _P, _P, _P, _P]),
             "fk_release_workspace": (_I, []),
+            "fk_autotune_table": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
+            "fk_autotune_clear": (None, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -406,3 +409,15 @@ def generate_sweep_1d(first: int, n: int, n_targets: int = 16, seed: int = 20250
 def fk_release_workspace():
     """Return the library's unused workspace memory on the current device."""
     _check(lib().fk_release_workspace())
+
+
+def fk_autotune_table() -> str:
+    """The tuned problem classes and their measured shapes, one line each."""
+    need = lib().fk_autotune_table(None, 0)
+    buf = ctypes.create_string_buffer(int(need))
+    lib().fk_autotune_table(buf, need)
+    return buf.value.decode()
+
+
+def fk_autotune_clear():
+    lib().fk_autotune_clear()

@@ -138,7 +138,7 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
       } else if (binned2) {
         const float* xf = reinterpret_cast<const float*>(x);
         FK_TRY(spread_binned_xy(p2, n, xf + static_cast<int64_t>(l1) * n, xf + static_cast<int64_t>(l2) * n, -1.0f,
-                                nullptr, 0, true, grid2, flags, st, inner));
+                                nullptr, 0, true, grid2, flags, st, inner, o.autotune != 0));
         FK_TRY(grid_to_modes<float>(p2, grid2, 0, 1, m, corr2, inv_n, blk, st, inner));
       } else {
         const float* fp = reinterpret_cast<const float*>(pts);

@@ -176,7 +176,7 @@ static fk_status spread_any(const EsPlan& p, int precision, const fk_opts& o, in
     if (!spread_binned_supported(p, n_y, with_ones))
       return set_error(FK_EINVAL, "binned spreading does not support d=%d w=%d channels=%d", p.d, p.w, nc);
     return spread_binned(p, n, static_cast<const float*>(x), static_cast<const float*>(y), n_y, with_ones, grid,
-                         flags, st, scr);
+                         flags, st, scr, o.autotune != 0);
   }
   return spread_atomic<float>(p, n, static_cast<const float*>(x), static_cast<const float*>(y), n_y, with_ones,
                               grid, flags, st);
@@ -227,6 +227,7 @@ void fk_default_opts(fk_opts* o) {
   o->upsampfac = 1.9;
   o->spread = FK_SPREAD_AUTO;
   o->deterministic = 0;
+  o->autotune = 0;
 }
 
 const char* fk_last_error(void) { return g_err.c_str(); }

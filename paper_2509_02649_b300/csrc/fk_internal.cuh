@@ -137,15 +137,33 @@ template <typename R>
 fk_status spread_atomic(const EsPlan& p, int64_t n, const R* x, const R* y, int n_y,
                         bool with_ones, double* grid, unsigned* flags, cudaStream_t st);
 
+// ------------------------------------------------------------------ autotuning
+// Tunables of the kernels whose best shape depends on the problem; a process-wide
+// table keyed by the problem's class holds the measured winners (autotune.cu).
+struct BinCfg {       // 2-D binned spreading
+  int per = 7;        // points per thread and tile of the partition scatter (5..7)
+  int cells = 0;      // cells per owner CTA (0: the kernel's maximum)
+  float qmul = 0.5f;  // per-round quota = mean + qmul sqrt(mean)
+};
+enum TuneKind { TUNE_SPREAD2D = 1, TUNE_SPREAD1D = 2, TUNE_CG2D = 3 };
+struct TuneKey {
+  int kind, a, b, c, d;  // kind-specific class (grid size, width, channels, log2 n ...)
+};
+bool tune_lookup(const TuneKey& k, BinCfg* out);           // on the current device
+void tune_store(const TuneKey& k, const BinCfg& v, const std::string& log);
+bool tune_lookup_int(const TuneKey& k, int* out);
+void tune_store_int(const TuneKey& k, int v, const std::string& log);
+
 // Binned register-accumulation spreading (fp32, d = 2, ones and/or one strength channel).
+// autotune: on the first call of a problem class, time the tunables and keep the best.
 fk_status spread_binned(const EsPlan& p, int64_t n, const float* x, const float* y, int n_y,
                         bool with_ones, double* grid, unsigned* flags, cudaStream_t st,
-                        Scratch& scratch);
+                        Scratch& scratch, bool autotune = false);
 bool spread_binned_supported(const EsPlan& p, int n_y, bool with_ones);
 // As spread_binned with the two coordinates as separate rows, the second taken times s1.
 fk_status spread_binned_xy(const EsPlan& p, int64_t n, const float* x0, const float* x1, float s1, const float* y,
                            int n_y, bool with_ones, double* grid, unsigned* flags, cudaStream_t st,
-                           Scratch& scratch);
+                           Scratch& scratch, bool autotune = false);
 
 // 1-D fixed-point shared-memory spreading (fp32 inputs, any channel count).  y_absmax:
 // device array of max|y_c| bit patterns for the n_y strength channels, or null to

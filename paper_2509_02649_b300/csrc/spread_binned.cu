@@ -421,11 +421,11 @@ constexpr int S2_TILE = S2_THREADS * S2_PER;    // 7168
 struct S2Layout {
   size_t stage, sorted, ints, bar, total;
 };
-__host__ __device__ inline S2Layout s2_layout(int G) {
+__host__ __device__ inline S2Layout s2_layout(int G, int tile = S2_TILE) {
   S2Layout L;
-  L.stage = 0;                                             // float [3][S2_TILE]
-  L.sorted = L.stage + sizeof(float) * 3 * S2_TILE;        // uint4 [S2_TILE]
-  L.ints = L.sorted + sizeof(uint4) * S2_TILE;             // int [4 (G + 1)]
+  L.stage = 0;                                             // float [3][tile]
+  L.sorted = L.stage + sizeof(float) * 3 * tile;           // uint4 [tile]
+  L.ints = L.sorted + sizeof(uint4) * tile;                // int [4 (G + 1)]
   L.bar = (L.ints + sizeof(int) * 4 * (G + 1) + 15) & ~static_cast<size_t>(15);
   L.total = L.bar + 16;
   return L;
@@ -534,10 +534,12 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter2(PartArgs A) {
 // One-pass scatter (no count pass): as k_bin_scatter2, but each tile reserves room
 // for its owner runs in fixed-capacity buckets with one global atomic per (tile,
 // owner).  A reservation that would pass the capacity writes nothing and sets ovf.
+template <int PER>
 __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter1(PartArgs A) {
+  constexpr int TILE = S2_THREADS * PER;
   extern __shared__ __align__(16) unsigned char smem[];
   const int G = A.G;
-  const S2Layout L = s2_layout(G);
+  const S2Layout L = s2_layout(G, TILE);
   float* stage = reinterpret_cast<float*>(smem + L.stage);
   uint4* sorted = reinterpret_cast<uint4*>(smem + L.sorted);
   int* tpos = reinterpret_cast<int*>(smem + L.ints);  // [G + 1] reserved slot in the bucket, -1: none
@@ -555,33 +557,33 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter1(PartArgs A) {
   }
   __syncthreads();
   auto issue = [&](int64_t t0) {
-    const int cnt = static_cast<int>(min(static_cast<int64_t>(S2_TILE), e0 - t0));
+    const int cnt = static_cast<int>(min(static_cast<int64_t>(TILE), e0 - t0));
     const unsigned bytes = static_cast<unsigned>(cnt) * 4u;
     fence_proxy_async();
     mbar_arrive_expect(bar, bytes * (A.has_y ? 3u : 2u));
     bulk_g2s(stage, A.x + t0, bytes, bar);
-    bulk_g2s(stage + S2_TILE, A.x1 + t0, bytes, bar);
-    if (A.has_y) bulk_g2s(stage + 2 * S2_TILE, A.y + t0, bytes, bar);
+    bulk_g2s(stage + TILE, A.x1 + t0, bytes, bar);
+    if (A.has_y) bulk_g2s(stage + 2 * TILE, A.y + t0, bytes, bar);
   };
   if (tid == 0 && s0 < e0) issue(s0);
   unsigned phase = 0;
-  for (int64_t t0 = s0; t0 < e0; t0 += S2_TILE) {
-    const int cnt = static_cast<int>(min(static_cast<int64_t>(S2_TILE), e0 - t0));
+  for (int64_t t0 = s0; t0 < e0; t0 += TILE) {
+    const int cnt = static_cast<int>(min(static_cast<int64_t>(TILE), e0 - t0));
     for (int o = tid; o <= G; o += S2_THREADS) tcnt[o] = 0;
     if (!mbar_wait(bar, phase, A.flags)) return;
     phase ^= 1u;
     __syncthreads();
-    uint4 rec[S2_PER];
+    uint4 rec[PER];
 #pragma unroll
-    for (int k = 0; k < S2_PER; ++k) {
+    for (int k = 0; k < PER; ++k) {
       const int i = k * S2_THREADS + tid;
       rec[k].x = 0xFFFFFFFFu;
       if (i < cnt) {
         float f0, f1;
         uint32_t key;
-        if (point_key(stage[i], stage[S2_TILE + i], A, inv_cpc, &f0, &f1, &key)) {
+        if (point_key(stage[i], stage[TILE + i], A, inv_cpc, &f0, &f1, &key)) {
           rec[k] = make_uint4(key, __float_as_uint(f0), __float_as_uint(f1),
-                              A.has_y ? __float_as_uint(stage[2 * S2_TILE + i]) : 0u);
+                              A.has_y ? __float_as_uint(stage[2 * TILE + i]) : 0u);
           atomicAdd(&tcnt[key >> 16], 1);
         } else {
           atomicOr(A.flags, FLAG_RANGE);
@@ -589,7 +591,7 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter1(PartArgs A) {
       }
     }
     __syncthreads();
-    if (tid == 0 && t0 + S2_TILE < e0) issue(t0 + S2_TILE);
+    if (tid == 0 && t0 + TILE < e0) issue(t0 + TILE);
     // reservations in the buckets, one global atomic per owner present in the tile;
     // the returned slot is needed only for the copy-out, so the atomic's latency
     // overlaps the scan and the placement
@@ -619,7 +621,7 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter1(PartArgs A) {
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < S2_PER; ++k) {
+    for (int k = 0; k < PER; ++k) {
       if (rec[k].x != 0xFFFFFFFFu) {
         const int p2 = atomicAdd(&tcur[rec[k].x >> 16], 1);
         sorted[p2] = rec[k];
@@ -658,6 +660,7 @@ struct AccArgs {
   const int* fill;
   int cap;
   const unsigned* ovf;
+  float qmul;  // per-round quota = mean load + qmul sqrt(mean load)
 };
 
 struct AccLayout {
@@ -800,7 +803,7 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
     int q = 0x7FFFFFFF;
     if (!last && my_ncells > 0) {
       const float lam = static_cast<float>(hi - lo) / static_cast<float>(my_ncells);
-      q = static_cast<int>(ceilf(lam + 0.5f * sqrtf(lam)));
+      q = static_cast<int>(ceilf(lam + A.qmul * sqrtf(lam)));
     }
     __syncthreads();
     const int mine = owns ? ccount[cell] : 0;
@@ -916,9 +919,11 @@ int sm_count() {
   return sms;
 }
 
-// owners: enough that each holds at most Cfg::CELLS cells, and at least one per SM
-static int owner_count(int64_t ncells, bool pair, int sms) {
-  const int cells = pair ? Cfg<true>::CELLS : Cfg<false>::CELLS;
+// owners: enough that each holds at most `cells` cells (Cfg::CELLS by default), and at
+// least one per SM
+static int owner_count(int64_t ncells, bool pair, int sms, int cells = 0) {
+  const int cmax = pair ? Cfg<true>::CELLS : Cfg<false>::CELLS;
+  if (cells <= 0 || cells > cmax) cells = cmax;
   int64_t G = (ncells + cells - 1) / cells;
   if (G < sms) G = sms;
   if (G > ncells) G = ncells;
@@ -935,18 +940,30 @@ bool spread_binned_supported(const EsPlan& p, int n_y, bool with_ones) {
 }
 
 fk_status spread_binned(const EsPlan& p, int64_t n, const float* x, const float* y, int n_y, bool with_ones,
-                        double* grid, unsigned* flags, cudaStream_t st, Scratch& scr) {
-  return spread_binned_xy(p, n, x, x + n, 1.0f, y, n_y, with_ones, grid, flags, st, scr);
+                        double* grid, unsigned* flags, cudaStream_t st, Scratch& scr, bool autotune) {
+  return spread_binned_xy(p, n, x, x + n, 1.0f, y, n_y, with_ones, grid, flags, st, scr, autotune);
 }
 
-fk_status spread_binned_xy(const EsPlan& p, int64_t n, const float* x, const float* x1, float s1, const float* y,
-                           int n_y, bool with_ones, double* grid, unsigned* flags, cudaStream_t st, Scratch& scr) {
-  if (!spread_binned_supported(p, n_y, with_ones)) return set_error(FK_EINVAL, "binned spreading: unsupported shape");
-  if (n >= (static_cast<int64_t>(1) << 31)) return set_error(FK_EINVAL, "binned spreading: n >= 2^31 per call");
+namespace {
+
+using Scatter1Fn = void (*)(PartArgs);
+Scatter1Fn pick_scatter1(int per, int* tile) {
+  switch (per) {
+    case 5: *tile = S2_THREADS * 5; return k_bin_scatter1<5>;
+    case 6: *tile = S2_THREADS * 6; return k_bin_scatter1<6>;
+    default: *tile = S2_THREADS * 7; return k_bin_scatter1<7>;
+  }
+}
+
+// one run of the 2-D binned spreader with explicit tunables
+fk_status spread_binned_run(const EsPlan& p, int64_t n, const float* x, const float* x1, float s1, const float* y,
+                            int n_y, bool with_ones, double* grid, unsigned* flags, cudaStream_t st, Scratch& scr,
+                            const BinCfg& cfg) {
   const int nch = n_y + (with_ones ? 1 : 0);
   const bool pair = (nch == 2);
   const int64_t ncells = static_cast<int64_t>(p.N) * p.N;
-  const int G = owner_count(ncells, pair, sm_count());
+  const int G = owner_count(ncells, pair, sm_count(), cfg.cells);
+  if (G > MAX_G) return set_error(FK_EINVAL, "binned spreading: %d owners exceed %d", G, MAX_G);
   const int cpc = static_cast<int>((ncells + G - 1) / G);
   const double c = p.N / (2.0 * M_PI);
 
@@ -1007,6 +1024,7 @@ fk_status spread_binned_xy(const EsPlan& p, int64_t n, const float* x, const flo
   A.fill = P.fill;
   A.cap = P.cap;
   A.ovf = ovf;
+  A.qmul = cfg.qmul;
   const KFn fn = pair ? pick2d<true>(p.w) : pick2d<false>(p.w);
   if (!fn) return set_error(FK_EINVAL, "binned spreading: w = %d not built", p.w);
   const int threads = pair ? Cfg<true>::THREADS : Cfg<false>::THREADS;
@@ -1016,8 +1034,11 @@ fk_status spread_binned_xy(const EsPlan& p, int64_t n, const float* x, const flo
   KernelTimer* kt = kernel_timer();
 
   if (one_pass) {
-    FK_CUDA(cudaFuncSetAttribute(k_bin_scatter1, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm2)));
-    k_bin_scatter1<<<P.nblk, S2_THREADS, sm2, st>>>(P); note_launch();
+    int tile1 = S2_TILE;
+    const Scatter1Fn s1fn = pick_scatter1(cfg.per, &tile1);
+    const size_t sm1 = s2_layout(G, tile1).total;
+    FK_CUDA(cudaFuncSetAttribute(s1fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm1)));
+    s1fn<<<P.nblk, S2_THREADS, sm1, st>>>(P); note_launch();
     FK_CUDA(cudaGetLastError());
     A.mode = 1;
     if (kt->on) cudaEventRecord(kt->start, st);
@@ -1054,6 +1075,84 @@ fk_status spread_binned_xy(const EsPlan& p, int64_t n, const float* x, const flo
   }
   FK_CUDA(cudaGetLastError());
   return FK_OK;
+}
+
+}  // namespace
+
+fk_status spread_binned_xy(const EsPlan& p, int64_t n, const float* x, const float* x1, float s1, const float* y,
+                           int n_y, bool with_ones, double* grid, unsigned* flags, cudaStream_t st, Scratch& scr,
+                           bool autotune) {
+  if (!spread_binned_supported(p, n_y, with_ones)) return set_error(FK_EINVAL, "binned spreading: unsupported shape");
+  if (n >= (static_cast<int64_t>(1) << 31)) return set_error(FK_EINVAL, "binned spreading: n >= 2^31 per call");
+  const int nch = n_y + (with_ones ? 1 : 0);
+  int lg = 0;
+  while ((static_cast<int64_t>(1) << (lg + 1)) <= n) ++lg;
+  const TuneKey key{TUNE_SPREAD2D, p.N, p.w, nch, lg};
+  BinCfg cfg;
+  if (tune_lookup(key, &cfg)) {
+    return spread_binned_run(p, n, x, x1, s1, y, n_y, with_ones, grid, flags, st, scr, cfg);
+  }
+  if (!autotune || n < (1 << 20)) return spread_binned_run(p, n, x, x1, s1, y, n_y, with_ones, grid, flags, st, scr, cfg);
+  // Coordinate search over the tunables, each trial a full run timed with events on
+  // this stream; the winner is cached for this (grid, width, channels, size class).
+  const bool pair = (nch == 2);
+  const int cmax = pair ? Cfg<true>::CELLS : Cfg<false>::CELLS;
+  const int64_t ncells = static_cast<int64_t>(p.N) * p.N;
+  const int sms = std::max(1, sm_count());
+  // cells per owner that give whole waves of owners over the SMs, and the default
+  const int waves_cells = static_cast<int>((ncells + 2 * sms - 1) / (2 * sms));
+  std::vector<int> cells_opts = {cmax};
+  if (waves_cells < cmax) cells_opts.push_back(waves_cells);
+  if (cmax * 7 / 8 != waves_cells) cells_opts.push_back(cmax * 7 / 8);
+  const std::vector<int> per_opts = {7, 6, 5};
+  const std::vector<float> q_opts = {0.5f, 0.25f, 1.0f};
+  cudaEvent_t e0, e1;
+  FK_CUDA(cudaEventCreate(&e0));
+  FK_CUDA(cudaEventCreate(&e1));
+  auto trial = [&](const BinCfg& c, float* ms) -> fk_status {
+    cudaEventRecord(e0, st);
+    {
+      Scratch inner(st);
+      FK_TRY(spread_binned_run(p, n, x, x1, s1, y, n_y, with_ones, grid, flags, st, inner, c));
+    }
+    cudaEventRecord(e1, st);
+    FK_CUDA(cudaEventSynchronize(e1));
+    FK_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    return FK_OK;
+  };
+  BinCfg best;
+  float best_ms = 0.f;
+  std::string log;
+  fk_status rc = trial(best, &best_ms);  // the default (first trial also warms caches)
+  if (rc == FK_OK) rc = trial(best, &best_ms);
+  char line[160];
+  snprintf(line, sizeof(line), "default %.3f ms", best_ms);
+  log += line;
+  for (int knob = 0; knob < 3 && rc == FK_OK; ++knob) {
+    const size_t cnt = knob == 0 ? per_opts.size() : (knob == 1 ? cells_opts.size() : q_opts.size());
+    for (size_t i = 0; i < cnt && rc == FK_OK; ++i) {
+      BinCfg c = best;
+      if (knob == 0) c.per = per_opts[i];
+      if (knob == 1) c.cells = cells_opts[i];
+      if (knob == 2) c.qmul = q_opts[i];
+      if (c.per == best.per && c.cells == best.cells && c.qmul == best.qmul) continue;
+      float ms = 0.f;
+      rc = trial(c, &ms);
+      snprintf(line, sizeof(line), "; per=%d cells=%d q=%.2f %.3f ms", c.per, c.cells, c.qmul, ms);
+      log += line;
+      if (rc == FK_OK && ms < best_ms) {
+        best = c;
+        best_ms = ms;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  FK_TRY(rc);
+  snprintf(line, sizeof(line), "  ->  per=%d cells=%d q=%.2f (%.3f ms)", best.per, best.cells, best.qmul, best_ms);
+  log += line;
+  tune_store(key, best, log);
+  return spread_binned_run(p, n, x, x1, s1, y, n_y, with_ones, grid, flags, st, scr, best);
 }
 
 }  // namespace fk
