@@ -255,7 +255,7 @@ def run_row(args, rank, local):
         x = torch.empty((1, chunk), dtype=torch.float32, device="cuda")
         y = torch.empty((nt, chunk), dtype=torch.float32, device="cuda")
         amax = torch.empty(nt, dtype=torch.int32, device="cuda")
-        acc = fk.Accumulator(1, m, nt, 1e-6, "mixed")
+        acc = fk.Accumulator(1, m, nt, 1e-6, "mixed", opts=fk.default_opts(autotune=1))
 
         def step():
             ev = []
@@ -302,7 +302,8 @@ def run_row(args, rank, local):
             L.backward()
             e1.record(st)
             torch.cuda.synchronize()
-            _, rep = fk.fk_fit_pik(x, y, m, 1.0, 1e-8, 1e-2, alpha, [1.0, -0.1], 1e-6, "mixed", report=True)
+            _, rep = fk.fk_fit_pik(x, y, m, 1.0, 1e-8, 1e-2, alpha, [1.0, -0.1], 1e-6, "mixed", report=True,
+                                   opts=fk.default_opts(autotune=1))
             return e0.elapsed_time(e1), rep["ms_kernel"], (L.item(), lt.grad.item(), mt.grad.item())
 
         f_pt = 49 * (2 * 2 + 1)
@@ -321,7 +322,7 @@ def run_row(args, rank, local):
         def step():
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            th, rep = fk.fk_fit_additive(x, y, m, [lam], 1e-6, "mixed", report=True)
+            th, rep = fk.fk_fit_additive(x, y, m, [lam], 1e-6, "mixed", report=True, opts=fk.default_opts(autotune=1))
             e1.record(st)
             torch.cuda.synchronize()
             return e0.elapsed_time(e1), rep["ms_spread"], rep
@@ -350,6 +351,7 @@ def run_row(args, rank, local):
                          "traffic": None, "kernel": kern, "flop_per_point": f_pt, "ms_kernel": mk,
                          "peak_basis": "of derived peak: 148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % sm_max},
             "clocks": clk.summary()}
+    line["autotune"] = fk.fk_autotune_table().strip() or None
     if W == "pik-heat":
         line["loss_and_grads"] = {"L": res[-1][2][0], "dL/dlambda": res[-1][2][1], "dL/dmu": res[-1][2][2]}
     if W == "additive-8d":

@@ -96,7 +96,7 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
     Scratch inner(st);  // released (stream-ordered) after each coordinate
     if (fixed1d)
       FK_TRY(spread1d_fixed(p1, n, reinterpret_cast<const float*>(x + static_cast<int64_t>(l) * n),
-                            reinterpret_cast<const float*>(y), nt, true, amax, grid1, false, flags, st, inner));
+                            reinterpret_cast<const float*>(y), nt, true, amax, grid1, false, flags, st, inner, o.autotune != 0));
     else
       FK_TRY(spread_atomic<R>(p1, n, x + static_cast<int64_t>(l) * n, y, nt, true, grid1, flags, st));
     if (precision == FK_FP64) {

@@ -167,7 +167,7 @@ static fk_status spread_any(const EsPlan& p, int precision, const fk_opts& o, in
     if (!spread1d_fixed_supported(p, n_y, with_ones))
       return set_error(FK_EINVAL, "fixed-point spreading does not support N=%d w=%d channels=%d", p.N, p.w, nc);
     return spread1d_fixed(p, n, static_cast<const float*>(x), static_cast<const float*>(y), n_y, with_ones, nullptr,
-                          grid, false, flags, st, scr);
+                          grid, false, flags, st, scr, o.autotune != 0);
   }
   if (o.spread == FK_SPREAD_FIXED) return set_error(FK_EINVAL, "fixed-point spreading is built for d = 1");
   const bool binned = (o.spread == FK_SPREAD_BINNED) ||
@@ -556,7 +556,7 @@ fk_status fk_accum_add(fk_accum* a, int64_t n, const void* x, const void* y, con
   if (a->precision == FK_MIXED && a->d == 1 && a->o.spread != FK_SPREAD_ATOMIC &&
       spread1d_fixed_supported(p, a->nt, true)) {
     FK_TRY(spread1d_fixed(p, n, static_cast<const float*>(x), static_cast<const float*>(y), a->nt, true, y_absmax,
-                          a->grid, true, a->flags, st, scr));
+                          a->grid, true, a->flags, st, scr, a->o.autotune != 0));
   } else {
     const int64_t G = ipow(p.N, a->d) * (1 + a->nt);
     double* tmp;

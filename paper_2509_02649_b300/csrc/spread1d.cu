@@ -302,17 +302,24 @@ bool spread1d_fixed_supported(const EsPlan& p, int n_y, bool with_ones) {
   return (nc + c - 1) / c <= MAXGRP;
 }
 
-fk_status spread1d_fixed(const EsPlan& p, int64_t n, const float* x, const float* y, int n_y, bool with_ones,
-                         const unsigned* y_absmax, double* grid, bool accumulate, unsigned* flags, cudaStream_t st,
-                         Scratch& scr) {
-  if (!spread1d_fixed_supported(p, n_y, with_ones))
-    return set_error(FK_EINVAL, "1-D fixed-point spreading: unsupported shape (N = %d, w = %d)", p.N, p.w);
+namespace {
+
+// channels per CTA at most for this grid size (shared-memory budget and CG)
+int channel_cap(int N) {
+  return static_cast<int>(std::min<size_t>(CG, SMEM_BUDGET / (8 * static_cast<size_t>(N + HALO))));
+}
+
+fk_status spread1d_run(const EsPlan& p, int64_t n, const float* x, const float* y, int n_y, bool with_ones,
+                       const unsigned* y_absmax, double* grid, bool accumulate, unsigned* flags, cudaStream_t st,
+                       Scratch& scr, int cmax_req) {
   const int nc = n_y + (with_ones ? 1 : 0);
   const int N = p.N;
   if (!accumulate) FK_CUDA(cudaMemsetAsync(grid, 0, sizeof(double) * N * nc, st));
   if (n == 0) return FK_OK;
 
-  const int cmax = static_cast<int>(std::min<size_t>(CG, SMEM_BUDGET / (8 * static_cast<size_t>(N + HALO))));
+  int cmax = channel_cap(N);
+  if (cmax_req > 0 && cmax_req < cmax) cmax = cmax_req;
+  if ((nc + cmax - 1) / cmax > MAXGRP) cmax = (nc + MAXGRP - 1) / MAXGRP;
   const int ngrp = (nc + cmax - 1) / cmax;
   Fx1dArgs A{};
   A.n = n;
@@ -382,6 +389,66 @@ fk_status spread1d_fixed(const EsPlan& p, int64_t n, const float* x, const float
   note_launch();
   FK_CUDA(cudaGetLastError());
   return FK_OK;
+}
+
+}  // namespace
+
+fk_status spread1d_fixed(const EsPlan& p, int64_t n, const float* x, const float* y, int n_y, bool with_ones,
+                         const unsigned* y_absmax, double* grid, bool accumulate, unsigned* flags, cudaStream_t st,
+                         Scratch& scr, bool autotune) {
+  if (!spread1d_fixed_supported(p, n_y, with_ones))
+    return set_error(FK_EINVAL, "1-D fixed-point spreading: unsupported shape (N = %d, w = %d)", p.N, p.w);
+  const int nc = n_y + (with_ones ? 1 : 0);
+  int lg = 0;
+  while ((static_cast<int64_t>(1) << (lg + 1)) <= n) ++lg;
+  const TuneKey key{TUNE_SPREAD1D, p.N, p.w, nc, lg};
+  int cm = 0;
+  if (tune_lookup_int(key, &cm) || !autotune || n < (1 << 20))
+    return spread1d_run(p, n, x, y, n_y, with_ones, y_absmax, grid, accumulate, flags, st, scr, cm);
+  // trials write a scratch grid when the call adds into the caller's grid
+  double* tgrid = grid;
+  if (accumulate) FK_TRY(scr.alloc(&tgrid, static_cast<size_t>(p.N) * nc));
+  // channels per CTA: more channels share each point's weights, fewer let more CTAs
+  // reside per SM; time each on this call's data (the grid is rewritten each time)
+  const int cap = channel_cap(p.N);
+  std::vector<int> opts = {cap};
+  if (cap > 2) opts.push_back(cap - 1);
+  if (cap > 1) opts.push_back((cap + 1) / 2 == cap - 1 ? 1 : (cap + 1) / 2);
+  cudaEvent_t e0, e1;
+  FK_CUDA(cudaEventCreate(&e0));
+  FK_CUDA(cudaEventCreate(&e1));
+  int best = cap;
+  float best_ms = 1e30f;
+  std::string log;
+  fk_status rc = FK_OK;
+  for (size_t i = 0; i <= opts.size() && rc == FK_OK; ++i) {
+    const int c = opts[i == 0 ? 0 : i - 1];  // the first option twice: warm-up, then timed
+    cudaEventRecord(e0, st);
+    {
+      Scratch inner(st);
+      rc = spread1d_run(p, n, x, y, n_y, with_ones, y_absmax, tgrid, false, flags, st, inner, c);
+    }
+    cudaEventRecord(e1, st);
+    if (rc != FK_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (i == 0) continue;
+    char line[64];
+    snprintf(line, sizeof(line), "%schannels/CTA=%d %.3f ms", log.empty() ? "" : "; ", c, ms);
+    log += line;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  FK_TRY(rc);
+  char line[64];
+  snprintf(line, sizeof(line), "  ->  channels/CTA=%d (%.3f ms)", best, best_ms);
+  tune_store_int(key, best, log + line);
+  return spread1d_run(p, n, x, y, n_y, with_ones, y_absmax, grid, accumulate, flags, st, scr, best);
 }
 
 }  // namespace fk

@@ -46,3 +46,25 @@ def test_autotune_2d_spreader():
     assert rel(T4.cpu().numpy(), To) < 1e-5
     fk.fk_autotune_clear()
     assert fk.fk_autotune_table() == ""
+
+
+def test_autotune_1d_spreader_and_accumulator():
+    fk.fk_autotune_clear()
+    n = 1 << 21
+    x, y, amax = fk.generate_sweep_1d(0, n, 16)
+    plain = fk.Accumulator(1, 1000, 16, 1e-6, "mixed")
+    plain.add(x, y, amax)
+    T0, b0, _ = plain.system()
+    plain.close()
+    tuned = fk.Accumulator(1, 1000, 16, 1e-6, "mixed", opts=fk.default_opts(autotune=1))
+    tuned.add(x, y, amax)
+    tuned.add(x, y, amax)  # the second add reuses the stored shape and adds once more
+    T1, b1, nt = tuned.system()
+    tuned.close()
+    assert nt == 2 * n
+    assert "spread1d" in fk.fk_autotune_table()
+    # the same points twice: the normalised sums are unchanged (integer sums: exact
+    # up to the fp64 scaling of the two chunks)
+    assert rel(T1.cpu().numpy(), T0.cpu().numpy()) < 1e-12
+    assert rel(b1.cpu().numpy(), b0.cpu().numpy()) < 1e-12
+    fk.fk_autotune_clear()
