@@ -161,6 +161,42 @@ def penalty_pik(d: int, m: int, lam: float, s: float, mu: float, alpha, a,
     return penalty_sobolev(d, m, lam, s, c0) + mu * np.abs(pde_symbol(d, m, alpha, a)) ** 2
 
 
+def box_moments(d: int, m: int, lo, hi) -> np.ndarray:
+    """Moments of the normalised Lebesgue measure of a box Omega = prod_l [lo_l, hi_l]
+    (inside the period [-pi, pi)^d):  c_j = (2 pi)^{-d} int_Omega e^{-i<j, x>} dx,
+    |j|_inf <= 2m, lexicographic.  The Fourier matrix C of Omega (§4, tractable
+    domains) is C_{k,k'} = c_{k-k'}: the form int_Omega |D f_theta|^2 dx / (2 pi)^d of
+    f_theta = sum_k theta_k e^{+i<k,x>} is (D theta)^* C (D theta).  Per coordinate
+    the integral is (e^{-i j hi} - e^{-i j lo}) / (-i j), or hi - lo at j = 0."""
+    lo = np.broadcast_to(np.asarray(lo, dtype=np.float64), (d,))
+    hi = np.broadcast_to(np.asarray(hi, dtype=np.float64), (d,))
+    j = np.arange(-2 * m, 2 * m + 1, dtype=np.float64)
+    out = np.ones(1, dtype=np.complex128)
+    for l in range(d):
+        with np.errstate(divide="ignore", invalid="ignore"):
+            f = (np.exp(-1j * j * hi[l]) - np.exp(-1j * j * lo[l])) / (-1j * j)
+        f[2 * m] = hi[l] - lo[l]
+        out = np.multiply.outer(out, f / (2 * np.pi)).ravel()
+    return out
+
+
+def penalty_pik_general(d: int, m: int, lam: float, s: float, mu: float, alpha, a,
+                        c_moments: np.ndarray, c0: float = 1.0) -> np.ndarray:
+    """Dense penalty lambda S^2 + mu D^* C D of §4 with a non-diagonal Fourier matrix
+    C_{k,k'} = c_{k-k'} (a sub-domain in closed form, or the collocation points'
+    moments (1/n_r) sum_r e^{-i<j, X_r>}); D = diag P(ik)."""
+    P = pde_symbol(d, m, alpha, a)
+    C = toeplitz_matrix(c_moments, d, m)
+    return np.diag(penalty_sobolev(d, m, lam, s, c0)) + mu * (np.conj(P)[:, None] * C * P[None, :])
+
+
+def fit_penalised(x: np.ndarray, y: np.ndarray, m: int, Pen: np.ndarray) -> np.ndarray:
+    """theta_hat = (Phi^*Phi/n + Pen)^{-1} Phi^*Y/n for a dense Hermitian penalty."""
+    d = np.atleast_2d(x).shape[0]
+    A = toeplitz_matrix(moments(x, m), d, m) + Pen
+    return solve_hpd(A, rhs(x, y, m).T).T
+
+
 def toeplitz_matrix(T: np.ndarray, d: int, m: int) -> np.ndarray:
     """Dense Sigma with Sigma_{k,k'} = T_{k-k'} (§2.3: Hermitian d-level block
     Toeplitz, determined by its first row)."""

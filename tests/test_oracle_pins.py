@@ -277,3 +277,89 @@ def test_hypergradient_matches_finite_differences():
             yy[i] = v
             return loss(lam, s, mu, a, yy)
         assert abs(fd(ly, y[i], rel=1e-3) - dY[i]) < 1e-6 * abs(dY[i]) + 1e-12
+
+
+# ------------------------------------------------------------------ sub-domain / collocation PIK
+def test_box_moments_full_period_is_identity():
+    for d in (1, 2):
+        c = O.box_moments(d, 3, -np.pi, np.pi)
+        want = np.zeros_like(c)
+        want[len(c) // 2] = 1.0
+        assert np.max(np.abs(c - want)) < 1e-15
+
+
+def test_box_moments_against_quadrature():
+    # midpoint rule on a fine grid of the box (exact for these smooth integrands up to
+    # O(h^2 j^2))
+    lo, hi, m = (-0.3, 0.1), (0.9, 1.2), 3
+    c = O.box_moments(2, m, lo, hi)
+    K = 4 * m + 1
+    g = 4000
+    u = lo[0] + (hi[0] - lo[0]) * (np.arange(g) + 0.5) / g
+    v = lo[1] + (hi[1] - lo[1]) * (np.arange(g) + 0.5) / g
+    area = (hi[0] - lo[0]) * (hi[1] - lo[1]) / g ** 2
+    for j0, j1 in [(0, 0), (1, -2), (-5, 3), (6, 6)]:
+        q = np.sum(np.exp(-1j * j0 * u))[()] * np.sum(np.exp(-1j * j1 * v)) * area / (2 * np.pi) ** 2
+        assert abs(c[(j0 + 2 * m) * K + (j1 + 2 * m)] - q) < 1e-6
+
+
+def test_penalty_form_is_the_integral_of_the_operator():
+    # theta^* (D^* C D) theta = (2 pi)^{-d} int_Omega |D f_theta|^2 dx, by quadrature of
+    # D f_theta built from its definition (derivatives of e^{i<k,x>})
+    g = np.random.default_rng(5)
+    m, lo, hi = 4, (-0.7, 0.2), (0.8, 1.5)
+    alpha, a = [[1, 0], [0, 2]], [1.0, -0.3]
+    D = (2 * m + 1) ** 2
+    th = g.standard_normal(D) + 1j * g.standard_normal(D)
+    Pen = O.penalty_pik_general(2, m, 0.0, 1.0, 1.0, alpha, a, O.box_moments(2, m, lo, hi))
+    form = np.real(np.conj(th) @ Pen @ th)
+    k = O.mode_grid(2, m).astype(np.float64)
+    npt = 600
+    u = lo[0] + (hi[0] - lo[0]) * (np.arange(npt) + 0.5) / npt
+    v = lo[1] + (hi[1] - lo[1]) * (np.arange(npt) + 0.5) / npt
+    U, V = np.meshgrid(u, v, indexing="ij")
+    Df = np.zeros(U.shape, dtype=np.complex128)
+    for t, (al, coef) in enumerate(zip(alpha, a)):
+        # d^al / dx^al of e^{i(k0 u + k1 v)} = (i k0)^al0 (i k1)^al1 e^{...}
+        fac = coef * (1j * k[:, 0]) ** al[0] * (1j * k[:, 1]) ** al[1]
+        Df += np.einsum("k,kij->ij", th * fac, np.exp(1j * (k[:, 0, None, None] * U + k[:, 1, None, None] * V)))
+    integral = np.sum(np.abs(Df) ** 2) * (hi[0] - lo[0]) * (hi[1] - lo[1]) / npt ** 2 / (2 * np.pi) ** 2
+    assert abs(form - integral) < 1e-5 * abs(integral)
+
+
+def test_collocation_moments_full_period_match_the_diagonal_penalty():
+    # equispaced collocation points over the period: their moments are delta_j, so the
+    # collocation penalty equals the full-period (diagonal) one
+    m = 3
+    xr = S.equispaced_2d(16, 16)
+    c = O.moments(xr, m)
+    Pen = O.penalty_pik_general(2, m, 1e-3, 1.0, 0.5, [[1, 0], [0, 2]], [1.0, -0.1], c)
+    want = np.diag(O.penalty_pik(2, m, 1e-3, 1.0, 0.5, [[1, 0], [0, 2]], [1.0, -0.1]))
+    assert np.max(np.abs(Pen - want)) < 1e-12 * np.max(np.abs(want))
+
+
+def test_general_pik_fit_minimises_the_objective():
+    # the fit zeroes the gradient of n^-1 |Phi theta - Y|^2 + theta^* Pen theta, checked
+    # with the objective evaluated by direct sums and finite differences along random
+    # directions
+    g = np.random.default_rng(8)
+    m, n = 3, 400
+    x = S.uniform_points(n, 2, 41)
+    y = np.sin(x[0]) * np.cos(x[1]) + 0.1 * g.standard_normal(n)
+    Pen = O.penalty_pik_general(2, m, 1e-2, 1.0, 0.3, [[1, 0], [0, 2]], [1.0, -0.1],
+                                O.box_moments(2, m, (-1.0, -0.5), (1.2, 0.9)))
+    th = O.fit_penalised(x, y, m, Pen)
+
+    def objective(t):
+        r = O.type2(t, x, m) - y  # complex predictions; the real target
+        return float(np.mean(np.abs(r) ** 2) + np.real(np.conj(t) @ Pen @ t))
+
+    J0 = objective(th)
+    for _ in range(4):
+        dirn = g.standard_normal(th.shape) + 1j * g.standard_normal(th.shape)
+        h = 1e-4
+        assert objective(th + h * dirn) - J0 > -1e-12
+        assert objective(th - h * dirn) - J0 > -1e-12
+        # second-order: the first-order term vanishes
+        fd = (objective(th + h * dirn) - objective(th - h * dirn)) / (2 * h)
+        assert abs(fd) < 1e-6
