@@ -151,6 +151,28 @@ FK_API fk_status fk_fit_pik(int d, int64_t n, const void* x, const void* y, int 
                      const int* alpha, const double* a, double eps, int precision,
                      const fk_opts* opts, double* theta, void* stream, fk_report* rep);
 
+/* Physics-informed estimator on a sub-domain or with collocation points (Sec. 4,
+ * tractable and intractable domains): the penalty is lambda (c0 + |k|^{2s}) on the
+ * diagonal plus mu D^* C D with D = diag P(ik) and the Hermitian Toeplitz C_{k,k'} =
+ * c_{k-k'}, so the system is solved with conjugate gradients (two circulant products
+ * per iteration) or, for D <= 1024, a dense Cholesky factorisation.
+ *   c_moments: device complex (4m+1)^d, c_j = (2 pi)^{-d} int_Omega e^{-i<j,x>} dx for a
+ *     domain Omega (fk_box_moments gives a box in closed form), or (1/n_r) sum_r
+ *     e^{-i<j, X_r>} for collocation points X_r (the T output of fk_build_system on them).
+ *     The full period has c_j = delta_j, where fk_fit_pik is the diagonal special case.
+ *   Other arguments as fk_fit_pik (n_terms >= 1). */
+FK_API fk_status fk_fit_pik_general(int d, int64_t n, const void* x, const void* y, int n_targets, int m,
+                                    double s, double lambda, double mu, int n_terms, const int* alpha,
+                                    const double* a, const double* c_moments, double eps, int precision,
+                                    const fk_opts* opts, double* theta, void* stream, fk_report* rep);
+
+/* Moments c_j (|j|_inf <= 2m) of the normalised Lebesgue measure of the box
+ * prod_l [lo_l, hi_l] (host arrays, -3 pi <= lo_l < hi_l <= 3 pi):
+ *   c_j = prod_l (e^{-i j_l hi_l} - e^{-i j_l lo_l}) / (-2 pi i j_l)  ((hi_l - lo_l)/(2 pi) at j_l = 0).
+ *   c_moments: device complex (4m+1)^d, lexicographic. */
+FK_API fk_status fk_box_moments(int d, int m, const double* lo, const double* hi, double* c_moments,
+                                void* stream);
+
 /* Low-bias additive estimator (Prop. 5.1): theta = (Sigma + lambda I)^{-1} (Phi_l^*Y/n)_l.
  *   d in [2, 16] coordinates; theta: device, [n_lambda][n_targets][d][2m+1] complex. */
 FK_API fk_status fk_fit_additive(int d, int64_t n, const void* x, const void* y, int n_targets,

@@ -12,6 +12,7 @@ import ctypes
 import os
 from typing import Optional, Sequence
 
+import numpy as np
 import torch
 
 from .build import LIB
@@ -29,7 +30,7 @@ EXPORTS = ["fk_default_opts", "fk_fit_sobolev", "fk_fit_pik", "fk_fit_additive",
            "fk_workspace_bytes", "fk_version", "fk_launch_count", "fk_type1_noalloc", "fk_penalty_grads",
            "fk_accum_create", "fk_accum_add", "fk_accum_system", "fk_accum_fit_sobolev", "fk_accum_reset",
            "fk_accum_destroy", "fk_generate_sweep_1d", "fk_release_workspace", "fk_autotune_table",
-           "fk_autotune_clear"]
+           "fk_autotune_clear", "fk_fit_pik_general", "fk_box_moments"]
 
 
 class FkError(RuntimeError):
@@ -96,6 +97,8 @@ def lib() -> ctypes.CDLL:
             "fk_release_workspace": (_I, []),
             "fk_autotune_table": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
             "fk_autotune_clear": (None, []),
+            "fk_fit_pik_general": (_I, [_I, _L, _P, _P, _I, _I, _D, _D, _D, _I, _P, _P, _P, _D, _I, _P, _P, _P, _P]),
+            "fk_box_moments": (_I, [_I, _I, _P, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -421,3 +424,31 @@ def fk_autotune_table() -> str:
 
 def fk_autotune_clear():
     lib().fk_autotune_clear()
+
+
+def fk_box_moments(d: int, m: int, lo, hi, device=None):
+    """c_j = (2 pi)^{-d} int_box e^{-i<j,x>} dx, |j|_inf <= 2m (device complex128)."""
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    c = torch.empty((4 * m + 1) ** d, dtype=torch.complex128, device=dev)
+    lo_a = _dbl_array([float(v) for v in np.broadcast_to(np.asarray(lo, dtype=float), (d,))])
+    hi_a = _dbl_array([float(v) for v in np.broadcast_to(np.asarray(hi, dtype=float), (d,))])
+    _check(lib().fk_box_moments(d, m, lo_a, hi_a, c.data_ptr(), _stream()))
+    return c
+
+
+def fk_fit_pik_general(x, y, m: int, s: float, lam: float, mu: float, alpha, a, c_moments, eps: float,
+                       precision="mixed", opts: Optional[Opts] = None, report: bool = False):
+    """theta [n_targets][D] with the penalty lambda(c0 + |k|^{2s}) + mu D^* C D, C = Toep(c_moments)."""
+    p = _prec(precision)
+    x = _points(x, p)
+    d, n = x.shape
+    y = y.reshape(-1, n).contiguous()
+    al = [int(v) for row in alpha for v in row]
+    alpha_arr = (ctypes.c_int * max(len(al), 1))(*al)
+    theta = torch.empty((y.shape[0], (2 * m + 1) ** d), dtype=torch.complex128, device=x.device)
+    c = c_moments.contiguous()
+    rep = Report()
+    _check(lib().fk_fit_pik_general(d, n, x.data_ptr(), y.data_ptr(), y.shape[0], m, s, lam, mu, len(a), alpha_arr,
+                                    _dbl_array(a), c.data_ptr(), eps, p, _opts_ptr(opts), theta.data_ptr(), _stream(),
+                                    ctypes.byref(rep) if report else None))
+    return (theta, rep.as_dict()) if report else theta

@@ -370,7 +370,7 @@ fk_status fk_solve(int d, int m, const double* T, const double* W, int n_w, cons
 static fk_status fit_common(int d, int64_t n, const void* x, const void* y, int n_targets, int m,
                             int penalty, double s, const double* lambdas, int n_lambda, double mu, int n_terms,
                             const int* alpha, const double* a, double eps, int precision, const fk_opts* opts,
-                            double* theta, void* stream, fk_report* rep) {
+                            double* theta, void* stream, fk_report* rep, const double* cmom = nullptr) {
   FK_TRY(check_common(d, n, m, eps, precision));
   if (!x || !y || !theta || !lambdas || n_targets < 1 || n_lambda < 1)
     return set_error(FK_EINVAL, "bad fit arguments");
@@ -393,10 +393,23 @@ static fk_status fit_common(int d, int64_t n, const void* x, const void* y, int 
   FK_TRY(scr.alloc(&W, D * n_lambda));
   EsPlan p;
   FK_TRY(build_system(d, n, x, y, n_targets, m, eps, precision, o, T, b, st, scr, fl.dev, &p, &tm));
-  FK_TRY(penalty_weights(d, m, penalty, s, o.sobolev_c0, lambdas, n_lambda, mu, n_terms, alpha, a, W, st));
+  PenOp op;
+  if (cmom) {
+    // sub-domain / collocation penalty: W keeps the Sobolev part, mu D^* C D is an operator
+    double* P;
+    FK_TRY(scr.alloc(&P, 2 * D));
+    FK_TRY(pde_symbol_vec(d, m, n_terms, alpha, a, P, st));
+    FK_TRY(penalty_weights(d, m, penalty, s, o.sobolev_c0, lambdas, n_lambda, 0.0, 0, nullptr, nullptr, W, st));
+    op.c = cmom;
+    op.P = P;
+    op.mu = mu;
+  } else {
+    FK_TRY(penalty_weights(d, m, penalty, s, o.sobolev_c0, lambdas, n_lambda, mu, n_terms, alpha, a, W, st));
+  }
   int iters = 0;
   double rr = 0;
-  FK_TRY(solve_system(d, m, T, W, n_lambda, b, n_targets, o, theta, st, scr, fl.dev, &iters, &rr));
+  FK_TRY(solve_system(d, m, T, W, n_lambda, b, n_targets, o, theta, st, scr, fl.dev, &iters, &rr,
+                      cmom ? &op : nullptr));
   tm.mark();
   FK_TRY(fl.check());
   if (rep) {
@@ -432,6 +445,23 @@ fk_status fk_fit_pik(int d, int64_t n, const void* x, const void* y, int n_targe
     return set_error(FK_EINVAL, "bad PDE operator arguments");
   return fit_common(d, n, x, y, n_targets, m, FK_PEN_SOBOLEV, s, &lambda, 1, mu, n_terms, alpha, a, eps, precision,
                     opts, theta, stream, rep);
+}
+
+fk_status fk_fit_pik_general(int d, int64_t n, const void* x, const void* y, int n_targets, int m, double s,
+                             double lambda, double mu, int n_terms, const int* alpha, const double* a,
+                             const double* c_moments, double eps, int precision, const fk_opts* opts, double* theta,
+                             void* stream, fk_report* rep) {
+  clear_error();
+  if (!c_moments) return set_error(FK_EINVAL, "c_moments is null (use fk_fit_pik for the full period)");
+  if (n_terms < 1 || n_terms > 16 || !alpha || !a) return set_error(FK_EINVAL, "bad PDE operator arguments");
+  return fit_common(d, n, x, y, n_targets, m, FK_PEN_SOBOLEV, s, &lambda, 1, mu, n_terms, alpha, a, eps, precision,
+                    opts, theta, stream, rep, c_moments);
+}
+
+fk_status fk_box_moments(int d, int m, const double* lo, const double* hi, double* c_moments, void* stream) {
+  clear_error();
+  if (d < 1 || d > 3 || m < 0 || !lo || !hi || !c_moments) return set_error(FK_EINVAL, "bad box moment arguments");
+  return box_moments(d, m, lo, hi, c_moments, static_cast<cudaStream_t>(stream));
 }
 
 fk_status fk_fit_additive(int d, int64_t n, const void* x, const void* y, int n_targets, int m,

@@ -194,10 +194,21 @@ fk_status penalty_weights(int d, int m, int penalty, double s, double c0, const 
                           int n_lambda, double mu, int n_terms, const int* alpha, const double* a,
                           double* W, cudaStream_t st);
 
-// Dense / CG solves of (Toep(T) + diag W_l) X = B.
+// Extra penalty mu D^* C D of §4 with a non-diagonal Fourier matrix C_{k,k'} = c_{k-k'}
+// (a sub-domain, or collocation points) and D = diag P(ik).
+struct PenOp {
+  const double* c = nullptr;  // (4m+1)^d complex moments, device
+  const double* P = nullptr;  // (2m+1)^d complex symbol, device
+  double mu = 0.0;
+};
+fk_status pde_symbol_vec(int d, int m, int n_terms, const int* alpha, const double* a, double* P, cudaStream_t st);
+fk_status box_moments(int d, int m, const double* lo, const double* hi, double* c, cudaStream_t st);
+
+// Dense / CG solves of (Toep(T) + diag W_l [+ mu D^* Toep(c) D]) X = B.
 fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, const double* rhs,
                        int n_rhs, const fk_opts& o, double* sol, cudaStream_t st,
-                       Scratch& scratch, unsigned* flags, int* cg_iters, double* rel_res);
+                       Scratch& scratch, unsigned* flags, int* cg_iters, double* rel_res,
+                       const PenOp* op = nullptr);
 
 // Variants with caller-supplied scratch (used by the entry point that allocates nothing).
 fk_status es_correction_into(const EsPlan& p, double* corr, double* gl_scratch, cudaStream_t st);

@@ -102,6 +102,137 @@ fk_status penalty_weights(int d, int m, int penalty, double s, double c0, const 
 
 // ---------------------------------------------------------------- dense assembly
 // A[r][c] = T_{k_r - k_c} + delta_rc W[r]
+// P(ik) = sum_t a_t prod_l (i k_l)^alpha_tl for every mode (complex, interleaved)
+__global__ void k_pde_symbol(int d, int m, PdeTerms pde, double* P) {
+  const int K = 2 * m + 1;
+  int64_t D = 1;
+  for (int l = 0; l < d; ++l) D *= K;
+  for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < D;
+       q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int k[3] = {0, 0, 0};
+    mode_of(q, d, m, k);
+    double pre = 0.0, pim = 0.0;
+    for (int tt = 0; tt < pde.n_terms; ++tt) {
+      double tre = pde.a[tt], tim = 0.0;
+      for (int l = 0; l < d; ++l)
+        for (int e = 0; e < pde.alpha[tt][l]; ++e) {
+          const double nre = -tim * k[l];
+          tim = tre * k[l];
+          tre = nre;
+        }
+      pre += tre;
+      pim += tim;
+    }
+    P[2 * q] = pre;
+    P[2 * q + 1] = pim;
+  }
+}
+
+// c_j = (2 pi)^{-d} int_box e^{-i<j,x>} dx for |j|_inf <= 2m (box in [-3 pi, 3 pi)^d)
+struct Box {
+  double lo[3], hi[3];
+};
+__global__ void k_box_moments(int d, int m, Box bx, double* c) {
+  const int K2 = 4 * m + 1;
+  int64_t M2 = 1;
+  for (int l = 0; l < d; ++l) M2 *= K2;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < M2;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int64_t q = t;
+    double re = 1.0, im = 0.0;
+    for (int l = d - 1; l >= 0; --l) {
+      const int j = static_cast<int>(q % K2) - 2 * m;
+      q /= K2;
+      double fr, fi;
+      if (j == 0) {
+        fr = bx.hi[l] - bx.lo[l];
+        fi = 0.0;
+      } else {
+        // (e^{-i j hi} - e^{-i j lo}) / (-i j) = (sin(j hi) - sin(j lo)) / j + i (cos(j hi) - cos(j lo)) / j
+        double sh, ch, sl, cl;
+        sincos(j * bx.hi[l], &sh, &ch);
+        sincos(j * bx.lo[l], &sl, &cl);
+        fr = (sh - sl) / j;
+        fi = (ch - cl) / j;
+      }
+      fr *= 0.15915494309189535;  // 1 / (2 pi)
+      fi *= 0.15915494309189535;
+      const double nr = re * fr - im * fi, ni = re * fi + im * fr;
+      re = nr;
+      im = ni;
+    }
+    c[2 * t] = re;
+    c[2 * t + 1] = im;
+  }
+}
+
+fk_status pde_symbol_vec(int d, int m, int n_terms, const int* alpha, const double* a, double* P, cudaStream_t st) {
+  if (n_terms < 0 || n_terms > 16) return set_error(FK_EINVAL, "n_terms must be in [0, 16]");
+  PdeTerms pde{};
+  pde.n_terms = n_terms;
+  for (int t = 0; t < n_terms; ++t) {
+    pde.a[t] = a[t];
+    for (int l = 0; l < d; ++l) {
+      if (alpha[t * d + l] < 0 || alpha[t * d + l] > 32) return set_error(FK_EINVAL, "alpha out of range");
+      pde.alpha[t][l] = alpha[t * d + l];
+    }
+  }
+  int64_t D = 1;
+  for (int l = 0; l < d; ++l) D *= (2 * m + 1);
+  k_pde_symbol<<<grid_for(D, 256), 256, 0, st>>>(d, m, pde, P); note_launch();
+  FK_CUDA(cudaGetLastError());
+  return FK_OK;
+}
+
+fk_status box_moments(int d, int m, const double* lo, const double* hi, double* c, cudaStream_t st) {
+  if (d < 1 || d > 3) return set_error(FK_EINVAL, "box moments: d = %d", d);
+  Box bx{};
+  for (int l = 0; l < d; ++l) {
+    if (!(lo[l] < hi[l]) || !(lo[l] >= -3.0 * M_PI) || !(hi[l] <= 3.0 * M_PI))
+      return set_error(FK_EINVAL, "box side %d: need -3 pi <= lo < hi <= 3 pi", l);
+    bx.lo[l] = lo[l];
+    bx.hi[l] = hi[l];
+  }
+  int64_t M2 = 1;
+  for (int l = 0; l < d; ++l) M2 *= (4 * m + 1);
+  k_box_moments<<<grid_for(M2, 256), 256, 0, st>>>(d, m, bx, c); note_launch();
+  FK_CUDA(cudaGetLastError());
+  return FK_OK;
+}
+
+// dense operator part: A[k][k'] += mu conj(P_k) c_{k-k'} P_k'
+__global__ void k_assemble_op(int d, int m, const double* c, const double* P, double mu, double* A) {
+  const int K = 2 * m + 1, K2 = 4 * m + 1;
+  int64_t D = 1;
+  for (int l = 0; l < d; ++l) D *= K;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < D * D;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = t / D, cc = t - r * D;
+    int kr[3] = {0, 0, 0}, kc[3] = {0, 0, 0};
+    mode_of(r, d, m, kr);
+    mode_of(cc, d, m, kc);
+    int64_t jidx = 0;
+    for (int l = 0; l < d; ++l) jidx = jidx * K2 + (kr[l] - kc[l] + 2 * m);
+    const double cr = c[2 * jidx], ci = c[2 * jidx + 1];
+    const double pr = P[2 * r], pi = -P[2 * r + 1];  // conj(P_k)
+    const double qr = P[2 * cc], qi = P[2 * cc + 1];
+    // conj(P_k) c P_k'
+    const double ar = pr * cr - pi * ci, ai = pr * ci + pi * cr;
+    A[2 * t] += mu * (ar * qr - ai * qi);
+    A[2 * t + 1] += mu * (ar * qi + ai * qr);
+  }
+}
+
+// Jacobi diagonal of the operator form: W_k + mu |P_k|^2 Re c_0
+__global__ void k_op_diag(int64_t D, int n_w, const double* W, const double* P, const double* c0, double mu,
+                          double* Wd) {
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < D * n_w;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t q = t % D;
+    Wd[t] = W[t] + mu * (P[2 * q] * P[2 * q] + P[2 * q + 1] * P[2 * q + 1]) * c0[0];
+  }
+}
+
 __global__ void k_assemble(int d, int m, const double* T, const double* W, double* A) {
   const int K = 2 * m + 1, K2 = 4 * m + 1;
   int64_t D = 1;
@@ -949,9 +1080,12 @@ __global__ void k_cgf_rows_inv(int K, int Lc, int logLc, int n_rhs, const cplx<d
   }
 }
 
-// 1-D: the whole matvec of one system per CTA
+// 1-D: the whole matvec of one system per CTA; with ch2 != null the operator term
+// mu conj(P) Toep(c) (P v) of a sub-domain / collocation penalty is added (second
+// circulant product on the same shared line)
 __global__ void k_cgf_1d(int K, int Lc, int logLc, int n_rhs, const cplx<double>* ch, const double* W, const double* v,
-                         double* q, const double* tw, CgScal sc, int zero_scalars, int cur, int want_dot) {
+                         double* q, const double* tw, CgScal sc, int zero_scalars, int cur, int want_dot,
+                         const cplx<double>* ch2, const double* P, double mu) {
   extern __shared__ unsigned char smem_raw[];
   cplx<double>* sl = reinterpret_cast<cplx<double>*>(smem_raw);
   __shared__ double red[32];
@@ -962,35 +1096,50 @@ __global__ void k_cgf_1d(int K, int Lc, int logLc, int n_rhs, const cplx<double>
     (cur ? sc.rz0 : sc.rz1)[s] = 0.0;
   }
   const double* vs = v + 2 * static_cast<int64_t>(s) * K;
-  for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
-    cplx<double> e;
-    e.x = (i < K) ? vs[2 * i] : 0.0;
-    e.y = (i < K) ? vs[2 * i + 1] : 0.0;
-    sl[bitrev(i, logLc)] = e;
-  }
-  __syncthreads();
-  fft_smem<double>(sl, Lc, -1, tw);
-  for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
-    const cplx<double> a = ch[i], e = sl[i];
-    cplx<double> t;
-    t.x = a.x * e.x - a.y * e.y;
-    t.y = a.x * e.y + a.y * e.x;
-    sl[i] = t;
-  }
-  __syncthreads();
-  bitrev_permute<double>(sl, Lc, logLc);
-  fft_smem<double>(sl, Lc, +1, tw);
   const double inv = 1.0 / static_cast<double>(Lc);
   const double* Ws = W + static_cast<int64_t>(s / n_rhs) * K;
   double* qs = q + 2 * static_cast<int64_t>(s) * K;
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < K; i += blockDim.x) {
-    const double qr = sl[i].x * inv + Ws[i] * vs[2 * i];
-    const double qi = sl[i].y * inv + Ws[i] * vs[2 * i + 1];
-    qs[2 * i] = qr;
-    qs[2 * i + 1] = qi;
-    acc += vs[2 * i] * qr + vs[2 * i + 1] * qi;
+  for (int pass = 0; pass < (ch2 ? 2 : 1); ++pass) {
+    const cplx<double>* spec = pass ? ch2 : ch;
+    for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
+      cplx<double> e;
+      e.x = (i < K) ? vs[2 * i] : 0.0;
+      e.y = (i < K) ? vs[2 * i + 1] : 0.0;
+      if (pass && i < K) {  // P v
+        const double pr = P[2 * i], pi = P[2 * i + 1];
+        const double ex = pr * e.x - pi * e.y, ey = pr * e.y + pi * e.x;
+        e.x = ex;
+        e.y = ey;
+      }
+      sl[bitrev(i, logLc)] = e;
+    }
+    __syncthreads();
+    fft_smem<double>(sl, Lc, -1, tw);
+    for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
+      const cplx<double> a = spec[i], e = sl[i];
+      cplx<double> t;
+      t.x = a.x * e.x - a.y * e.y;
+      t.y = a.x * e.y + a.y * e.x;
+      sl[i] = t;
+    }
+    __syncthreads();
+    bitrev_permute<double>(sl, Lc, logLc);
+    fft_smem<double>(sl, Lc, +1, tw);
+    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+      if (pass == 0) {
+        qs[2 * i] = sl[i].x * inv + Ws[i] * vs[2 * i];
+        qs[2 * i + 1] = sl[i].y * inv + Ws[i] * vs[2 * i + 1];
+      } else {  // + mu conj(P) (.)
+        const double pr = P[2 * i], pi = -P[2 * i + 1];
+        const double tr = sl[i].x * inv, ti = sl[i].y * inv;
+        qs[2 * i] += mu * (pr * tr - pi * ti);
+        qs[2 * i + 1] += mu * (pr * ti + pi * tr);
+      }
+    }
+    __syncthreads();
   }
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) acc += vs[2 * i] * qs[2 * i] + vs[2 * i + 1] * qs[2 * i + 1];
   if (want_dot) {
     const double t = block_sum(acc, red);
     if (threadIdx.x == 0) sc.pq[s] = t;
@@ -1080,7 +1229,8 @@ __global__ void k_cgf_init(int64_t D, int n_rhs, const double* W, double T0, con
 
 static fk_status cg_solve_fused(int d, int m, const double* T, const double* W, int n_w, const double* rhs, int n_rhs,
                                 const fk_opts& o, double* sol, cudaStream_t st, Scratch& scr, int* iters_out,
-                                double* relres_out) {
+                                double* relres_out, const PenOp* op = nullptr) {
+  if (op && d != 1) return set_error(FK_EINVAL, "operator penalty: the multi-launch CG is built for d = 1");
   const int K = 2 * m + 1;
   int Lc = next_pow2i(4 * m + 1);
   if (Lc < 2) Lc = 2;
@@ -1114,6 +1264,21 @@ static fk_status cg_solve_fused(int d, int m, const double* T, const double* W, 
   FK_CUDA(cudaStreamSynchronize(st));
   if (!(T0 > 0.0)) T0 = 1.0;
 
+  // operator penalty: its circulant spectrum, and W + mu |P|^2 c_0 as the Jacobi diagonal
+  cplx<double>* ch2 = nullptr;
+  const double* Wd = W;
+  if (op) {
+    FK_TRY(scr.alloc(&ch2, LL));
+    FK_CUDA(cudaMemsetAsync(ch2, 0, sizeof(cplx<double>) * LL, st));
+    k_circ_embed<<<grid_for(M2, 256), 256, 0, st>>>(d, m, Lc, op->c, ch2); note_launch();
+    FK_TRY(fft_lines<double>(ch2, Lc, 1, Lc, 1, -1, tw, st));
+    double* wd;
+    FK_TRY(scr.alloc(&wd, D * n_w));
+    k_op_diag<<<grid_for(D * n_w, 256), 256, 0, st>>>(D, n_w, W, op->P, op->c + 2 * centre, op->mu, wd); note_launch();
+    FK_CUDA(cudaGetLastError());
+    Wd = wd;
+  }
+
   double *r, *z, *p, *q, *scal;
   int *active, *cnt;
   cplx<double>* buf = nullptr;
@@ -1130,7 +1295,7 @@ static fk_status cg_solve_fused(int d, int m, const double* T, const double* W, 
   k_set_active<<<(nsys + 255) / 256, 256, 0, st>>>(nsys, active); note_launch();
   double* x = sol;
   const dim3 gv(static_cast<unsigned>(std::min<int64_t>((D + 255) / 256, 64)), nsys);
-  k_cgf_init<<<gv, 256, 0, st>>>(D, n_rhs, W, T0, rhs, x, r, z, p, sc); note_launch();
+  k_cgf_init<<<gv, 256, 0, st>>>(D, n_rhs, Wd, T0, rhs, x, r, z, p, sc); note_launch();
   FK_CUDA(cudaGetLastError());
   const int thr = Lc >= 256 ? 256 : (Lc >= 64 ? Lc / 2 : 32);
   if (line_sm > 48 * 1024) {
@@ -1141,7 +1306,9 @@ static fk_status cg_solve_fused(int d, int m, const double* T, const double* W, 
   }
   auto matvec = [&](const double* v, double* out, int zero, int cur, int dot) -> fk_status {
     if (d == 1) {
-      k_cgf_1d<<<nsys, thr, line_sm, st>>>(K, Lc, logLc, n_rhs, ch, W, v, out, tw, sc, zero, cur, dot); note_launch();
+      k_cgf_1d<<<nsys, thr, line_sm, st>>>(K, Lc, logLc, n_rhs, ch, W, v, out, tw, sc, zero, cur, dot, ch2,
+                                           op ? op->P : nullptr, op ? op->mu : 0.0);
+      note_launch();
     } else {
       k_cgf_rows_fwd<<<dim3(K, nsys), thr, line_sm, st>>>(K, Lc, logLc, v, buf, tw, sc, zero, cur); note_launch();
       k_cgf_cols<<<dim3(Lc, nsys), thr, line_sm, st>>>(K, Lc, logLc, buf, ch, tw, sc); note_launch();
@@ -1156,7 +1323,7 @@ static fk_status cg_solve_fused(int d, int m, const double* T, const double* W, 
   for (it = 0; it < o.cg_maxit; ++it) {
     const int cur = it & 1;
     FK_TRY(matvec(p, q, 1, cur, 1));
-    k_cgf_update<<<gv, 256, 0, st>>>(D, n_rhs, W, T0, sc, cur, p, q, x, r, z); note_launch();
+    k_cgf_update<<<gv, 256, 0, st>>>(D, n_rhs, Wd, T0, sc, cur, p, q, x, r, z); note_launch();
     k_cgf_direction<<<gv, 256, 0, st>>>(D, tol2, sc, cur, z, p); note_launch();
     FK_CUDA(cudaGetLastError());
     if ((it & 3) == 3 || it + 1 == o.cg_maxit) {
@@ -1188,13 +1355,15 @@ static fk_status cg_solve_fused(int d, int m, const double* T, const double* W, 
 // ---------------------------------------------------------------- dispatcher
 fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, const double* rhs, int n_rhs,
                               const fk_opts& o, double* sol, cudaStream_t st, Scratch& scr, unsigned* flags,
-                              int* iters_out, double* relres_out, bool* handled);
+                              int* iters_out, double* relres_out, bool* handled, const PenOp* op);
+__global__ void k_dense_residual(const double* A, int64_t D, const double* X, const double* B, double* R, int n_rhs);
 
 fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, const double* rhs, int n_rhs,
                        const fk_opts& o, double* sol, cudaStream_t st, Scratch& scratch, unsigned* flags,
-                       int* cg_iters, double* rel_res) {
+                       int* cg_iters, double* rel_res, const PenOp* op) {
   int64_t D = 1;
   for (int l = 0; l < d; ++l) D *= (2 * m + 1);
+  const bool with_op = op && op->c && op->P && op->mu != 0.0;
   int solver = o.solver;
   if (solver == FK_SOLVER_AUTO) solver = (D <= 1024) ? FK_SOLVER_CHOL : FK_SOLVER_CG;
   if (cg_iters) *cg_iters = 0;
@@ -1203,20 +1372,28 @@ fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, 
     if (d == 2) {
       bool handled = false;
       const fk_status rc = cg_solve_persistent(m, T, W, n_w, rhs, n_rhs, o, sol, st, scratch, flags, cg_iters, rel_res,
-                                               &handled);
+                                               &handled, with_op ? op : nullptr);
       if (handled || rc != FK_OK) return rc;
+      if (with_op) return set_error(FK_EINVAL, "the operator penalty's CG needs a cooperative launch");
     }
-    if (d <= 2) return cg_solve_fused(d, m, T, W, n_w, rhs, n_rhs, o, sol, st, scratch, cg_iters, rel_res);
+    if (d <= 2) return cg_solve_fused(d, m, T, W, n_w, rhs, n_rhs, o, sol, st, scratch, cg_iters, rel_res,
+                                      with_op ? op : nullptr);
+    if (with_op) return set_error(FK_EINVAL, "the operator penalty is built for d <= 2");
     return cg_solve(d, m, T, W, n_w, rhs, n_rhs, o, sol, st, scratch, cg_iters, rel_res);
   }
   if (D > 8192) return set_error(FK_EINVAL, "dense Cholesky limited to D <= 8192 (D = %lld)", (long long)D);
-  double *A, *R;
+  double *A, *R, *A0 = nullptr;
   FK_TRY(scratch.alloc(&A, 2 * D * D));
   FK_TRY(scratch.alloc(&R, 2 * D * n_rhs));
+  if (with_op) FK_TRY(scratch.alloc(&A0, 2 * D * D));  // the assembled matrix, for the refinement residual
   for (int l = 0; l < n_w; ++l) {
     const double* Wl = W + l * D;
     double* X = sol + 2 * static_cast<int64_t>(l) * n_rhs * D;
     k_assemble<<<grid_for(D * D, 256), 256, 0, st>>>(d, m, T, Wl, A); note_launch();
+    if (with_op) {
+      k_assemble_op<<<grid_for(D * D, 256), 256, 0, st>>>(d, m, op->c, op->P, op->mu, A); note_launch();
+      FK_CUDA(cudaMemcpyAsync(A0, A, sizeof(double) * 2 * D * D, cudaMemcpyDeviceToDevice, st));
+    }
     FK_CUDA(cudaGetLastError());
     double* linv;
     FK_TRY(scratch.alloc(&linv, 2 * NB * NB));
@@ -1225,7 +1402,11 @@ fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, 
     FK_TRY(trisolve(A, D, X, n_rhs, st, &scratch, flags));
     FK_CUDA(cudaGetLastError());
     for (int it = 0; it < o.refine_steps; ++it) {
-      k_residual_dense<<<grid_for(D * n_rhs, 128), 128, 0, st>>>(d, m, T, Wl, X, rhs, R, n_rhs); note_launch();
+      if (with_op) {
+        k_dense_residual<<<grid_for(D * n_rhs, 128), 128, 0, st>>>(A0, D, X, rhs, R, n_rhs); note_launch();
+      } else {
+        k_residual_dense<<<grid_for(D * n_rhs, 128), 128, 0, st>>>(d, m, T, Wl, X, rhs, R, n_rhs); note_launch();
+      }
       FK_TRY(trisolve(A, D, R, n_rhs, st, &scratch, flags));
       k_axpy_c<<<grid_for(2 * D * n_rhs, 256), 256, 0, st>>>(2 * D * n_rhs, R, X); note_launch();
       FK_CUDA(cudaGetLastError());
@@ -1319,6 +1500,12 @@ struct CgP {
   GridBar* bar;
   unsigned* flags;
   int* info;  // [0] iterations, [1] systems not converged
+  // operator penalty mu conj(P) Toep(c) (P v) (ch2 null: none); Wd: the Jacobi diagonal
+  const cplx<double>* ch2;
+  const double* P;
+  double mu;
+  const double* Wd;
+  cplx<double>* buf2;
 };
 
 // all CTAs of the launch; false when the wait gave up (the caller returns)
@@ -1405,15 +1592,42 @@ __device__ void cgp_rows_fwd(const CgP& A, cplx<double>* sl, int it, bool final_
     for (int i = threadIdx.x; i < Lc; i += blockDim.x) ob[i] = sl[i];
     if (!final_pass && row == 0 && threadIdx.x == 0) A.pq[s] = 0.0;
     __syncthreads();
+    if (A.ch2) {
+      // the same row times P, for the operator penalty (this thread's own writes of p)
+      const double* v = final_pass ? A.x : A.p;
+      for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
+        cplx<double> e;
+        e.x = e.y = 0.0;
+        if (i < K) {
+          const double vr = final_pass ? __ldcg(v + o + 2 * i) : v[o + 2 * i];
+          const double vi = final_pass ? __ldcg(v + o + 2 * i + 1) : v[o + 2 * i + 1];
+          const int64_t pk = static_cast<int64_t>(row) * K + i;
+          const double pr = A.P[2 * pk], pim = A.P[2 * pk + 1];
+          e.x = pr * vr - pim * vi;
+          e.y = pr * vi + pim * vr;
+        }
+        sl[bitrev(i, A.logLc)] = e;
+      }
+      __syncthreads();
+      fft_smem<double>(sl, Lc, -1, A.tw);
+      cplx<double>* ob2 = A.buf2 + (static_cast<int64_t>(s) * K + row) * Lc;
+      for (int i = threadIdx.x; i < Lc; i += blockDim.x) ob2[i] = sl[i];
+      __syncthreads();
+    }
   }
 }
 
 // P2
 __device__ void cgp_cols(const CgP& A, cplx<double>* sl, int it, bool final_pass) {
   const int K = A.K, Lc = A.Lc;
-  for (int item = blockIdx.x; item < A.nsys * Lc; item += gridDim.x) {
+  const int nitems = A.nsys * Lc * (A.ch2 ? 2 : 1);
+  for (int item2 = blockIdx.x; item2 < nitems; item2 += gridDim.x) {
+    const bool second = item2 >= A.nsys * Lc;  // the operator penalty's product
+    const int item = second ? item2 - A.nsys * Lc : item2;
+    const cplx<double>* spec = second ? A.ch2 : A.ch;
+    cplx<double>* base = second ? A.buf2 : A.buf;
     const int s = item / Lc, c = item - s * Lc;
-    if (!final_pass && c == 0 && threadIdx.x == 0) {
+    if (!second && !final_pass && c == 0 && threadIdx.x == 0) {
       // next iteration's accumulators; a finished system carries its values over so
       // that it stays finished
       const bool act = cg_active(A, it, s);
@@ -1422,7 +1636,7 @@ __device__ void cgp_cols(const CgP& A, cplx<double>* sl, int it, bool final_pass
       A.rr[nxt] = act ? 0.0 : __ldcg(A.rr + cur);
     }
     if (!final_pass && !cg_active(A, it, s)) continue;
-    cplx<double>* bcol = A.buf + static_cast<int64_t>(s) * K * Lc + c;
+    cplx<double>* bcol = base + static_cast<int64_t>(s) * K * Lc + c;
     for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
       cplx<double> e;
       e.x = e.y = 0.0;
@@ -1436,7 +1650,7 @@ __device__ void cgp_cols(const CgP& A, cplx<double>* sl, int it, bool final_pass
     __syncthreads();
     fft_smem<double>(sl, Lc, -1, A.tw);
     for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
-      const cplx<double> a = A.ch[static_cast<int64_t>(i) * Lc + c], e = sl[i];
+      const cplx<double> a = spec[static_cast<int64_t>(i) * Lc + c], e = sl[i];
       cplx<double> t;
       t.x = a.x * e.x - a.y * e.y;
       t.y = a.x * e.y + a.y * e.x;
@@ -1470,14 +1684,35 @@ __device__ void cgp_rows_inv(const CgP& A, cplx<double>* sl, double* red, int it
     const int64_t o = 2 * (s * A.D + static_cast<int64_t>(row) * K);
     const double* Ws = A.W + static_cast<int64_t>(s / A.n_rhs) * A.D + static_cast<int64_t>(row) * K;
     const double* v = final_pass ? A.x : A.p;
+    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+      const double vr = __ldcg(v + o + 2 * i), vi = __ldcg(v + o + 2 * i + 1);
+      A.q[o + 2 * i] = sl[i].x * inv + Ws[i] * vr;
+      A.q[o + 2 * i + 1] = sl[i].y * inv + Ws[i] * vi;
+    }
+    if (A.ch2) {
+      __syncthreads();
+      const cplx<double>* bb2 = A.buf2 + (static_cast<int64_t>(s) * K + row) * Lc;
+      for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
+        const double2 w2 = __ldcg(reinterpret_cast<const double2*>(bb2 + i));
+        cplx<double> e;
+        e.x = w2.x;
+        e.y = w2.y;
+        sl[bitrev(i, A.logLc)] = e;
+      }
+      __syncthreads();
+      fft_smem<double>(sl, Lc, +1, A.tw);
+      for (int i = threadIdx.x; i < K; i += blockDim.x) {
+        const int64_t pk = static_cast<int64_t>(row) * K + i;
+        const double pr = A.P[2 * pk], pim = -A.P[2 * pk + 1];  // conj(P)
+        const double tr = sl[i].x * inv, ti = sl[i].y * inv;
+        A.q[o + 2 * i] += A.mu * (pr * tr - pim * ti);
+        A.q[o + 2 * i + 1] += A.mu * (pr * ti + pim * tr);
+      }
+    }
     double acc = 0.0;
     for (int i = threadIdx.x; i < K; i += blockDim.x) {
       const double vr = __ldcg(v + o + 2 * i), vi = __ldcg(v + o + 2 * i + 1);
-      const double qr = sl[i].x * inv + Ws[i] * vr;
-      const double qi = sl[i].y * inv + Ws[i] * vi;
-      A.q[o + 2 * i] = qr;
-      A.q[o + 2 * i + 1] = qi;
-      acc += vr * qr + vi * qi;
+      acc += vr * A.q[o + 2 * i] + vi * A.q[o + 2 * i + 1];
     }
     if (!final_pass) {
       const double t = block_sum_all(acc, red);
@@ -1495,7 +1730,7 @@ __device__ void cgp_update(const CgP& A, double* red, int it, bool final_pass, d
   for (int item = blockIdx.x; item < A.nsys * nch; item += gridDim.x) {
     const int s = item / nch, cb = item - s * nch;
     if (!final_pass && !cg_active(A, it, s)) continue;
-    const double* Ws = A.W + static_cast<int64_t>(s / A.n_rhs) * D;
+    const double* Ws = A.Wd + static_cast<int64_t>(s / A.n_rhs) * D;
     const double* bs = A.b + 2 * static_cast<int64_t>(s % A.n_rhs) * D;
     double a1 = 0.0, a2 = 0.0;
     const double alpha = final_pass ? 0.0 : __ldcg(A.rz + (it & 1) * A.nsys + s) / __ldcg(A.pq + s);
@@ -1540,7 +1775,7 @@ __device__ void cgp_init(const CgP& A, double* red, double T0) {
   const int nch = static_cast<int>((D + chunk - 1) / chunk);
   for (int item = blockIdx.x; item < A.nsys * nch; item += gridDim.x) {
     const int s = item / nch, cb = item - s * nch;
-    const double* Ws = A.W + static_cast<int64_t>(s / A.n_rhs) * D;
+    const double* Ws = A.Wd + static_cast<int64_t>(s / A.n_rhs) * D;
     const double* bs = A.b + 2 * static_cast<int64_t>(s % A.n_rhs) * D;
     double a1 = 0.0, a2 = 0.0;
     for (int64_t k = static_cast<int64_t>(cb) * chunk + threadIdx.x; k < min(D, static_cast<int64_t>(cb + 1) * chunk);
@@ -1609,7 +1844,7 @@ __global__ void __launch_bounds__(256) k_cg_persist2d(CgP A) {
 
 fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, const double* rhs, int n_rhs,
                               const fk_opts& o, double* sol, cudaStream_t st, Scratch& scr, unsigned* flags,
-                              int* iters_out, double* relres_out, bool* handled) {
+                              int* iters_out, double* relres_out, bool* handled, const PenOp* op) {
   *handled = false;
   int dev = 0, coop = 0, sms = 0;
   FK_CUDA(cudaGetDevice(&dev));
@@ -1670,6 +1905,25 @@ fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, 
   FK_TRY(fft_lines<double>(ch, Lc, Lc, 1, Lc, -1, tw, st));
   A.ch = ch;
   A.tw = tw;
+  A.Wd = W;
+  if (op) {
+    cplx<double>* ch2;
+    FK_TRY(scr.alloc(&ch2, static_cast<int64_t>(Lc) * Lc));
+    FK_CUDA(cudaMemsetAsync(ch2, 0, sizeof(cplx<double>) * Lc * Lc, st));
+    k_circ_embed<<<grid_for(M2, 256), 256, 0, st>>>(2, m, Lc, op->c, ch2); note_launch();
+    FK_CUDA(cudaGetLastError());
+    FK_TRY(fft_lines<double>(ch2, Lc, Lc, Lc, 1, -1, tw, st));
+    FK_TRY(fft_lines<double>(ch2, Lc, Lc, 1, Lc, -1, tw, st));
+    double* wd;
+    FK_TRY(scr.alloc(&wd, D * n_w));
+    k_op_diag<<<grid_for(D * n_w, 256), 256, 0, st>>>(D, n_w, W, op->P, op->c + 2 * centre, op->mu, wd); note_launch();
+    FK_CUDA(cudaGetLastError());
+    A.ch2 = ch2;
+    A.P = op->P;
+    A.mu = op->mu;
+    A.Wd = wd;
+    FK_TRY(scr.alloc(&A.buf2, static_cast<size_t>(nsys) * K * Lc));
+  }
   FK_TRY(scr.alloc(&A.r, 2 * D * nsys));
   FK_TRY(scr.alloc(&A.z, 2 * D * nsys));
   FK_TRY(scr.alloc(&A.p, 2 * D * nsys));
