@@ -136,6 +136,67 @@ __global__ void k_t1_2d_cols(const cplx<R>* H, int N, int logN, int kout, const 
   }
 }
 
+// 3-D: lines of dimension 2 (contiguous, real grid) -> H1[line][jj2], then lines of
+// dimension 1 -> H2[c][i0][jj1][jj2], then dimension 0 with corr and scale.
+template <typename R>
+__global__ void k_t1_3d_a(const double* grid, int N, int logN, int c0, int kout, const double* tw, cplx<R>* H1) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<R>* s = reinterpret_cast<cplx<R>*>(smem_raw);
+  const int64_t line = blockIdx.x;  // (c N + i0) N + i1
+  const double* g = grid + (static_cast<int64_t>(c0) * N * N + line) * N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    cplx<R> v;
+    v.x = static_cast<R>(g[i]);
+    v.y = R(0);
+    s[bitrev(i, logN)] = v;
+  }
+  __syncthreads();
+  fft_smem<R>(s, N, -1, tw);
+  const int K = 2 * kout + 1;
+  for (int t = threadIdx.x; t < K; t += blockDim.x) H1[line * K + t] = s[(t - kout + N) & (N - 1)];
+}
+
+template <typename R>
+__global__ void k_t1_3d_b(const cplx<R>* H1, int N, int logN, int kout, const double* tw, cplx<R>* H2) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<R>* s = reinterpret_cast<cplx<R>*>(smem_raw);
+  const int K = 2 * kout + 1;
+  const int64_t b = blockIdx.x;  // (c N + i0) K + jj2
+  const int64_t ci0 = b / K;
+  const int jj2 = static_cast<int>(b - ci0 * K);
+  const cplx<R>* h = H1 + ci0 * N * K + jj2;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) s[bitrev(i, logN)] = h[static_cast<int64_t>(i) * K];
+  __syncthreads();
+  fft_smem<R>(s, N, -1, tw);
+  for (int t = threadIdx.x; t < K; t += blockDim.x) H2[(ci0 * K + t) * K + jj2] = s[(t - kout + N) & (N - 1)];
+}
+
+template <typename R>
+__global__ void k_t1_3d_c(const cplx<R>* H2, int N, int logN, int kout, const double* corr, int corr_off,
+                          double scale, const double* tw, double* out) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<R>* s = reinterpret_cast<cplx<R>*>(smem_raw);
+  const int K = 2 * kout + 1;
+  const int64_t KK = static_cast<int64_t>(K) * K;
+  const int64_t b = blockIdx.x;  // c K K + jj1 K + jj2
+  const int64_t c = b / KK;
+  const int64_t rem = b - c * KK;
+  const int jj1 = static_cast<int>(rem / K), jj2 = static_cast<int>(rem - static_cast<int64_t>(jj1) * K);
+  const cplx<R>* h = H2 + c * N * KK + rem;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) s[bitrev(i, logN)] = h[static_cast<int64_t>(i) * KK];
+  __syncthreads();
+  fft_smem<R>(s, N, -1, tw);
+  double* o = out + c * 2 * KK * K;
+  const double f12 = corr[jj1 + corr_off] * corr[jj2 + corr_off] * scale;
+  for (int t = threadIdx.x; t < K; t += blockDim.x) {
+    const cplx<R> v = s[(t - kout + N) & (N - 1)];
+    const double f = corr[t + corr_off] * f12;
+    const int64_t idx = static_cast<int64_t>(t) * KK + rem;
+    o[2 * idx] = static_cast<double>(v.x) * f;
+    o[2 * idx + 1] = static_cast<double>(v.y) * f;
+  }
+}
+
 template <typename R>
 static fk_status set_smem(const void* fn, size_t sm) {
   if (sm > 48 * 1024) FK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -167,6 +228,23 @@ fk_status grid_to_modes(const EsPlan& p, const double* grid, int c0, int nc, int
     k_t1_2d_rows<R><<<nc * N, 256, sm, st>>>(grid, N, logN, c0, kout, tw, H); note_launch();
     FK_CUDA(cudaGetLastError());
     k_t1_2d_cols<R><<<nc * K, 256, sm, st>>>(H, N, logN, kout, corr, corr_off, scale, tw, out); note_launch();
+    FK_CUDA(cudaGetLastError());
+  } else if (p.d == 3) {
+    cplx<R>* H1 = nullptr;
+    cplx<R>* H2 = nullptr;
+    FK_TRY(scratch.alloc(&H1, static_cast<size_t>(nc) * N * N * K));
+    FK_TRY(scratch.alloc(&H2, static_cast<size_t>(nc) * N * K * K));
+    FK_TRY(set_smem<R>((const void*)k_t1_3d_a<R>, sm));
+    FK_TRY(set_smem<R>((const void*)k_t1_3d_b<R>, sm));
+    FK_TRY(set_smem<R>((const void*)k_t1_3d_c<R>, sm));
+    k_t1_3d_a<R><<<static_cast<unsigned>(static_cast<int64_t>(nc) * N * N), 256, sm, st>>>(grid, N, logN, c0, kout, tw,
+                                                                                           H1);
+    note_launch();
+    k_t1_3d_b<R><<<static_cast<unsigned>(static_cast<int64_t>(nc) * N * K), 256, sm, st>>>(H1, N, logN, kout, tw, H2);
+    note_launch();
+    k_t1_3d_c<R><<<static_cast<unsigned>(static_cast<int64_t>(nc) * K * K), 256, sm, st>>>(H2, N, logN, kout, corr,
+                                                                                           corr_off, scale, tw, out);
+    note_launch();
     FK_CUDA(cudaGetLastError());
   } else {
     return set_error(FK_EINVAL, "d = %d transforms are not built", p.d);

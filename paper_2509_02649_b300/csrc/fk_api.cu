@@ -89,7 +89,7 @@ static fk_opts resolve_opts(const fk_opts* o) {
 }
 
 static fk_status check_common(int d, int64_t n, int m, double eps, int precision) {
-  if (d < 1 || d > 2) return set_error(FK_EINVAL, "d = %d: transforms are built for d in {1, 2}", d);
+  if (d < 1 || d > 3) return set_error(FK_EINVAL, "d = %d: transforms are built for d in {1, 2, 3}", d);
   if (n < 1) return set_error(FK_EINVAL, "n = %lld < 1", (long long)n);
   if (m < 0) return set_error(FK_EINVAL, "m = %d < 0", m);
   if (!(eps >= 1e-14 && eps <= 1e-1)) return set_error(FK_EINVAL, "eps = %g outside [1e-14, 1e-1]", eps);
@@ -348,7 +348,7 @@ fk_status fk_penalty_weights(int d, int m, int penalty, double s, double c0, con
 fk_status fk_solve(int d, int m, const double* T, const double* W, int n_w, const double* rhs, int n_rhs,
                    const fk_opts* opts, double* sol, void* stream, fk_report* rep) {
   clear_error();
-  if (d < 1 || d > 2 || m < 0 || n_w < 1 || n_rhs < 1 || !T || !W || !rhs || !sol)
+  if (d < 1 || d > 3 || m < 0 || n_w < 1 || n_rhs < 1 || !T || !W || !rhs || !sol)
     return set_error(FK_EINVAL, "bad solve arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const fk_opts o = resolve_opts(opts);

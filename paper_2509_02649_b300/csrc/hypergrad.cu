@@ -180,7 +180,7 @@ fk_status fk_hypergrad(int d, int64_t n, const void* x, int64_t n_v, const void*
                        const double* T, const double* W, const double* theta, double eps, int precision,
                        const fk_opts* opts, double* loss, double* dW, double* dY, void* stream) {
   clear_error();
-  if (d < 1 || d > 2) return set_error(FK_EINVAL, "d = %d: transforms are built for d in {1, 2}", d);
+  if (d < 1 || d > 3) return set_error(FK_EINVAL, "d = %d: transforms are built for d in {1, 2, 3}", d);
   if (n < 1 || n_v < 1 || m < 0) return set_error(FK_EINVAL, "bad sizes n=%lld n_v=%lld m=%d", (long long)n,
                                                  (long long)n_v, m);
   if (!(eps >= 1e-14 && eps <= 1e-1)) return set_error(FK_EINVAL, "eps = %g outside [1e-14, 1e-1]", eps);

@@ -837,6 +837,14 @@ static fk_status fft_nd(const Circ& c, int nsys, int sign, cudaStream_t st) {
       FK_TRY(fft_lines<double>(c.buf + s * c.LL, c.Lc, c.Lc, 1, c.Lc, sign, c.tw, st));  // columns
     return FK_OK;
   }
+  if (c.d == 3) {
+    const int64_t L2 = static_cast<int64_t>(c.Lc) * c.Lc;
+    FK_TRY(fft_lines<double>(c.buf, c.Lc, static_cast<int64_t>(nsys) * L2, c.Lc, 1, sign, c.tw, st));
+    for (int64_t q = 0; q < static_cast<int64_t>(nsys) * c.Lc; ++q)
+      FK_TRY(fft_lines<double>(c.buf + q * L2, c.Lc, c.Lc, 1, c.Lc, sign, c.tw, st));
+    for (int s = 0; s < nsys; ++s) FK_TRY(fft_lines<double>(c.buf + s * c.LL, c.Lc, L2, 1, L2, sign, c.tw, st));
+    return FK_OK;
+  }
   return set_error(FK_EINVAL, "CG: d = %d not built", c.d);
 }
 

@@ -62,11 +62,11 @@ __global__ void k_spread_atomic(int d, Win<R> win, R beta, int64_t n, const R* _
                                 unsigned* flags) {
   const int N = win.N, w = win.W;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  const int64_t G = (d == 1) ? N : static_cast<int64_t>(N) * N;
+  const int64_t G = (d == 1) ? N : (d == 2 ? static_cast<int64_t>(N) * N : static_cast<int64_t>(N) * N * N);
   const int nc = n_y + with_ones;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
-    R ker[2][MAXW];
-    int l0[2];
+    R ker[3][MAXW];
+    int l0[3];
     bool ok = true;
     for (int l = 0; l < d; ++l) {
       R f;
@@ -82,13 +82,24 @@ __global__ void k_spread_atomic(int d, Win<R> win, R beta, int64_t n, const R* _
           const int idx = wrap_node(l0[0] + a, N);
           atomicAdd(g + idx, str * static_cast<double>(ker[0][a]));
         }
-      } else {
+      } else if (d == 2) {
         for (int a = 0; a < w; ++a) {
           const int r = wrap_node(l0[0] + a, N);
           const double sa = str * static_cast<double>(ker[0][a]);
           for (int b = 0; b < w; ++b) {
             const int cidx = wrap_node(l0[1] + b, N);
             atomicAdd(g + static_cast<int64_t>(r) * N + cidx, sa * static_cast<double>(ker[1][b]));
+          }
+        }
+      } else {
+        for (int a = 0; a < w; ++a) {
+          const int64_t r = wrap_node(l0[0] + a, N);
+          const double sa = str * static_cast<double>(ker[0][a]);
+          for (int b = 0; b < w; ++b) {
+            const int64_t rb = r * N + wrap_node(l0[1] + b, N);
+            const double sb = sa * static_cast<double>(ker[1][b]);
+            for (int c = 0; c < w; ++c)
+              atomicAdd(g + rb * N + wrap_node(l0[2] + c, N), sb * static_cast<double>(ker[2][c]));
           }
         }
       }
@@ -99,10 +110,11 @@ __global__ void k_spread_atomic(int d, Win<R> win, R beta, int64_t n, const R* _
 template <typename R>
 fk_status spread_atomic(const EsPlan& p, int64_t n, const R* x, const R* y, int n_y, bool with_ones,
                         double* grid, unsigned* flags, cudaStream_t st) {
-  if (p.d < 1 || p.d > 2) return set_error(FK_EINVAL, "spread: d = %d not built", p.d);
+  if (p.d < 1 || p.d > 3) return set_error(FK_EINVAL, "spread: d = %d not built", p.d);
   if (p.w > MAXW) return set_error(FK_EINTERNAL, "w > %d", MAXW);
   const int nc = n_y + (with_ones ? 1 : 0);
-  const int64_t G = (p.d == 1) ? p.N : static_cast<int64_t>(p.N) * p.N;
+  int64_t G = 1;
+  for (int l = 0; l < p.d; ++l) G *= p.N;
   FK_CUDA(cudaMemsetAsync(grid, 0, sizeof(double) * G * nc, st));
   if (n == 0) return FK_OK;
   const int block = 256;
@@ -129,8 +141,11 @@ template <typename R>
 __global__ void k_t2_place(int d, int N, int kc, int corr_off, const double* coef, int n_sets,
                            const double* corr, cplx<R>* G) {
   const int K = 2 * kc + 1;
-  const int64_t D = (d == 1) ? K : static_cast<int64_t>(K) * K;
-  const int64_t GN = (d == 1) ? N : static_cast<int64_t>(N) * N;
+  int64_t D = 1, GN = 1;
+  for (int l = 0; l < d; ++l) {
+    D *= K;
+    GN *= N;
+  }
   const int64_t total = D * n_sets;
   for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
        t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -142,10 +157,17 @@ __global__ void k_t2_place(int d, int N, int kc, int corr_off, const double* coe
       const int k = static_cast<int>(q) - kc;
       f = corr[q + corr_off];
       node = (k + N) & (N - 1);
-    } else {
+    } else if (d == 2) {
       const int a = static_cast<int>(q / K), b = static_cast<int>(q - static_cast<int64_t>(a) * K);
       f = corr[a + corr_off] * corr[b + corr_off];
       node = static_cast<int64_t>((a - kc + N) & (N - 1)) * N + ((b - kc + N) & (N - 1));
+    } else {
+      const int a = static_cast<int>(q / (static_cast<int64_t>(K) * K));
+      const int64_t rem = q - static_cast<int64_t>(a) * K * K;
+      const int b = static_cast<int>(rem / K), c = static_cast<int>(rem - static_cast<int64_t>(b) * K);
+      f = corr[a + corr_off] * corr[b + corr_off] * corr[c + corr_off];
+      node = (static_cast<int64_t>((a - kc + N) & (N - 1)) * N + ((b - kc + N) & (N - 1))) * N +
+             ((c - kc + N) & (N - 1));
     }
     cplx<R> v;
     v.x = static_cast<R>(coef[2 * t] * f);
@@ -158,11 +180,12 @@ template <typename R>
 __global__ void k_t2_interp(int d, Win<R> win, R beta, int64_t n, const R* __restrict__ x, int n_sets,
                             const cplx<R>* __restrict__ G, double* out, unsigned* flags) {
   const int N = win.N, w = win.W;
-  const int64_t GN = (d == 1) ? N : static_cast<int64_t>(N) * N;
+  int64_t GN = 1;
+  for (int l = 0; l < d; ++l) GN *= N;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    R ker[2][MAXW];
-    int l0[2];
+    R ker[3][MAXW];
+    int l0[3];
     bool ok = true;
     for (int l = 0; l < d; ++l) {
       R f;
@@ -179,12 +202,24 @@ __global__ void k_t2_interp(int d, Win<R> win, R beta, int64_t n, const R* __res
       double acc = 0.0;
       if (d == 1) {
         for (int a = 0; a < w; ++a) acc += static_cast<double>(ker[0][a]) * static_cast<double>(g[wrap_node(l0[0] + a, N)].x);
-      } else {
+      } else if (d == 2) {
         for (int a = 0; a < w; ++a) {
           const int r = wrap_node(l0[0] + a, N);
           R row = R(0);
           for (int b = 0; b < w; ++b) row += ker[1][b] * g[static_cast<int64_t>(r) * N + (wrap_node(l0[1] + b, N))].x;
           acc += static_cast<double>(ker[0][a]) * static_cast<double>(row);
+        }
+      } else {
+        for (int a = 0; a < w; ++a) {
+          const int64_t r = wrap_node(l0[0] + a, N);
+          R plane = R(0);
+          for (int b = 0; b < w; ++b) {
+            const int64_t rb = r * N + wrap_node(l0[1] + b, N);
+            R row = R(0);
+            for (int c = 0; c < w; ++c) row += ker[2][c] * g[rb * N + wrap_node(l0[2] + c, N)].x;
+            plane += ker[1][b] * row;
+          }
+          acc += static_cast<double>(ker[0][a]) * static_cast<double>(plane);
         }
       }
       out[s * n + i] = acc;
@@ -195,10 +230,11 @@ __global__ void k_t2_interp(int d, Win<R> win, R beta, int64_t n, const R* __res
 template <typename R>
 fk_status type2_eval(const EsPlan& p, int kmax_c, const double* coef, int n_sets, int64_t n, const R* x,
                      const double* corr, double* out, unsigned* flags, cudaStream_t st, Scratch& scratch) {
-  if (p.d < 1 || p.d > 2) return set_error(FK_EINVAL, "type 2: d = %d not built", p.d);
+  if (p.d < 1 || p.d > 3) return set_error(FK_EINVAL, "type 2: d = %d not built", p.d);
   if (kmax_c > p.kmax) return set_error(FK_EINTERNAL, "type 2: kmax_c > plan kmax");
   const int N = p.N;
-  const int64_t GN = (p.d == 1) ? N : static_cast<int64_t>(N) * N;
+  int64_t GN = 1;
+  for (int l = 0; l < p.d; ++l) GN *= N;
   cplx<R>* G = nullptr;
   double* tw = nullptr;
   FK_TRY(scratch.alloc(&G, GN * n_sets));
@@ -206,11 +242,19 @@ fk_status type2_eval(const EsPlan& p, int kmax_c, const double* coef, int n_sets
   FK_TRY(fft_twiddles(N, tw, st));
   FK_CUDA(cudaMemsetAsync(G, 0, sizeof(cplx<R>) * GN * n_sets, st));
   const int K = 2 * kmax_c + 1;
-  const int64_t D = (p.d == 1) ? K : static_cast<int64_t>(K) * K;
+  int64_t D = 1;
+  for (int l = 0; l < p.d; ++l) D *= K;
   k_t2_place<R><<<grid_for(D * n_sets, 256), 256, 0, st>>>(p.d, N, kmax_c, p.kmax - kmax_c, coef, n_sets, corr, G); note_launch();
   FK_CUDA(cudaGetLastError());
   if (p.d == 1) {
     FK_TRY(fft_lines<R>(G, N, n_sets, N, 1, +1, tw, st));
+  } else if (p.d == 3) {
+    // every line of each dimension: last, middle (one call per first index), first
+    const int64_t NN = static_cast<int64_t>(N) * N;
+    FK_TRY(fft_lines<R>(G, N, static_cast<int64_t>(n_sets) * NN, N, 1, +1, tw, st));
+    for (int64_t s2 = 0; s2 < static_cast<int64_t>(n_sets) * N; ++s2)
+      FK_TRY(fft_lines<R>(G + s2 * NN, N, N, 1, N, +1, tw, st));
+    for (int sidx = 0; sidx < n_sets; ++sidx) FK_TRY(fft_lines<R>(G + sidx * GN, N, NN, 1, NN, +1, tw, st));
   } else {
     // columns first (only the K nonzero ones per set), then every row
     for (int s = 0; s < n_sets; ++s) {
