@@ -142,6 +142,17 @@ FK_API fk_status fk_fit_sobolev(int d, int64_t n, const void* x, const void* y, 
                          double eps, int precision, const fk_opts* opts,
                          double* theta, void* stream, fk_report* rep);
 
+/* Sweep over pairs (s_i, lambda_i) of the Sobolev or low-bias estimator from one
+ * spreading pass (Sec. 3 experiments sweep s and lambda): penalty row i is
+ * lambda_i (c0 + |k|^{2 s_i}) (or lambda_i for FK_PEN_LOWBIAS), and all n_pairs x
+ * n_targets systems share T and b and are solved in one batch.
+ *   s_values, lambdas: host, n_pairs;  theta: device, [n_pairs][n_targets][D] complex.
+ *   Other arguments as fk_fit_sobolev. */
+FK_API fk_status fk_fit_sobolev_pairs(int d, int64_t n, const void* x, const void* y, int n_targets, int m,
+                                      const double* s_values, const double* lambdas, int n_pairs, int penalty,
+                                      double eps, int precision, const fk_opts* opts, double* theta,
+                                      void* stream, fk_report* rep);
+
 /* Physics-informed estimator (Sec. 4, tractable domain = full period):
  *   W_k = lambda (c0 + |k|^{2s}) + mu |P(ik)|^2,  P(ik) = sum_t a_t prod_l (i k_l)^{alpha_t,l}.
  *   alpha: host, n_terms x d non-negative ints; a: host, n_terms reals.

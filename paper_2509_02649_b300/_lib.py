@@ -30,7 +30,7 @@ EXPORTS = ["fk_default_opts", "fk_fit_sobolev", "fk_fit_pik", "fk_fit_additive",
            "fk_workspace_bytes", "fk_version", "fk_launch_count", "fk_type1_noalloc", "fk_penalty_grads",
            "fk_accum_create", "fk_accum_add", "fk_accum_system", "fk_accum_fit_sobolev", "fk_accum_reset",
            "fk_accum_destroy", "fk_generate_sweep_1d", "fk_release_workspace", "fk_autotune_table",
-           "fk_autotune_clear", "fk_fit_pik_general", "fk_box_moments"]
+           "fk_autotune_clear", "fk_fit_pik_general", "fk_box_moments", "fk_fit_sobolev_pairs"]
 
 
 class FkError(RuntimeError):
@@ -99,6 +99,7 @@ def lib() -> ctypes.CDLL:
             "fk_autotune_clear": (None, []),
             "fk_fit_pik_general": (_I, [_I, _L, _P, _P, _I, _I, _D, _D, _D, _I, _P, _P, _P, _D, _I, _P, _P, _P, _P]),
             "fk_box_moments": (_I, [_I, _I, _P, _P, _P, _P]),
+            "fk_fit_sobolev_pairs": (_I, [_I, _L, _P, _P, _I, _I, _P, _P, _I, _I, _D, _I, _P, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -451,4 +452,22 @@ def fk_fit_pik_general(x, y, m: int, s: float, lam: float, mu: float, alpha, a, 
     _check(lib().fk_fit_pik_general(d, n, x.data_ptr(), y.data_ptr(), y.shape[0], m, s, lam, mu, len(a), alpha_arr,
                                     _dbl_array(a), c.data_ptr(), eps, p, _opts_ptr(opts), theta.data_ptr(), _stream(),
                                     ctypes.byref(rep) if report else None))
+    return (theta, rep.as_dict()) if report else theta
+
+
+def fk_fit_sobolev_pairs(x, y, m: int, s_values, lambdas, eps: float, precision="mixed",
+                         penalty: int = FK_PEN_SOBOLEV, opts: Optional[Opts] = None, report: bool = False):
+    """theta [n_pairs][n_targets][D]: one fit per (s_i, lambda_i) from one spreading pass."""
+    p = _prec(precision)
+    x = _points(x, p)
+    d, n = x.shape
+    y = y.reshape(-1, n).contiguous()
+    sv, lv = [float(v) for v in s_values], [float(v) for v in lambdas]
+    if len(sv) != len(lv):
+        raise ValueError("s_values and lambdas differ in length")
+    theta = torch.empty((len(sv), y.shape[0], (2 * m + 1) ** d), dtype=torch.complex128, device=x.device)
+    rep = Report()
+    _check(lib().fk_fit_sobolev_pairs(d, n, x.data_ptr(), y.data_ptr(), y.shape[0], m, _dbl_array(sv), _dbl_array(lv),
+                                      len(sv), penalty, eps, p, _opts_ptr(opts), theta.data_ptr(), _stream(),
+                                      ctypes.byref(rep) if report else None))
     return (theta, rep.as_dict()) if report else theta

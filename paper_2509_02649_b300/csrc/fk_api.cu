@@ -447,6 +447,58 @@ fk_status fk_fit_pik(int d, int64_t n, const void* x, const void* y, int n_targe
                     opts, theta, stream, rep);
 }
 
+fk_status fk_fit_sobolev_pairs(int d, int64_t n, const void* x, const void* y, int n_targets, int m,
+                               const double* s_values, const double* lambdas, int n_pairs, int penalty, double eps,
+                               int precision, const fk_opts* opts, double* theta, void* stream, fk_report* rep) {
+  clear_error();
+  FK_TRY(check_common(d, n, m, eps, precision));
+  if (!x || !y || !theta || !s_values || !lambdas || n_targets < 1 || n_pairs < 1)
+    return set_error(FK_EINVAL, "bad fit arguments");
+  if (penalty != FK_PEN_SOBOLEV && penalty != FK_PEN_LOWBIAS) return set_error(FK_EINVAL, "unknown penalty");
+  for (int i = 0; i < n_pairs; ++i) {
+    if (!(lambdas[i] >= 0.0)) return set_error(FK_EINVAL, "lambda[%d] = %g < 0", i, lambdas[i]);
+    if (!(s_values[i] >= 0.0)) return set_error(FK_EINVAL, "s[%d] = %g < 0", i, s_values[i]);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const fk_opts o = resolve_opts(opts);
+  Scratch scr(st);
+  Flags fl(st);
+  FK_TRY(fl.init(scr));
+  Timer tm(st, rep != nullptr);
+  KernelTimerScope kts(rep != nullptr);
+  tm.mark();
+  const int64_t D = ipow(2 * m + 1, d), M2 = ipow(4 * m + 1, d);
+  double *T, *b, *W;
+  FK_TRY(scr.alloc(&T, 2 * M2));
+  FK_TRY(scr.alloc(&b, 2 * D * n_targets));
+  FK_TRY(scr.alloc(&W, D * n_pairs));
+  EsPlan p;
+  FK_TRY(build_system(d, n, x, y, n_targets, m, eps, precision, o, T, b, st, scr, fl.dev, &p, &tm));
+  // one penalty row per (s, lambda) pair; all rows share T and b (one spreading pass)
+  for (int i = 0; i < n_pairs; ++i)
+    FK_TRY(penalty_weights(d, m, penalty, s_values[i], o.sobolev_c0, lambdas + i, 1, 0.0, 0, nullptr, nullptr,
+                           W + static_cast<int64_t>(i) * D, st));
+  int iters = 0;
+  double rr = 0;
+  FK_TRY(solve_system(d, m, T, W, n_pairs, b, n_targets, o, theta, st, scr, fl.dev, &iters, &rr));
+  tm.mark();
+  FK_TRY(fl.check());
+  if (rep) {
+    *rep = fk_report{};
+    rep->ms_spread = tm.ms(1, 2);
+    rep->ms_fft = tm.ms(2, 3);
+    rep->ms_solve = tm.ms(3, 4);
+    rep->ms_total = tm.ms(0, 4);
+    rep->cg_iters = iters;
+    rep->rel_residual = rr;
+    rep->n_used = n;
+    rep->fine_grid = p.N;
+    rep->kernel_width = p.w;
+    rep->ms_kernel = kts.ms();
+  }
+  return FK_OK;
+}
+
 fk_status fk_fit_pik_general(int d, int64_t n, const void* x, const void* y, int n_targets, int m, double s,
                              double lambda, double mu, int n_terms, const int* alpha, const double* a,
                              const double* c_moments, double eps, int precision, const fk_opts* opts, double* theta,

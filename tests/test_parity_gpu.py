@@ -277,3 +277,18 @@ def test_binned_spreader_clustered_points(n):
     bo = O.rhs(x.astype(np.float64), y.astype(np.float64), m)
     assert rel(host(T), To) <= 10 * eps
     assert rel(host(b)[0], bo) <= 10 * eps
+
+
+@pytest.mark.parametrize("d,m,solver", [(1, 30, "cg"), (2, 10, "chol"), (2, 12, "cg")])
+def test_sobolev_pairs_sweep(d, m, solver):
+    # 6 (s, lambda) pairs from one spreading pass, each against its own oracle fit
+    n = 8000
+    x = S.uniform_points(n, d, 61)
+    y = (np.sin(x[0]) * (np.cos(x[1]) if d == 2 else 1.0) + 0.1 * np.random.default_rng(4).standard_normal(n))
+    pairs = [(0.5, 1e-3), (1.0, 1e-3), (1.5, 1e-4), (2.0, 1e-5), (2.5, 1e-2), (1.25, 3e-4)]
+    opts = fk.default_opts(solver=fk.FK_SOLVER_CHOL if solver == "chol" else fk.FK_SOLVER_CG, cg_tol=1e-13)
+    th = fk.fk_fit_sobolev_pairs(dev(x, torch.float64), dev(y, torch.float64), m, [p[0] for p in pairs],
+                                 [p[1] for p in pairs], 1e-12, "fp64", opts=opts).cpu().numpy()
+    for i, (s, lam) in enumerate(pairs):
+        want = O.fit(x, y, m, O.penalty_sobolev(d, m, lam, s))
+        assert rel(th[i, 0], want) < 1e-9, (s, lam)
