@@ -10,6 +10,7 @@
 // evaluated by Gauss-Legendre quadrature whose nodes come from Newton's method on
 // the Legendre recurrence, all in fp64 on the device.
 #include "fk_internal.cuh"
+#include "es_poly.cuh"
 
 #include <map>
 #include <mutex>
@@ -161,5 +162,47 @@ fk_status es_correction_into(const EsPlan& p, double* corr, double* gl_scratch, 
 }
 
 int es_gl_nodes() { return GL_Q; }
+
+}  // namespace fk
+
+namespace fk {
+
+// Chebyshev interpolation of each tap at the 9 Chebyshev points of (-1/2, 1/2), then
+// the change of basis to powers of g (T_0 = 1, T_1 = u, T_{k+1} = 2 u T_k - T_{k-1},
+// u = 2 g), in fp64.
+EsPoly es_poly(int w, double beta) {
+  constexpr int P = ES_POLY_DEG, NP = P + 1;
+  EsPoly out{};
+  const double c = 0.5 * (w - 1);
+  auto phi = [&](double z) {
+    const double t = 1.0 - z * z;
+    return t > 0.0 ? std::exp(beta * (std::sqrt(t) - 1.0)) : 0.0;
+  };
+  // monomial coefficients of T_k(u), k = 0..P
+  double Tm[NP][NP] = {};
+  Tm[0][0] = 1.0;
+  Tm[1][1] = 1.0;
+  for (int k = 1; k + 1 < NP; ++k)
+    for (int j = 0; j < NP; ++j) Tm[k + 1][j] = (j > 0 ? 2.0 * Tm[k][j - 1] : 0.0) - Tm[k - 1][j];
+  for (int a = 0; a < (w + 1) / 2 && a < ES_POLY_MAXW / 2; ++a) {
+    double v[NP], ch[NP], mono[NP] = {};
+    for (int j = 0; j < NP; ++j) {
+      const double u = std::cos(M_PI * (j + 0.5) / NP);
+      v[j] = phi((a - c - 0.5 * u) * 2.0 / w);
+    }
+    for (int k = 0; k < NP; ++k) {
+      double s = 0.0;
+      for (int j = 0; j < NP; ++j) s += v[j] * std::cos(M_PI * k * (j + 0.5) / NP);
+      ch[k] = (k == 0 ? 1.0 : 2.0) * s / NP;
+    }
+    for (int k = 0; k < NP; ++k)
+      for (int j = 0; j < NP; ++j) mono[j] += ch[k] * Tm[k][j];
+    // powers of u = 2 g  ->  powers of g
+    for (int j = 0; j < NP; ++j) mono[j] *= std::ldexp(1.0, j);
+    for (int j = 0; j < 5; ++j) out.e[a][j] = static_cast<float>(mono[2 * j]);
+    for (int j = 0; j < 4; ++j) out.o[a][j] = static_cast<float>(mono[2 * j + 1]);
+  }
+  return out;
+}
 
 }  // namespace fk

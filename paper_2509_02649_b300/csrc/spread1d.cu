@@ -23,6 +23,7 @@
 // last kernel scales back into the fp64 grid.
 #include "fk_internal.cuh"
 #include "window.cuh"
+#include "es_poly.cuh"
 
 namespace fk {
 
@@ -44,7 +45,7 @@ struct Fx1dArgs {
   int with_ones;
   int N;
   float c_hi, c_lo;   // N / (2 pi) as a float pair
-  float bl;           // beta log2(e)
+  EsPoly poly;        // tap polynomials of the plan's width
   int ngrp;
   int grp_c0[MAXGRP];  // first channel of each group (channel 0 = ones when with_ones)
   int grp_nc[MAXGRP];
@@ -54,18 +55,6 @@ struct Fx1dArgs {
   unsigned long long* acc; // [nc][N] int64 accumulators
   unsigned* flags;
 };
-
-__device__ __forceinline__ float rsqrt_ap(float v) {
-  float r;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
-  return r;
-}
-
-__device__ __forceinline__ float ex2_ap(float v) {
-  float r;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
-  return r;
-}
 
 // hi-word change of one low-word add: qsign + carry out of (old + q), where qsign is
 // the sign extension (0 or -1) of q
@@ -113,7 +102,6 @@ __global__ void __launch_bounds__(THREADS) k_spread1d_fx(Fx1dArgs A) {
   }
   __syncthreads();
 
-  const float sc = 2.0f / W;
   // one point: window, W weights, then per channel W low-word adds in flight before
   // the (rare) carries are settled
   auto one = [&](float xv, const float* yv) {
@@ -124,13 +112,7 @@ __global__ void __launch_bounds__(THREADS) k_spread1d_fx(Fx1dArgs A) {
       return;
     }
     float psi[W];
-    const float z0 = -f * sc;
-#pragma unroll
-    for (int a = 0; a < W; ++a) {
-      const float z = fmaf(static_cast<float>(a), sc, z0);
-      const float t = fmaxf(fmaf(-z, z, 1.0f), 1e-30f);
-      psi[a] = ex2_ap(fmaf(A.bl, t * rsqrt_ap(t), -A.bl));
-    }
+    es_taps_poly<W>(f - 0.5f * static_cast<float>(W - 1), A.poly, psi);
     const int b = wrap_node(l0, N);
 #pragma unroll
     for (int c = 0; c < CG; ++c) {
@@ -331,7 +313,7 @@ fk_status spread1d_run(const EsPlan& p, int64_t n, const float* x, const float* 
   const CoordConst cc = coord_const(N);
   A.c_hi = cc.hi;
   A.c_lo = cc.lo;
-  A.bl = static_cast<float>(p.beta * 1.4426950408889634);
+  A.poly = es_poly(p.w, p.beta);
   A.ngrp = ngrp;
   A.flags = flags;
   A.vec = ((reinterpret_cast<uintptr_t>(x) & 15) == 0 && (n & 3) == 0 &&

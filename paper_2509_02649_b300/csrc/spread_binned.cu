@@ -30,6 +30,7 @@
 //                 register window into the fp64 grid.
 #include "fk_internal.cuh"
 #include "window.cuh"
+#include "es_poly.cuh"
 
 namespace fk {
 
@@ -42,38 +43,6 @@ constexpr int THREADS_ACC = 448;                 // accumulation CTA size (one C
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ float rsqrt_approx(float v) {
-  float r;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
-  return r;
-}
-
-__device__ __forceinline__ float sqrt_approx(float v) {
-  float r;
-  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
-  return r;
-}
-
-__device__ __forceinline__ float ex2_approx(float v) {
-  float r;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
-  return r;
-}
-
-// ES weights of one coordinate from its fractional offset f in (w/2 - 1, w/2]:
-// psi_a = 2^(bl (sqrt(1 - z_a^2) - 1)), bl = beta log2(e), z_a = (a - f) 2 / w.
-template <int W>
-__device__ __forceinline__ void es_taps(float f, float bl, float* out) {
-  const float sc = 2.0f / W;
-  const float z0 = -f * sc;
-#pragma unroll
-  for (int a = 0; a < W; ++a) {
-    const float z = fmaf(static_cast<float>(a), sc, z0);
-    const float t = fmaxf(fmaf(-z, z, 1.0f), 0.0f);
-    out[a] = ex2_approx(fmaf(bl, sqrt_approx(t), -bl));
-  }
 }
 
 __device__ __forceinline__ bool wait_counter(const int* ctr, int target, unsigned* flags) {
@@ -649,6 +618,7 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter1(PartArgs A) {
 struct AccArgs {
   int N, G, cells_per, ncells;
   float beta;
+  EsPoly poly;  // tap polynomials of the plan's width
   int with_ones;
   const int* tot;   // [G]
   const uint4* rec;
@@ -692,7 +662,7 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
   const int my_first_cell = b * cpc;
   const int my_ncells = max(0, min(cpc, A.ncells - my_first_cell));
   const bool owns = cell < my_ncells;
-  const float bl = A.beta * 1.4426950408889634f;
+  const float gc = 0.5f * static_cast<float>(W - 1);  // window centre: g = f - gc
   const AccLayout L = acc_layout(cpc);
   uint4* stage = reinterpret_cast<uint4*>(smem + L.stage);
   unsigned short* nxt = reinterpret_cast<unsigned short*>(smem + L.nxt);
@@ -824,8 +794,8 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
           const uint4 rb = st[rj];
           ri = nxt[rj];
           float ea[W], eb[W];
-          es_taps<W>(__uint_as_float(ch == 0 ? ra.y : ra.z), bl, ea);
-          es_taps<W>(__uint_as_float(ch == 0 ? rb.y : rb.z), bl, eb);
+          es_taps_poly<W>(__uint_as_float(ch == 0 ? ra.y : ra.z) - gc, A.poly, ea);
+          es_taps_poly<W>(__uint_as_float(ch == 0 ? rb.y : rb.z) - gc, A.poly, eb);
           const float wa = (ch == 0) ? 1.0f : __uint_as_float(ra.w);
           const float wb = (ch == 0) ? 1.0f : __uint_as_float(rb.w);
 #pragma unroll
@@ -840,7 +810,7 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
           const uint4 ra = st[ri];
           ri = nxt[ri];
           float ea[W];
-          es_taps<W>(__uint_as_float(ch == 0 ? ra.y : ra.z), bl, ea);
+          es_taps_poly<W>(__uint_as_float(ch == 0 ? ra.y : ra.z) - gc, A.poly, ea);
           const float wa = (ch == 0) ? 1.0f : __uint_as_float(ra.w);
 #pragma unroll
           for (int j = 0; j < W; ++j) {
@@ -854,8 +824,8 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
           const uint4 rec = st[ri];
           ri = nxt[ri];
           float px[W], py[W];
-          es_taps<W>(__uint_as_float(rec.y), bl, px);
-          es_taps<W>(__uint_as_float(rec.z), bl, py);
+          es_taps_poly<W>(__uint_as_float(rec.y) - gc, A.poly, px);
+          es_taps_poly<W>(__uint_as_float(rec.z) - gc, A.poly, py);
           const float sv = A.with_ones ? 1.0f : __uint_as_float(rec.w);
 #pragma unroll
           for (int i = 0; i < W; ++i) {
@@ -1016,6 +986,7 @@ fk_status spread_binned_run(const EsPlan& p, int64_t n, const float* x, const fl
   A.cells_per = cpc;
   A.ncells = static_cast<int>(ncells);
   A.beta = static_cast<float>(p.beta);
+  A.poly = es_poly(p.w, p.beta);
   A.with_ones = with_ones ? 1 : 0;
   A.tot = P.tot;
   A.rec = P.rec;
