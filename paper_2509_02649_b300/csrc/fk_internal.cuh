@@ -60,6 +60,16 @@ __host__ __device__ inline cd cmul(cd a, cd b) { return cd{a.x * b.x - a.y * b.y
 __host__ __device__ inline cd cconjmul(cd a, cd b) { return cd{a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x}; }  // conj(a)*b
 __host__ __device__ inline cd cscale(cd a, double s) { return cd{a.x * s, a.y * s}; }
 __host__ __device__ inline cd cconj(cd a) { return cd{a.x, -a.y}; }
+// acc + a b, acc + a conj(b), acc + conj(a) b: four FMAs each
+__host__ __device__ inline cd cfma(cd a, cd b, cd acc) {
+  return cd{fma(-a.y, b.y, fma(a.x, b.x, acc.x)), fma(a.y, b.x, fma(a.x, b.y, acc.y))};
+}
+__host__ __device__ inline cd cfma_cj(cd a, cd b, cd acc) {
+  return cd{fma(a.y, b.y, fma(a.x, b.x, acc.x)), fma(-a.x, b.y, fma(a.y, b.x, acc.y))};
+}
+__host__ __device__ inline cd cjfma(cd a, cd b, cd acc) {
+  return cd{fma(a.y, b.y, fma(a.x, b.x, acc.x)), fma(-a.y, b.x, fma(a.x, b.y, acc.y))};
+}
 
 template <typename R> struct cplx { R x, y; };
 

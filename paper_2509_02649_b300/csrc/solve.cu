@@ -256,13 +256,28 @@ __global__ void k_assemble(int d, int m, const double* T, const double* W, doubl
 // ---------------------------------------------------------------- Cholesky
 constexpr int NB = 32;
 
-__global__ void k_chol_diag(double* A, int64_t D, int kb, int nb, unsigned* flags, double* Linv) {
+// Factor the nb x nb diagonal block in place (one CTA).  Step j takes the pivot, scales
+// column j and updates the trailing lower triangle; the entries (i, k), k > j, i >= k,
+// listed with k descending, make step j's active set a prefix of one table, so only
+// warps with work issue (this part's FP64 pipe costs the same per warp instruction
+// whatever the number of active lanes).
+__global__ void k_chol_diag(double* A, int64_t D, int kb, int nb, unsigned* flags) {
   __shared__ cd s[NB][NB + 1];
+  __shared__ double rdiag[NB];                  // 1 / L_jj: one FP64 division per pivot
+  __shared__ unsigned short tab[NB * (NB + 1) / 2];  // (i << 8) | k
   const int tid = threadIdx.x;
   for (int t = tid; t < nb * nb; t += blockDim.x) {
     const int i = t / nb, j = t % nb;
     const double* p = A + 2 * ((kb + i) * D + (kb + j));
     s[i][j] = cd{p[0], p[1]};
+  }
+  for (int t = tid; t < (nb - 1) * nb / 2; t += blockDim.x) {
+    int k = nb - 1, before = 0;  // group k holds the nb - k entries (k .. nb - 1, k)
+    while (t >= before + (nb - k)) {
+      before += nb - k;
+      --k;
+    }
+    tab[t] = static_cast<unsigned short>(((k + t - before) << 8) | k);
   }
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
@@ -272,15 +287,18 @@ __global__ void k_chol_diag(double* A, int64_t D, int kb, int nb, unsigned* flag
         atomicOr(flags, FLAG_NOTPD);
         piv = 1.0;
       }
-      s[j][j] = cd{sqrt(piv), 0.0};
+      const double r = rsqrt(piv);  // one FP64 sequence for both the pivot and its inverse
+      s[j][j] = cd{piv * r, 0.0};
+      rdiag[j] = r;
     }
     __syncthreads();
-    const double inv = 1.0 / s[j][j].x;
+    const double inv = rdiag[j];
     for (int i = j + 1 + tid; i < nb; i += blockDim.x) s[i][j] = cscale(s[i][j], inv);
     __syncthreads();
-    for (int t = tid; t < nb * nb; t += blockDim.x) {
-      const int i = t / nb, k = t % nb;
-      if (i > j && k > j && k <= i) s[i][k] = csub(s[i][k], cmul(s[i][j], cconj(s[k][j])));
+    const int act = (nb - 1 - j) * (nb - j) / 2;  // entries with k > j
+    for (int t = tid; t < act; t += blockDim.x) {
+      const int i = tab[t] >> 8, k = tab[t] & 0xFF;
+      s[i][k] = cfma_cj(cd{-s[i][j].x, -s[i][j].y}, s[k][j], s[i][k]);
     }
     __syncthreads();
   }
@@ -295,34 +313,43 @@ __global__ void k_chol_diag(double* A, int64_t D, int kb, int nb, unsigned* flag
       p[1] = 0.0;
     }
   }
-  if (Linv) {
-    // inverse of the lower-triangular block by forward substitution L v = e_c, for the
-    // panel update as a product: 8 threads per column c share each step's inner sum
-    // (FP64 work spread over the whole CTA; this part's FP64 rate is low per warp)
-    __shared__ cd v[NB][NB + 1];
-    const int c = tid >> 3, sub = tid & 7;
-    for (int i = 0; i < nb; ++i) {
-      cd acc = cd{0.0, 0.0};
-      if (c < nb)
-        for (int p = c + sub; p < i; p += 8) acc = cadd(acc, cmul(s[i][p], v[p][c]));
-#pragma unroll
-      for (int o = 4; o > 0; o >>= 1) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-      }
-      if (c < nb && sub == 0) {
-        const cd rhs = (i == c) ? cd{1.0, 0.0} : cd{0.0, 0.0};
-        v[i][c] = (i < c) ? cd{0.0, 0.0} : cscale(csub(rhs, acc), 1.0 / s[i][i].x);
-      }
-      __syncthreads();
-    }
-    for (int t = tid; t < NB * NB; t += blockDim.x) {
-      const int i = t / NB, j = t % NB;
-      const cd val = (i < nb && j < nb) ? v[i][j] : cd{0.0, 0.0};
-      Linv[2 * t] = val.x;
-      Linv[2 * t + 1] = val.y;
-    }
+}
+
+// Inverse of the factored diagonal block, one column per CTA (one warp) so that the
+// FP64 work spreads over nb SMs: L v = e_c by right-looking substitution, lane i
+// holding v_i; after v_p is known every lane i > p takes away L_ip v_p.
+// Linv: [NB][NB] complex, zero above the diagonal and beyond nb.
+static_assert(NB == 32, "one lane per row of a diagonal block");
+__global__ void k_chol_inv(const double* A, int64_t D, int kb, int nb, double* Linv) {
+  __shared__ cd s[NB][NB + 1];
+  const int c = blockIdx.x, lane = threadIdx.x;
+  for (int t = lane; t < nb * nb; t += 32) {
+    const int i = t / nb, j = t % nb;
+    const double* p = A + 2 * ((kb + i) * D + (kb + j));
+    s[i][j] = (j <= i) ? cd{p[0], p[1]} : cd{0.0, 0.0};
   }
+  __syncwarp();
+  const double rd = (lane < nb) ? 1.0 / s[lane][lane].x : 0.0;
+  cd acc = cd{(lane == c) ? 1.0 : 0.0, 0.0};
+  cd v = cd{0.0, 0.0};
+  for (int p = c; p < nb; ++p) {
+    if (lane == p) v = cscale(acc, rd);
+    const cd vp = cd{__shfl_sync(0xffffffffu, v.x, p), __shfl_sync(0xffffffffu, v.y, p)};
+    if (lane > p && lane < nb) acc = cfma(cd{-s[lane][p].x, -s[lane][p].y}, vp, acc);
+  }
+  // column c of the inverse: rows lane >= c
+  const cd val = (lane < nb && lane >= c) ? v : cd{0.0, 0.0};
+  Linv[2 * (lane * NB + c)] = val.x;
+  Linv[2 * (lane * NB + c) + 1] = val.y;
+}
+
+// columns c >= nb of the inverse are zero
+__global__ void k_chol_inv_pad(int nb, double* Linv) {
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x)
+    if (t % NB >= nb) {
+      Linv[2 * t] = 0.0;
+      Linv[2 * t + 1] = 0.0;
+    }
 }
 
 // rows i >= kb + nb of the panel: x L11^H = a  =>  x_j = (a_j - sum_{p<j} x_p conj(L11[j][p])) / L11[j][j]
@@ -349,29 +376,35 @@ __global__ void k_chol_panel(double* A, int64_t D, int kb, int nb) {
   }
 }
 
-// A22[i][j] -= sum_p L21[i][p] conj(L21[j][p]),  lower triangle, 32x32 tiles
-__global__ void k_chol_update(double* A, int64_t D, int kb, int nb) {
+// A22[i][j] -= sum_p L21[i][p] conj(L21[j][p]),  lower triangle, TT x TT tiles
+template <int TT>
+__global__ void __launch_bounds__(256) k_chol_update(double* A, int64_t D, int kb, int nb) {
   const int64_t base = kb + nb;
   const int ti = blockIdx.y, tj = blockIdx.x;
   if (tj > ti) return;
-  const int64_t i0 = base + static_cast<int64_t>(ti) * 32, j0 = base + static_cast<int64_t>(tj) * 32;
-  __shared__ cd Li[32][NB + 1], Lj[32][NB + 1];
-  for (int t = threadIdx.x; t < 32 * nb; t += blockDim.x) {
+  const int64_t i0 = base + static_cast<int64_t>(ti) * TT, j0 = base + static_cast<int64_t>(tj) * TT;
+  __shared__ cd Li[TT][NB + 1], Lj[TT][NB + 1];
+  for (int t = threadIdx.x; t < TT * nb; t += blockDim.x) {
     const int r = t / nb, p = t % nb;
     const int64_t gi = i0 + r, gj = j0 + r;
     Li[r][p] = (gi < D) ? cd{A[2 * (gi * D + kb + p)], A[2 * (gi * D + kb + p) + 1]} : cd{0, 0};
     Lj[r][p] = (gj < D) ? cd{A[2 * (gj * D + kb + p)], A[2 * (gj * D + kb + p) + 1]} : cd{0, 0};
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
-    const int r = t / 32, c = t % 32;
+  for (int t = threadIdx.x; t < TT * TT; t += blockDim.x) {
+    const int r = t / TT, c = t % TT;
     const int64_t gi = i0 + r, gj = j0 + c;
     if (gi >= D || gj >= D || gj > gi) continue;
-    cd acc = cd{0, 0};
-    for (int p = 0; p < nb; ++p) acc = cadd(acc, cmul(Li[r][p], cconj(Lj[c][p])));
+    cd a0 = cd{0, 0}, a1 = cd{0, 0};
+    int p = 0;
+    for (; p + 1 < nb; p += 2) {
+      a0 = cfma_cj(Li[r][p], Lj[c][p], a0);
+      a1 = cfma_cj(Li[r][p + 1], Lj[c][p + 1], a1);
+    }
+    if (p < nb) a0 = cfma_cj(Li[r][p], Lj[c][p], a0);
     double* q = A + 2 * (gi * D + gj);
-    q[0] -= acc.x;
-    q[1] -= acc.y;
+    q[0] -= a0.x + a1.x;
+    q[1] -= a0.y + a1.y;
   }
 }
 
@@ -396,26 +429,50 @@ __global__ void k_chol_panel_mm(double* A, int64_t D, int kb, int nb, const doub
     const int64_t row = r0 + r;
     if (row >= D || j >= nb) continue;
     cd acc = cd{0, 0};
-    for (int p = 0; p <= j; ++p) acc = cadd(acc, cmul(At[r][p], cconj(Li[j][p])));
+    for (int p = 0; p <= j; ++p) acc = cfma_cj(At[r][p], Li[j][p], acc);
     A[2 * (row * D + kb + j)] = acc.x;
     A[2 * (row * D + kb + j) + 1] = acc.y;
   }
 }
 
+// Blocked right-looking Cholesky A = L L^H in place (lower triangle; the strict upper
+// triangle is zeroed).  linv (optional): [ceil(D / NB)][NB][NB] complex, receives the
+// inverse of every diagonal block (zero-padded); the panel update and the triangular
+// solves use them as products.
+static int64_t linv_blocks(int64_t D) { return (D + NB - 1) / NB; }
+
 static fk_status cholesky(double* A, int64_t D, unsigned* flags, cudaStream_t st, double* linv) {
+  int sms = 0, dev = 0;
+  FK_CUDA(cudaGetDevice(&dev));
+  FK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   for (int kb = 0; kb < D; kb += NB) {
     const int nb = static_cast<int>(std::min<int64_t>(NB, D - kb));
     const int64_t rest = D - kb - nb;
-    k_chol_diag<<<1, 256, 0, st>>>(A, D, kb, nb, flags, (rest > 0 && linv) ? linv : nullptr); note_launch();
+    double* li = linv ? linv + 2 * static_cast<int64_t>(kb / NB) * NB * NB : nullptr;
+    k_chol_diag<<<1, 256, 0, st>>>(A, D, kb, nb, flags); note_launch();
+    if (li) {
+      if (nb < NB) {
+        k_chol_inv_pad<<<1, 256, 0, st>>>(nb, li); note_launch();
+      }
+      k_chol_inv<<<nb, 32, 0, st>>>(A, D, kb, nb, li); note_launch();
+    }
     if (rest > 0) {
-      if (linv) {
-        k_chol_panel_mm<<<static_cast<int>((rest + PANEL_ROWS - 1) / PANEL_ROWS), 256, 0, st>>>(A, D, kb, nb, linv);
+      if (li) {
+        k_chol_panel_mm<<<static_cast<int>((rest + PANEL_ROWS - 1) / PANEL_ROWS), 256, 0, st>>>(A, D, kb, nb, li);
         note_launch();
       } else {
         k_chol_panel<<<static_cast<int>((rest + 127) / 128), 128, 0, st>>>(A, D, kb, nb); note_launch();
       }
-      const int nt = static_cast<int>((rest + 31) / 32);
-      k_chol_update<<<dim3(nt, nt), 256, 0, st>>>(A, D, kb, nb); note_launch();
+      // 32 x 32 tiles while they fill the SMs twice over, else 16 x 16 (each tile's FP64
+      // work sits on one SM, so the late, small updates need more, smaller tiles)
+      const int64_t n32 = (rest + 31) / 32;
+      if (n32 * (n32 + 1) / 2 >= 2 * static_cast<int64_t>(sms)) {
+        k_chol_update<32><<<dim3(static_cast<unsigned>(n32), static_cast<unsigned>(n32)), 256, 0, st>>>(A, D, kb, nb);
+      } else {
+        const int64_t n16 = (rest + 15) / 16;
+        k_chol_update<16><<<dim3(static_cast<unsigned>(n16), static_cast<unsigned>(n16)), 256, 0, st>>>(A, D, kb, nb);
+      }
+      note_launch();
     }
     FK_CUDA(cudaGetLastError());
   }
@@ -491,6 +548,7 @@ __global__ void k_trisolve(const double* L, int64_t D, double* X, int n_rhs) {
 // (forward) or one column (backward) and 32 independent loads.  L: row-major complex
 // lower triangle (the Cholesky factor), X: B on entry, solution on exit.
 constexpr int TS_NB = 32;
+static_assert(TS_NB == NB, "the triangular solves use the Cholesky's diagonal-block inverses");
 constexpr int TS_THREADS = 512;
 
 __global__ void __launch_bounds__(TS_THREADS) k_trisolve_blk(const double* __restrict__ L, int D, double* X) {
@@ -575,16 +633,16 @@ __global__ void __launch_bounds__(TS_THREADS) k_trisolve_blk(const double* __res
   }
 }
 
-fk_status trisolve_coop(const double* L, int64_t D, double* X, int n_rhs, cudaStream_t st, Scratch& scr,
-                        unsigned* flags, bool* handled);
+fk_status trisolve_coop(const double* L, const double* Linv, int64_t D, double* X, int n_rhs, cudaStream_t st,
+                        Scratch& scr, unsigned* flags, bool* handled);
 
 // The cooperative form spreads the FP64 updates over every SM (this part's FP64 rate
 // makes one SM the bottleneck at D ~ 1000); the one-CTA blocked form is the fallback.
 static fk_status trisolve(const double* L, int64_t D, double* X, int n_rhs, cudaStream_t st, Scratch* scr = nullptr,
-                          unsigned* flags = nullptr) {
+                          unsigned* flags = nullptr, const double* Linv = nullptr) {
   if (scr && flags) {
     bool handled = false;
-    FK_TRY(trisolve_coop(L, D, X, n_rhs, st, *scr, flags, &handled));
+    FK_TRY(trisolve_coop(L, Linv, D, X, n_rhs, st, *scr, flags, &handled));
     if (handled) return FK_OK;
   }
   const size_t smem = sizeof(cd) * (static_cast<size_t>(D) + TS_NB * (TS_NB + 1));
@@ -1404,10 +1462,10 @@ fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, 
     }
     FK_CUDA(cudaGetLastError());
     double* linv;
-    FK_TRY(scratch.alloc(&linv, 2 * NB * NB));
+    FK_TRY(scratch.alloc(&linv, 2 * linv_blocks(D) * NB * NB));
     FK_TRY(cholesky(A, D, flags, st, linv));
     FK_CUDA(cudaMemcpyAsync(X, rhs, sizeof(double) * 2 * D * n_rhs, cudaMemcpyDeviceToDevice, st));
-    FK_TRY(trisolve(A, D, X, n_rhs, st, &scratch, flags));
+    FK_TRY(trisolve(A, D, X, n_rhs, st, &scratch, flags, linv));
     FK_CUDA(cudaGetLastError());
     for (int it = 0; it < o.refine_steps; ++it) {
       if (with_op) {
@@ -1415,7 +1473,7 @@ fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, 
       } else {
         k_residual_dense<<<grid_for(D * n_rhs, 128), 128, 0, st>>>(d, m, T, Wl, X, rhs, R, n_rhs); note_launch();
       }
-      FK_TRY(trisolve(A, D, R, n_rhs, st, &scratch, flags));
+      FK_TRY(trisolve(A, D, R, n_rhs, st, &scratch, flags, linv));
       k_axpy_c<<<grid_for(2 * D * n_rhs, 256), 256, 0, st>>>(2 * D * n_rhs, R, X); note_launch();
       FK_CUDA(cudaGetLastError());
     }
@@ -1454,13 +1512,13 @@ fk_status solve_dense(const double* A, int64_t D, double* X, int n_rhs, int refi
   FK_CUDA(cudaMemcpyAsync(L, A, sizeof(double) * 2 * D * D, cudaMemcpyDeviceToDevice, st));
   FK_CUDA(cudaMemcpyAsync(B, X, sizeof(double) * 2 * D * n_rhs, cudaMemcpyDeviceToDevice, st));
   double* linv;
-  FK_TRY(scr.alloc(&linv, 2 * NB * NB));
+  FK_TRY(scr.alloc(&linv, 2 * linv_blocks(D) * NB * NB));
   FK_TRY(cholesky(L, D, flags, st, linv));
-  FK_TRY(trisolve(L, D, X, n_rhs, st, &scr, flags));
+  FK_TRY(trisolve(L, D, X, n_rhs, st, &scr, flags, linv));
   FK_CUDA(cudaGetLastError());
   for (int it = 0; it < refine; ++it) {
     k_dense_residual<<<grid_for(D * n_rhs, 128), 128, 0, st>>>(A, D, X, B, R, n_rhs); note_launch();
-    FK_TRY(trisolve(L, D, R, n_rhs, st, &scr, flags));
+    FK_TRY(trisolve(L, D, R, n_rhs, st, &scr, flags, linv));
     k_axpy_c<<<grid_for(2 * D * n_rhs, 256), 256, 0, st>>>(2 * D * n_rhs, R, X); note_launch();
     FK_CUDA(cudaGetLastError());
   }
@@ -1987,14 +2045,24 @@ namespace {
 // separated by barriers; within a phase each row has one writer.
 struct TsP {
   const double* L;
+  const double* Linv;  // [blocks][TS_NB][TS_NB] inverses of the diagonal blocks, or null
   int D;
   double* x;      // [D] complex, b in / solution out
   GridBar* bar;
   unsigned* flags;
 };
 
-// all threads of CTA 0: stage the diagonal block (independent loads in flight)
+// all threads of CTA 0: stage the diagonal block, or its inverse (independent loads in
+// flight)
 __device__ void ts_stage(const TsP& A, int kb, int nb, cd* dg) {
+  if (A.Linv) {
+    const double* li = A.Linv + 2 * static_cast<int64_t>(kb / TS_NB) * TS_NB * TS_NB;
+    for (int t = threadIdx.x; t < TS_NB * TS_NB; t += blockDim.x) {
+      const int r = t / TS_NB, c = t - r * TS_NB;
+      dg[r * (TS_NB + 1) + c] = cd{__ldg(li + 2 * t), __ldg(li + 2 * t + 1)};
+    }
+    return;
+  }
   for (int t = threadIdx.x; t < TS_NB * TS_NB; t += blockDim.x) {
     const int r = t / TS_NB, c = t - r * TS_NB;
     dg[r * (TS_NB + 1) + c] = (r < nb && c <= r)
@@ -2008,6 +2076,34 @@ __device__ void ts_stage(const TsP& A, int kb, int nb, cd* dg) {
 __device__ void ts_diag(const TsP& A, int kb, int nb, bool fwd, cd* dg) {
   const int lane = threadIdx.x & 31;
   cd yv = (lane < nb) ? cd{__ldcg(A.x + 2 * (kb + lane)), __ldcg(A.x + 2 * (kb + lane) + 1)} : cd{0, 0};
+  if (A.Linv) {
+    // y = Linv r (forward) or Linv^H r (backward): one output per lane, two partial sums
+    __shared__ cd rv[TS_NB];
+    rv[lane] = yv;
+    __syncwarp();
+    // the inverse blocks are zero above the diagonal (and beyond nb), so full sums
+    cd s0 = cd{0, 0}, s1 = cd{0, 0};
+    if (fwd) {
+#pragma unroll 4
+      for (int j = 0; j < TS_NB; j += 2) {
+        s0 = cfma(dg[lane * (TS_NB + 1) + j], rv[j], s0);
+        s1 = cfma(dg[lane * (TS_NB + 1) + j + 1], rv[j + 1], s1);
+      }
+    } else {
+#pragma unroll 4
+      for (int j = 0; j < TS_NB; j += 2) {
+        s0 = cjfma(dg[j * (TS_NB + 1) + lane], rv[j], s0);
+        s1 = cjfma(dg[(j + 1) * (TS_NB + 1) + lane], rv[j + 1], s1);
+      }
+    }
+    __syncwarp();
+    if (lane < nb) {
+      const cd v = cadd(s0, s1);
+      A.x[2 * (kb + lane)] = v.x;
+      A.x[2 * (kb + lane) + 1] = v.y;
+    }
+    return;
+  }
   for (int s = 0; s < nb; ++s) {
     const int i = fwd ? s : nb - 1 - s;
     cd t = cd{0, 0};
@@ -2058,20 +2154,24 @@ __global__ void __launch_bounds__(256) k_trisolve_coop(TsP A) {
       const int nkb = fwd ? kb + nb : kb - TS_NB;  // next block start
       const int nnb = has_next ? min(TS_NB, D - nkb) : 0;
       auto update = [&](int r) {
-        cd acc = cd{0, 0};
+        cd a0 = cd{0, 0}, a1 = cd{0, 0};
         if (fwd) {
+          const double* lr = A.L + 2 * (static_cast<int64_t>(r) * D + kb);
 #pragma unroll 8
-          for (int j = 0; j < nb; ++j)
-            acc = cadd(acc, cmul(cd{__ldg(A.L + 2 * (static_cast<int64_t>(r) * D + kb + j)),
-                                    __ldg(A.L + 2 * (static_cast<int64_t>(r) * D + kb + j) + 1)}, yb[j]));
+          for (int j = 0; j < nb; j += 2) {
+            a0 = cfma(cd{__ldg(lr + 2 * j), __ldg(lr + 2 * j + 1)}, yb[j], a0);
+            if (j + 1 < nb) a1 = cfma(cd{__ldg(lr + 2 * j + 2), __ldg(lr + 2 * j + 3)}, yb[j + 1], a1);
+          }
         } else {
 #pragma unroll 8
-          for (int j = 0; j < nb; ++j)
-            acc = cadd(acc, cconjmul(cd{__ldg(A.L + 2 * (static_cast<int64_t>(kb + j) * D + r)),
-                                        __ldg(A.L + 2 * (static_cast<int64_t>(kb + j) * D + r) + 1)}, yb[j]));
+          for (int j = 0; j < nb; j += 2) {
+            const double* l0 = A.L + 2 * (static_cast<int64_t>(kb + j) * D + r);
+            a0 = cjfma(cd{__ldg(l0), __ldg(l0 + 1)}, yb[j], a0);
+            if (j + 1 < nb) a1 = cjfma(cd{__ldg(l0 + 2 * D), __ldg(l0 + 2 * D + 1)}, yb[j + 1], a1);
+          }
         }
-        A.x[2 * r] = __ldcg(A.x + 2 * r) - acc.x;
-        A.x[2 * r + 1] = __ldcg(A.x + 2 * r + 1) - acc.y;
+        A.x[2 * r] = __ldcg(A.x + 2 * r) - (a0.x + a1.x);
+        A.x[2 * r + 1] = __ldcg(A.x + 2 * r + 1) - (a0.y + a1.y);
       };
       if (blockIdx.x == 0) {
         // the next block's rows, then its diagonal solve
@@ -2100,8 +2200,8 @@ __global__ void __launch_bounds__(256) k_trisolve_coop(TsP A) {
 }  // namespace
 
 // nullptr-free launcher: returns false in *handled when a cooperative launch is not possible
-fk_status trisolve_coop(const double* L, int64_t D, double* X, int n_rhs, cudaStream_t st, Scratch& scr,
-                        unsigned* flags, bool* handled) {
+fk_status trisolve_coop(const double* L, const double* Linv, int64_t D, double* X, int n_rhs, cudaStream_t st,
+                        Scratch& scr, unsigned* flags, bool* handled) {
   *handled = false;
   int dev = 0, coop = 0, sms = 0;
   FK_CUDA(cudaGetDevice(&dev));
@@ -2112,8 +2212,8 @@ fk_status trisolve_coop(const double* L, int64_t D, double* X, int n_rhs, cudaSt
   FK_TRY(scr.alloc(&misc, 16 * static_cast<size_t>(n_rhs)));
   FK_CUDA(cudaMemsetAsync(misc, 0, 16 * static_cast<size_t>(n_rhs), st));
   for (int r = 0; r < n_rhs; ++r) {
-    TsP A{L, static_cast<int>(D), X + 2 * static_cast<int64_t>(r) * D, reinterpret_cast<GridBar*>(misc + 16 * r),
-          flags};
+    TsP A{L, Linv, static_cast<int>(D), X + 2 * static_cast<int64_t>(r) * D,
+          reinterpret_cast<GridBar*>(misc + 16 * r), flags};
     void* args[] = {&A};
     FK_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_trisolve_coop), dim3(sms), dim3(256), args, 0,
                                         st));
