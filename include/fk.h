@@ -256,6 +256,35 @@ FK_API fk_status fk_accum_fit_sobolev(fk_accum* acc, double s, int penalty, cons
 FK_API fk_status fk_accum_reset(fk_accum* acc, void* stream);
 FK_API fk_status fk_accum_destroy(fk_accum* acc);
 
+/* Capture of calls into one CUDA graph (no counterpart in the paper; the batching
+ * form of the fits: a whole fit, e.g. the additive model's 8 + 28 transforms, Gram
+ * assembly and dense solve, replayed with one graph launch).
+ *   fk_capture_begin: starts capturing the calling host thread's library calls made
+ *     on `stream` (a created stream, not the legacy default stream).  Until
+ *     fk_capture_end the calls only record work: they return FK_OK without running
+ *     it, and their outputs are written when the graph is launched.  Calls whose path
+ *     needs a host round trip return FK_EINVAL and nothing of them is recorded:
+ *     conjugate-gradient solves (use FK_SOLVER_CHOL, D <= 8192), fk_hypergrad,
+ *     fk_penalty_grads, fk_accum_*, fk_type1_noalloc, any call given a report, and
+ *     fits with more than 256 lambdas.  Autotuning is off during a capture (stored
+ *     shapes are used).
+ *   fk_capture_end: ends the capture and returns the instantiated graph in *graph; if
+ *     any call failed during the capture the graph is discarded (FK_EINVAL).
+ *   fk_graph_launch: runs the recorded work on `stream` against the same buffers, so
+ *     new data written into the inputs give new outputs.  Scratch memory is allocated
+ *     and freed inside the graph.
+ *   fk_graph_status: waits for the last launch, then returns the device-side condition
+ *     of that run (FK_ERANGE, FK_ENOTPD, FK_ETIMEOUT) or FK_OK.
+ *   fk_graph_destroy: waits for the last launch and frees the graph (NULL allowed).
+ * Host arrays passed to captured calls (lambdas, PDE terms, box corners) are read at
+ * capture time; device buffers must stay valid while the graph is used. */
+typedef struct fk_graph fk_graph;
+FK_API fk_status fk_capture_begin(void* stream);
+FK_API fk_status fk_capture_end(void* stream, fk_graph** graph);
+FK_API fk_status fk_graph_launch(fk_graph* graph, void* stream);
+FK_API fk_status fk_graph_status(fk_graph* graph);
+FK_API fk_status fk_graph_destroy(fk_graph* graph);
+
 /* Synthetic 1-D sweep sample generated on the device (the paper's experiments are on
  * synthetic data; this one is too large to pass from the host).  Points first ..
  * first + n - 1 of the sample keyed by (seed, workload):

@@ -8,8 +8,10 @@ call raises.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
+import threading
 from typing import Optional, Sequence
 
 import numpy as np
@@ -30,7 +32,8 @@ EXPORTS = ["fk_default_opts", "fk_fit_sobolev", "fk_fit_pik", "fk_fit_additive",
            "fk_workspace_bytes", "fk_version", "fk_launch_count", "fk_type1_noalloc", "fk_penalty_grads",
            "fk_accum_create", "fk_accum_add", "fk_accum_system", "fk_accum_fit_sobolev", "fk_accum_reset",
            "fk_accum_destroy", "fk_generate_sweep_1d", "fk_release_workspace", "fk_autotune_table",
-           "fk_autotune_clear", "fk_fit_pik_general", "fk_box_moments", "fk_fit_sobolev_pairs"]
+           "fk_autotune_clear", "fk_fit_pik_general", "fk_box_moments", "fk_fit_sobolev_pairs",
+           "fk_capture_begin", "fk_capture_end", "fk_graph_launch", "fk_graph_status", "fk_graph_destroy"]
 
 
 class FkError(RuntimeError):
@@ -99,6 +102,11 @@ def lib() -> ctypes.CDLL:
             "fk_autotune_clear": (None, []),
             "fk_fit_pik_general": (_I, [_I, _L, _P, _P, _I, _I, _D, _D, _D, _I, _P, _P, _P, _D, _I, _P, _P, _P, _P]),
             "fk_box_moments": (_I, [_I, _I, _P, _P, _P, _P]),
+            "fk_capture_begin": (_I, [_P]),
+            "fk_capture_end": (_I, [_P, ctypes.POINTER(_P)]),
+            "fk_graph_launch": (_I, [_P, _P]),
+            "fk_graph_status": (_I, [_P]),
+            "fk_graph_destroy": (_I, [_P]),
             "fk_fit_sobolev_pairs": (_I, [_I, _L, _P, _P, _I, _I, _P, _P, _I, _I, _D, _I, _P, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
@@ -125,6 +133,32 @@ def _prec(precision) -> int:
     return {"fp64": FK_FP64, "mixed": FK_MIXED}[precision]
 
 
+_CAP = threading.local()
+
+
+def _capturing() -> bool:
+    return getattr(_CAP, "active", False)
+
+
+def _dense(t: torch.Tensor) -> torch.Tensor:
+    """t itself when contiguous; a copy otherwise, which a capture cannot record."""
+    if t.is_contiguous():
+        return t
+    if _capturing():
+        raise ValueError("inputs of a captured call must be contiguous (a copy would not outlive the capture)")
+    return t.contiguous()
+
+
+def _out(out, shape, dtype, device):
+    if out is None:
+        if _capturing():
+            raise ValueError("pass out= to a captured call: its outputs must outlive the capture")
+        return torch.empty(shape, dtype=dtype, device=device)
+    if tuple(out.shape) != tuple(shape) or out.dtype != dtype or not out.is_contiguous() or out.device != device:
+        raise ValueError("out must be a contiguous %s tensor of shape %s on %s" % (dtype, tuple(shape), device))
+    return out
+
+
 def _points(x: torch.Tensor, prec: int) -> torch.Tensor:
     want = torch.float64 if prec == FK_FP64 else torch.float32
     if not x.is_cuda:
@@ -133,7 +167,7 @@ def _points(x: torch.Tensor, prec: int) -> torch.Tensor:
         raise ValueError("points must be %s for this precision" % want)
     if x.dim() == 1:
         x = x.unsqueeze(0)
-    return x.contiguous()
+    return _dense(x)
 
 
 def default_opts(**kw) -> Opts:
@@ -153,15 +187,17 @@ def _dbl_array(vals: Sequence[float]):
     return arr
 
 
-def fk_build_system(x, y, m: int, eps: float, precision="mixed", opts: Optional[Opts] = None, report: bool = False):
-    """Moments T ((4m+1)^d complex) and right-hand sides b ([n_targets][D] complex), both / n."""
+def fk_build_system(x, y, m: int, eps: float, precision="mixed", opts: Optional[Opts] = None, report: bool = False,
+                    out=None):
+    """Moments T ((4m+1)^d complex) and right-hand sides b ([n_targets][D] complex), both / n.
+    out: optional (T, b) tensors to write into (required during a capture)."""
     p = _prec(precision)
     x = _points(x, p)
     d, n = x.shape
-    y = y.reshape(-1, n).contiguous() if y is not None else None
+    y = _dense(y.reshape(-1, n)) if y is not None else None
     nt = 0 if y is None else y.shape[0]
-    T = torch.empty((4 * m + 1) ** d, dtype=torch.complex128, device=x.device)
-    b = torch.empty((max(nt, 1), (2 * m + 1) ** d), dtype=torch.complex128, device=x.device)
+    T = _out(None if out is None else out[0], ((4 * m + 1) ** d,), torch.complex128, x.device)
+    b = _out(None if out is None else out[1], (max(nt, 1), (2 * m + 1) ** d), torch.complex128, x.device)
     rep = Report()
     _check(lib().fk_build_system(d, n, x.data_ptr(), y.data_ptr() if y is not None else None, nt, m, eps, p,
                                  _opts_ptr(opts), T.data_ptr(), b.data_ptr(), _stream(),
@@ -171,14 +207,14 @@ def fk_build_system(x, y, m: int, eps: float, precision="mixed", opts: Optional[
 
 
 def fk_fit_sobolev(x, y, m: int, s: float, lambdas, eps: float, precision="mixed", penalty: int = FK_PEN_SOBOLEV,
-                   opts: Optional[Opts] = None, report: bool = False):
+                   opts: Optional[Opts] = None, report: bool = False, out=None):
     """theta [n_lambda][n_targets][D] complex128 (Eq. 2 with the Sec. 3.1 / 3.2 penalty)."""
     p = _prec(precision)
     x = _points(x, p)
     d, n = x.shape
-    y = y.reshape(-1, n).contiguous()
+    y = _dense(y.reshape(-1, n))
     lam = list(lambdas) if hasattr(lambdas, "__len__") else [lambdas]
-    theta = torch.empty((len(lam), y.shape[0], (2 * m + 1) ** d), dtype=torch.complex128, device=x.device)
+    theta = _out(out, (len(lam), y.shape[0], (2 * m + 1) ** d), torch.complex128, x.device)
     rep = Report()
     _check(lib().fk_fit_sobolev(d, n, x.data_ptr(), y.data_ptr(), y.shape[0], m, s, penalty, _dbl_array(lam), len(lam),
                                 eps, p, _opts_ptr(opts), theta.data_ptr(), _stream(),
@@ -205,28 +241,28 @@ def fk_fit_pik(x, y, m: int, s: float, lam: float, mu: float, alpha, a, eps: flo
 
 
 def fk_fit_additive(x, y, m: int, lambdas, eps: float, precision="mixed", opts: Optional[Opts] = None,
-                    report: bool = False):
+                    report: bool = False, out=None):
     """theta [n_lambda][n_targets][d][2m+1] complex128 (Prop. 5.1)."""
     p = _prec(precision)
     x = _points(x, p)
     d, n = x.shape
-    y = y.reshape(-1, n).contiguous()
+    y = _dense(y.reshape(-1, n))
     lam = list(lambdas) if hasattr(lambdas, "__len__") else [lambdas]
-    theta = torch.empty((len(lam), y.shape[0], d, 2 * m + 1), dtype=torch.complex128, device=x.device)
+    theta = _out(out, (len(lam), y.shape[0], d, 2 * m + 1), torch.complex128, x.device)
     rep = Report()
     _check(lib().fk_fit_additive(d, n, x.data_ptr(), y.data_ptr(), y.shape[0], m, _dbl_array(lam), len(lam), eps, p,
                                  _opts_ptr(opts), theta.data_ptr(), _stream(), ctypes.byref(rep) if report else None))
     return (theta, rep.as_dict()) if report else theta
 
 
-def fk_predict(theta, xq, m: int, eps: float, precision="mixed", additive: bool = False):
+def fk_predict(theta, xq, m: int, eps: float, precision="mixed", additive: bool = False, out=None):
     """f [n_sets][n_q] float64: Re sum_k theta_k e^{i<k,x>} (or the additive sum)."""
     p = _prec(precision)
     xq = _points(xq, p)
     d, nq = xq.shape
     per = d * (2 * m + 1) if additive else (2 * m + 1) ** d
-    th = theta.reshape(-1, per).contiguous()
-    f = torch.empty((th.shape[0], nq), dtype=torch.float64, device=xq.device)
+    th = _dense(theta.reshape(-1, per))
+    f = _out(out, (th.shape[0], nq), torch.float64, xq.device)
     _check(lib().fk_predict(1 if additive else 0, d, m, th.data_ptr(), th.shape[0], nq, xq.data_ptr(), eps, p,
                             f.data_ptr(), _stream()))
     return f
@@ -471,3 +507,55 @@ def fk_fit_sobolev_pairs(x, y, m: int, s_values, lambdas, eps: float, precision=
                                       len(sv), penalty, eps, p, _opts_ptr(opts), theta.data_ptr(), _stream(),
                                       ctypes.byref(rep) if report else None))
     return (theta, rep.as_dict()) if report else theta
+
+
+class Graph:
+    """Library calls recorded by `capture`, replayed with one graph launch."""
+
+    def __init__(self):
+        self._ptr = _P()
+
+    def launch(self, stream=None):
+        if not self._ptr:
+            raise ValueError("graph is closed or was not captured")
+        _check(lib().fk_graph_launch(self._ptr, _stream(stream)))
+
+    def status(self):
+        """Waits for the last launch and raises FkError on a device-side condition."""
+        _check(lib().fk_graph_status(self._ptr))
+
+    def close(self):
+        if self._ptr:
+            lib().fk_graph_destroy(self._ptr)
+            self._ptr = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@contextlib.contextmanager
+def capture(stream=None):
+    """Record the library calls of the block (made on `stream`, which becomes the current
+    stream inside) into a Graph.  Calls inside record work only; pass out= for their
+    outputs and keep inputs and outputs alive while the graph is used."""
+    s = torch.cuda.Stream() if stream is None else stream
+    if s.cuda_stream == 0:
+        raise ValueError("capture needs a created stream, not the default stream")
+    g = Graph()
+    g.stream = s
+    s.wait_stream(torch.cuda.current_stream())
+    _check(lib().fk_capture_begin(s.cuda_stream))
+    _CAP.active = True
+    ok = False
+    try:
+        with torch.cuda.stream(s):
+            yield g
+        ok = True
+    finally:
+        _CAP.active = False
+        rc = lib().fk_capture_end(s.cuda_stream, ctypes.byref(g._ptr))
+        if ok:
+            _check(rc)

@@ -65,15 +65,21 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
                             int n_lambda, double eps, int precision, const fk_opts& o, double* theta,
                             cudaStream_t st, fk_report* rep) {
   Scratch scr(st);
+  CaptureCtx* cap = capture_ctx();
   unsigned* flags;
-  FK_TRY(scr.alloc(&flags, 1));
-  FK_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned), st));
+  if (cap) {
+    flags = cap->flags;
+  } else {
+    FK_TRY(scr.alloc(&flags, 1));
+    FK_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned), st));
+  }
   const int K = 2 * m + 1, M2 = 4 * m + 1;
   const int64_t Dall = static_cast<int64_t>(d) * K;
   const int npairs = d * (d - 1) / 2;
-  cudaEvent_t ev[4];
-  for (int i = 0; i < 4; ++i) cudaEventCreate(&ev[i]);
-  cudaEventRecord(ev[0], st);
+  cudaEvent_t ev[4] = {};
+  if (rep)
+    for (int i = 0; i < 4; ++i) cudaEventCreate(&ev[i]);
+  if (rep) cudaEventRecord(ev[0], st);
 
   // 1-D moments and right-hand sides per coordinate
   EsPlan p1;
@@ -146,7 +152,7 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
         FK_TRY(grid_to_modes<float>(p2, grid2, 0, 1, m, corr2, inv_n, blk, st, inner));
       }
     }
-  cudaEventRecord(ev[1], st);
+  if (rep) cudaEventRecord(ev[1], st);
   // block Gram + lambda I, dense solve per lambda
   double* A;
   FK_TRY(scr.alloc(&A, 2 * Dall * Dall));
@@ -158,7 +164,8 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
     Scratch inner(st);
     FK_TRY(solve_dense(A, Dall, X, nt, o.refine_steps, st, inner, flags));
   }
-  cudaEventRecord(ev[2], st);
+  if (cap) return FK_OK;  // the graph's flag word is read by fk_graph_status
+  if (rep) cudaEventRecord(ev[2], st);
   unsigned h = 0;
   FK_CUDA(cudaMemcpyAsync(&h, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   FK_CUDA(cudaStreamSynchronize(st));
@@ -174,20 +181,23 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
     rep->fine_grid = p2.N;
     rep->kernel_width = p2.w;
   }
-  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
-  if (h & FLAG_RANGE) return set_error(FK_ERANGE, "a point lies outside [-3 pi, 3 pi)");
-  if (h & FLAG_NOTPD) return set_error(FK_ENOTPD, "Cholesky met a non-positive pivot");
-  if (h) return set_error(FK_EINTERNAL, "device flag 0x%x", h);
-  return FK_OK;
+  if (rep)
+    for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  return flags_status(h);
 }
 
 template <typename R>
 fk_status predict_additive_impl(int d, int m, const double* theta, int n_sets, int64_t nq, const R* xq, double eps,
                                 double* f, cudaStream_t st) {
   Scratch scr(st);
+  CaptureCtx* cap = capture_ctx();
   unsigned* flags;
-  FK_TRY(scr.alloc(&flags, 1));
-  FK_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned), st));
+  if (cap) {
+    flags = cap->flags;
+  } else {
+    FK_TRY(scr.alloc(&flags, 1));
+    FK_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned), st));
+  }
   const int K = 2 * m + 1;
   EsPlan p;
   FK_TRY(make_es_plan(1, m, eps, 1.9, &p));
@@ -205,11 +215,11 @@ fk_status predict_additive_impl(int d, int m, const double* theta, int n_sets, i
                                                                                    part, f); note_launch();
     FK_CUDA(cudaGetLastError());
   }
+  if (cap) return FK_OK;
   unsigned h = 0;
   FK_CUDA(cudaMemcpyAsync(&h, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   FK_CUDA(cudaStreamSynchronize(st));
-  if (h & FLAG_RANGE) return set_error(FK_ERANGE, "a point lies outside [-3 pi, 3 pi)");
-  return FK_OK;
+  return flags_status(h);
 }
 
 }  // namespace

@@ -133,8 +133,15 @@ fk_status es_correction(const EsPlan& p, double* corr, cudaStream_t st) {
       src = it->second;
     } else {
       FK_CUDA(cudaMalloc(&src, bytes));
-      fk_status stt = es_correction_compute(p, src, st);
-      if (stt == FK_OK && cudaStreamSynchronize(st) != cudaSuccess) stt = set_error(FK_ECUDA, "es_correction sync");
+      // during a capture the table is made on a stream of its own, outside the graph
+      cudaStream_t cs = st;
+      if (capture_ctx() && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaFree(src);
+        return set_error(FK_ECUDA, "es_correction stream");
+      }
+      fk_status stt = es_correction_compute(p, src, cs);
+      if (stt == FK_OK && cudaStreamSynchronize(cs) != cudaSuccess) stt = set_error(FK_ECUDA, "es_correction sync");
+      if (cs != st) cudaStreamDestroy(cs);
       if (stt != FK_OK) {
         cudaFree(src);
         return stt;

@@ -72,7 +72,17 @@ fk_status set_error(fk_status st, const char* fmt, ...) {
   vsnprintf(buf, sizeof(buf), fmt, ap);
   va_end(ap);
   g_err = buf;
+  if (CaptureCtx* c = capture_ctx()) c->failed = true;
   return st;
+}
+
+fk_status flags_status(unsigned h) {
+  if (h & FLAG_RANGE) return set_error(FK_ERANGE, "a point lies outside [-3 pi, 3 pi)");
+  if (h & FLAG_NOTPD) return set_error(FK_ENOTPD, "Cholesky met a non-positive pivot");
+  if (h & FLAG_TIMEOUT) return set_error(FK_ETIMEOUT, "a bounded device wait gave up");
+  if (h & FLAG_INTERNAL) return set_error(FK_EINTERNAL, "device index check failed");
+  if (h) return set_error(FK_EINTERNAL, "device flag 0x%x", h);
+  return FK_OK;
 }
 
 void clear_error() { g_err.clear(); }
@@ -85,6 +95,7 @@ static fk_opts resolve_opts(const fk_opts* o) {
   if (r.cg_maxit <= 0) r.cg_maxit = 1000;
   if (r.refine_steps < 0) r.refine_steps = 0;
   if (r.upsampfac <= 1.0) r.upsampfac = 1.9;
+  if (capture_ctx()) r.autotune = 0;  // tuning times kernels on the host clock
   return r;
 }
 
@@ -108,20 +119,22 @@ struct Flags {
   unsigned* dev = nullptr;
   cudaStream_t st;
   explicit Flags(cudaStream_t s) : st(s) {}
+  // during a capture the graph's flag word, read by fk_graph_status after a replay
   fk_status init(Scratch& scr) {
+    if (CaptureCtx* c = capture_ctx()) {
+      dev = c->flags;
+      return FK_OK;
+    }
     FK_TRY(scr.alloc(&dev, 1));
     FK_CUDA(cudaMemsetAsync(dev, 0, sizeof(unsigned), st));
     return FK_OK;
   }
   fk_status check() {
+    if (capture_ctx()) return FK_OK;
     unsigned h = 0;
     FK_CUDA(cudaMemcpyAsync(&h, dev, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     FK_CUDA(cudaStreamSynchronize(st));
-    if (h & FLAG_RANGE) return set_error(FK_ERANGE, "a point lies outside [-3 pi, 3 pi)");
-    if (h & FLAG_NOTPD) return set_error(FK_ENOTPD, "Cholesky met a non-positive pivot");
-    if (h & FLAG_TIMEOUT) return set_error(FK_ETIMEOUT, "a bounded device wait gave up");
-    if (h & FLAG_INTERNAL) return set_error(FK_EINTERNAL, "device index check failed");
-    return FK_OK;
+    return flags_status(h);
   }
 };
 
@@ -267,6 +280,7 @@ fk_status fk_type1(int d, int64_t n, const void* x, const void* c, int n_ch, int
   FK_TRY(check_common(d, n, 0, eps, precision));
   if (kmax < 0 || n_ch < 1 || !x || !c || !out) return set_error(FK_EINVAL, "bad type-1 arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, true, false, "fk_type1"));
   const fk_opts o = resolve_opts(nullptr);
   Scratch scr(st);
   Flags fl(st);
@@ -288,6 +302,7 @@ fk_status fk_type2(int d, int kmax, const double* coef, int n_sets, int64_t n, c
   FK_TRY(check_common(d, n, 0, eps, precision));
   if (kmax < 0 || n_sets < 1 || !x || !coef || !out) return set_error(FK_EINVAL, "bad type-2 arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, true, false, "fk_type2"));
   const fk_opts o = resolve_opts(nullptr);
   Scratch scr(st);
   Flags fl(st);
@@ -311,6 +326,7 @@ fk_status fk_build_system(int d, int64_t n, const void* x, const void* y, int n_
   if (!x || !T || (n_targets > 0 && (!y || !b)) || n_targets < 0)
     return set_error(FK_EINVAL, "bad build_system arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, true, rep != nullptr, "fk_build_system"));
   const fk_opts o = resolve_opts(opts);
   Scratch scr(st);
   Flags fl(st);
@@ -351,6 +367,7 @@ fk_status fk_solve(int d, int m, const double* T, const double* W, int n_w, cons
   if (d < 1 || d > 3 || m < 0 || n_w < 1 || n_rhs < 1 || !T || !W || !rhs || !sol)
     return set_error(FK_EINVAL, "bad solve arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, true, rep != nullptr, "fk_solve"));
   const fk_opts o = resolve_opts(opts);
   Scratch scr(st);
   Flags fl(st);
@@ -379,6 +396,7 @@ static fk_status fit_common(int d, int64_t n, const void* x, const void* y, int 
   if (s < 0) return set_error(FK_EINVAL, "s < 0");
   if (mu < 0) return set_error(FK_EINVAL, "mu < 0");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, true, rep != nullptr, "the fit"));
   const fk_opts o = resolve_opts(opts);
   Scratch scr(st);
   Flags fl(st);
@@ -460,6 +478,7 @@ fk_status fk_fit_sobolev_pairs(int d, int64_t n, const void* x, const void* y, i
     if (!(s_values[i] >= 0.0)) return set_error(FK_EINVAL, "s[%d] = %g < 0", i, s_values[i]);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, true, rep != nullptr, "fk_fit_sobolev_pairs"));
   const fk_opts o = resolve_opts(opts);
   Scratch scr(st);
   Flags fl(st);
@@ -529,6 +548,7 @@ fk_status fk_fit_additive(int d, int64_t n, const void* x, const void* y, int n_
   for (int i = 0; i < n_lambda; ++i)
     if (!(lambdas[i] > 0.0)) return set_error(FK_EINVAL, "lambda[%d] = %g must be > 0 (Sigma is singular)", i, lambdas[i]);
   if (static_cast<int64_t>(d) * (2 * m + 1) > 8192) return set_error(FK_EINVAL, "d (2m + 1) > 8192");
+  FK_TRY(capture_check(static_cast<cudaStream_t>(stream), true, rep != nullptr, "fk_fit_additive"));
   return fit_additive(d, n, x, y, n_targets, m, lambdas, n_lambda, eps, precision, resolve_opts(opts), theta,
                       static_cast<cudaStream_t>(stream), rep);
 }
@@ -541,6 +561,7 @@ fk_status fk_predict(int additive, int d, int m, const double* theta, int n_sets
       return set_error(FK_EINVAL, "bad additive prediction arguments");
     if (!(eps >= 1e-14 && eps <= 1e-1)) return set_error(FK_EINVAL, "eps = %g outside [1e-14, 1e-1]", eps);
     if (precision != FK_FP64 && precision != FK_MIXED) return set_error(FK_EINVAL, "unknown precision %d", precision);
+    FK_TRY(capture_check(static_cast<cudaStream_t>(stream), true, false, "fk_predict"));
     return predict_additive(d, m, theta, n_sets, n_q, xq, eps, precision, f, static_cast<cudaStream_t>(stream));
   }
   return fk_type2(d, m, theta, n_sets, n_q, xq, eps, precision, f, stream);
@@ -594,6 +615,7 @@ fk_status fk_accum_create(int d, int m, int n_targets, double eps, int precision
   FK_TRY(check_common(d, 1, m, eps, precision));
   if (n_targets < 0 || n_targets > 1024) return set_error(FK_EINVAL, "n_targets = %d outside [0, 1024]", n_targets);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, false, false, "fk_accum_create"));
   fk_accum* a = new fk_accum();
   a->d = d;
   a->m = m;
@@ -633,6 +655,7 @@ fk_status fk_accum_add(fk_accum* a, int64_t n, const void* x, const void* y, con
   if (n == 0) return FK_OK;
   if (!x || (a->nt > 0 && !y)) return set_error(FK_EINVAL, "null points or targets");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, false, false, "fk_accum_add"));
   Scratch scr(st);
   const EsPlan& p = a->p;
   if (a->precision == FK_MIXED && a->d == 1 && a->o.spread != FK_SPREAD_ATOMIC &&
@@ -656,6 +679,7 @@ fk_status fk_accum_system(fk_accum* a, double* T, double* b, int64_t* n_total, v
   if (!a) return set_error(FK_EINVAL, "null accumulator");
   if (a->n_total < 1) return set_error(FK_EINVAL, "no points added");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, false, false, "fk_accum_system"));
   Scratch scr(st);
   const double inv_n = 1.0 / static_cast<double>(a->n_total);
   if (T) FK_TRY(modes_any(a->p, a->precision, a->grid, 0, 1, 2 * a->m, a->corr, inv_n, T, st, scr));
@@ -674,6 +698,7 @@ fk_status fk_accum_fit_sobolev(fk_accum* a, double s, int penalty, const double*
     if (!(lambdas[i] >= 0.0)) return set_error(FK_EINVAL, "lambda[%d] = %g < 0", i, lambdas[i]);
   if (a->n_total < 1) return set_error(FK_EINVAL, "no points added");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, false, false, "fk_accum_fit_sobolev"));
   Scratch scr(st);
   Flags fl(st);
   FK_TRY(fl.init(scr));
@@ -714,6 +739,7 @@ fk_status fk_accum_reset(fk_accum* a, void* stream) {
   clear_error();
   if (!a) return set_error(FK_EINVAL, "null accumulator");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, false, false, "fk_accum_reset"));
   const int64_t G = ipow(a->p.N, a->d) * (1 + a->nt);
   FK_CUDA(cudaMemsetAsync(a->grid, 0, sizeof(double) * G, st));
   FK_CUDA(cudaMemsetAsync(a->flags, 0, sizeof(unsigned), st));

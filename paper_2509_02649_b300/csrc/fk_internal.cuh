@@ -95,7 +95,21 @@ fk_status make_es_plan(int d, int kmax, double eps, double upsampfac, EsPlan* p)
 // memory instead of mapping it again; fk_release_workspace() trims it.
 cudaMemPool_t workspace_pool();
 
-// Stream-ordered scratch allocation tracked for release at scope exit.
+// Active capture of this host thread's library calls into a CUDA graph (capture.cu).
+struct CaptureCtx {
+  cudaStream_t st = nullptr;
+  unsigned* flags = nullptr;  // the graph's flag word
+  bool failed = false;        // a call returned an error during the capture
+};
+CaptureCtx* capture_ctx();
+// FK_EINVAL when a capture is active and the call cannot be recorded (another stream,
+// a report, or a host round trip on its path)
+fk_status capture_check(cudaStream_t st, bool capturable, bool wants_report, const char* what);
+// status of a device flag word
+fk_status flags_status(unsigned h);
+
+// Stream-ordered scratch allocation tracked for release at scope exit (during a
+// capture: graph allocation nodes from the capturing stream).
 struct Scratch {
   cudaStream_t st;
   std::vector<void*> ptrs;
@@ -112,7 +126,7 @@ struct Scratch {
     size_t bytes = elems * sizeof(T);
     if (bytes == 0) bytes = 16;
     void* q = nullptr;
-    cudaMemPool_t pool = workspace_pool();
+    cudaMemPool_t pool = capture_ctx() ? nullptr : workspace_pool();
     cudaError_t e = pool ? cudaMallocFromPoolAsync(&q, bytes, pool, st) : cudaMallocAsync(&q, bytes, st);
     if (e != cudaSuccess) {
       cudaGetLastError();

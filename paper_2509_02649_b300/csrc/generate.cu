@@ -118,6 +118,7 @@ extern "C" fk_status fk_generate_sweep_1d(uint64_t seed, int workload, int64_t f
   if (n > 0 && (!x || (n_targets > 0 && !y))) return set_error(FK_EINVAL, "null output");
   if (workload < 0) return set_error(FK_EINVAL, "workload < 0");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, true, false, "fk_generate_sweep_1d"));
   if (y_absmax && n_targets > 0) FK_CUDA(cudaMemsetAsync(y_absmax, 0, sizeof(unsigned) * n_targets, st));
   if (n == 0) return FK_OK;
   const int64_t quads = (n + 3) / 4;

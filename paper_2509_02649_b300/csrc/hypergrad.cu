@@ -192,6 +192,7 @@ fk_status fk_hypergrad(int d, int64_t n, const void* x, int64_t n_v, const void*
   if (o.cg_maxit <= 0) o.cg_maxit = 1000;
   if (o.upsampfac <= 1.0) o.upsampfac = 1.9;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, false, false, "fk_hypergrad"));
   if (precision == FK_FP64)
     return hypergrad_impl<double>(d, n, static_cast<const double*>(x), n_v, static_cast<const double*>(xv),
                                   static_cast<const double*>(yv), m, T, W, theta, eps, precision, o, loss, dW, dY, st);
@@ -216,6 +217,7 @@ fk_status fk_penalty_grads(int d, int m, double s, double c0, double lambda, dou
     }
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, false, false, "fk_penalty_grads"));
   double* dout = nullptr;
   FK_CUDA(cudaMallocAsync(&dout, sizeof(double) * (3 + n_terms), st));
   k_penalty_grads<<<1, 256, 0, st>>>(d, m, s, c0, lambda, mu, pde, dW, dout); note_launch();

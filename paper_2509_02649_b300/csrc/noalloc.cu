@@ -63,6 +63,7 @@ extern "C" fk_status fk_type1_noalloc(int d, int64_t n, const void* x, const voi
   if (precision != FK_FP64 && precision != FK_MIXED) return set_error(FK_EINVAL, "unknown precision %d", precision);
   if (kmax < 0 || n_ch < 1 || !x || !c || !out) return set_error(FK_EINVAL, "bad type-1 arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, false, false, "fk_type1_noalloc"));
   EsPlan p;
   FK_TRY(make_es_plan(d, kmax, eps, 1.9, &p));
   const size_t G = (d == 1) ? static_cast<size_t>(p.N) : static_cast<size_t>(p.N) * p.N;

@@ -29,8 +29,14 @@ __device__ inline void mode_of(int64_t q, int d, int m, int* k) {
   }
 }
 
-__global__ void k_penalty(int d, int m, int penalty, double s, double c0, const double* lambdas, int n_lambda,
-                          double mu, PdeTerms pde, double* W) {
+// lambdas by value (a captured graph keeps launch parameters, not host memory)
+constexpr int LAM_INLINE = 256;
+struct LamList {
+  double v[LAM_INLINE];
+};
+
+__global__ void k_penalty(int d, int m, int penalty, double s, double c0, const double* lambdas, LamList lin,
+                          int n_lambda, double mu, PdeTerms pde, double* W) {
   const int K = 2 * m + 1;
   int64_t D = 1;
   for (int l = 0; l < d; ++l) D *= K;
@@ -41,7 +47,7 @@ __global__ void k_penalty(int d, int m, int penalty, double s, double c0, const 
     const int64_t q = t - li * D;
     int k[3] = {0, 0, 0};
     mode_of(q, d, m, k);
-    const double lam = lambdas[li];
+    const double lam = lambdas ? lambdas[li] : lin.v[li];
     double wv;
     if (penalty == FK_PEN_LOWBIAS) {
       wv = lam;
@@ -86,13 +92,23 @@ fk_status penalty_weights(int d, int m, int penalty, double s, double c0, const 
       pde.alpha[t][l] = alpha[t * d + l];
     }
   }
+  int64_t D = 1;
+  for (int l = 0; l < d; ++l) D *= (2 * m + 1);
+  LamList lin{};
+  if (n_lambda <= LAM_INLINE) {
+    for (int i = 0; i < n_lambda; ++i) lin.v[i] = lambdas[i];
+    k_penalty<<<grid_for(D * n_lambda, 256), 256, 0, st>>>(d, m, penalty, s, c0, nullptr, lin, n_lambda, mu, pde, W);
+    note_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
+  }
+  if (capture_ctx()) return set_error(FK_EINVAL, "more than %d lambdas in one captured call", LAM_INLINE);
   double* dl = nullptr;
   FK_CUDA(cudaMallocAsync(&dl, sizeof(double) * n_lambda, st));
   cudaError_t e = cudaMemcpyAsync(dl, lambdas, sizeof(double) * n_lambda, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
-    int64_t D = 1;
-    for (int l = 0; l < d; ++l) D *= (2 * m + 1);
-    k_penalty<<<grid_for(D * n_lambda, 256), 256, 0, st>>>(d, m, penalty, s, c0, dl, n_lambda, mu, pde, W); note_launch();
+    k_penalty<<<grid_for(D * n_lambda, 256), 256, 0, st>>>(d, m, penalty, s, c0, dl, lin, n_lambda, mu, pde, W);
+    note_launch();
     e = cudaGetLastError();
   }
   cudaFreeAsync(dl, st);
@@ -1435,6 +1451,9 @@ fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, 
   if (cg_iters) *cg_iters = 0;
   if (rel_res) *rel_res = 0.0;
   if (solver == FK_SOLVER_CG) {
+    if (capture_ctx())
+      return set_error(FK_EINVAL, "conjugate gradients test convergence on the host: not capturable "
+                                  "(the Cholesky solver is, for D <= 8192)");
     if (d == 2) {
       bool handled = false;
       const fk_status rc = cg_solve_persistent(m, T, W, n_w, rhs, n_rhs, o, sol, st, scratch, flags, cg_iters, rel_res,
@@ -1912,6 +1931,7 @@ fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, 
                               const fk_opts& o, double* sol, cudaStream_t st, Scratch& scr, unsigned* flags,
                               int* iters_out, double* relres_out, bool* handled, const PenOp* op) {
   *handled = false;
+  if (capture_ctx()) return FK_OK;  // the one-CTA form is recorded instead of a cooperative launch
   int dev = 0, coop = 0, sms = 0;
   FK_CUDA(cudaGetDevice(&dev));
   FK_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
