@@ -356,6 +356,23 @@ def run_row(args, rank, local):
         line["loss_and_grads"] = {"L": res[-1][2][0], "dL/dlambda": res[-1][2][1], "dL/dmu": res[-1][2][2]}
     if W == "additive-8d":
         line["report"] = res[-1][2]
+        # the same fit recorded once into a CUDA graph and replayed: one launch per step
+        gst = torch.cuda.Stream()
+        gst.wait_stream(st)
+        out = torch.empty((1, 1, d, 2 * m + 1), dtype=torch.complex128, device=x.device)
+        with fk.capture(gst) as graph:
+            fk.fk_fit_additive(x, y, m, [lam], 1e-6, "mixed", out=out)
+        graph.launch(gst)
+        graph.status()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(gst)
+        for _ in range(args.steps):
+            graph.launch(gst)
+        g1.record(gst)
+        graph.status()
+        line["graph"] = {"ms_per_step": g0.elapsed_time(g1) / args.steps, "graph_launches_per_step": 1,
+                         "what": "fk_capture_begin/end of one fit, replayed with fk_graph_launch"}
+        graph.close()
     print(json.dumps(line), flush=True)
 
 

@@ -763,11 +763,23 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
     }
     // records of this round: [CARRY - nc, CARRY + nr) of the buffer
     const int lo = CARRY - nc, hi = CARRY + nr;
-    for (int idx = lo + tid; idx < hi; idx += THREADS) {
-      const int cl = static_cast<int>(st[idx].x & 0xFFFFu);
-      if (cl == 0xFFFF) continue;  // run padding
-      atomicAdd(&ccount[cl], 1);
-      nxt[idx] = static_cast<unsigned short>(atomicExch(&head[cl], idx));
+    // four records per thread and trip, so that their shared-memory atomics overlap
+    for (int base = lo + tid; base < hi; base += 4 * THREADS) {
+      int cl[4], old[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int idx = base + u * THREADS;
+        cl[u] = (idx < hi) ? static_cast<int>(st[idx].x & 0xFFFFu) : 0xFFFF;  // 0xFFFF: run padding
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (cl[u] != 0xFFFF) {
+          atomicAdd(&ccount[cl[u]], 1);
+          old[u] = atomicExch(&head[cl[u]], base + u * THREADS);
+        }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (cl[u] != 0xFFFF) nxt[base + u * THREADS] = static_cast<unsigned short>(old[u]);
     }
     const bool last = (r == nrounds - 1);
     int q = 0x7FFFFFFF;
