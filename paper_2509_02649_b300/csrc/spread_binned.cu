@@ -605,11 +605,16 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter1(PartArgs A) {
     }
     __syncthreads();
     const int valid = toff[G];
-    for (int j = tid; j < valid; j += S2_THREADS) {
-      const uint4 r = sorted[j];
-      const int o = static_cast<int>(r.x >> 16);
-      const int pos = tpos[o];
-      if (pos >= 0) A.rec[static_cast<int64_t>(o) * A.cap + pos + (j - toff[o])] = r;
+    // a fixed trip count, so that every thread's PER loads are in flight at once
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int j = k * S2_THREADS + tid;
+      if (j < valid) {
+        const uint4 r = sorted[j];
+        const int o = static_cast<int>(r.x >> 16);
+        const int pos = tpos[o];
+        if (pos >= 0) A.rec[static_cast<int64_t>(o) * A.cap + pos + (j - toff[o])] = r;
+      }
     }
     __syncthreads();
   }
