@@ -30,7 +30,7 @@ WL = dict(workload="2d-sobolev", d=2, n=100_000_000, m=32, s=2.0, lam=1e-6, eps=
 METRIC = "fit points/s (NUFFT Gram+RHS+solve)"
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
-ACC_DRAM_BYTES_PER_POINT = (321.17632e6 + 3.851264e6) / 2e7  # k_bin_accumulate, 2-D, w = 7
+ACC_DRAM_BYTES_PER_POINT = (321.178112e6 + 4.125184e6) / 2e7  # k_bin_accumulate, 2-D, w = 7
 
 
 def parse():
@@ -452,7 +452,7 @@ def main():
     peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = f_pt * n / (ms_kernel / 1e3) / 1e12
     # DRAM bytes of one k_bin_accumulate launch: ncu capture of this kernel at n = 2e7
-    # (dram__bytes_read.sum 321.2 MB + dram__bytes_write.sum 3.85 MB), scaled by points
+    # (dram__bytes_read.sum 321.2 MB + dram__bytes_write.sum 4.1 MB), scaled by points
     # (the reads are the 16-byte partition records, the writes the grid flush)
     traffic = ACC_DRAM_BYTES_PER_POINT * n if (d == 2 and w == 7) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
@@ -466,6 +466,13 @@ def main():
                           "ms_solve": statistics.mean(r["ms_solve"] for r in reps), "cg_iters": reps[-1]["cg_iters"]},
                 "hbm_view": {"bytes_per_point_input": 12, "achieved_GBs": 12 * n / (ms_spread / 1e3) / 1e9,
                              "peak_GBs": peaks.get("hbm_gbs"), "of": "measured"}}
+    # the whole fit against the slower of the point bytes over HBM and the spreading
+    # arithmetic at the FP32 peak (points/s)
+    hbm = peaks.get("hbm_gbs") or 6400.0
+    bound_pts = min(hbm * 1e9 / 12.0, peak_tflops * 1e12 / f_pt)
+    roofline["fit_view"] = {"bound_points_per_s": bound_pts, "achieved_points_per_s": value / world,
+                            "frac": value / world / bound_pts,
+                            "basis": "min(measured HBM / 12 B, derived FP32 peak / %d flop) per GPU" % f_pt}
 
     line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
