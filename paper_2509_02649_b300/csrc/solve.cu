@@ -1594,13 +1594,17 @@ struct CgP {
 };
 
 // all CTAs of the launch; false when the wait gave up (the caller returns)
+// The CTA barrier orders the block's writes before thread 0's fence and arrival, and
+// thread 0's fence after the release orders them before the block's later reads (the
+// cumulativity argument of a cooperative grid barrier), so only thread 0 fences.
 __device__ bool grid_sync(GridBar* gb, unsigned* flags) {
   __shared__ int s_ok;
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned g = atomicAdd(&gb->gen, 0u);
+    unsigned g;  // the generation cannot advance before this CTA arrives
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(&gb->gen) : "memory");
+    __threadfence();
     if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
       atomicExch(&gb->count, 0u);
       __threadfence();
