@@ -6,6 +6,8 @@
 // matvec runs through a circulant embedding and FFTs (Sec. 2.3, matvec via FFT),
 // batched over every (penalty, right-hand side) pair.
 #include "fk_internal.cuh"
+
+#include <cstring>
 #include "fft_device.cuh"
 
 #include <map>
@@ -2019,34 +2021,32 @@ fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, 
   FK_TRY(scr.alloc(&A.p, 2 * D * nsys));
   FK_TRY(scr.alloc(&A.q, 2 * D * nsys));
   FK_TRY(scr.alloc(&A.buf, static_cast<size_t>(nsys) * K * Lc));
+  // scalars [rz 2n | rr 2n | pq n | bb n | rres n | info], then the barrier: one memset,
+  // and bb, rres and info come back in one copy
   double* scal;
-  FK_TRY(scr.alloc(&scal, 7 * static_cast<size_t>(nsys)));
-  FK_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * 7 * nsys, st));
+  FK_TRY(scr.alloc(&scal, 7 * static_cast<size_t>(nsys) + 1 + 8));
+  FK_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * (7 * nsys + 1 + 8), st));
   A.rz = scal;
   A.rr = scal + 2 * nsys;
   A.pq = scal + 4 * nsys;
   A.bb = scal + 5 * nsys;
   A.rres = scal + 6 * nsys;
-  unsigned char* misc;
-  FK_TRY(scr.alloc(&misc, 64));
-  FK_CUDA(cudaMemsetAsync(misc, 0, 64, st));
-  A.bar = reinterpret_cast<GridBar*>(misc);
-  A.info = reinterpret_cast<int*>(misc + 32);
+  A.info = reinterpret_cast<int*>(scal + 7 * nsys);
+  A.bar = reinterpret_cast<GridBar*>(scal + 7 * nsys + 1);
   A.flags = flags;
   void* args[] = {&A};
   FK_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_cg_persist2d), dim3(nb), dim3(threads), args, smem,
                                       st));
   note_launch();
-  int info[2] = {0, 0};
-  unsigned fl = 0;
-  std::vector<double> rres(nsys), bb(nsys);
-  FK_CUDA(cudaMemcpyAsync(info, A.info, sizeof(info), cudaMemcpyDeviceToHost, st));
-  FK_CUDA(cudaMemcpyAsync(rres.data(), A.rres, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
-  FK_CUDA(cudaMemcpyAsync(bb.data(), A.bb, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
-  FK_CUDA(cudaMemcpyAsync(&fl, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  std::vector<double> back(2 * static_cast<size_t>(nsys) + 1);  // bb, rres, info
+  FK_CUDA(cudaMemcpyAsync(back.data(), A.bb, sizeof(double) * back.size(), cudaMemcpyDeviceToHost, st));
   FK_CUDA(cudaStreamSynchronize(st));
   *handled = true;
-  if (fl & FLAG_TIMEOUT) return set_error(FK_ETIMEOUT, "CG grid barrier gave up");
+  const double* bb = back.data();
+  const double* rres = bb + nsys;
+  int info[2];
+  std::memcpy(info, bb + 2 * nsys, sizeof(info));
+  // a barrier that gave up sets FK_ETIMEOUT in the flag word, which the caller checks
   double worst = 0.0;
   for (int s = 0; s < nsys; ++s) worst = std::max(worst, bb[s] > 0 ? std::sqrt(rres[s] / bb[s]) : std::sqrt(rres[s]));
   if (iters_out) *iters_out = info[0];
