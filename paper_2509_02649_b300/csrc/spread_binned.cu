@@ -570,22 +570,24 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter1(PartArgs A) {
       if (my_c > 0) my_pos = atomicAdd(A.fill + tid, my_c);
     }
     if (tid >= S2_THREADS - 32) {  // exclusive scan of the tile counts (last warp)
+      // each lane sums a run of consecutive owners, one warp scan of the run sums,
+      // then each lane writes its run's prefixes: no serial loop over warp-wide chunks
       const int ln = tid - (S2_THREADS - 32);
-      int carry = 0;
-      for (int o0 = 0; o0 <= G; o0 += 32) {
-        const int o = o0 + ln;
-        const int v = (o < G) ? tcnt[o] : 0;
-        int incl = v;
+      const int per = (G + 1 + 31) / 32;
+      const int o0 = ln * per, o1 = min(o0 + per, G + 1);
+      int run = 0;
+      for (int o = o0; o < o1; ++o) run += (o < G) ? tcnt[o] : 0;
+      int incl = run;
 #pragma unroll
-        for (int dd = 1; dd < 32; dd <<= 1) {
-          const int t = __shfl_up_sync(0xffffffffu, incl, dd);
-          if (ln >= dd) incl += t;
-        }
-        if (o <= G) {
-          tcur[o] = carry + incl - v;
-          toff[o] = carry + incl - v;
-        }
-        carry += __shfl_sync(0xffffffffu, incl, 31);
+      for (int dd = 1; dd < 32; dd <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, dd);
+        if (ln >= dd) incl += t;
+      }
+      int acc = incl - run;
+      for (int o = o0; o < o1; ++o) {
+        tcur[o] = acc;
+        toff[o] = acc;
+        acc += (o < G) ? tcnt[o] : 0;
       }
     }
     __syncthreads();
