@@ -264,7 +264,8 @@ FK_API fk_status fk_accum_destroy(fk_accum* acc);
  *     fk_capture_end the calls only record work: they return FK_OK without running
  *     it, and their outputs are written when the graph is launched.  Calls whose path
  *     needs a host round trip return FK_EINVAL and nothing of them is recorded:
- *     conjugate-gradient solves (use FK_SOLVER_CHOL, D <= 8192), fk_hypergrad,
+ *     conjugate-gradient solves other than the 2-D single-launch solver (use
+ *     FK_SOLVER_CHOL, D <= 8192, for the others), fk_hypergrad,
  *     fk_penalty_grads, fk_accum_*, fk_type1_noalloc, any call given a report, and
  *     fits with more than 256 lambdas.  Autotuning is off during a capture (stored
  *     shapes are used).
@@ -274,7 +275,7 @@ FK_API fk_status fk_accum_destroy(fk_accum* acc);
  *     new data written into the inputs give new outputs.  Scratch memory is allocated
  *     and freed inside the graph.
  *   fk_graph_status: waits for the last launch, then returns the device-side condition
- *     of that run (FK_ERANGE, FK_ENOTPD, FK_ETIMEOUT) or FK_OK.
+ *     of that run (FK_ERANGE, FK_ENOTPD, FK_ETIMEOUT, FK_ENOCONV) or FK_OK.
  *   fk_graph_destroy: waits for the last launch and frees the graph (NULL allowed).
  * Host arrays passed to captured calls (lambdas, PDE terms, box corners) are read at
  * capture time; device buffers must stay valid while the graph is used. */
@@ -284,6 +285,11 @@ FK_API fk_status fk_capture_end(void* stream, fk_graph** graph);
 FK_API fk_status fk_graph_launch(fk_graph* graph, void* stream);
 FK_API fk_status fk_graph_status(fk_graph* graph);
 FK_API fk_status fk_graph_destroy(fk_graph* graph);
+/* Time (ms) of the main spreading kernel (the 2-D binned accumulation, the 1-D
+ * fixed-point spreader or the atomic spreader) in the last launch of the graph, from
+ * event record nodes placed around it at capture (the last such kernel if the capture
+ * holds several).  Waits for that launch. */
+FK_API fk_status fk_graph_kernel_ms(fk_graph* graph, float* ms);
 
 /* Synthetic 1-D sweep sample generated on the device (the paper's experiments are on
  * synthetic data; this one is too large to pass from the host).  Points first ..

@@ -33,7 +33,8 @@ EXPORTS = ["fk_default_opts", "fk_fit_sobolev", "fk_fit_pik", "fk_fit_additive",
            "fk_accum_create", "fk_accum_add", "fk_accum_system", "fk_accum_fit_sobolev", "fk_accum_reset",
            "fk_accum_destroy", "fk_generate_sweep_1d", "fk_release_workspace", "fk_autotune_table",
            "fk_autotune_clear", "fk_fit_pik_general", "fk_box_moments", "fk_fit_sobolev_pairs",
-           "fk_capture_begin", "fk_capture_end", "fk_graph_launch", "fk_graph_status", "fk_graph_destroy"]
+           "fk_capture_begin", "fk_capture_end", "fk_graph_launch", "fk_graph_status", "fk_graph_destroy",
+           "fk_graph_kernel_ms"]
 
 
 class FkError(RuntimeError):
@@ -107,6 +108,7 @@ def lib() -> ctypes.CDLL:
             "fk_graph_launch": (_I, [_P, _P]),
             "fk_graph_status": (_I, [_P]),
             "fk_graph_destroy": (_I, [_P]),
+            "fk_graph_kernel_ms": (_I, [_P, ctypes.POINTER(ctypes.c_float)]),
             "fk_fit_sobolev_pairs": (_I, [_I, _L, _P, _P, _I, _I, _P, _P, _I, _I, _D, _I, _P, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
@@ -523,6 +525,12 @@ class Graph:
     def status(self):
         """Waits for the last launch and raises FkError on a device-side condition."""
         _check(lib().fk_graph_status(self._ptr))
+
+    def kernel_ms(self) -> float:
+        """Time of the main spreading kernel in the last launch (event record nodes)."""
+        v = ctypes.c_float()
+        _check(lib().fk_graph_kernel_ms(self._ptr, ctypes.byref(v)))
+        return v.value
 
     def close(self):
         if self._ptr:

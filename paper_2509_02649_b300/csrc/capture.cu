@@ -8,16 +8,21 @@
 //    stream, freed inside the graph);
 //  * report device-side conditions into one flag word owned by the graph, zeroed at
 //    the start of every replay and read by fk_graph_status;
-//  * never synchronise: calls whose path needs a host round trip (conjugate gradients,
-//    the held-out loss, streaming sums, per-call reports, autotuning) refuse with
-//    FK_EINVAL instead of being recorded.
+//  * never synchronise: calls whose path needs a host round trip (conjugate gradients
+//    other than the 2-D single-launch solver, the held-out loss, streaming sums,
+//    per-call reports, autotuning) refuse with FK_EINVAL instead of being recorded;
+//  * bracket the main spreading kernel with event record nodes, so that its time in
+//    the last replay can be read (fk_graph_kernel_ms).
 #include "fk_internal.cuh"
 
 struct fk_graph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   unsigned* flags = nullptr;
-  cudaStream_t last = nullptr;
+  cudaStream_t last = nullptr;  // stream of the last launch (may be the legacy stream)
+  bool launched = false;
+  cudaEvent_t kstart = nullptr, kstop = nullptr;  // main spreading kernel, if recorded
+  bool timed = false;
 };
 
 namespace fk {
@@ -55,6 +60,14 @@ fk_status fk_capture_begin(void* stream) {
     delete c;
     return set_error(FK_ENOMEM, "capture flag word");
   }
+  if (cudaEventCreate(&c->kstart) != cudaSuccess || cudaEventCreate(&c->kstop) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->kstart) cudaEventDestroy(c->kstart);
+    if (c->kstop) cudaEventDestroy(c->kstop);
+    cudaFree(c->flags);
+    delete c;
+    return set_error(FK_ECUDA, "capture events");
+  }
   cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) {
@@ -62,6 +75,8 @@ fk_status fk_capture_begin(void* stream) {
     cudaStreamEndCapture(st, &g);
     if (g) cudaGraphDestroy(g);
     cudaGetLastError();
+    cudaEventDestroy(c->kstart);
+    cudaEventDestroy(c->kstop);
     cudaFree(c->flags);
     delete c;
     return set_error(FK_ECUDA, "stream capture: %s", cudaGetErrorString(e));
@@ -83,6 +98,8 @@ fk_status fk_capture_end(void* stream, fk_graph** out) {
   if (e != cudaSuccess || failed || !g) {
     if (g) cudaGraphDestroy(g);
     cudaGetLastError();
+    cudaEventDestroy(c->kstart);
+    cudaEventDestroy(c->kstop);
     cudaFree(c->flags);
     delete c;
     if (failed) return set_error(FK_EINVAL, "a captured call failed; the graph is discarded");
@@ -93,6 +110,8 @@ fk_status fk_capture_end(void* stream, fk_graph** out) {
   if (e != cudaSuccess) {
     cudaGetLastError();
     cudaGraphDestroy(g);
+    cudaEventDestroy(c->kstart);
+    cudaEventDestroy(c->kstop);
     cudaFree(c->flags);
     delete c;
     return set_error(FK_ECUDA, "graph instantiation: %s", cudaGetErrorString(e));
@@ -101,6 +120,9 @@ fk_status fk_capture_end(void* stream, fk_graph** out) {
   r->graph = g;
   r->exec = exec;
   r->flags = c->flags;
+  r->kstart = c->kstart;
+  r->kstop = c->kstop;
+  r->timed = c->timed;
   delete c;
   *out = r;
   clear_error();
@@ -114,6 +136,7 @@ fk_status fk_graph_launch(fk_graph* g, void* stream) {
   FK_CUDA(cudaGraphLaunch(g->exec, st));
   note_launch();
   g->last = st;
+  g->launched = true;
   return FK_OK;
 }
 
@@ -121,7 +144,7 @@ fk_status fk_graph_status(fk_graph* g) {
   clear_error();
   if (!g) return set_error(FK_EINVAL, "null graph");
   unsigned h = 0;
-  if (g->last) FK_CUDA(cudaStreamSynchronize(g->last));
+  if (g->launched) FK_CUDA(cudaStreamSynchronize(g->last));
   FK_CUDA(cudaMemcpy(&h, g->flags, sizeof(unsigned), cudaMemcpyDeviceToHost));
   return flags_status(h);
 }
@@ -129,11 +152,23 @@ fk_status fk_graph_status(fk_graph* g) {
 fk_status fk_graph_destroy(fk_graph* g) {
   clear_error();
   if (!g) return FK_OK;
-  if (g->last) cudaStreamSynchronize(g->last);
+  if (g->launched) cudaStreamSynchronize(g->last);
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   if (g->flags) cudaFree(g->flags);
+  if (g->kstart) cudaEventDestroy(g->kstart);
+  if (g->kstop) cudaEventDestroy(g->kstop);
   delete g;
+  return FK_OK;
+}
+
+fk_status fk_graph_kernel_ms(fk_graph* g, float* ms) {
+  clear_error();
+  if (!g || !ms) return set_error(FK_EINVAL, "null argument");
+  if (!g->timed) return set_error(FK_EINVAL, "the captured calls ran no timed spreading kernel");
+  if (!g->launched) return set_error(FK_EINVAL, "the graph has not been launched");
+  FK_CUDA(cudaEventSynchronize(g->kstop));
+  FK_CUDA(cudaEventElapsedTime(ms, g->kstart, g->kstop));
   return FK_OK;
 }
 

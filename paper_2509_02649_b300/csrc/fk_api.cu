@@ -18,24 +18,46 @@ static thread_local KernelTimer g_ktimer;
 KernelTimer* kernel_timer() { return &g_ktimer; }
 
 // Arms the main-kernel timer for one call when a report is requested.
+// During a capture the timer records the capture's own events as event record nodes,
+// read after a replay by fk_graph_kernel_ms.
 struct KernelTimerScope {
   KernelTimer* t;
-  explicit KernelTimerScope(bool enabled) : t(kernel_timer()) {
-    t->on = enabled;
+  cudaEvent_t own_start = nullptr, own_stop = nullptr;
+  CaptureCtx* cap;
+  explicit KernelTimerScope(bool enabled) : t(kernel_timer()), cap(capture_ctx()) {
     t->recorded = false;
+    t->rec_flags = 0;
+    if (cap) {
+      own_start = t->start;
+      own_stop = t->stop;
+      t->start = cap->kstart;
+      t->stop = cap->kstop;
+      t->rec_flags = cudaEventRecordExternal;
+      t->on = cap->kstart != nullptr;
+      return;
+    }
+    t->on = enabled;
     if (enabled && !t->start) {
       cudaEventCreate(&t->start);
       cudaEventCreate(&t->stop);
     }
   }
   double ms() {
-    if (!t->on || !t->recorded) return 0.0;
+    if (cap || !t->on || !t->recorded) return 0.0;
     float v = 0.f;
     cudaEventSynchronize(t->stop);
     cudaEventElapsedTime(&v, t->start, t->stop);
     return v;
   }
-  ~KernelTimerScope() { t->on = false; }
+  ~KernelTimerScope() {
+    if (cap) {
+      if (t->recorded) cap->timed = true;
+      t->start = own_start;
+      t->stop = own_stop;
+      t->rec_flags = 0;
+    }
+    t->on = false;
+  }
 };
 
 static std::mutex g_pool_mutex;
@@ -81,6 +103,7 @@ fk_status flags_status(unsigned h) {
   if (h & FLAG_NOTPD) return set_error(FK_ENOTPD, "Cholesky met a non-positive pivot");
   if (h & FLAG_TIMEOUT) return set_error(FK_ETIMEOUT, "a bounded device wait gave up");
   if (h & FLAG_INTERNAL) return set_error(FK_EINTERNAL, "device index check failed");
+  if (h & FLAG_NOCONV) return set_error(FK_ENOCONV, "conjugate gradients did not converge");
   if (h) return set_error(FK_EINTERNAL, "device flag 0x%x", h);
   return FK_OK;
 }

@@ -26,6 +26,7 @@ struct KernelTimer {
   bool on = false;
   bool recorded = false;
   cudaEvent_t start = nullptr, stop = nullptr;
+  unsigned rec_flags = 0;  // cudaEventRecordExternal during a capture (event record nodes)
 };
 KernelTimer* kernel_timer();  // thread-local
 
@@ -49,6 +50,7 @@ enum : unsigned {
   FLAG_NOTPD = 2u,      // Cholesky pivot <= 0
   FLAG_INTERNAL = 4u,   // an index check failed
   FLAG_TIMEOUT = 8u,    // a bounded wait gave up
+  FLAG_NOCONV = 16u,    // conjugate gradients did not converge
 };
 
 // ------------------------------------------------------------------ complex
@@ -100,6 +102,8 @@ struct CaptureCtx {
   cudaStream_t st = nullptr;
   unsigned* flags = nullptr;  // the graph's flag word
   bool failed = false;        // a call returned an error during the capture
+  cudaEvent_t kstart = nullptr, kstop = nullptr;  // main spreading kernel of the captured calls
+  bool timed = false;                             // recorded as event nodes at least once
 };
 CaptureCtx* capture_ctx();
 // FK_EINVAL when a capture is active and the call cannot be recorded (another stream,

@@ -1453,9 +1453,6 @@ fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, 
   if (cg_iters) *cg_iters = 0;
   if (rel_res) *rel_res = 0.0;
   if (solver == FK_SOLVER_CG) {
-    if (capture_ctx())
-      return set_error(FK_EINVAL, "conjugate gradients test convergence on the host: not capturable "
-                                  "(the Cholesky solver is, for D <= 8192)");
     if (d == 2) {
       bool handled = false;
       const fk_status rc = cg_solve_persistent(m, T, W, n_w, rhs, n_rhs, o, sol, st, scratch, flags, cg_iters, rel_res,
@@ -1463,6 +1460,9 @@ fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, 
       if (handled || rc != FK_OK) return rc;
       if (with_op) return set_error(FK_EINVAL, "the operator penalty's CG needs a cooperative launch");
     }
+    if (capture_ctx())
+      return set_error(FK_EINVAL, "this conjugate-gradient path tests convergence on the host: not capturable "
+                                  "(the 2-D single-launch CG and the Cholesky solver are)");
     if (d <= 2) return cg_solve_fused(d, m, T, W, n_w, rhs, n_rhs, o, sol, st, scratch, cg_iters, rel_res,
                                       with_op ? op : nullptr);
     if (with_op) return set_error(FK_EINVAL, "the operator penalty is built for d <= 2");
@@ -1920,6 +1920,7 @@ __global__ void __launch_bounds__(256) k_cg_persist2d(CgP A) {
     for (int s = 0; s < A.nsys; ++s) left += cg_active(A, it, s) ? 1 : 0;
     A.info[0] = it;
     A.info[1] = left;
+    if (left) atomicOr(A.flags, FLAG_NOCONV);
   }
   // true residual of the result
   cgp_rows_fwd(A, sl, it, true);
@@ -1937,7 +1938,6 @@ fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, 
                               const fk_opts& o, double* sol, cudaStream_t st, Scratch& scr, unsigned* flags,
                               int* iters_out, double* relres_out, bool* handled, const PenOp* op) {
   *handled = false;
-  if (capture_ctx()) return FK_OK;  // the one-CTA form is recorded instead of a cooperative launch
   int dev = 0, coop = 0, sms = 0;
   FK_CUDA(cudaGetDevice(&dev));
   FK_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
@@ -2038,6 +2038,13 @@ fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, 
   FK_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_cg_persist2d), dim3(nb), dim3(threads), args, smem,
                                       st));
   note_launch();
+  if (capture_ctx()) {
+    // recorded, not run: no read-back; non-convergence reaches the graph's flag word
+    *handled = true;
+    if (iters_out) *iters_out = 0;
+    if (relres_out) *relres_out = 0.0;
+    return FK_OK;
+  }
   std::vector<double> back(2 * static_cast<size_t>(nsys) + 1);  // bb, rres, info
   FK_CUDA(cudaMemcpyAsync(back.data(), A.bb, sizeof(double) * back.size(), cudaMemcpyDeviceToHost, st));
   FK_CUDA(cudaStreamSynchronize(st));

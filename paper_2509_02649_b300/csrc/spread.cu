@@ -119,11 +119,11 @@ fk_status spread_atomic(const EsPlan& p, int64_t n, const R* x, const R* y, int 
   if (n == 0) return FK_OK;
   const int block = 256;
   KernelTimer* kt = kernel_timer();
-  if (kt->on) cudaEventRecord(kt->start, st);
+  if (kt->on) cudaEventRecordWithFlags(kt->start, st, kt->rec_flags);
   k_spread_atomic<R><<<grid_for(n, block, 148 * 16), block, 0, st>>>(
       p.d, make_win<R>(p.N, p.w), static_cast<R>(p.beta), n, x, y, n_y, with_ones ? 1 : 0, grid, flags); note_launch();
   if (kt->on) {
-    cudaEventRecord(kt->stop, st);
+    cudaEventRecordWithFlags(kt->stop, st, kt->rec_flags);
     kt->recorded = true;
   }
   FK_CUDA(cudaGetLastError());

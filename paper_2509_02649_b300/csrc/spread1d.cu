@@ -359,10 +359,10 @@ fk_status spread1d_run(const EsPlan& p, int64_t n, const float* x, const float* 
   if (!fn) return set_error(FK_EINVAL, "1-D fixed-point spreading: w = %d not built", p.w);
   FK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_max)));
   KernelTimer* kt = kernel_timer();
-  if (kt->on) cudaEventRecord(kt->start, st);
+  if (kt->on) cudaEventRecordWithFlags(kt->start, st, kt->rec_flags);
   fn<<<nblocks, THREADS, smem_max, st>>>(A); note_launch();
   if (kt->on) {
-    cudaEventRecord(kt->stop, st);
+    cudaEventRecordWithFlags(kt->stop, st, kt->rec_flags);
     kt->recorded = true;
   }
   FK_CUDA(cudaGetLastError());

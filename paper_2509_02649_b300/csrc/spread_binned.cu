@@ -1031,10 +1031,10 @@ fk_status spread_binned_run(const EsPlan& p, int64_t n, const float* x, const fl
     s1fn<<<P.nblk, S2_THREADS, sm1, st>>>(P); note_launch();
     FK_CUDA(cudaGetLastError());
     A.mode = 1;
-    if (kt->on) cudaEventRecord(kt->start, st);
+    if (kt->on) cudaEventRecordWithFlags(kt->start, st, kt->rec_flags);
     fn<<<G, threads, sm, st>>>(A); note_launch();
     if (kt->on) {
-      cudaEventRecord(kt->stop, st);
+      cudaEventRecordWithFlags(kt->stop, st, kt->rec_flags);
       kt->recorded = true;
     }
     FK_CUDA(cudaGetLastError());
@@ -1057,10 +1057,10 @@ fk_status spread_binned_run(const EsPlan& p, int64_t n, const float* x, const fl
     k_bin_scatter<<<P.nblk, S_THREADS, sm_scatter, st>>>(P); note_launch();
   }
   FK_CUDA(cudaGetLastError());
-  if (!one_pass && kt->on) cudaEventRecord(kt->start, st);
+  if (!one_pass && kt->on) cudaEventRecordWithFlags(kt->start, st, kt->rec_flags);
   fn<<<G, threads, sm, st>>>(A); note_launch();
   if (!one_pass && kt->on) {
-    cudaEventRecord(kt->stop, st);
+    cudaEventRecordWithFlags(kt->stop, st, kt->rec_flags);
     kt->recorded = true;
   }
   FK_CUDA(cudaGetLastError());

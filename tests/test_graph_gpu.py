@@ -138,12 +138,12 @@ def test_replay_reports_range_error_then_recovers():
 
 
 def test_uncapturable_calls_refuse_and_leave_the_stream_usable():
-    n, m = 20_000, 40  # D = 81^2 > 1024: the automatic solver is CG
-    x = torch.empty((2, n), dtype=torch.float32, device="cuda")
+    n, m = 20_000, 600  # 1-D, D = 1201 > 1024: the automatic solver is the batched 1-D CG
+    x = torch.empty((1, n), dtype=torch.float32, device="cuda")
     y = torch.empty((1, n), dtype=torch.float32, device="cuda")
     fill_uniform(x, 51)
     fill_normal(y, 52)
-    out = torch.empty((1, 1, (2 * m + 1) ** 2), dtype=torch.complex128, device="cuda")
+    out = torch.empty((1, 1, 2 * m + 1), dtype=torch.complex128, device="cuda")
     torch.cuda.synchronize()
     with pytest.raises(fk.FkError) as e:
         with fk.capture():
@@ -152,7 +152,7 @@ def test_uncapturable_calls_refuse_and_leave_the_stream_usable():
     with pytest.raises(fk.FkError):
         with fk.capture():
             fk.fk_fit_sobolev(x, y, 5, 2.0, [1e-4], 1e-6, "mixed", out=torch.empty(
-                (1, 1, 121), dtype=torch.complex128, device="cuda"), report=True)
+                (1, 1, 11), dtype=torch.complex128, device="cuda"), report=True)
     with pytest.raises(ValueError):
         with fk.capture():
             fk.fk_fit_sobolev(x, y, 5, 2.0, [1e-4], 1e-6, "mixed")  # no out=
@@ -160,6 +160,36 @@ def test_uncapturable_calls_refuse_and_leave_the_stream_usable():
     th = fk.fk_fit_sobolev(x, y, m, 2.0, [1e-4], 1e-6, "mixed")
     torch.cuda.synchronize()
     assert torch.isfinite(th.real).all()
+
+
+def test_two_d_cg_fit_replays_with_kernel_timing():
+    # the 2-D single-launch CG (D = 41^2 > 1024) records into the graph; its convergence
+    # failure reaches the graph's status as FK_ENOCONV
+    n, m = 400_000, 20
+    x = torch.empty((2, n), dtype=torch.float32, device="cuda")
+    y = torch.empty((1, n), dtype=torch.float32, device="cuda")
+    theta = torch.empty((1, 1, (2 * m + 1) ** 2), dtype=torch.complex128, device="cuda")
+    fill_uniform(x, 91)
+    fill_normal(y, 92)
+    y.mul_(0.05).add_(torch.exp(-(x ** 2).sum(0)))
+    torch.cuda.synchronize()
+    with fk.capture() as g:
+        fk.fk_fit_sobolev(x, y, m, 2.0, [1e-6], 1e-6, "mixed", out=theta)
+    g.launch()
+    g.status()
+    assert g.kernel_ms() > 0.0
+    want = fk.fk_fit_sobolev(x, y, m, 2.0, [1e-6], 1e-6, "mixed")
+    torch.cuda.synchronize()
+    assert rel(theta.cpu().numpy(), want.cpu().numpy()) < 1e-6
+    g.close()
+    opts = fk.default_opts(cg_maxit=1, cg_tol=1e-15)
+    with fk.capture() as g2:
+        fk.fk_fit_sobolev(x, y, m, 2.0, [1e-6], 1e-6, "mixed", opts=opts, out=theta)
+    g2.launch()
+    with pytest.raises(fk.FkError) as e:
+        g2.status()
+    assert e.value.name == "FK_ENOCONV"
+    g2.close()
 
 
 def test_graph_of_many_small_fits_matches_direct_calls():
