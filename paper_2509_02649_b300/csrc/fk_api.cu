@@ -397,7 +397,7 @@ fk_status fk_solve(int d, int m, const double* T, const double* W, int n_w, cons
   FK_TRY(fl.init(scr));
   int iters = 0;
   double rr = 0;
-  FK_TRY(solve_system(d, m, T, W, n_w, rhs, n_rhs, o, sol, st, scr, fl.dev, &iters, &rr));
+  FK_TRY(solve_system(d, m, T, W, n_w, rhs, n_rhs, o, sol, st, scr, fl.dev, &iters, rep ? &rr : nullptr));
   FK_TRY(fl.check());
   if (rep) {
     *rep = fk_report{};
@@ -449,7 +449,7 @@ static fk_status fit_common(int d, int64_t n, const void* x, const void* y, int 
   }
   int iters = 0;
   double rr = 0;
-  FK_TRY(solve_system(d, m, T, W, n_lambda, b, n_targets, o, theta, st, scr, fl.dev, &iters, &rr,
+  FK_TRY(solve_system(d, m, T, W, n_lambda, b, n_targets, o, theta, st, scr, fl.dev, &iters, rep ? &rr : nullptr,
                       cmom ? &op : nullptr));
   tm.mark();
   FK_TRY(fl.check());
@@ -522,7 +522,7 @@ fk_status fk_fit_sobolev_pairs(int d, int64_t n, const void* x, const void* y, i
                            W + static_cast<int64_t>(i) * D, st));
   int iters = 0;
   double rr = 0;
-  FK_TRY(solve_system(d, m, T, W, n_pairs, b, n_targets, o, theta, st, scr, fl.dev, &iters, &rr));
+  FK_TRY(solve_system(d, m, T, W, n_pairs, b, n_targets, o, theta, st, scr, fl.dev, &iters, rep ? &rr : nullptr));
   tm.mark();
   FK_TRY(fl.check());
   if (rep) {
@@ -740,7 +740,7 @@ fk_status fk_accum_fit_sobolev(fk_accum* a, double s, int penalty, const double*
   FK_TRY(penalty_weights(d, m, penalty, s, a->o.sobolev_c0, lambdas, n_lambda, 0.0, 0, nullptr, nullptr, W, st));
   int iters = 0;
   double rr = 0;
-  FK_TRY(solve_system(d, m, T, W, n_lambda, b, a->nt, a->o, theta, st, scr, fl.dev, &iters, &rr));
+  FK_TRY(solve_system(d, m, T, W, n_lambda, b, a->nt, a->o, theta, st, scr, fl.dev, &iters, rep ? &rr : nullptr));
   tm.mark();
   FK_TRY(fl.check());
   FK_TRY(accum_flags(a, st));

@@ -1593,6 +1593,8 @@ struct CgP {
   double mu;
   const double* Wd;
   cplx<double>* buf2;
+  double* idg;         // [n_w][D] inverse Jacobi diagonal 1 / (T_0 + Wd), set by the init phase
+  int final_residual;  // one more matvec for |b - A x| (reports only)
 };
 
 // all CTAs of the launch; false when the wait gave up (the caller returns)
@@ -1814,14 +1816,14 @@ __device__ void cgp_rows_inv(const CgP& A, cplx<double>* sl, double* red, int it
 }
 
 // P4 (final: |b - q|^2 into rres)
-__device__ void cgp_update(const CgP& A, double* red, int it, bool final_pass, double T0) {
+__device__ void cgp_update(const CgP& A, double* red, int it, bool final_pass) {
   const int64_t D = A.D;
-  const int chunk = 4 * blockDim.x;
+  const int chunk = blockDim.x;  // one entry per thread: the phase spreads over D / 256 CTAs
   const int nch = static_cast<int>((D + chunk - 1) / chunk);
   for (int item = blockIdx.x; item < A.nsys * nch; item += gridDim.x) {
     const int s = item / nch, cb = item - s * nch;
     if (!final_pass && !cg_active(A, it, s)) continue;
-    const double* Ws = A.Wd + static_cast<int64_t>(s / A.n_rhs) * D;
+    const double* idg = A.idg + static_cast<int64_t>(s / A.n_rhs) * D;
     const double* bs = A.b + 2 * static_cast<int64_t>(s % A.n_rhs) * D;
     double a1 = 0.0, a2 = 0.0;
     const double alpha = final_pass ? 0.0 : __ldcg(A.rz + (it & 1) * A.nsys + s) / __ldcg(A.pq + s);
@@ -1840,7 +1842,7 @@ __device__ void cgp_update(const CgP& A, double* red, int it, bool final_pass, d
       const double r0 = __ldcg(A.r + o) - alpha * q0, r1 = __ldcg(A.r + o + 1) - alpha * q1;
       A.r[o] = r0;
       A.r[o + 1] = r1;
-      const double id = 1.0 / (T0 + Ws[k]);
+      const double id = __ldcg(idg + k);
       A.z[o] = r0 * id;
       A.z[o + 1] = r1 * id;
       a1 += (r0 * r0 + r1 * r1) * id;
@@ -1874,6 +1876,7 @@ __device__ void cgp_init(const CgP& A, double* red, double T0) {
       const int64_t o = 2 * (s * D + k);
       const double b0 = bs[2 * k], b1 = bs[2 * k + 1];
       const double id = 1.0 / (T0 + Ws[k]);
+      if (s % A.n_rhs == 0) A.idg[static_cast<int64_t>(s / A.n_rhs) * D + k] = id;
       A.x[o] = 0.0;
       A.x[o + 1] = 0.0;
       A.r[o] = b0;
@@ -1912,7 +1915,7 @@ __global__ void __launch_bounds__(256) k_cg_persist2d(CgP A) {
     if (!grid_sync(A.bar, A.flags)) return;
     cgp_rows_inv(A, sl, red, it, false);
     if (!grid_sync(A.bar, A.flags)) return;
-    cgp_update(A, red, it, false, T0);
+    cgp_update(A, red, it, false);
     if (!grid_sync(A.bar, A.flags)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1922,6 +1925,7 @@ __global__ void __launch_bounds__(256) k_cg_persist2d(CgP A) {
     A.info[1] = left;
     if (left) atomicOr(A.flags, FLAG_NOCONV);
   }
+  if (!A.final_residual) return;
   // true residual of the result
   cgp_rows_fwd(A, sl, it, true);
   if (!grid_sync(A.bar, A.flags)) return;
@@ -1929,7 +1933,7 @@ __global__ void __launch_bounds__(256) k_cg_persist2d(CgP A) {
   if (!grid_sync(A.bar, A.flags)) return;
   cgp_rows_inv(A, sl, red, it, true);
   if (!grid_sync(A.bar, A.flags)) return;
-  cgp_update(A, red, it, true, T0);
+  cgp_update(A, red, it, true);
 }
 
 }  // namespace
@@ -2017,6 +2021,8 @@ fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, 
     FK_TRY(scr.alloc(&A.buf2, static_cast<size_t>(nsys) * K * Lc));
   }
   FK_TRY(scr.alloc(&A.r, 2 * D * nsys));
+  FK_TRY(scr.alloc(&A.idg, D * n_w));
+  A.final_residual = relres_out != nullptr;
   FK_TRY(scr.alloc(&A.z, 2 * D * nsys));
   FK_TRY(scr.alloc(&A.p, 2 * D * nsys));
   FK_TRY(scr.alloc(&A.q, 2 * D * nsys));
@@ -2055,7 +2061,8 @@ fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, 
   std::memcpy(info, bb + 2 * nsys, sizeof(info));
   // a barrier that gave up sets FK_ETIMEOUT in the flag word, which the caller checks
   double worst = 0.0;
-  for (int s = 0; s < nsys; ++s) worst = std::max(worst, bb[s] > 0 ? std::sqrt(rres[s] / bb[s]) : std::sqrt(rres[s]));
+  if (relres_out)
+    for (int s = 0; s < nsys; ++s) worst = std::max(worst, bb[s] > 0 ? std::sqrt(rres[s] / bb[s]) : std::sqrt(rres[s]));
   if (iters_out) *iters_out = info[0];
   if (relres_out) *relres_out = worst;
   if (info[1] != 0) return set_error(FK_ENOCONV, "CG did not converge in %d iterations", o.cg_maxit);
