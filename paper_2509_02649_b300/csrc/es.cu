@@ -178,7 +178,8 @@ namespace fk {
 // the change of basis to powers of g (T_0 = 1, T_1 = u, T_{k+1} = 2 u T_k - T_{k-1},
 // u = 2 g), in fp64.
 EsPoly es_poly(int w, double beta) {
-  constexpr int P = ES_POLY_DEG, NP = P + 1;
+  constexpr int PMAX = 8;
+  const int P = es_poly_deg(w), NP = P + 1;
   EsPoly out{};
   const double c = 0.5 * (w - 1);
   auto phi = [&](double z) {
@@ -186,13 +187,13 @@ EsPoly es_poly(int w, double beta) {
     return t > 0.0 ? std::exp(beta * (std::sqrt(t) - 1.0)) : 0.0;
   };
   // monomial coefficients of T_k(u), k = 0..P
-  double Tm[NP][NP] = {};
+  double Tm[PMAX + 1][PMAX + 1] = {};
   Tm[0][0] = 1.0;
   Tm[1][1] = 1.0;
   for (int k = 1; k + 1 < NP; ++k)
     for (int j = 0; j < NP; ++j) Tm[k + 1][j] = (j > 0 ? 2.0 * Tm[k][j - 1] : 0.0) - Tm[k - 1][j];
   for (int a = 0; a < (w + 1) / 2 && a < ES_POLY_MAXW / 2; ++a) {
-    double v[NP], ch[NP], mono[NP] = {};
+    double v[PMAX + 1], ch[PMAX + 1], mono[PMAX + 1] = {};
     for (int j = 0; j < NP; ++j) {
       const double u = std::cos(M_PI * (j + 0.5) / NP);
       v[j] = phi((a - c - 0.5 * u) * 2.0 / w);
@@ -206,8 +207,8 @@ EsPoly es_poly(int w, double beta) {
       for (int j = 0; j < NP; ++j) mono[j] += ch[k] * Tm[k][j];
     // powers of u = 2 g  ->  powers of g
     for (int j = 0; j < NP; ++j) mono[j] *= std::ldexp(1.0, j);
-    for (int j = 0; j < 5; ++j) out.e[a][j] = static_cast<float>(mono[2 * j]);
-    for (int j = 0; j < 4; ++j) out.o[a][j] = static_cast<float>(mono[2 * j + 1]);
+    for (int j = 0; 2 * j < NP; ++j) out.e[a][j] = static_cast<float>(mono[2 * j]);
+    for (int j = 0; 2 * j + 1 < NP; ++j) out.o[a][j] = static_cast<float>(mono[2 * j + 1]);
   }
   return out;
 }
