@@ -32,6 +32,8 @@
 #include "window.cuh"
 #include "es_poly.cuh"
 
+#include <type_traits>
+
 namespace fk {
 
 namespace {
@@ -839,20 +841,30 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
           }
         }
       } else {
-        for (int k = 0; k < nproc; ++k) {
-          const uint4 rec = st[ri];
-          ri = nxt[ri];
-          float px[W], py[W];
-          es_taps_poly<W>(__uint_as_float(rec.y) - gc, A.poly, px);
-          es_taps_poly<W>(__uint_as_float(rec.z) - gc, A.poly, py);
-          const float sv = A.with_ones ? 1.0f : __uint_as_float(rec.w);
+        // one channel: ones (no strength multiply) or the strengths
+        auto one_channel = [&](auto ones_tag) {
+          constexpr bool ONES = decltype(ones_tag)::value;
+          for (int k = 0; k < nproc; ++k) {
+            const uint4 rec = st[ri];
+            ri = nxt[ri];
+            float px[W], py[W];
+            es_taps_poly<W>(__uint_as_float(rec.y) - gc, A.poly, px);
+            es_taps_poly<W>(__uint_as_float(rec.z) - gc, A.poly, py);
+            if (!ONES) {
+              const float sv = __uint_as_float(rec.w);
 #pragma unroll
-          for (int i = 0; i < W; ++i) {
-            const float pa = px[i] * sv;
+              for (int i = 0; i < W; ++i) px[i] *= sv;
+            }
 #pragma unroll
-            for (int j = 0; j < W; ++j) acc[i][j] = fmaf(pa, py[j], acc[i][j]);
+            for (int i = 0; i < W; ++i)
+#pragma unroll
+              for (int j = 0; j < W; ++j) acc[i][j] = fmaf(px[i], py[j], acc[i][j]);
           }
-        }
+        };
+        if (A.with_ones)
+          one_channel(std::true_type{});
+        else
+          one_channel(std::false_type{});
       }
     }
     if (owns) {
