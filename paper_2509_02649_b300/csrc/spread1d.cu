@@ -120,25 +120,22 @@ __global__ void __launch_bounds__(THREADS) k_spread1d_fx(Fx1dArgs A) {
       const float v = yv[c] * S[c];
       unsigned* lc = lo + c * stride + b;
       unsigned old[W];
+      int qv[W];
 #pragma unroll
       for (int a = 0; a < W; ++a) {
-        const int q = __float_as_int(fmaf(psi[a], v, MAGIC)) - MAGIC_BITS;
-        old[a] = atomicAdd(lc + a, static_cast<unsigned>(q));
+        qv[a] = __float_as_int(fmaf(psi[a], v, MAGIC)) - MAGIC_BITS;
+        old[a] = atomicAdd(lc + a, static_cast<unsigned>(qv[a]));
       }
       // high-word change per tap: sign extension of q plus the carry out of the
       // low-word add; nonzero only when the low word wraps (rare)
       int any = 0;
 #pragma unroll
-      for (int a = 0; a < W; ++a) {
-        const int q = __float_as_int(fmaf(psi[a], v, MAGIC)) - MAGIC_BITS;
-        any |= carry_delta(old[a], static_cast<unsigned>(q), q >> 31);
-      }
+      for (int a = 0; a < W; ++a) any |= carry_delta(old[a], static_cast<unsigned>(qv[a]), qv[a] >> 31);
       if (any) {
         int* hc = hi + c * stride + b;
 #pragma unroll
         for (int a = 0; a < W; ++a) {
-          const int q = __float_as_int(fmaf(psi[a], v, MAGIC)) - MAGIC_BITS;
-          const int dh = carry_delta(old[a], static_cast<unsigned>(q), q >> 31);
+          const int dh = carry_delta(old[a], static_cast<unsigned>(qv[a]), qv[a] >> 31);
           if (dh) atomicAdd(hc + a, dh);
         }
       }
