@@ -370,30 +370,6 @@ __global__ void k_chol_inv_pad(int nb, double* Linv) {
     }
 }
 
-// rows i >= kb + nb of the panel: x L11^H = a  =>  x_j = (a_j - sum_{p<j} x_p conj(L11[j][p])) / L11[j][j]
-__global__ void k_chol_panel(double* A, int64_t D, int kb, int nb) {
-  __shared__ cd L[NB][NB + 1];
-  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
-    const int i = t / nb, j = t % nb;
-    const double* p = A + 2 * ((kb + i) * D + (kb + j));
-    L[i][j] = cd{p[0], p[1]};
-  }
-  __syncthreads();
-  const int64_t row = kb + nb + blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (row >= D) return;
-  double* a = A + 2 * (row * D + kb);
-  cd x[NB];
-  for (int j = 0; j < nb; ++j) {
-    cd v = cd{a[2 * j], a[2 * j + 1]};
-    for (int p = 0; p < j; ++p) v = csub(v, cmul(x[p], cconj(L[j][p])));
-    x[j] = cscale(v, 1.0 / L[j][j].x);
-  }
-  for (int j = 0; j < nb; ++j) {
-    a[2 * j] = x[j].x;
-    a[2 * j + 1] = x[j].y;
-  }
-}
-
 // A22[i][j] -= sum_p L21[i][p] conj(L21[j][p]),  lower triangle, TT x TT tiles
 template <int TT>
 __global__ void __launch_bounds__(256) k_chol_update(double* A, int64_t D, int kb, int nb) {
@@ -454,9 +430,9 @@ __global__ void k_chol_panel_mm(double* A, int64_t D, int kb, int nb, const doub
 }
 
 // Blocked right-looking Cholesky A = L L^H in place (lower triangle; the strict upper
-// triangle is zeroed).  linv (optional): [ceil(D / NB)][NB][NB] complex, receives the
-// inverse of every diagonal block (zero-padded); the panel update and the triangular
-// solves use them as products.
+// triangle is zeroed).  linv: [ceil(D / NB)][NB][NB] complex, receives the inverse of
+// every diagonal block (zero-padded); the panel update and the triangular solves use
+// them as products.
 static int64_t linv_blocks(int64_t D) { return (D + NB - 1) / NB; }
 
 static fk_status cholesky(double* A, int64_t D, unsigned* flags, cudaStream_t st, double* linv) {
@@ -466,21 +442,15 @@ static fk_status cholesky(double* A, int64_t D, unsigned* flags, cudaStream_t st
   for (int kb = 0; kb < D; kb += NB) {
     const int nb = static_cast<int>(std::min<int64_t>(NB, D - kb));
     const int64_t rest = D - kb - nb;
-    double* li = linv ? linv + 2 * static_cast<int64_t>(kb / NB) * NB * NB : nullptr;
+    double* li = linv + 2 * static_cast<int64_t>(kb / NB) * NB * NB;
     k_chol_diag<<<1, 256, 0, st>>>(A, D, kb, nb, flags); note_launch();
-    if (li) {
-      if (nb < NB) {
-        k_chol_inv_pad<<<1, 256, 0, st>>>(nb, li); note_launch();
-      }
-      k_chol_inv<<<nb, 32, 0, st>>>(A, D, kb, nb, li); note_launch();
+    if (nb < NB) {
+      k_chol_inv_pad<<<1, 256, 0, st>>>(nb, li); note_launch();
     }
+    k_chol_inv<<<nb, 32, 0, st>>>(A, D, kb, nb, li); note_launch();
     if (rest > 0) {
-      if (li) {
-        k_chol_panel_mm<<<static_cast<int>((rest + PANEL_ROWS - 1) / PANEL_ROWS), 256, 0, st>>>(A, D, kb, nb, li);
-        note_launch();
-      } else {
-        k_chol_panel<<<static_cast<int>((rest + 127) / 128), 128, 0, st>>>(A, D, kb, nb); note_launch();
-      }
+      k_chol_panel_mm<<<static_cast<int>((rest + PANEL_ROWS - 1) / PANEL_ROWS), 256, 0, st>>>(A, D, kb, nb, li);
+      note_launch();
       // 32 x 32 tiles while they fill the SMs twice over, else 16 x 16 (each tile's FP64
       // work sits on one SM, so the late, small updates need more, smaller tiles)
       const int64_t n32 = (rest + 31) / 32;
@@ -495,68 +465,6 @@ static fk_status cholesky(double* A, int64_t D, unsigned* flags, cudaStream_t st
     FK_CUDA(cudaGetLastError());
   }
   return FK_OK;
-}
-
-// Triangular solves for RB right-hand sides per CTA; X holds B on entry, solution on exit.
-// forward:  y_i = (b_i - sum_{j<i} L_ij y_j) / L_ii       (row i of L, contiguous)
-// backward: x_j = y_j / L_jj;  y_i -= conj(L_ji) x_j, i<j  (row j of L, contiguous)
-constexpr int RB = 8;
-__global__ void k_trisolve(const double* L, int64_t D, double* X, int n_rhs) {
-  const int r0 = blockIdx.x * RB;
-  const int nr = min(RB, n_rhs - r0);
-  __shared__ cd red[RB][32];
-  __shared__ cd val[RB];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  // forward
-  for (int64_t i = 0; i < D; ++i) {
-    cd acc[RB];
-    for (int r = 0; r < RB; ++r) acc[r] = cd{0, 0};
-    for (int64_t j = tid; j < i; j += blockDim.x) {
-      const cd l = cd{L[2 * (i * D + j)], L[2 * (i * D + j) + 1]};
-      for (int r = 0; r < nr; ++r) {
-        const double* y = X + 2 * ((r0 + r) * D + j);
-        acc[r] = cadd(acc[r], cmul(l, cd{y[0], y[1]}));
-      }
-    }
-    for (int r = 0; r < nr; ++r) {
-      for (int o = 16; o > 0; o >>= 1) {
-        acc[r].x += __shfl_down_sync(0xffffffffu, acc[r].x, o);
-        acc[r].y += __shfl_down_sync(0xffffffffu, acc[r].y, o);
-      }
-      if (lane == 0) red[r][warp] = acc[r];
-    }
-    __syncthreads();
-    if (tid < nr) {
-      cd s = cd{0, 0};
-      for (int w = 0; w < nw; ++w) s = cadd(s, red[tid][w]);
-      double* y = X + 2 * ((r0 + tid) * D + i);
-      const double lii = L[2 * (i * D + i)];
-      y[0] = (y[0] - s.x) / lii;
-      y[1] = (y[1] - s.y) / lii;
-    }
-    __syncthreads();
-  }
-  // backward
-  for (int64_t j = D - 1; j >= 0; --j) {
-    if (tid < nr) {
-      double* y = X + 2 * ((r0 + tid) * D + j);
-      const double ljj = L[2 * (j * D + j)];
-      y[0] /= ljj;
-      y[1] /= ljj;
-      val[tid] = cd{y[0], y[1]};
-    }
-    __syncthreads();
-    for (int64_t i = tid; i < j; i += blockDim.x) {
-      const cd l = cd{L[2 * (j * D + i)], -L[2 * (j * D + i) + 1]};
-      for (int r = 0; r < nr; ++r) {
-        double* y = X + 2 * ((r0 + r) * D + i);
-        const cd v = cmul(l, val[r]);
-        y[0] -= v.x;
-        y[1] -= v.y;
-      }
-    }
-    __syncthreads();
-  }
 }
 
 // R = B - A X  (dense Hermitian A given by T, W) for refinement; one CTA per (rhs, row block)
@@ -663,13 +571,11 @@ static fk_status trisolve(const double* L, int64_t D, double* X, int n_rhs, cuda
     FK_TRY(trisolve_coop(L, Linv, D, X, n_rhs, st, *scr, flags, &handled));
     if (handled) return FK_OK;
   }
+  // D <= 8192 (the dense route's limit): the vector fits in shared memory
   const size_t smem = sizeof(cd) * (static_cast<size_t>(D) + TS_NB * (TS_NB + 1));
-  if (smem <= 200 * 1024) {
-    FK_CUDA(cudaFuncSetAttribute(k_trisolve_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    k_trisolve_blk<<<n_rhs, TS_THREADS, smem, st>>>(L, static_cast<int>(D), X); note_launch();
-  } else {
-    k_trisolve<<<(n_rhs + RB - 1) / RB, 256, 0, st>>>(L, D, X, n_rhs); note_launch();
-  }
+  if (smem > 200 * 1024) return set_error(FK_EINVAL, "triangular solve: D = %lld too large", (long long)D);
+  FK_CUDA(cudaFuncSetAttribute(k_trisolve_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  k_trisolve_blk<<<n_rhs, TS_THREADS, smem, st>>>(L, static_cast<int>(D), X); note_launch();
   FK_CUDA(cudaGetLastError());
   return FK_OK;
 }
