@@ -240,10 +240,13 @@ def run_row(args, rank, local):
     pik-heat:    n = 1e9 (t, x) points, heat prior, fit + held-out loss and its
                  gradient (autograd) on 1e7 validation points.
     additive-8d: n = 2e8 points in d = 8, m = 64: 8 1-D and 28 2-D transforms,
-                 block Gram and dense FP64 solve."""
+                 block Gram and dense FP64 solve.
+    --n overrides the point count (smaller cases for profiling); --no-autotune keeps
+    the spreaders' default shapes."""
     import torch
     import paper_2509_02649_b300 as fk
     torch.cuda.set_device(local)
+    tune = 0 if args.no_autotune else 1
     st = torch.cuda.current_stream()
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2032.0)
@@ -256,7 +259,7 @@ def run_row(args, rank, local):
         x = torch.empty((1, chunk), dtype=torch.float32, device="cuda")
         y = torch.empty((nt, chunk), dtype=torch.float32, device="cuda")
         amax = torch.empty(nt, dtype=torch.int32, device="cuda")
-        acc = fk.Accumulator(1, m, nt, 1e-6, "mixed", opts=fk.default_opts(autotune=1))
+        acc = fk.Accumulator(1, m, nt, 1e-6, "mixed", opts=fk.default_opts(autotune=tune))
 
         def step():
             ev = []
@@ -286,7 +289,7 @@ def run_row(args, rank, local):
                "chunk": chunk, "timed": "spreading of every chunk + transform + batched solve; generation excluded"}
         kern = "k_spread1d_fx (fixed-point shared-memory spreading, 17 channels)"
     elif W == "pik-heat":
-        n, nv, m = 1_000_000_000, 10_000_000, 25
+        n, nv, m = (args.n if args.n != WL["n"] else 1_000_000_000), 10_000_000, 25
         x = _dev_uniform(torch, n, 2, 11)
         y = torch.exp(-0.1 * x[0]) * torch.sin(x[1]) + 0.1 * _dev_normal(torch, n, 12)
         xv = _dev_uniform(torch, nv, 2, 13)
@@ -304,7 +307,7 @@ def run_row(args, rank, local):
             e1.record(st)
             torch.cuda.synchronize()
             _, rep = fk.fk_fit_pik(x, y, m, 1.0, 1e-8, 1e-2, alpha, [1.0, -0.1], 1e-6, "mixed", report=True,
-                                   opts=fk.default_opts(autotune=1))
+                                   opts=fk.default_opts(autotune=tune))
             return e0.elapsed_time(e1), rep["ms_kernel"], (L.item(), lt.grad.item(), mt.grad.item())
 
         f_pt = 49 * (2 * 2 + 1)
@@ -313,7 +316,7 @@ def run_row(args, rank, local):
                "timed": "fit + held-out loss + hypergradient (autograd forward and backward)"}
         kern = "k_bin_accumulate (register-accumulation spreading, training fit)"
     else:
-        n, d, m = 200_000_000, 8, 64
+        n, d, m = (args.n if args.n != WL["n"] else 200_000_000), 8, 64
         lam = n ** (-0.8)
         x = _dev_uniform(torch, n, d, 41)
         y = 0.1 * _dev_normal(torch, n, 42)
@@ -323,7 +326,7 @@ def run_row(args, rank, local):
         def step():
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            th, rep = fk.fk_fit_additive(x, y, m, [lam], 1e-6, "mixed", report=True, opts=fk.default_opts(autotune=1))
+            th, rep = fk.fk_fit_additive(x, y, m, [lam], 1e-6, "mixed", report=True, opts=fk.default_opts(autotune=tune))
             e1.record(st)
             torch.cuda.synchronize()
             return e0.elapsed_time(e1), rep["ms_spread"], rep
