@@ -170,6 +170,40 @@ __device__ __forceinline__ bool skip_guarded(const PartArgs& A) {
 }
 
 // owner and packed key of one point; returns false for a point out of range
+// Partition records.  Rec16 {owner << 16 | local cell, f0, f1, y} (fp32 bits) carries a
+// strength; Rec8 is the ones-only form of the one-pass partition, half the bytes and
+// twice the records per accumulation round:
+//   lo = v0 | v1 << 24,  hi = v1 >> 8 | local cell << 16,
+//   v = (w/2 - f) 2^24 in [0, 2^24): exact, since f in (w/2 - 1, w/2] is a multiple
+//   of 2^-24 for w >= 3 (fp32 spacing below 4), so g = f - (w - 1)/2 = 1/2 - v 2^-24
+//   decodes to the same fp32 value.
+struct Rec16 {
+  using T = uint4;
+  static constexpr int CAPR = 4096, CARRY = 2048;
+  __device__ static int cell(const uint4& r) { return static_cast<int>(r.x & 0xFFFFu); }
+  __device__ static float g0(const uint4& r, float gc) { return __uint_as_float(r.y) - gc; }
+  __device__ static float g1(const uint4& r, float gc) { return __uint_as_float(r.z) - gc; }
+  __device__ static float y(const uint4& r) { return __uint_as_float(r.w); }
+};
+struct Rec8 {
+  using T = uint2;
+  static constexpr int CAPR = 8192, CARRY = 4096;
+  __device__ static int cell(const uint2& r) { return static_cast<int>(r.y >> 16); }
+  __device__ static float g0(const uint2& r, float) {
+    return fmaf(static_cast<float>(r.x & 0xFFFFFFu), -5.9604644775390625e-8f, 0.5f);
+  }
+  __device__ static float g1(const uint2& r, float) {
+    return fmaf(static_cast<float>(__funnelshift_r(r.x, r.y, 24) & 0xFFFFFFu), -5.9604644775390625e-8f, 0.5f);
+  }
+  __device__ static float y(const uint2&) { return 1.0f; }
+};
+// Rec8 of a Rec16 {key, f0, f1, -} built by the partition (w: kernel width)
+__device__ __forceinline__ uint2 pack_rec8(const uint4& r, float half_w) {
+  const unsigned v0 = static_cast<unsigned>((half_w - __uint_as_float(r.y)) * 16777216.0f);
+  const unsigned v1 = static_cast<unsigned>((half_w - __uint_as_float(r.z)) * 16777216.0f);
+  return make_uint2(v0 | (v1 << 24), (v1 >> 8) | ((r.x & 0xFFFFu) << 16));
+}
+
 __device__ __forceinline__ bool point_key(float x0, float x1, const PartArgs& A, float inv_cpc, float* f0, float* f1,
                                           uint32_t* packed) {
   int la, lb;
@@ -505,7 +539,7 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter2(PartArgs A) {
 // One-pass scatter (no count pass): as k_bin_scatter2, but each tile reserves room
 // for its owner runs in fixed-capacity buckets with one global atomic per (tile,
 // owner).  A reservation that would pass the capacity writes nothing and sets ovf.
-template <int PER>
+template <int PER, bool REC8>
 __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter1(PartArgs A) {
   constexpr int TILE = S2_THREADS * PER;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -617,7 +651,13 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter1(PartArgs A) {
         const uint4 r = sorted[j];
         const int o = static_cast<int>(r.x >> 16);
         const int pos = tpos[o];
-        if (pos >= 0) A.rec[static_cast<int64_t>(o) * A.cap + pos + (j - toff[o])] = r;
+        const int64_t at = static_cast<int64_t>(o) * A.cap + pos + (j - toff[o]);
+        if (pos >= 0) {
+          if (REC8)
+            reinterpret_cast<uint2*>(A.rec)[at] = pack_rec8(r, 0.5f * static_cast<float>(A.W));
+          else
+            A.rec[at] = r;
+        }
       }
     }
     __syncthreads();
@@ -645,19 +685,24 @@ struct AccArgs {
 struct AccLayout {
   size_t stage, nxt, head, ccount, total;
 };
+template <typename R>
 __host__ __device__ inline AccLayout acc_layout(int cpc) {
+  constexpr int CAPR = R::CAPR, CARRY = R::CARRY;
   AccLayout L{};
-  L.stage = 0;                                                      // [2][CARRY + CAPR] uint4
-  L.nxt = L.stage + sizeof(uint4) * 2 * (CARRY + CAPR);             // [CARRY + CAPR] u16
+  L.stage = 0;                                                      // [2][CARRY + CAPR] records
+  L.nxt = L.stage + sizeof(typename R::T) * 2 * (CARRY + CAPR);     // [CARRY + CAPR] u16
   L.head = (L.nxt + sizeof(unsigned short) * (CARRY + CAPR) + 15) & ~static_cast<size_t>(15);  // [cpc] int
   L.ccount = L.head + sizeof(int) * cpc;                            // [cpc] int
   L.total = L.ccount + sizeof(int) * cpc;
   return L;
 }
 
-template <int W, bool PAIR>
+template <int W, bool PAIR, typename R>
 __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArgs A) {
+  static_assert(!PAIR || sizeof(typename R::T) == 16, "pair mode carries a strength");
+  using RT = typename R::T;
   constexpr int THREADS = Cfg<PAIR>::THREADS;
+  constexpr int CAPR = R::CAPR, CARRY = R::CARRY;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_base, s_count, s_ncarry, s_nleft, s_abort;
   __shared__ __align__(8) uint64_t s_bar[2];
@@ -672,8 +717,8 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
   const int my_ncells = max(0, min(cpc, A.ncells - my_first_cell));
   const bool owns = cell < my_ncells;
   const float gc = 0.5f * static_cast<float>(W - 1);  // window centre: g = f - gc
-  const AccLayout L = acc_layout(cpc);
-  uint4* stage = reinterpret_cast<uint4*>(smem + L.stage);
+  const AccLayout L = acc_layout<R>(cpc);
+  RT* stage = reinterpret_cast<RT*>(smem + L.stage);
   unsigned short* nxt = reinterpret_cast<unsigned short*>(smem + L.nxt);
   int* head = reinterpret_cast<int*>(smem + L.head);
   int* ccount = reinterpret_cast<int*>(smem + L.ccount);
@@ -751,16 +796,19 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
 
   auto issue = [&](int r) {
     const int nr = min(CAPR, count - r * CAPR);
-    uint4* dst = stage + (r & 1) * (CARRY + CAPR) + CARRY;
+    RT* dst = stage + (r & 1) * (CARRY + CAPR) + CARRY;
+    // whole 16-byte units (an 8-byte record list of odd length reads one record past its
+    // end, inside the record buffer, which the round never links)
+    const unsigned bytes = (static_cast<unsigned>(nr) * static_cast<unsigned>(sizeof(RT)) + 15u) & ~15u;
     fence_proxy_async();
-    mbar_arrive_expect(&s_bar[r & 1], static_cast<unsigned>(nr) * 16u);
-    bulk_g2s(dst, A.rec + base + static_cast<int64_t>(r) * CAPR, static_cast<unsigned>(nr) * 16u, &s_bar[r & 1]);
+    mbar_arrive_expect(&s_bar[r & 1], bytes);
+    bulk_g2s(dst, reinterpret_cast<const RT*>(A.rec) + base + static_cast<int64_t>(r) * CAPR, bytes, &s_bar[r & 1]);
   };
   if (tid == 0) issue(0);
 
   for (int r = 0; r < nrounds; ++r) {
     const int buf = r & 1;
-    uint4* st = stage + buf * (CARRY + CAPR);
+    RT* st = stage + buf * (CARRY + CAPR);
     const int nr = min(CAPR, count - r * CAPR);
     const int nc = s_ncarry;
     if (!mbar_wait(&s_bar[buf], (r >> 1) & 1, A.flags)) s_abort = 1;
@@ -778,7 +826,7 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int idx = base + u * THREADS;
-        cl[u] = (idx < hi) ? static_cast<int>(st[idx].x & 0xFFFFu) : 0xFFFF;  // 0xFFFF: run padding
+        cl[u] = (idx < hi) ? R::cell(st[idx]) : 0xFFFF;  // 0xFFFF: run padding
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u)
@@ -804,7 +852,7 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
     int ri = owns ? head[cell] : 0xFFFF;
     if (owns) {
       const int nproc = min(mine, q);
-      if (PAIR) {
+      if constexpr (PAIR) {
         // lane 0 of the pair: ones channel, window [a][b]; lane 1: strength channel,
         // window transposed ([b][a]) because it holds the second coordinate's weights.
         // Two records per iteration for independent work in flight.
@@ -845,13 +893,13 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
         auto one_channel = [&](auto ones_tag) {
           constexpr bool ONES = decltype(ones_tag)::value;
           for (int k = 0; k < nproc; ++k) {
-            const uint4 rec = st[ri];
+            const RT rec = st[ri];
             ri = nxt[ri];
             float px[W], py[W];
-            es_taps_poly<W>(__uint_as_float(rec.y) - gc, A.poly, px);
-            es_taps_poly<W>(__uint_as_float(rec.z) - gc, A.poly, py);
+            es_taps_poly<W>(R::g0(rec, gc), A.poly, px);
+            es_taps_poly<W>(R::g1(rec, gc), A.poly, py);
             if (!ONES) {
-              const float sv = __uint_as_float(rec.w);
+              const float sv = R::y(rec);
 #pragma unroll
               for (int i = 0; i < W; ++i) px[i] *= sv;
             }
@@ -880,7 +928,7 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
     if (tid == 0) s_ncarry = 0;
     __syncthreads();
     if (owns && ch == 0 && mine > q) {
-      uint4* nst = stage + (buf ^ 1) * (CARRY + CAPR);
+      RT* nst = stage + (buf ^ 1) * (CARRY + CAPR);
       int dst = CARRY - nleft + atomicAdd(&s_ncarry, mine - q);
       while (ri != 0xFFFF) {
         nst[dst++] = st[ri];
@@ -899,14 +947,14 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
 
 using KFn = void (*)(AccArgs);
 
-template <bool PAIR>
+template <bool PAIR, typename R>
 KFn pick2d(int w) {
   switch (w) {
-    case 4: return k_bin_accumulate<4, PAIR>;
-    case 5: return k_bin_accumulate<5, PAIR>;
-    case 6: return k_bin_accumulate<6, PAIR>;
-    case 7: return k_bin_accumulate<7, PAIR>;
-    case 8: return k_bin_accumulate<8, PAIR>;
+    case 4: return k_bin_accumulate<4, PAIR, R>;
+    case 5: return k_bin_accumulate<5, PAIR, R>;
+    case 6: return k_bin_accumulate<6, PAIR, R>;
+    case 7: return k_bin_accumulate<7, PAIR, R>;
+    case 8: return k_bin_accumulate<8, PAIR, R>;
     default: return nullptr;
   }
 }
@@ -948,11 +996,12 @@ fk_status spread_binned(const EsPlan& p, int64_t n, const float* x, const float*
 namespace {
 
 using Scatter1Fn = void (*)(PartArgs);
+template <bool REC8>
 Scatter1Fn pick_scatter1(int per, int* tile) {
   switch (per) {
-    case 5: *tile = S2_THREADS * 5; return k_bin_scatter1<5>;
-    case 6: *tile = S2_THREADS * 6; return k_bin_scatter1<6>;
-    default: *tile = S2_THREADS * 7; return k_bin_scatter1<7>;
+    case 5: *tile = S2_THREADS * 5; return k_bin_scatter1<5, REC8>;
+    case 6: *tile = S2_THREADS * 6; return k_bin_scatter1<6, REC8>;
+    default: *tile = S2_THREADS * 7; return k_bin_scatter1<7, REC8>;
   }
 }
 
@@ -1027,24 +1076,30 @@ fk_status spread_binned_run(const EsPlan& p, int64_t n, const float* x, const fl
   A.cap = P.cap;
   A.ovf = ovf;
   A.qmul = cfg.qmul;
-  const KFn fn = pair ? pick2d<true>(p.w) : pick2d<false>(p.w);
+  // exact-partition (and strength-carrying) records: Rec16; the one-pass partition of
+  // ones only writes Rec8
+  const KFn fn = pair ? pick2d<true, Rec16>(p.w) : pick2d<false, Rec16>(p.w);
   if (!fn) return set_error(FK_EINVAL, "binned spreading: w = %d not built", p.w);
   const int threads = pair ? Cfg<true>::THREADS : Cfg<false>::THREADS;
-  const size_t sm = acc_layout(cpc).total;
+  const size_t sm = acc_layout<Rec16>(cpc).total;
   FK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+  const bool rec8 = one_pass && !pair && with_ones && n_y == 0;
+  const KFn fn1 = rec8 ? pick2d<false, Rec8>(p.w) : fn;
+  const size_t sm_1 = rec8 ? acc_layout<Rec8>(cpc).total : sm;
+  if (rec8) FK_CUDA(cudaFuncSetAttribute(fn1, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm_1)));
   const size_t sm2 = s2_layout(G).total;
   KernelTimer* kt = kernel_timer();
 
   if (one_pass) {
     int tile1 = S2_TILE;
-    const Scatter1Fn s1fn = pick_scatter1(cfg.per, &tile1);
+    const Scatter1Fn s1fn = rec8 ? pick_scatter1<true>(cfg.per, &tile1) : pick_scatter1<false>(cfg.per, &tile1);
     const size_t sm1 = s2_layout(G, tile1).total;
     FK_CUDA(cudaFuncSetAttribute(s1fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm1)));
     s1fn<<<P.nblk, S2_THREADS, sm1, st>>>(P); note_launch();
     FK_CUDA(cudaGetLastError());
     A.mode = 1;
     if (kt->on) cudaEventRecordWithFlags(kt->start, st, kt->rec_flags);
-    fn<<<G, threads, sm, st>>>(A); note_launch();
+    fn1<<<G, threads, sm_1, st>>>(A); note_launch();
     if (kt->on) {
       cudaEventRecordWithFlags(kt->stop, st, kt->rec_flags);
       kt->recorded = true;

@@ -279,6 +279,24 @@ def test_binned_spreader_clustered_points(n):
     assert rel(host(b)[0], bo) <= 10 * eps
 
 
+@pytest.mark.parametrize("kind", ["uniform", "ragged", "clustered"])
+def test_binned_moments_ones_only(kind):
+    # moments alone (no strengths): the one-pass partition writes 8-byte records; crowded
+    # points fall back to the exact partition's 16-byte records
+    m, eps = 16, 1e-6
+    if kind == "clustered":
+        n = 300_000
+        g = np.random.default_rng(98)
+        x = np.clip(g.normal(-1.1, 0.02, size=(2, n)), -np.pi, np.pi - 1e-6).astype(np.float32)
+        x[:, : n // 10] = S.uniform_points(n // 10, 2, 34).astype(np.float32)
+    else:
+        n = 1_000_000 if kind == "uniform" else 1_000_003
+        x = S.uniform_points(n, 2, 35).astype(np.float32)
+    T, b = fk.fk_build_system(dev(x, torch.float32), None, m, eps, "mixed",
+                              opts=fk.default_opts(spread=fk.FK_SPREAD_BINNED))
+    assert rel(host(T), O.moments(x.astype(np.float64), m)) <= 10 * eps
+
+
 @pytest.mark.parametrize("d,m,solver", [(1, 30, "cg"), (2, 10, "chol"), (2, 12, "cg")])
 def test_sobolev_pairs_sweep(d, m, solver):
     # 6 (s, lambda) pairs from one spreading pass, each against its own oracle fit
