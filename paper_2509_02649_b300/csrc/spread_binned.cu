@@ -10,24 +10,25 @@
 // each lane evaluates the ES weights of one coordinate and the pair swaps them
 // with one shuffle, so every weight is computed once.
 //
-// Four launches.  Owner o holds cells [o cpc, (o+1) cpc), cpc <= 448 (224 in pair
-// mode, so that each lane keeps its w x w window in registers without spilling).
-//   k_bin_count   (full occupancy) counts, per block of the input, the points whose
-//                 window-start cell belongs to each owner;
-//   k_bin_scan    turns the counts into per-(block, owner) offsets and per-owner totals,
-//                 each run padded to whole 128-byte lines (sentinel records) so that
-//                 the scattered record writes never share a line between blocks;
-//   k_bin_scatter (one block per SM) recomputes each point's cell and fractional
-//                 offsets, sorts a tile by owner in shared memory and writes 16-byte
-//                 records {owner:local cell, f0, f1, strength} into per-owner buckets
-//                 as long contiguous runs (coalesced stores);
+// Owner o holds cells [o cpc, (o+1) cpc), cpc <= 448 (224 in pair mode, so that each
+// lane keeps its w x w window in registers without spilling).
+//   k_bin_scatter1 (one block per SM, one pass) recomputes each point's cell and
+//                 fractional offsets, sorts a tile by owner in shared memory, reserves
+//                 room in the owner buckets (fixed capacity: mean load + 2 % + 4096)
+//                 with one global atomic per (tile, owner) and writes the tile's runs
+//                 as contiguous records: 16 bytes {owner:local cell, f0, f1, strength},
+//                 or 8 bytes (cell and fixed-point offsets) when only ones are spread;
 //   k_bin_accumulate (one CTA per owner) streams its owner's bucket with double-
 //                 buffered TMA bulk copies, links each round's records into per-cell
 //                 lists in shared memory, and lets each lane run over at most a quota
-//                 of its cell's points (the mean load plus half a standard deviation);
-//                 the excess of fuller cells is carried into the next round, which
-//                 keeps the warps' trip counts even.  At the end each lane adds its
-//                 register window into the fp64 grid.
+//                 of its cell's points (the mean load plus a fraction of a standard
+//                 deviation); the excess of fuller cells is carried into the next
+//                 round, which keeps the warps' trip counts even.  A lane adds its
+//                 register window into the fp64 grid every 2048 points and at the end.
+// A bucket that would overflow (crowded points) sets a device flag; the exact
+// partition (k_bin_count, k_bin_scan, k_bin_scatter2 or k_bin_scatter, then
+// k_bin_accumulate on its 16-byte records) is always enqueued after and runs only when
+// that flag is set, so there is no host round trip.
 #include "fk_internal.cuh"
 #include "window.cuh"
 #include "es_poly.cuh"
