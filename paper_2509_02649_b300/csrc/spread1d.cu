@@ -6,9 +6,10 @@
 // in input order and every window tap is one shared-memory atomic.  On this part
 // 32-bit integer shared atomics are native while fp32 and 64-bit ones are compare-
 // and-swap loops, so each contribution psi_a * y is rounded to a fixed-point
-// integer q = round(psi_a * y * S) and added as a 64-bit integer held in two 32-bit
-// words: the low word takes an atomic add whose returned old value gives the carry,
-// and the high word is touched only on a carry or a borrow (rare).
+// integer q = round(psi_a * y * S) and added to a 64-bit sum split in two: the low
+// 32-bit word in shared memory takes an atomic add whose returned old value gives the
+// carry, and the high part, in the global int64 accumulator, gets +-2^32 only when the
+// low word wraps (rare: the low words start at 2^31).
 //
 // Scale: per channel S = 2^(21 - e) with max|y| <= 2^e (ones: e = 1), so every
 // |q| <= 2^21 and q is formed with one FFMA against the constant 1.5 * 2^23 (the
@@ -17,9 +18,9 @@
 // with the accumulated magnitude, unlike an fp32 running sum.  Integer sums do not
 // depend on the order of the additions, so the result is bitwise reproducible.
 //
-// Layout: channel groups of at most `cmax` channels share a CTA (cmax N 8 bytes of
+// Layout: channel groups of at most `cmax` channels share a CTA (cmax N 4 bytes of
 // shared memory); the CTAs of a group split the points into contiguous ranges; at
-// the end each CTA adds its integer grids into a global int64 accumulator, which a
+// the end each CTA adds its low words into the global int64 accumulator, which a
 // last kernel scales back into the fp64 grid.
 #include "fk_internal.cuh"
 #include "window.cuh"
@@ -30,7 +31,7 @@ namespace fk {
 namespace {
 
 constexpr int MAXGRP = 64;                      // channel groups per call
-constexpr int CG = 4;                           // channels per CTA at most
+constexpr int CG = 6;                           // channels per CTA at most
 constexpr int HALO = 16;                        // padding nodes after each grid (>= max W - 1)
 constexpr int THREADS = 1024;
 constexpr size_t SMEM_BUDGET = 220 * 1024;      // bytes of integer grids per CTA
@@ -82,12 +83,14 @@ __global__ void __launch_bounds__(THREADS) k_spread1d_fx(Fx1dArgs A) {
   const int nblk = A.grp_b0[g + 1] - A.grp_b0[g];
   const int lb = b - A.grp_b0[g];
   const int N = A.N;
-  // [nc][N + HALO] low and high words: a window starting at node b < N ends before
-  // N + HALO, and the halo is added into nodes 0 .. HALO - 1 at the end
+  // [nc][N + HALO] low words: a window starting at node b < N ends before N + HALO,
+  // and the halo is added into nodes 0 .. HALO - 1 at the end.  The high words live in
+  // the global int64 accumulator: a wrap of a low word adds +-2^32 there directly.
+  // The low words start at 2^31 (the sums at that bias), so a signed sum hovering
+  // around zero never wraps and the carry branch stays cold.
   const int stride = N + HALO;
   unsigned* lo = smem_fx;
-  int* hi = reinterpret_cast<int*>(smem_fx + nc * stride);
-  for (int i = threadIdx.x; i < 2 * nc * stride; i += blockDim.x) smem_fx[i] = 0u;
+  for (int i = threadIdx.x; i < nc * stride; i += blockDim.x) lo[i] = 0x80000000u;
 
   // per-channel scales
   float S[CG];
@@ -132,11 +135,11 @@ __global__ void __launch_bounds__(THREADS) k_spread1d_fx(Fx1dArgs A) {
 #pragma unroll
       for (int a = 0; a < W; ++a) any |= carry_delta(old[a], static_cast<unsigned>(qv[a]), qv[a] >> 31);
       if (any) {
-        int* hc = hi + c * stride + b;
+        unsigned long long* hc = A.acc + static_cast<int64_t>(c0 + c) * N;
 #pragma unroll
         for (int a = 0; a < W; ++a) {
           const int dh = carry_delta(old[a], static_cast<unsigned>(qv[a]), qv[a] >> 31);
-          if (dh) atomicAdd(hc + a, dh);
+          if (dh) atomicAdd(hc + ((b + a) & (N - 1)), static_cast<unsigned long long>(static_cast<long long>(dh) << 32));
         }
       }
     }
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(THREADS) k_spread1d_fx(Fx1dArgs A) {
   // add the CTA's integer grids (halo folded onto nodes 0 .. HALO - 1) into the
   // global accumulators
   for (int t = threadIdx.x; t < nc * stride; t += blockDim.x) {
-    const long long v = (static_cast<long long>(hi[t]) << 32) + static_cast<long long>(lo[t]);
+    const long long v = static_cast<long long>(lo[t]) - 0x80000000LL;
     if (v != 0) {
       const int c = t / stride, node = (t - c * stride) & (N - 1);
       atomicAdd(A.acc + static_cast<int64_t>(c0 + c) * N + node, static_cast<unsigned long long>(v));
@@ -275,7 +278,7 @@ fk_status absmax_channels(int64_t n, const float* y, int n_y, unsigned* amax, cu
 bool spread1d_fixed_supported(const EsPlan& p, int n_y, bool with_ones) {
   const int nc = n_y + (with_ones ? 1 : 0);
   if (p.d != 1 || nc < 1 || p.w < 2 || p.w > 16) return false;
-  const int64_t cmax = static_cast<int64_t>(SMEM_BUDGET / (8 * static_cast<size_t>(p.N + HALO)));
+  const int64_t cmax = static_cast<int64_t>(SMEM_BUDGET / (4 * static_cast<size_t>(p.N + HALO)));
   if (cmax < 1) return false;
   const int64_t c = std::min<int64_t>(cmax, CG);
   return (nc + c - 1) / c <= MAXGRP;
@@ -285,7 +288,7 @@ namespace {
 
 // channels per CTA at most for this grid size (shared-memory budget and CG)
 int channel_cap(int N) {
-  return static_cast<int>(std::min<size_t>(CG, SMEM_BUDGET / (8 * static_cast<size_t>(N + HALO))));
+  return static_cast<int>(std::min<size_t>(CG, SMEM_BUDGET / (4 * static_cast<size_t>(N + HALO))));
 }
 
 fk_status spread1d_run(const EsPlan& p, int64_t n, const float* x, const float* y, int n_y, bool with_ones,
@@ -323,7 +326,7 @@ fk_status spread1d_run(const EsPlan& p, int64_t n, const float* x, const float* 
     A.grp_c0[g] = c;
     A.grp_nc[g] = sz;
     c += sz;
-    smem_max = std::max(smem_max, sizeof(unsigned) * 2 * static_cast<size_t>(sz) * (N + HALO));
+    smem_max = std::max(smem_max, sizeof(unsigned) * static_cast<size_t>(sz) * (N + HALO));
   }
   // CTAs: as many as fit on the device at once, shared out by channel count, and no
   // more than one per 4096 points (each CTA zeroes and flushes whole grids)
@@ -391,8 +394,7 @@ fk_status spread1d_fixed(const EsPlan& p, int64_t n, const float* x, const float
   // reside per SM; time each on this call's data (the grid is rewritten each time)
   const int cap = channel_cap(p.N);
   std::vector<int> opts = {cap};
-  if (cap > 2) opts.push_back(cap - 1);
-  if (cap > 1) opts.push_back((cap + 1) / 2 == cap - 1 ? 1 : (cap + 1) / 2);
+  for (int c = cap - 1; c >= 1 && opts.size() < 5; --c) opts.push_back(c);
   cudaEvent_t e0, e1;
   FK_CUDA(cudaEventCreate(&e0));
   FK_CUDA(cudaEventCreate(&e1));
