@@ -169,6 +169,7 @@ fk_status spread_atomic(const EsPlan& p, int64_t n, const R* x, const R* y, int 
 // Tunables of the kernels whose best shape depends on the problem; a process-wide
 // table keyed by the problem's class holds the measured winners (autotune.cu).
 struct BinCfg {       // 2-D binned spreading
+  int half = 1;       // 1: partition blocks of 512 threads, two per SM (half tiles)
   int per = 7;        // points per thread and tile of the partition scatter (5..7)
   int cells = 0;      // cells per owner CTA (0: the kernel's maximum)
   float qmul = 0.5f;  // per-round quota = mean + qmul sqrt(mean)

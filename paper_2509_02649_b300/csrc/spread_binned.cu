@@ -540,9 +540,10 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter2(PartArgs A) {
 // One-pass scatter (no count pass): as k_bin_scatter2, but each tile reserves room
 // for its owner runs in fixed-capacity buckets with one global atomic per (tile,
 // owner).  A reservation that would pass the capacity writes nothing and sets ovf.
-template <int PER, bool REC8>
-__global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter1(PartArgs A) {
-  constexpr int TILE = S2_THREADS * PER;
+// T threads per block: 1024 (one block per SM) or 512 (two per SM, half the tile)
+template <int PER, bool REC8, int T>
+__global__ void __launch_bounds__(T, 1024 / T) k_bin_scatter1(PartArgs A) {
+  constexpr int TILE = T * PER;
   extern __shared__ __align__(16) unsigned char smem[];
   const int G = A.G;
   const S2Layout L = s2_layout(G, TILE);
@@ -575,14 +576,14 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter1(PartArgs A) {
   unsigned phase = 0;
   for (int64_t t0 = s0; t0 < e0; t0 += TILE) {
     const int cnt = static_cast<int>(min(static_cast<int64_t>(TILE), e0 - t0));
-    for (int o = tid; o <= G; o += S2_THREADS) tcnt[o] = 0;
+    for (int o = tid; o <= G; o += T) tcnt[o] = 0;
     if (!mbar_wait(bar, phase, A.flags)) return;
     phase ^= 1u;
     __syncthreads();
     uint4 rec[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-      const int i = k * S2_THREADS + tid;
+      const int i = k * T + tid;
       rec[k].x = 0xFFFFFFFFu;
       if (i < cnt) {
         float f0, f1;
@@ -606,10 +607,10 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter1(PartArgs A) {
       my_c = tcnt[tid];
       if (my_c > 0) my_pos = atomicAdd(A.fill + tid, my_c);
     }
-    if (tid >= S2_THREADS - 32) {  // exclusive scan of the tile counts (last warp)
+    if (tid >= T - 32) {  // exclusive scan of the tile counts (last warp)
       // each lane sums a run of consecutive owners, one warp scan of the run sums,
       // then each lane writes its run's prefixes: no serial loop over warp-wide chunks
-      const int ln = tid - (S2_THREADS - 32);
+      const int ln = tid - (T - 32);
       const int per = (G + 1 + 31) / 32;
       const int o0 = ln * per, o1 = min(o0 + per, G + 1);
       int run = 0;
@@ -647,7 +648,7 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter1(PartArgs A) {
     // a fixed trip count, so that every thread's PER loads are in flight at once
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-      const int j = k * S2_THREADS + tid;
+      const int j = k * T + tid;
       if (j < valid) {
         const uint4 r = sorted[j];
         const int o = static_cast<int>(r.x >> 16);
@@ -997,13 +998,18 @@ fk_status spread_binned(const EsPlan& p, int64_t n, const float* x, const float*
 namespace {
 
 using Scatter1Fn = void (*)(PartArgs);
-template <bool REC8>
-Scatter1Fn pick_scatter1(int per, int* tile) {
+template <bool REC8, int T>
+Scatter1Fn pick_scatter1_t(int per, int* tile) {
   switch (per) {
-    case 5: *tile = S2_THREADS * 5; return k_bin_scatter1<5, REC8>;
-    case 6: *tile = S2_THREADS * 6; return k_bin_scatter1<6, REC8>;
-    default: *tile = S2_THREADS * 7; return k_bin_scatter1<7, REC8>;
+    case 5: *tile = T * 5; return k_bin_scatter1<5, REC8, T>;
+    case 6: *tile = T * 6; return k_bin_scatter1<6, REC8, T>;
+    default: *tile = T * 7; return k_bin_scatter1<7, REC8, T>;
   }
+}
+template <bool REC8>
+Scatter1Fn pick_scatter1(int per, bool half, int* tile, int* threads) {
+  *threads = half ? S2_THREADS / 2 : S2_THREADS;
+  return half ? pick_scatter1_t<REC8, S2_THREADS / 2>(per, tile) : pick_scatter1_t<REC8, S2_THREADS>(per, tile);
 }
 
 // one run of the 2-D binned spreader with explicit tunables
@@ -1033,7 +1039,8 @@ fk_status spread_binned_run(const EsPlan& p, int64_t n, const float* x, const fl
   P.y = y;
   P.has_y = n_y > 0 ? 1 : 0;
   // one partition block per SM; count and scatter use the same block ranges
-  P.nblk = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + P_TILE - 1) / P_TILE, sm_count())));
+  P.nblk = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + P_TILE - 1) / P_TILE,
+                                                                    static_cast<int64_t>(sm_count()) * (cfg.half ? 2 : 1))));
   P.range = ((n + P.nblk - 1) / P.nblk + 3) & ~static_cast<int64_t>(3);
   P.vec_ok = ((reinterpret_cast<uintptr_t>(x) & 15) == 0 && (reinterpret_cast<uintptr_t>(x1) & 15) == 0 &&
               (n & 3) == 0 &&
@@ -1092,11 +1099,12 @@ fk_status spread_binned_run(const EsPlan& p, int64_t n, const float* x, const fl
   KernelTimer* kt = kernel_timer();
 
   if (one_pass) {
-    int tile1 = S2_TILE;
-    const Scatter1Fn s1fn = rec8 ? pick_scatter1<true>(cfg.per, &tile1) : pick_scatter1<false>(cfg.per, &tile1);
+    int tile1 = S2_TILE, threads1 = S2_THREADS;
+    const Scatter1Fn s1fn = rec8 ? pick_scatter1<true>(cfg.per, cfg.half != 0, &tile1, &threads1)
+                                 : pick_scatter1<false>(cfg.per, cfg.half != 0, &tile1, &threads1);
     const size_t sm1 = s2_layout(G, tile1).total;
     FK_CUDA(cudaFuncSetAttribute(s1fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm1)));
-    s1fn<<<P.nblk, S2_THREADS, sm1, st>>>(P); note_launch();
+    s1fn<<<P.nblk, threads1, sm1, st>>>(P); note_launch();
     FK_CUDA(cudaGetLastError());
     A.mode = 1;
     if (kt->on) cudaEventRecordWithFlags(kt->start, st, kt->rec_flags);
@@ -1164,6 +1172,7 @@ fk_status spread_binned_xy(const EsPlan& p, int64_t n, const float* x, const flo
   if (cmax * 7 / 8 != waves_cells) cells_opts.push_back(cmax * 7 / 8);
   const std::vector<int> per_opts = {7, 6, 5};
   const std::vector<float> q_opts = {0.5f, 0.25f, 1.0f};
+  const std::vector<int> half_opts = {0, 1};
   cudaEvent_t e0, e1;
   FK_CUDA(cudaEventCreate(&e0));
   FK_CUDA(cudaEventCreate(&e1));
@@ -1186,17 +1195,19 @@ fk_status spread_binned_xy(const EsPlan& p, int64_t n, const float* x, const flo
   char line[160];
   snprintf(line, sizeof(line), "default %.3f ms", best_ms);
   log += line;
-  for (int knob = 0; knob < 3 && rc == FK_OK; ++knob) {
-    const size_t cnt = knob == 0 ? per_opts.size() : (knob == 1 ? cells_opts.size() : q_opts.size());
+  for (int knob = 0; knob < 4 && rc == FK_OK; ++knob) {
+    const size_t cnt = knob == 0 ? half_opts.size()
+                                 : (knob == 1 ? per_opts.size() : (knob == 2 ? cells_opts.size() : q_opts.size()));
     for (size_t i = 0; i < cnt && rc == FK_OK; ++i) {
       BinCfg c = best;
-      if (knob == 0) c.per = per_opts[i];
-      if (knob == 1) c.cells = cells_opts[i];
-      if (knob == 2) c.qmul = q_opts[i];
-      if (c.per == best.per && c.cells == best.cells && c.qmul == best.qmul) continue;
+      if (knob == 0) c.half = half_opts[i];
+      if (knob == 1) c.per = per_opts[i];
+      if (knob == 2) c.cells = cells_opts[i];
+      if (knob == 3) c.qmul = q_opts[i];
+      if (c.half == best.half && c.per == best.per && c.cells == best.cells && c.qmul == best.qmul) continue;
       float ms = 0.f;
       rc = trial(c, &ms);
-      snprintf(line, sizeof(line), "; per=%d cells=%d q=%.2f %.3f ms", c.per, c.cells, c.qmul, ms);
+      snprintf(line, sizeof(line), "; half=%d per=%d cells=%d q=%.2f %.3f ms", c.half, c.per, c.cells, c.qmul, ms);
       log += line;
       if (rc == FK_OK && ms < best_ms) {
         best = c;
@@ -1207,7 +1218,8 @@ fk_status spread_binned_xy(const EsPlan& p, int64_t n, const float* x, const flo
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   FK_TRY(rc);
-  snprintf(line, sizeof(line), "  ->  per=%d cells=%d q=%.2f (%.3f ms)", best.per, best.cells, best.qmul, best_ms);
+  snprintf(line, sizeof(line), "  ->  half=%d per=%d cells=%d q=%.2f (%.3f ms)", best.half, best.per, best.cells,
+           best.qmul, best_ms);
   log += line;
   tune_store(key, best, log);
   return spread_binned_run(p, n, x, x1, s1, y, n_y, with_ones, grid, flags, st, scr, best);
