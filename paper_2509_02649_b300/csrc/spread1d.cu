@@ -299,8 +299,11 @@ fk_status spread1d_run(const EsPlan& p, int64_t n, const float* x, const float* 
   if (!accumulate) FK_CUDA(cudaMemsetAsync(grid, 0, sizeof(double) * N * nc, st));
   if (n == 0) return FK_OK;
 
+  // default: half the shared-memory cap, so that two 1024-thread CTAs share an SM (the
+  // fastest measured shape at N = 8192, 17 channels)
   int cmax = channel_cap(N);
   if (cmax_req > 0 && cmax_req < cmax) cmax = cmax_req;
+  else if (cmax_req <= 0) cmax = (cmax + 1) / 2;
   if ((nc + cmax - 1) / cmax > MAXGRP) cmax = (nc + MAXGRP - 1) / MAXGRP;
   const int ngrp = (nc + cmax - 1) / cmax;
   Fx1dArgs A{};
