@@ -154,6 +154,7 @@ struct PartArgs {
   int* off;         // [nblk][G] offset of the block's run inside its owner's bucket
   int* tot;         // [G]
   uint4* rec;       // records, bucketed by owner
+  float* ybuf;      // strengths of 8-byte records with a strength, same indices
   unsigned* flags;
   float c_hi, c_lo;
   // one-pass partition: owner o's bucket is rec[o cap, (o + 1) cap), filled through
@@ -180,6 +181,7 @@ __device__ __forceinline__ bool skip_guarded(const PartArgs& A) {
 //   decodes to the same fp32 value.
 struct Rec16 {
   using T = uint4;
+  static constexpr bool HAS_Y = true, SPLIT_Y = false;
   static constexpr int CAPR = 4096, CARRY = 2048;
   __device__ static int cell(const uint4& r) { return static_cast<int>(r.x & 0xFFFFu); }
   __device__ static float g0(const uint4& r, float gc) { return __uint_as_float(r.y) - gc; }
@@ -188,6 +190,7 @@ struct Rec16 {
 };
 struct Rec8 {
   using T = uint2;
+  static constexpr bool HAS_Y = false, SPLIT_Y = false;
   static constexpr int CAPR = 8192, CARRY = 4096;
   __device__ static int cell(const uint2& r) { return static_cast<int>(r.y >> 16); }
   __device__ static float g0(const uint2& r, float) {
@@ -197,6 +200,12 @@ struct Rec8 {
     return fmaf(static_cast<float>(__funnelshift_r(r.x, r.y, 24) & 0xFFFFFFu), -5.9604644775390625e-8f, 0.5f);
   }
   __device__ static float y(const uint2&) { return 1.0f; }
+};
+// Rec8 records with the strengths in a parallel stream of floats (same indices):
+// 12 bytes per point, 5632 records per round
+struct Rec8Y : Rec8 {
+  static constexpr bool HAS_Y = true, SPLIT_Y = true;
+  static constexpr int CAPR = 5632, CARRY = 2560;
 };
 // Rec8 of a Rec16 {key, f0, f1, -} built by the partition (w: kernel width)
 __device__ __forceinline__ uint2 pack_rec8(const uint4& r, float half_w) {
@@ -655,10 +664,12 @@ __global__ void __launch_bounds__(T, 1024 / T) k_bin_scatter1(PartArgs A) {
         const int pos = tpos[o];
         const int64_t at = static_cast<int64_t>(o) * A.cap + pos + (j - toff[o]);
         if (pos >= 0) {
-          if (REC8)
+          if (REC8) {
             reinterpret_cast<uint2*>(A.rec)[at] = pack_rec8(r, 0.5f * static_cast<float>(A.W));
-          else
+            if (A.has_y) A.ybuf[at] = __uint_as_float(r.w);
+          } else {
             A.rec[at] = r;
+          }
         }
       }
     }
@@ -673,6 +684,7 @@ struct AccArgs {
   int with_ones;
   const int* tot;   // [G]
   const uint4* rec;
+  const float* ybuf;  // strengths beside 8-byte records (Rec8Y)
   double* grid;
   unsigned* flags;
   // mode 0: buckets from the exact partition (tot); 1: one-pass buckets (fill, cap),
@@ -685,14 +697,16 @@ struct AccArgs {
 };
 
 struct AccLayout {
-  size_t stage, nxt, head, ccount, total;
+  size_t stage, ystage, nxt, head, ccount, total;
 };
 template <typename R>
 __host__ __device__ inline AccLayout acc_layout(int cpc) {
   constexpr int CAPR = R::CAPR, CARRY = R::CARRY;
   AccLayout L{};
   L.stage = 0;                                                      // [2][CARRY + CAPR] records
-  L.nxt = L.stage + sizeof(typename R::T) * 2 * (CARRY + CAPR);     // [CARRY + CAPR] u16
+  L.ystage = L.stage + sizeof(typename R::T) * 2 * (CARRY + CAPR);  // [2][CARRY + CAPR] floats
+  const size_t yb = R::SPLIT_Y ? sizeof(float) * 2 * (CARRY + CAPR) : 0;
+  L.nxt = L.ystage + yb;                                            // [CARRY + CAPR] u16
   L.head = (L.nxt + sizeof(unsigned short) * (CARRY + CAPR) + 15) & ~static_cast<size_t>(15);  // [cpc] int
   L.ccount = L.head + sizeof(int) * cpc;                            // [cpc] int
   L.total = L.ccount + sizeof(int) * cpc;
@@ -701,7 +715,7 @@ __host__ __device__ inline AccLayout acc_layout(int cpc) {
 
 template <int W, bool PAIR, typename R>
 __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArgs A) {
-  static_assert(!PAIR || sizeof(typename R::T) == 16, "pair mode carries a strength");
+  static_assert(!PAIR || R::HAS_Y, "pair mode carries a strength");
   using RT = typename R::T;
   constexpr int THREADS = Cfg<PAIR>::THREADS;
   constexpr int CAPR = R::CAPR, CARRY = R::CARRY;
@@ -721,6 +735,7 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
   const float gc = 0.5f * static_cast<float>(W - 1);  // window centre: g = f - gc
   const AccLayout L = acc_layout<R>(cpc);
   RT* stage = reinterpret_cast<RT*>(smem + L.stage);
+  float* ystage = reinterpret_cast<float*>(smem + L.ystage);  // SPLIT_Y only
   unsigned short* nxt = reinterpret_cast<unsigned short*>(smem + L.nxt);
   int* head = reinterpret_cast<int*>(smem + L.head);
   int* ccount = reinterpret_cast<int*>(smem + L.ccount);
@@ -802,15 +817,20 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
     // whole 16-byte units (an 8-byte record list of odd length reads one record past its
     // end, inside the record buffer, which the round never links)
     const unsigned bytes = (static_cast<unsigned>(nr) * static_cast<unsigned>(sizeof(RT)) + 15u) & ~15u;
+    const unsigned ybytes = R::SPLIT_Y ? ((static_cast<unsigned>(nr) * 4u + 15u) & ~15u) : 0u;
     fence_proxy_async();
-    mbar_arrive_expect(&s_bar[r & 1], bytes);
+    mbar_arrive_expect(&s_bar[r & 1], bytes + ybytes);
     bulk_g2s(dst, reinterpret_cast<const RT*>(A.rec) + base + static_cast<int64_t>(r) * CAPR, bytes, &s_bar[r & 1]);
+    if (R::SPLIT_Y)
+      bulk_g2s(ystage + (r & 1) * (CARRY + CAPR) + CARRY, A.ybuf + base + static_cast<int64_t>(r) * CAPR, ybytes,
+               &s_bar[r & 1]);
   };
   if (tid == 0) issue(0);
 
   for (int r = 0; r < nrounds; ++r) {
     const int buf = r & 1;
     RT* st = stage + buf * (CARRY + CAPR);
+    const float* yst = ystage + buf * (CARRY + CAPR);
     const int nr = min(CAPR, count - r * CAPR);
     const int nc = s_ncarry;
     if (!mbar_wait(&s_bar[buf], (r >> 1) & 1, A.flags)) s_abort = 1;
@@ -859,16 +879,22 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
         // window transposed ([b][a]) because it holds the second coordinate's weights.
         // Two records per iteration for independent work in flight.
         int k = 0;
+        // strength of the record at index i (the ones lane uses 1)
+        auto strength = [&](const RT& r, int i) {
+          if constexpr (R::SPLIT_Y) return yst[i];
+          else return R::y(r);
+        };
         for (; k + 1 < nproc; k += 2) {
-          const uint4 ra = st[ri];
-          const int rj = nxt[ri];
-          const uint4 rb = st[rj];
+          const int ia = ri;
+          const RT ra = st[ia];
+          const int rj = nxt[ia];
+          const RT rb = st[rj];
           ri = nxt[rj];
           float ea[W], eb[W];
-          es_taps_poly<W>(__uint_as_float(ch == 0 ? ra.y : ra.z) - gc, A.poly, ea);
-          es_taps_poly<W>(__uint_as_float(ch == 0 ? rb.y : rb.z) - gc, A.poly, eb);
-          const float wa = (ch == 0) ? 1.0f : __uint_as_float(ra.w);
-          const float wb = (ch == 0) ? 1.0f : __uint_as_float(rb.w);
+          es_taps_poly<W>(ch == 0 ? R::g0(ra, gc) : R::g1(ra, gc), A.poly, ea);
+          es_taps_poly<W>(ch == 0 ? R::g0(rb, gc) : R::g1(rb, gc), A.poly, eb);
+          const float wa = (ch == 0) ? 1.0f : strength(ra, ia);
+          const float wb = (ch == 0) ? 1.0f : strength(rb, rj);
 #pragma unroll
           for (int j = 0; j < W; ++j) {
             const float ta = wa * __shfl_xor_sync(pmask, ea[j], 1);
@@ -878,11 +904,12 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
           }
         }
         if (k < nproc) {
-          const uint4 ra = st[ri];
-          ri = nxt[ri];
+          const int ia = ri;
+          const RT ra = st[ia];
+          ri = nxt[ia];
           float ea[W];
-          es_taps_poly<W>(__uint_as_float(ch == 0 ? ra.y : ra.z) - gc, A.poly, ea);
-          const float wa = (ch == 0) ? 1.0f : __uint_as_float(ra.w);
+          es_taps_poly<W>(ch == 0 ? R::g0(ra, gc) : R::g1(ra, gc), A.poly, ea);
+          const float wa = (ch == 0) ? 1.0f : strength(ra, ia);
 #pragma unroll
           for (int j = 0; j < W; ++j) {
             const float ta = wa * __shfl_xor_sync(pmask, ea[j], 1);
@@ -895,13 +922,16 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
         auto one_channel = [&](auto ones_tag) {
           constexpr bool ONES = decltype(ones_tag)::value;
           for (int k = 0; k < nproc; ++k) {
-            const RT rec = st[ri];
-            ri = nxt[ri];
+            const int ir = ri;
+            const RT rec = st[ir];
+            ri = nxt[ir];
             float px[W], py[W];
             es_taps_poly<W>(R::g0(rec, gc), A.poly, px);
             es_taps_poly<W>(R::g1(rec, gc), A.poly, py);
             if (!ONES) {
-              const float sv = R::y(rec);
+              float sv;
+              if constexpr (R::SPLIT_Y) sv = yst[ir];
+              else sv = R::y(rec);
 #pragma unroll
               for (int i = 0; i < W; ++i) px[i] *= sv;
             }
@@ -931,9 +961,12 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
     __syncthreads();
     if (owns && ch == 0 && mine > q) {
       RT* nst = stage + (buf ^ 1) * (CARRY + CAPR);
+      float* nyst = ystage + (buf ^ 1) * (CARRY + CAPR);
       int dst = CARRY - nleft + atomicAdd(&s_ncarry, mine - q);
       while (ri != 0xFFFF) {
-        nst[dst++] = st[ri];
+        nst[dst] = st[ri];
+        if (R::SPLIT_Y) nyst[dst] = yst[ri];
+        ++dst;
         ri = nxt[ri];
       }
     }
@@ -1091,10 +1124,22 @@ fk_status spread_binned_run(const EsPlan& p, int64_t n, const float* x, const fl
   const int threads = pair ? Cfg<true>::THREADS : Cfg<false>::THREADS;
   const size_t sm = acc_layout<Rec16>(cpc).total;
   FK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
-  const bool rec8 = one_pass && !pair && with_ones && n_y == 0;
-  const KFn fn1 = rec8 ? pick2d<false, Rec8>(p.w) : fn;
-  const size_t sm_1 = rec8 ? acc_layout<Rec8>(cpc).total : sm;
-  if (rec8) FK_CUDA(cudaFuncSetAttribute(fn1, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm_1)));
+  // the one-pass partition writes 8-byte records, with the strengths in a parallel
+  // stream when there are any
+  const bool rec8 = one_pass;
+  const bool spl = n_y > 0;
+  KFn fn1 = fn;
+  size_t sm_1 = sm;
+  if (rec8) {
+    fn1 = spl ? (pair ? pick2d<true, Rec8Y>(p.w) : pick2d<false, Rec8Y>(p.w)) : pick2d<false, Rec8>(p.w);
+    sm_1 = spl ? acc_layout<Rec8Y>(cpc).total : acc_layout<Rec8>(cpc).total;
+    FK_CUDA(cudaFuncSetAttribute(fn1, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm_1)));
+    if (spl) {
+      // + 4: a round's bulk copy rounds its byte count up to 16 (reads <= 3 floats past)
+      FK_TRY(scr.alloc(&P.ybuf, static_cast<size_t>(P.cap) * G + 4));
+      A.ybuf = P.ybuf;
+    }
+  }
   const size_t sm2 = s2_layout(G).total;
   KernelTimer* kt = kernel_timer();
 
