@@ -191,7 +191,7 @@ struct Rec16 {
 struct Rec8 {
   using T = uint2;
   static constexpr bool HAS_Y = false, SPLIT_Y = false;
-  static constexpr int CAPR = 8192, CARRY = 4096;
+  static constexpr int CAPR = 10240, CARRY = 2048;
   __device__ static int cell(const uint2& r) { return static_cast<int>(r.y >> 16); }
   __device__ static float g0(const uint2& r, float) {
     return fmaf(static_cast<float>(r.x & 0xFFFFFFu), -5.9604644775390625e-8f, 0.5f);
@@ -202,10 +202,10 @@ struct Rec8 {
   __device__ static float y(const uint2&) { return 1.0f; }
 };
 // Rec8 records with the strengths in a parallel stream of floats (same indices):
-// 12 bytes per point, 5632 records per round
+// 12 bytes per point, 6656 records per round
 struct Rec8Y : Rec8 {
   static constexpr bool HAS_Y = true, SPLIT_Y = true;
-  static constexpr int CAPR = 5632, CARRY = 2560;
+  static constexpr int CAPR = 6656, CARRY = 1536;
 };
 // Rec8 of a Rec16 {key, f0, f1, -} built by the partition (w: kernel width)
 __device__ __forceinline__ uint2 pack_rec8(const uint4& r, float half_w) {
