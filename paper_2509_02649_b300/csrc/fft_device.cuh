@@ -17,10 +17,27 @@ __device__ __forceinline__ cplx<R> tw_get(const double* tw, int idx, int sign) {
   return r;
 }
 
-// In-place radix-2 DIT over s[0..N) (already in bit-reversed order).
+// In-place radix-2 DIT over s[0..N) (already in bit-reversed order).  The first two
+// stages have the twiddles 1 and e^{sign i pi/2} = sign i: no multiplications.
 template <typename R>
 __device__ void fft_smem(cplx<R>* s, int N, int sign, const double* tw) {
-  for (int len = 2; len <= N; len <<= 1) {
+  if (N >= 4) {
+    // stages len = 2 and 4 together: each thread a group of four
+    for (int g = threadIdx.x; g < (N >> 2); g += blockDim.x) {
+      cplx<R>* q = s + 4 * g;
+      const cplx<R> a0 = q[0], a1 = q[1], a2 = q[2], a3 = q[3];
+      const cplx<R> b0{a0.x + a1.x, a0.y + a1.y}, b1{a0.x - a1.x, a0.y - a1.y};
+      const cplx<R> b2{a2.x + a3.x, a2.y + a3.y}, b3{a2.x - a3.x, a2.y - a3.y};
+      // b3 times sign i
+      const cplx<R> t3{sign < 0 ? b3.y : -b3.y, sign < 0 ? -b3.x : b3.x};
+      q[0] = cplx<R>{b0.x + b2.x, b0.y + b2.y};
+      q[2] = cplx<R>{b0.x - b2.x, b0.y - b2.y};
+      q[1] = cplx<R>{b1.x + t3.x, b1.y + t3.y};
+      q[3] = cplx<R>{b1.x - t3.x, b1.y - t3.y};
+    }
+    __syncthreads();
+  }
+  for (int len = (N >= 4 ? 8 : 2); len <= N; len <<= 1) {
     const int half = len >> 1;
     const int tstep = N / len;
     for (int b = threadIdx.x; b < (N >> 1); b += blockDim.x) {
