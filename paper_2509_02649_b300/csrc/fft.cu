@@ -8,6 +8,10 @@
 // run in place in shared memory.  Twiddles e^{-2 pi i t / N} come from an fp64
 // table built once per plan with sincospi.
 #include "fk_internal.cuh"
+
+#include <map>
+#include <mutex>
+#include <utility>
 #include "fft_device.cuh"
 
 namespace fk {
@@ -24,6 +28,40 @@ __global__ void k_twiddles(int N, double* tw) {
 fk_status fft_twiddles(int N, double* tw, cudaStream_t st) {
   k_twiddles<<<(N + 255) / 256, 256, 0, st>>>(N, tw); note_launch();
   FK_CUDA(cudaGetLastError());
+  return FK_OK;
+}
+
+// Twiddle tables depend only on N: computed once per device and N, kept for the
+// life of the process (during a stream capture the first computation runs on a
+// stream of its own, outside the graph).
+fk_status twiddle_table(int N, cudaStream_t st, const double** out) {
+  int dev = 0;
+  FK_CUDA(cudaGetDevice(&dev));
+  static std::mutex mtx;
+  static std::map<std::pair<int, int>, double*> cache;
+  std::lock_guard<std::mutex> lock(mtx);
+  const auto key = std::make_pair(dev, N);
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    *out = it->second;
+    return FK_OK;
+  }
+  double* tw = nullptr;
+  FK_CUDA(cudaMalloc(&tw, sizeof(double) * 2 * static_cast<size_t>(N)));
+  cudaStream_t cs = st;
+  if (capture_ctx() && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaFree(tw);
+    return set_error(FK_ECUDA, "twiddle stream");
+  }
+  fk_status rc = fft_twiddles(N, tw, cs);
+  if (rc == FK_OK && cudaStreamSynchronize(cs) != cudaSuccess) rc = set_error(FK_ECUDA, "twiddle table");
+  if (cs != st) cudaStreamDestroy(cs);
+  if (rc != FK_OK) {
+    cudaFree(tw);
+    return rc;
+  }
+  cache.emplace(key, tw);
+  *out = tw;
   return FK_OK;
 }
 
@@ -212,9 +250,8 @@ fk_status grid_to_modes(const EsPlan& p, const double* grid, int c0, int nc, int
   const size_t sm = static_cast<size_t>(N) * sizeof(cplx<R>);
   if (sm > 200 * 1024) return set_error(FK_EINVAL, "fine grid %d too long for one CTA", N);
   const int corr_off = p.kmax - kout;
-  double* tw = nullptr;
-  FK_TRY(scratch.alloc(&tw, 2 * static_cast<size_t>(N)));
-  FK_TRY(fft_twiddles(N, tw, st));
+  const double* tw = nullptr;
+  FK_TRY(twiddle_table(N, st, &tw));
   const int K = 2 * kout + 1;
   if (p.d == 1) {
     FK_TRY(set_smem<R>((const void*)k_t1_1d<R>, sm));

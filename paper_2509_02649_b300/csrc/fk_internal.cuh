@@ -262,5 +262,7 @@ template <typename R>
 fk_status fft_lines(cplx<R>* data, int N, int64_t n_lines, int64_t line_stride, int64_t elem_stride,
                     int sign, const double* tw, cudaStream_t st);
 fk_status fft_twiddles(int N, double* tw, cudaStream_t st);  // tw[2t..2t+1] = e^{-2 pi i t / N}
+// the same table, computed once per device and N and cached (*out stays valid)
+fk_status twiddle_table(int N, cudaStream_t st, const double** out);
 
 }  // namespace fk

@@ -623,10 +623,13 @@ __global__ void k_circ_embed(int d, int m, int Lc, const double* T, cplx<double>
        t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     int64_t q = t, node = 0, mul = 1;
     int jj[3];
+    bool aliased = false;  // Lc = 4m: the lag -2m shares its node with +2m, which keeps it
     for (int l = d - 1; l >= 0; --l) {
       jj[l] = static_cast<int>(q % K2) - 2 * m;
+      aliased |= Lc < K2 && jj[l] == -2 * m;
       q /= K2;
     }
+    if (aliased) continue;
     for (int l = d - 1; l >= 0; --l) {
       node += mul * ((jj[l] + Lc) % Lc);
       mul *= Lc;
@@ -808,7 +811,7 @@ struct Circ {
   int64_t LL, D;
   cplx<double>* ch;   // FFT of the circulant
   cplx<double>* buf;  // nsys * LL
-  double* tw;
+  const double* tw;
 };
 
 static fk_status fft_nd(const Circ& c, int nsys, int sign, cudaStream_t st) {
@@ -886,8 +889,7 @@ static fk_status cg_solve(int d, int m, const double* T, const double* W, int n_
   const int64_t D = c.D;
   FK_TRY(scr.alloc(&c.ch, c.LL));
   FK_TRY(scr.alloc(&c.buf, c.LL * nsys));
-  FK_TRY(scr.alloc(&c.tw, 2 * static_cast<size_t>(c.Lc)));
-  FK_TRY(fft_twiddles(c.Lc, c.tw, st));
+  FK_TRY(twiddle_table(c.Lc, st, &c.tw));
   FK_CUDA(cudaMemsetAsync(c.ch, 0, sizeof(cplx<double>) * c.LL, st));
   int64_t M2 = 1;
   for (int l = 0; l < d; ++l) M2 *= (4 * m + 1);
@@ -1232,10 +1234,9 @@ static fk_status cg_solve_fused(int d, int m, const double* T, const double* W, 
   const int64_t D = (d == 1) ? K : static_cast<int64_t>(K) * K;
   const int64_t LL = (d == 1) ? Lc : static_cast<int64_t>(Lc) * Lc;
   cplx<double>* ch;
-  double* tw;
+  const double* tw;
   FK_TRY(scr.alloc(&ch, LL));
-  FK_TRY(scr.alloc(&tw, 2 * static_cast<size_t>(Lc)));
-  FK_TRY(fft_twiddles(Lc, tw, st));
+  FK_TRY(twiddle_table(Lc, st, &tw));
   FK_CUDA(cudaMemsetAsync(ch, 0, sizeof(cplx<double>) * LL, st));
   int64_t M2 = 1;
   for (int l = 0; l < d; ++l) M2 *= (4 * m + 1);
@@ -1475,7 +1476,7 @@ namespace {
 constexpr long long BAR_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
 struct GridBar {
-  unsigned count, gen;
+  unsigned count, unused;  // count: arrivals since the launch (zeroed before it)
 };
 
 struct CgP {
@@ -1501,39 +1502,46 @@ struct CgP {
   cplx<double>* buf2;
   double* idg;         // [n_w][D] inverse Jacobi diagonal 1 / (T_0 + Wd), set by the init phase
   int final_residual;  // one more matvec for |b - A x| (reports only)
+  // Lc = 4m (alias): the circulant cannot tell the lags -2m and +2m apart and holds
+  // +2m; the terms of lag -2m in either coordinate are added from the Toeplitz
+  // entries themselves (Tc, and Cc for the operator penalty) into corr
+  // [nsys][4][K]: 0/1 the moment matrix's row-0 / column-0 corrections, 2/3 the
+  // operator's.
+  int alias;
+  const double* Tc;
+  const double* Cc;
+  cplx<double>* corr;
 };
 
 // all CTAs of the launch; false when the wait gave up (the caller returns)
-// The CTA barrier orders the block's writes before thread 0's fence and arrival, and
-// thread 0's fence after the release orders them before the block's later reads (the
-// cumulativity argument of a cooperative grid barrier), so only thread 0 fences.
+// The arrival counter only grows: a CTA's arrival returns the count before it, which
+// names its barrier, and the CTA waits until the count reaches that barrier's last
+// arrival.  The CTA barrier orders the block's writes before thread 0's releasing
+// arrival, and thread 0's acquiring loads order the later barrier's reads after every
+// other CTA's arrival, so no thread needs a separate fence.
 __device__ bool grid_sync(GridBar* gb, unsigned* flags) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    unsigned g;  // the generation cannot advance before this CTA arrives
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(&gb->gen) : "memory");
-    __threadfence();
-    if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
-      atomicExch(&gb->count, 0u);
-      __threadfence();
-      atomicAdd(&gb->gen, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*reinterpret_cast<volatile unsigned*>(&gb->gen) == g) {
-        if (*reinterpret_cast<volatile unsigned*>(flags) & FLAG_TIMEOUT) {
-          ok = 0;
-          break;
-        }
-        if (clock64() - t0 > BAR_WAIT_CYCLES) {
-          atomicOr(flags, FLAG_TIMEOUT);
-          ok = 0;
-          break;
-        }
+    unsigned old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(&gb->count) : "memory");
+    const unsigned target = (old / gridDim.x + 1) * gridDim.x;
+    const long long t0 = clock64();
+    while (true) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&gb->count) : "memory");
+      if (static_cast<int>(v - target) >= 0) break;
+      if (*reinterpret_cast<volatile unsigned*>(flags) & FLAG_TIMEOUT) {
+        ok = 0;
+        break;
+      }
+      if (clock64() - t0 > BAR_WAIT_CYCLES) {
+        atomicOr(flags, FLAG_TIMEOUT);
+        ok = 0;
+        break;
       }
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
@@ -1616,11 +1624,93 @@ __device__ void cgp_rows_fwd(const CgP& A, cplx<double>* sl, int it, bool final_
   }
 }
 
-// P2
+// corrections per system: one warp per output, 8 outputs per task, for the row-0 and
+// column-0 parts of each aliased product
+__host__ __device__ __forceinline__ int cg_alias_tasks(int K, bool op) { return (op ? 4 : 2) * ((K + 7) / 8); }
+
+// Lag -2m terms of the Toeplitz product for one task.  With modes indexed 0..K-1
+// (j = index - m), lag (d1, d2) = j - k, and Lc = 4m, the circulant applied the
+// entry at lag alias(d) (each -2m coordinate replaced by +2m) where the product wants
+// T[d].  The differences are nonzero only where d1 = -2m (outputs of row 0, inputs
+// from row K-1) or d2 = -2m (outputs of column 0, inputs from column K-1); the second
+// set leaves out d1 = -2m, which the first already holds.
+__device__ void cgp_alias_task(const CgP& A, int t, int it, bool final_pass) {
+  const int K = A.K, m = (K - 1) / 2, K2 = 4 * m + 1;
+  const int ngrp = (K + 7) / 8, per = cg_alias_tasks(K, A.ch2 != nullptr);
+  const int s = t / per, r = t - s * per;
+  const int kind = r / ngrp, g = r - kind * ngrp;
+  if (!final_pass && !cg_active(A, it, s)) return;
+  const int e = g * 8 + static_cast<int>(threadIdx.x >> 5);
+  if (e >= K) return;
+  const int lane = threadIdx.x & 31;
+  const double* Tm = kind >= 2 ? A.Cc : A.Tc;
+  const bool col0 = kind & 1;
+  const double* v = (final_pass ? A.x : A.p) + 2 * static_cast<int64_t>(s) * A.D;
+  double sr = 0.0, si = 0.0;
+  for (int k = lane; k < K; k += 32) {
+    const int dd = e - k + 2 * m;  // lag along the convolved coordinate, + 2m
+    int64_t ia, ib;                // T entries of the true and of the applied lag
+    if (!col0) {
+      ia = dd;
+      ib = static_cast<int64_t>(4 * m) * K2 + (dd == 0 ? 4 * m : dd);
+    } else {
+      if (dd == 0) continue;
+      ia = static_cast<int64_t>(dd) * K2;
+      ib = ia + 4 * m;
+    }
+    const int64_t pk = col0 ? static_cast<int64_t>(k) * K + (K - 1) : static_cast<int64_t>(K - 1) * K + k;
+    double vr = __ldcg(v + 2 * pk), vi = __ldcg(v + 2 * pk + 1);
+    if (kind >= 2) {
+      const double pr = A.P[2 * pk], pim = A.P[2 * pk + 1];
+      const double ur = pr * vr - pim * vi;
+      vi = pr * vi + pim * vr;
+      vr = ur;
+    }
+    const double dr = __ldg(Tm + 2 * ia) - __ldg(Tm + 2 * ib);
+    const double di = __ldg(Tm + 2 * ia + 1) - __ldg(Tm + 2 * ib + 1);
+    sr += dr * vr - di * vi;
+    si += dr * vi + di * vr;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_down_sync(0xffffffffu, sr, o);
+    si += __shfl_down_sync(0xffffffffu, si, o);
+  }
+  if (lane == 0) {
+    cplx<double>& c = A.corr[(static_cast<int64_t>(s) * 4 + kind) * K + e];
+    c.x = sr;
+    c.y = si;
+  }
+}
+
+// the correction of output (row, i): row 0 takes task 0 (2), column 0 task 1 (3)
+__device__ __forceinline__ cplx<double> cg_alias_corr(const CgP& A, int s, int row, int i, int base) {
+  cplx<double> c;
+  c.x = c.y = 0.0;
+  if (!A.alias) return c;
+  const cplx<double>* cs = A.corr + static_cast<int64_t>(s) * 4 * A.K;
+  if (row == 0) {
+    const double2 a = __ldcg(reinterpret_cast<const double2*>(cs + base * A.K + i));
+    c.x += a.x;
+    c.y += a.y;
+  }
+  if (i == 0) {
+    const double2 b = __ldcg(reinterpret_cast<const double2*>(cs + (base + 1) * A.K + row));
+    c.x += b.x;
+    c.y += b.y;
+  }
+  return c;
+}
+
+// P2 (and the alias corrections, on the CTAs past the columns)
 __device__ void cgp_cols(const CgP& A, cplx<double>* sl, int it, bool final_pass) {
   const int K = A.K, Lc = A.Lc;
   const int nitems = A.nsys * Lc * (A.ch2 ? 2 : 1);
-  for (int item2 = blockIdx.x; item2 < nitems; item2 += gridDim.x) {
+  const int ntot = nitems + (A.alias ? A.nsys * cg_alias_tasks(K, A.ch2 != nullptr) : 0);
+  for (int item2 = blockIdx.x; item2 < ntot; item2 += gridDim.x) {
+    if (item2 >= nitems) {
+      cgp_alias_task(A, item2 - nitems, it, final_pass);
+      continue;
+    }
     const bool second = item2 >= A.nsys * Lc;  // the operator penalty's product
     const int item = second ? item2 - A.nsys * Lc : item2;
     const cplx<double>* spec = second ? A.ch2 : A.ch;
@@ -1685,8 +1775,9 @@ __device__ void cgp_rows_inv(const CgP& A, cplx<double>* sl, double* red, int it
     const double* v = final_pass ? A.x : A.p;
     for (int i = threadIdx.x; i < K; i += blockDim.x) {
       const double vr = __ldcg(v + o + 2 * i), vi = __ldcg(v + o + 2 * i + 1);
-      A.q[o + 2 * i] = sl[i].x * inv + Ws[i] * vr;
-      A.q[o + 2 * i + 1] = sl[i].y * inv + Ws[i] * vi;
+      const cplx<double> c = cg_alias_corr(A, s, row, i, 0);
+      A.q[o + 2 * i] = sl[i].x * inv + c.x + Ws[i] * vr;
+      A.q[o + 2 * i + 1] = sl[i].y * inv + c.y + Ws[i] * vi;
     }
     if (A.ch2) {
       __syncthreads();
@@ -1703,7 +1794,8 @@ __device__ void cgp_rows_inv(const CgP& A, cplx<double>* sl, double* red, int it
       for (int i = threadIdx.x; i < K; i += blockDim.x) {
         const int64_t pk = static_cast<int64_t>(row) * K + i;
         const double pr = A.P[2 * pk], pim = -A.P[2 * pk + 1];  // conj(P)
-        const double tr = sl[i].x * inv, ti = sl[i].y * inv;
+        const cplx<double> c = cg_alias_corr(A, s, row, i, 2);
+        const double tr = sl[i].x * inv + c.x, ti = sl[i].y * inv + c.y;
         A.q[o + 2 * i] += A.mu * (pr * tr - pim * ti);
         A.q[o + 2 * i + 1] += A.mu * (pr * ti + pim * tr);
       }
@@ -1853,7 +1945,10 @@ fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, 
   FK_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   FK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int K = 2 * m + 1;
-  int Lc = next_pow2i(4 * m + 1);
+  // the lags span 4m + 1 values; where 4m is a power of two the circulant takes
+  // length 4m and the lag -2m is added separately (a quarter of the FFT work of 8m)
+  const bool alias = m >= 1 && next_pow2i(4 * m) == 4 * m;
+  int Lc = alias ? 4 * m : next_pow2i(4 * m + 1);
   if (Lc < 2) Lc = 2;
   int logLc = 0;
   while ((1 << logLc) < Lc) ++logLc;
@@ -1877,7 +1972,8 @@ fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, 
   if (per_sm < 1) return FK_OK;
   const int nsys = n_w * n_rhs;
   const int64_t D = static_cast<int64_t>(K) * K;
-  const int64_t want = std::max<int64_t>(static_cast<int64_t>(nsys) * Lc, 1);
+  const int64_t want = std::max<int64_t>(
+      static_cast<int64_t>(nsys) * (Lc * (op ? 2 : 1) + (alias ? cg_alias_tasks(K, op != nullptr) : 0)), 1);
   const int nb = static_cast<int>(std::min<int64_t>(want, static_cast<int64_t>(std::min(per_sm, 2)) * sms));
 
   CgP A{};
@@ -1895,10 +1991,9 @@ fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, 
   int64_t centre = 2 * static_cast<int64_t>(4 * m + 1) * m + 2 * m;  // index of T_(0,0)
   A.T0p = T + 2 * centre;
   cplx<double>* ch;
-  double* tw;
+  const double* tw;
   FK_TRY(scr.alloc(&ch, static_cast<int64_t>(Lc) * Lc));
-  FK_TRY(scr.alloc(&tw, 2 * static_cast<size_t>(Lc)));
-  FK_TRY(fft_twiddles(Lc, tw, st));
+  FK_TRY(twiddle_table(Lc, st, &tw));
   FK_CUDA(cudaMemsetAsync(ch, 0, sizeof(cplx<double>) * Lc * Lc, st));
   const int64_t M2 = static_cast<int64_t>(4 * m + 1) * (4 * m + 1);
   k_circ_embed<<<grid_for(M2, 256), 256, 0, st>>>(2, m, Lc, T, ch); note_launch();
@@ -1926,6 +2021,10 @@ fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, 
     A.Wd = wd;
     FK_TRY(scr.alloc(&A.buf2, static_cast<size_t>(nsys) * K * Lc));
   }
+  A.alias = alias ? 1 : 0;
+  A.Tc = T;
+  A.Cc = op ? op->c : nullptr;
+  if (alias) FK_TRY(scr.alloc(&A.corr, static_cast<size_t>(nsys) * 4 * K));
   FK_TRY(scr.alloc(&A.r, 2 * D * nsys));
   FK_TRY(scr.alloc(&A.idg, D * n_w));
   A.final_residual = relres_out != nullptr;

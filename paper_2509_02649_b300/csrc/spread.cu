@@ -236,10 +236,9 @@ fk_status type2_eval(const EsPlan& p, int kmax_c, const double* coef, int n_sets
   int64_t GN = 1;
   for (int l = 0; l < p.d; ++l) GN *= N;
   cplx<R>* G = nullptr;
-  double* tw = nullptr;
+  const double* tw = nullptr;
   FK_TRY(scratch.alloc(&G, GN * n_sets));
-  FK_TRY(scratch.alloc(&tw, 2 * static_cast<size_t>(N)));
-  FK_TRY(fft_twiddles(N, tw, st));
+  FK_TRY(twiddle_table(N, st, &tw));
   FK_CUDA(cudaMemsetAsync(G, 0, sizeof(cplx<R>) * GN * n_sets, st));
   const int K = 2 * kmax_c + 1;
   int64_t D = 1;

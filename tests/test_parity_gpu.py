@@ -175,6 +175,31 @@ def test_cholesky_and_cg_agree_with_oracle_solve(d, m):
     assert rep["cg_iters"] > 0
 
 
+@pytest.mark.parametrize("m", [15, 16])
+def test_cg_corner_lags(m):
+    # A shifted lattice of 2m points per period puts |T| at the lags +-2m on the order
+    # of T_0, with T_(-2m) != T_(2m).  For m = 16 the cooperative CG's circulant has
+    # length 4m and adds the lag -2m terms itself; m = 15 takes length 8m - 2 -> 64.
+    lat = S.equispaced_2d(2 * m, 2 * m) + 0.3 / m
+    x = np.concatenate([lat, S.uniform_points(3000, 2, 29)], axis=1)
+    x = (x + np.pi) % (2 * np.pi) - np.pi
+    To = O.moments(x, m)
+    K2 = 4 * m + 1
+    Tm = To.reshape(K2, K2)
+    assert abs(Tm[0, 2 * m] - Tm[4 * m, 2 * m]) > 0.1 * Tm[2 * m, 2 * m].real
+    D = (2 * m + 1) ** 2
+    g = np.random.default_rng(8)
+    rhs = g.standard_normal((2, D)) + 1j * g.standard_normal((2, D))
+    lams = [1e-4, 1e-1]
+    Wo = np.stack([O.penalty_sobolev(2, m, l, 1.5) for l in lams])
+    sol = host(fk.fk_solve(torch.from_numpy(To).cuda(), torch.from_numpy(Wo).cuda(), torch.from_numpy(rhs).cuda(), 2,
+                           m, opts=fk.default_opts(solver=fk.FK_SOLVER_CG, cg_tol=1e-13)))
+    A = O.toeplitz_matrix(To, 2, m)
+    for li in range(2):
+        want = O.solve_hpd(A + np.diag(Wo[li]), rhs.T).T
+        assert rel(sol[li], want) < 1e-10, li
+
+
 def test_not_positive_definite_reported():
     m = 4
     x = S.uniform_points(100, 1, 28)
