@@ -589,18 +589,22 @@ __global__ void __launch_bounds__(T, 1024 / T) k_bin_scatter1(PartArgs A) {
     if (!mbar_wait(bar, phase, A.flags)) return;
     phase ^= 1u;
     __syncthreads();
+    // rk: the point's rank among the tile's points of its owner (its place in the
+    // owner's run)
     uint4 rec[PER];
+    int rk[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const int i = k * T + tid;
       rec[k].x = 0xFFFFFFFFu;
+      rk[k] = 0;
       if (i < cnt) {
         float f0, f1;
         uint32_t key;
         if (point_key(stage[i], stage[TILE + i], A, inv_cpc, &f0, &f1, &key)) {
           rec[k] = make_uint4(key, __float_as_uint(f0), __float_as_uint(f1),
                               A.has_y ? __float_as_uint(stage[2 * TILE + i]) : 0u);
-          atomicAdd(&tcnt[key >> 16], 1);
+          rk[k] = atomicAdd(&tcnt[key >> 16], 1);
         } else {
           atomicOr(A.flags, FLAG_RANGE);
         }
@@ -632,19 +636,14 @@ __global__ void __launch_bounds__(T, 1024 / T) k_bin_scatter1(PartArgs A) {
       }
       int acc = incl - run;
       for (int o = o0; o < o1; ++o) {
-        tcur[o] = acc;
         toff[o] = acc;
         acc += (o < G) ? tcnt[o] : 0;
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      if (rec[k].x != 0xFFFFFFFFu) {
-        const int p2 = atomicAdd(&tcur[rec[k].x >> 16], 1);
-        sorted[p2] = rec[k];
-      }
-    }
+    for (int k = 0; k < PER; ++k)
+      if (rec[k].x != 0xFFFFFFFFu) sorted[toff[rec[k].x >> 16] + rk[k]] = rec[k];
     if (tid < G) {
       if (my_c > 0 && my_pos + my_c > A.cap) {
         atomicOr(A.ovf, 1u);
