@@ -16,15 +16,15 @@
 //                 fractional offsets, sorts a tile by owner in shared memory, reserves
 //                 room in the owner buckets (fixed capacity: mean load + 2 % + 4096)
 //                 with one global atomic per (tile, owner) and writes the tile's runs
-//                 as contiguous records: 16 bytes {owner:local cell, f0, f1, strength},
-//                 or 8 bytes (cell and fixed-point offsets) when only ones are spread;
+//                 as contiguous records: 8 bytes (local cell and fixed-point window
+//                 offsets), with the strengths in a parallel stream of floats;
 //   k_bin_accumulate (one CTA per owner) streams its owner's bucket with double-
-//                 buffered TMA bulk copies, links each round's records into per-cell
-//                 lists in shared memory, and lets each lane run over at most a quota
-//                 of its cell's points (the mean load plus a fraction of a standard
-//                 deviation); the excess of fuller cells is carried into the next
-//                 round, which keeps the warps' trip counts even.  A lane adds its
-//                 register window into the fp64 grid every 2048 points and at the end.
+//                 buffered TMA bulk copies and links each round's records into per-cell
+//                 lists in shared memory.  A record whose rank in its cell reaches the
+//                 round's quota (the mean load plus a fraction of a standard deviation)
+//                 moves to the next round's buffer instead, which keeps the warps' trip
+//                 counts even.  A lane adds its register window into the fp64 grid
+//                 every 2048 points and at the end.
 // A bucket that would overflow (crowded points) sets a device flag; the exact
 // partition (k_bin_count, k_bin_scan, k_bin_scatter2 or k_bin_scatter, then
 // k_bin_accumulate on its 16-byte records) is always enqueued after and runs only when
@@ -41,39 +41,13 @@ namespace {
 
 constexpr int MAX_G = 511;  // owners (< partition block size, for the block-wide scans)
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
-constexpr int CARRY = 2048;                      // records a CTA may defer to its next round
 constexpr int THREADS_ACC = 448;                 // accumulation CTA size (one CTA per SM)
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ bool wait_counter(const int* ctr, int target, unsigned* flags) {
-  const long long t0 = clock64();
-  while (true) {
-    if (*reinterpret_cast<const volatile int*>(ctr) >= target) break;
-    if (clock64() - t0 > WAIT_CYCLES) {
-      atomicOr(flags, FLAG_TIMEOUT);
-      return false;
-    }
-    if (*reinterpret_cast<const volatile unsigned*>(flags) & FLAG_TIMEOUT) return false;
-    __nanosleep(64);
-  }
-  __threadfence();
-  return true;
-}
-
 // ---------------------------------------------------------------- async copies
-__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
 __device__ __forceinline__ void mbar_init(uint64_t* bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -108,28 +82,9 @@ __device__ __forceinline__ void bulk_g2s(void* sdst, const void* gsrc, unsigned 
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
-// one warp: exclusive scan of v[0..cnt) in place, returns the total (all lanes)
-__device__ __forceinline__ int warp_exclusive_scan(int* v, int cnt, int lane) {
-  int carry = 0;
-  for (int o0 = 0; o0 < cnt; o0 += 32) {
-    const int o = o0 + lane;
-    const int x = (o < cnt) ? v[o] : 0;
-    int incl = x;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += t;
-    }
-    if (o < cnt) v[o] = carry + incl - x;
-    carry += __shfl_sync(0xffffffffu, incl, 31);
-  }
-  return carry;
-}
-
 constexpr int P_THREADS = 1024;  // count kernel
 constexpr int P_NWARPS = P_THREADS / 32;
 constexpr int P_TILE = 4096;     // points per partition block, at least
-constexpr int CAPR = 4096;       // records per accumulation round
 constexpr int FLUSH_PTS = 2048;  // points per fp32 register run before an fp64 flush
 
 // cells per owner: one lane per cell, or two (one per channel) in pair mode
@@ -696,7 +651,7 @@ struct AccArgs {
 };
 
 struct AccLayout {
-  size_t stage, ystage, nxt, head, ccount, total;
+  size_t stage, ystage, nxt, head, ccount, xcnt, total;
 };
 template <typename R>
 __host__ __device__ inline AccLayout acc_layout(int cpc) {
@@ -708,7 +663,8 @@ __host__ __device__ inline AccLayout acc_layout(int cpc) {
   L.nxt = L.ystage + yb;                                            // [CARRY + CAPR] u16
   L.head = (L.nxt + sizeof(unsigned short) * (CARRY + CAPR) + 15) & ~static_cast<size_t>(15);  // [cpc] int
   L.ccount = L.head + sizeof(int) * cpc;                            // [cpc] int
-  L.total = L.ccount + sizeof(int) * cpc;
+  L.xcnt = L.ccount + sizeof(int) * cpc;                            // [cpc] int
+  L.total = L.xcnt + sizeof(int) * cpc;
   return L;
 }
 
@@ -719,7 +675,8 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
   constexpr int THREADS = Cfg<PAIR>::THREADS;
   constexpr int CAPR = R::CAPR, CARRY = R::CARRY;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_base, s_count, s_ncarry, s_nleft, s_abort;
+  __shared__ int s_base, s_count, s_abort;
+  __shared__ int s_ncar[2];  // records deferred into buffer b (counted during the round before)
   __shared__ __align__(8) uint64_t s_bar[2];
   const int tid = threadIdx.x, lane = tid & 31;
   const int b = blockIdx.x;
@@ -738,6 +695,7 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
   unsigned short* nxt = reinterpret_cast<unsigned short*>(smem + L.nxt);
   int* head = reinterpret_cast<int*>(smem + L.head);
   int* ccount = reinterpret_cast<int*>(smem + L.ccount);
+  int* xcnt = reinterpret_cast<int*>(smem + L.xcnt);  // records linked beyond the quota
 
   if (A.mode != 0) {
     const bool ov = *reinterpret_cast<const volatile unsigned*>(A.ovf) != 0u;
@@ -747,7 +705,7 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
     if (tid == 0) {
       s_base = b * A.cap;
       s_count = min(__ldg(A.fill + b), A.cap);
-      s_ncarry = 0;
+      s_ncar[0] = s_ncar[1] = 0;
       s_abort = 0;
       mbar_init(&s_bar[0]);
       mbar_init(&s_bar[1]);
@@ -767,7 +725,7 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
       for (int w = 0; w < THREADS / 32; ++w) sum += wsum[w];
       s_base = sum;
       s_count = __ldg(A.tot + b);
-      s_ncarry = 0;
+      s_ncar[0] = s_ncar[1] = 0;
       s_abort = 0;
       mbar_init(&s_bar[0]);
       mbar_init(&s_bar[1]);
@@ -777,6 +735,7 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
   for (int i = tid; i < cpc; i += THREADS) {
     head[i] = 0xFFFF;
     ccount[i] = 0;
+    xcnt[i] = 0;
   }
   __syncthreads();
   const int base = s_base, count = s_count;
@@ -827,52 +786,66 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
   if (tid == 0) issue(0);
 
   for (int r = 0; r < nrounds; ++r) {
-    const int buf = r & 1;
+    const int buf = r & 1, nb = buf ^ 1;
     RT* st = stage + buf * (CARRY + CAPR);
     const float* yst = ystage + buf * (CARRY + CAPR);
+    RT* nst = stage + nb * (CARRY + CAPR);
+    float* nyst = ystage + nb * (CARRY + CAPR);
     const int nr = min(CAPR, count - r * CAPR);
-    const int nc = s_ncarry;
+    const int nc = min(s_ncar[buf], CARRY);
     if (!mbar_wait(&s_bar[buf], (r >> 1) & 1, A.flags)) s_abort = 1;
     __syncthreads();
     if (s_abort) return;
-    if (tid == 0) {
-      if (r + 1 < nrounds) issue(r + 1);
-      s_nleft = 0;
-    }
-    // records of this round: [CARRY - nc, CARRY + nr) of the buffer
+    if (tid == 0 && r + 1 < nrounds) issue(r + 1);
+    // records of this round: [CARRY - nc, CARRY + nr) of the buffer, the ones deferred
+    // from the last round in front
     const int lo = CARRY - nc, hi = CARRY + nr;
-    // four records per thread and trip, so that their shared-memory atomics overlap
-    for (int base = lo + tid; base < hi; base += 4 * THREADS) {
-      int cl[4], old[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int idx = base + u * THREADS;
-        cl[u] = (idx < hi) ? R::cell(st[idx]) : 0xFFFF;  // 0xFFFF: run padding
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (cl[u] != 0xFFFF) {
-          atomicAdd(&ccount[cl[u]], 1);
-          old[u] = atomicExch(&head[cl[u]], base + u * THREADS);
-        }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (cl[u] != 0xFFFF) nxt[base + u * THREADS] = static_cast<unsigned short>(old[u]);
-    }
     const bool last = (r == nrounds - 1);
     int q = 0x7FFFFFFF;
     if (!last && my_ncells > 0) {
       const float lam = static_cast<float>(hi - lo) / static_cast<float>(my_ncells);
       q = static_cast<int>(ceilf(lam + A.qmul * sqrtf(lam)));
     }
+    // A record's rank in its cell (the count atomic's old value) decides at once: below
+    // the quota it is linked into the cell's list, else it moves to the front of the
+    // next buffer (deferred to the next round) while there is room, and is linked
+    // beyond the quota (xcnt) when there is not.  LU records per thread and trip, so
+    // that their shared-memory atomics overlap.
+    constexpr int LU = 4;
+    for (int base = lo + tid; base < hi; base += LU * THREADS) {
+      int cl[LU], rk[LU];
+#pragma unroll
+      for (int u = 0; u < LU; ++u) {
+        const int idx = base + u * THREADS;
+        cl[u] = (idx < hi) ? R::cell(st[idx]) : 0xFFFF;  // 0xFFFF: run padding
+      }
+#pragma unroll
+      for (int u = 0; u < LU; ++u)
+        if (cl[u] != 0xFFFF) rk[u] = atomicAdd(&ccount[cl[u]], 1);
+#pragma unroll
+      for (int u = 0; u < LU; ++u)
+        if (cl[u] != 0xFFFF) {
+          const int idx = base + u * THREADS;
+          bool link = rk[u] < q;
+          if (!link) {
+            const int pd = atomicAdd(&s_ncar[nb], 1);
+            if (pd < CARRY) {
+              nst[CARRY - 1 - pd] = st[idx];
+              if (R::SPLIT_Y) nyst[CARRY - 1 - pd] = yst[idx];
+            } else {
+              link = true;
+              atomicAdd(&xcnt[cl[u]], 1);
+            }
+          }
+          if (link) nxt[idx] = static_cast<unsigned short>(atomicExch(&head[cl[u]], idx));
+        }
+    }
     __syncthreads();
-    const int mine = owns ? ccount[cell] : 0;
-    if (ch == 0 && mine > q) atomicAdd(&s_nleft, mine - q);
-    __syncthreads();
-    if (s_nleft > CARRY) q = 0x7FFFFFFF;  // not enough room: process everything now
+    if (tid == 0) s_ncar[buf] = 0;  // read by every thread before this round's first barrier
+    const int mine = owns ? min(ccount[cell], q) + xcnt[cell] : 0;
     int ri = owns ? head[cell] : 0xFFFF;
     if (owns) {
-      const int nproc = min(mine, q);
+      const int nproc = mine;
       if constexpr (PAIR) {
         // lane 0 of the pair: ones channel, window [a][b]; lane 1: strength channel,
         // window transposed ([b][a]) because it holds the second coordinate's weights.
@@ -947,33 +920,20 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
       }
     }
     if (owns) {
-      since += min(mine, q);
+      since += mine;
       if (since >= FLUSH_PTS) {
         flush();
         since = 0;
       }
-    }
-    __syncthreads();
-    // deferred records go in front of the next buffer's TMA region
-    const int nleft = (q == 0x7FFFFFFF) ? 0 : s_nleft;
-    if (tid == 0) s_ncarry = 0;
-    __syncthreads();
-    if (owns && ch == 0 && mine > q) {
-      RT* nst = stage + (buf ^ 1) * (CARRY + CAPR);
-      float* nyst = ystage + (buf ^ 1) * (CARRY + CAPR);
-      int dst = CARRY - nleft + atomicAdd(&s_ncarry, mine - q);
-      while (ri != 0xFFFF) {
-        nst[dst] = st[ri];
-        if (R::SPLIT_Y) nyst[dst] = yst[ri];
-        ++dst;
-        ri = nxt[ri];
+      // this cell's lists are done (both lanes of a pair read them before their loop);
+      // the next round's linking starts after its first barrier
+      if constexpr (PAIR) __syncwarp(pmask);
+      if (ch == 0) {
+        head[cell] = 0xFFFF;
+        ccount[cell] = 0;
+        xcnt[cell] = 0;
       }
     }
-    for (int i = tid; i < cpc; i += THREADS) {
-      head[i] = 0xFFFF;
-      ccount[i] = 0;
-    }
-    __syncthreads();
   }
   // flush the register window into the fp64 grid
   if (owns && since > 0) flush();
