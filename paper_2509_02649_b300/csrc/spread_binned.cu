@@ -86,6 +86,7 @@ constexpr int P_THREADS = 1024;  // count kernel
 constexpr int P_NWARPS = P_THREADS / 32;
 constexpr int P_TILE = 4096;     // points per partition block, at least
 constexpr int FLUSH_PTS = 2048;  // points per fp32 register run before an fp64 flush
+constexpr long long NO_ROOM = -(1ll << 62);  // one-pass partition: the owner's bucket is full
 
 // cells per owner: one lane per cell, or two (one per channel) in pair mode
 template <bool PAIR>
@@ -513,10 +514,11 @@ __global__ void __launch_bounds__(T, 1024 / T) k_bin_scatter1(PartArgs A) {
   const S2Layout L = s2_layout(G, TILE);
   float* stage = reinterpret_cast<float*>(smem + L.stage);
   uint4* sorted = reinterpret_cast<uint4*>(smem + L.sorted);
-  int* tpos = reinterpret_cast<int*>(smem + L.ints);  // [G + 1] reserved slot in the bucket, -1: none
-  int* tcnt = tpos + (G + 1);                          // [G + 1] counts of the tile
-  int* tcur = tcnt + (G + 1);                          // [G + 1] placement cursors
-  int* toff = tcur + (G + 1);                          // [G + 1] run starts inside the tile
+  int* tcnt = reinterpret_cast<int*>(smem + L.ints);  // [G + 1] counts of the tile
+  int* toff = tcnt + (G + 1);                          // [G + 1] run starts inside the tile
+  // [G + 1] bucket index of tile slot 0 for each owner's run (owner base + reserved
+  // slot - run start; may be negative), or NO_ROOM
+  long long* gdelta = reinterpret_cast<long long*>(toff + (G + 1));
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
   const int tid = threadIdx.x;
   const float inv_cpc = 1.0f / static_cast<float>(A.cells_per);
@@ -604,7 +606,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_bin_scatter1(PartArgs A) {
         atomicOr(A.ovf, 1u);
         my_pos = -1;
       }
-      tpos[tid] = my_pos;
+      gdelta[tid] = my_pos >= 0 ? static_cast<long long>(tid) * A.cap + my_pos - toff[tid] : NO_ROOM;
     }
     __syncthreads();
     const int valid = toff[G];
@@ -614,10 +616,9 @@ __global__ void __launch_bounds__(T, 1024 / T) k_bin_scatter1(PartArgs A) {
       const int j = k * T + tid;
       if (j < valid) {
         const uint4 r = sorted[j];
-        const int o = static_cast<int>(r.x >> 16);
-        const int pos = tpos[o];
-        const int64_t at = static_cast<int64_t>(o) * A.cap + pos + (j - toff[o]);
-        if (pos >= 0) {
+        const long long gd = gdelta[r.x >> 16];
+        const int64_t at = gd + j;
+        if (gd != NO_ROOM) {
           if (REC8) {
             reinterpret_cast<uint2*>(A.rec)[at] = pack_rec8(r, 0.5f * static_cast<float>(A.W));
             if (A.has_y) A.ybuf[at] = __uint_as_float(r.w);
