@@ -37,6 +37,7 @@ constexpr int THREADS = 1024;
 constexpr size_t SMEM_BUDGET = 220 * 1024;      // bytes of integer grids per CTA
 constexpr float MAGIC = 12582912.0f;            // 1.5 * 2^23
 constexpr int MAGIC_BITS = 0x4B400000;
+constexpr unsigned WRAP_MARGIN = 1u << 22;      // > max |q| = 2^21 (+1)
 
 struct Fx1dArgs {
   int64_t n;
@@ -129,12 +130,14 @@ __global__ void __launch_bounds__(THREADS) k_spread1d_fx(Fx1dArgs A) {
         qv[a] = __float_as_int(fmaf(psi[a], v, MAGIC)) - MAGIC_BITS;
         old[a] = atomicAdd(lc + a, static_cast<unsigned>(qv[a]));
       }
-      // high-word change per tap: sign extension of q plus the carry out of the
-      // low-word add; nonzero only when the low word wraps (rare)
-      int any = 0;
+      // a low word can wrap only if it was within |q| <= 2^21 (+1 for a tap rounding
+      // above 1) of 0 mod 2^32 before the add: one unsigned min over the taps screens
+      // for that, and the exact high-word changes (sign extension of q plus the carry
+      // out of the add) are taken only then (rare: the words start at 2^31)
+      unsigned near = 0xFFFFFFFFu;
 #pragma unroll
-      for (int a = 0; a < W; ++a) any |= carry_delta(old[a], static_cast<unsigned>(qv[a]), qv[a] >> 31);
-      if (any) {
+      for (int a = 0; a < W; ++a) near = min(near, old[a] + WRAP_MARGIN);
+      if (near < 2u * WRAP_MARGIN) {
         unsigned long long* hc = A.acc + static_cast<int64_t>(c0 + c) * N;
 #pragma unroll
         for (int a = 0; a < W; ++a) {

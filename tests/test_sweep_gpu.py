@@ -93,6 +93,22 @@ def test_fixed_spread_is_bitwise_reproducible():
     assert torch.equal(T1, T2) and torch.equal(b1, b2)
 
 
+def test_fixed_spread_low_word_wraps():
+    # 3e6 points at one position: every CTA adds thousands of same-sign contributions
+    # to the same nodes, so the 32-bit low words wrap many times.  Closed form:
+    # T_j = e^{-i j x0}, b_k = mean(y) e^{-i k x0}.
+    n, m = 3_000_000, 20
+    x0 = np.float32(0.3)
+    x = np.full((1, n), x0, dtype=np.float32)
+    y = (1.0 + 0.5 * np.random.default_rng(3).random((2, n))).astype(np.float32)
+    T, b = fk.fk_build_system(dev(x), dev(y), m, 1e-6, "mixed", opts=fk.default_opts(spread=fk.FK_SPREAD_FIXED))
+    j = np.arange(-2 * m, 2 * m + 1)
+    assert rel(host(T), np.exp(-1j * j * np.float64(x0))) < 1e-5
+    k = np.arange(-m, m + 1)
+    for t in range(2):
+        assert rel(host(b)[t], y[t].astype(np.float64).mean() * np.exp(-1j * k * np.float64(x0))) < 1e-5
+
+
 def test_fixed_spread_scale_handling():
     x, y = sweep_sample(20_000, 3)
     X = dev(x)
