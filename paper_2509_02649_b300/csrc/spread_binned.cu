@@ -88,15 +88,49 @@ constexpr int P_TILE = 4096;     // points per partition block, at least
 constexpr int FLUSH_PTS = 2048;  // points per fp32 register run before an fp64 flush
 constexpr long long NO_ROOM = -(1ll << 62);  // one-pass partition: the owner's bucket is full
 
-// cells per owner: one lane per cell, or two (one per channel) in pair mode
+// cells per owner: one lane per cell, or two (one per channel) in pair mode, whose
+// CTAs have 16 warps (four per scheduler)
 template <bool PAIR>
 struct Cfg {
-  static constexpr int THREADS = THREADS_ACC;
-  static constexpr int CELLS = PAIR ? THREADS_ACC / 2 : THREADS_ACC;
+  static constexpr int THREADS = PAIR ? 512 : THREADS_ACC;
+  static constexpr int CELLS = PAIR ? 256 : THREADS_ACC;
+};
+
+// Cells of owner o: nb "big" owners of cb cells, then owners of cs cells.  Two sizes
+// let a grid of ~two waves give each wave whole multiples of four warps per SM (16
+// then 12 in pair mode), so that no scheduler of an SM carries more warps than another.
+struct OwnerMap {
+  int nb, cb, cs;
+  float inv_cb, inv_cs;
+  __host__ __device__ int first(int o) const { return o < nb ? o * cb : nb * cb + (o - nb) * cs; }
+  __host__ __device__ int cells(int o) const { return o < nb ? cb : cs; }
+  // owner of cell `key` and the cell's index inside it
+  __device__ __forceinline__ int owner(int key, int* local) const {
+    const int kb = nb * cb;
+    int o, base, c;
+    float inv;
+    if (key < kb) {
+      base = 0;
+      c = cb;
+      inv = inv_cb;
+    } else {
+      base = kb;
+      c = cs;
+      inv = inv_cs;
+    }
+    const int k = key - base;
+    int q = __float2int_rd(static_cast<float>(k) * inv);
+    if (q * c > k) --q;
+    else if ((q + 1) * c <= k) ++q;
+    o = (key < kb ? 0 : nb) + q;
+    *local = k - q * c;
+    return o;
+  }
 };
 
 struct PartArgs {
-  int N, W, G, cells_per;
+  int N, W, G;
+  OwnerMap om;
   int64_t n;
   const float* x;    // first coordinate (row)
   const float* x1;   // second coordinate (row), taken times s1 (the additive model's
@@ -113,15 +147,23 @@ struct PartArgs {
   float* ybuf;      // strengths of 8-byte records with a strength, same indices
   unsigned* flags;
   float c_hi, c_lo;
-  // one-pass partition: owner o's bucket is rec[o cap, (o + 1) cap), filled through
-  // atomic reservations on fill[o]; ovf is set when a bucket would overflow, and the
-  // exact kernels (count, scan, scatter) then run instead (guarded = 1: they return at
-  // once when ovf is clear)
+  // one-pass partition: owner o's bucket is rec[bucket_base(o), + bucket_cap(o)) (cap
+  // for the big owners, cap_s for the others), filled through atomic reservations on
+  // fill[o]; ovf is set when a bucket would overflow, and the exact kernels (count,
+  // scan, scatter) then run instead (guarded = 1: they return at once when ovf is clear)
   int* fill;
-  int cap;
+  int cap, cap_s;
   unsigned* ovf;
   int guarded;
 };
+
+__host__ __device__ __forceinline__ int64_t bucket_base(const OwnerMap& om, int cap, int cap_s, int o) {
+  return o < om.nb ? static_cast<int64_t>(o) * cap
+                   : static_cast<int64_t>(om.nb) * cap + static_cast<int64_t>(o - om.nb) * cap_s;
+}
+__host__ __device__ __forceinline__ int bucket_cap(const OwnerMap& om, int cap, int cap_s, int o) {
+  return o < om.nb ? cap : cap_s;
+}
 
 __device__ __forceinline__ bool skip_guarded(const PartArgs& A) {
   return A.guarded && *reinterpret_cast<const volatile unsigned*>(A.ovf) == 0u;
@@ -170,17 +212,16 @@ __device__ __forceinline__ uint2 pack_rec8(const uint4& r, float half_w) {
   return make_uint2(v0 | (v1 << 24), (v1 >> 8) | ((r.x & 0xFFFFu) << 16));
 }
 
-__device__ __forceinline__ bool point_key(float x0, float x1, const PartArgs& A, float inv_cpc, float* f0, float* f1,
+__device__ __forceinline__ bool point_key(float x0, float x1, const PartArgs& A, float* f0, float* f1,
                                           uint32_t* packed) {
   int la, lb;
   if (!window_f32(x0, A.N, A.c_hi, A.c_lo, A.W, &la, f0)) return false;
   if (!window_f32(A.s1 * x1, A.N, A.c_hi, A.c_lo, A.W, &lb, f1)) return false;
   const int N = A.N;
   const int key = wrap_node(la, N) * N + wrap_node(lb, N);
-  int o = __float2int_rd(static_cast<float>(key) * inv_cpc);
-  if (o * A.cells_per > key) --o;
-  else if ((o + 1) * A.cells_per <= key) ++o;
-  *packed = (static_cast<uint32_t>(o) << 16) | static_cast<uint32_t>(key - o * A.cells_per);
+  int local;
+  const int o = A.om.owner(key, &local);
+  *packed = (static_cast<uint32_t>(o) << 16) | static_cast<uint32_t>(local);
   return true;
 }
 
@@ -189,7 +230,6 @@ __global__ void __launch_bounds__(P_THREADS) k_bin_count(PartArgs A) {
   extern __shared__ int whist[];  // [P_NWARPS][G]
   const int tid = threadIdx.x, warp = tid >> 5;
   const int G = A.G;
-  const float inv_cpc = 1.0f / static_cast<float>(A.cells_per);
   for (int o = tid; o < P_NWARPS * G; o += P_THREADS) whist[o] = 0;
   __syncthreads();
   const int64_t s = static_cast<int64_t>(blockIdx.x) * A.range;
@@ -198,7 +238,7 @@ __global__ void __launch_bounds__(P_THREADS) k_bin_count(PartArgs A) {
   auto one = [&](float a0, float a1) {
     float f0, f1;
     uint32_t k;
-    if (point_key(a0, a1, A, inv_cpc, &f0, &f1, &k)) atomicAdd(&wh[k >> 16], 1);
+    if (point_key(a0, a1, A, &f0, &f1, &k)) atomicAdd(&wh[k >> 16], 1);
     else atomicOr(A.flags, FLAG_RANGE);
   };
   if (A.vec_ok) {
@@ -295,7 +335,6 @@ __global__ void __launch_bounds__(S_THREADS, 1) k_bin_scatter(PartArgs A) {
   int* tcnt = cursor + (G + 1);                                            // [G + 1] tile counts -> offsets
   int* tcur = tcnt + (G + 1);                                              // [G] fill cursors inside the tile
   const int tid = threadIdx.x;
-  const float inv_cpc = 1.0f / static_cast<float>(A.cells_per);
   owner_bases(A.tot, G, cursor, wsum);
   for (int o = tid; o < G; o += S_THREADS) cursor[o] += A.off[static_cast<size_t>(blockIdx.x) * G + o];
   const int64_t s0 = static_cast<int64_t>(blockIdx.x) * A.range;
@@ -309,7 +348,7 @@ __global__ void __launch_bounds__(S_THREADS, 1) k_bin_scatter(PartArgs A) {
       float f0, f1;
       uint32_t k;
       unsigned short o = 0xFFFF;
-      if (point_key(a0, a1, A, inv_cpc, &f0, &f1, &k)) {
+      if (point_key(a0, a1, A, &f0, &f1, &k)) {
         o = static_cast<unsigned short>(k >> 16);
         atomicAdd(&tcnt[o], 1);
       }
@@ -356,7 +395,7 @@ __global__ void __launch_bounds__(S_THREADS, 1) k_bin_scatter(PartArgs A) {
       if (o == 0xFFFF) continue;
       float f0, f1;
       uint32_t k;
-      point_key(__ldg(A.x + t0 + i), __ldg(A.x1 + t0 + i), A, inv_cpc, &f0, &f1, &k);
+      point_key(__ldg(A.x + t0 + i), __ldg(A.x1 + t0 + i), A, &f0, &f1, &k);
       const int pos = atomicAdd(&tcur[o], 1);
       sorted[pos] = make_uint4(k, __float_as_uint(f0), __float_as_uint(f1),
                                A.has_y ? __float_as_uint(__ldg(A.y + t0 + i)) : 0u);
@@ -415,7 +454,6 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter2(PartArgs A) {
   int* tcur = tcnt + (G + 1);                            // [G + 1]
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
   const int tid = threadIdx.x;
-  const float inv_cpc = 1.0f / static_cast<float>(A.cells_per);
   owner_bases(A.tot, G, cursor, wsum);
   for (int o = tid; o < G; o += S2_THREADS) cursor[o] += A.off[static_cast<size_t>(blockIdx.x) * G + o];
   const int64_t s0 = static_cast<int64_t>(blockIdx.x) * A.range;
@@ -450,7 +488,7 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter2(PartArgs A) {
       if (i < cnt) {
         float f0, f1;
         uint32_t key;
-        if (point_key(stage[i], stage[S2_TILE + i], A, inv_cpc, &f0, &f1, &key)) {
+        if (point_key(stage[i], stage[S2_TILE + i], A, &f0, &f1, &key)) {
           rec[k] = make_uint4(key, __float_as_uint(f0), __float_as_uint(f1),
                               A.has_y ? __float_as_uint(stage[2 * S2_TILE + i]) : 0u);
           atomicAdd(&tcnt[key >> 16], 1);
@@ -521,7 +559,6 @@ __global__ void __launch_bounds__(T, 1024 / T) k_bin_scatter1(PartArgs A) {
   long long* gdelta = reinterpret_cast<long long*>(toff + (G + 1));
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
   const int tid = threadIdx.x;
-  const float inv_cpc = 1.0f / static_cast<float>(A.cells_per);
   const int64_t s0 = static_cast<int64_t>(blockIdx.x) * A.range;
   const int64_t e0 = min(A.n, s0 + A.range);
   if (tid == 0) {
@@ -558,7 +595,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_bin_scatter1(PartArgs A) {
       if (i < cnt) {
         float f0, f1;
         uint32_t key;
-        if (point_key(stage[i], stage[TILE + i], A, inv_cpc, &f0, &f1, &key)) {
+        if (point_key(stage[i], stage[TILE + i], A, &f0, &f1, &key)) {
           rec[k] = make_uint4(key, __float_as_uint(f0), __float_as_uint(f1),
                               A.has_y ? __float_as_uint(stage[2 * TILE + i]) : 0u);
           rk[k] = atomicAdd(&tcnt[key >> 16], 1);
@@ -602,11 +639,11 @@ __global__ void __launch_bounds__(T, 1024 / T) k_bin_scatter1(PartArgs A) {
     for (int k = 0; k < PER; ++k)
       if (rec[k].x != 0xFFFFFFFFu) sorted[toff[rec[k].x >> 16] + rk[k]] = rec[k];
     if (tid < G) {
-      if (my_c > 0 && my_pos + my_c > A.cap) {
+      if (my_c > 0 && my_pos + my_c > bucket_cap(A.om, A.cap, A.cap_s, tid)) {
         atomicOr(A.ovf, 1u);
         my_pos = -1;
       }
-      gdelta[tid] = my_pos >= 0 ? static_cast<long long>(tid) * A.cap + my_pos - toff[tid] : NO_ROOM;
+      gdelta[tid] = my_pos >= 0 ? bucket_base(A.om, A.cap, A.cap_s, tid) + my_pos - toff[tid] : NO_ROOM;
     }
     __syncthreads();
     const int valid = toff[G];
@@ -633,7 +670,9 @@ __global__ void __launch_bounds__(T, 1024 / T) k_bin_scatter1(PartArgs A) {
 }
 
 struct AccArgs {
-  int N, G, cells_per, ncells;
+  int N, G, ncells;
+  OwnerMap om;
+  int cpc_max;  // cells of the largest owner (the shared-memory layout's size)
   float beta;
   EsPoly poly;  // tap polynomials of the plan's width
   int with_ones;
@@ -646,7 +685,7 @@ struct AccArgs {
   // skipped when ovf is set; 2: exact buckets, run only when ovf is set
   int mode;
   const int* fill;
-  int cap;
+  int cap, cap_s;
   const unsigned* ovf;
   float qmul;  // per-round quota = mean load + qmul sqrt(mean load)
 };
@@ -682,12 +721,12 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
   const int tid = threadIdx.x, lane = tid & 31;
   const int b = blockIdx.x;
   const int N = A.N;
-  const int cpc = A.cells_per;
+  const int cpc = A.cpc_max;
   const int cell = PAIR ? (tid >> 1) : tid;
   const int ch = PAIR ? (tid & 1) : 0;
   const unsigned pmask = 3u << (lane & 30);
-  const int my_first_cell = b * cpc;
-  const int my_ncells = max(0, min(cpc, A.ncells - my_first_cell));
+  const int my_first_cell = A.om.first(b);
+  const int my_ncells = max(0, min(A.om.cells(b), A.ncells - my_first_cell));
   const bool owns = cell < my_ncells;
   const float gc = 0.5f * static_cast<float>(W - 1);  // window centre: g = f - gc
   const AccLayout L = acc_layout<R>(cpc);
@@ -704,8 +743,8 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
   }
   if (A.mode == 1) {
     if (tid == 0) {
-      s_base = b * A.cap;
-      s_count = min(__ldg(A.fill + b), A.cap);
+      s_base = static_cast<int>(bucket_base(A.om, A.cap, A.cap_s, b));
+      s_count = min(__ldg(A.fill + b), bucket_cap(A.om, A.cap, A.cap_s, b));
       s_ncar[0] = s_ncar[1] = 0;
       s_abort = 0;
       mbar_init(&s_bar[0]);
@@ -963,15 +1002,36 @@ int sm_count() {
   return sms;
 }
 
-// owners: enough that each holds at most `cells` cells (Cfg::CELLS by default), and at
-// least one per SM
-static int owner_count(int64_t ncells, bool pair, int sms, int cells = 0) {
+// Owners.  Pair mode by default, when the cells fill between one and two waves of
+// 16-warp owners: one wave (one per SM) of Cfg::CELLS cells, then owners of 3/4 of
+// that (12 warps), so that each wave keeps the four schedulers of an SM equally busy.
+// Otherwise (or with an explicit `cells`): uniform owners of at most `cells` cells
+// (Cfg::CELLS by default), at least one per SM.
+struct OwnerPlan {
+  OwnerMap om;
+  int G;
+};
+static OwnerPlan owner_plan(int64_t ncells, bool pair, int sms, int cells = 0) {
   const int cmax = pair ? Cfg<true>::CELLS : Cfg<false>::CELLS;
+  OwnerPlan P{};
+  if (cells <= 0 && pair && sms > 0) {
+    const int cb = cmax, cs = cmax * 3 / 4;
+    const int64_t kb = static_cast<int64_t>(sms) * cb;
+    if (ncells > kb && ncells <= kb + static_cast<int64_t>(sms) * cs) {
+      const int ns = static_cast<int>((ncells - kb + cs - 1) / cs);
+      P.om = OwnerMap{sms, cb, cs, 1.0f / static_cast<float>(cb), 1.0f / static_cast<float>(cs)};
+      P.G = sms + ns;
+      return P;
+    }
+  }
   if (cells <= 0 || cells > cmax) cells = cmax;
   int64_t G = (ncells + cells - 1) / cells;
   if (G < sms) G = sms;
   if (G > ncells) G = ncells;
-  return static_cast<int>(G);
+  const int cpc = static_cast<int>((ncells + G - 1) / G);
+  P.om = OwnerMap{static_cast<int>(G), cpc, cpc, 1.0f / static_cast<float>(cpc), 1.0f / static_cast<float>(cpc)};
+  P.G = static_cast<int>(G);
+  return P;
 }
 
 bool spread_binned_supported(const EsPlan& p, int n_y, bool with_ones) {
@@ -980,7 +1040,7 @@ bool spread_binned_supported(const EsPlan& p, int n_y, bool with_ones) {
   const int sms = sm_count();
   if (sms <= 0) return false;
   const int64_t ncells = static_cast<int64_t>(p.N) * p.N;
-  return owner_count(ncells, nch == 2, sms) <= MAX_G;
+  return owner_plan(ncells, nch == 2, sms).G <= MAX_G;
 }
 
 fk_status spread_binned(const EsPlan& p, int64_t n, const float* x, const float* y, int n_y, bool with_ones,
@@ -1012,9 +1072,10 @@ fk_status spread_binned_run(const EsPlan& p, int64_t n, const float* x, const fl
   const int nch = n_y + (with_ones ? 1 : 0);
   const bool pair = (nch == 2);
   const int64_t ncells = static_cast<int64_t>(p.N) * p.N;
-  const int G = owner_count(ncells, pair, sm_count(), cfg.cells);
+  const OwnerPlan op = owner_plan(ncells, pair, sm_count(), cfg.cells);
+  const int G = op.G;
   if (G > MAX_G) return set_error(FK_EINVAL, "binned spreading: %d owners exceed %d", G, MAX_G);
-  const int cpc = static_cast<int>((ncells + G - 1) / G);
+  const int cpc = op.om.cb;  // the largest owner
   const double c = p.N / (2.0 * M_PI);
 
   FK_CUDA(cudaMemsetAsync(grid, 0, sizeof(double) * ncells * nch, st));
@@ -1024,7 +1085,7 @@ fk_status spread_binned_run(const EsPlan& p, int64_t n, const float* x, const fl
   P.N = p.N;
   P.W = p.w;
   P.G = G;
-  P.cells_per = cpc;
+  P.om = op.om;
   P.n = n;
   P.x = x;
   P.x1 = x1;
@@ -1046,25 +1107,34 @@ fk_status spread_binned_run(const EsPlan& p, int64_t n, const float* x, const fl
   FK_TRY(scr.alloc(&P.cnt, static_cast<size_t>(P.nblk) * G));
   FK_TRY(scr.alloc(&P.off, static_cast<size_t>(P.nblk) * G));
   FK_TRY(scr.alloc(&P.tot, static_cast<size_t>(G)));
-  // one-pass bucket capacity: the mean load plus 2 % and 4096 records (a uniform
-  // sample's counts are within a few standard deviations, sqrt(n / G), of the mean)
+  // one-pass bucket capacity: an owner's mean load (points x its share of the cells)
+  // plus 2 % and 4096 records (a uniform sample's counts are within a few standard
+  // deviations, sqrt(load), of the mean)
   const int64_t exact_len = n + static_cast<int64_t>(P.nblk) * G * 7;  // + run padding
-  const int64_t cap = ((n / G) + (n / G) / 50 + 4096 + 7) & ~static_cast<int64_t>(7);
-  const bool one_pass = P.vec_ok && cap * G < (static_cast<int64_t>(1) << 31);
-  FK_TRY(scr.alloc(&P.rec, static_cast<size_t>(one_pass ? std::max<int64_t>(exact_len, cap * G) : exact_len)));
+  auto cap_for = [&](int cells) {
+    const int64_t load = static_cast<int64_t>(static_cast<double>(n) * cells / static_cast<double>(ncells)) + 1;
+    return (load + load / 50 + 4096 + 7) & ~static_cast<int64_t>(7);
+  };
+  const int64_t cap = cap_for(op.om.cb), cap_s = cap_for(op.om.cs);
+  const int64_t rec_total =
+      op.om.nb < G ? op.om.nb * cap + static_cast<int64_t>(G - op.om.nb) * cap_s : static_cast<int64_t>(G) * cap;
+  const bool one_pass = P.vec_ok && rec_total < (static_cast<int64_t>(1) << 31);
+  FK_TRY(scr.alloc(&P.rec, static_cast<size_t>(one_pass ? std::max<int64_t>(exact_len, rec_total) : exact_len)));
   unsigned* ovf = nullptr;
   if (one_pass) {
     FK_TRY(scr.alloc(&P.fill, static_cast<size_t>(G) + 1));
     ovf = reinterpret_cast<unsigned*>(P.fill + G);
     FK_CUDA(cudaMemsetAsync(P.fill, 0, sizeof(int) * (G + 1), st));
     P.cap = static_cast<int>(cap);
+    P.cap_s = static_cast<int>(cap_s);
     P.ovf = ovf;
   }
 
   AccArgs A{};
   A.N = p.N;
   A.G = G;
-  A.cells_per = cpc;
+  A.om = op.om;
+  A.cpc_max = cpc;
   A.ncells = static_cast<int>(ncells);
   A.beta = static_cast<float>(p.beta);
   A.poly = es_poly(p.w, p.beta);
@@ -1075,6 +1145,7 @@ fk_status spread_binned_run(const EsPlan& p, int64_t n, const float* x, const fl
   A.flags = flags;
   A.fill = P.fill;
   A.cap = P.cap;
+  A.cap_s = P.cap_s;
   A.ovf = ovf;
   A.qmul = cfg.qmul;
   // exact-partition (and strength-carrying) records: Rec16; the one-pass partition of
@@ -1096,7 +1167,7 @@ fk_status spread_binned_run(const EsPlan& p, int64_t n, const float* x, const fl
     FK_CUDA(cudaFuncSetAttribute(fn1, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm_1)));
     if (spl) {
       // + 4: a round's bulk copy rounds its byte count up to 16 (reads <= 3 floats past)
-      FK_TRY(scr.alloc(&P.ybuf, static_cast<size_t>(P.cap) * G + 4));
+      FK_TRY(scr.alloc(&P.ybuf, static_cast<size_t>(rec_total) + 4));
       A.ybuf = P.ybuf;
     }
   }
