@@ -101,32 +101,24 @@ struct Cfg {
 // then 12 in pair mode), so that no scheduler of an SM carries more warps than another.
 struct OwnerMap {
   int nb, cb, cs;
-  float inv_cb, inv_cs;
+  // ceil(2^32 / cells): k / cells = (k m) >> 32 exactly for k < 2^18 and cells <= 2^9
+  // (the error k (m - 2^32 / cells) / 2^32 < 2^-14 stays below the gap 1 / cells)
+  unsigned long long mb, ms;
   __host__ __device__ int first(int o) const { return o < nb ? o * cb : nb * cb + (o - nb) * cs; }
   __host__ __device__ int cells(int o) const { return o < nb ? cb : cs; }
   // owner of cell `key` and the cell's index inside it
   __device__ __forceinline__ int owner(int key, int* local) const {
     const int kb = nb * cb;
-    int o, base, c;
-    float inv;
-    if (key < kb) {
-      base = 0;
-      c = cb;
-      inv = inv_cb;
-    } else {
-      base = kb;
-      c = cs;
-      inv = inv_cs;
-    }
-    const int k = key - base;
-    int q = __float2int_rd(static_cast<float>(k) * inv);
-    if (q * c > k) --q;
-    else if ((q + 1) * c <= k) ++q;
-    o = (key < kb ? 0 : nb) + q;
-    *local = k - q * c;
-    return o;
+    const bool big = key < kb;
+    const unsigned k = static_cast<unsigned>(big ? key : key - kb);
+    const int q = static_cast<int>((static_cast<unsigned long long>(k) * (big ? mb : ms)) >> 32);
+    *local = static_cast<int>(k) - q * (big ? cb : cs);
+    return (big ? 0 : nb) + q;
   }
 };
+__host__ inline unsigned long long owner_magic(int cells) {
+  return ((1ull << 32) + static_cast<unsigned long long>(cells) - 1) / static_cast<unsigned long long>(cells);
+}
 
 struct PartArgs {
   int N, W, G;
@@ -1019,7 +1011,7 @@ static OwnerPlan owner_plan(int64_t ncells, bool pair, int sms, int cells = 0) {
     const int64_t kb = static_cast<int64_t>(sms) * cb;
     if (ncells > kb && ncells <= kb + static_cast<int64_t>(sms) * cs) {
       const int ns = static_cast<int>((ncells - kb + cs - 1) / cs);
-      P.om = OwnerMap{sms, cb, cs, 1.0f / static_cast<float>(cb), 1.0f / static_cast<float>(cs)};
+      P.om = OwnerMap{sms, cb, cs, owner_magic(cb), owner_magic(cs)};
       P.G = sms + ns;
       return P;
     }
@@ -1029,7 +1021,7 @@ static OwnerPlan owner_plan(int64_t ncells, bool pair, int sms, int cells = 0) {
   if (G < sms) G = sms;
   if (G > ncells) G = ncells;
   const int cpc = static_cast<int>((ncells + G - 1) / G);
-  P.om = OwnerMap{static_cast<int>(G), cpc, cpc, 1.0f / static_cast<float>(cpc), 1.0f / static_cast<float>(cpc)};
+  P.om = OwnerMap{static_cast<int>(G), cpc, cpc, owner_magic(cpc), owner_magic(cpc)};
   P.G = static_cast<int>(G);
   return P;
 }
@@ -1040,7 +1032,8 @@ bool spread_binned_supported(const EsPlan& p, int n_y, bool with_ones) {
   const int sms = sm_count();
   if (sms <= 0) return false;
   const int64_t ncells = static_cast<int64_t>(p.N) * p.N;
-  return owner_plan(ncells, nch == 2, sms).G <= MAX_G;
+  // the owner division (OwnerMap) is exact for cell indices below 2^18
+  return ncells <= (1 << 18) && owner_plan(ncells, nch == 2, sms).G <= MAX_G;
 }
 
 fk_status spread_binned(const EsPlan& p, int64_t n, const float* x, const float* y, int n_y, bool with_ones,
