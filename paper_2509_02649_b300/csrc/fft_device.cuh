@@ -17,44 +17,72 @@ __device__ __forceinline__ cplx<R> tw_get(const double* tw, int idx, int sign) {
   return r;
 }
 
-// In-place radix-2 DIT over s[0..N) (already in bit-reversed order).  The first two
-// stages have the twiddles 1 and e^{sign i pi/2} = sign i: no multiplications.
+template <typename R>
+__device__ __forceinline__ cplx<R> cmul_tw(const cplx<R>& w, const cplx<R>& v) {
+  cplx<R> r;
+  r.x = v.x * w.x - v.y * w.y;
+  r.y = v.x * w.y + v.y * w.x;
+  return r;
+}
+
+// In-place decimation-in-time FFT over s[0..N) (already in bit-reversed order), radix
+// 4 with one radix-2 stage last when log2 N is odd.  With bit-reversed input, the
+// four consecutive size-q blocks that a radix-4 stage combines hold the DFTs of the
+// subsequences of index residue 0, 2, 1, 3 (mod 4) of the size-4q subsequence being
+// formed; output m of the size-4q DFT at k + m q is
+//   sum_r (sign i)^(r m) w^(r k) D_r[k],  w = e^{sign 2 pi i / (4q)}.
+// The first stage (q = 1) has the twiddles 1: no multiplications.
 template <typename R>
 __device__ void fft_smem(cplx<R>* s, int N, int sign, const double* tw) {
+  // (x + i y) times sign i
+  auto rot = [sign](const cplx<R>& v) {
+    cplx<R> r;
+    r.x = sign < 0 ? v.y : -v.y;
+    r.y = sign < 0 ? -v.x : v.x;
+    return r;
+  };
+  int q = 1;
   if (N >= 4) {
-    // stages len = 2 and 4 together: each thread a group of four
     for (int g = threadIdx.x; g < (N >> 2); g += blockDim.x) {
-      cplx<R>* q = s + 4 * g;
-      const cplx<R> a0 = q[0], a1 = q[1], a2 = q[2], a3 = q[3];
+      cplx<R>* p = s + 4 * g;
+      const cplx<R> a0 = p[0], a1 = p[1], a2 = p[2], a3 = p[3];
       const cplx<R> b0{a0.x + a1.x, a0.y + a1.y}, b1{a0.x - a1.x, a0.y - a1.y};
-      const cplx<R> b2{a2.x + a3.x, a2.y + a3.y}, b3{a2.x - a3.x, a2.y - a3.y};
-      // b3 times sign i
-      const cplx<R> t3{sign < 0 ? b3.y : -b3.y, sign < 0 ? -b3.x : b3.x};
-      q[0] = cplx<R>{b0.x + b2.x, b0.y + b2.y};
-      q[2] = cplx<R>{b0.x - b2.x, b0.y - b2.y};
-      q[1] = cplx<R>{b1.x + t3.x, b1.y + t3.y};
-      q[3] = cplx<R>{b1.x - t3.x, b1.y - t3.y};
+      const cplx<R> b2{a2.x + a3.x, a2.y + a3.y};
+      const cplx<R> t3 = rot(cplx<R>{a2.x - a3.x, a2.y - a3.y});
+      p[0] = cplx<R>{b0.x + b2.x, b0.y + b2.y};
+      p[2] = cplx<R>{b0.x - b2.x, b0.y - b2.y};
+      p[1] = cplx<R>{b1.x + t3.x, b1.y + t3.y};
+      p[3] = cplx<R>{b1.x - t3.x, b1.y - t3.y};
+    }
+    __syncthreads();
+    q = 4;
+  }
+  for (; 4 * q <= N; q *= 4) {
+    const int tstep = N / (4 * q);
+    for (int b = threadIdx.x; b < (N >> 2); b += blockDim.x) {
+      const int grp = b / q;
+      const int k = b - grp * q;
+      cplx<R>* p = s + grp * 4 * q + k;
+      const cplx<R> t0 = p[0];
+      const cplx<R> t2 = cmul_tw(tw_get<R>(tw, 2 * k * tstep, sign), p[q]);      // residue 2
+      const cplx<R> t1 = cmul_tw(tw_get<R>(tw, k * tstep, sign), p[2 * q]);      // residue 1
+      const cplx<R> t3 = cmul_tw(tw_get<R>(tw, 3 * k * tstep, sign), p[3 * q]);  // residue 3
+      const cplx<R> a{t0.x + t2.x, t0.y + t2.y}, bb{t0.x - t2.x, t0.y - t2.y};
+      const cplx<R> c{t1.x + t3.x, t1.y + t3.y};
+      const cplx<R> d = rot(cplx<R>{t1.x - t3.x, t1.y - t3.y});
+      p[0] = cplx<R>{a.x + c.x, a.y + c.y};
+      p[q] = cplx<R>{bb.x + d.x, bb.y + d.y};
+      p[2 * q] = cplx<R>{a.x - c.x, a.y - c.y};
+      p[3 * q] = cplx<R>{bb.x - d.x, bb.y - d.y};
     }
     __syncthreads();
   }
-  for (int len = (N >= 4 ? 8 : 2); len <= N; len <<= 1) {
-    const int half = len >> 1;
-    const int tstep = N / len;
-    for (int b = threadIdx.x; b < (N >> 1); b += blockDim.x) {
-      const int grp = b / half;
-      const int k = b - grp * half;
-      const int i0 = grp * len + k;
-      const int i1 = i0 + half;
-      const cplx<R> w = tw_get<R>(tw, k * tstep, sign);
-      const cplx<R> a = s[i0];
-      const cplx<R> v = s[i1];
-      cplx<R> bw;
-      bw.x = v.x * w.x - v.y * w.y;
-      bw.y = v.x * w.y + v.y * w.x;
-      s[i0].x = a.x + bw.x;
-      s[i0].y = a.y + bw.y;
-      s[i1].x = a.x - bw.x;
-      s[i1].y = a.y - bw.y;
+  if (q < N) {  // 2 q == N: the even- and odd-index halves
+    for (int k = threadIdx.x; k < q; k += blockDim.x) {
+      const cplx<R> a = s[k];
+      const cplx<R> v = cmul_tw(tw_get<R>(tw, k, sign), s[k + q]);
+      s[k] = cplx<R>{a.x + v.x, a.y + v.y};
+      s[k + q] = cplx<R>{a.x - v.x, a.y - v.y};
     }
     __syncthreads();
   }

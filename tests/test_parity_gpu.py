@@ -277,6 +277,28 @@ def test_binned_and_atomic_spreaders_agree_config2_grid():
         assert abs(Tg[(j0 + 2 * m) * K + (j1 + 2 * m)] - want) < 1e-6
 
 
+def test_binned_clustered_points_two_owner_sizes():
+    # the workload's grid (N = 256: owners of 256 cells, then of 192) with crowded
+    # points, which overflow the one-pass buckets: the exact partition, with the same
+    # owner map, takes over on the device
+    m, eps, n = 32, 1e-6, 1_500_001
+    g = np.random.default_rng(97)
+    x = np.clip(g.normal(-0.8, 0.03, size=(2, n)), -np.pi, np.pi - 1e-6).astype(np.float32)
+    x[:, : n // 5] = S.uniform_points(n // 5, 2, 36).astype(np.float32)
+    y = np.sin(x[1].astype(np.float64)).astype(np.float32)
+    xd, yd = dev(x, torch.float32), dev(y, torch.float32)
+    Tb, bb = fk.fk_build_system(xd, yd, m, eps, "mixed", opts=fk.default_opts(spread=fk.FK_SPREAD_BINNED))
+    Ta, ba = fk.fk_build_system(xd, yd, m, eps, "mixed", opts=fk.default_opts(spread=fk.FK_SPREAD_ATOMIC))
+    assert rel(host(Tb), host(Ta)) < 1e-6
+    assert rel(host(bb), host(ba)) < 1e-6
+    K = 4 * m + 1
+    Tg = host(Tb)
+    x0, x1 = x[0].astype(np.float64), x[1].astype(np.float64)
+    for j0, j1 in [(0, 0), (3, -1), (-64, 64), (17, 40)]:
+        want = np.mean(np.exp(-1j * (j0 * x0 + j1 * x1)))
+        assert abs(Tg[(j0 + 2 * m) * K + (j1 + 2 * m)] - want) < 1e-6
+
+
 def test_binned_rejects_out_of_range_points():
     x = S.uniform_points(2000, 2, 32).astype(np.float32)
     x[1, 1234] = 20.0
