@@ -1459,17 +1459,21 @@ namespace fk {
 
 // ---------------------------------------------------------------- CG in one cooperative launch
 // The fused CG above costs five dependent launches per iteration (2-D) and a host
-// round trip every four; at the workloads' sizes (D = 65^2, Lc = 256) each launch does
+// round trip every four; at the workloads' sizes (D = 65^2, Lc = 128) each launch does
 // microseconds of work.  Here all iterations run in one cooperative launch whose CTAs
-// meet at a grid barrier between the phases of an iteration:
+// meet at a grid barrier between the three phases of an iteration:
 //   P1 rows:    p = z + beta p (p = z at the first iteration) for one row of modes,
-//               zero-padded to Lc and transformed along the row;
+//               zero-padded to Lc and transformed along the row; sum W |p|^2;
 //   P2 columns: transform along the column, times the circulant spectrum, inverse;
-//   P3 rows:    inverse transform, q = (.) / Lc^2 + W p, and <p, q>;
-//   P4 update:  x += alpha p, r -= alpha q, z = r / diag, <r, z> and |r|^2.
-// Scalars that an iteration reads and the next one accumulates are kept in two copies
-// selected by the iteration's parity, so every CTA sees the same values within an
-// iteration without an extra barrier.  After convergence one more matvec of x gives
+//               sum |p^|^2 c^ / Lc^2, the circulant's part of <p, A p> (Parseval);
+//   P3 rows:    inverse transform, q = (.) / Lc^2 + W p, and, since <p, A p> is
+//               complete, the row's update x += alpha p, r -= alpha q, z = r / diag
+//               with its parts of <r, z> and |r|^2.
+// <p, A p> from the spectrum instead of <p, q> after P3 saves a fourth phase and its
+// barrier; x and r stay consistent whatever rounding alpha carries (both take the same
+// alpha).  Scalars that an iteration reads and the next one accumulates are kept in two
+// copies selected by the iteration's parity, so every CTA sees the same values within
+// an iteration without an extra barrier.  After convergence one more matvec of x gives
 // the true residual |b - A x|.  The barrier's wait is bounded (FK_ETIMEOUT).
 namespace {
 
@@ -1490,7 +1494,7 @@ struct CgP {
   const double* tw;
   double *x, *r, *z, *p, *q;
   cplx<double>* buf;
-  double *rz, *rr, *pq, *bb, *rres;  // rz, rr: [2][nsys]
+  double *rz, *rr, *pq, *bb, *rres;  // rz, rr, pq: [2][nsys] by iteration parity
   GridBar* bar;
   unsigned* flags;
   int* info;  // [0] iterations, [1] systems not converged
@@ -1563,16 +1567,19 @@ __device__ __forceinline__ double block_sum_all(double v, double* red) {
   return t;  // valid in thread 0
 }
 
-// P1 (final: the rows of x instead of the new direction)
-__device__ void cgp_rows_fwd(const CgP& A, cplx<double>* sl, int it, bool final_pass) {
+// P1: p = z + beta p and the row's transform (final: the rows of x); the penalty's
+// part of <p, A p>, sum W |p|^2, goes into pq
+__device__ void cgp_rows_fwd(const CgP& A, cplx<double>* sl, double* red, int it, bool final_pass) {
   const int K = A.K, Lc = A.Lc;
   for (int item = blockIdx.x; item < A.nsys * K; item += gridDim.x) {
     const int s = item / K, row = item - s * K;
     if (!final_pass && !cg_active(A, it, s)) continue;
     const int64_t o = 2 * (s * A.D + static_cast<int64_t>(row) * K);
+    const double* Ws = A.W + static_cast<int64_t>(s / A.n_rhs) * A.D + static_cast<int64_t>(row) * K;
     double beta = 0.0;
     if (!final_pass && it > 0)
       beta = __ldcg(A.rz + (it & 1) * A.nsys + s) / __ldcg(A.rz + ((it + 1) & 1) * A.nsys + s);
+    double pw = 0.0;
     for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
       cplx<double> e;
       e.x = e.y = 0.0;
@@ -1589,15 +1596,19 @@ __device__ void cgp_rows_fwd(const CgP& A, cplx<double>* sl, int it, bool final_
           }
           A.p[o + 2 * i] = e.x;
           A.p[o + 2 * i + 1] = e.y;
+          pw += Ws[i] * (e.x * e.x + e.y * e.y);
         }
       }
       sl[bitrev(i, A.logLc)] = e;
+    }
+    if (!final_pass) {
+      const double t = block_sum_all(pw, red);
+      if (threadIdx.x == 0) atomicAdd(A.pq + (it & 1) * A.nsys + s, t);
     }
     __syncthreads();
     fft_smem<double>(sl, Lc, -1, A.tw);
     cplx<double>* ob = A.buf + (static_cast<int64_t>(s) * K + row) * Lc;
     for (int i = threadIdx.x; i < Lc; i += blockDim.x) ob[i] = sl[i];
-    if (!final_pass && row == 0 && threadIdx.x == 0) A.pq[s] = 0.0;
     __syncthreads();
     if (A.ch2) {
       // the same row times P, for the operator penalty (this thread's own writes of p)
@@ -1679,6 +1690,19 @@ __device__ void cgp_alias_task(const CgP& A, int t, int it, bool final_pass) {
     cplx<double>& c = A.corr[(static_cast<int64_t>(s) * 4 + kind) * K + e];
     c.x = sr;
     c.y = si;
+    if (!final_pass) {
+      // its part of <p, A p>: Re(conj(v_j) c_j) at the output mode j (v = P p for the
+      // operator's corrections, which rows_inv multiplies by mu conj(P_j))
+      const int64_t pj = col0 ? static_cast<int64_t>(e) * K : static_cast<int64_t>(e);
+      double vr = __ldcg(v + 2 * pj), vi = __ldcg(v + 2 * pj + 1);
+      if (kind >= 2) {
+        const double pr = A.P[2 * pj], pim = A.P[2 * pj + 1];
+        const double ur = pr * vr - pim * vi;
+        vi = pr * vi + pim * vr;
+        vr = ur;
+      }
+      atomicAdd(A.pq + (it & 1) * A.nsys + s, (kind >= 2 ? A.mu : 1.0) * (vr * sr + vi * si));
+    }
   }
 }
 
@@ -1702,7 +1726,7 @@ __device__ __forceinline__ cplx<double> cg_alias_corr(const CgP& A, int s, int r
 }
 
 // P2 (and the alias corrections, on the CTAs past the columns)
-__device__ void cgp_cols(const CgP& A, cplx<double>* sl, int it, bool final_pass) {
+__device__ void cgp_cols(const CgP& A, cplx<double>* sl, double* red, int it, bool final_pass) {
   const int K = A.K, Lc = A.Lc;
   const int nitems = A.nsys * Lc * (A.ch2 ? 2 : 1);
   const int ntot = nitems + (A.alias ? A.nsys * cg_alias_tasks(K, A.ch2 != nullptr) : 0);
@@ -1723,6 +1747,7 @@ __device__ void cgp_cols(const CgP& A, cplx<double>* sl, int it, bool final_pass
       const int cur = (it & 1) * A.nsys + s, nxt = ((it + 1) & 1) * A.nsys + s;
       A.rz[nxt] = act ? 0.0 : __ldcg(A.rz + cur);
       A.rr[nxt] = act ? 0.0 : __ldcg(A.rr + cur);
+      A.pq[nxt] = 0.0;
     }
     if (!final_pass && !cg_active(A, it, s)) continue;
     cplx<double>* bcol = base + static_cast<int64_t>(s) * K * Lc + c;
@@ -1738,12 +1763,21 @@ __device__ void cgp_cols(const CgP& A, cplx<double>* sl, int it, bool final_pass
     }
     __syncthreads();
     fft_smem<double>(sl, Lc, -1, A.tw);
+    // <u, C u> = sum |u^|^2 c^ / Lc^2 (Parseval) for this column's spectrum: the
+    // circulant product's part of <p, A p>
+    double pc = 0.0;
     for (int i = threadIdx.x; i < Lc; i += blockDim.x) {
       const cplx<double> a = spec[static_cast<int64_t>(i) * Lc + c], e = sl[i];
+      pc += a.x * (e.x * e.x + e.y * e.y);
       cplx<double> t;
       t.x = a.x * e.x - a.y * e.y;
       t.y = a.x * e.y + a.y * e.x;
       sl[i] = t;
+    }
+    if (!final_pass) {
+      const double t = block_sum_all(pc, red);
+      if (threadIdx.x == 0)
+        atomicAdd(A.pq + (it & 1) * A.nsys + s, (second ? A.mu : 1.0) * t / (static_cast<double>(Lc) * Lc));
     }
     __syncthreads();
     bitrev_permute<double>(sl, Lc, A.logLc);
@@ -1800,49 +1834,31 @@ __device__ void cgp_rows_inv(const CgP& A, cplx<double>* sl, double* red, int it
         A.q[o + 2 * i + 1] += A.mu * (pr * ti + pim * tr);
       }
     }
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < K; i += blockDim.x) {
-      const double vr = __ldcg(v + o + 2 * i), vi = __ldcg(v + o + 2 * i + 1);
-      acc += vr * A.q[o + 2 * i] + vi * A.q[o + 2 * i + 1];
-    }
-    if (!final_pass) {
-      const double t = block_sum_all(acc, red);
-      if (threadIdx.x == 0) atomicAdd(A.pq + s, t);
-    }
-    __syncthreads();
-  }
-}
-
-// P4 (final: |b - q|^2 into rres)
-__device__ void cgp_update(const CgP& A, double* red, int it, bool final_pass) {
-  const int64_t D = A.D;
-  const int chunk = blockDim.x;  // one entry per thread: the phase spreads over D / 256 CTAs
-  const int nch = static_cast<int>((D + chunk - 1) / chunk);
-  for (int item = blockIdx.x; item < A.nsys * nch; item += gridDim.x) {
-    const int s = item / nch, cb = item - s * nch;
-    if (!final_pass && !cg_active(A, it, s)) continue;
-    const double* idg = A.idg + static_cast<int64_t>(s / A.n_rhs) * D;
-    const double* bs = A.b + 2 * static_cast<int64_t>(s % A.n_rhs) * D;
+    // this row's update (the same threads wrote its q above): alpha = rho / <p, A p>,
+    // <p, A p> complete since the column phase; x += alpha p, r -= alpha q,
+    // z = r / diag, and the row's parts of <r, z> and |r|^2 for the next iteration
+    // (final pass: |b - A x|^2)
+    const int cur = (it & 1) * A.nsys + s, nxt = ((it + 1) & 1) * A.nsys + s;
+    const double alpha = final_pass ? 0.0 : __ldcg(A.rz + cur) / __ldcg(A.pq + cur);
+    const double* idg = A.idg + static_cast<int64_t>(s / A.n_rhs) * A.D + static_cast<int64_t>(row) * K;
+    const double* bs = A.b + 2 * (static_cast<int64_t>(s % A.n_rhs) * A.D + static_cast<int64_t>(row) * K);
     double a1 = 0.0, a2 = 0.0;
-    const double alpha = final_pass ? 0.0 : __ldcg(A.rz + (it & 1) * A.nsys + s) / __ldcg(A.pq + s);
-    for (int64_t k = static_cast<int64_t>(cb) * chunk + threadIdx.x; k < min(D, static_cast<int64_t>(cb + 1) * chunk);
-         k += blockDim.x) {
-      const int64_t o = 2 * (s * D + k);
-      const double q0 = __ldcg(A.q + o), q1 = __ldcg(A.q + o + 1);
+    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+      const double q0 = A.q[o + 2 * i], q1 = A.q[o + 2 * i + 1];
       if (final_pass) {
-        const double e0 = bs[2 * k] - q0, e1 = bs[2 * k + 1] - q1;
+        const double e0 = bs[2 * i] - q0, e1 = bs[2 * i + 1] - q1;
         a1 += e0 * e0 + e1 * e1;
         continue;
       }
-      const double p0 = __ldcg(A.p + o), p1 = __ldcg(A.p + o + 1);
-      A.x[o] = __ldcg(A.x + o) + alpha * p0;
-      A.x[o + 1] = __ldcg(A.x + o + 1) + alpha * p1;
-      const double r0 = __ldcg(A.r + o) - alpha * q0, r1 = __ldcg(A.r + o + 1) - alpha * q1;
-      A.r[o] = r0;
-      A.r[o + 1] = r1;
-      const double id = __ldcg(idg + k);
-      A.z[o] = r0 * id;
-      A.z[o + 1] = r1 * id;
+      const double p0 = __ldcg(A.p + o + 2 * i), p1 = __ldcg(A.p + o + 2 * i + 1);
+      A.x[o + 2 * i] = __ldcg(A.x + o + 2 * i) + alpha * p0;
+      A.x[o + 2 * i + 1] = __ldcg(A.x + o + 2 * i + 1) + alpha * p1;
+      const double r0 = __ldcg(A.r + o + 2 * i) - alpha * q0, r1 = __ldcg(A.r + o + 2 * i + 1) - alpha * q1;
+      A.r[o + 2 * i] = r0;
+      A.r[o + 2 * i + 1] = r1;
+      const double id = __ldcg(idg + i);
+      A.z[o + 2 * i] = r0 * id;
+      A.z[o + 2 * i + 1] = r1 * id;
       a1 += (r0 * r0 + r1 * r1) * id;
       a2 += r0 * r0 + r1 * r1;
     }
@@ -1852,10 +1868,11 @@ __device__ void cgp_update(const CgP& A, double* red, int it, bool final_pass) {
       if (final_pass) {
         atomicAdd(A.rres + s, t1);
       } else {
-        atomicAdd(A.rz + ((it + 1) & 1) * A.nsys + s, t1);
-        atomicAdd(A.rr + ((it + 1) & 1) * A.nsys + s, t2);
+        atomicAdd(A.rz + nxt, t1);
+        atomicAdd(A.rr + nxt, t2);
       }
     }
+    __syncthreads();
   }
 }
 
@@ -1907,13 +1924,11 @@ __global__ void __launch_bounds__(256) k_cg_persist2d(CgP A) {
     bool any = false;
     for (int s = 0; s < A.nsys && !any; ++s) any = cg_active(A, it, s);
     if (!any) break;
-    cgp_rows_fwd(A, sl, it, false);
+    cgp_rows_fwd(A, sl, red, it, false);
     if (!grid_sync(A.bar, A.flags)) return;
-    cgp_cols(A, sl, it, false);
+    cgp_cols(A, sl, red, it, false);
     if (!grid_sync(A.bar, A.flags)) return;
     cgp_rows_inv(A, sl, red, it, false);
-    if (!grid_sync(A.bar, A.flags)) return;
-    cgp_update(A, red, it, false);
     if (!grid_sync(A.bar, A.flags)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1925,13 +1940,11 @@ __global__ void __launch_bounds__(256) k_cg_persist2d(CgP A) {
   }
   if (!A.final_residual) return;
   // true residual of the result
-  cgp_rows_fwd(A, sl, it, true);
+  cgp_rows_fwd(A, sl, red, it, true);
   if (!grid_sync(A.bar, A.flags)) return;
-  cgp_cols(A, sl, it, true);
+  cgp_cols(A, sl, red, it, true);
   if (!grid_sync(A.bar, A.flags)) return;
   cgp_rows_inv(A, sl, red, it, true);
-  if (!grid_sync(A.bar, A.flags)) return;
-  cgp_update(A, red, it, true);
 }
 
 }  // namespace
@@ -2032,18 +2045,18 @@ fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, 
   FK_TRY(scr.alloc(&A.p, 2 * D * nsys));
   FK_TRY(scr.alloc(&A.q, 2 * D * nsys));
   FK_TRY(scr.alloc(&A.buf, static_cast<size_t>(nsys) * K * Lc));
-  // scalars [rz 2n | rr 2n | pq n | bb n | rres n | info], then the barrier: one memset,
+  // scalars [rz 2n | rr 2n | pq 2n | bb n | rres n | info], then the barrier: one memset,
   // and bb, rres and info come back in one copy
   double* scal;
-  FK_TRY(scr.alloc(&scal, 7 * static_cast<size_t>(nsys) + 1 + 8));
-  FK_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * (7 * nsys + 1 + 8), st));
+  FK_TRY(scr.alloc(&scal, 8 * static_cast<size_t>(nsys) + 1 + 8));
+  FK_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * (8 * nsys + 1 + 8), st));
   A.rz = scal;
   A.rr = scal + 2 * nsys;
   A.pq = scal + 4 * nsys;
-  A.bb = scal + 5 * nsys;
-  A.rres = scal + 6 * nsys;
-  A.info = reinterpret_cast<int*>(scal + 7 * nsys);
-  A.bar = reinterpret_cast<GridBar*>(scal + 7 * nsys + 1);
+  A.bb = scal + 6 * nsys;
+  A.rres = scal + 7 * nsys;
+  A.info = reinterpret_cast<int*>(scal + 8 * nsys);
+  A.bar = reinterpret_cast<GridBar*>(scal + 8 * nsys + 1);
   A.flags = flags;
   void* args[] = {&A};
   FK_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_cg_persist2d), dim3(nb), dim3(threads), args, smem,
