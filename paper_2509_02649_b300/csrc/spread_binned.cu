@@ -192,10 +192,10 @@ struct Rec8 {
   __device__ static float y(const uint2&) { return 1.0f; }
 };
 // Rec8 records with the strengths in a parallel stream of floats (same indices):
-// 12 bytes per point, 6656 records per round
+// 12 bytes per point, 8192 records per round (and up to 512 deferred ones in front)
 struct Rec8Y : Rec8 {
   static constexpr bool HAS_Y = true, SPLIT_Y = true;
-  static constexpr int CAPR = 6656, CARRY = 1536;
+  static constexpr int CAPR = 8192, CARRY = 512;
 };
 // Rec8 of a Rec16 {key, f0, f1, -} built by the partition (w: kernel width)
 __device__ __forceinline__ uint2 pack_rec8(const uint4& r, float half_w) {
