@@ -30,7 +30,7 @@ WL = dict(workload="2d-sobolev", d=2, n=100_000_000, m=32, s=2.0, lam=1e-6, eps=
 METRIC = "fit points/s (NUFFT Gram+RHS+solve)"
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
-ACC_DRAM_BYTES_PER_POINT = (241.207808e6 + 5.877248e6) / 2e7  # k_bin_accumulate, 2-D, w = 7
+ACC_DRAM_BYTES_PER_POINT = (241.207040e6 + 6.003200e6) / 2e7  # k_bin_accumulate, 2-D, w = 7
 
 
 def parse():
@@ -506,7 +506,7 @@ def main():
     peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = f_pt * n / (ms_kernel / 1e3) / 1e12
     # DRAM bytes of one k_bin_accumulate launch: ncu capture of this kernel at n = 2e7
-    # (dram__bytes_read.sum 241.2 MB + dram__bytes_write.sum 5.9 MB), scaled by points
+    # (dram__bytes_read.sum 241.2 MB + dram__bytes_write.sum 6.0 MB), scaled by points
     # (the reads are the 8-byte partition records and the strengths, the writes the flush)
     traffic = ACC_DRAM_BYTES_PER_POINT * n if (d == 2 and w == 7) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",

@@ -1240,7 +1240,7 @@ fk_status spread_binned_xy(const EsPlan& p, int64_t n, const float* x, const flo
   if (waves_cells < cmax) cells_opts.push_back(waves_cells);
   if (cmax * 7 / 8 != waves_cells) cells_opts.push_back(cmax * 7 / 8);
   const std::vector<int> per_opts = {7, 6, 5};
-  const std::vector<float> q_opts = {0.5f, 0.25f, 1.0f};
+  const std::vector<float> q_opts = {0.5f, 0.25f, 1.0f, 0.125f};
   const std::vector<int> half_opts = {0, 1};
   cudaEvent_t e0, e1;
   FK_CUDA(cudaEventCreate(&e0));
