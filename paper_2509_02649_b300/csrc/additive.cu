@@ -66,7 +66,7 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
                             cudaStream_t st, fk_report* rep) {
   Scratch scr(st);
   CaptureCtx* cap = capture_ctx();
-  unsigned* flags;
+  unsigned* flags = nullptr;
   if (cap) {
     flags = cap->flags;
   } else {
@@ -84,7 +84,7 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
   // 1-D moments and right-hand sides per coordinate
   EsPlan p1;
   FK_TRY(make_es_plan(1, 2 * m, eps, o.upsampfac, &p1));
-  double *corr1, *grid1, *T1, *bt, *rhs;
+  double *corr1 = nullptr, *grid1 = nullptr, *T1 = nullptr, *bt = nullptr, *rhs = nullptr;
   FK_TRY(scr.alloc(&corr1, 2 * static_cast<size_t>(p1.kmax) + 1));
   FK_TRY(scr.alloc(&grid1, static_cast<size_t>(p1.N) * (1 + nt)));
   FK_TRY(scr.alloc(&T1, 2 * static_cast<size_t>(d) * M2));
@@ -119,7 +119,7 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
   // 2-D blocks of ones at (X_l1, -X_l2)
   EsPlan p2;
   FK_TRY(make_es_plan(2, m, eps, o.upsampfac, &p2));
-  double *corr2, *grid2, *Bp;
+  double *corr2 = nullptr, *grid2 = nullptr, *Bp = nullptr;
   R* pts = nullptr;
   FK_TRY(scr.alloc(&corr2, 2 * static_cast<size_t>(p2.kmax) + 1));
   FK_TRY(scr.alloc(&grid2, static_cast<size_t>(p2.N) * p2.N));
@@ -154,7 +154,7 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
     }
   if (rep) cudaEventRecord(ev[1], st);
   // block Gram + lambda I, dense solve per lambda
-  double* A;
+  double* A = nullptr;
   FK_TRY(scr.alloc(&A, 2 * Dall * Dall));
   for (int li = 0; li < n_lambda; ++li) {
     k_additive_gram<<<grid_for(Dall * Dall, 256), 256, 0, st>>>(d, m, T1, Bp, lambdas[li], A); note_launch();
@@ -191,7 +191,7 @@ fk_status predict_additive_impl(int d, int m, const double* theta, int n_sets, i
                                 double* f, cudaStream_t st) {
   Scratch scr(st);
   CaptureCtx* cap = capture_ctx();
-  unsigned* flags;
+  unsigned* flags = nullptr;
   if (cap) {
     flags = cap->flags;
   } else {
@@ -201,7 +201,7 @@ fk_status predict_additive_impl(int d, int m, const double* theta, int n_sets, i
   const int K = 2 * m + 1;
   EsPlan p;
   FK_TRY(make_es_plan(1, m, eps, 1.9, &p));
-  double *corr, *coef, *part;
+  double *corr = nullptr, *coef = nullptr, *part = nullptr;
   FK_TRY(scr.alloc(&corr, 2 * static_cast<size_t>(m) + 1));
   FK_TRY(scr.alloc(&coef, 2 * static_cast<size_t>(n_sets) * K));
   FK_TRY(scr.alloc(&part, static_cast<size_t>(n_sets) * nq));

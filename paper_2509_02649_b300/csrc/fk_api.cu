@@ -233,7 +233,7 @@ static fk_status build_system(int d, int64_t n, const void* x, const void* y, in
   if (plan_out) *plan_out = p;
   const int nc = 1 + n_targets;
   const int64_t G = ipow(p.N, d);
-  double *grid, *corr;
+  double *grid = nullptr, *corr = nullptr;
   FK_TRY(scr.alloc(&grid, G * nc));
   FK_TRY(scr.alloc(&corr, 2 * static_cast<size_t>(p.kmax) + 1));
   FK_TRY(es_correction(p, corr, st));
@@ -310,7 +310,7 @@ fk_status fk_type1(int d, int64_t n, const void* x, const void* c, int n_ch, int
   FK_TRY(fl.init(scr));
   EsPlan p;
   FK_TRY(make_es_plan(d, kmax, eps, o.upsampfac, &p));
-  double *grid, *corr;
+  double *grid = nullptr, *corr = nullptr;
   FK_TRY(scr.alloc(&grid, ipow(p.N, d) * n_ch));
   FK_TRY(scr.alloc(&corr, 2 * static_cast<size_t>(kmax) + 1));
   FK_TRY(es_correction(p, corr, st));
@@ -332,7 +332,7 @@ fk_status fk_type2(int d, int kmax, const double* coef, int n_sets, int64_t n, c
   FK_TRY(fl.init(scr));
   EsPlan p;
   FK_TRY(make_es_plan(d, kmax, eps, o.upsampfac, &p));
-  double* corr;
+  double* corr = nullptr;
   FK_TRY(scr.alloc(&corr, 2 * static_cast<size_t>(kmax) + 1));
   FK_TRY(es_correction(p, corr, st));
   if (precision == FK_FP64)
@@ -428,7 +428,7 @@ static fk_status fit_common(int d, int64_t n, const void* x, const void* y, int 
   KernelTimerScope kts(rep != nullptr);
   tm.mark();
   const int64_t D = ipow(2 * m + 1, d), M2 = ipow(4 * m + 1, d);
-  double *T, *b, *W;
+  double *T = nullptr, *b = nullptr, *W = nullptr;
   FK_TRY(scr.alloc(&T, 2 * M2));
   FK_TRY(scr.alloc(&b, 2 * D * n_targets));
   FK_TRY(scr.alloc(&W, D * n_lambda));
@@ -437,7 +437,7 @@ static fk_status fit_common(int d, int64_t n, const void* x, const void* y, int 
   PenOp op;
   if (cmom) {
     // sub-domain / collocation penalty: W keeps the Sobolev part, mu D^* C D is an operator
-    double* P;
+    double* P = nullptr;
     FK_TRY(scr.alloc(&P, 2 * D));
     FK_TRY(pde_symbol_vec(d, m, n_terms, alpha, a, P, st));
     FK_TRY(penalty_weights(d, m, penalty, s, o.sobolev_c0, lambdas, n_lambda, 0.0, 0, nullptr, nullptr, W, st));
@@ -510,7 +510,7 @@ fk_status fk_fit_sobolev_pairs(int d, int64_t n, const void* x, const void* y, i
   KernelTimerScope kts(rep != nullptr);
   tm.mark();
   const int64_t D = ipow(2 * m + 1, d), M2 = ipow(4 * m + 1, d);
-  double *T, *b, *W;
+  double *T = nullptr, *b = nullptr, *W = nullptr;
   FK_TRY(scr.alloc(&T, 2 * M2));
   FK_TRY(scr.alloc(&b, 2 * D * n_targets));
   FK_TRY(scr.alloc(&W, D * n_pairs));
@@ -687,7 +687,7 @@ fk_status fk_accum_add(fk_accum* a, int64_t n, const void* x, const void* y, con
                           a->grid, true, a->flags, st, scr, a->o.autotune != 0));
   } else {
     const int64_t G = ipow(p.N, a->d) * (1 + a->nt);
-    double* tmp;
+    double* tmp = nullptr;
     FK_TRY(scr.alloc(&tmp, G));
     FK_TRY(spread_any(p, a->precision, a->o, n, x, y, a->nt, true, tmp, a->flags, st, scr));
     k_add_grid<<<grid_for(G, 256), 256, 0, st>>>(G, tmp, a->grid); note_launch();
@@ -729,7 +729,7 @@ fk_status fk_accum_fit_sobolev(fk_accum* a, double s, int penalty, const double*
   tm.mark();
   const int d = a->d, m = a->m;
   const int64_t D = ipow(2 * m + 1, d), M2 = ipow(4 * m + 1, d);
-  double *T, *b, *W;
+  double *T = nullptr, *b = nullptr, *W = nullptr;
   FK_TRY(scr.alloc(&T, 2 * M2));
   FK_TRY(scr.alloc(&b, 2 * D * a->nt));
   FK_TRY(scr.alloc(&W, D * n_lambda));

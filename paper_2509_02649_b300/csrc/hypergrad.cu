@@ -114,12 +114,12 @@ fk_status hypergrad_impl(int d, int64_t n, const R* x, int64_t n_v, const R* xv,
                          const double* W, const double* theta, double eps, int precision, const fk_opts& o,
                          double* loss, double* dW, double* dY, cudaStream_t st) {
   Scratch scr(st);
-  unsigned* flags;
+  unsigned* flags = nullptr;
   FK_TRY(scr.alloc(&flags, 1));
   FK_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned), st));
   EsPlan p;
   FK_TRY(make_es_plan(d, m, eps, o.upsampfac, &p));
-  double* corr;
+  double* corr = nullptr;
   FK_TRY(scr.alloc(&corr, 2 * static_cast<size_t>(m) + 1));
   FK_TRY(es_correction(p, corr, st));
   int64_t D = 1, G = 1;
@@ -128,8 +128,8 @@ fk_status hypergrad_impl(int d, int64_t n, const R* x, int64_t n_v, const R* xv,
     G *= p.N;
   }
   // predictions at the validation points and residuals
-  double *f, *sum, *g, *z, *grid;
-  R* r;
+  double *f = nullptr, *sum = nullptr, *g = nullptr, *z = nullptr, *grid = nullptr;
+  R* r = nullptr;
   FK_TRY(scr.alloc(&f, static_cast<size_t>(n_v)));
   FK_TRY(scr.alloc(&r, static_cast<size_t>(n_v)));
   FK_TRY(scr.alloc(&sum, 1));

@@ -908,8 +908,8 @@ static fk_status cg_solve(int d, int m, const double* T, const double* W, int n_
   FK_CUDA(cudaStreamSynchronize(st));
   if (!(T0 > 0.0)) T0 = 1.0;
 
-  double *r, *z, *p, *q, *scal;
-  int *active, *cnt;
+  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *scal = nullptr;
+  int *active = nullptr, *cnt = nullptr;
   FK_TRY(scr.alloc(&r, 2 * D * nsys));
   FK_TRY(scr.alloc(&z, 2 * D * nsys));
   FK_TRY(scr.alloc(&p, 2 * D * nsys));
@@ -1233,8 +1233,8 @@ static fk_status cg_solve_fused(int d, int m, const double* T, const double* W, 
   const int nsys = n_w * n_rhs;
   const int64_t D = (d == 1) ? K : static_cast<int64_t>(K) * K;
   const int64_t LL = (d == 1) ? Lc : static_cast<int64_t>(Lc) * Lc;
-  cplx<double>* ch;
-  const double* tw;
+  cplx<double>* ch = nullptr;
+  const double* tw = nullptr;
   FK_TRY(scr.alloc(&ch, LL));
   FK_TRY(twiddle_table(Lc, st, &tw));
   FK_CUDA(cudaMemsetAsync(ch, 0, sizeof(cplx<double>) * LL, st));
@@ -1263,15 +1263,15 @@ static fk_status cg_solve_fused(int d, int m, const double* T, const double* W, 
     FK_CUDA(cudaMemsetAsync(ch2, 0, sizeof(cplx<double>) * LL, st));
     k_circ_embed<<<grid_for(M2, 256), 256, 0, st>>>(d, m, Lc, op->c, ch2); note_launch();
     FK_TRY(fft_lines<double>(ch2, Lc, 1, Lc, 1, -1, tw, st));
-    double* wd;
+    double* wd = nullptr;
     FK_TRY(scr.alloc(&wd, D * n_w));
     k_op_diag<<<grid_for(D * n_w, 256), 256, 0, st>>>(D, n_w, W, op->P, op->c + 2 * centre, op->mu, wd); note_launch();
     FK_CUDA(cudaGetLastError());
     Wd = wd;
   }
 
-  double *r, *z, *p, *q, *scal;
-  int *active, *cnt;
+  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *scal = nullptr;
+  int *active = nullptr, *cnt = nullptr;
   cplx<double>* buf = nullptr;
   FK_TRY(scr.alloc(&r, 2 * D * nsys));
   FK_TRY(scr.alloc(&z, 2 * D * nsys));
@@ -1376,7 +1376,7 @@ fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, 
     return cg_solve(d, m, T, W, n_w, rhs, n_rhs, o, sol, st, scratch, cg_iters, rel_res);
   }
   if (D > 8192) return set_error(FK_EINVAL, "dense Cholesky limited to D <= 8192 (D = %lld)", (long long)D);
-  double *A, *R, *A0 = nullptr;
+  double *A = nullptr, *R = nullptr, *A0 = nullptr;
   FK_TRY(scratch.alloc(&A, 2 * D * D));
   FK_TRY(scratch.alloc(&R, 2 * D * n_rhs));
   if (with_op) FK_TRY(scratch.alloc(&A0, 2 * D * D));  // the assembled matrix, for the refinement residual
@@ -1389,7 +1389,7 @@ fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, 
       FK_CUDA(cudaMemcpyAsync(A0, A, sizeof(double) * 2 * D * D, cudaMemcpyDeviceToDevice, st));
     }
     FK_CUDA(cudaGetLastError());
-    double* linv;
+    double* linv = nullptr;
     FK_TRY(scratch.alloc(&linv, 2 * linv_blocks(D) * NB * NB));
     FK_TRY(cholesky(A, D, flags, st, linv));
     FK_CUDA(cudaMemcpyAsync(X, rhs, sizeof(double) * 2 * D * n_rhs, cudaMemcpyDeviceToDevice, st));
@@ -1433,13 +1433,13 @@ __global__ void k_dense_residual(const double* A, int64_t D, const double* X, co
 // X holds B on entry and the solution on exit.
 fk_status solve_dense(const double* A, int64_t D, double* X, int n_rhs, int refine, cudaStream_t st, Scratch& scr,
                       unsigned* flags) {
-  double *L, *B, *R;
+  double *L = nullptr, *B = nullptr, *R = nullptr;
   FK_TRY(scr.alloc(&L, 2 * D * D));
   FK_TRY(scr.alloc(&B, 2 * D * n_rhs));
   FK_TRY(scr.alloc(&R, 2 * D * n_rhs));
   FK_CUDA(cudaMemcpyAsync(L, A, sizeof(double) * 2 * D * D, cudaMemcpyDeviceToDevice, st));
   FK_CUDA(cudaMemcpyAsync(B, X, sizeof(double) * 2 * D * n_rhs, cudaMemcpyDeviceToDevice, st));
-  double* linv;
+  double* linv = nullptr;
   FK_TRY(scr.alloc(&linv, 2 * linv_blocks(D) * NB * NB));
   FK_TRY(cholesky(L, D, flags, st, linv));
   FK_TRY(trisolve(L, D, X, n_rhs, st, &scr, flags, linv));
@@ -2003,8 +2003,8 @@ fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, 
   A.x = sol;
   int64_t centre = 2 * static_cast<int64_t>(4 * m + 1) * m + 2 * m;  // index of T_(0,0)
   A.T0p = T + 2 * centre;
-  cplx<double>* ch;
-  const double* tw;
+  cplx<double>* ch = nullptr;
+  const double* tw = nullptr;
   FK_TRY(scr.alloc(&ch, static_cast<int64_t>(Lc) * Lc));
   FK_TRY(twiddle_table(Lc, st, &tw));
   FK_CUDA(cudaMemsetAsync(ch, 0, sizeof(cplx<double>) * Lc * Lc, st));
@@ -2017,14 +2017,14 @@ fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, 
   A.tw = tw;
   A.Wd = W;
   if (op) {
-    cplx<double>* ch2;
+    cplx<double>* ch2 = nullptr;
     FK_TRY(scr.alloc(&ch2, static_cast<int64_t>(Lc) * Lc));
     FK_CUDA(cudaMemsetAsync(ch2, 0, sizeof(cplx<double>) * Lc * Lc, st));
     k_circ_embed<<<grid_for(M2, 256), 256, 0, st>>>(2, m, Lc, op->c, ch2); note_launch();
     FK_CUDA(cudaGetLastError());
     FK_TRY(fft_lines<double>(ch2, Lc, Lc, Lc, 1, -1, tw, st));
     FK_TRY(fft_lines<double>(ch2, Lc, Lc, 1, Lc, -1, tw, st));
-    double* wd;
+    double* wd = nullptr;
     FK_TRY(scr.alloc(&wd, D * n_w));
     k_op_diag<<<grid_for(D * n_w, 256), 256, 0, st>>>(D, n_w, W, op->P, op->c + 2 * centre, op->mu, wd); note_launch();
     FK_CUDA(cudaGetLastError());
@@ -2047,7 +2047,7 @@ fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, 
   FK_TRY(scr.alloc(&A.buf, static_cast<size_t>(nsys) * K * Lc));
   // scalars [rz 2n | rr 2n | pq 2n | bb n | rres n | info], then the barrier: one memset,
   // and bb, rres and info come back in one copy
-  double* scal;
+  double* scal = nullptr;
   FK_TRY(scr.alloc(&scal, 8 * static_cast<size_t>(nsys) + 1 + 8));
   FK_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * (8 * nsys + 1 + 8), st));
   A.rz = scal;
@@ -2264,7 +2264,7 @@ fk_status trisolve_coop(const double* L, const double* Linv, int64_t D, double* 
   FK_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   FK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (!coop || D < 2 * TS_NB || D > (1 << 30)) return FK_OK;
-  unsigned char* misc;
+  unsigned char* misc = nullptr;
   FK_TRY(scr.alloc(&misc, 16 * static_cast<size_t>(n_rhs)));
   FK_CUDA(cudaMemsetAsync(misc, 0, 16 * static_cast<size_t>(n_rhs), st));
   for (int r = 0; r < n_rhs; ++r) {

@@ -61,9 +61,8 @@ struct Fx1dArgs {
 // hi-word change of one low-word add: qsign + carry out of (old + q), where qsign is
 // the sign extension (0 or -1) of q
 __device__ __forceinline__ int carry_delta(unsigned old, unsigned q, int qsign) {
-  unsigned nw;
   int dh;
-  asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, 0;" : "=r"(nw), "=r"(dh) : "r"(old), "r"(q), "r"(qsign));
+  asm("{\n\t.reg .u32 t;\n\tadd.cc.u32 t, %1, %2;\n\taddc.u32 %0, %3, 0;\n\t}" : "=r"(dh) : "r"(old), "r"(q), "r"(qsign));
   return dh;
 }
 
