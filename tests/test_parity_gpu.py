@@ -200,6 +200,29 @@ def test_cg_corner_lags(m):
         assert rel(sol[li], want) < 1e-10, li
 
 
+@pytest.mark.parametrize("d", [1, 2])
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_constant_mode_only(d, precision):
+    # m = 0, the degenerate case: one mode, T_0 = 1 and W_0 = lambda (1 + 0^(2s)), so
+    # theta_0 = mean(y) / (1 + lambda) and the prediction is that constant everywhere
+    n, lam = 5001, 0.3
+    td = torch.float32 if precision == "mixed" else torch.float64
+    eps, tol = (1e-6, 1e-5) if precision == "mixed" else (1e-12, 1e-11)
+    x = S.uniform_points(n, d, 41)
+    y = 1.5 + np.sin(x[0])
+    xs = x.astype(np.float32) if precision == "mixed" else x
+    ys = y.astype(np.float32) if precision == "mixed" else y
+    th = fk.fk_fit_sobolev(dev(xs, td), dev(ys, td), 0, 2.0, [lam], eps, precision)
+    want = ys.astype(np.float64).mean() / (1.0 + lam)
+    got = host(th)[0, 0]
+    assert got.shape == (1,)
+    assert abs(got[0] - want) < tol * abs(want)
+    xq = S.uniform_points(300, d, 42)
+    xq = xq.astype(np.float32) if precision == "mixed" else xq
+    f = host(fk.fk_predict(th[0], dev(xq, td), 0, eps, precision))[0]
+    assert np.max(np.abs(f - want)) < tol * abs(want)
+
+
 def test_not_positive_definite_reported():
     m = 4
     x = S.uniform_points(100, 1, 28)
