@@ -48,6 +48,29 @@ def test_autotune_2d_spreader():
     assert fk.fk_autotune_table() == ""
 
 
+def test_autotune_2d_spreader_two_owner_sizes():
+    # the 256 x 256 grid (m = 32), whose default owners come in two sizes; the trials
+    # also time uniform owners in the same kernel, and the kept shape must agree with
+    # the untuned call and with direct sums
+    fk.fk_autotune_clear()
+    n, m = 1 << 21, 32
+    x, y = S.wl2_sobolev_2d(n, dtype=np.float32)
+    X = torch.from_numpy(x).cuda()
+    Y = torch.from_numpy(y).cuda()
+    plain = fk.fk_build_system(X, Y, m, 1e-6, "mixed")
+    tuned = fk.fk_build_system(X, Y, m, 1e-6, "mixed", opts=fk.default_opts(autotune=1))
+    assert "spread2d" in fk.fk_autotune_table()
+    for a, b in zip(tuned, plain):
+        assert rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-6
+    K = 4 * m + 1
+    T = tuned[0].cpu().numpy()
+    x0, x1 = x[0].astype(np.float64), x[1].astype(np.float64)
+    for j0, j1 in [(0, 0), (1, -2), (-64, 64), (40, -17)]:
+        want = np.mean(np.exp(-1j * (j0 * x0 + j1 * x1)))
+        assert abs(T[(j0 + 2 * m) * K + (j1 + 2 * m)] - want) < 1e-6
+    fk.fk_autotune_clear()
+
+
 def test_autotune_1d_spreader_and_accumulator():
     fk.fk_autotune_clear()
     n = 1 << 21
