@@ -9,6 +9,13 @@ deconvolution to the moments T and right-hand side b, penalty assembly and the
 FP64 conjugate-gradient solve.  Inputs (1.2 GB) are larger than L2, so no flush
 runs between steps.
 
+The same line carries, under "rows", the other hot-path rows at full size, each
+timed with its own (smaller) step count, clocks and roofline: the additive model
+(d = 8, n = 2e8), the physics-informed fit with its held-out-loss hypergradient
+(n = 1e9) and the 1-D sweep (1e10 points, 256 lambdas x 16 targets).  FP32 peaks are
+measured on the device (fk_peak_fp32); the mixed result is gated against the FP64
+path at eps = 1e-12.
+
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle instead.
 """
 from __future__ import annotations
@@ -28,9 +35,9 @@ sys.path.insert(0, ROOT)
 
 WL = dict(workload="2d-sobolev", d=2, n=100_000_000, m=32, s=2.0, lam=1e-6, eps=1e-6)
 METRIC = "fit points/s (NUFFT Gram+RHS+solve)"
-SM_COUNT = 148
-FP32_LANES_PER_SM = 128
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (derived peak, reported beside the measured one)
 ACC_DRAM_BYTES_PER_POINT = (241.207040e6 + 6.003200e6) / 2e7  # k_bin_accumulate, 2-D, w = 7
+SPREAD1D_DRAM_BYTES_PER_POINT = (5.09e9 + 5.1e6) / 67108864  # k_spread1d_fx, 17 channels
 
 
 def parse():
@@ -49,6 +56,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="skip the graph-replay measurement")
+    ap.add_argument("--no-rows", action="store_true",
+                    help="headline line only (skip the sweep-1d, pik-heat and additive-8d rows)")
     ap.add_argument("--workload", default="2d-sobolev", choices=["2d-sobolev", "sweep-1d", "pik-heat", "additive-8d"],
                     help="2d-sobolev is the headline line; the others time the other hot-path rows")
     a = ap.parse_args()
@@ -64,6 +73,19 @@ def measured_peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {}
+
+
+def fp32_peak(fk):
+    """Measured FP32 FMA throughput (fk_peak_fp32) and the derived one, in TFLOP/s."""
+    import torch
+    measured, sms = fk.fk_peak_fp32()
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = sms or props.multi_processor_count
+    sm_max = measured_peaks().get("sm_max_mhz", 2032.0)
+    derived = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    return {"measured": measured, "derived": derived, "sm_count": sms,
+            "basis": "of measured: fk_peak_fp32 (FFMA chains, 2048 threads per SM, best of 3 launches); derived = "
+                     "%d SMs x %d FP32 lanes x 2 flop x %.0f MHz" % (sms, FP32_LANES_PER_SM, sm_max)}
 
 
 def host_cores():
@@ -231,7 +253,7 @@ def _dev_normal(torch, n, seed):
     return torch.randn(n, generator=g, device="cuda", dtype=torch.float32)
 
 
-def run_row(args, rank, local):
+def run_row(args, rank, local, W=None, steps=None, warmup=None, peak=None, n=None):
     """Time one of the other hot-path rows on one GPU (inputs drawn on the device).
 
     sweep-1d:    1e10 points (2^28-point chunks from the counter-based generator; the
@@ -241,19 +263,20 @@ def run_row(args, rank, local):
                  gradient (autograd) on 1e7 validation points.
     additive-8d: n = 2e8 points in d = 8, m = 64: 8 1-D and 28 2-D transforms,
                  block Gram and dense FP64 solve.
-    --n overrides the point count (smaller cases for profiling); --no-autotune keeps
-    the spreaders' default shapes."""
+    n overrides the point count (smaller cases for profiling); --no-autotune keeps
+    the spreaders' default shapes.  Returns the row's JSON object."""
     import torch
     import paper_2509_02649_b300 as fk
     torch.cuda.set_device(local)
     tune = 0 if args.no_autotune else 1
     st = torch.cuda.current_stream()
-    peaks = measured_peaks()
-    sm_max = peaks.get("sm_max_mhz", 2032.0)
-    p32 = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    W = args.workload
+    W = W or args.workload
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    peak = peak or fp32_peak(fk)
+    p32 = peak["measured"]
     if W == "sweep-1d":
-        n_total = args.n if args.n != WL["n"] else 10_000_000_000
+        n_total = n or 10_000_000_000
         chunk, m, nt = min(1 << 28, (n_total + 3) // 4 * 4), 1000, 16
         lams = list(np.logspace(-12, -2, 256))
         x = torch.empty((1, chunk), dtype=torch.float32, device="cuda")
@@ -288,8 +311,11 @@ def run_row(args, rank, local):
         cfg = {"workload": W, "n": n_total, "d": 1, "m": m, "s": 1.0, "n_lambda": 256, "n_targets": nt, "eps": 1e-6,
                "chunk": chunk, "timed": "spreading of every chunk + transform + batched solve; generation excluded"}
         kern = "k_spread1d_fx (fixed-point shared-memory spreading, 17 channels)"
+        traffic = SPREAD1D_DRAM_BYTES_PER_POINT * chunk
+        traffic_note = ("ncu capture of k_spread1d_fx at n = 2^26 (5.09 GB read + 5.1 MB written), scaled to one "
+                        "launch (one 2^28-point chunk)")
     elif W == "pik-heat":
-        n, nv, m = (args.n if args.n != WL["n"] else 1_000_000_000), 10_000_000, 25
+        n, nv, m = (n or 1_000_000_000), 10_000_000, 25
         x = _dev_uniform(torch, n, 2, 11)
         y = torch.exp(-0.1 * x[0]) * torch.sin(x[1]) + 0.1 * _dev_normal(torch, n, 12)
         xv = _dev_uniform(torch, nv, 2, 13)
@@ -315,8 +341,11 @@ def run_row(args, rank, local):
                "operator": "d_t - 0.1 d_xx", "eps": 1e-6,
                "timed": "fit + held-out loss + hypergradient (autograd forward and backward)"}
         kern = "k_bin_accumulate (register-accumulation spreading, training fit)"
+        traffic = ACC_DRAM_BYTES_PER_POINT * n
+        traffic_note = ("ncu capture of k_bin_accumulate at n = 2e7 (2-D sobolev, the same 256^2 grid and w = 7), "
+                        "scaled to one launch by points")
     else:
-        n, d, m = (args.n if args.n != WL["n"] else 200_000_000), 8, 64
+        n, d, m = (n or 200_000_000), 8, 64
         lam = n ** (-0.8)
         x = _dev_uniform(torch, n, d, 41)
         y = 0.1 * _dev_normal(torch, n, 42)
@@ -335,25 +364,27 @@ def run_row(args, rank, local):
         cfg = {"workload": W, "n": n, "d": d, "m": m, "lambda": lam, "eps": 1e-6,
                "timed": "8 1-D + 28 2-D type-1 transforms, block Gram, dense FP64 solve"}
         kern = "all spreading kernels of the 36 transforms"
-    for _ in range(max(1, args.warmup)):
+        traffic, traffic_note = None, "spreading kernels changed since the last ncu capture"
+    for _ in range(max(1, warmup)):
         step()
     torch.cuda.synchronize()
     launches0 = fk.fk_launch_count()
     res = []
     with ClockSampler(local) as clk:
-        for _ in range(args.steps):
+        for _ in range(steps):
             res.append(step())
-    launches = (fk.fk_launch_count() - launches0) // max(1, args.steps)
+    launches = (fk.fk_launch_count() - launches0) // max(1, steps)
     ms = statistics.median(r[0] for r in res)
     mk = statistics.median(r[1] for r in res)
     achieved = f_pt * n / (mk / 1e3) / 1e12
     line = {"metric": "fit points/s (" + W + ")", "value": n / (ms / 1e3), "unit": "points/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "steps": steps, "warmup": warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (drawn on the device)",
             "config": cfg, "gpu_launches_per_step": launches,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": p32, "unit": "TFLOP/s", "frac": achieved / p32,
-                         "traffic": None, "kernel": kern, "flop_per_point": f_pt, "ms_kernel": mk,
-                         "peak_basis": "of derived peak: 148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % sm_max},
+                         "traffic": traffic, "traffic_basis": traffic_note, "kernel": kern, "flop_per_point": f_pt,
+                         "ms_kernel": mk, "peak_basis": peak["basis"], "peak_derived": peak["derived"],
+                         "frac_of_derived": achieved / peak["derived"]},
             "clocks": clk.summary()}
     line["autotune"] = fk.fk_autotune_table().strip() or None
     if W == "pik-heat":
@@ -370,14 +401,14 @@ def run_row(args, rank, local):
         graph.status()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         g0.record(gst)
-        for _ in range(args.steps):
+        for _ in range(steps):
             graph.launch(gst)
         g1.record(gst)
         graph.status()
-        line["graph"] = {"ms_per_step": g0.elapsed_time(g1) / args.steps, "graph_launches_per_step": 1,
+        line["graph"] = {"ms_per_step": g0.elapsed_time(g1) / steps, "graph_launches_per_step": 1,
                          "what": "fk_capture_begin/end of one fit, replayed with fk_graph_launch"}
         graph.close()
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -389,7 +420,7 @@ def main():
         run_reference(args, rank)
         return
     if args.workload != "2d-sobolev":
-        run_row(args, rank, local)
+        print(json.dumps(run_row(args, rank, local, n=(args.n if args.n != WL["n"] else None))), flush=True)
         return
 
     import torch
@@ -407,6 +438,7 @@ def main():
     y_h = torch.from_numpy(y_np).pin_memory()
     x = x_h.cuda()
     y = y_h.cuda()
+    peak = fp32_peak(fk)
     spread = {"auto": fk.FK_SPREAD_AUTO, "atomic": fk.FK_SPREAD_ATOMIC, "binned": fk.FK_SPREAD_BINNED}[args.spread]
     # the first warm-up step times the spreader's tunable shapes and keeps the fastest
     opts = fk.default_opts(spread=spread, autotune=0 if args.no_autotune else 1)
@@ -502,8 +534,7 @@ def main():
     C = 2
     f_pt = (w ** d) * (2 * C + (d - 1))
     peaks = measured_peaks()
-    sm_max = peaks.get("sm_max_mhz", 2032.0)
-    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    peak_tflops = peak["measured"]
     achieved = f_pt * n / (ms_kernel / 1e3) / 1e12
     # DRAM bytes of one k_bin_accumulate launch: ncu capture of this kernel at n = 2e7
     # (dram__bytes_read.sum 241.2 MB + dram__bytes_write.sum 6.0 MB), scaled by points
@@ -513,9 +544,11 @@ def main():
                 "frac": achieved / peak_tflops, "traffic": traffic,
                 "kernel": "k_bin_accumulate (register-accumulation spreading)",
                 "flop_per_point": f_pt, "kernel_width": w, "ms_kernel": ms_kernel,
-                "peak_basis": "of derived peak: 148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % sm_max,
+                "peak_basis": peak["basis"], "peak_derived": peak["derived"],
+                "frac_of_derived": achieved / peak["derived"], "sm_count": peak["sm_count"],
                 "stage": {"ms_spread_all_kernels": ms_spread,
                           "achieved_TFLOPs": f_pt * n / (ms_spread / 1e3) / 1e12,
+                          "frac": f_pt * n / (ms_spread / 1e3) / 1e12 / peak_tflops,
                           "ms_fft": statistics.mean(r["ms_fft"] for r in reps),
                           "ms_solve": statistics.mean(r["ms_solve"] for r in reps), "cg_iters": reps[-1]["cg_iters"]},
                 "hbm_view": {"bytes_per_point_input": 12, "achieved_GBs": 12 * n / (ms_spread / 1e3) / 1e9,
@@ -526,7 +559,7 @@ def main():
     bound_pts = min(hbm * 1e9 / 12.0, peak_tflops * 1e12 / f_pt)
     roofline["fit_view"] = {"bound_points_per_s": bound_pts, "achieved_points_per_s": value / world,
                             "frac": value / world / bound_pts,
-                            "basis": "min(measured HBM / 12 B, derived FP32 peak / %d flop) per GPU" % f_pt}
+                            "basis": "min(measured HBM / 12 B, measured FP32 peak / %d flop) per GPU" % f_pt}
 
     line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -607,9 +640,24 @@ def main():
         torch.cuda.synchronize()
         fms = f0.elapsed_time(f1) / k
         err = float(torch.linalg.norm(theta - th64) / torch.linalg.norm(th64))
+        # accuracy reference: the FP64 path at eps = 1e-12 (itself gated <= 1e-10 against the
+        # oracle at small n); the metric's gate is rel err <= 1e-5 for the mixed path
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(st)
+        th_acc = fk.fk_fit_sobolev(x64, y64, m, s, [lam], 1e-12, "fp64")
+        a1.record(st)
+        torch.cuda.synchronize()
+        err_acc = float(torch.linalg.norm(theta - th_acc) / torch.linalg.norm(th_acc))
         line["fp64_path"] = {"value": n / (fms / 1e3), "unit": "points/s", "ms_per_step": fms,
                              "mixed_speedup": (n / (ms_step / 1e3)) / (n / (fms / 1e3)),
-                             "theta_rel_err_mixed_vs_fp64": err, "eps": eps}
+                             "theta_rel_err_mixed_vs_fp64": err, "eps": eps,
+                             "accuracy_reference": {"eps": 1e-12, "precision": "fp64",
+                                                    "ms": a0.elapsed_time(a1),
+                                                    "theta_rel_err_mixed": err_acc,
+                                                    "theta_rel_err_fp64_eps1e-6": float(
+                                                        torch.linalg.norm(th64 - th_acc) / torch.linalg.norm(th_acc)),
+                                                    "gate": 1e-5, "pass": err_acc <= 1e-5}}
         del x64, y64
 
     if rank == 0 and not args.no_cpu_baseline:
@@ -617,6 +665,16 @@ def main():
         t_cpu, _ = cpu_oracle_fit(x_np[:, :n_o], y_np[:n_o], m, s, lam)
         line["cpu_baseline"] = {"value": n_o / t_cpu, "unit": "points/s", "cores": host_cores(), "kind": "oracle",
                                 "sample": "first %d points of the workload: direct sums + dense solve D=4225" % n_o}
+    if rank == 0 and not args.no_rows:
+        # the other hot-path rows, each at full size with its own step count, clocks and
+        # roofline (the headline's inputs are released first)
+        del x, y
+        torch.cuda.empty_cache()
+        rows = {}
+        for wl, k, w0 in (("additive-8d", 5, 2), ("pik-heat", 5, 2), ("sweep-1d", 2, 1)):
+            rows[wl] = run_row(args, rank, local, W=wl, steps=k, warmup=w0, peak=peak)
+            torch.cuda.empty_cache()
+        line["rows"] = rows
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

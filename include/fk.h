@@ -101,6 +101,9 @@ typedef struct {
                          (partition tile, cells per owner, round quota) on the call's own data,
                          keeps the fastest in a process-wide table and uses it from then on;
                          that first call runs the spreading several times (default 0) */
+  long long wait_cycles; /* bound, in SM clock cycles, of each grid-barrier wait of the single-
+                         launch conjugate-gradient solver; a wait that runs out makes the call
+                         return FK_ETIMEOUT (default 0 = about 2 s at the maximum clock) */
 } fk_opts;
 
 /* Filled when a non-NULL pointer is passed (the call then synchronises `stream`). */
@@ -215,16 +218,23 @@ FK_API fk_status fk_type2(int d, int kmax, const double* coef, int n_sets, int64
  * time (a process whose device memory is wholly reserved by its own pool allocator,
  * or a service that forbids device allocation after start-up).  The paper has no
  * counterpart to this entry point.
- *   All scratch comes from one built-in device array of FK_NOALLOC_SCRATCH_BYTES,
- *   which every GPU that loads the library holds until the process exits; no
- *   cudaMalloc / cudaMallocAsync / cudaFree is called.  Shapes whose scratch would
+ *   All scratch comes from one built-in device array of FK_NOALLOC_SCRATCH_BYTES;
+ *   no cudaMalloc / cudaMallocAsync / cudaFree is called.  Shapes whose scratch would
  *   exceed it (d = 2 needs about 16 N^2 n_ch bytes, N the upsampled grid) return
  *   FK_EINVAL with the required size in fk_last_error().
- *   The first call on a device looks up the array's device address (with that
- *   device current); make that first call before any stream capture.
- *   Calls share the array: calls whose work overlaps on the GPU (other streams,
- *   other host threads) race on it.  The call synchronises `stream`.
- *   Spreading uses the atomic form for both precisions.  Arguments as fk_type1. */
+ *   The first call on a device does a one-time set-up with that device current: it
+ *   looks up the array's device address (which, under the CUDA runtime's lazy module
+ *   loading, is when the array is placed in device memory), loads the kernels later
+ *   calls launch, and computes the quadrature nodes of the correction factors.  That
+ *   call needs about FK_NOALLOC_SCRATCH_BYTES of free device memory plus the code, and
+ *   returns FK_ECUDA if it cannot get them: make it at start-up, before device memory
+ *   is reserved elsewhere, and before any stream capture.  The array is then held by
+ *   that device until the process exits.
+ *   Calls share the array and it keeps the last call's contents (the grid and the flag
+ *   word are cleared each call; tables of the last call's plan are reused).  Calls
+ *   whose work overlaps on the GPU (other streams, other host threads) race on it.
+ *   The call synchronises `stream`.  Spreading uses the atomic form for both
+ *   precisions.  Arguments and argument checks as fk_type1, with d in {1, 2}. */
 #define FK_NOALLOC_SCRATCH_BYTES (16u << 20)
 FK_API fk_status fk_type1_noalloc(int d, int64_t n, const void* x, const void* c, int n_ch, int kmax,
                                   double eps, int precision, double* out, void* stream);
@@ -349,6 +359,14 @@ FK_API size_t fk_workspace_bytes(int d, int m, int64_t n, int n_ch, double eps, 
 /* Number of CUDA kernels this library has launched in the process so far
  * (monotonic; a caller takes differences around a region of interest). */
 FK_API int64_t fk_launch_count(void);
+
+/* Measurement helper (no counterpart in the paper): the FP32 FMA throughput of the
+ * current device, the peak the spreading kernels' flop rates are reported against.
+ * One kernel of independent FMA chains (2048 threads per SM) is launched four times on
+ * `stream` and timed with CUDA events; *tflops (host) receives the best of the last
+ * three, at 2 flop per FMA, and *sm_count (host, may be NULL) the device's
+ * multiprocessor count.  Synchronises `stream`; not capturable. */
+FK_API fk_status fk_peak_fp32(double* tflops, int* sm_count, void* stream);
 
 /* Library version string. */
 FK_API const char* fk_version(void);

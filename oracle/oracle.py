@@ -10,7 +10,7 @@ dimensional example).  Library primitives serve as steps: numpy ``cos``/``sin``
 for each phase factor (evaluated directly, no recurrences), ``matmul`` for sums
 over points, LAPACK's Cholesky for the Hermitian solve.
 
-Conventions (readings of the paper, listed in the design doc):
+Conventions (readings of the paper where it is silent or inconsistent):
   * frequency scale pi/(2L) = 1: points are radians, caller rescales (§2.2);
   * modes K = {k in Z^d : |k|_inf <= m}, lexicographic, last dimension fastest
     (§2.2, space H_m);

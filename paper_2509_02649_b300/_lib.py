@@ -34,7 +34,7 @@ EXPORTS = ["fk_default_opts", "fk_fit_sobolev", "fk_fit_pik", "fk_fit_additive",
            "fk_accum_destroy", "fk_generate_sweep_1d", "fk_release_workspace", "fk_autotune_table",
            "fk_autotune_clear", "fk_fit_pik_general", "fk_box_moments", "fk_fit_sobolev_pairs",
            "fk_capture_begin", "fk_capture_end", "fk_graph_launch", "fk_graph_status", "fk_graph_destroy",
-           "fk_graph_kernel_ms"]
+           "fk_graph_kernel_ms", "fk_peak_fp32"]
 
 
 class FkError(RuntimeError):
@@ -47,7 +47,8 @@ class FkError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("cg_tol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
                 ("refine_steps", ctypes.c_int), ("sobolev_c0", ctypes.c_double), ("upsampfac", ctypes.c_double),
-                ("spread", ctypes.c_int), ("deterministic", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("spread", ctypes.c_int), ("deterministic", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("wait_cycles", ctypes.c_longlong)]
 
 
 class Report(ctypes.Structure):
@@ -110,6 +111,7 @@ def lib() -> ctypes.CDLL:
             "fk_graph_destroy": (_I, [_P]),
             "fk_graph_kernel_ms": (_I, [_P, ctypes.POINTER(ctypes.c_float)]),
             "fk_fit_sobolev_pairs": (_I, [_I, _L, _P, _P, _I, _I, _P, _P, _I, _I, _D, _I, _P, _P, _P, _P]),
+            "fk_peak_fp32": (_I, [ctypes.POINTER(_D), ctypes.POINTER(_I), _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -334,6 +336,14 @@ def fk_hypergrad(x, xv, yv, m: int, T, W, theta, eps: float, precision="mixed", 
                               eps, p, _opts_ptr(opts), ctypes.byref(loss), dW.data_ptr(),
                               dY.data_ptr() if dY is not None else None, _stream()))
     return loss.value, dW, dY
+
+
+def fk_peak_fp32():
+    """(measured FP32 FMA throughput in TFLOP/s, multiprocessor count) of the current device."""
+    t = _D()
+    sms = _I()
+    _check(lib().fk_peak_fp32(ctypes.byref(t), ctypes.byref(sms), _stream()))
+    return t.value, sms.value
 
 
 def fk_launch_count() -> int:

@@ -157,14 +157,24 @@ fk_status es_correction(const EsPlan& p, double* corr, cudaStream_t st) {
 
 namespace fk {
 
-// Same as es_correction, with the quadrature scratch (2 * GL_Q doubles) supplied by
-// the caller instead of allocated.
-fk_status es_correction_into(const EsPlan& p, double* corr, double* gl_scratch, cudaStream_t st) {
-  k_gauss_legendre<<<1, GL_Q, 0, st>>>(gl_scratch, gl_scratch + GL_Q); note_launch();
-  const int K = 2 * p.kmax + 1;
-  k_es_correction<<<(K + 127) / 128, 128, 0, st>>>(p.kmax, p.N, p.w, p.beta, gl_scratch, gl_scratch + GL_Q,
-                                                    corr); note_launch();
+fk_status es_gl_nodes_into(double* gl, cudaStream_t st) {
+  k_gauss_legendre<<<1, GL_Q, 0, st>>>(gl, gl + GL_Q); note_launch();
   FK_CUDA(cudaGetLastError());
+  return FK_OK;
+}
+
+// As es_correction, from quadrature nodes already in device memory (es_gl_nodes_into).
+fk_status es_correction_from_nodes(const EsPlan& p, double* corr, const double* gl, cudaStream_t st) {
+  const int K = 2 * p.kmax + 1;
+  k_es_correction<<<(K + 127) / 128, 128, 0, st>>>(p.kmax, p.N, p.w, p.beta, gl, gl + GL_Q, corr); note_launch();
+  FK_CUDA(cudaGetLastError());
+  return FK_OK;
+}
+
+fk_status preload_es_kernels() {
+  cudaFuncAttributes fa;
+  FK_CUDA(cudaFuncGetAttributes(&fa, k_gauss_legendre));
+  FK_CUDA(cudaFuncGetAttributes(&fa, k_es_correction));
   return FK_OK;
 }
 

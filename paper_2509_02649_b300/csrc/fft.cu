@@ -297,9 +297,9 @@ template fk_status grid_to_modes<double>(const EsPlan&, const double*, int, int,
 
 namespace fk {
 
-// Same as grid_to_modes, with the twiddle table (2 N doubles) and, for d = 2, the
-// row-transform intermediate (nc * N * (2 kout + 1) complex values) supplied by the
-// caller instead of allocated.
+// Same as grid_to_modes, with the twiddle table (2 N doubles, filled by fft_twiddles)
+// and, for d = 2, the row-transform intermediate (nc * N * (2 kout + 1) complex values)
+// supplied by the caller instead of allocated.
 template <typename R>
 fk_status grid_to_modes_into(const EsPlan& p, const double* grid, int c0, int nc, int kout, const double* corr,
                              double scale, double* out, cudaStream_t st, double* tw, cplx<R>* H) {
@@ -308,7 +308,6 @@ fk_status grid_to_modes_into(const EsPlan& p, const double* grid, int c0, int nc
   const size_t sm = static_cast<size_t>(N) * sizeof(cplx<R>);
   if (sm > 200 * 1024) return set_error(FK_EINVAL, "fine grid %d too long for one CTA", N);
   const int corr_off = p.kmax - kout;
-  FK_TRY(fft_twiddles(N, tw, st));
   const int K = 2 * kout + 1;
   if (p.d == 1) {
     FK_TRY(set_smem<R>((const void*)k_t1_1d<R>, sm));
@@ -326,6 +325,18 @@ fk_status grid_to_modes_into(const EsPlan& p, const double* grid, int c0, int nc
   }
   return FK_OK;
 }
+fk_status preload_modes_kernels() {
+  cudaFuncAttributes fa;
+  FK_CUDA(cudaFuncGetAttributes(&fa, k_twiddles));
+  FK_CUDA(cudaFuncGetAttributes(&fa, k_t1_1d<float>));
+  FK_CUDA(cudaFuncGetAttributes(&fa, k_t1_1d<double>));
+  FK_CUDA(cudaFuncGetAttributes(&fa, k_t1_2d_rows<float>));
+  FK_CUDA(cudaFuncGetAttributes(&fa, k_t1_2d_rows<double>));
+  FK_CUDA(cudaFuncGetAttributes(&fa, k_t1_2d_cols<float>));
+  FK_CUDA(cudaFuncGetAttributes(&fa, k_t1_2d_cols<double>));
+  return FK_OK;
+}
+
 template fk_status grid_to_modes_into<float>(const EsPlan&, const double*, int, int, int, const double*, double,
                                              double*, cudaStream_t, double*, cplx<float>*);
 template fk_status grid_to_modes_into<double>(const EsPlan&, const double*, int, int, int, const double*, double,

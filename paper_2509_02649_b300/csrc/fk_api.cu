@@ -118,11 +118,12 @@ static fk_opts resolve_opts(const fk_opts* o) {
   if (r.cg_maxit <= 0) r.cg_maxit = 1000;
   if (r.refine_steps < 0) r.refine_steps = 0;
   if (r.upsampfac <= 1.0) r.upsampfac = 1.9;
+  if (r.wait_cycles < 0) r.wait_cycles = 0;
   if (capture_ctx()) r.autotune = 0;  // tuning times kernels on the host clock
   return r;
 }
 
-static fk_status check_common(int d, int64_t n, int m, double eps, int precision) {
+fk_status check_common(int d, int64_t n, int m, double eps, int precision) {
   if (d < 1 || d > 3) return set_error(FK_EINVAL, "d = %d: transforms are built for d in {1, 2, 3}", d);
   if (n < 1) return set_error(FK_EINVAL, "n = %lld < 1", (long long)n);
   if (m < 0) return set_error(FK_EINVAL, "m = %d < 0", m);
@@ -238,11 +239,17 @@ static fk_status build_system(int d, int64_t n, const void* x, const void* y, in
   FK_TRY(scr.alloc(&corr, 2 * static_cast<size_t>(p.kmax) + 1));
   FK_TRY(es_correction(p, corr, st));
   if (tm) tm->mark();
-  FK_TRY(spread_any(p, precision, o, n, x, y, n_targets, true, grid, flags, st, scr));
+  {
+    NvtxRange r("fk spread");
+    FK_TRY(spread_any(p, precision, o, n, x, y, n_targets, true, grid, flags, st, scr));
+  }
   if (tm) tm->mark();
-  const double inv_n = 1.0 / static_cast<double>(n);
-  FK_TRY(modes_any(p, precision, grid, 0, 1, 2 * m, corr, inv_n, T, st, scr));
-  if (n_targets > 0) FK_TRY(modes_any(p, precision, grid, 1, n_targets, m, corr, inv_n, b, st, scr));
+  {
+    NvtxRange r("fk transform");
+    const double inv_n = 1.0 / static_cast<double>(n);
+    FK_TRY(modes_any(p, precision, grid, 0, 1, 2 * m, corr, inv_n, T, st, scr));
+    if (n_targets > 0) FK_TRY(modes_any(p, precision, grid, 1, n_targets, m, corr, inv_n, b, st, scr));
+  }
   if (tm) tm->mark();
   return FK_OK;
 }
@@ -264,6 +271,7 @@ void fk_default_opts(fk_opts* o) {
   o->spread = FK_SPREAD_AUTO;
   o->deterministic = 0;
   o->autotune = 0;
+  o->wait_cycles = 0;
 }
 
 const char* fk_last_error(void) { return g_err.c_str(); }
@@ -449,8 +457,11 @@ static fk_status fit_common(int d, int64_t n, const void* x, const void* y, int 
   }
   int iters = 0;
   double rr = 0;
-  FK_TRY(solve_system(d, m, T, W, n_lambda, b, n_targets, o, theta, st, scr, fl.dev, &iters, rep ? &rr : nullptr,
-                      cmom ? &op : nullptr));
+  {
+    NvtxRange r("fk solve");
+    FK_TRY(solve_system(d, m, T, W, n_lambda, b, n_targets, o, theta, st, scr, fl.dev, &iters, rep ? &rr : nullptr,
+                        cmom ? &op : nullptr));
+  }
   tm.mark();
   FK_TRY(fl.check());
   if (rep) {
@@ -679,6 +690,7 @@ fk_status fk_accum_add(fk_accum* a, int64_t n, const void* x, const void* y, con
   if (!x || (a->nt > 0 && !y)) return set_error(FK_EINVAL, "null points or targets");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   FK_TRY(capture_check(st, false, false, "fk_accum_add"));
+  NvtxRange range("fk accum add");
   Scratch scr(st);
   const EsPlan& p = a->p;
   if (a->precision == FK_MIXED && a->d == 1 && a->o.spread != FK_SPREAD_ATOMIC &&

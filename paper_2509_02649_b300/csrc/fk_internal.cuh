@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/fk.h"
 
 namespace fk {
@@ -17,6 +19,9 @@ namespace fk {
 // ------------------------------------------------------------------ errors
 fk_status set_error(fk_status st, const char* fmt, ...);
 void clear_error();
+// Host-side checks shared by the entry points: d in {1, 2, 3}, n >= 1, m >= 0,
+// eps in [1e-14, 1e-1], a known precision (FK_EINVAL with a message otherwise).
+fk_status check_common(int d, int64_t n, int m, double eps, int precision);
 // Process-wide count of kernels this library has launched (fk_launch_count).
 void note_launch();
 
@@ -29,6 +34,15 @@ struct KernelTimer {
   unsigned rec_flags = 0;  // cudaEventRecordExternal during a capture (event record nodes)
 };
 KernelTimer* kernel_timer();  // thread-local
+
+// Named range around a host-side stage of a call (spreading, transform, solve, ...),
+// shown on profilers' timelines; NVTX calls cost nothing when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 #define FK_CUDA(call)                                                          \
   do {                                                                         \
@@ -240,8 +254,17 @@ fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, 
                        const PenOp* op = nullptr);
 
 // Variants with caller-supplied scratch (used by the entry point that allocates nothing).
-fk_status es_correction_into(const EsPlan& p, double* corr, double* gl_scratch, cudaStream_t st);
+// es_gl_nodes_into writes the 2 es_gl_nodes() quadrature nodes and weights that
+// es_correction_from_nodes reads.
+fk_status es_gl_nodes_into(double* gl, cudaStream_t st);
+fk_status es_correction_from_nodes(const EsPlan& p, double* corr, const double* gl, cudaStream_t st);
 int es_gl_nodes();
+// Force the lazy loading of the kernels the entry point without allocation launches
+// (the ES tables, the atomic spreaders, the twiddles and the type-1 mode extraction),
+// so that its later calls need no device memory for code.
+fk_status preload_es_kernels();
+fk_status preload_spread_atomic_kernels();
+fk_status preload_modes_kernels();
 template <typename R>
 fk_status grid_to_modes_into(const EsPlan& p, const double* grid, int c0, int nc, int kout, const double* corr,
                              double scale, double* out, cudaStream_t st, double* tw, cplx<R>* H);

@@ -1477,7 +1477,7 @@ namespace fk {
 // the true residual |b - A x|.  The barrier's wait is bounded (FK_ETIMEOUT).
 namespace {
 
-constexpr long long BAR_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+constexpr long long BAR_WAIT_CYCLES = 4000000000LL;  // default bound of a barrier wait: ~2 s at 2 GHz
 
 struct GridBar {
   unsigned count, unused;  // count: arrivals since the launch (zeroed before it)
@@ -1515,6 +1515,7 @@ struct CgP {
   const double* Tc;
   const double* Cc;
   cplx<double>* corr;
+  long long wait;  // bound of each grid-barrier wait in SM cycles (0: BAR_WAIT_CYCLES)
 };
 
 // all CTAs of the launch; false when the wait gave up (the caller returns)
@@ -1523,7 +1524,8 @@ struct CgP {
 // arrival.  The CTA barrier orders the block's writes before thread 0's releasing
 // arrival, and thread 0's acquiring loads order the later barrier's reads after every
 // other CTA's arrival, so no thread needs a separate fence.
-__device__ bool grid_sync(GridBar* gb, unsigned* flags) {
+__device__ bool grid_sync(GridBar* gb, unsigned* flags, long long wait) {
+  const long long limit = wait > 0 ? wait : BAR_WAIT_CYCLES;
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1540,7 +1542,7 @@ __device__ bool grid_sync(GridBar* gb, unsigned* flags) {
         ok = 0;
         break;
       }
-      if (clock64() - t0 > BAR_WAIT_CYCLES) {
+      if (clock64() - t0 > limit) {
         atomicOr(flags, FLAG_TIMEOUT);
         ok = 0;
         break;
@@ -1918,18 +1920,18 @@ __global__ void __launch_bounds__(256) k_cg_persist2d(CgP A) {
   double T0 = __ldg(A.T0p);
   if (!(T0 > 0.0)) T0 = 1.0;
   cgp_init(A, red, T0);
-  if (!grid_sync(A.bar, A.flags)) return;
+  if (!grid_sync(A.bar, A.flags, A.wait)) return;
   int it = 0;
   for (; it < A.maxit; ++it) {
     bool any = false;
     for (int s = 0; s < A.nsys && !any; ++s) any = cg_active(A, it, s);
     if (!any) break;
     cgp_rows_fwd(A, sl, red, it, false);
-    if (!grid_sync(A.bar, A.flags)) return;
+    if (!grid_sync(A.bar, A.flags, A.wait)) return;
     cgp_cols(A, sl, red, it, false);
-    if (!grid_sync(A.bar, A.flags)) return;
+    if (!grid_sync(A.bar, A.flags, A.wait)) return;
     cgp_rows_inv(A, sl, red, it, false);
-    if (!grid_sync(A.bar, A.flags)) return;
+    if (!grid_sync(A.bar, A.flags, A.wait)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     int left = 0;
@@ -1941,9 +1943,9 @@ __global__ void __launch_bounds__(256) k_cg_persist2d(CgP A) {
   if (!A.final_residual) return;
   // true residual of the result
   cgp_rows_fwd(A, sl, red, it, true);
-  if (!grid_sync(A.bar, A.flags)) return;
+  if (!grid_sync(A.bar, A.flags, A.wait)) return;
   cgp_cols(A, sl, red, it, true);
-  if (!grid_sync(A.bar, A.flags)) return;
+  if (!grid_sync(A.bar, A.flags, A.wait)) return;
   cgp_rows_inv(A, sl, red, it, true);
 }
 
@@ -2041,6 +2043,7 @@ fk_status cg_solve_persistent(int m, const double* T, const double* W, int n_w, 
   FK_TRY(scr.alloc(&A.r, 2 * D * nsys));
   FK_TRY(scr.alloc(&A.idg, D * n_w));
   A.final_residual = relres_out != nullptr;
+  A.wait = o.wait_cycles;
   FK_TRY(scr.alloc(&A.z, 2 * D * nsys));
   FK_TRY(scr.alloc(&A.p, 2 * D * nsys));
   FK_TRY(scr.alloc(&A.q, 2 * D * nsys));
@@ -2106,6 +2109,7 @@ struct TsP {
   double* x;      // [D] complex, b in / solution out
   GridBar* bar;
   unsigned* flags;
+  long long wait;  // bound of each grid-barrier wait in SM cycles (0: BAR_WAIT_CYCLES)
 };
 
 // all threads of CTA 0: stage the diagonal block, or its inverse (independent loads in
@@ -2197,7 +2201,7 @@ __global__ void __launch_bounds__(256) k_trisolve_coop(TsP A) {
       __syncthreads();
       if (threadIdx.x < 32) ts_diag(A, kb0, nb0, fwd, dg);
     }
-    if (!grid_sync(A.bar, A.flags)) return;
+    if (!grid_sync(A.bar, A.flags, A.wait)) return;
     for (int s = 0; s < nblocks; ++s) {
       const int bi = fwd ? s : nblocks - 1 - s;
       const int kb = bi * TS_NB, nb = min(TS_NB, D - kb);
@@ -2248,7 +2252,7 @@ __global__ void __launch_bounds__(256) k_trisolve_coop(TsP A) {
           update(rr);
         }
       }
-      if (!grid_sync(A.bar, A.flags)) return;
+      if (!grid_sync(A.bar, A.flags, A.wait)) return;
     }
   }
 }

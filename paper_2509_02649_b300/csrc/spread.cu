@@ -129,6 +129,13 @@ fk_status spread_atomic(const EsPlan& p, int64_t n, const R* x, const R* y, int 
   FK_CUDA(cudaGetLastError());
   return FK_OK;
 }
+fk_status preload_spread_atomic_kernels() {
+  cudaFuncAttributes fa;
+  FK_CUDA(cudaFuncGetAttributes(&fa, k_spread_atomic<float>));
+  FK_CUDA(cudaFuncGetAttributes(&fa, k_spread_atomic<double>));
+  return FK_OK;
+}
+
 template fk_status spread_atomic<float>(const EsPlan&, int64_t, const float*, const float*, int, bool, double*,
                                         unsigned*, cudaStream_t);
 template fk_status spread_atomic<double>(const EsPlan&, int64_t, const double*, const double*, int, bool,

@@ -72,6 +72,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsign
     }
   }
 }
+// After a wait gave up (the flag is set): wait once more, with the same bound, for the
+// bulk copy that the phase still expects, so that the CTA does not exit while a copy
+// into its shared memory is in flight.  Each kernel here has at most one copy in
+// flight when it waits (the next one is issued after the wait succeeds), so this is
+// the last wait before the CTA returns; its result is ignored.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, unsigned parity) {
+  const long long t0 = clock64();
+  while (true) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done || clock64() - t0 > WAIT_CYCLES) return;
+  }
+}
 // global -> shared bulk copy (TMA), completion counted in bytes on `bar`
 __device__ __forceinline__ void bulk_g2s(void* sdst, const void* gsrc, unsigned bytes, uint64_t* bar) {
   asm volatile(
@@ -469,7 +486,10 @@ __global__ void __launch_bounds__(S2_THREADS, 1) k_bin_scatter2(PartArgs A) {
   for (int64_t t0 = s0; t0 < e0; t0 += S2_TILE) {
     const int cnt = static_cast<int>(min(static_cast<int64_t>(S2_TILE), e0 - t0));
     for (int o = tid; o <= G; o += S2_THREADS) tcnt[o] = 0;
-    if (!mbar_wait(bar, phase, A.flags)) return;
+    if (!mbar_wait(bar, phase, A.flags)) {
+      mbar_drain(bar, phase);
+      return;
+    }
     phase ^= 1u;
     __syncthreads();
     uint4 rec[S2_PER];
@@ -572,7 +592,10 @@ __global__ void __launch_bounds__(T, 1024 / T) k_bin_scatter1(PartArgs A) {
   for (int64_t t0 = s0; t0 < e0; t0 += TILE) {
     const int cnt = static_cast<int>(min(static_cast<int64_t>(TILE), e0 - t0));
     for (int o = tid; o <= G; o += T) tcnt[o] = 0;
-    if (!mbar_wait(bar, phase, A.flags)) return;
+    if (!mbar_wait(bar, phase, A.flags)) {
+      mbar_drain(bar, phase);
+      return;
+    }
     phase ^= 1u;
     __syncthreads();
     // rk: the point's rank among the tile's points of its owner (its place in the
@@ -827,7 +850,10 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
     const int nc = min(s_ncar[buf], CARRY);
     if (!mbar_wait(&s_bar[buf], (r >> 1) & 1, A.flags)) s_abort = 1;
     __syncthreads();
-    if (s_abort) return;
+    if (s_abort) {
+      mbar_drain(&s_bar[buf], (r >> 1) & 1);
+      return;
+    }
     if (tid == 0 && r + 1 < nrounds) issue(r + 1);
     // records of this round: [CARRY - nc, CARRY + nr) of the buffer, the ones deferred
     // from the last round in front

@@ -148,3 +148,16 @@ def test_additive_full_size_closed_form():
     f = fk.fk_predict(theta, xq, m, 1e-6, "mixed", additive=True).reshape(-1).cpu().numpy()
     fstar = sum(torch.sin((j + 1) * xq[j]) / (j + 1) for j in range(d)).cpu().numpy().astype(np.float64)
     assert np.sqrt(np.mean((f - fstar) ** 2)) < 2e-3
+
+
+def test_mixed_fit_within_gate_against_accurate_fp64_reference():
+    """The metric's gate for the mixed path (rel err of theta <= 1e-5) against a reference
+    accurate well below it: the FP64 path at eps = 1e-12, which the parity tests gate at
+    <= 1e-10 against the oracle at small n.  2-D Sobolev workload at n = 1e7."""
+    n, m, s, lam = 10_000_000, 32, 2.0, 1e-6
+    x = uniform(n, 2, 71)
+    y = torch.exp(-(x * x).sum(0)) + 0.05 * normal(n, 72)[0]
+    th_mixed = fk.fk_fit_sobolev(x, y, m, s, [lam], 1e-6, "mixed")
+    th_ref = fk.fk_fit_sobolev(x.double(), y.double(), m, s, [lam], 1e-12, "fp64")
+    err = float(torch.linalg.norm(th_mixed - th_ref) / torch.linalg.norm(th_ref))
+    assert err <= 1e-5, err
