@@ -98,6 +98,7 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
     FK_TRY(scr.alloc(&amax, static_cast<size_t>(nt)));
     FK_TRY(absmax_channels(n, reinterpret_cast<const float*>(y), nt, amax, st));
   }
+  NvtxRange stage_range("fk additive 1-D");
   for (int l = 0; l < d; ++l) {
     Scratch inner(st);  // released (stream-ordered) after each coordinate
     if (fixed1d)
@@ -124,13 +125,33 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
   FK_TRY(scr.alloc(&corr2, 2 * static_cast<size_t>(p2.kmax) + 1));
   FK_TRY(scr.alloc(&grid2, static_cast<size_t>(p2.N) * p2.N));
   FK_TRY(scr.alloc(&Bp, 2 * static_cast<size_t>(npairs > 0 ? npairs : 1) * K * K));
-  // mixed path: the partition reads X_l1 and X_l2 in place; otherwise the pair's
-  // points are gathered into (X_l1, -X_l2) rows first
-  const bool binned2 = precision == FK_MIXED && o.spread != FK_SPREAD_ATOMIC && spread_binned_supported(p2, 0, true);
-  if (!binned2) FK_TRY(scr.alloc(&pts, 2 * static_cast<size_t>(n)));
+  // mixed path: one partition per first coordinate l1 serves all its partners (row
+  // owners), or else one partition per pair reading X_l1 and X_l2 in place; otherwise
+  // the pair's points are gathered into (X_l1, -X_l2) rows first
+  const bool mixed_binned = precision == FK_MIXED && o.spread != FK_SPREAD_ATOMIC;
+  const bool rowpairs = mixed_binned && additive_pairs_supported(p2, d, n);
+  const bool binned2 = mixed_binned && !rowpairs && spread_binned_supported(p2, 0, true);
+  if (!binned2 && !rowpairs) FK_TRY(scr.alloc(&pts, 2 * static_cast<size_t>(n)));
   FK_TRY(es_correction(p2, corr2, st));
+  stage_range.next("fk additive pairs");
+  if (rowpairs) {
+    const int64_t NN = static_cast<int64_t>(p2.N) * p2.N;
+    AddPairState S;
+    double* pg = nullptr;
+    FK_TRY(scr.alloc(&pg, static_cast<size_t>(d - 1) * NN));
+    FK_TRY(additive_pairs_begin(p2, d, n, reinterpret_cast<const float*>(x), flags, st, scr, &S));
+    int pair = 0;
+    for (int l1 = 0; l1 + 1 < d; ++l1) {
+      FK_TRY(additive_pairs_row(S, l1, pg, flags, st));
+      for (int l2 = l1 + 1; l2 < d; ++l2, ++pair) {
+        Scratch inner(st);
+        FK_TRY(grid_to_modes<float>(p2, pg + (l2 - l1 - 1) * NN, 0, 1, m, corr2, inv_n,
+                                    Bp + 2 * static_cast<int64_t>(pair) * K * K, st, inner));
+      }
+    }
+  }
   int pair = 0;
-  for (int l1 = 0; l1 < d; ++l1)
+  for (int l1 = 0; l1 < d && !rowpairs; ++l1)
     for (int l2 = l1 + 1; l2 < d; ++l2, ++pair) {
       Scratch inner(st);  // released (stream-ordered) after each pair
       if (!binned2) {
@@ -154,6 +175,7 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
     }
   if (rep) cudaEventRecord(ev[1], st);
   // block Gram + lambda I, dense solve per lambda
+  stage_range.next("fk additive solve");
   double* A = nullptr;
   FK_TRY(scr.alloc(&A, 2 * Dall * Dall));
   for (int li = 0; li < n_lambda; ++li) {

@@ -40,6 +40,10 @@ KernelTimer* kernel_timer();  // thread-local
 struct NvtxRange {
   explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
   ~NvtxRange() { nvtxRangePop(); }
+  void next(const char* name) {  // ends this range and starts the next stage's
+    nvtxRangePop();
+    nvtxRangePushA(name);
+  }
   NvtxRange(const NvtxRange&) = delete;
   NvtxRange& operator=(const NvtxRange&) = delete;
 };
@@ -207,6 +211,26 @@ bool spread_binned_supported(const EsPlan& p, int n_y, bool with_ones);
 fk_status spread_binned_xy(const EsPlan& p, int64_t n, const float* x0, const float* x1, float s1, const float* y,
                            int n_y, bool with_ones, double* grid, unsigned* flags, cudaStream_t st,
                            Scratch& scratch, bool autotune = false);
+
+// Pair grids of the additive model (Sec. 5): for l1 < d - 1, the N x N grids of ones at
+// (X_l1, -X_l2) for the partners l2 = l1 + 1 .. d - 1, from one partition of the points
+// by the rows of coordinate l1 (mixed path, N <= 256, 4 <= w <= 8).  begin allocates the
+// record streams in scr and counts coordinate 0's rows; row(l1) must follow for
+// l1 = 0, 1, .. in order (each partition counts the next coordinate's rows) and writes
+// the d - 1 - l1 grids [partner][N^2] (zeroed inside).
+struct AddPairState {
+  EsPlan p;
+  int d = 0, G = 0;
+  int64_t n = 0, stride = 0;
+  const float* x = nullptr;  // SoA rows [d][n]
+  int* cnt = nullptr;        // [3][G]: counts of two coordinates' row owners, reservations
+  unsigned* o1 = nullptr;    // [stride] row words
+  unsigned* code = nullptr;  // [d - 1][stride] code words
+};
+bool additive_pairs_supported(const EsPlan& p, int d, int64_t n);
+fk_status additive_pairs_begin(const EsPlan& p, int d, int64_t n, const float* x, unsigned* flags, cudaStream_t st,
+                               Scratch& scr, AddPairState* S);
+fk_status additive_pairs_row(AddPairState& S, int l1, double* grids, unsigned* flags, cudaStream_t st);
 
 // 1-D fixed-point shared-memory spreading (fp32 inputs, any channel count).  y_absmax:
 // device array of max|y_c| bit patterns for the n_y strength channels, or null to

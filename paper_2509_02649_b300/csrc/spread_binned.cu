@@ -189,15 +189,19 @@ __device__ __forceinline__ bool skip_guarded(const PartArgs& A) {
 struct Rec16 {
   using T = uint4;
   static constexpr bool HAS_Y = true, SPLIT_Y = false;
+  static constexpr int NP_THREADS = THREADS_ACC;  // CTA size (= cells) without pair mode
   static constexpr int CAPR = 4096, CARRY = 2048;
   __device__ static int cell(const uint4& r) { return static_cast<int>(r.x & 0xFFFFu); }
   __device__ static float g0(const uint4& r, float gc) { return __uint_as_float(r.y) - gc; }
   __device__ static float g1(const uint4& r, float gc) { return __uint_as_float(r.z) - gc; }
   __device__ static float y(const uint4& r) { return __uint_as_float(r.w); }
+  // first coordinate's offset given the parallel stream (unused by this type)
+  __device__ static float g0x(const uint4& r, const float*, int, float gc) { return g0(r, gc); }
 };
 struct Rec8 {
   using T = uint2;
   static constexpr bool HAS_Y = false, SPLIT_Y = false;
+  static constexpr int NP_THREADS = THREADS_ACC;
   static constexpr int CAPR = 10240, CARRY = 2048;
   __device__ static int cell(const uint2& r) { return static_cast<int>(r.y >> 16); }
   __device__ static float g0(const uint2& r, float) {
@@ -207,12 +211,33 @@ struct Rec8 {
     return fmaf(static_cast<float>(__funnelshift_r(r.x, r.y, 24) & 0xFFFFFFu), -5.9604644775390625e-8f, 0.5f);
   }
   __device__ static float y(const uint2&) { return 1.0f; }
+  __device__ static float g0x(const uint2& r, const float*, int, float gc) { return g0(r, gc); }
 };
 // Rec8 records with the strengths in a parallel stream of floats (same indices):
 // 12 bytes per point, 8192 records per round (and up to 512 deferred ones in front)
 struct Rec8Y : Rec8 {
   static constexpr bool HAS_Y = true, SPLIT_Y = true;
   static constexpr int CAPR = 8192, CARRY = 512;
+};
+// Additive-model pair records (owners of two grid rows).  The record is the column
+// coordinate's code word  r << 31 | c2 << 23 | v2  (r: the row inside the owner's two
+// rows, c2: the window-start column, v2 = (w/2 - f2) 2^23) and the parallel stream holds
+// the row coordinate's word  o1 = c1 << 24 | v1  (c1: window-start row, v1 = (w/2 - f1)
+// 2^23, bit 23 clear).  f in (w/2 - 1, w/2] is a multiple of 2^-23 for f >= 1 (fp32
+// spacing), so both offsets are exact for w >= 4, and g = f - (w-1)/2 = 1.5 - (1 + v 2^-23)
+// decodes with one OR and one (exact) subtraction.
+struct RecAdd {
+  using T = unsigned;
+  static constexpr bool HAS_Y = false, SPLIT_Y = true;
+  static constexpr int NP_THREADS = 512;  // one lane per cell of two 256-node rows
+  static constexpr int CAPR = 10240, CARRY = 1024;
+  __device__ static int cell(unsigned r) { return static_cast<int>(r >> 23); }
+  __device__ static float g0(unsigned, float) { return 0.0f; }  // (in the parallel stream)
+  __device__ static float g1(unsigned r, float) { return 1.5f - __uint_as_float(0x3F800000u | (r & 0x7FFFFFu)); }
+  __device__ static float y(unsigned) { return 1.0f; }
+  __device__ static float g0x(unsigned, const float* par, int i, float) {
+    return 1.5f - __uint_as_float(0x3F800000u | (__float_as_uint(par[i]) & 0x7FFFFFu));
+  }
 };
 // Rec8 of a Rec16 {key, f0, f1, -} built by the partition (w: kernel width)
 __device__ __forceinline__ uint2 pack_rec8(const uint4& r, float half_w) {
@@ -703,6 +728,12 @@ struct AccArgs {
   int cap, cap_s;
   const unsigned* ovf;
   float qmul;  // per-round quota = mean load + qmul sqrt(mean load)
+  // several problems sharing the owner layout in one launch: CTA (b, sub) with
+  // b = blockIdx / nsub; problem sub reads rec + sub sub_rec_stride (the parallel stream
+  // ybuf is shared) and adds into grid + sub sub_grid_stride
+  int nsub;
+  int64_t sub_rec_stride, sub_grid_stride;
+  int pad4;  // exact buckets (mode 0) start at multiples of 4 records (16-byte copies)
 };
 
 struct AccLayout {
@@ -724,17 +755,21 @@ __host__ __device__ inline AccLayout acc_layout(int cpc) {
 }
 
 template <int W, bool PAIR, typename R>
-__global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArgs A) {
+__global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) k_bin_accumulate(AccArgs A) {
   static_assert(!PAIR || R::HAS_Y, "pair mode carries a strength");
   using RT = typename R::T;
-  constexpr int THREADS = Cfg<PAIR>::THREADS;
+  constexpr int THREADS = PAIR ? Cfg<true>::THREADS : R::NP_THREADS;
   constexpr int CAPR = R::CAPR, CARRY = R::CARRY;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_base, s_count, s_abort;
   __shared__ int s_ncar[2];  // records deferred into buffer b (counted during the round before)
   __shared__ __align__(8) uint64_t s_bar[2];
   const int tid = threadIdx.x, lane = tid & 31;
-  const int b = blockIdx.x;
+  const int nsub = A.nsub > 0 ? A.nsub : 1;
+  const int b = blockIdx.x / nsub;
+  const int sub = blockIdx.x - b * nsub;
+  const typename R::T* recs = reinterpret_cast<const typename R::T*>(A.rec) + sub * A.sub_rec_stride;
+  double* grid_s = A.grid + sub * A.sub_grid_stride;
   const int N = A.N;
   const int cpc = A.cpc_max;
   const int cell = PAIR ? (tid >> 1) : tid;
@@ -770,7 +805,7 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
     // bucket of this owner = [sum of earlier totals, + tot[b]): one load per thread
     __shared__ int wsum[32];
     int v = 0;
-    for (int o = tid; o < b; o += THREADS) v += __ldg(A.tot + o);
+    for (int o = tid; o < b; o += THREADS) v += A.pad4 ? ((__ldg(A.tot + o) + 3) & ~3) : __ldg(A.tot + o);
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
     if (lane == 0) wsum[tid >> 5] = v;
@@ -811,7 +846,7 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
     const int64_t GN = static_cast<int64_t>(N) * N;
     const int c0 = key / N;
     const int c1 = key - c0 * N;
-    double* g = A.grid + (PAIR ? ch : 0) * GN;
+    double* g = grid_s + (PAIR ? ch : 0) * GN;
     const bool transposed = PAIR && ch == 1;
 #pragma unroll
     for (int i = 0; i < W; ++i)
@@ -833,7 +868,7 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
     const unsigned ybytes = R::SPLIT_Y ? ((static_cast<unsigned>(nr) * 4u + 15u) & ~15u) : 0u;
     fence_proxy_async();
     mbar_arrive_expect(&s_bar[r & 1], bytes + ybytes);
-    bulk_g2s(dst, reinterpret_cast<const RT*>(A.rec) + base + static_cast<int64_t>(r) * CAPR, bytes, &s_bar[r & 1]);
+    bulk_g2s(dst, recs + base + static_cast<int64_t>(r) * CAPR, bytes, &s_bar[r & 1]);
     if (R::SPLIT_Y)
       bulk_g2s(ystage + (r & 1) * (CARRY + CAPR) + CARRY, A.ybuf + base + static_cast<int64_t>(r) * CAPR, ybytes,
                &s_bar[r & 1]);
@@ -956,7 +991,7 @@ __global__ void __launch_bounds__(Cfg<PAIR>::THREADS, 1) k_bin_accumulate(AccArg
             const RT rec = st[ir];
             ri = nxt[ir];
             float px[W], py[W];
-            es_taps_poly<W>(R::g0(rec, gc), A.poly, px);
+            es_taps_poly<W>(R::g0x(rec, yst, ir, gc), A.poly, px);
             es_taps_poly<W>(R::g1(rec, gc), A.poly, py);
             if (!ONES) {
               float sv;
@@ -1318,6 +1353,338 @@ fk_status spread_binned_xy(const EsPlan& p, int64_t n, const float* x, const flo
   log += line;
   tune_store(key, best, log);
   return spread_binned_run(p, n, x, x1, s1, y, n_y, with_ones, grid, flags, st, scr, best);
+}
+
+}  // namespace fk
+
+// ---------------------------------------------------------------- additive-model pairs
+// The 2-D transforms of ones at (X_l1, -X_l2), l2 > l1 (Sec. 5, Complexity), grouped by
+// their first coordinate l1.  Owners are pairs of grid rows of coordinate l1, so a
+// point has the same owner for every partner l2: one partition per l1 sorts the points
+// by row owner and writes the row word once plus one code word per partner (RecAdd),
+// and one accumulation launch runs the (owner, partner) CTAs of all partners of l1.
+// Bucket sizes are exact, counted before the partition (coordinate 0 by k_add_count,
+// coordinate l1 + 1 by the partition of l1, which reads it as its first partner), so
+// no bucket overflows; buckets start at multiples of 4 records for the 16-byte copies.
+namespace fk {
+namespace {
+
+constexpr int AP_THREADS = 512;               // partition CTA (two per SM)
+constexpr int AP_PER = 4;                     // points per thread and tile
+constexpr int AP_TILE = AP_THREADS * AP_PER;  // 2048
+
+struct AddPartArgs {
+  int N, W, G, P;   // grid nodes per dimension (<= 256), width, row owners (N / 2), partners
+  int64_t n;
+  const float* xl1;  // coordinate l1 (n floats); partner p is the row xl1 + (1 + p) n
+  int vec_ok;        // 16-byte aligned rows and n % 4 == 0: bulk copies of the tiles
+  int64_t range;     // points per CTA (multiple of 4)
+  const int* cnt;    // [G] exact bucket sizes of this l1
+  int* fill;         // [G] reservation counters (zeroed)
+  int* cnt_next;     // [G] (zeroed) counts of the row owners of coordinate l1 + 1, or null
+  unsigned* o1;      // row words, bucketed
+  unsigned* code;    // [P][stride] code words, bucketed like o1
+  int64_t stride;
+  unsigned* flags;
+  float c_hi, c_lo;
+};
+
+// window of one coordinate on the pair grid: window-start node and the 23-bit offset
+// v = (w/2 - f) 2^23 (exact for w >= 4); false outside [-3 pi, 3 pi)
+__device__ __forceinline__ bool add_window(float x, const AddPartArgs& A, int* node, unsigned* v) {
+  int l0;
+  float f;
+  if (!window_f32(x, A.N, A.c_hi, A.c_lo, A.W, &l0, &f)) return false;
+  *node = wrap_node(l0, A.N);
+  *v = static_cast<unsigned>((0.5f * static_cast<float>(A.W) - f) * 8388608.0f);
+  return true;
+}
+
+// row owners of coordinate xl1 counted into cnt_next
+__global__ void __launch_bounds__(512) k_add_count(AddPartArgs A) {
+  __shared__ int h[256];
+  for (int o = threadIdx.x; o < A.G; o += blockDim.x) h[o] = 0;
+  __syncthreads();
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < A.n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int c;
+    unsigned v;
+    if (add_window(__ldg(A.xl1 + i), A, &c, &v)) atomicAdd(&h[c >> 1], 1);
+    else atomicOr(A.flags, FLAG_RANGE);
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < A.G; o += blockDim.x)
+    if (h[o]) atomicAdd(A.cnt_next + o, h[o]);
+}
+
+struct ApLayout {
+  size_t stage, srow, scode, base, tcnt, toff, hnext, gdelta, bar, total;
+};
+__host__ __device__ inline ApLayout ap_layout(int P, int G) {
+  ApLayout L;
+  L.stage = 0;                                                     // float [P + 1][AP_TILE]
+  L.srow = L.stage + sizeof(float) * (P + 1) * AP_TILE;            // unsigned [AP_TILE]
+  L.scode = L.srow + sizeof(unsigned) * AP_TILE;                   // unsigned [AP_TILE]
+  L.base = L.scode + sizeof(unsigned) * AP_TILE;                   // int [G]
+  L.tcnt = L.base + sizeof(int) * G;                               // int [G + 1]
+  L.toff = L.tcnt + sizeof(int) * (G + 1);                         // int [G + 1]
+  L.hnext = L.toff + sizeof(int) * (G + 1);                        // int [G]
+  L.gdelta = (L.hnext + sizeof(int) * G + 7) & ~static_cast<size_t>(7);  // long long [G]
+  L.bar = (L.gdelta + sizeof(long long) * G + 15) & ~static_cast<size_t>(15);
+  L.total = L.bar + 16;
+  return L;
+}
+
+__global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int wsum[AP_THREADS / 32];
+  const int G = A.G, P = A.P, tid = threadIdx.x;
+  const ApLayout L = ap_layout(P, G);
+  float* stage = reinterpret_cast<float*>(smem + L.stage);
+  unsigned* srow = reinterpret_cast<unsigned*>(smem + L.srow);    // row words in owner order
+  unsigned* scode = reinterpret_cast<unsigned*>(smem + L.scode);  // one partner's codes in owner order
+  int* base = reinterpret_cast<int*>(smem + L.base);              // bucket starts
+  int* tcnt = reinterpret_cast<int*>(smem + L.tcnt);              // tile counts
+  int* toff = reinterpret_cast<int*>(smem + L.toff);              // tile run starts
+  int* hnext = reinterpret_cast<int*>(smem + L.hnext);            // counts for the next l1
+  long long* gdelta = reinterpret_cast<long long*>(smem + L.gdelta);  // bucket slot of tile slot 0
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
+  // bucket starts: exclusive scan of the counts padded to 4 (G <= blockDim)
+  {
+    const int lane = tid & 31, warp = tid >> 5;
+    const int v = tid < G ? ((__ldg(A.cnt + tid) + 3) & ~3) : 0;
+    int incl = v;
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, dd);
+      if (lane >= dd) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int pre = 0;
+    for (int w = 0; w < warp; ++w) pre += wsum[w];
+    if (tid < G) {
+      base[tid] = pre + incl - v;
+      hnext[tid] = 0;
+    }
+  }
+  if (tid == 0) {
+    mbar_init(bar);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  const int64_t s0 = static_cast<int64_t>(blockIdx.x) * A.range;
+  const int64_t e0 = min(A.n, s0 + A.range);
+  unsigned phase = 0;
+  for (int64_t t0 = s0; t0 < e0; t0 += AP_TILE) {
+    const int cnt = static_cast<int>(min(static_cast<int64_t>(AP_TILE), e0 - t0));
+    for (int o = tid; o <= G; o += AP_THREADS) tcnt[o] = 0;
+    if (A.vec_ok) {
+      if (tid == 0) {
+        const unsigned bytes = static_cast<unsigned>(cnt) * 4u;  // cnt % 4 == 0
+        fence_proxy_async();
+        mbar_arrive_expect(bar, bytes * static_cast<unsigned>(P + 1));
+        for (int q = 0; q <= P; ++q) bulk_g2s(stage + q * AP_TILE, A.xl1 + q * A.n + t0, bytes, bar);
+      }
+      if (!mbar_wait(bar, phase, A.flags)) {
+        mbar_drain(bar, phase);
+        return;
+      }
+      phase ^= 1u;
+    } else {
+      for (int q = 0; q <= P; ++q)
+        for (int i = tid; i < cnt; i += AP_THREADS) stage[q * AP_TILE + i] = __ldg(A.xl1 + q * A.n + t0 + i);
+    }
+    __syncthreads();
+    // row word and rank of each point inside its owner's run of the tile
+    unsigned w1[AP_PER];
+    int rk[AP_PER];
+#pragma unroll
+    for (int k = 0; k < AP_PER; ++k) {
+      const int i = k * AP_THREADS + tid;
+      w1[k] = 0xFFFFFFFFu;
+      rk[k] = 0;
+      if (i < cnt) {
+        int c;
+        unsigned v;
+        if (add_window(stage[i], A, &c, &v)) {
+          w1[k] = (static_cast<unsigned>(c) << 24) | v;
+          rk[k] = atomicAdd(&tcnt[c >> 1], 1);
+        } else {
+          atomicOr(A.flags, FLAG_RANGE);
+        }
+        if (A.cnt_next && add_window(stage[AP_TILE + i], A, &c, &v)) atomicAdd(&hnext[c >> 1], 1);
+      }
+    }
+    __syncthreads();
+    // bucket room: one global atomic per owner present; exclusive scan of the tile counts
+    int my_c = 0, my_pos = 0;
+    if (tid < G) {
+      my_c = tcnt[tid];
+      if (my_c > 0) my_pos = atomicAdd(A.fill + tid, my_c);
+    }
+    if (tid >= AP_THREADS - 32) {
+      const int ln = tid - (AP_THREADS - 32);
+      const int per = (G + 1 + 31) / 32;
+      const int o0 = ln * per, o1 = min(o0 + per, G + 1);
+      int run = 0;
+      for (int o = o0; o < o1; ++o) run += (o < G) ? tcnt[o] : 0;
+      int incl = run;
+#pragma unroll
+      for (int dd = 1; dd < 32; dd <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, dd);
+        if (ln >= dd) incl += t;
+      }
+      int acc = incl - run;
+      for (int o = o0; o < o1; ++o) {
+        toff[o] = acc;
+        acc += (o < G) ? tcnt[o] : 0;
+      }
+    }
+    __syncthreads();
+    if (tid < G) gdelta[tid] = static_cast<long long>(base[tid]) + my_pos - toff[tid];
+#pragma unroll
+    for (int k = 0; k < AP_PER; ++k)
+      if (w1[k] != 0xFFFFFFFFu) srow[toff[w1[k] >> 25] + rk[k]] = w1[k];
+    __syncthreads();
+    const int valid = toff[G];
+    for (int j = tid; j < valid; j += AP_THREADS) {
+      const unsigned w = srow[j];
+      A.o1[gdelta[w >> 25] + j] = w;
+    }
+    // one code stream per partner, in the same order
+    for (int p = 0; p < P; ++p) {
+#pragma unroll
+      for (int k = 0; k < AP_PER; ++k) {
+        if (w1[k] == 0xFFFFFFFFu) continue;
+        const int i = k * AP_THREADS + tid;
+        int c;
+        unsigned v, code = 0u;
+        if (add_window(-stage[(1 + p) * AP_TILE + i], A, &c, &v))
+          code = ((((w1[k] >> 24) & 1u) * static_cast<unsigned>(A.N) + static_cast<unsigned>(c)) << 23) | v;
+        else
+          atomicOr(A.flags, FLAG_RANGE);
+        scode[toff[w1[k] >> 25] + rk[k]] = code;
+      }
+      __syncthreads();
+      unsigned* out = A.code + p * A.stride;
+      for (int j = tid; j < valid; j += AP_THREADS) out[gdelta[srow[j] >> 25] + j] = scode[j];
+      __syncthreads();
+    }
+  }
+  if (A.cnt_next)
+    for (int o = tid; o < G; o += AP_THREADS)
+      if (hnext[o]) atomicAdd(A.cnt_next + o, hnext[o]);
+}
+
+}  // namespace
+
+bool additive_pairs_supported(const EsPlan& p, int d, int64_t n) {
+  return p.d == 2 && p.N >= 16 && p.N <= 256 && p.w >= 4 && p.w <= 8 && d >= 2 && d <= 16 && n >= 1 &&
+         n + 4LL * 256 + 16 < (static_cast<int64_t>(1) << 31) && sm_count() > 0;
+}
+
+fk_status additive_pairs_begin(const EsPlan& p, int d, int64_t n, const float* x, unsigned* flags, cudaStream_t st,
+                               Scratch& scr, AddPairState* S) {
+  if (!additive_pairs_supported(p, d, n)) return set_error(FK_EINTERNAL, "additive pairs: unsupported shape");
+  *S = AddPairState{};
+  S->p = p;
+  S->d = d;
+  S->n = n;
+  S->x = x;
+  S->G = p.N / 2;
+  S->stride = (n + 4LL * S->G + 16 + 3) & ~static_cast<int64_t>(3);
+  // counts of rows l (current) and l + 1 (next): [2][G]; fill [G]
+  FK_TRY(scr.alloc(&S->cnt, 3 * static_cast<size_t>(S->G)));
+  FK_TRY(scr.alloc(&S->o1, static_cast<size_t>(S->stride)));
+  FK_TRY(scr.alloc(&S->code, static_cast<size_t>(S->stride) * (d - 1)));
+  FK_CUDA(cudaMemsetAsync(S->cnt, 0, sizeof(int) * 3 * S->G, st));
+  AddPartArgs A{};
+  const CoordConst cc = coord_const(p.N);
+  A.N = p.N;
+  A.W = p.w;
+  A.G = S->G;
+  A.n = n;
+  A.xl1 = x;
+  A.cnt_next = S->cnt;  // counts of coordinate 0
+  A.flags = flags;
+  A.c_hi = cc.hi;
+  A.c_lo = cc.lo;
+  k_add_count<<<grid_for(n, 512, 4 * sm_count()), 512, 0, st>>>(A); note_launch();
+  FK_CUDA(cudaGetLastError());
+  return FK_OK;
+}
+
+fk_status additive_pairs_row(AddPairState& S, int l1, double* grids, unsigned* flags, cudaStream_t st) {
+  const EsPlan& p = S.p;
+  const int G = S.G, P = S.d - 1 - l1, N = p.N;
+  if (P < 1) return FK_OK;
+  int* cnt = S.cnt + (l1 & 1) * G;
+  int* cnt_next = S.cnt + ((l1 + 1) & 1) * G;
+  int* fill = S.cnt + 2 * G;
+  const int sms = sm_count();
+  FK_CUDA(cudaMemsetAsync(fill, 0, sizeof(int) * G, st));
+  if (l1 + 2 <= S.d - 1) FK_CUDA(cudaMemsetAsync(cnt_next, 0, sizeof(int) * G, st));
+  AddPartArgs A{};
+  const CoordConst cc = coord_const(N);
+  A.N = N;
+  A.W = p.w;
+  A.G = G;
+  A.P = P;
+  A.n = S.n;
+  A.xl1 = S.x + static_cast<int64_t>(l1) * S.n;
+  A.vec_ok = ((reinterpret_cast<uintptr_t>(S.x) & 15) == 0 && (S.n & 3) == 0) ? 1 : 0;
+  const int nblk = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((S.n + AP_TILE - 1) / AP_TILE, 2LL * sms)));
+  A.range = ((S.n + nblk - 1) / nblk + 3) & ~static_cast<int64_t>(3);
+  A.cnt = cnt;
+  A.fill = fill;
+  A.cnt_next = (l1 + 2 <= S.d - 1) ? cnt_next : nullptr;  // rows of l1 + 1 are needed if it has partners
+  A.o1 = S.o1;
+  A.code = S.code;
+  A.stride = S.stride;
+  A.flags = flags;
+  A.c_hi = cc.hi;
+  A.c_lo = cc.lo;
+  const size_t sm_part = ap_layout(P, G).total;
+  FK_CUDA(cudaFuncSetAttribute(k_add_part, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm_part)));
+  k_add_part<<<nblk, AP_THREADS, sm_part, st>>>(A); note_launch();
+  FK_CUDA(cudaGetLastError());
+
+  // accumulation: CTA (owner b, partner sub), owners of two rows (2N cells, one lane each)
+  FK_CUDA(cudaMemsetAsync(grids, 0, sizeof(double) * N * N * P, st));
+  AccArgs B{};
+  B.N = N;
+  B.G = G;
+  B.om = OwnerMap{G, 2 * N, 2 * N, owner_magic(2 * N), owner_magic(2 * N)};
+  B.cpc_max = 2 * N;
+  B.ncells = N * N;
+  B.beta = static_cast<float>(p.beta);
+  B.poly = es_poly(p.w, p.beta);
+  B.with_ones = 1;
+  B.tot = cnt;
+  B.rec = reinterpret_cast<const uint4*>(S.code);
+  B.ybuf = reinterpret_cast<const float*>(S.o1);
+  B.grid = grids;
+  B.flags = flags;
+  B.mode = 0;
+  B.qmul = 0.5f;
+  B.nsub = P;
+  B.sub_rec_stride = S.stride;
+  B.sub_grid_stride = static_cast<int64_t>(N) * N;
+  B.pad4 = 1;
+  const KFn fn = pick2d<false, RecAdd>(p.w);
+  if (!fn) return set_error(FK_EINVAL, "additive pairs: w = %d not built", p.w);
+  const size_t sm_acc = acc_layout<RecAdd>(2 * N).total;
+  FK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm_acc)));
+  KernelTimer* kt = kernel_timer();
+  if (kt->on) cudaEventRecordWithFlags(kt->start, st, kt->rec_flags);
+  fn<<<G * P, RecAdd::NP_THREADS, sm_acc, st>>>(B); note_launch();
+  if (kt->on) {
+    cudaEventRecordWithFlags(kt->stop, st, kt->rec_flags);
+    kt->recorded = true;
+  }
+  FK_CUDA(cudaGetLastError());
+  return FK_OK;
 }
 
 }  // namespace fk
