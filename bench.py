@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--no-graph", action="store_true", help="skip the graph-replay measurement")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="skip the graph-replay measurements (headline and additive rows)")
     ap.add_argument("--no-rows", action="store_true",
                     help="headline line only (skip the sweep-1d, pik-heat and additive-8d rows)")
     ap.add_argument("--workload", default="2d-sobolev", choices=["2d-sobolev", "sweep-1d", "pik-heat", "additive-8d"],
@@ -391,6 +392,7 @@ def run_row(args, rank, local, W=None, steps=None, warmup=None, peak=None, n=Non
         line["loss_and_grads"] = {"L": res[-1][2][0], "dL/dlambda": res[-1][2][1], "dL/dmu": res[-1][2][2]}
     if W == "additive-8d":
         line["report"] = res[-1][2]
+    if W == "additive-8d" and not args.no_graph:
         # the same fit recorded once into a CUDA graph and replayed: one launch per step
         gst = torch.cuda.Stream()
         gst.wait_stream(st)

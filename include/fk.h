@@ -266,6 +266,27 @@ FK_API fk_status fk_accum_fit_sobolev(fk_accum* acc, double s, int penalty, cons
 FK_API fk_status fk_accum_reset(fk_accum* acc, void* stream);
 FK_API fk_status fk_accum_destroy(fk_accum* acc);
 
+/* Accumulator state on the host: checkpoint / resume of a chunked run, and the
+ * reduction of shards.  The sums of Sec. 2.3 are additive over points, so a run can
+ * stop after any chunk and resume from its saved sums, and shards of the points spread
+ * by separate accumulators (other streams, devices or processes) combine by adding
+ * their sums; fk_accum_system then divides by the total point count.
+ *   fk_accum_state_bytes: size of the state (a 64-byte header, then the fp64 grids
+ *     [1 + n_targets][N^d] as stored).
+ *   fk_accum_save: writes the state (point count, device flags, grids) into buf (host,
+ *     cap bytes); synchronises `stream`.
+ *   fk_accum_load: replaces the accumulator's sums by a saved state of an accumulator
+ *     of the same (d, m, n_targets, eps, precision, options), else FK_EINVAL.
+ *   fk_accum_add_state: adds a saved state's sums, point count and flags to the
+ *     accumulator (the shard reduction); synchronises `stream`.
+ * The 1-D fixed-point path adds each chunk's sums to the fp64 grids in chunk order, so
+ * a run resumed from a state saved after chunk k gives the same bits as the run that
+ * was not interrupted. */
+FK_API size_t fk_accum_state_bytes(const fk_accum* acc);
+FK_API fk_status fk_accum_save(fk_accum* acc, void* buf, size_t cap, void* stream);
+FK_API fk_status fk_accum_load(fk_accum* acc, const void* buf, size_t len, void* stream);
+FK_API fk_status fk_accum_add_state(fk_accum* acc, const void* buf, size_t len, void* stream);
+
 /* Capture of calls into one CUDA graph (no counterpart in the paper; the batching
  * form of the fits: a whole fit, e.g. the additive model's 8 + 28 transforms, Gram
  * assembly and dense solve, replayed with one graph launch).

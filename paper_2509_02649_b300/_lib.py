@@ -34,7 +34,8 @@ EXPORTS = ["fk_default_opts", "fk_fit_sobolev", "fk_fit_pik", "fk_fit_additive",
            "fk_accum_destroy", "fk_generate_sweep_1d", "fk_release_workspace", "fk_autotune_table",
            "fk_autotune_clear", "fk_fit_pik_general", "fk_box_moments", "fk_fit_sobolev_pairs",
            "fk_capture_begin", "fk_capture_end", "fk_graph_launch", "fk_graph_status", "fk_graph_destroy",
-           "fk_graph_kernel_ms", "fk_peak_fp32"]
+           "fk_graph_kernel_ms", "fk_peak_fp32", "fk_accum_state_bytes", "fk_accum_save", "fk_accum_load",
+           "fk_accum_add_state"]
 
 
 class FkError(RuntimeError):
@@ -112,6 +113,10 @@ def lib() -> ctypes.CDLL:
             "fk_graph_kernel_ms": (_I, [_P, ctypes.POINTER(ctypes.c_float)]),
             "fk_fit_sobolev_pairs": (_I, [_I, _L, _P, _P, _I, _I, _P, _P, _I, _I, _D, _I, _P, _P, _P, _P]),
             "fk_peak_fp32": (_I, [ctypes.POINTER(_D), ctypes.POINTER(_I), _P]),
+            "fk_accum_state_bytes": (ctypes.c_size_t, [_P]),
+            "fk_accum_save": (_I, [_P, _P, ctypes.c_size_t, _P]),
+            "fk_accum_load": (_I, [_P, _P, ctypes.c_size_t, _P]),
+            "fk_accum_add_state": (_I, [_P, _P, ctypes.c_size_t, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -423,6 +428,22 @@ class Accumulator:
 
     def reset(self):
         _check(lib().fk_accum_reset(self._h, _stream()))
+
+    def state(self) -> bytes:
+        """The sums so far (point count, device flags, fp64 grids) as bytes: a checkpoint,
+        or one shard's part of a reduction."""
+        n = int(lib().fk_accum_state_bytes(self._h))
+        buf = ctypes.create_string_buffer(n)
+        _check(lib().fk_accum_save(self._h, buf, n, _stream()))
+        return buf.raw
+
+    def load_state(self, state: bytes):
+        """Replace the sums by a saved state (same accumulator shape)."""
+        _check(lib().fk_accum_load(self._h, state, len(state), _stream()))
+
+    def add_state(self, state: bytes):
+        """Add another accumulator's saved sums (shard reduction)."""
+        _check(lib().fk_accum_add_state(self._h, state, len(state), _stream()))
 
     def close(self):
         if self._h:

@@ -3,6 +3,7 @@
 #include "fk_internal.cuh"
 
 #include <atomic>
+#include <cstring>
 #include <mutex>
 #include <chrono>
 #include <vector>
@@ -779,6 +780,120 @@ fk_status fk_accum_reset(fk_accum* a, void* stream) {
   FK_CUDA(cudaMemsetAsync(a->grid, 0, sizeof(double) * G, st));
   FK_CUDA(cudaMemsetAsync(a->flags, 0, sizeof(unsigned), st));
   a->n_total = 0;
+  return FK_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- accumulator state
+// Host image of an accumulator: a fixed header, then the fp64 grids [1 + n_targets][N^d]
+// as stored on the device.
+namespace fk {
+namespace {
+struct AccumHeader {
+  char magic[8];  // "FKACCUM1"
+  int32_t d, m, n_targets, precision, N, w;
+  double eps;
+  int64_t n_total;
+  uint32_t flags, reserved;
+  int64_t grid_doubles;
+};
+static_assert(sizeof(AccumHeader) == 64, "header layout");
+const char kAccumMagic[8] = {'F', 'K', 'A', 'C', 'C', 'U', 'M', '1'};
+
+int64_t accum_grid_doubles(const fk_accum* a) { return ipow(a->p.N, a->d) * (1 + a->nt); }
+
+fk_status accum_check_state(const fk_accum* a, const void* buf, size_t len, const AccumHeader** out) {
+  if (!buf || len < sizeof(AccumHeader)) return set_error(FK_EINVAL, "state buffer too short");
+  const AccumHeader* h = static_cast<const AccumHeader*>(buf);
+  if (std::memcmp(h->magic, kAccumMagic, 8) != 0) return set_error(FK_EINVAL, "not an accumulator state");
+  if (h->d != a->d || h->m != a->m || h->n_targets != a->nt || h->precision != a->precision || h->N != a->p.N ||
+      h->w != a->p.w || h->eps != a->eps)
+    return set_error(FK_EINVAL, "state of another accumulator shape (d=%d m=%d targets=%d precision=%d eps=%g)", h->d,
+                     h->m, h->n_targets, h->precision, h->eps);
+  if (h->grid_doubles != accum_grid_doubles(a) ||
+      len < sizeof(AccumHeader) + sizeof(double) * static_cast<size_t>(h->grid_doubles))
+    return set_error(FK_EINVAL, "state buffer holds %zu bytes, the grids need more", len);
+  *out = h;
+  return FK_OK;
+}
+
+__global__ void k_or_flag(unsigned* flags, unsigned v) { atomicOr(flags, v); }
+}  // namespace
+}  // namespace fk
+
+extern "C" {
+
+size_t fk_accum_state_bytes(const fk_accum* a) {
+  if (!a) return 0;
+  return sizeof(AccumHeader) + sizeof(double) * static_cast<size_t>(accum_grid_doubles(a));
+}
+
+fk_status fk_accum_save(fk_accum* a, void* buf, size_t cap, void* stream) {
+  clear_error();
+  if (!a || !buf) return set_error(FK_EINVAL, "null accumulator or buffer");
+  if (cap < fk_accum_state_bytes(a)) return set_error(FK_EINVAL, "state needs %zu bytes, buffer has %zu",
+                                                      fk_accum_state_bytes(a), cap);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, false, false, "fk_accum_save"));
+  AccumHeader h{};
+  std::memcpy(h.magic, kAccumMagic, 8);
+  h.d = a->d;
+  h.m = a->m;
+  h.n_targets = a->nt;
+  h.precision = a->precision;
+  h.N = a->p.N;
+  h.w = a->p.w;
+  h.eps = a->eps;
+  h.n_total = a->n_total;
+  h.grid_doubles = accum_grid_doubles(a);
+  unsigned char* out = static_cast<unsigned char*>(buf);
+  FK_CUDA(cudaMemcpyAsync(&h.flags, a->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  FK_CUDA(cudaMemcpyAsync(out + sizeof(AccumHeader), a->grid, sizeof(double) * h.grid_doubles,
+                          cudaMemcpyDeviceToHost, st));
+  FK_CUDA(cudaStreamSynchronize(st));
+  std::memcpy(out, &h, sizeof(h));
+  return FK_OK;
+}
+
+fk_status fk_accum_load(fk_accum* a, const void* buf, size_t len, void* stream) {
+  clear_error();
+  if (!a) return set_error(FK_EINVAL, "null accumulator");
+  const AccumHeader* h = nullptr;
+  FK_TRY(accum_check_state(a, buf, len, &h));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, false, false, "fk_accum_load"));
+  const unsigned char* in = static_cast<const unsigned char*>(buf);
+  FK_CUDA(cudaMemcpyAsync(a->grid, in + sizeof(AccumHeader), sizeof(double) * h->grid_doubles,
+                          cudaMemcpyHostToDevice, st));
+  const unsigned fl = h->flags;
+  FK_CUDA(cudaMemcpyAsync(a->flags, &fl, sizeof(unsigned), cudaMemcpyHostToDevice, st));
+  FK_CUDA(cudaStreamSynchronize(st));
+  a->n_total = h->n_total;
+  return FK_OK;
+}
+
+fk_status fk_accum_add_state(fk_accum* a, const void* buf, size_t len, void* stream) {
+  clear_error();
+  if (!a) return set_error(FK_EINVAL, "null accumulator");
+  const AccumHeader* h = nullptr;
+  FK_TRY(accum_check_state(a, buf, len, &h));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, false, false, "fk_accum_add_state"));
+  Scratch scr(st);
+  double* tmp = nullptr;
+  FK_TRY(scr.alloc(&tmp, static_cast<size_t>(h->grid_doubles)));
+  const unsigned char* in = static_cast<const unsigned char*>(buf);
+  FK_CUDA(cudaMemcpyAsync(tmp, in + sizeof(AccumHeader), sizeof(double) * h->grid_doubles, cudaMemcpyHostToDevice,
+                          st));
+  k_add_grid<<<grid_for(h->grid_doubles, 256), 256, 0, st>>>(h->grid_doubles, tmp, a->grid); note_launch();
+  FK_CUDA(cudaGetLastError());
+  if (h->flags) {
+    k_or_flag<<<1, 1, 0, st>>>(a->flags, h->flags); note_launch();
+    FK_CUDA(cudaGetLastError());
+  }
+  FK_CUDA(cudaStreamSynchronize(st));  // the host buffer is read before return
+  a->n_total += h->n_total;
   return FK_OK;
 }
 

@@ -190,6 +190,9 @@ struct Rec16 {
   using T = uint4;
   static constexpr bool HAS_Y = true, SPLIT_Y = false;
   static constexpr int NP_THREADS = THREADS_ACC;  // CTA size (= cells) without pair mode
+  // records come from partitions that write only cells of their owner (checked bucket
+  // capacities), so linking does not re-check them
+  static constexpr bool CHECK_CELL = false;
   static constexpr int CAPR = 4096, CARRY = 2048;
   __device__ static int cell(const uint4& r) { return static_cast<int>(r.x & 0xFFFFu); }
   __device__ static float g0(const uint4& r, float gc) { return __uint_as_float(r.y) - gc; }
@@ -202,6 +205,7 @@ struct Rec8 {
   using T = uint2;
   static constexpr bool HAS_Y = false, SPLIT_Y = false;
   static constexpr int NP_THREADS = THREADS_ACC;
+  static constexpr bool CHECK_CELL = false;
   static constexpr int CAPR = 10240, CARRY = 2048;
   __device__ static int cell(const uint2& r) { return static_cast<int>(r.y >> 16); }
   __device__ static float g0(const uint2& r, float) {
@@ -230,6 +234,8 @@ struct RecAdd {
   using T = unsigned;
   static constexpr bool HAS_Y = false, SPLIT_Y = true;
   static constexpr int NP_THREADS = 512;  // one lane per cell of two 256-node rows
+  // linking checks each record's cell against the owner's cells (2N may be < 512)
+  static constexpr bool CHECK_CELL = true;
   static constexpr int CAPR = 10240, CARRY = 1024;
   __device__ static int cell(unsigned r) { return static_cast<int>(r >> 23); }
   __device__ static float g0(unsigned, float) { return 0.0f; }  // (in the parallel stream)
@@ -911,6 +917,12 @@ __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) 
       for (int u = 0; u < LU; ++u) {
         const int idx = base + u * THREADS;
         cl[u] = (idx < hi) ? R::cell(st[idx]) : 0xFFFF;  // 0xFFFF: run padding
+        if constexpr (R::CHECK_CELL) {
+          if (cl[u] >= cpc) {  // a record that names no cell of this owner
+            if (cl[u] != 0xFFFF) atomicOr(A.flags, FLAG_INTERNAL);
+            cl[u] = 0xFFFF;
+          }
+        }
       }
 #pragma unroll
       for (int u = 0; u < LU; ++u)
@@ -1542,7 +1554,13 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
       }
     }
     __syncthreads();
-    if (tid < G) gdelta[tid] = static_cast<long long>(base[tid]) + my_pos - toff[tid];
+    if (tid < G) {
+      // the buckets are exact; a reservation beyond one (a count that disagrees with the
+      // placement) is reported and its run is not written
+      const bool room = my_pos + my_c <= __ldg(A.cnt + tid);
+      if (!room) atomicOr(A.flags, FLAG_INTERNAL);
+      gdelta[tid] = room ? static_cast<long long>(base[tid]) + my_pos - toff[tid] : NO_ROOM;
+    }
 #pragma unroll
     for (int k = 0; k < AP_PER; ++k)
       if (w1[k] != 0xFFFFFFFFu) srow[toff[w1[k] >> 25] + rk[k]] = w1[k];
@@ -1550,7 +1568,8 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
     const int valid = toff[G];
     for (int j = tid; j < valid; j += AP_THREADS) {
       const unsigned w = srow[j];
-      A.o1[gdelta[w >> 25] + j] = w;
+      const long long gd = gdelta[w >> 25];
+      if (gd != NO_ROOM) A.o1[gd + j] = w;
     }
     // one code stream per partner, in the same order
     for (int p = 0; p < P; ++p) {
@@ -1568,7 +1587,10 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
       }
       __syncthreads();
       unsigned* out = A.code + p * A.stride;
-      for (int j = tid; j < valid; j += AP_THREADS) out[gdelta[srow[j] >> 25] + j] = scode[j];
+      for (int j = tid; j < valid; j += AP_THREADS) {
+        const long long gd = gdelta[srow[j] >> 25];
+        if (gd != NO_ROOM) out[gd + j] = scode[j];
+      }
       __syncthreads();
     }
   }

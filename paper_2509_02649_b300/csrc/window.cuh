@@ -20,18 +20,21 @@ namespace fk {
 __device__ __forceinline__ bool window_f32(float x, int N, float c_hi, float c_lo, int W, int* l0, float* f) {
   const float lim = 9.42477796076938f;  // 3 pi rounded down
   if (!(x >= -lim && x < lim)) return false;
-  const float p = x * c_hi;
+  // explicitly rounded operations (never contracted into FMAs), so that every kernel
+  // computes the same window for the same x: partitions count points in one kernel and
+  // place them in another
+  const float p = __fmul_rn(x, c_hi);
   const float t = fmaf(x, c_lo, fmaf(x, c_hi, -p));  // x c_lo + (x c_hi - p)
   const float hN = 0.5f * static_cast<float>(N);
   const float hW = 0.5f * static_cast<float>(W);
-  float l = ceilf(((hN + p) + t) - hW);
-  float fr = ((hN - l) + p) + t;
+  float l = ceilf(__fsub_rn(__fadd_rn(__fadd_rn(hN, p), t), hW));
+  float fr = __fadd_rn(__fadd_rn(__fsub_rn(hN, l), p), t);
   if (fr > hW) {
-    l += 1.0f;
-    fr -= 1.0f;
+    l = __fadd_rn(l, 1.0f);
+    fr = __fsub_rn(fr, 1.0f);
   } else if (fr <= hW - 1.0f) {
-    l -= 1.0f;
-    fr += 1.0f;
+    l = __fsub_rn(l, 1.0f);
+    fr = __fadd_rn(fr, 1.0f);
   }
   *l0 = static_cast<int>(l);
   *f = fr;
