@@ -96,7 +96,13 @@ typedef struct {
   double upsampfac;   /* minimum fine-grid oversampling sigma (default 1.9; grids are powers of 2) */
   int spread;         /* fk_spread: AUTO = BINNED (d = 2) or FIXED (d = 1) for FK_MIXED where the
                          shape allows, else ATOMIC; FK_FP64 always spreads with ATOMIC */
-  int deterministic;  /* reserved: 1 asks for run-to-run identical sums (default 0) */
+  int deterministic;  /* 1: run-to-run identical type-1 sums (T, b, and the additive blocks): every
+                         contribution is rounded to a 64-bit fixed-point integer (scale 2^(61-e)
+                         with n max|strength| <= 2^e) and summed with integer atomics, for d = 1,
+                         2, 3 and both precisions (the 1-D mixed fixed-point spreader is used
+                         where it applies: its sums are order-independent already).  Slower than
+                         the default register accumulation; the solvers' own reductions are not
+                         covered (default 0) */
   int autotune;       /* 1: the first call of a problem class times the kernels' tunable shapes
                          (partition tile, cells per owner, round quota) on the call's own data,
                          keeps the fastest in a process-wide table and uses it from then on;
@@ -362,6 +368,23 @@ FK_API fk_status fk_hypergrad(int d, int64_t n, const void* x, int64_t n_v, cons
                        const void* yv, int m, const double* T, const double* W,
                        const double* theta, double eps, int precision, const fk_opts* opts,
                        double* loss, double* dW, double* dY, void* stream);
+
+/* The same hypergradient in two halves, the forward and backward passes of the autograd
+ * form (not in the paper):
+ *   fk_heldout_loss: r = f(xv) - yv with f(x) = Re sum_k theta_k e^{+i<k,x>} (Eq. 1) and
+ *     L = mean(r^2).  theta: device D complex; xv, yv: device (precision of x); loss: host;
+ *     r: device n_v values in the precision of x.  Synchronises `stream`.
+ *   fk_adjoint: g = type1(xv, r) / n_v, z = A^{-1} g with A = Toep(T) + diag W (the fit's
+ *     matrix: T of the training points), dW_k = -2 Re(conj(z_k) theta_k), and, when zy is
+ *     not NULL, zy = zscale z (device D complex).  With zscale = 2 c / n, the type-2 sums
+ *     fk_type2(zy, X) give c dL/dY at any chunk X of the n training points, so the points
+ *     can be produced chunk by chunk instead of stored.  Synchronises `stream`. */
+FK_API fk_status fk_heldout_loss(int d, int m, const double* theta, int64_t n_v, const void* xv, const void* yv,
+                                 double eps, int precision, const fk_opts* opts, double* loss, void* r,
+                                 void* stream);
+FK_API fk_status fk_adjoint(int d, int m, int64_t n_v, const void* xv, const void* r, const double* T,
+                            const double* W, const double* theta, double eps, int precision, const fk_opts* opts,
+                            double zscale, double* dW, double* zy, void* stream);
 
 /* Chain rule from dL/dW (device, D doubles) to the penalty's parameters of
  *   W_k = lambda (c0 + |k|^{2s}) + mu |P(ik)|^2   (Sec. 3.1 and Sec. 4):

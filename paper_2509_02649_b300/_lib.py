@@ -17,7 +17,7 @@ from typing import Optional, Sequence
 import numpy as np
 import torch
 
-from .build import LIB
+from .build import lib_path
 
 FK_FP64, FK_MIXED = 0, 1
 FK_PEN_SOBOLEV, FK_PEN_LOWBIAS = 0, 1
@@ -35,7 +35,7 @@ EXPORTS = ["fk_default_opts", "fk_fit_sobolev", "fk_fit_pik", "fk_fit_additive",
            "fk_autotune_clear", "fk_fit_pik_general", "fk_box_moments", "fk_fit_sobolev_pairs",
            "fk_capture_begin", "fk_capture_end", "fk_graph_launch", "fk_graph_status", "fk_graph_destroy",
            "fk_graph_kernel_ms", "fk_peak_fp32", "fk_accum_state_bytes", "fk_accum_save", "fk_accum_load",
-           "fk_accum_add_state"]
+           "fk_accum_add_state", "fk_heldout_loss", "fk_adjoint"]
 
 
 class FkError(RuntimeError):
@@ -72,9 +72,11 @@ _D = ctypes.c_double
 def lib() -> ctypes.CDLL:
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB):
-            raise RuntimeError("libfk.so is not built (run paper_2509_02649_b300/build.py); no fallback exists")
-        L = ctypes.CDLL(LIB)
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError("%s is not built (run paper_2509_02649_b300/build.py); no fallback exists"
+                               % os.path.basename(path))
+        L = ctypes.CDLL(path)
         sig = {
             "fk_default_opts": (None, [_P]),
             "fk_fit_sobolev": (_I, [_I, _L, _P, _P, _I, _I, _D, _I, _P, _I, _D, _I, _P, _P, _P, _P]),
@@ -117,6 +119,8 @@ def lib() -> ctypes.CDLL:
             "fk_accum_save": (_I, [_P, _P, ctypes.c_size_t, _P]),
             "fk_accum_load": (_I, [_P, _P, ctypes.c_size_t, _P]),
             "fk_accum_add_state": (_I, [_P, _P, ctypes.c_size_t, _P]),
+            "fk_heldout_loss": (_I, [_I, _I, _P, _L, _P, _P, _D, _I, _P, _P, _P, _P]),
+            "fk_adjoint": (_I, [_I, _I, _L, _P, _P, _P, _P, _P, _D, _I, _P, _D, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -351,6 +355,33 @@ def fk_peak_fp32():
     return t.value, sms.value
 
 
+def fk_heldout_loss(theta, xv, yv, m: int, eps: float, precision="mixed", opts: Optional[Opts] = None):
+    """(L = mean(r^2), r = f(xv) - yv on the device) for the fit theta (D complex)."""
+    p = _prec(precision)
+    xv = _points(xv, p)
+    d, nv = xv.shape
+    r = torch.empty(nv, dtype=xv.dtype, device=xv.device)
+    loss = ctypes.c_double(0.0)
+    _check(lib().fk_heldout_loss(d, m, _dense(theta).data_ptr(), nv, xv.data_ptr(), _dense(yv).data_ptr(), eps, p,
+                                 _opts_ptr(opts), ctypes.byref(loss), r.data_ptr(), _stream()))
+    return loss.value, r
+
+
+def fk_adjoint(xv, r, T, W, theta, m: int, eps: float, precision="mixed", opts: Optional[Opts] = None,
+               zscale: float = 0.0, want_zy: bool = False):
+    """(dL/dW [D] float64, zy = zscale z [D] complex128 or None) from the residual r at xv."""
+    p = _prec(precision)
+    xv = _points(xv, p)
+    d, nv = xv.shape
+    D = (2 * m + 1) ** d
+    dW = torch.empty(D, dtype=torch.float64, device=xv.device)
+    zy = torch.empty(D, dtype=torch.complex128, device=xv.device) if want_zy else None
+    _check(lib().fk_adjoint(d, m, nv, xv.data_ptr(), _dense(r).data_ptr(), _dense(T).data_ptr(), _dense(W).data_ptr(),
+                            _dense(theta).data_ptr(), eps, p, _opts_ptr(opts), zscale, dW.data_ptr(),
+                            zy.data_ptr() if zy is not None else None, _stream()))
+    return dW, zy
+
+
 def fk_launch_count() -> int:
     """Kernels libfk has launched in this process so far."""
     return int(lib().fk_launch_count())
@@ -394,7 +425,10 @@ class Accumulator:
         self._h = h
         self._keep = []  # chunk tensors kept alive until the next synchronising call
 
-    def add(self, x, y=None, y_absmax=None):
+    def add(self, x, y=None, y_absmax=None, keep: bool = True):
+        """Spread a chunk.  keep=False drops the references to the chunk at once: safe when
+        its memory comes from torch on the current stream, whose caching allocator hands
+        it out again only to work ordered after this call."""
         x = _points(x, self.prec)
         n = x.shape[1]
         if x.shape[0] != self.d:
@@ -405,7 +439,8 @@ class Accumulator:
             raise ValueError("y_absmax must be the int32 bit patterns written by generate_sweep_1d")
         _check(lib().fk_accum_add(self._h, n, x.data_ptr(), y.data_ptr() if self.nt else None,
                                   y_absmax.data_ptr() if y_absmax is not None else None, _stream()))
-        self._keep.append((x, y, y_absmax))
+        if keep:
+            self._keep.append((x, y, y_absmax))
 
     def system(self):
         T = torch.empty((4 * self.m + 1) ** self.d, dtype=torch.complex128, device=self.device)

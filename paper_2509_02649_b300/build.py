@@ -1,4 +1,9 @@
-"""Build libfk.so (the CUDA path and its C-ABI) in-tree with nvcc for sm_103a."""
+"""Build libfk.so (the CUDA path and its C-ABI) in-tree with nvcc for sm_103a.
+
+build(checked=True) builds libfk_checked.so instead: the same sources compiled with
+FK_CHECKED, whose kernels test their data-dependent indices and report a failed test as
+FK_EINTERNAL (the bounds-checked build).  The binding loads it when the environment
+variable FK_CHECKED is 1."""
 from __future__ import annotations
 
 import glob
@@ -9,6 +14,12 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libfk.so")
+LIB_CHECKED = os.path.join(HERE, "libfk_checked.so")
+
+
+def lib_path() -> str:
+    """The library the binding loads: the bounds-checked build when FK_CHECKED=1."""
+    return LIB_CHECKED if os.environ.get("FK_CHECKED") == "1" else LIB
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -16,26 +27,27 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(HERE, "..", "include", "fk.h")]
     return all(os.path.getmtime(f) <= t for f in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    if not force and up_to_date(lib):
+        return lib
     nvcc = os.environ.get("NVCC", "nvcc")
-    objdir = os.path.join(HERE, "_build")
+    objdir = os.path.join(HERE, "_build_checked" if checked else "_build")
     os.makedirs(objdir, exist_ok=True)
     objs = []
     procs = []
     for src in sources():
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
         cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-               "-rdc=false", "-c", src, "-o", obj]
+               "-rdc=false", *(["-DFK_CHECKED"] if checked else []), "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -50,11 +62,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write("nvcc failed on %s\n" % src)
     if failed:
         raise RuntimeError("libfk build failed")
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     subprocess.check_call([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

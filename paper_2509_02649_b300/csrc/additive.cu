@@ -93,6 +93,9 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
   FK_TRY(es_correction(p1, corr1, st));
   const double inv_n = 1.0 / static_cast<double>(n);
   const bool fixed1d = (precision == FK_MIXED) && o.spread != FK_SPREAD_ATOMIC && spread1d_fixed_supported(p1, nt, true);
+  // deterministic sums (fk_opts.deterministic): 64-bit fixed-point spreading wherever the
+  // 1-D fixed-point spreader does not apply
+  const bool det = o.deterministic != 0;
   unsigned* amax = nullptr;
   if (fixed1d) {
     FK_TRY(scr.alloc(&amax, static_cast<size_t>(nt)));
@@ -104,6 +107,8 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
     if (fixed1d)
       FK_TRY(spread1d_fixed(p1, n, reinterpret_cast<const float*>(x + static_cast<int64_t>(l) * n),
                             reinterpret_cast<const float*>(y), nt, true, amax, grid1, false, flags, st, inner, o.autotune != 0));
+    else if (det)
+      FK_TRY(spread_deterministic<R>(p1, n, x + static_cast<int64_t>(l) * n, y, nt, true, grid1, flags, st, inner));
     else
       FK_TRY(spread_atomic<R>(p1, n, x + static_cast<int64_t>(l) * n, y, nt, true, grid1, flags, st));
     if (precision == FK_FP64) {
@@ -128,7 +133,7 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
   // mixed path: one partition per first coordinate l1 serves all its partners (row
   // owners), or else one partition per pair reading X_l1 and X_l2 in place; otherwise
   // the pair's points are gathered into (X_l1, -X_l2) rows first
-  const bool mixed_binned = precision == FK_MIXED && o.spread != FK_SPREAD_ATOMIC;
+  const bool mixed_binned = precision == FK_MIXED && o.spread != FK_SPREAD_ATOMIC && !det;
   const bool rowpairs = mixed_binned && additive_pairs_supported(p2, d, n);
   const bool binned2 = mixed_binned && !rowpairs && spread_binned_supported(p2, 0, true);
   if (!binned2 && !rowpairs) FK_TRY(scr.alloc(&pts, 2 * static_cast<size_t>(n)));
@@ -159,7 +164,13 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
         FK_CUDA(cudaGetLastError());
       }
       double* blk = Bp + 2 * static_cast<int64_t>(pair) * K * K;
-      if (precision == FK_FP64) {
+      if (det) {
+        FK_TRY(spread_deterministic<R>(p2, n, pts, nullptr, 0, true, grid2, flags, st, inner));
+        if (precision == FK_FP64)
+          FK_TRY(grid_to_modes<double>(p2, grid2, 0, 1, m, corr2, inv_n, blk, st, inner));
+        else
+          FK_TRY(grid_to_modes<float>(p2, grid2, 0, 1, m, corr2, inv_n, blk, st, inner));
+      } else if (precision == FK_FP64) {
         FK_TRY(spread_atomic<double>(p2, n, reinterpret_cast<const double*>(pts), nullptr, 0, true, grid2, flags, st));
         FK_TRY(grid_to_modes<double>(p2, grid2, 0, 1, m, corr2, inv_n, blk, st, inner));
       } else if (binned2) {

@@ -196,6 +196,17 @@ struct Timer {
 static fk_status spread_any(const EsPlan& p, int precision, const fk_opts& o, int64_t n, const void* x,
                             const void* y, int n_y, bool with_ones, double* grid, unsigned* flags,
                             cudaStream_t st, Scratch& scr) {
+  // deterministic sums: the 1-D fixed-point spreader (order-independent already) where it
+  // applies, else 64-bit fixed-point global sums
+  const bool fixed1d = precision == FK_MIXED && p.d == 1 && o.spread != FK_SPREAD_ATOMIC &&
+                       spread1d_fixed_supported(p, n_y, with_ones);
+  if (o.deterministic && !fixed1d) {
+    if (precision == FK_FP64)
+      return spread_deterministic<double>(p, n, static_cast<const double*>(x), static_cast<const double*>(y), n_y,
+                                          with_ones, grid, flags, st, scr);
+    return spread_deterministic<float>(p, n, static_cast<const float*>(x), static_cast<const float*>(y), n_y,
+                                       with_ones, grid, flags, st, scr);
+  }
   if (precision == FK_FP64)
     return spread_atomic<double>(p, n, static_cast<const double*>(x), static_cast<const double*>(y), n_y,
                                  with_ones, grid, flags, st);

@@ -183,6 +183,12 @@ template <typename R>
 fk_status spread_atomic(const EsPlan& p, int64_t n, const R* x, const R* y, int n_y,
                         bool with_ones, double* grid, unsigned* flags, cudaStream_t st);
 
+// Deterministic form (fk_opts.deterministic): 64-bit fixed-point integer sums, scaled
+// back into the fp64 grid (zeroed inside); bitwise reproducible for d = 1, 2, 3.
+template <typename R>
+fk_status spread_deterministic(const EsPlan& p, int64_t n, const R* x, const R* y, int n_y, bool with_ones,
+                               double* grid, unsigned* flags, cudaStream_t st, Scratch& scr);
+
 // ------------------------------------------------------------------ autotuning
 // Tunables of the kernels whose best shape depends on the problem; a process-wide
 // table keyed by the problem's class holds the measured winners (autotune.cu).

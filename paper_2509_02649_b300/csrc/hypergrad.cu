@@ -169,12 +169,125 @@ fk_status hypergrad_impl(int d, int64_t n, const R* x, int64_t n_v, const R* xv,
   return FK_OK;
 }
 
+// forward half: predictions at the validation points, residual r (precision R) and the loss
+template <typename R>
+fk_status heldout_loss_impl(int d, int m, const double* theta, int64_t n_v, const R* xv, const R* yv, double eps,
+                            const fk_opts& o, double* loss, R* r, cudaStream_t st) {
+  Scratch scr(st);
+  unsigned* flags = nullptr;
+  FK_TRY(scr.alloc(&flags, 1));
+  FK_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned), st));
+  EsPlan p;
+  FK_TRY(make_es_plan(d, m, eps, o.upsampfac, &p));
+  double *corr = nullptr, *f = nullptr, *sum = nullptr;
+  FK_TRY(scr.alloc(&corr, 2 * static_cast<size_t>(m) + 1));
+  FK_TRY(es_correction(p, corr, st));
+  FK_TRY(scr.alloc(&f, static_cast<size_t>(n_v)));
+  FK_TRY(scr.alloc(&sum, 1));
+  FK_TRY(type2_eval<R>(p, m, theta, 1, n_v, xv, corr, f, flags, st, scr));
+  FK_CUDA(cudaMemsetAsync(sum, 0, sizeof(double), st));
+  k_residual<R><<<grid_for(n_v, 256, 148 * 8), 256, 0, st>>>(n_v, f, yv, r, sum); note_launch();
+  FK_CUDA(cudaGetLastError());
+  double hsum = 0.0;
+  unsigned hflags = 0;
+  FK_CUDA(cudaMemcpyAsync(&hsum, sum, sizeof(double), cudaMemcpyDeviceToHost, st));
+  FK_CUDA(cudaMemcpyAsync(&hflags, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  FK_CUDA(cudaStreamSynchronize(st));
+  FK_TRY(flags_status(hflags));
+  *loss = hsum / static_cast<double>(n_v);
+  return FK_OK;
+}
+
+// backward half: g = type1(xv, r) / n_v, z = A^{-1} g, dW = -2 Re(conj(z) theta), zy = zscale z
+template <typename R>
+fk_status adjoint_impl(int d, int m, int64_t n_v, const R* xv, const R* r, const double* T, const double* W,
+                       const double* theta, double eps, int precision, const fk_opts& o, double zscale, double* dW,
+                       double* zy, cudaStream_t st) {
+  Scratch scr(st);
+  unsigned* flags = nullptr;
+  FK_TRY(scr.alloc(&flags, 1));
+  FK_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned), st));
+  EsPlan p;
+  FK_TRY(make_es_plan(d, m, eps, o.upsampfac, &p));
+  int64_t D = 1, G = 1;
+  for (int l = 0; l < d; ++l) {
+    D *= (2 * m + 1);
+    G *= p.N;
+  }
+  double *corr = nullptr, *g = nullptr, *z = nullptr, *grid = nullptr;
+  FK_TRY(scr.alloc(&corr, 2 * static_cast<size_t>(m) + 1));
+  FK_TRY(es_correction(p, corr, st));
+  FK_TRY(scr.alloc(&g, 2 * static_cast<size_t>(D)));
+  FK_TRY(scr.alloc(&z, 2 * static_cast<size_t>(D)));
+  FK_TRY(scr.alloc(&grid, static_cast<size_t>(G)));
+  FK_TRY(spread_atomic<R>(p, n_v, xv, r, 1, false, grid, flags, st));
+  if (precision == FK_FP64)
+    FK_TRY(grid_to_modes<double>(p, grid, 0, 1, m, corr, 1.0 / static_cast<double>(n_v), g, st, scr));
+  else
+    FK_TRY(grid_to_modes<float>(p, grid, 0, 1, m, corr, 1.0 / static_cast<double>(n_v), g, st, scr));
+  int iters = 0;
+  double rr = 0.0;
+  FK_TRY(solve_system(d, m, T, W, 1, g, 1, o, z, st, scr, flags, &iters, &rr));
+  k_dW<<<grid_for(D, 256), 256, 0, st>>>(D, z, theta, dW); note_launch();
+  FK_CUDA(cudaGetLastError());
+  if (zy) {
+    FK_CUDA(cudaMemcpyAsync(zy, z, sizeof(double) * 2 * D, cudaMemcpyDeviceToDevice, st));
+    k_scale<<<grid_for(2 * D, 256), 256, 0, st>>>(2 * D, zscale, zy); note_launch();
+    FK_CUDA(cudaGetLastError());
+  }
+  unsigned hflags = 0;
+  FK_CUDA(cudaMemcpyAsync(&hflags, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  FK_CUDA(cudaStreamSynchronize(st));
+  return flags_status(hflags);
+}
+
+fk_opts hyper_opts(const fk_opts* opts) {
+  fk_opts o;
+  fk_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.cg_tol <= 0) o.cg_tol = 1e-13;
+  if (o.cg_maxit <= 0) o.cg_maxit = 1000;
+  if (o.upsampfac <= 1.0) o.upsampfac = 1.9;
+  return o;
+}
+
 }  // namespace
 }  // namespace fk
 
 using namespace fk;
 
 extern "C" {
+
+fk_status fk_heldout_loss(int d, int m, const double* theta, int64_t n_v, const void* xv, const void* yv, double eps,
+                          int precision, const fk_opts* opts, double* loss, void* r, void* stream) {
+  clear_error();
+  FK_TRY(check_common(d, n_v, m, eps, precision));
+  if (!theta || !xv || !yv || !loss || !r) return set_error(FK_EINVAL, "null pointer argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, false, false, "fk_heldout_loss"));
+  const fk_opts o = hyper_opts(opts);
+  if (precision == FK_FP64)
+    return heldout_loss_impl<double>(d, m, theta, n_v, static_cast<const double*>(xv), static_cast<const double*>(yv),
+                                     eps, o, loss, static_cast<double*>(r), st);
+  return heldout_loss_impl<float>(d, m, theta, n_v, static_cast<const float*>(xv), static_cast<const float*>(yv), eps,
+                                  o, loss, static_cast<float*>(r), st);
+}
+
+fk_status fk_adjoint(int d, int m, int64_t n_v, const void* xv, const void* r, const double* T, const double* W,
+                     const double* theta, double eps, int precision, const fk_opts* opts, double zscale, double* dW,
+                     double* zy, void* stream) {
+  clear_error();
+  FK_TRY(check_common(d, n_v, m, eps, precision));
+  if (!xv || !r || !T || !W || !theta || !dW) return set_error(FK_EINVAL, "null pointer argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, false, false, "fk_adjoint"));
+  const fk_opts o = hyper_opts(opts);
+  if (precision == FK_FP64)
+    return adjoint_impl<double>(d, m, n_v, static_cast<const double*>(xv), static_cast<const double*>(r), T, W, theta,
+                                eps, precision, o, zscale, dW, zy, st);
+  return adjoint_impl<float>(d, m, n_v, static_cast<const float*>(xv), static_cast<const float*>(r), T, W, theta, eps,
+                             precision, o, zscale, dW, zy, st);
+}
 
 fk_status fk_hypergrad(int d, int64_t n, const void* x, int64_t n_v, const void* xv, const void* yv, int m,
                        const double* T, const double* W, const double* theta, double eps, int precision,

@@ -129,6 +129,150 @@ fk_status spread_atomic(const EsPlan& p, int64_t n, const R* x, const R* y, int 
   FK_CUDA(cudaGetLastError());
   return FK_OK;
 }
+// ---------------------------------------------------------------- deterministic form
+// Each contribution str * prod psi is rounded to a 64-bit fixed-point integer and added
+// with integer atomics, whose sums do not depend on the order of the additions; the
+// integer sums are then scaled back into the fp64 grid, so repeated runs give the same
+// bits.  Scale of channel c: S_c = 2^(61 - e_c) with n max|str_c| <= 2^e_c (ones: max 1);
+// every |product| <= max|str_c| (the ES weights are <= 1), so every partial sum stays
+// below 2^61 + n in magnitude, and each contribution is rounded to the nearest multiple
+// of 2^(e_c - 61), a relative error of at most n 2^-62 of the channel's largest possible
+// sum.
+
+template <typename R>
+__global__ void k_absmax_det(int64_t n, const R* __restrict__ y, int n_y, unsigned long long* amax) {
+  const int c = blockIdx.y;
+  const R* yc = y + static_cast<int64_t>(c) * n;
+  double m = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double a = fabs(static_cast<double>(yc[i]));
+    m = (a > m) ? a : m;  // NaN inputs are left out
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  // non-negative doubles order as their bit patterns
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(amax + c, static_cast<unsigned long long>(__double_as_longlong(m)));
+}
+
+// scale[c] = 2^(61 - e_c), inv[c] = 2^(e_c - 61), n max|str_c| <= 2^e_c
+__global__ void k_det_scale(int nc, int with_ones, int64_t n, const unsigned long long* amax, double* scale,
+                            double* inv) {
+  const int c = threadIdx.x;
+  if (c >= nc) return;
+  const double m = (with_ones && c == 0) ? 1.0 : __longlong_as_double(static_cast<long long>(amax[c - with_ones]));
+  const double tot = m * static_cast<double>(n);
+  int e = 0;
+  if (tot > 0.0) {
+    const double fr = frexp(tot, &e);  // tot = fr 2^e, fr in [0.5, 1): tot <= 2^e
+    (void)fr;
+  }
+  scale[c] = ldexp(1.0, 61 - e);
+  inv[c] = ldexp(1.0, e - 61);
+}
+
+template <typename R>
+__global__ void k_spread_det(int d, Win<R> win, R beta, int64_t n, const R* __restrict__ x, const R* __restrict__ y,
+                             int n_y, int with_ones, const double* __restrict__ scale, unsigned long long* acc,
+                             unsigned* flags) {
+  const int N = win.N, w = win.W;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t G = (d == 1) ? N : (d == 2 ? static_cast<int64_t>(N) * N : static_cast<int64_t>(N) * N * N);
+  const int nc = n_y + with_ones;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
+    R ker[3][MAXW];
+    int l0[3];
+    bool ok = true;
+    for (int l = 0; l < d; ++l) {
+      R f;
+      if (!win(x[l * n + i], &l0[l], &f)) { ok = false; break; }
+      es_weights<R>(f, w, beta, ker[l]);
+    }
+    if (!ok) { atomicOr(flags, FLAG_RANGE); continue; }
+    for (int c = 0; c < nc; ++c) {
+      const double str = ((with_ones && c == 0) ? 1.0 : static_cast<double>(y[(c - with_ones) * n + i])) * scale[c];
+      unsigned long long* g = acc + c * G;
+      if (d == 1) {
+        for (int a = 0; a < w; ++a)
+          atomicAdd(g + wrap_node(l0[0] + a, N),
+                    static_cast<unsigned long long>(__double2ll_rn(str * static_cast<double>(ker[0][a]))));
+      } else if (d == 2) {
+        for (int a = 0; a < w; ++a) {
+          const int64_t r = wrap_node(l0[0] + a, N);
+          const double sa = str * static_cast<double>(ker[0][a]);
+          for (int b = 0; b < w; ++b)
+            atomicAdd(g + r * N + wrap_node(l0[1] + b, N),
+                      static_cast<unsigned long long>(__double2ll_rn(sa * static_cast<double>(ker[1][b]))));
+        }
+      } else {
+        for (int a = 0; a < w; ++a) {
+          const int64_t r = wrap_node(l0[0] + a, N);
+          const double sa = str * static_cast<double>(ker[0][a]);
+          for (int b = 0; b < w; ++b) {
+            const int64_t rb = r * N + wrap_node(l0[1] + b, N);
+            const double sb = sa * static_cast<double>(ker[1][b]);
+            for (int cc = 0; cc < w; ++cc)
+              atomicAdd(g + rb * N + wrap_node(l0[2] + cc, N),
+                        static_cast<unsigned long long>(__double2ll_rn(sb * static_cast<double>(ker[2][cc]))));
+          }
+        }
+      }
+    }
+  }
+}
+
+__global__ void k_det_to_grid(int64_t total, int64_t G, const double* inv, const unsigned long long* acc,
+                              double* grid) {
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    grid[t] = static_cast<double>(static_cast<long long>(acc[t])) * inv[t / G];
+}
+
+template <typename R>
+fk_status spread_deterministic(const EsPlan& p, int64_t n, const R* x, const R* y, int n_y, bool with_ones,
+                               double* grid, unsigned* flags, cudaStream_t st, Scratch& scr) {
+  if (p.d < 1 || p.d > 3) return set_error(FK_EINVAL, "spread: d = %d not built", p.d);
+  if (p.w > MAXW) return set_error(FK_EINTERNAL, "w > %d", MAXW);
+  const int nc = n_y + (with_ones ? 1 : 0);
+  if (nc < 1 || nc > 1024) return set_error(FK_EINVAL, "deterministic spreading: %d channels", nc);
+  int64_t G = 1;
+  for (int l = 0; l < p.d; ++l) G *= p.N;
+  unsigned long long *acc = nullptr, *amax = nullptr;
+  double* sc = nullptr;
+  FK_TRY(scr.alloc(&acc, static_cast<size_t>(G) * nc));
+  FK_TRY(scr.alloc(&amax, static_cast<size_t>(n_y > 0 ? n_y : 1)));
+  FK_TRY(scr.alloc(&sc, 2 * static_cast<size_t>(nc)));
+  FK_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * G * nc, st));
+  FK_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned long long) * (n_y > 0 ? n_y : 1), st));
+  if (n_y > 0 && n > 0) {
+    if (n_y > 65535) return set_error(FK_EINVAL, "deterministic spreading: %d channels", n_y);
+    k_absmax_det<R><<<dim3(grid_for(n, 256, 148 * 8), n_y), 256, 0, st>>>(n, y, n_y, amax); note_launch();
+    FK_CUDA(cudaGetLastError());
+  }
+  k_det_scale<<<1, 1024, 0, st>>>(nc, with_ones ? 1 : 0, n, amax, sc, sc + nc); note_launch();
+  FK_CUDA(cudaGetLastError());
+  if (n > 0) {
+    KernelTimer* kt = kernel_timer();
+    if (kt->on) cudaEventRecordWithFlags(kt->start, st, kt->rec_flags);
+    k_spread_det<R><<<grid_for(n, 256, 148 * 16), 256, 0, st>>>(p.d, make_win<R>(p.N, p.w), static_cast<R>(p.beta), n,
+                                                                   x, y, n_y, with_ones ? 1 : 0, sc, acc, flags);
+    note_launch();
+    if (kt->on) {
+      cudaEventRecordWithFlags(kt->stop, st, kt->rec_flags);
+      kt->recorded = true;
+    }
+    FK_CUDA(cudaGetLastError());
+  }
+  const int64_t total = G * nc;
+  k_det_to_grid<<<grid_for(total, 256), 256, 0, st>>>(total, G, sc + nc, acc, grid); note_launch();
+  FK_CUDA(cudaGetLastError());
+  return FK_OK;
+}
+template fk_status spread_deterministic<float>(const EsPlan&, int64_t, const float*, const float*, int, bool, double*,
+                                               unsigned*, cudaStream_t, Scratch&);
+template fk_status spread_deterministic<double>(const EsPlan&, int64_t, const double*, const double*, int, bool,
+                                                double*, unsigned*, cudaStream_t, Scratch&);
+
 fk_status preload_spread_atomic_kernels() {
   cudaFuncAttributes fa;
   FK_CUDA(cudaFuncGetAttributes(&fa, k_spread_atomic<float>));

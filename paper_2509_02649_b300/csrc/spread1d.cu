@@ -25,6 +25,7 @@
 #include "fk_internal.cuh"
 #include "window.cuh"
 #include "es_poly.cuh"
+#include "checked.cuh"
 
 namespace fk {
 
@@ -117,6 +118,7 @@ __global__ void __launch_bounds__(THREADS) k_spread1d_fx(Fx1dArgs A) {
     float psi[W];
     es_taps_poly<W>(f - 0.5f * static_cast<float>(W - 1), A.poly, psi);
     const int b = wrap_node(l0, N);
+    if (!fk_check(b >= 0 && b < N, A.flags)) return;
 #pragma unroll
     for (int c = 0; c < CG; ++c) {
       if (c >= nc) break;

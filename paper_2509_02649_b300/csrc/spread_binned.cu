@@ -32,6 +32,7 @@
 #include "fk_internal.cuh"
 #include "window.cuh"
 #include "es_poly.cuh"
+#include "checked.cuh"
 
 #include <type_traits>
 
@@ -701,7 +702,8 @@ __global__ void __launch_bounds__(T, 1024 / T) k_bin_scatter1(PartArgs A) {
         const uint4 r = sorted[j];
         const long long gd = gdelta[r.x >> 16];
         const int64_t at = gd + j;
-        if (gd != NO_ROOM) {
+        if (gd != NO_ROOM &&
+            fk_check(at >= 0 && at < bucket_base(A.om, A.cap, A.cap_s, A.G), A.flags)) {
           if (REC8) {
             reinterpret_cast<uint2*>(A.rec)[at] = pack_rec8(r, 0.5f * static_cast<float>(A.W));
             if (A.has_y) A.ybuf[at] = __uint_as_float(r.w);
@@ -859,8 +861,9 @@ __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) 
 #pragma unroll
       for (int j = 0; j < W; ++j) {
         const int a = transposed ? j : i, bb = transposed ? i : j;
-        atomicAdd(g + static_cast<int64_t>((c0 + a) & (N - 1)) * N + ((c1 + bb) & (N - 1)),
-                  static_cast<double>(acc[i][j]));
+        if (fk_check(key < A.ncells, A.flags))
+          atomicAdd(g + static_cast<int64_t>((c0 + a) & (N - 1)) * N + ((c1 + bb) & (N - 1)),
+                    static_cast<double>(acc[i][j]));
         acc[i][j] = 0.f;
       }
   };
@@ -917,7 +920,7 @@ __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) 
       for (int u = 0; u < LU; ++u) {
         const int idx = base + u * THREADS;
         cl[u] = (idx < hi) ? R::cell(st[idx]) : 0xFFFF;  // 0xFFFF: run padding
-        if constexpr (R::CHECK_CELL) {
+        if (R::CHECK_CELL || kChecked) {
           if (cl[u] >= cpc) {  // a record that names no cell of this owner
             if (cl[u] != 0xFFFF) atomicOr(A.flags, FLAG_INTERNAL);
             cl[u] = 0xFFFF;
@@ -963,8 +966,10 @@ __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) 
         };
         for (; k + 1 < nproc; k += 2) {
           const int ia = ri;
+          if (!fk_check(ia < hi, A.flags)) break;
           const RT ra = st[ia];
           const int rj = nxt[ia];
+          if (!fk_check(rj < hi, A.flags)) break;
           const RT rb = st[rj];
           ri = nxt[rj];
           float ea[W], eb[W];
@@ -980,7 +985,7 @@ __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) 
             for (int i = 0; i < W; ++i) acc[i][j] = fmaf(eb[i], tb, fmaf(ea[i], ta, acc[i][j]));
           }
         }
-        if (k < nproc) {
+        if (k < nproc && fk_check(ri < hi, A.flags)) {
           const int ia = ri;
           const RT ra = st[ia];
           ri = nxt[ia];
@@ -1000,6 +1005,7 @@ __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) 
           constexpr bool ONES = decltype(ones_tag)::value;
           for (int k = 0; k < nproc; ++k) {
             const int ir = ri;
+            if (!fk_check(ir < hi, A.flags)) break;
             const RT rec = st[ir];
             ri = nxt[ir];
             float px[W], py[W];
@@ -1569,7 +1575,7 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
     for (int j = tid; j < valid; j += AP_THREADS) {
       const unsigned w = srow[j];
       const long long gd = gdelta[w >> 25];
-      if (gd != NO_ROOM) A.o1[gd + j] = w;
+      if (gd != NO_ROOM && fk_check(gd + j >= 0 && gd + j < A.stride, A.flags)) A.o1[gd + j] = w;
     }
     // one code stream per partner, in the same order
     for (int p = 0; p < P; ++p) {
@@ -1589,7 +1595,7 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
       unsigned* out = A.code + p * A.stride;
       for (int j = tid; j < valid; j += AP_THREADS) {
         const long long gd = gdelta[srow[j] >> 25];
-        if (gd != NO_ROOM) out[gd + j] = scode[j];
+        if (gd != NO_ROOM && fk_check(gd + j >= 0 && gd + j < A.stride, A.flags)) out[gd + j] = scode[j];
       }
       __syncthreads();
     }

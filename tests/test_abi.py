@@ -30,6 +30,16 @@ def test_library_exports_every_declared_symbol():
     assert set(_lib.EXPORTS) == names
 
 
+def test_checked_build_exports_the_same_symbols():
+    """The bounds-checked build (FK_CHECKED) exports the same C-ABI."""
+    path = os.path.join(ROOT, "paper_2509_02649_b300", "libfk_checked.so")
+    if not os.path.exists(path):
+        pytest.skip("libfk_checked.so is not built")
+    L = ctypes.CDLL(path)
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+
+
 def test_version_and_defaults():
     L = fk.lib()
     assert b"sm_103a" in L.fk_version()
