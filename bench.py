@@ -392,6 +392,31 @@ def run_row(args, rank, local, W=None, steps=None, warmup=None, peak=None, n=Non
         line["loss_and_grads"] = {"L": res[-1][2][0], "dL/dlambda": res[-1][2][1], "dL/dmu": res[-1][2][2]}
     if W == "additive-8d":
         line["report"] = res[-1][2]
+        # a grid search over 300 lambdas (the paper's Sec. 5 experiment) from one transform
+        # pass: one eigendecomposition for all lambdas against one Cholesky solve per lambda
+        lams300 = list(np.logspace(-6, -1, 300))
+        sweep = {}
+        for name, solver in (("eigen", fk.FK_SOLVER_EIG), ("cholesky", fk.FK_SOLVER_CHOL)):
+            torch.cuda.synchronize()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(st)
+            th300, rep300 = fk.fk_fit_additive(x, y, m, lams300, 1e-6, "mixed", report=True,
+                                               opts=fk.default_opts(autotune=tune, solver=solver))
+            s1.record(st)
+            torch.cuda.synchronize()
+            sweep[name] = {"ms": s0.elapsed_time(s1), "ms_solve": rep300["ms_solve"], "theta": th300}
+        # what the estimator determines: the coefficients with k != 0 and the sum of the d
+        # intercepts (their differences are fixed by lambda alone, condition ~ d / lambda)
+        def unique(t):
+            t = t.reshape(len(lams300), d, 2 * m + 1)
+            return torch.cat([torch.cat([t[:, :, :m], t[:, :, m + 1:]], dim=2).reshape(len(lams300), -1),
+                              t[:, :, m].sum(dim=1, keepdim=True)], dim=1)
+        ue, uc = unique(sweep["eigen"]["theta"]), unique(sweep["cholesky"]["theta"])
+        diff = float(((ue - uc).abs().pow(2).sum(1).sqrt() / uc.abs().pow(2).sum(1).sqrt()).max())
+        line["lambda_sweep_300"] = {k: {"ms": v["ms"], "ms_solve": v["ms_solve"]} for k, v in sweep.items()}
+        line["lambda_sweep_300"]["lambdas"] = "300 log-spaced in [1e-6, 1e-1]"
+        line["lambda_sweep_300"]["max_rel_diff_eigen_vs_cholesky"] = diff
+        del sweep
     if W == "additive-8d" and not args.no_graph:
         # the same fit recorded once into a CUDA graph and replayed: one launch per step
         gst = torch.cuda.Stream()

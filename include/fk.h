@@ -79,7 +79,11 @@ typedef enum {
 
 typedef enum { FK_FP64 = 0, FK_MIXED = 1 } fk_precision;
 typedef enum { FK_PEN_SOBOLEV = 0, FK_PEN_LOWBIAS = 1 } fk_penalty;
-typedef enum { FK_SOLVER_AUTO = 0, FK_SOLVER_CHOL = 1, FK_SOLVER_CG = 2 } fk_solver;
+/* EIG: the eigen route for sweeps over lambda (Sec. 5 grid search): one FP64 Hermitian
+   eigendecomposition (parallel cyclic Jacobi) of S^-1 A0 S^-1 serves every penalty of the
+   form lambda_l S^2, then O(D^2) per lambda and right-hand side.  Used by fk_fit_sobolev
+   (Sobolev with c0 > 0, or low-bias) and fk_fit_additive; D <= 8192; not capturable. */
+typedef enum { FK_SOLVER_AUTO = 0, FK_SOLVER_CHOL = 1, FK_SOLVER_CG = 2, FK_SOLVER_EIG = 3 } fk_solver;
 /* Spreading methods of the mixed path: ATOMIC = fp64 global atomics per tap; BINNED =
    2-D partition + register accumulation (d = 2, ones and/or one strength channel);
    FIXED = 1-D integer fixed-point sums in shared memory (d = 1, any channel count,
@@ -88,7 +92,7 @@ typedef enum { FK_SPREAD_AUTO = 0, FK_SPREAD_ATOMIC = 1, FK_SPREAD_BINNED = 2, F
 
 /* Options; pass NULL for defaults (fk_default_opts). */
 typedef struct {
-  int solver;         /* fk_solver; AUTO = Cholesky for D <= 1024, else CG */
+  int solver;         /* fk_solver; AUTO = Cholesky for D <= 1024, else CG; EIG for lambda sweeps */
   double cg_tol;      /* relative residual target of CG (default 1e-13) */
   int cg_maxit;       /* CG iteration cap (default 1000) */
   int refine_steps;   /* iterative-refinement steps after a Cholesky solve (default 1) */

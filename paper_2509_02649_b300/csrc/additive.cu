@@ -185,11 +185,22 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
       }
     }
   if (rep) cudaEventRecord(ev[1], st);
-  // block Gram + lambda I, dense solve per lambda
+  // block Gram + lambda I, dense solve per lambda (or one eigendecomposition for all)
   stage_range.next("fk additive solve");
   double* A = nullptr;
   FK_TRY(scr.alloc(&A, 2 * Dall * Dall));
-  for (int li = 0; li < n_lambda; ++li) {
+  if (o.solver == FK_SOLVER_EIG) {
+    if (cap) return set_error(FK_EINVAL, "the eigen route tests convergence on the host: not capturable");
+    double *U = nullptr, *ev = nullptr;
+    FK_TRY(scr.alloc(&U, 2 * Dall * Dall));
+    FK_TRY(scr.alloc(&ev, Dall));
+    k_additive_gram<<<grid_for(Dall * Dall, 256), 256, 0, st>>>(d, m, T1, Bp, 0.0, A); note_launch();
+    FK_CUDA(cudaGetLastError());
+    int sweeps = 0;
+    FK_TRY(eig_hermitian(Dall, A, U, ev, st, scr, &sweeps));
+    FK_TRY(eig_sweep_solve(Dall, U, ev, nullptr, rhs, nt, lambdas, n_lambda, theta, st, scr));
+  }
+  for (int li = 0; li < n_lambda && o.solver != FK_SOLVER_EIG; ++li) {
     k_additive_gram<<<grid_for(Dall * Dall, 256), 256, 0, st>>>(d, m, T1, Bp, lambdas[li], A); note_launch();
     FK_CUDA(cudaGetLastError());
     double* X = theta + 2 * static_cast<int64_t>(li) * nt * Dall;

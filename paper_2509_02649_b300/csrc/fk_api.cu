@@ -454,6 +454,46 @@ static fk_status fit_common(int d, int64_t n, const void* x, const void* y, int 
   FK_TRY(scr.alloc(&W, D * n_lambda));
   EsPlan p;
   FK_TRY(build_system(d, n, x, y, n_targets, m, eps, precision, o, T, b, st, scr, fl.dev, &p, &tm));
+  if (o.solver == FK_SOLVER_EIG) {
+    // eigen route: every penalty is lambda_l S^2 with S^2 the weights at lambda = 1
+    if (cmom || mu != 0.0 || n_terms > 0)
+      return set_error(FK_EINVAL, "the eigen route needs penalties lambda S^2 (no physics-informed term)");
+    if (penalty == FK_PEN_SOBOLEV && !(o.sobolev_c0 > 0.0))
+      return set_error(FK_EINVAL, "the eigen route needs c0 > 0 (S^2 = c0 + |k|^{2s} invertible)");
+    if (D > 8192) return set_error(FK_EINVAL, "the eigen route is limited to D <= 8192 (D = %lld)", (long long)D);
+    if (capture_ctx()) return set_error(FK_EINVAL, "the eigen route tests convergence on the host: not capturable");
+    NvtxRange r("fk solve (eigen route)");
+    const double one = 1.0;
+    double *S2 = nullptr, *sinv = nullptr, *zero = nullptr, *A = nullptr, *U = nullptr, *ev = nullptr;
+    FK_TRY(scr.alloc(&S2, D));
+    FK_TRY(scr.alloc(&sinv, D));
+    FK_TRY(scr.alloc(&zero, D));
+    FK_TRY(scr.alloc(&A, 2 * D * D));
+    FK_TRY(scr.alloc(&U, 2 * D * D));
+    FK_TRY(scr.alloc(&ev, D));
+    FK_TRY(penalty_weights(d, m, penalty, s, o.sobolev_c0, &one, 1, 0.0, 0, nullptr, nullptr, S2, st));
+    FK_TRY(inv_sqrt(D, S2, sinv, st));
+    FK_CUDA(cudaMemsetAsync(zero, 0, sizeof(double) * D, st));
+    FK_TRY(assemble_toeplitz(d, m, T, zero, A, st));
+    FK_TRY(eig_scale_sym(D, sinv, A, st));
+    int sweeps = 0;
+    FK_TRY(eig_hermitian(D, A, U, ev, st, scr, &sweeps));
+    FK_TRY(eig_sweep_solve(D, U, ev, sinv, b, n_targets, lambdas, n_lambda, theta, st, scr));
+    tm.mark();
+    FK_TRY(fl.check());
+    if (rep) {
+      *rep = fk_report{};
+      rep->ms_spread = tm.ms(1, 2);
+      rep->ms_fft = tm.ms(2, 3);
+      rep->ms_solve = tm.ms(3, 4);
+      rep->ms_total = tm.ms(0, 4);
+      rep->n_used = n;
+      rep->fine_grid = p.N;
+      rep->kernel_width = p.w;
+      rep->ms_kernel = kts.ms();
+    }
+    return FK_OK;
+  }
   PenOp op;
   if (cmom) {
     // sub-domain / collocation penalty: W keeps the Sobolev part, mu D^* C D is an operator
@@ -539,6 +579,8 @@ fk_status fk_fit_sobolev_pairs(int d, int64_t n, const void* x, const void* y, i
   FK_TRY(scr.alloc(&W, D * n_pairs));
   EsPlan p;
   FK_TRY(build_system(d, n, x, y, n_targets, m, eps, precision, o, T, b, st, scr, fl.dev, &p, &tm));
+  if (o.solver == FK_SOLVER_EIG)
+    return set_error(FK_EINVAL, "the eigen route needs one penalty shape lambda S^2 for the whole sweep");
   // one penalty row per (s, lambda) pair; all rows share T and b (one spreading pass)
   for (int i = 0; i < n_pairs; ++i)
     FK_TRY(penalty_weights(d, m, penalty, s_values[i], o.sobolev_c0, lambdas + i, 1, 0.0, 0, nullptr, nullptr,

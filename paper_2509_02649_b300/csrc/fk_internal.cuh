@@ -299,6 +299,19 @@ template <typename R>
 fk_status grid_to_modes_into(const EsPlan& p, const double* grid, int c0, int nc, int kout, const double* corr,
                              double scale, double* out, cudaStream_t st, double* tw, cplx<R>* H);
 
+// Eigen route (eig.cu): Hermitian eigendecomposition by parallel cyclic Jacobi (A, D x D
+// complex row-major, is overwritten; U gets the eigenvectors as columns, ev the
+// eigenvalues), and the sweep solve theta[l][rhs] = S^-1 U (ev + lambda_l)^-1 U^H S^-1 b[rhs]
+// (sinv = 1/S, or null for S = I; lambdas on the host).
+fk_status eig_hermitian(int64_t D, double* A, double* U, double* ev, cudaStream_t st, Scratch& scr, int* sweeps);
+fk_status eig_sweep_solve(int64_t D, const double* U, const double* ev, const double* sinv, const double* b,
+                          int n_rhs, const double* lambdas, int n_lambda, double* sol, cudaStream_t st, Scratch& scr);
+fk_status eig_scale_sym(int64_t D, const double* sinv, double* A, cudaStream_t st);
+// Toep(T) + diag W as a dense D x D complex matrix (W: D doubles on the device)
+fk_status assemble_toeplitz(int d, int m, const double* T, const double* W, double* A, cudaStream_t st);
+// 1 / sqrt(w) elementwise
+fk_status inv_sqrt(int64_t n, const double* w, double* out, cudaStream_t st);
+
 // Dense Hermitian positive definite solve (A row-major complex, kept); X: B in, solution out.
 fk_status solve_dense(const double* A, int64_t D, double* X, int n_rhs, int refine, cudaStream_t st, Scratch& scr,
                       unsigned* flags);

@@ -271,6 +271,27 @@ __global__ void k_assemble(int d, int m, const double* T, const double* W, doubl
   }
 }
 
+
+__global__ void k_inv_sqrt(int64_t n, const double* w, double* out) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    out[i] = 1.0 / sqrt(w[i]);
+}
+
+fk_status assemble_toeplitz(int d, int m, const double* T, const double* W, double* A, cudaStream_t st) {
+  int64_t D = 1;
+  for (int l = 0; l < d; ++l) D *= (2 * m + 1);
+  k_assemble<<<grid_for(D * D, 256), 256, 0, st>>>(d, m, T, W, A); note_launch();
+  FK_CUDA(cudaGetLastError());
+  return FK_OK;
+}
+
+fk_status inv_sqrt(int64_t n, const double* w, double* out, cudaStream_t st) {
+  k_inv_sqrt<<<grid_for(n, 256), 256, 0, st>>>(n, w, out); note_launch();
+  FK_CUDA(cudaGetLastError());
+  return FK_OK;
+}
+
 // ---------------------------------------------------------------- Cholesky
 constexpr int NB = 32;
 
@@ -1357,6 +1378,9 @@ fk_status solve_system(int d, int m, const double* T, const double* W, int n_w, 
   const bool with_op = op && op->c && op->P && op->mu != 0.0;
   int solver = o.solver;
   if (solver == FK_SOLVER_AUTO) solver = (D <= 1024) ? FK_SOLVER_CHOL : FK_SOLVER_CG;
+  if (solver == FK_SOLVER_EIG)
+    return set_error(FK_EINVAL, "the eigen route serves whole sweeps of penalties lambda S^2: use it through "
+                                "fk_fit_sobolev or fk_fit_additive");
   if (cg_iters) *cg_iters = 0;
   if (rel_res) *rel_res = 0.0;
   if (solver == FK_SOLVER_CG) {
