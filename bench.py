@@ -36,7 +36,10 @@ sys.path.insert(0, ROOT)
 WL = dict(workload="2d-sobolev", d=2, n=100_000_000, m=32, s=2.0, lam=1e-6, eps=1e-6)
 METRIC = "fit points/s (NUFFT Gram+RHS+solve)"
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (derived peak, reported beside the measured one)
-ACC_DRAM_BYTES_PER_POINT = (241.207040e6 + 6.003200e6) / 2e7  # k_bin_accumulate, 2-D, w = 7
+ACC_DRAM_BYTES_PER_POINT = (241.227776e6 + 6.060544e6) / 2e7  # k_bin_accumulate, 2-D, w = 7
+# k_bin_accumulate on the additive model's pair records: one launch serves the 7 partners
+# of coordinate 0 (DRAM bytes per point and partner)
+ADD_ACC_DRAM_BYTES_PER_POINT_PAIR = (647.362304e6 + 7.018496e6) / (2e7 * 7)
 SPREAD1D_DRAM_BYTES_PER_POINT = (5.09e9 + 5.1e6) / 67108864  # k_spread1d_fx, 17 channels
 
 
@@ -365,7 +368,10 @@ def run_row(args, rank, local, W=None, steps=None, warmup=None, peak=None, n=Non
         cfg = {"workload": W, "n": n, "d": d, "m": m, "lambda": lam, "eps": 1e-6,
                "timed": "8 1-D + 28 2-D type-1 transforms, block Gram, dense FP64 solve"}
         kern = "all spreading kernels of the 36 transforms"
-        traffic, traffic_note = None, "spreading kernels changed since the last ncu capture"
+        traffic = ADD_ACC_DRAM_BYTES_PER_POINT_PAIR * n * (d - 1)
+        traffic_note = ("ncu capture of the pair accumulation (k_bin_accumulate on row-owner records) for the "
+                        "%d partners of coordinate 0 at n = 2e7 (647.4 MB read + 7.0 MB written), scaled to that "
+                        "launch at this n" % (d - 1))
     for _ in range(max(1, warmup)):
         step()
     torch.cuda.synchronize()
