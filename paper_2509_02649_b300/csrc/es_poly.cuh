@@ -53,6 +53,33 @@ __device__ __forceinline__ void es_taps_poly(float g, const EsPoly& P, float* ou
   }
 }
 
+// the same weights as mirrored pairs: pr[a] = (tap a, tap W - 1 - a) for a < W / 2 and,
+// for odd W, *mid = tap W / 2 (each value computed by the same operations as above)
+template <int W>
+__device__ __forceinline__ void es_taps_poly_pairs(float g, const EsPoly& P, float2* pr, float* mid) {
+  static_assert(W <= ES_POLY_MAXW, "width");
+  constexpr int DEG = es_poly_deg(W);
+  constexpr int NE = DEG / 2 + 1, NO = (DEG + 1) / 2;
+  const float g2 = g * g;
+#pragma unroll
+  for (int a = 0; a < W / 2; ++a) {
+    float E = P.e[a][NE - 1];
+#pragma unroll
+    for (int j = NE - 2; j >= 0; --j) E = fmaf(E, g2, P.e[a][j]);
+    float O = P.o[a][NO - 1];
+#pragma unroll
+    for (int j = NO - 2; j >= 0; --j) O = fmaf(O, g2, P.o[a][j]);
+    pr[a] = make_float2(fmaf(g, O, E), fmaf(-g, O, E));
+  }
+  if (W & 1) {
+    constexpr int a = W / 2;
+    float E = P.e[a][NE - 1];
+#pragma unroll
+    for (int j = NE - 2; j >= 0; --j) E = fmaf(E, g2, P.e[a][j]);
+    *mid = E;
+  }
+}
+
 // coefficients for a plan's width and shape (host, fp64 arithmetic)
 EsPoly es_poly(int w, double beta);
 

@@ -762,6 +762,59 @@ __host__ __device__ inline AccLayout acc_layout(int cpc) {
   return L;
 }
 
+// W x W fp32 register window, acc[i][j] for tap i of the first coordinate and tap j of
+// the second.  Scalar form: one fmaf per element.  Packed form: rows k and W - 1 - k
+// of a column share a 64-bit register pair, so that one packed FMA (fma.rn.f32x2,
+// sm_100 and later) updates both from the mirrored weight pair that the tap polynomial
+// yields at once (es_taps_poly_pairs); every element is still one fused multiply-add
+// rounded to nearest.  The packed form pays where each lane evaluates both
+// coordinates' weights itself (one channel per lane); in pair mode the partner's
+// weights arrive one by one through shuffles and the scalar form measured faster.
+template <int W, bool PACKED>
+struct Win;
+template <int W>
+struct Win<W, false> {
+  float a[W][W];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+#pragma unroll
+      for (int j = 0; j < W; ++j) a[i][j] = 0.f;
+  }
+  __device__ __forceinline__ float get(int i, int j) const { return a[i][j]; }
+  // column j += e t
+  __device__ __forceinline__ void fma_col(const float* e, float t, int j) {
+#pragma unroll
+    for (int i = 0; i < W; ++i) a[i][j] = fmaf(e[i], t, a[i][j]);
+  }
+};
+template <int W>
+struct Win<W, true> {
+  float2 p[W / 2][W];        // (row k, row W - 1 - k) of column j
+  float r[(W & 1) ? W : 1];  // the middle row when W is odd
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+#pragma unroll
+      for (int k = 0; k < W / 2; ++k) p[k][j] = make_float2(0.f, 0.f);
+      if constexpr (W & 1) r[j] = 0.f;
+    }
+  }
+  __device__ __forceinline__ float get(int i, int j) const {
+    if constexpr (W & 1) {
+      if (i == W / 2) return r[j];
+    }
+    return i < W / 2 ? p[i][j].x : p[W - 1 - i][j].y;
+  }
+  // column j += e t, e as mirrored pairs (and the middle weight)
+  __device__ __forceinline__ void fma_col(const float2* ep, float emid, float t, int j) {
+    const float2 t2 = make_float2(t, t);
+#pragma unroll
+    for (int k = 0; k < W / 2; ++k) p[k][j] = __ffma2_rn(ep[k], t2, p[k][j]);
+    if constexpr (W & 1) r[j] = fmaf(emid, t, r[j]);
+  }
+};
+
 template <int W, bool PAIR, typename R>
 __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) k_bin_accumulate(AccArgs A) {
   static_assert(!PAIR || R::HAS_Y, "pair mode carries a strength");
@@ -840,11 +893,8 @@ __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) 
   const int nrounds = (count + CAPR - 1) / CAPR;
   if (nrounds == 0) return;
 
-  float acc[W][W];
-#pragma unroll
-  for (int a = 0; a < W; ++a)
-#pragma unroll
-    for (int c = 0; c < W; ++c) acc[a][c] = 0.f;
+  Win<W, !PAIR> acc;
+  acc.zero();
   // the register window goes into the fp64 grid at the end, and also whenever FLUSH_PTS
   // points have been added since the last flush, so that an fp32 running sum never
   // spans more than that many points (crowded cells)
@@ -863,9 +913,9 @@ __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) 
         const int a = transposed ? j : i, bb = transposed ? i : j;
         if (fk_check(key < A.ncells, A.flags))
           atomicAdd(g + static_cast<int64_t>((c0 + a) & (N - 1)) * N + ((c1 + bb) & (N - 1)),
-                    static_cast<double>(acc[i][j]));
-        acc[i][j] = 0.f;
+                    static_cast<double>(acc.get(i, j)));
       }
+    acc.zero();
   };
 
   auto issue = [&](int r) {
@@ -981,8 +1031,8 @@ __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) 
           for (int j = 0; j < W; ++j) {
             const float ta = wa * __shfl_xor_sync(pmask, ea[j], 1);
             const float tb = wb * __shfl_xor_sync(pmask, eb[j], 1);
-#pragma unroll
-            for (int i = 0; i < W; ++i) acc[i][j] = fmaf(eb[i], tb, fmaf(ea[i], ta, acc[i][j]));
+            acc.fma_col(ea, ta, j);
+            acc.fma_col(eb, tb, j);
           }
         }
         if (k < nproc && fk_check(ri < hi, A.flags)) {
@@ -995,8 +1045,7 @@ __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) 
 #pragma unroll
           for (int j = 0; j < W; ++j) {
             const float ta = wa * __shfl_xor_sync(pmask, ea[j], 1);
-#pragma unroll
-            for (int i = 0; i < W; ++i) acc[i][j] = fmaf(ea[i], ta, acc[i][j]);
+            acc.fma_col(ea, ta, j);
           }
         }
       } else {
@@ -1008,20 +1057,20 @@ __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) 
             if (!fk_check(ir < hi, A.flags)) break;
             const RT rec = st[ir];
             ri = nxt[ir];
-            float px[W], py[W];
-            es_taps_poly<W>(R::g0x(rec, yst, ir, gc), A.poly, px);
+            float2 px[W / 2];
+            float pm = 0.f, py[W];
+            es_taps_poly_pairs<W>(R::g0x(rec, yst, ir, gc), A.poly, px, &pm);
             es_taps_poly<W>(R::g1(rec, gc), A.poly, py);
             if (!ONES) {
               float sv;
               if constexpr (R::SPLIT_Y) sv = yst[ir];
               else sv = R::y(rec);
 #pragma unroll
-              for (int i = 0; i < W; ++i) px[i] *= sv;
+              for (int k = 0; k < W / 2; ++k) px[k] = __fmul2_rn(px[k], make_float2(sv, sv));
+              pm *= sv;
             }
 #pragma unroll
-            for (int i = 0; i < W; ++i)
-#pragma unroll
-              for (int j = 0; j < W; ++j) acc[i][j] = fmaf(px[i], py[j], acc[i][j]);
+            for (int j = 0; j < W; ++j) acc.fma_col(px, pm, py[j], j);
           }
         };
         if (A.with_ones)
