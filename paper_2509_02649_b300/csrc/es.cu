@@ -219,6 +219,7 @@ EsPoly es_poly(int w, double beta) {
     for (int j = 0; j < NP; ++j) mono[j] *= std::ldexp(1.0, j);
     for (int j = 0; 2 * j < NP; ++j) out.e[a][j] = static_cast<float>(mono[2 * j]);
     for (int j = 0; 2 * j + 1 < NP; ++j) out.o[a][j] = static_cast<float>(mono[2 * j + 1]);
+    for (int j = 0; j < 4; ++j) out.eo[a][j] = make_float2(out.e[a][j], out.o[a][j]);
   }
   return out;
 }

@@ -24,10 +24,28 @@ __host__ __device__ constexpr int es_poly_deg(int w) { return w <= 7 ? 7 : 8; }
 struct EsPoly {
   float e[ES_POLY_MAXW / 2][5];  // even part of tap a, coefficients of g^0, g^2, .., g^(2 ne - 2)
   float o[ES_POLY_MAXW / 2][4];  // odd part / g, coefficients of g^0, g^2, .., g^(2 no - 2)
+  float2 eo[ES_POLY_MAXW / 2][4];  // (e[a][j], o[a][j]): both Horner chains in one packed FMA per step
 };
 
-// weights of taps 0 .. W - 1 at offset g = f - (W - 1) / 2
-template <int W>
+// E_a(g^2) and O_a(g^2) of tap pair a as (E, O), the two Horner chains advanced together
+// by packed FMAs (fma.rn.f32x2): the same operations, in the same order, as two scalar
+// chains, so the values are identical
+template <int NE, int NO>
+__device__ __forceinline__ float2 es_eo(const EsPoly& P, int a, float g2) {
+  static_assert(NE == NO || NE == NO + 1, "coefficient counts");
+  const float2 g22 = make_float2(g2, g2);
+  float2 eo;
+  if constexpr (NE == NO) eo = P.eo[a][NO - 1];
+  else eo = make_float2(fmaf(P.e[a][NE - 1], g2, P.e[a][NE - 2]), P.o[a][NO - 1]);
+#pragma unroll
+  for (int j = NO - 2; j >= 0; --j) eo = __ffma2_rn(eo, g22, P.eo[a][j]);
+  return eo;
+}
+
+// weights of taps 0 .. W - 1 at offset g = f - (W - 1) / 2.  PH: advance the even and
+// odd Horner chains of a tap pair together with packed FMAs (same values; which form
+// schedules better depends on the caller's register pressure, so callers choose)
+template <int W, bool PH = false>
 __device__ __forceinline__ void es_taps_poly(float g, const EsPoly& P, float* out) {
   static_assert(W <= ES_POLY_MAXW, "width");
   constexpr int DEG = es_poly_deg(W);
@@ -35,12 +53,19 @@ __device__ __forceinline__ void es_taps_poly(float g, const EsPoly& P, float* ou
   const float g2 = g * g;
 #pragma unroll
   for (int a = 0; a < W / 2; ++a) {
-    float E = P.e[a][NE - 1];
+    float E, O;
+    if constexpr (PH) {
+      const float2 eo = es_eo<NE, NO>(P, a, g2);
+      E = eo.x;
+      O = eo.y;
+    } else {
+      E = P.e[a][NE - 1];
 #pragma unroll
-    for (int j = NE - 2; j >= 0; --j) E = fmaf(E, g2, P.e[a][j]);
-    float O = P.o[a][NO - 1];
+      for (int j = NE - 2; j >= 0; --j) E = fmaf(E, g2, P.e[a][j]);
+      O = P.o[a][NO - 1];
 #pragma unroll
-    for (int j = NO - 2; j >= 0; --j) O = fmaf(O, g2, P.o[a][j]);
+      for (int j = NO - 2; j >= 0; --j) O = fmaf(O, g2, P.o[a][j]);
+    }
     out[a] = fmaf(g, O, E);
     out[W - 1 - a] = fmaf(-g, O, E);
   }

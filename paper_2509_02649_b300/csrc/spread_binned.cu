@@ -1023,8 +1023,8 @@ __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) 
           const RT rb = st[rj];
           ri = nxt[rj];
           float ea[W], eb[W];
-          es_taps_poly<W>(ch == 0 ? R::g0(ra, gc) : R::g1(ra, gc), A.poly, ea);
-          es_taps_poly<W>(ch == 0 ? R::g0(rb, gc) : R::g1(rb, gc), A.poly, eb);
+          es_taps_poly<W, true>(ch == 0 ? R::g0(ra, gc) : R::g1(ra, gc), A.poly, ea);
+          es_taps_poly<W, true>(ch == 0 ? R::g0(rb, gc) : R::g1(rb, gc), A.poly, eb);
           const float wa = (ch == 0) ? 1.0f : strength(ra, ia);
           const float wb = (ch == 0) ? 1.0f : strength(rb, rj);
 #pragma unroll
@@ -1040,7 +1040,7 @@ __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) 
           const RT ra = st[ia];
           ri = nxt[ia];
           float ea[W];
-          es_taps_poly<W>(ch == 0 ? R::g0(ra, gc) : R::g1(ra, gc), A.poly, ea);
+          es_taps_poly<W, true>(ch == 0 ? R::g0(ra, gc) : R::g1(ra, gc), A.poly, ea);
           const float wa = (ch == 0) ? 1.0f : strength(ra, ia);
 #pragma unroll
           for (int j = 0; j < W; ++j) {
