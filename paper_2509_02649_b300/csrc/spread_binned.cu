@@ -24,7 +24,7 @@
 //                 round's quota (the mean load plus a fraction of a standard deviation)
 //                 moves to the next round's buffer instead, which keeps the warps' trip
 //                 counts even.  A lane adds its register window into the fp64 grid
-//                 every 2048 points and at the end.
+//                 every 2048 points, every 256 in a crowded round, and at the end.
 // A bucket that would overflow (crowded points) sets a device flag; the exact
 // partition (k_bin_count, k_bin_scan, k_bin_scatter2 or k_bin_scatter, then
 // k_bin_accumulate on its 16-byte records) is always enqueued after and runs only when
@@ -104,6 +104,11 @@ constexpr int P_THREADS = 1024;  // count kernel
 constexpr int P_NWARPS = P_THREADS / 32;
 constexpr int P_TILE = 4096;     // points per partition block, at least
 constexpr int FLUSH_PTS = 2048;  // points per fp32 register run before an fp64 flush
+// a lane whose round holds more than CROWD_RUN records (a crowded cell: the mean load
+// per round is 16-45) flushes after every CROWD_RUN of them, since a crowded cell's
+// points are often near-equal and their fp32 rounding errors then add up in one sign
+// (a run of L equal terms is off by up to L 2^-25 of its sum)
+constexpr int CROWD_RUN = 256;
 constexpr long long NO_ROOM = -(1ll << 62);  // one-pass partition: the owner's bucket is full
 
 // cells per owner: one lane per cell, or two (one per channel) in pair mode, whose
@@ -1002,8 +1007,8 @@ __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) 
     if (tid == 0) s_ncar[buf] = 0;  // read by every thread before this round's first barrier
     const int mine = owns ? min(ccount[cell], q) + xcnt[cell] : 0;
     int ri = owns ? head[cell] : 0xFFFF;
-    if (owns) {
-      const int nproc = mine;
+    // walk the next nproc records of this lane's list into the window
+    auto walk = [&](const int nproc) {
       if constexpr (PAIR) {
         // lane 0 of the pair: ones channel, window [a][b]; lane 1: strength channel,
         // window transposed ([b][a]) because it holds the second coordinate's weights.
@@ -1066,7 +1071,7 @@ __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) 
               if constexpr (R::SPLIT_Y) sv = yst[ir];
               else sv = R::y(rec);
 #pragma unroll
-              for (int k = 0; k < W / 2; ++k) px[k] = __fmul2_rn(px[k], make_float2(sv, sv));
+              for (int t = 0; t < W / 2; ++t) px[t] = __fmul2_rn(px[t], make_float2(sv, sv));
               pm *= sv;
             }
 #pragma unroll
@@ -1078,13 +1083,28 @@ __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) 
         else
           one_channel(std::false_type{});
       }
+    };
+    // the lane's records of this round in runs that end where FLUSH_PTS points have
+    // gone into the window since its last flush, so that no fp32 running sum spans more
+    // than FLUSH_PTS points, and in runs of at most CROWD_RUN, each flushed, when the
+    // round is crowded
+    if (since + mine < FLUSH_PTS && mine <= CROWD_RUN) {
+      walk(mine);
+      since += mine;
+    } else {
+      const bool crowded = mine > CROWD_RUN;
+      for (int left = mine; left > 0;) {
+        const int nproc = min(left, min(CROWD_RUN, FLUSH_PTS - since));
+        walk(nproc);
+        left -= nproc;
+        since += nproc;
+        if (since >= FLUSH_PTS || crowded) {
+          flush();
+          since = 0;
+        }
+      }
     }
     if (owns) {
-      since += mine;
-      if (since >= FLUSH_PTS) {
-        flush();
-        since = 0;
-      }
       // this cell's lists are done (both lanes of a pair read them before their loop);
       // the next round's linking starts after its first barrier
       if constexpr (PAIR) __syncwarp(pmask);

@@ -349,6 +349,28 @@ def test_binned_spreader_clustered_points(n):
     assert rel(host(b)[0], bo) <= 10 * eps
 
 
+@pytest.mark.parametrize("with_y", [True, False])
+def test_binned_all_points_in_one_cell(with_y):
+    # every point at the same place: each accumulation round finds one cell holding all
+    # of its records, far past the cell's slots, so most records move to the next round
+    # or go straight into the grid; the normalised sums are e^{-i j x} (b: times the
+    # mean strength)
+    m, eps, n = 12, 1e-6, 150_001
+    x0 = np.array([0.7312, -2.0419], dtype=np.float32)
+    x = np.repeat(x0[:, None], n, axis=1)
+    y = np.linspace(0.5, 1.5, n).astype(np.float32) if with_y else None
+    T, b = fk.fk_build_system(dev(x, torch.float32), dev(y, torch.float32) if with_y else None, m, eps, "mixed",
+                              opts=fk.default_opts(spread=fk.FK_SPREAD_BINNED))
+    xs = x0.astype(np.float64)
+    j = np.arange(-2 * m, 2 * m + 1)
+    To = np.exp(-1j * (j[:, None] * xs[0] + j[None, :] * xs[1])).ravel()
+    assert rel(host(T), To) <= 10 * eps
+    if with_y:
+        k = np.arange(-m, m + 1)
+        bo = np.exp(-1j * (k[:, None] * xs[0] + k[None, :] * xs[1])).ravel() * np.mean(y.astype(np.float64))
+        assert rel(host(b)[0], bo) <= 10 * eps
+
+
 @pytest.mark.parametrize("kind", ["uniform", "ragged", "clustered"])
 def test_binned_moments_ones_only(kind):
     # moments alone (no strengths): the one-pass partition writes 8-byte records; crowded
