@@ -1084,17 +1084,36 @@ __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) 
           one_channel(std::false_type{});
       }
     };
-    // the lane's records of this round in runs that end where FLUSH_PTS points have
-    // gone into the window since its last flush, so that no fp32 running sum spans more
-    // than FLUSH_PTS points, and in runs of at most CROWD_RUN, each flushed, when the
-    // round is crowded
-    if (since + mine < FLUSH_PTS && mine <= CROWD_RUN) {
-      walk(mine);
-      since += mine;
+    // the lane's records of this round: in one run, flushed once FLUSH_PTS points have
+    // gone into the window since its last flush; a crowded round (more than CROWD_RUN
+    // records) in runs of CROWD_RUN, each flushed.  So no fp32 running sum spans more
+    // than FLUSH_PTS + CROWD_RUN points, and a crowded cell's no more than CROWD_RUN
+    // besides what came before it.  (Splitting ordinary rounds at FLUSH_PTS instead
+    // makes the lanes of a warp diverge where one of them crosses it.)
+    // (The two forms below differ only in where the ordinary round's flush check sits;
+    // each measured fastest for its mode.)
+    const bool crowded = mine > CROWD_RUN;
+    int left = mine;
+    if constexpr (PAIR) {
+      do {
+        const int nproc = crowded ? min(left, CROWD_RUN) : left;
+        walk(nproc);
+        left -= nproc;
+        if (crowded) {
+          flush();
+          since = 0;
+        }
+      } while (left > 0);
+      if (!crowded) {
+        since += mine;
+        if (since >= FLUSH_PTS) {
+          flush();
+          since = 0;
+        }
+      }
     } else {
-      const bool crowded = mine > CROWD_RUN;
-      for (int left = mine; left > 0;) {
-        const int nproc = min(left, min(CROWD_RUN, FLUSH_PTS - since));
+      do {
+        const int nproc = crowded ? min(left, CROWD_RUN) : left;
         walk(nproc);
         left -= nproc;
         since += nproc;
@@ -1102,7 +1121,7 @@ __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) 
           flush();
           since = 0;
         }
-      }
+      } while (left > 0);
     }
     if (owns) {
       // this cell's lists are done (both lanes of a pair read them before their loop);
