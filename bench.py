@@ -36,10 +36,10 @@ sys.path.insert(0, ROOT)
 WL = dict(workload="2d-sobolev", d=2, n=100_000_000, m=32, s=2.0, lam=1e-6, eps=1e-6)
 METRIC = "fit points/s (NUFFT Gram+RHS+solve)"
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (derived peak, reported beside the measured one)
-ACC_DRAM_BYTES_PER_POINT = (241.231872e6 + 6.243840e6) / 2e7  # k_bin_accumulate, 2-D, w = 7
+ACC_DRAM_BYTES_PER_POINT = (241.220096e6 + 6.502656e6) / 2e7  # k_bin_accumulate, 2-D, w = 7
 # k_bin_accumulate on the additive model's pair records: one launch serves the 7 partners
 # of coordinate 0 (DRAM bytes per point and partner)
-ADD_ACC_DRAM_BYTES_PER_POINT_PAIR = (646.827008e6 + 6.575104e6) / (2e7 * 7)
+ADD_ACC_DRAM_BYTES_PER_POINT_PAIR = (646.848512e6 + 7.094272e6) / (2e7 * 7)
 SPREAD1D_DRAM_BYTES_PER_POINT = (5.09e9 + 5.1e6) / 67108864  # k_spread1d_fx, 17 channels
 
 
@@ -370,7 +370,7 @@ def run_row(args, rank, local, W=None, steps=None, warmup=None, peak=None, n=Non
         kern = "all spreading kernels of the 36 transforms"
         traffic = ADD_ACC_DRAM_BYTES_PER_POINT_PAIR * n * (d - 1)
         traffic_note = ("ncu capture of the pair accumulation (k_bin_accumulate on row-owner records) for the "
-                        "%d partners of coordinate 0 at n = 2e7 (646.8 MB read + 6.6 MB written), scaled to that "
+                        "%d partners of coordinate 0 at n = 2e7 (646.8 MB read + 7.1 MB written), scaled to that "
                         "launch at this n" % (d - 1))
     for _ in range(max(1, warmup)):
         step()
@@ -570,7 +570,7 @@ def main():
     peak_tflops = peak["measured"]
     achieved = f_pt * n / (ms_kernel / 1e3) / 1e12
     # DRAM bytes of one k_bin_accumulate launch: ncu capture of this kernel at n = 2e7
-    # (dram__bytes_read.sum 241.2 MB + dram__bytes_write.sum 6.2 MB), scaled by points
+    # (dram__bytes_read.sum 241.2 MB + dram__bytes_write.sum 6.5 MB), scaled by points
     # (the reads are the 8-byte partition records and the strengths, the writes the flush)
     traffic = ACC_DRAM_BYTES_PER_POINT * n if (d == 2 and w == 7) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
