@@ -244,9 +244,9 @@ struct RecAdd {
   static constexpr bool CHECK_CELL = true;
   static constexpr int CAPR = 10240, CARRY = 1024;
   __device__ static int cell(unsigned r) { return static_cast<int>(r >> 23); }
-  __device__ static float g0(unsigned, float) { return 0.0f; }  // (in the parallel stream)
+  // (no g0 or y: the row coordinate's offset comes from the parallel stream, g0x, and
+  // the pair transforms carry no strength)
   __device__ static float g1(unsigned r, float) { return 1.5f - __uint_as_float(0x3F800000u | (r & 0x7FFFFFu)); }
-  __device__ static float y(unsigned) { return 1.0f; }
   __device__ static float g0x(unsigned, const float* par, int i, float) {
     return 1.5f - __uint_as_float(0x3F800000u | (__float_as_uint(par[i]) & 0x7FFFFFu));
   }
