@@ -104,8 +104,9 @@ def host_cores():
 
 
 class ClockSampler:
-    """SM clock and clock-event (throttle) reasons sampled every 200 ms while the timed
-    region runs.
+    """SM clock and clock-event (throttle) reasons sampled while the timed region runs:
+    every 10 ms through NVML (so that a 40 ms region still gets a few samples), every
+    200 ms through nvidia-smi.
 
     The samples come from NVML (libnvidia-ml, the library nvidia-smi reads) through
     ctypes: an `nvidia-smi -lms 200` process stalled the GPU for ~10 ms per query,
@@ -155,7 +156,7 @@ class ClockSampler:
                     if nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and \
                             nv.nvmlDeviceGetCurrentClocksEventReasons(h, ctypes.byref(rs)) == 0:
                         self.samples.append((float(clk.value), int(rs.value)))
-                    self.stop.wait(0.2)
+                    self.stop.wait(0.01)
 
             self.thread = threading.Thread(target=run, daemon=True)
             self.thread.start()
