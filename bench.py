@@ -394,6 +394,16 @@ def run_row(args, rank, local, W=None, steps=None, warmup=None, peak=None, n=Non
                          "ms_kernel": mk, "peak_basis": peak["basis"], "peak_derived": peak["derived"],
                          "frac_of_derived": achieved / peak["derived"]},
             "clocks": clk.summary()}
+    if W == "sweep-1d":
+        # the spreader is bound by its shared-memory atomics (one 32-bit add per tap and
+        # channel): its rate against the measured peaks of that operation
+        dist, rnd = fk.fk_peak_smem_atomics()
+        ops = 7 * (1 + nt) * n / (mk / 1e3) / 1e9
+        line["atomic_view"] = {"achieved": ops, "unit": "G lane ops/s", "atomics_per_point": 7 * (1 + nt),
+                               "peak_distinct_banks": dist, "frac_distinct_banks": ops / dist,
+                               "peak_random_windows": rnd, "frac_random_windows": ops / rnd,
+                               "basis": "of measured: fk_peak_smem_atomics (32-bit adds with returned value, "
+                                        "windows of 7 words, two 1024-thread CTAs per SM)"}
     line["autotune"] = fk.fk_autotune_table().strip() or None
     if W == "pik-heat":
         line["loss_and_grads"] = {"L": res[-1][2][0], "dL/dlambda": res[-1][2][1], "dL/dmu": res[-1][2][2]}

@@ -416,6 +416,15 @@ FK_API int64_t fk_launch_count(void);
  * multiprocessor count.  Synchronises `stream`; not capturable. */
 FK_API fk_status fk_peak_fp32(double* tflops, int* sm_count, void* stream);
 
+/* Measurement helper (no counterpart in the paper): the throughput of 32-bit integer
+ * shared-memory atomic adds with a returned old value (the 1-D fixed-point spreader's
+ * operation), in 1e9 lane operations per second, the peak its atomic rate is reported
+ * against.  Two 1024-thread CTAs per SM each add into windows of 7 consecutive words of
+ * a 98 KB array: *gops_distinct (host) when the 32 lanes of every warp instruction hit 32
+ * different banks, *gops_random (host) for random windows.  Each is the best of three
+ * launches after one warm-up on `stream`.  Synchronises `stream`; not capturable. */
+FK_API fk_status fk_peak_smem_atomics(double* gops_distinct, double* gops_random, void* stream);
+
 /* Library version string. */
 FK_API const char* fk_version(void);
 

@@ -34,7 +34,7 @@ EXPORTS = ["fk_default_opts", "fk_fit_sobolev", "fk_fit_pik", "fk_fit_additive",
            "fk_accum_destroy", "fk_generate_sweep_1d", "fk_release_workspace", "fk_autotune_table",
            "fk_autotune_clear", "fk_fit_pik_general", "fk_box_moments", "fk_fit_sobolev_pairs",
            "fk_capture_begin", "fk_capture_end", "fk_graph_launch", "fk_graph_status", "fk_graph_destroy",
-           "fk_graph_kernel_ms", "fk_peak_fp32", "fk_accum_state_bytes", "fk_accum_save", "fk_accum_load",
+           "fk_graph_kernel_ms", "fk_peak_fp32", "fk_peak_smem_atomics", "fk_accum_state_bytes", "fk_accum_save", "fk_accum_load",
            "fk_accum_add_state", "fk_heldout_loss", "fk_adjoint"]
 
 
@@ -115,6 +115,7 @@ def lib() -> ctypes.CDLL:
             "fk_graph_kernel_ms": (_I, [_P, ctypes.POINTER(ctypes.c_float)]),
             "fk_fit_sobolev_pairs": (_I, [_I, _L, _P, _P, _I, _I, _P, _P, _I, _I, _D, _I, _P, _P, _P, _P]),
             "fk_peak_fp32": (_I, [ctypes.POINTER(_D), ctypes.POINTER(_I), _P]),
+            "fk_peak_smem_atomics": (_I, [ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
             "fk_accum_state_bytes": (ctypes.c_size_t, [_P]),
             "fk_accum_save": (_I, [_P, _P, ctypes.c_size_t, _P]),
             "fk_accum_load": (_I, [_P, _P, ctypes.c_size_t, _P]),
@@ -353,6 +354,15 @@ def fk_peak_fp32():
     sms = _I()
     _check(lib().fk_peak_fp32(ctypes.byref(t), ctypes.byref(sms), _stream()))
     return t.value, sms.value
+
+
+def fk_peak_smem_atomics():
+    """(distinct-bank, random-window) throughput of 32-bit shared-memory atomic adds with a
+    returned value, in 1e9 lane operations per second, on the current device."""
+    dd = _D()
+    dr = _D()
+    _check(lib().fk_peak_smem_atomics(ctypes.byref(dd), ctypes.byref(dr), _stream()))
+    return dd.value, dr.value
 
 
 def fk_heldout_loss(theta, xv, yv, m: int, eps: float, precision="mixed", opts: Optional[Opts] = None):

@@ -17,3 +17,13 @@ def test_peak_fp32_is_plausible():
     # highest SM clock: 2032 MHz on B300; allow 2.2 GHz for any part of this family
     ceiling = sms * 128 * 2 * 2.2e9 / 1e12
     assert 0.5 * sms * 128 * 2 * 1.5e9 / 1e12 < tflops <= ceiling
+
+
+def test_shared_atomic_peak_is_plausible():
+    # a warp instruction is at least one shared-memory wavefront, so an SM completes at
+    # most 32 lane operations per clock; random windows conflict on banks, so they run
+    # slower than windows whose lanes all sit on different banks
+    distinct, random = fk.fk_peak_smem_atomics()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ceiling = sms * 32 * 2.2e9 / 1e9
+    assert 0 < random < distinct <= ceiling
