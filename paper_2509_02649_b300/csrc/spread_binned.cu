@@ -1524,14 +1524,15 @@ __global__ void __launch_bounds__(512) k_add_count(AddPartArgs A) {
 }
 
 struct ApLayout {
-  size_t stage, srow, scode, base, tcnt, toff, hnext, gdelta, bar, total;
+  size_t stage, srow, scode, gdj, base, tcnt, toff, hnext, gdelta, bar, total;
 };
 __host__ __device__ inline ApLayout ap_layout(int P, int G) {
   ApLayout L;
   L.stage = 0;                                                     // float [P + 1][AP_TILE]
   L.srow = L.stage + sizeof(float) * (P + 1) * AP_TILE;            // unsigned [AP_TILE]
-  L.scode = L.srow + sizeof(unsigned) * AP_TILE;                   // unsigned [AP_TILE]
-  L.base = L.scode + sizeof(unsigned) * AP_TILE;                   // int [G]
+  L.scode = L.srow + sizeof(unsigned) * AP_TILE;                   // unsigned [2][AP_TILE]
+  L.gdj = L.scode + sizeof(unsigned) * 2 * AP_TILE;                // long long [AP_TILE]
+  L.base = L.gdj + sizeof(long long) * AP_TILE;                    // int [G]
   L.tcnt = L.base + sizeof(int) * G;                               // int [G + 1]
   L.toff = L.tcnt + sizeof(int) * (G + 1);                         // int [G + 1]
   L.hnext = L.toff + sizeof(int) * (G + 1);                        // int [G]
@@ -1548,7 +1549,8 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
   const ApLayout L = ap_layout(P, G);
   float* stage = reinterpret_cast<float*>(smem + L.stage);
   unsigned* srow = reinterpret_cast<unsigned*>(smem + L.srow);    // row words in owner order
-  unsigned* scode = reinterpret_cast<unsigned*>(smem + L.scode);  // one partner's codes in owner order
+  unsigned* scode = reinterpret_cast<unsigned*>(smem + L.scode);  // two partners' codes in owner order
+  long long* gdj = reinterpret_cast<long long*>(smem + L.gdj);    // bucket slot of tile slot j, or -1
   int* base = reinterpret_cast<int*>(smem + L.base);              // bucket starts
   int* tcnt = reinterpret_cast<int*>(smem + L.tcnt);              // tile counts
   int* toff = reinterpret_cast<int*>(smem + L.toff);              // tile run starts
@@ -1663,10 +1665,18 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
     for (int j = tid; j < valid; j += AP_THREADS) {
       const unsigned w = srow[j];
       const long long gd = gdelta[w >> 25];
-      if (gd != NO_ROOM && fk_check(gd + j >= 0 && gd + j < A.stride, A.flags)) A.o1[gd + j] = w;
+      long long at = -1;
+      if (gd != NO_ROOM && fk_check(gd + j >= 0 && gd + j < A.stride, A.flags)) {
+        at = gd + j;
+        A.o1[at] = w;
+      }
+      gdj[j] = at;  // read by this thread only until the partners' barrier below
     }
-    // one code stream per partner, in the same order
+    // one code stream per partner, in the same order; two code buffers, so that one
+    // barrier per partner suffices (a buffer is rewritten two partners later, after
+    // every thread has passed the barrier in between)
     for (int p = 0; p < P; ++p) {
+      unsigned* sc = scode + (p & 1) * AP_TILE;
 #pragma unroll
       for (int k = 0; k < AP_PER; ++k) {
         if (w1[k] == 0xFFFFFFFFu) continue;
@@ -1677,16 +1687,16 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
           code = ((((w1[k] >> 24) & 1u) * static_cast<unsigned>(A.N) + static_cast<unsigned>(c)) << 23) | v;
         else
           atomicOr(A.flags, FLAG_RANGE);
-        scode[toff[w1[k] >> 25] + rk[k]] = code;
+        sc[toff[w1[k] >> 25] + rk[k]] = code;
       }
       __syncthreads();
       unsigned* out = A.code + p * A.stride;
       for (int j = tid; j < valid; j += AP_THREADS) {
-        const long long gd = gdelta[srow[j] >> 25];
-        if (gd != NO_ROOM && fk_check(gd + j >= 0 && gd + j < A.stride, A.flags)) out[gd + j] = scode[j];
+        const long long at = gdj[j];
+        if (at >= 0) out[at] = sc[j];
       }
-      __syncthreads();
     }
+    __syncthreads();  // the stage and code buffers are free for the next tile
   }
   if (A.cnt_next)
     for (int o = tid; o < G; o += AP_THREADS)
