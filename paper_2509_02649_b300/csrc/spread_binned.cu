@@ -967,8 +967,9 @@ __global__ void __launch_bounds__(PAIR ? Cfg<true>::THREADS : R::NP_THREADS, 1) 
     // the quota it is linked into the cell's list, else it moves to the front of the
     // next buffer (deferred to the next round) while there is room, and is linked
     // beyond the quota (xcnt) when there is not.  LU records per thread and trip, so
-    // that their shared-memory atomics overlap.
-    constexpr int LU = 4;
+    // that their shared-memory atomics overlap (measured best: 4 in pair mode, 2 with one
+    // lane per cell).
+    constexpr int LU = PAIR ? 4 : 2;
     for (int base = lo + tid; base < hi; base += LU * THREADS) {
       int cl[LU], rk[LU];
 #pragma unroll
