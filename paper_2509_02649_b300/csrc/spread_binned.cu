@@ -242,7 +242,7 @@ struct RecAdd {
   static constexpr int NP_THREADS = 512;  // one lane per cell of two 256-node rows
   // linking checks each record's cell against the owner's cells (2N may be < 512)
   static constexpr bool CHECK_CELL = true;
-  static constexpr int CAPR = 10240, CARRY = 1024;
+  static constexpr int CAPR = 10752, CARRY = 512;
   __device__ static int cell(unsigned r) { return static_cast<int>(r >> 23); }
   // (no g0 or y: the row coordinate's offset comes from the parallel stream, g0x, and
   // the pair transforms carry no strength)
