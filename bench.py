@@ -39,7 +39,7 @@ FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (derived peak, reported beside 
 ACC_DRAM_BYTES_PER_POINT = (241.220096e6 + 6.502656e6) / 2e7  # k_bin_accumulate, 2-D, w = 7
 # k_bin_accumulate on the additive model's pair records: one launch serves the 7 partners
 # of coordinate 0 (DRAM bytes per point and partner)
-ADD_ACC_DRAM_BYTES_PER_POINT_PAIR = (646.848512e6 + 7.094272e6) / (2e7 * 7)
+ADD_ACC_DRAM_BYTES_PER_POINT_PAIR = (646.954496e6 + 7.005440e6) / (2e7 * 7)
 SPREAD1D_DRAM_BYTES_PER_POINT = (5.09e9 + 5.1e6) / 67108864  # k_spread1d_fx, 17 channels
 
 
@@ -371,7 +371,7 @@ def run_row(args, rank, local, W=None, steps=None, warmup=None, peak=None, n=Non
         kern = "all spreading kernels of the 36 transforms"
         traffic = ADD_ACC_DRAM_BYTES_PER_POINT_PAIR * n * (d - 1)
         traffic_note = ("ncu capture of the pair accumulation (k_bin_accumulate on row-owner records) for the "
-                        "%d partners of coordinate 0 at n = 2e7 (646.8 MB read + 7.1 MB written), scaled to that "
+                        "%d partners of coordinate 0 at n = 2e7 (647.0 MB read + 7.0 MB written), scaled to that "
                         "launch at this n" % (d - 1))
     for _ in range(max(1, warmup)):
         step()
