@@ -161,3 +161,43 @@ def test_mixed_fit_within_gate_against_accurate_fp64_reference():
     th_ref = fk.fk_fit_sobolev(x.double(), y.double(), m, s, [lam], 1e-12, "fp64")
     err = float(torch.linalg.norm(th_mixed - th_ref) / torch.linalg.norm(th_ref))
     assert err <= 1e-5, err
+
+
+def test_headline_full_size_in_the_bench_configuration():
+    """The 2-D Sobolev workload at its full size (n = 1e8, m = 32, s = 2, lambda = 1e-6,
+    eps = 1e-6) run the way the bench times it: autotuned shapes, the fit recorded once
+    into a CUDA graph and replayed.  The replayed theta must pass the metric's gate
+    against the FP64 path at eps = 1e-12 and agree with the direct call; and the moments
+    T_j that the same kernels build are compared, at a few modes, with their definition
+    (the mean of exp(-i j.x) over all 1e8 points, summed in fp64 on the host)."""
+    n, m, s, lam = 100_000_000, 32, 2.0, 1e-6
+    x = uniform(n, 2, 81)
+    y = torch.exp(-(x * x).sum(0)) + 0.05 * normal(n, 82)[0]
+    opts = fk.default_opts(autotune=1)
+    th_direct = fk.fk_fit_sobolev(x, y, m, s, [lam], 1e-6, "mixed", opts=opts)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    th_graph = torch.empty_like(th_direct)
+    with fk.capture(st) as graph:
+        fk.fk_fit_sobolev(x, y, m, s, [lam], 1e-6, "mixed", opts=opts, out=th_graph)
+    for _ in range(2):
+        graph.launch(st)
+    graph.status()
+    torch.cuda.synchronize()
+    th_ref = fk.fk_fit_sobolev(x.double(), y.double(), m, s, [lam], 1e-12, "fp64")
+    err = float(torch.linalg.norm(th_graph - th_ref) / torch.linalg.norm(th_ref))
+    assert err <= 1e-5, err
+    assert float(torch.linalg.norm(th_graph - th_direct) / torch.linalg.norm(th_direct)) <= 1e-6
+    T, _ = fk.fk_build_system(x, y, m, 1e-6, "mixed", opts=opts)
+    Tg = T.cpu().numpy().ravel()
+    xh = x.cpu().numpy().astype(np.float64)
+    K = 4 * m + 1
+    for j0, j1 in [(1, 0), (-3, 7), (64, -64), (-40, 25)]:
+        acc = 0j
+        for c0 in range(0, n, 10_000_000):
+            ph = j0 * xh[0, c0:c0 + 10_000_000] + j1 * xh[1, c0:c0 + 10_000_000]
+            acc += np.cos(ph).sum() - 1j * np.sin(ph).sum()
+        want = acc / n
+        got = Tg[(j0 + 2 * m) * K + (j1 + 2 * m)]
+        # the NUFFT's error is eps times the sum of |strengths| / n = 1e-6 at most
+        assert abs(got - want) <= 2e-6, (j0, j1, got, want)
