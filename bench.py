@@ -619,31 +619,19 @@ def main():
             "autotune": fk.fk_autotune_table().strip() or None}
 
     if rank == 0 and not args.no_e2e:
-        # end to end through the public API: every step copies its inputs from pinned host
-        # memory and reads theta back.  The copy is streamed in 8 chunks on a copy stream
-        # and each chunk is spread (fk_accum_add) as soon as it has landed, so the
+        # end to end through the public API with host buffers: every step hands the pinned
+        # host inputs to fk_accum_add_host, which copies them in chunks of 2^22 points on
+        # the accumulator's copy stream and spreads each chunk once it has landed, so the
         # spreading hides under the host link (~54 GB/s); the last chunk's spreading, the
-        # transform and the solve (fk_accum_fit_sobolev) follow the copy.
+        # transform and the solve (fk_accum_fit_sobolev) follow the copy, and theta is
+        # read back.
         theta_h = torch.empty(theta.shape, dtype=theta.dtype).pin_memory()
-        chunks = 8
-        c = (n + chunks - 1) // chunks
-        bounds = [(i * c, min(n, (i + 1) * c)) for i in range(chunks)]
-        xd = [torch.empty((2, b - a), dtype=torch.float32, device=x.device) for a, b in bounds]
-        yd = [torch.empty((1, b - a), dtype=torch.float32, device=x.device) for a, b in bounds]
-        cs = torch.cuda.Stream()
+        y_h2 = y_h.reshape(1, -1)
         acc = fk.Accumulator(2, m, 1, eps, "mixed", opts=opts)
 
         def e2e_step():
             acc.reset()
-            for i, (a, b) in enumerate(bounds):
-                with torch.cuda.stream(cs):
-                    xd[i][0].copy_(x_h[0, a:b], non_blocking=True)
-                    xd[i][1].copy_(x_h[1, a:b], non_blocking=True)
-                    yd[i][0].copy_(y_h.reshape(-1)[a:b], non_blocking=True)
-                    landed = torch.cuda.Event()
-                    landed.record(cs)
-                st.wait_event(landed)
-                acc.add(xd[i], yd[i])
+            acc.add_host(x_h, y_h2)
             th = acc.fit_sobolev(s, [lam])
             theta_h.copy_(th, non_blocking=True)
             return th
@@ -661,11 +649,11 @@ def main():
         ems = ee0.elapsed_time(ee1) / k
         err_e = float((th_e - theta).abs().norm() / theta.abs().norm())
         acc.close()
-        del xd, yd
         line["e2e"] = {"value": n / (ems / 1e3), "unit": "points/s", "h2d_bytes_per_step": 12 * n,
                        "d2h_bytes_per_step": int(theta.numel() * 16), "ms_per_step": ems,
-                       "what": "pinned host inputs copied in 8 chunks, each spread on arrival "
-                               "(fk_accum_add), then fk_accum_fit_sobolev and theta read back",
+                       "what": "pinned host inputs passed to fk_accum_add_host (chunks of 2^22 points "
+                               "copied on its copy stream, each spread on arrival), then "
+                               "fk_accum_fit_sobolev and theta read back",
                        "theta_rel_diff_vs_resident": err_e}
 
     if rank == 0 and not args.no_fp64:

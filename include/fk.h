@@ -260,6 +260,20 @@ FK_API fk_status fk_type1_noalloc(int d, int64_t n, const void* x, const void* c
  *     of the 1-D mixed spreader, which otherwise reads y once more to find it.
  *     Asynchronous: inputs must stay valid until `stream` passes the call.
  *     Range errors surface at the next fk_accum_system / fk_accum_fit_sobolev.
+ *   fk_accum_add_host: as fk_accum_add, with x (d x n) and y (n_targets x n) in HOST
+ *     memory, row-major (coordinate l of point j at x[l n + j]).  The points go to the
+ *     device in chunks of `chunk` points (0: FK_HOST_CHUNK_DEFAULT) through two
+ *     device staging buffers owned by the accumulator (allocated by the first call,
+ *     reallocated for a larger chunk, freed by fk_accum_destroy).  Each chunk is copied
+ *     row by row on the accumulator's own copy stream and spread on `stream` once it
+ *     has landed, so the copy of chunk i + 1 overlaps the spreading of chunk i.
+ *     Page-locked host memory (cudaHostAlloc, cudaHostRegister) gets the link's full
+ *     rate; pageable memory works, with the copies staged by the CUDA driver.  The call
+ *     returns once the copies and spreads are enqueued: the host arrays must stay valid
+ *     and unchanged until `stream` passes the call.  y_absmax is not taken (the 1-D
+ *     fixed-point spreader finds each chunk's scale on the device).
+ *     Errors: FK_EINVAL (null accumulator or arrays, n or chunk < 0), FK_ENOMEM
+ *     (staging), FK_ECUDA; range errors as fk_accum_add.
  *   fk_accum_system: T (device complex (4m+1)^d) and b (device complex [n_targets][D]),
  *     each divided by the total point count; either may be NULL.  Synchronises.
  *   fk_accum_fit_sobolev: theta [n_lambda][n_targets][D] as fk_fit_sobolev.
@@ -270,6 +284,9 @@ FK_API fk_status fk_accum_create(int d, int m, int n_targets, double eps, int pr
                                  const fk_opts* opts, fk_accum** out, void* stream);
 FK_API fk_status fk_accum_add(fk_accum* acc, int64_t n, const void* x, const void* y,
                               const unsigned* y_absmax, void* stream);
+#define FK_HOST_CHUNK_DEFAULT (((int64_t)1) << 22)
+FK_API fk_status fk_accum_add_host(fk_accum* acc, int64_t n, const void* x, const void* y, int64_t chunk,
+                                   void* stream);
 FK_API fk_status fk_accum_system(fk_accum* acc, double* T, double* b, int64_t* n_total, void* stream);
 FK_API fk_status fk_accum_fit_sobolev(fk_accum* acc, double s, int penalty, const double* lambdas,
                                       int n_lambda, double* theta, void* stream, fk_report* rep);

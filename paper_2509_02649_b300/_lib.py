@@ -35,7 +35,7 @@ EXPORTS = ["fk_default_opts", "fk_fit_sobolev", "fk_fit_pik", "fk_fit_additive",
            "fk_autotune_clear", "fk_fit_pik_general", "fk_box_moments", "fk_fit_sobolev_pairs",
            "fk_capture_begin", "fk_capture_end", "fk_graph_launch", "fk_graph_status", "fk_graph_destroy",
            "fk_graph_kernel_ms", "fk_peak_fp32", "fk_peak_smem_atomics", "fk_accum_state_bytes", "fk_accum_save", "fk_accum_load",
-           "fk_accum_add_state", "fk_heldout_loss", "fk_adjoint"]
+           "fk_accum_add_state", "fk_heldout_loss", "fk_adjoint", "fk_accum_add_host"]
 
 
 class FkError(RuntimeError):
@@ -97,6 +97,7 @@ def lib() -> ctypes.CDLL:
             "fk_penalty_grads": (_I, [_I, _I, _D, _D, _D, _D, _I, _P, _P, _P, _P, _P]),
             "fk_accum_create": (_I, [_I, _I, _I, _D, _I, _P, ctypes.POINTER(_P), _P]),
             "fk_accum_add": (_I, [_P, _L, _P, _P, _P, _P]),
+            "fk_accum_add_host": (_I, [_P, _L, _P, _P, _L, _P]),
             "fk_accum_system": (_I, [_P, _P, _P, ctypes.POINTER(_L), _P]),
             "fk_accum_fit_sobolev": (_I, [_P, _D, _I, _P, _I, _P, _P, _P]),
             "fk_accum_reset": (_I, [_P, _P]),
@@ -451,6 +452,23 @@ class Accumulator:
                                   y_absmax.data_ptr() if y_absmax is not None else None, _stream()))
         if keep:
             self._keep.append((x, y, y_absmax))
+
+    def add_host(self, x, y=None, chunk: int = 0):
+        """Spread points held in host memory (fk_accum_add_host): x (d, n) and y
+        (n_targets, n) CPU tensors of the accumulator's dtype, page-locked for the link's
+        full rate.  They are kept alive until the next synchronising call."""
+        dt = torch.float64 if self.prec == FK_FP64 else torch.float32
+        if x.device.type != "cpu" or x.dtype != dt or x.dim() != 2 or x.shape[0] != self.d:
+            raise ValueError("x must be a CPU tensor of shape (%d, n) and dtype %s" % (self.d, dt))
+        x = x.contiguous()
+        n = x.shape[1]
+        if self.nt:
+            if y is None or y.device.type != "cpu" or y.dtype != dt or y.numel() != self.nt * n:
+                raise ValueError("y must be a CPU tensor of %d x %d values of dtype %s" % (self.nt, n, dt))
+            y = y.reshape(self.nt, n).contiguous()
+        _check(lib().fk_accum_add_host(self._h, n, x.data_ptr(), y.data_ptr() if self.nt else None, int(chunk),
+                                       _stream()))
+        self._keep.append((x, y))
 
     def system(self):
         T = torch.empty((4 * self.m + 1) ** self.d, dtype=torch.complex128, device=self.device)

@@ -671,6 +671,14 @@ struct fk_accum {
   double* corr = nullptr;    // [2 kmax + 1]
   unsigned* flags = nullptr;
   int device = 0;
+  // fk_accum_add_host: two device staging buffers of stage_pts points each ((d + nt)
+  // rows), the stream their copies run on, and per buffer the event of its copy's
+  // arrival and the event after which its last spread no longer reads it
+  void* stage[2] = {nullptr, nullptr};
+  int64_t stage_pts = 0;
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t landed[2] = {nullptr, nullptr};
+  cudaEvent_t freed[2] = {nullptr, nullptr};
 };
 
 namespace fk {
@@ -760,6 +768,65 @@ fk_status fk_accum_add(fk_accum* a, int64_t n, const void* x, const void* y, con
     FK_CUDA(cudaGetLastError());
   }
   a->n_total += n;
+  return FK_OK;
+}
+
+fk_status fk_accum_add_host(fk_accum* a, int64_t n, const void* x, const void* y, int64_t chunk, void* stream) {
+  clear_error();
+  if (!a) return set_error(FK_EINVAL, "null accumulator");
+  if (n < 0) return set_error(FK_EINVAL, "n = %lld < 0", (long long)n);
+  if (chunk < 0) return set_error(FK_EINVAL, "chunk = %lld < 0", (long long)chunk);
+  if (n == 0) return FK_OK;
+  if (!x || (a->nt > 0 && !y)) return set_error(FK_EINVAL, "null points or targets");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FK_TRY(capture_check(st, false, false, "fk_accum_add_host"));
+  NvtxRange range("fk accum add host");
+  const int64_t C = std::min(n, chunk > 0 ? chunk : FK_HOST_CHUNK_DEFAULT);
+  const size_t es = a->precision == FK_FP64 ? sizeof(double) : sizeof(float);
+  const int rows = a->d + a->nt;
+  if (!a->copy_st) {
+    FK_CUDA(cudaStreamCreateWithFlags(&a->copy_st, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+      FK_CUDA(cudaEventCreateWithFlags(&a->landed[b], cudaEventDisableTiming));
+      FK_CUDA(cudaEventCreateWithFlags(&a->freed[b], cudaEventDisableTiming));
+    }
+  }
+  if (a->stage_pts < C) {
+    // earlier spreads may still read the old buffers
+    for (int b = 0; b < 2; ++b) FK_CUDA(cudaEventSynchronize(a->freed[b]));
+    for (int b = 0; b < 2; ++b) {
+      cudaFree(a->stage[b]);
+      a->stage[b] = nullptr;
+    }
+    a->stage_pts = 0;
+    for (int b = 0; b < 2; ++b)
+      if (cudaMalloc(&a->stage[b], es * rows * static_cast<size_t>(C)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(a->stage[0]);
+        a->stage[0] = nullptr;
+        return set_error(FK_ENOMEM, "staging buffers (2 x %lld points)", (long long)C);
+      }
+    a->stage_pts = C;
+  }
+  const char* xh = static_cast<const char*>(x);
+  const char* yh = static_cast<const char*>(y);
+  for (int64_t i = 0, p0 = 0; p0 < n; ++i, p0 += C) {
+    const int b = static_cast<int>(i & 1);
+    const int64_t cnt = std::min(C, n - p0);
+    char* dst = static_cast<char*>(a->stage[b]);
+    // one copy per row of the chunk (coordinates, then targets), each landing contiguous
+    FK_CUDA(cudaStreamWaitEvent(a->copy_st, a->freed[b], 0));
+    for (int r = 0; r < rows; ++r) {
+      const char* src = r < a->d ? xh + es * (static_cast<size_t>(r) * n + p0)
+                                 : yh + es * (static_cast<size_t>(r - a->d) * n + p0);
+      FK_CUDA(cudaMemcpyAsync(dst + es * static_cast<size_t>(r) * cnt, src, es * cnt, cudaMemcpyHostToDevice,
+                              a->copy_st));
+    }
+    FK_CUDA(cudaEventRecord(a->landed[b], a->copy_st));
+    FK_CUDA(cudaStreamWaitEvent(st, a->landed[b], 0));
+    FK_TRY(fk_accum_add(a, cnt, dst, a->nt ? dst + es * static_cast<size_t>(a->d) * cnt : nullptr, nullptr, stream));
+    FK_CUDA(cudaEventRecord(a->freed[b], st));
+  }
   return FK_OK;
 }
 
@@ -959,6 +1026,16 @@ fk_status fk_accum_destroy(fk_accum* a) {
   cudaFree(a->grid);
   cudaFree(a->corr);
   cudaFree(a->flags);
+  if (a->copy_st) {
+    for (int b = 0; b < 2; ++b) cudaEventSynchronize(a->freed[b]);
+    cudaStreamSynchronize(a->copy_st);
+    for (int b = 0; b < 2; ++b) {
+      cudaFree(a->stage[b]);
+      cudaEventDestroy(a->landed[b]);
+      cudaEventDestroy(a->freed[b]);
+    }
+    cudaStreamDestroy(a->copy_st);
+  }
   if (cur != a->device) cudaSetDevice(cur);
   delete a;
   return FK_OK;

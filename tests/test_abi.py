@@ -69,3 +69,10 @@ def test_invalid_arguments_rejected_on_host(args, needle):
 
 def test_workspace_bound_is_positive():
     assert fk.lib().fk_workspace_bytes(2, 32, 10 ** 8, 1, 1e-6, 1) > 0
+
+
+def test_host_add_rejects_a_null_accumulator():
+    L = fk.lib()
+    dummy = ctypes.c_void_p(16)  # never dereferenced: validation fails first
+    assert L.fk_accum_add_host(None, 10, dummy, dummy, 0, None) == 1  # FK_EINVAL
+    assert b"null accumulator" in L.fk_last_error()
