@@ -1538,8 +1538,8 @@ __host__ __device__ inline ApLayout ap_layout(int P, int G) {
   L.toff = L.tcnt + sizeof(int) * (G + 1);                         // int [G + 1]
   L.hnext = L.toff + sizeof(int) * (G + 1);                        // int [G]
   L.gdelta = (L.hnext + sizeof(int) * G + 7) & ~static_cast<size_t>(7);  // long long [G]
-  L.bar = (L.gdelta + sizeof(long long) * G + 15) & ~static_cast<size_t>(15);
-  L.total = L.bar + 16;
+  L.bar = (L.gdelta + sizeof(long long) * G + 15) & ~static_cast<size_t>(15);  // uint64_t [P + 1]
+  L.total = L.bar + sizeof(uint64_t) * (P + 1);
   return L;
 }
 
@@ -1557,7 +1557,7 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
   int* toff = reinterpret_cast<int*>(smem + L.toff);              // tile run starts
   int* hnext = reinterpret_cast<int*>(smem + L.hnext);            // counts for the next l1
   long long* gdelta = reinterpret_cast<long long*>(smem + L.gdelta);  // bucket slot of tile slot 0
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);     // one per staged row
   // bucket starts: exclusive scan of the counts padded to 4 (G <= blockDim)
   {
     const int lane = tid & 31, warp = tid >> 5;
@@ -1578,28 +1578,40 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
     }
   }
   if (tid == 0) {
-    mbar_init(bar);
+    for (int q = 0; q <= P; ++q) mbar_init(bar + q);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
   const int64_t s0 = static_cast<int64_t>(blockIdx.x) * A.range;
   const int64_t e0 = min(A.n, s0 + A.range);
+  // Staged row q (0: coordinate l1, 1 + p: partner p) of the tile at t0 arrives on
+  // bar[q].  Each row of the next tile is requested as soon as every thread has passed
+  // the barrier after the row's last read in this tile (row 0 after the row words,
+  // row 1 + p after partner p's codes), so the loads overlap this tile's work.
+  auto issue_row = [&](int q, int64_t t) {
+    const unsigned bytes = static_cast<unsigned>(min(static_cast<int64_t>(AP_TILE), e0 - t)) * 4u;  // % 16 == 0
+    fence_proxy_async();
+    mbar_arrive_expect(bar + q, bytes);
+    bulk_g2s(stage + q * AP_TILE, A.xl1 + q * A.n + t, bytes, bar + q);
+  };
+  if (A.vec_ok && tid == 0 && s0 < e0)
+    for (int q = 0; q <= P; ++q) issue_row(q, s0);
   unsigned phase = 0;
+  // after a wait gave up: wait (bounded) for each row copy still in flight, that of the
+  // next tile (parity phase ^ 1) for rows 0 .. last when the next tile was requested,
+  // else that of this tile (a phase already complete returns at once)
+  auto drain = [&](int last, bool next) {
+    for (int q = 0; q <= P; ++q) mbar_drain(bar + q, (next && q <= last) ? (phase ^ 1u) : phase);
+  };
   for (int64_t t0 = s0; t0 < e0; t0 += AP_TILE) {
     const int cnt = static_cast<int>(min(static_cast<int64_t>(AP_TILE), e0 - t0));
+    const bool next = t0 + AP_TILE < e0;
     for (int o = tid; o <= G; o += AP_THREADS) tcnt[o] = 0;
     if (A.vec_ok) {
-      if (tid == 0) {
-        const unsigned bytes = static_cast<unsigned>(cnt) * 4u;  // cnt % 4 == 0
-        fence_proxy_async();
-        mbar_arrive_expect(bar, bytes * static_cast<unsigned>(P + 1));
-        for (int q = 0; q <= P; ++q) bulk_g2s(stage + q * AP_TILE, A.xl1 + q * A.n + t0, bytes, bar);
-      }
-      if (!mbar_wait(bar, phase, A.flags)) {
-        mbar_drain(bar, phase);
+      if (!mbar_wait(bar, phase, A.flags) || !mbar_wait(bar + 1, phase, A.flags)) {
+        drain(-1, next);
         return;
       }
-      phase ^= 1u;
     } else {
       for (int q = 0; q <= P; ++q)
         for (int i = tid; i < cnt; i += AP_THREADS) stage[q * AP_TILE + i] = __ldg(A.xl1 + q * A.n + t0 + i);
@@ -1626,6 +1638,7 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
       }
     }
     __syncthreads();
+    if (A.vec_ok && tid == 0 && next) issue_row(0, t0 + AP_TILE);
     // bucket room: one global atomic per owner present; exclusive scan of the tile counts
     int my_c = 0, my_pos = 0;
     if (tid < G) {
@@ -1678,6 +1691,10 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
     // every thread has passed the barrier in between)
     for (int p = 0; p < P; ++p) {
       unsigned* sc = scode + (p & 1) * AP_TILE;
+      if (A.vec_ok && p >= 1 && !mbar_wait(bar + 1 + p, phase, A.flags)) {
+        drain(p, next);
+        return;
+      }
 #pragma unroll
       for (int k = 0; k < AP_PER; ++k) {
         if (w1[k] == 0xFFFFFFFFu) continue;
@@ -1691,13 +1708,15 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
         sc[toff[w1[k] >> 25] + rk[k]] = code;
       }
       __syncthreads();
+      if (A.vec_ok && tid == 0 && next) issue_row(1 + p, t0 + AP_TILE);
       unsigned* out = A.code + p * A.stride;
       for (int j = tid; j < valid; j += AP_THREADS) {
         const long long at = gdj[j];
         if (at >= 0) out[at] = sc[j];
       }
     }
-    __syncthreads();  // the stage and code buffers are free for the next tile
+    __syncthreads();  // the code buffers are free for the next tile
+    phase ^= 1u;
   }
   if (A.cnt_next)
     for (int o = tid; o < G; o += AP_THREADS)
