@@ -39,6 +39,15 @@ def test_fit_additive_matches_oracle(precision, eps, tol, d, m, n):
     for li, lam in enumerate(lams):
         tho = O.fit_additive(X.astype(np.float64), y.astype(np.float64), m, lam)
         assert rel(unique_part(th[li, 0], d, m), unique_part(tho, d, m)) <= tol
+        # The intercepts are equal in exact arithmetic: the intercept columns of Sigma
+        # coincide, so v = e_(l,0) - e_(l',0) has Sigma v = 0 and (Sigma + lambda I)
+        # v = lambda v.  An error E in the computed Sigma (and b) moves theta along v by at
+        # most (|E| |theta| + |db|) / lambda, with |E| <= eps |Sigma| and |Sigma| ~ d (the
+        # all-intercepts direction); 10x margin.
+        ic = th[li, 0].reshape(d, 2 * m + 1)[:, m]
+        spread = float(np.max(np.abs(ic - ic.mean())))
+        bound = 10 * eps * d * np.linalg.norm(th[li, 0]) / lam
+        assert spread <= bound
     Xq = S.uniform_points(3000, d, 42).astype(nd)
     f = fk.fk_predict(torch.from_numpy(th[0]).cuda(), torch.from_numpy(Xq).to("cuda", td), m, eps, precision,
                       additive=True).cpu().numpy()[0]
