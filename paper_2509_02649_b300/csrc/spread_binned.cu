@@ -614,6 +614,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_bin_scatter1(PartArgs A) {
     mbar_init(bar);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
+  for (int o = tid; o <= G; o += T) tcnt[o] = 0;
   __syncthreads();
   auto issue = [&](int64_t t0) {
     const int cnt = static_cast<int>(min(static_cast<int64_t>(TILE), e0 - t0));
@@ -626,15 +627,20 @@ __global__ void __launch_bounds__(T, 1024 / T) k_bin_scatter1(PartArgs A) {
   };
   if (tid == 0 && s0 < e0) issue(s0);
   unsigned phase = 0;
+  // Three barriers per tile.  Each thread waits for the tile's bulk copy itself; the
+  // tile counts are zeroed after their last read of the tile before (between its
+  // second and third barriers), and every shared array the next tile writes before its
+  // first barrier (the counts) is one this tile no longer reads after its third, while
+  // those it writes later (run starts, bucket positions, sorted records, the staged
+  // points) are only written after that first barrier, which every thread reaches
+  // after its copy-out.
   for (int64_t t0 = s0; t0 < e0; t0 += TILE) {
     const int cnt = static_cast<int>(min(static_cast<int64_t>(TILE), e0 - t0));
-    for (int o = tid; o <= G; o += T) tcnt[o] = 0;
     if (!mbar_wait(bar, phase, A.flags)) {
       mbar_drain(bar, phase);
       return;
     }
     phase ^= 1u;
-    __syncthreads();
     // rk: the point's rank among the tile's points of its owner (its place in the
     // owner's run)
     uint4 rec[PER];
@@ -687,6 +693,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_bin_scatter1(PartArgs A) {
       }
     }
     __syncthreads();
+    for (int o = tid; o <= G; o += T) tcnt[o] = 0;  // the next tile's counts
 #pragma unroll
     for (int k = 0; k < PER; ++k)
       if (rec[k].x != 0xFFFFFFFFu) sorted[toff[rec[k].x >> 16] + rk[k]] = rec[k];
@@ -718,7 +725,6 @@ __global__ void __launch_bounds__(T, 1024 / T) k_bin_scatter1(PartArgs A) {
         }
       }
     }
-    __syncthreads();
   }
 }
 
@@ -1581,6 +1587,7 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
     for (int q = 0; q <= P; ++q) mbar_init(bar + q);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
+  for (int o = tid; o <= G; o += AP_THREADS) tcnt[o] = 0;
   __syncthreads();
   const int64_t s0 = static_cast<int64_t>(blockIdx.x) * A.range;
   const int64_t e0 = min(A.n, s0 + A.range);
@@ -1606,7 +1613,8 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
   for (int64_t t0 = s0; t0 < e0; t0 += AP_TILE) {
     const int cnt = static_cast<int>(min(static_cast<int64_t>(AP_TILE), e0 - t0));
     const bool next = t0 + AP_TILE < e0;
-    for (int o = tid; o <= G; o += AP_THREADS) tcnt[o] = 0;
+    // the tile counts were zeroed after their last read of the tile before; with bulk
+    // copies each thread waits for the staged rows itself, plain loads need a barrier
     if (A.vec_ok) {
       if (!mbar_wait(bar, phase, A.flags) || !mbar_wait(bar + 1, phase, A.flags)) {
         drain(-1, next);
@@ -1615,8 +1623,8 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
     } else {
       for (int q = 0; q <= P; ++q)
         for (int i = tid; i < cnt; i += AP_THREADS) stage[q * AP_TILE + i] = __ldg(A.xl1 + q * A.n + t0 + i);
+      __syncthreads();
     }
-    __syncthreads();
     // row word and rank of each point inside its owner's run of the tile
     unsigned w1[AP_PER];
     int rk[AP_PER];
@@ -1664,6 +1672,7 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
       }
     }
     __syncthreads();
+    for (int o = tid; o <= G; o += AP_THREADS) tcnt[o] = 0;  // the next tile's counts
     if (tid < G) {
       // the buckets are exact; a reservation beyond one (a count that disagrees with the
       // placement) is reported and its run is not written
