@@ -88,7 +88,15 @@ typedef enum { FK_SOLVER_AUTO = 0, FK_SOLVER_CHOL = 1, FK_SOLVER_CG = 2, FK_SOLV
    2-D partition + register accumulation (d = 2, ones and/or one strength channel);
    FIXED = 1-D integer fixed-point sums in shared memory (d = 1, any channel count,
    bitwise reproducible). */
-typedef enum { FK_SPREAD_AUTO = 0, FK_SPREAD_ATOMIC = 1, FK_SPREAD_BINNED = 2, FK_SPREAD_FIXED = 3 } fk_spread;
+typedef enum {
+  FK_SPREAD_AUTO = 0,
+  FK_SPREAD_ATOMIC = 1,
+  FK_SPREAD_BINNED = 2,
+  FK_SPREAD_FIXED = 3,        /* d = 1: integer (fixed-point) sums in shared memory; small grids are kept as
+                                 32 lane copies per CTA, so that each lane's atomics go to its own bank */
+  FK_SPREAD_FIXED_SHARED = 4  /* FIXED with one copy of each grid per CTA (no lane copies); the same sums
+                                 bit for bit, since integer sums do not depend on the order of the adds */
+} fk_spread;
 
 /* Options; pass NULL for defaults (fk_default_opts). */
 typedef struct {
@@ -99,7 +107,8 @@ typedef struct {
   double sobolev_c0;  /* c0 in lambda (c0 + |k|^{2s}); the paper's value is 1 (default 1) */
   double upsampfac;   /* minimum fine-grid oversampling sigma (default 1.9; grids are powers of 2) */
   int spread;         /* fk_spread: AUTO = BINNED (d = 2) or FIXED (d = 1) for FK_MIXED where the
-                         shape allows, else ATOMIC; FK_FP64 always spreads with ATOMIC */
+                         shape allows, else ATOMIC; FK_FP64 always spreads with ATOMIC; FIXED_SHARED
+                         as FIXED without lane copies */
   int deterministic;  /* 1: run-to-run identical type-1 sums (T, b, and the additive blocks): every
                          contribution is rounded to a 64-bit fixed-point integer (scale 2^(61-e)
                          with n max|strength| <= 2^e) and summed with integer atomics, for d = 1,

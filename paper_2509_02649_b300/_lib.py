@@ -22,7 +22,7 @@ from .build import lib_path
 FK_FP64, FK_MIXED = 0, 1
 FK_PEN_SOBOLEV, FK_PEN_LOWBIAS = 0, 1
 FK_SOLVER_AUTO, FK_SOLVER_CHOL, FK_SOLVER_CG, FK_SOLVER_EIG = 0, 1, 2, 3
-FK_SPREAD_AUTO, FK_SPREAD_ATOMIC, FK_SPREAD_BINNED, FK_SPREAD_FIXED = 0, 1, 2, 3
+FK_SPREAD_AUTO, FK_SPREAD_ATOMIC, FK_SPREAD_BINNED, FK_SPREAD_FIXED, FK_SPREAD_FIXED_SHARED = 0, 1, 2, 3, 4
 
 STATUS = {0: "FK_OK", 1: "FK_EINVAL", 2: "FK_ERANGE", 3: "FK_ENOMEM", 4: "FK_ECUDA", 5: "FK_ENOTPD",
           6: "FK_ENOCONV", 7: "FK_ETIMEOUT", 8: "FK_EINTERNAL"}

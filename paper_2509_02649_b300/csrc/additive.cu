@@ -106,7 +106,8 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
     Scratch inner(st);  // released (stream-ordered) after each coordinate
     if (fixed1d)
       FK_TRY(spread1d_fixed(p1, n, reinterpret_cast<const float*>(x + static_cast<int64_t>(l) * n),
-                            reinterpret_cast<const float*>(y), nt, true, amax, grid1, false, flags, st, inner, o.autotune != 0));
+                            reinterpret_cast<const float*>(y), nt, true, amax, grid1, false, flags, st, inner, o.autotune != 0,
+                            o.spread != FK_SPREAD_FIXED_SHARED));
     else if (det)
       FK_TRY(spread_deterministic<R>(p1, n, x + static_cast<int64_t>(l) * n, y, nt, true, grid1, flags, st, inner));
     else

@@ -211,14 +211,14 @@ static fk_status spread_any(const EsPlan& p, int precision, const fk_opts& o, in
     return spread_atomic<double>(p, n, static_cast<const double*>(x), static_cast<const double*>(y), n_y,
                                  with_ones, grid, flags, st);
   const int nc = n_y + (with_ones ? 1 : 0);
-  if (p.d == 1 && (o.spread == FK_SPREAD_FIXED ||
-                   (o.spread == FK_SPREAD_AUTO && spread1d_fixed_supported(p, n_y, with_ones)))) {
+  const bool fixed_req = o.spread == FK_SPREAD_FIXED || o.spread == FK_SPREAD_FIXED_SHARED;
+  if (p.d == 1 && (fixed_req || (o.spread == FK_SPREAD_AUTO && spread1d_fixed_supported(p, n_y, with_ones)))) {
     if (!spread1d_fixed_supported(p, n_y, with_ones))
       return set_error(FK_EINVAL, "fixed-point spreading does not support N=%d w=%d channels=%d", p.N, p.w, nc);
     return spread1d_fixed(p, n, static_cast<const float*>(x), static_cast<const float*>(y), n_y, with_ones, nullptr,
-                          grid, false, flags, st, scr, o.autotune != 0);
+                          grid, false, flags, st, scr, o.autotune != 0, o.spread != FK_SPREAD_FIXED_SHARED);
   }
-  if (o.spread == FK_SPREAD_FIXED) return set_error(FK_EINVAL, "fixed-point spreading is built for d = 1");
+  if (fixed_req) return set_error(FK_EINVAL, "fixed-point spreading is built for d = 1");
   const bool binned = (o.spread == FK_SPREAD_BINNED) ||
                       (o.spread == FK_SPREAD_AUTO && spread_binned_supported(p, n_y, with_ones));
   if (binned) {
@@ -758,7 +758,8 @@ fk_status fk_accum_add(fk_accum* a, int64_t n, const void* x, const void* y, con
   if (a->precision == FK_MIXED && a->d == 1 && a->o.spread != FK_SPREAD_ATOMIC &&
       spread1d_fixed_supported(p, a->nt, true)) {
     FK_TRY(spread1d_fixed(p, n, static_cast<const float*>(x), static_cast<const float*>(y), a->nt, true, y_absmax,
-                          a->grid, true, a->flags, st, scr, a->o.autotune != 0));
+                          a->grid, true, a->flags, st, scr, a->o.autotune != 0,
+                          a->o.spread != FK_SPREAD_FIXED_SHARED));
   } else {
     const int64_t G = ipow(p.N, a->d) * (1 + a->nt);
     double* tmp = nullptr;

@@ -244,7 +244,7 @@ fk_status additive_pairs_row(AddPairState& S, int l1, double* grids, unsigned* f
 bool spread1d_fixed_supported(const EsPlan& p, int n_y, bool with_ones);
 fk_status spread1d_fixed(const EsPlan& p, int64_t n, const float* x, const float* y, int n_y, bool with_ones,
                          const unsigned* y_absmax, double* grid, bool accumulate, unsigned* flags, cudaStream_t st,
-                         Scratch& scratch, bool autotune = false);
+                         Scratch& scratch, bool autotune = false, bool lane_copies = true);
 // amax[c] = bit pattern of max_i |y[c][i]| (amax zeroed here first)
 fk_status absmax_channels(int64_t n, const float* y, int n_y, unsigned* amax, cudaStream_t st);
 

@@ -22,6 +22,14 @@
 // shared memory); the CTAs of a group split the points into contiguous ranges; at
 // the end each CTA adds its low words into the global int64 accumulator, which a
 // last kernel scales back into the fp64 grid.
+//
+// Lane replicas (small grids, REP): the 32 lanes' windows start at unrelated nodes, so
+// one warp's atomics land on ~3.6 words of the same bank on average and the shared-
+// memory pipe serialises them.  When 32 copies of the group's grids fit in shared
+// memory they are stored node-major with the lane index fastest (word (c, node) of
+// lane L at ((c stride + node) 32 + L)): every lane adds into its own copy, which is
+// its own bank, so each atomic instruction is one wavefront.  The copies are summed
+// (as integers, so the result is the same bit for bit) when the CTA flushes.
 #include "fk_internal.cuh"
 #include "window.cuh"
 #include "es_poly.cuh"
@@ -74,7 +82,7 @@ __device__ __forceinline__ int scale_exp(float v) {
   return e;
 }
 
-template <int W>
+template <int W, bool REP>
 __global__ void __launch_bounds__(THREADS) k_spread1d_fx(Fx1dArgs A) {
   extern __shared__ unsigned smem_fx[];
   const int b = blockIdx.x;
@@ -90,8 +98,12 @@ __global__ void __launch_bounds__(THREADS) k_spread1d_fx(Fx1dArgs A) {
   // The low words start at 2^31 (the sums at that bias), so a signed sum hovering
   // around zero never wraps and the carry branch stays cold.
   const int stride = N + HALO;
-  unsigned* lo = smem_fx;
-  for (int i = threadIdx.x; i < nc * stride; i += blockDim.x) lo[i] = 0x80000000u;
+  // REP: word (c, node) of lane L at ((c stride + node) << 5) | L (lane L's own bank)
+  const int lane = threadIdx.x & 31;
+  unsigned* lo = smem_fx + (REP ? lane : 0);
+  constexpr int SH = REP ? 5 : 0;
+  const int words = (nc * stride) << SH;
+  for (int i = threadIdx.x; i < words; i += blockDim.x) smem_fx[i] = 0x80000000u;
 
   // per-channel scales
   float S[CG];
@@ -123,13 +135,13 @@ __global__ void __launch_bounds__(THREADS) k_spread1d_fx(Fx1dArgs A) {
     for (int c = 0; c < CG; ++c) {
       if (c >= nc) break;
       const float v = yv[c] * S[c];
-      unsigned* lc = lo + c * stride + b;
+      unsigned* lc = lo + ((c * stride + b) << SH);
       unsigned old[W];
       int qv[W];
 #pragma unroll
       for (int a = 0; a < W; ++a) {
         qv[a] = __float_as_int(fmaf(psi[a], v, MAGIC)) - MAGIC_BITS;
-        old[a] = atomicAdd(lc + a, static_cast<unsigned>(qv[a]));
+        old[a] = atomicAdd(lc + (a << SH), static_cast<unsigned>(qv[a]));
       }
       // a low word can wrap only if it was within |q| <= 2^21 (+1 for a tap rounding
       // above 1) of 0 mod 2^32 before the add: one unsigned min over the taps screens
@@ -203,7 +215,16 @@ __global__ void __launch_bounds__(THREADS) k_spread1d_fx(Fx1dArgs A) {
   // add the CTA's integer grids (halo folded onto nodes 0 .. HALO - 1) into the
   // global accumulators
   for (int t = threadIdx.x; t < nc * stride; t += blockDim.x) {
-    const long long v = static_cast<long long>(lo[t]) - 0x80000000LL;
+    long long v;
+    if constexpr (REP) {
+      // the 32 lane copies of word t, read from bank (r + lane) at step r: conflict free
+      const unsigned* row = smem_fx + (t << 5);
+      v = 0;
+#pragma unroll 8
+      for (int r = 0; r < 32; ++r) v += static_cast<long long>(row[(r + lane) & 31]) - 0x80000000LL;
+    } else {
+      v = static_cast<long long>(lo[t]) - 0x80000000LL;
+    }
     if (v != 0) {
       const int c = t / stride, node = (t - c * stride) & (N - 1);
       atomicAdd(A.acc + static_cast<int64_t>(c0 + c) * N + node, static_cast<unsigned long long>(v));
@@ -242,27 +263,27 @@ __global__ void k_fx_to_grid(int64_t total, int N, int with_ones, const unsigned
 using FxFn = void (*)(Fx1dArgs);
 
 template <int W>
-FxFn fx_fn() {
-  return k_spread1d_fx<W>;
+FxFn fx_fn(bool rep) {
+  return rep ? k_spread1d_fx<W, true> : k_spread1d_fx<W, false>;
 }
 
-FxFn pick_fx(int w) {
+FxFn pick_fx(int w, bool rep) {
   switch (w) {
-    case 2: return fx_fn<2>();
-    case 3: return fx_fn<3>();
-    case 4: return fx_fn<4>();
-    case 5: return fx_fn<5>();
-    case 6: return fx_fn<6>();
-    case 7: return fx_fn<7>();
-    case 8: return fx_fn<8>();
-    case 9: return fx_fn<9>();
-    case 10: return fx_fn<10>();
-    case 11: return fx_fn<11>();
-    case 12: return fx_fn<12>();
-    case 13: return fx_fn<13>();
-    case 14: return fx_fn<14>();
-    case 15: return fx_fn<15>();
-    case 16: return fx_fn<16>();
+    case 2: return fx_fn<2>(rep);
+    case 3: return fx_fn<3>(rep);
+    case 4: return fx_fn<4>(rep);
+    case 5: return fx_fn<5>(rep);
+    case 6: return fx_fn<6>(rep);
+    case 7: return fx_fn<7>(rep);
+    case 8: return fx_fn<8>(rep);
+    case 9: return fx_fn<9>(rep);
+    case 10: return fx_fn<10>(rep);
+    case 11: return fx_fn<11>(rep);
+    case 12: return fx_fn<12>(rep);
+    case 13: return fx_fn<13>(rep);
+    case 14: return fx_fn<14>(rep);
+    case 15: return fx_fn<15>(rep);
+    case 16: return fx_fn<16>(rep);
     default: return nullptr;
   }
 }
@@ -290,24 +311,40 @@ bool spread1d_fixed_supported(const EsPlan& p, int n_y, bool with_ones) {
 
 namespace {
 
-// channels per CTA at most for this grid size (shared-memory budget and CG)
-int channel_cap(int N) {
-  return static_cast<int>(std::min<size_t>(CG, SMEM_BUDGET / (4 * static_cast<size_t>(N + HALO))));
+// channels per CTA at most for this grid size (shared-memory budget and CG); rep: with
+// 32 lane copies of each grid
+int channel_cap(int N, bool rep = false) {
+  const size_t per = 4 * static_cast<size_t>(N + HALO) * (rep ? 32 : 1);
+  return static_cast<int>(std::min<size_t>(CG, SMEM_BUDGET / per));
 }
+
+// shape of a launch: channels per CTA (0: default) and lane copies; the autotuner's
+// table holds it as one int, channels + 1000 with lane copies
+struct Fx1dShape {
+  int cmax;
+  bool rep;
+};
+inline int shape_code(Fx1dShape s) { return s.cmax + (s.rep ? 1000 : 0); }
+inline Fx1dShape shape_of(int v) { return Fx1dShape{v % 1000, v >= 1000}; }
 
 fk_status spread1d_run(const EsPlan& p, int64_t n, const float* x, const float* y, int n_y, bool with_ones,
                        const unsigned* y_absmax, double* grid, bool accumulate, unsigned* flags, cudaStream_t st,
-                       Scratch& scr, int cmax_req) {
+                       Scratch& scr, Fx1dShape shape) {
   const int nc = n_y + (with_ones ? 1 : 0);
   const int N = p.N;
   if (!accumulate) FK_CUDA(cudaMemsetAsync(grid, 0, sizeof(double) * N * nc, st));
   if (n == 0) return FK_OK;
 
-  // default: half the shared-memory cap, so that two 1024-thread CTAs share an SM (the
-  // fastest measured shape at N = 8192, 17 channels)
-  int cmax = channel_cap(N);
+  // default (cmax 0): with lane copies (where 32 copies of one channel fit: small
+  // grids), as many channels per CTA as fit; without, half the shared-memory cap, so
+  // that two 1024-thread CTAs share an SM (the fastest measured shape at N = 8192, 17
+  // channels)
+  const int cmax_req = shape.cmax;
+  const int rcap = channel_cap(N, true);
+  const bool rep = shape.rep && rcap >= 1 && (nc + rcap - 1) / rcap <= MAXGRP;
+  int cmax = channel_cap(N, rep);
   if (cmax_req > 0 && cmax_req < cmax) cmax = cmax_req;
-  else if (cmax_req <= 0) cmax = (cmax + 1) / 2;
+  else if (cmax_req <= 0 && !rep) cmax = (cmax + 1) / 2;
   if ((nc + cmax - 1) / cmax > MAXGRP) cmax = (nc + MAXGRP - 1) / MAXGRP;
   const int ngrp = (nc + cmax - 1) / cmax;
   Fx1dArgs A{};
@@ -333,14 +370,16 @@ fk_status spread1d_run(const EsPlan& p, int64_t n, const float* x, const float* 
     A.grp_c0[g] = c;
     A.grp_nc[g] = sz;
     c += sz;
-    smem_max = std::max(smem_max, sizeof(unsigned) * static_cast<size_t>(sz) * (N + HALO));
+    smem_max = std::max(smem_max, sizeof(unsigned) * static_cast<size_t>(sz) * (N + HALO) * (rep ? 32 : 1));
   }
   // CTAs: as many as fit on the device at once, shared out by channel count, and no
-  // more than one per 4096 points (each CTA zeroes and flushes whole grids)
+  // more than one per 4096 points, 32768 with lane copies (each CTA zeroes and flushes
+  // whole grids)
   const int sms = std::max(1, sm_count());
   const int per_sm = std::max(1, std::min<int>(2, static_cast<int>((228 * 1024) / (smem_max + 1024))));
   const int64_t total_ctas = static_cast<int64_t>(sms) * per_sm;
-  const int64_t by_n = std::max<int64_t>(1, (n + 4095) / 4096);
+  const int64_t per_cta = rep ? 32768 : 4096;  // lane copies: 32 times the grid words to zero and flush
+  const int64_t by_n = std::max<int64_t>(1, (n + per_cta - 1) / per_cta);
   A.grp_b0[0] = 0;
   for (int g = 0; g < ngrp; ++g) {
     int64_t k = (total_ctas * A.grp_nc[g] + nc - 1) / nc;
@@ -362,7 +401,7 @@ fk_status spread1d_run(const EsPlan& p, int64_t n, const float* x, const float* 
   FK_TRY(scr.alloc(&A.acc, static_cast<size_t>(nc) * N));
   FK_CUDA(cudaMemsetAsync(A.acc, 0, sizeof(unsigned long long) * nc * N, st));
 
-  const FxFn fn = pick_fx(p.w);
+  const FxFn fn = pick_fx(p.w, rep);
   if (!fn) return set_error(FK_EINVAL, "1-D fixed-point spreading: w = %d not built", p.w);
   FK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_max)));
   KernelTimer* kt = kernel_timer();
@@ -384,28 +423,34 @@ fk_status spread1d_run(const EsPlan& p, int64_t n, const float* x, const float* 
 
 fk_status spread1d_fixed(const EsPlan& p, int64_t n, const float* x, const float* y, int n_y, bool with_ones,
                          const unsigned* y_absmax, double* grid, bool accumulate, unsigned* flags, cudaStream_t st,
-                         Scratch& scr, bool autotune) {
+                         Scratch& scr, bool autotune, bool lane_copies) {
   if (!spread1d_fixed_supported(p, n_y, with_ones))
     return set_error(FK_EINVAL, "1-D fixed-point spreading: unsupported shape (N = %d, w = %d)", p.N, p.w);
   const int nc = n_y + (with_ones ? 1 : 0);
   int lg = 0;
   while ((static_cast<int64_t>(1) << (lg + 1)) <= n) ++lg;
+  // without lane copies: the default shape without them (not tuned)
+  if (!lane_copies)
+    return spread1d_run(p, n, x, y, n_y, with_ones, y_absmax, grid, accumulate, flags, st, scr, Fx1dShape{0, false});
   const TuneKey key{TUNE_SPREAD1D, p.N, p.w, nc, lg};
   int cm = 0;
   if (tune_lookup_int(key, &cm) || !autotune || n < (1 << 20))
-    return spread1d_run(p, n, x, y, n_y, with_ones, y_absmax, grid, accumulate, flags, st, scr, cm);
+    return spread1d_run(p, n, x, y, n_y, with_ones, y_absmax, grid, accumulate, flags, st, scr,
+                        cm > 0 ? shape_of(cm) : Fx1dShape{0, true});
   // trials write a scratch grid when the call adds into the caller's grid
   double* tgrid = grid;
   if (accumulate) FK_TRY(scr.alloc(&tgrid, static_cast<size_t>(p.N) * nc));
   // channels per CTA: more channels share each point's weights, fewer let more CTAs
-  // reside per SM; time each on this call's data (the grid is rewritten each time)
-  const int cap = channel_cap(p.N);
-  std::vector<int> opts = {cap};
-  for (int c = cap - 1; c >= 1 && opts.size() < 5; --c) opts.push_back(c);
+  // reside per SM; with or without lane copies where they fit; time each on this
+  // call's data (the grid is rewritten each time)
+  const int cap = channel_cap(p.N), rcap = channel_cap(p.N, true);
+  std::vector<int> opts;
+  for (int c = rcap; c >= 1 && opts.size() < 3; --c) opts.push_back(shape_code(Fx1dShape{c, true}));
+  for (int c = cap; c >= 1 && opts.size() < 8; --c) opts.push_back(shape_code(Fx1dShape{c, false}));
   cudaEvent_t e0, e1;
   FK_CUDA(cudaEventCreate(&e0));
   FK_CUDA(cudaEventCreate(&e1));
-  int best = cap;
+  int best = opts[0];
   float best_ms = 1e30f;
   std::string log;
   fk_status rc = FK_OK;
@@ -414,7 +459,7 @@ fk_status spread1d_fixed(const EsPlan& p, int64_t n, const float* x, const float
     cudaEventRecord(e0, st);
     {
       Scratch inner(st);
-      rc = spread1d_run(p, n, x, y, n_y, with_ones, y_absmax, tgrid, false, flags, st, inner, c);
+      rc = spread1d_run(p, n, x, y, n_y, with_ones, y_absmax, tgrid, false, flags, st, inner, shape_of(c));
     }
     cudaEventRecord(e1, st);
     if (rc != FK_OK) break;
@@ -423,7 +468,8 @@ fk_status spread1d_fixed(const EsPlan& p, int64_t n, const float* x, const float
     cudaEventElapsedTime(&ms, e0, e1);
     if (i == 0) continue;
     char line[64];
-    snprintf(line, sizeof(line), "%schannels/CTA=%d %.3f ms", log.empty() ? "" : "; ", c, ms);
+    snprintf(line, sizeof(line), "%schannels/CTA=%d%s %.3f ms", log.empty() ? "" : "; ", c % 1000,
+             c >= 1000 ? " lane copies" : "", ms);
     log += line;
     if (ms < best_ms) {
       best_ms = ms;
@@ -434,9 +480,10 @@ fk_status spread1d_fixed(const EsPlan& p, int64_t n, const float* x, const float
   cudaEventDestroy(e1);
   FK_TRY(rc);
   char line[64];
-  snprintf(line, sizeof(line), "  ->  channels/CTA=%d (%.3f ms)", best, best_ms);
+  snprintf(line, sizeof(line), "  ->  channels/CTA=%d%s (%.3f ms)", best % 1000, best >= 1000 ? " lane copies" : "",
+           best_ms);
   tune_store_int(key, best, log + line);
-  return spread1d_run(p, n, x, y, n_y, with_ones, y_absmax, grid, accumulate, flags, st, scr, best);
+  return spread1d_run(p, n, x, y, n_y, with_ones, y_absmax, grid, accumulate, flags, st, scr, shape_of(best));
 }
 
 }  // namespace fk

@@ -85,6 +85,37 @@ def test_fixed_spread_against_atomic_spread():
     assert rel(host(bf), host(ba)) < 1e-6
 
 
+@pytest.mark.parametrize("m,nt,n", [(20, 2, 300_001), (50, 1, 1_000_000), (50, 4, 77_777), (100, 0, 2_000_003),
+                                    (50, 1, 3)])
+def test_fixed_spread_lane_copies_match_one_copy(m, nt, n):
+    # grids of 256, 512 and 1024 nodes, where 32 lane copies fit in shared memory: the
+    # integer sums are the same whichever copy each addition went to, so the moments
+    # and right-hand sides agree bit for bit with the one-copy layout (ragged n takes the
+    # scalar load path; the last case has a single CTA and three points)
+    x, y = sweep_sample(n, max(nt, 1))
+    X = dev(x)
+    Y = dev(y[:nt]) if nt else None
+    T1, b1 = fk.fk_build_system(X, Y, m, 1e-6, "mixed", opts=fk.default_opts(spread=fk.FK_SPREAD_FIXED))
+    T0, b0 = fk.fk_build_system(X, Y, m, 1e-6, "mixed", opts=fk.default_opts(spread=fk.FK_SPREAD_FIXED_SHARED))
+    assert torch.equal(T1, T0) and torch.equal(b1, b0)
+    To = O.moments(x.astype(np.float64), m)
+    assert rel(host(T1), To) < 1e-5
+
+
+def test_fixed_spread_lane_copies_low_words_wrap():
+    # every point at one node: each lane copy's low words wrap many times, and the
+    # carries go to the shared high words; same sums as the one-copy layout
+    n, m = 2_000_000, 50
+    x = np.full((1, n), np.float32(-1.1), dtype=np.float32)
+    y = (1.0 + 0.5 * np.random.default_rng(5).random((1, n))).astype(np.float32)
+    X, Y = dev(x), dev(y)
+    T1, b1 = fk.fk_build_system(X, Y, m, 1e-6, "mixed", opts=fk.default_opts(spread=fk.FK_SPREAD_FIXED))
+    T0, b0 = fk.fk_build_system(X, Y, m, 1e-6, "mixed", opts=fk.default_opts(spread=fk.FK_SPREAD_FIXED_SHARED))
+    assert torch.equal(T1, T0) and torch.equal(b1, b0)
+    j = np.arange(-2 * m, 2 * m + 1)
+    assert rel(host(T1), np.exp(-1j * j * np.float64(x[0, 0]))) < 1e-5
+
+
 def test_fixed_spread_is_bitwise_reproducible():
     x, y = sweep_sample(200_000)
     X, Y = dev(x), dev(y)
