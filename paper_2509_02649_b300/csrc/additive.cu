@@ -60,6 +60,23 @@ __global__ void k_add_into(int64_t n, const double* a, double* acc) {
     acc[i] += a[i];
 }
 
+// Two non-blocking streams per device and host thread for work forked off the caller's
+// stream (joined back before the call returns), created on first use and kept: a stream
+// that joined a capture must outlive it, and per-thread streams keep one thread's
+// capture from taking in another thread's work.
+fk_status side_streams(cudaStream_t out[2]) {
+  constexpr int MAXD = 64;
+  thread_local cudaStream_t tab[MAXD][2] = {};
+  int dev = 0;
+  FK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= MAXD) return set_error(FK_EINTERNAL, "side streams: device %d", dev);
+  for (int k = 0; k < 2; ++k) {
+    if (!tab[dev][k]) FK_CUDA(cudaStreamCreateWithFlags(&tab[dev][k], cudaStreamNonBlocking));
+    out[k] = tab[dev][k];
+  }
+  return FK_OK;
+}
+
 template <typename R>
 fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, int m, const double* lambdas,
                             int n_lambda, double eps, int precision, const fk_opts& o, double* theta,
@@ -141,19 +158,48 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
   FK_TRY(es_correction(p2, corr2, st));
   stage_range.next("fk additive pairs");
   if (rowpairs) {
+    // Partitions on the caller's stream, in order; accumulation l1 on side stream l1 & 1
+    // (record set l1 & 1), so that the next partition and accumulation fill the SMs that
+    // an accumulation's last wave leaves idle (128 owners x P partners of one-SM CTAs),
+    // instead of each launch ending in a part-filled wave.  Partition l1 + 2 waits for
+    // accumulation l1, which reads the same record set.
     const int64_t NN = static_cast<int64_t>(p2.N) * p2.N;
     AddPairState S;
     double* pg = nullptr;
-    FK_TRY(scr.alloc(&pg, static_cast<size_t>(d - 1) * NN));
+    FK_TRY(scr.alloc(&pg, static_cast<size_t>(npairs) * NN));
     FK_TRY(additive_pairs_begin(p2, d, n, reinterpret_cast<const float*>(x), flags, st, scr, &S));
-    int pair = 0;
-    for (int l1 = 0; l1 + 1 < d; ++l1) {
-      FK_TRY(additive_pairs_row(S, l1, pg, flags, st));
-      for (int l2 = l1 + 1; l2 < d; ++l2, ++pair) {
-        Scratch inner(st);
-        FK_TRY(grid_to_modes<float>(p2, pg + (l2 - l1 - 1) * NN, 0, 1, m, corr2, inv_n,
-                                    Bp + 2 * static_cast<int64_t>(pair) * K * K, st, inner));
-      }
+    cudaStream_t side[2];
+    FK_TRY(side_streams(side));
+    cudaEvent_t ev_part = nullptr, ev_done[2] = {};
+    FK_CUDA(cudaEventCreateWithFlags(&ev_part, cudaEventDisableTiming));
+    FK_CUDA(cudaEventCreateWithFlags(&ev_done[0], cudaEventDisableTiming));
+    FK_CUDA(cudaEventCreateWithFlags(&ev_done[1], cudaEventDisableTiming));
+    bool used[2] = {false, false};
+    fk_status rc = FK_OK;
+    int pair0 = 0;
+    for (int l1 = 0; l1 + 1 < d && rc == FK_OK; ++l1) {
+      const int s = l1 & 1;
+      if (used[s]) FK_CUDA(cudaStreamWaitEvent(st, ev_done[s], 0));
+      rc = additive_pairs_part(S, l1, flags, st);
+      if (rc != FK_OK) break;
+      FK_CUDA(cudaEventRecord(ev_part, st));
+      FK_CUDA(cudaStreamWaitEvent(side[s], ev_part, 0));
+      rc = additive_pairs_acc(S, l1, pg + pair0 * NN, flags, side[s]);
+      FK_CUDA(cudaEventRecord(ev_done[s], side[s]));
+      used[s] = true;
+      pair0 += d - 1 - l1;
+    }
+    // join the side streams (also after an error, so that nothing is left forked)
+    for (int s = 0; s < 2; ++s)
+      if (used[s]) FK_CUDA(cudaStreamWaitEvent(st, ev_done[s], 0));
+    cudaEventDestroy(ev_part);
+    cudaEventDestroy(ev_done[0]);
+    cudaEventDestroy(ev_done[1]);
+    FK_TRY(rc);
+    for (int pair = 0; pair < npairs; ++pair) {
+      Scratch inner(st);
+      FK_TRY(grid_to_modes<float>(p2, pg + pair * NN, 0, 1, m, corr2, inv_n,
+                                  Bp + 2 * static_cast<int64_t>(pair) * K * K, st, inner));
     }
   }
   int pair = 0;

@@ -1749,11 +1749,13 @@ fk_status additive_pairs_begin(const EsPlan& p, int d, int64_t n, const float* x
   S->x = x;
   S->G = p.N / 2;
   S->stride = (n + 4LL * S->G + 16 + 3) & ~static_cast<int64_t>(3);
-  // counts of rows l (current) and l + 1 (next): [2][G]; fill [G]
-  FK_TRY(scr.alloc(&S->cnt, 3 * static_cast<size_t>(S->G)));
-  FK_TRY(scr.alloc(&S->o1, static_cast<size_t>(S->stride)));
-  FK_TRY(scr.alloc(&S->code, static_cast<size_t>(S->stride) * (d - 1)));
-  FK_CUDA(cudaMemsetAsync(S->cnt, 0, sizeof(int) * 3 * S->G, st));
+  // counts of each coordinate's rows: [d][G]; fill [G]
+  FK_TRY(scr.alloc(&S->cnt, (static_cast<size_t>(d) + 1) * S->G));
+  for (int s = 0; s < 2 && s < d - 1; ++s) {
+    FK_TRY(scr.alloc(&S->o1[s], static_cast<size_t>(S->stride)));
+    FK_TRY(scr.alloc(&S->code[s], static_cast<size_t>(S->stride) * (d - 1 - s)));
+  }
+  FK_CUDA(cudaMemsetAsync(S->cnt, 0, sizeof(int) * (d + 1) * S->G, st));
   AddPartArgs A{};
   const CoordConst cc = coord_const(p.N);
   A.N = p.N;
@@ -1770,16 +1772,15 @@ fk_status additive_pairs_begin(const EsPlan& p, int d, int64_t n, const float* x
   return FK_OK;
 }
 
-fk_status additive_pairs_row(AddPairState& S, int l1, double* grids, unsigned* flags, cudaStream_t st) {
+fk_status additive_pairs_part(AddPairState& S, int l1, unsigned* flags, cudaStream_t st) {
   const EsPlan& p = S.p;
   const int G = S.G, P = S.d - 1 - l1, N = p.N;
   if (P < 1) return FK_OK;
-  int* cnt = S.cnt + (l1 & 1) * G;
-  int* cnt_next = S.cnt + ((l1 + 1) & 1) * G;
-  int* fill = S.cnt + 2 * G;
+  int* cnt = S.cnt + l1 * G;
+  int* cnt_next = S.cnt + (l1 + 1) * G;  // zeroed by begin
+  int* fill = S.cnt + S.d * G;
   const int sms = sm_count();
   FK_CUDA(cudaMemsetAsync(fill, 0, sizeof(int) * G, st));
-  if (l1 + 2 <= S.d - 1) FK_CUDA(cudaMemsetAsync(cnt_next, 0, sizeof(int) * G, st));
   AddPartArgs A{};
   const CoordConst cc = coord_const(N);
   A.N = N;
@@ -1794,8 +1795,8 @@ fk_status additive_pairs_row(AddPairState& S, int l1, double* grids, unsigned* f
   A.cnt = cnt;
   A.fill = fill;
   A.cnt_next = (l1 + 2 <= S.d - 1) ? cnt_next : nullptr;  // rows of l1 + 1 are needed if it has partners
-  A.o1 = S.o1;
-  A.code = S.code;
+  A.o1 = S.o1[l1 & 1];
+  A.code = S.code[l1 & 1];
   A.stride = S.stride;
   A.flags = flags;
   A.c_hi = cc.hi;
@@ -1804,7 +1805,13 @@ fk_status additive_pairs_row(AddPairState& S, int l1, double* grids, unsigned* f
   FK_CUDA(cudaFuncSetAttribute(k_add_part, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm_part)));
   k_add_part<<<nblk, AP_THREADS, sm_part, st>>>(A); note_launch();
   FK_CUDA(cudaGetLastError());
+  return FK_OK;
+}
 
+fk_status additive_pairs_acc(AddPairState& S, int l1, double* grids, unsigned* flags, cudaStream_t st) {
+  const EsPlan& p = S.p;
+  const int G = S.G, P = S.d - 1 - l1, N = p.N;
+  if (P < 1) return FK_OK;
   // accumulation: CTA (owner b, partner sub), owners of two rows (2N cells, one lane each)
   FK_CUDA(cudaMemsetAsync(grids, 0, sizeof(double) * N * N * P, st));
   AccArgs B{};
@@ -1816,9 +1823,9 @@ fk_status additive_pairs_row(AddPairState& S, int l1, double* grids, unsigned* f
   B.beta = static_cast<float>(p.beta);
   B.poly = es_poly(p.w, p.beta);
   B.with_ones = 1;
-  B.tot = cnt;
-  B.rec = reinterpret_cast<const uint4*>(S.code);
-  B.ybuf = reinterpret_cast<const float*>(S.o1);
+  B.tot = S.cnt + l1 * G;
+  B.rec = reinterpret_cast<const uint4*>(S.code[l1 & 1]);
+  B.ybuf = reinterpret_cast<const float*>(S.o1[l1 & 1]);
   B.grid = grids;
   B.flags = flags;
   B.mode = 0;
