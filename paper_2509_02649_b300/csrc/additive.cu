@@ -8,6 +8,8 @@
 //             transpose
 // right-hand side b_l[k] = (1/n) sum_i Y_i e^{-i k X_il}, and theta = (Sigma + lambda I)^{-1} b
 // by a dense FP64 Cholesky solve of size d(2m+1) with one refinement step.
+#include <functional>
+
 #include "fk_internal.cuh"
 
 namespace fk {
@@ -60,17 +62,18 @@ __global__ void k_add_into(int64_t n, const double* a, double* acc) {
     acc[i] += a[i];
 }
 
-// Two non-blocking streams per device and host thread for work forked off the caller's
+// Non-blocking streams per device and host thread for work forked off the caller's
 // stream (joined back before the call returns), created on first use and kept: a stream
 // that joined a capture must outlive it, and per-thread streams keep one thread's
 // capture from taking in another thread's work.
-fk_status side_streams(cudaStream_t out[2]) {
+constexpr int NSIDE = 3;
+fk_status side_streams(cudaStream_t out[NSIDE]) {
   constexpr int MAXD = 64;
-  thread_local cudaStream_t tab[MAXD][2] = {};
+  thread_local cudaStream_t tab[MAXD][NSIDE] = {};
   int dev = 0;
   FK_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= MAXD) return set_error(FK_EINTERNAL, "side streams: device %d", dev);
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < NSIDE; ++k) {
     if (!tab[dev][k]) FK_CUDA(cudaStreamCreateWithFlags(&tab[dev][k], cudaStreamNonBlocking));
     out[k] = tab[dev][k];
   }
@@ -119,27 +122,68 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
     FK_TRY(absmax_channels(n, reinterpret_cast<const float*>(y), nt, amax, st));
   }
   NvtxRange stage_range("fk additive 1-D");
-  for (int l = 0; l < d; ++l) {
-    Scratch inner(st);  // released (stream-ordered) after each coordinate
-    if (fixed1d)
-      FK_TRY(spread1d_fixed(p1, n, reinterpret_cast<const float*>(x + static_cast<int64_t>(l) * n),
-                            reinterpret_cast<const float*>(y), nt, true, amax, grid1, false, flags, st, inner, o.autotune != 0,
-                            o.spread != FK_SPREAD_FIXED_SHARED));
-    else if (det)
-      FK_TRY(spread_deterministic<R>(p1, n, x + static_cast<int64_t>(l) * n, y, nt, true, grid1, flags, st, inner));
-    else
-      FK_TRY(spread_atomic<R>(p1, n, x + static_cast<int64_t>(l) * n, y, nt, true, grid1, flags, st));
-    if (precision == FK_FP64) {
-      FK_TRY(grid_to_modes<double>(p1, grid1, 0, 1, 2 * m, corr1, inv_n, T1 + 2 * static_cast<int64_t>(l) * M2, st, inner));
-      FK_TRY(grid_to_modes<double>(p1, grid1, 1, nt, m, corr1, inv_n, bt, st, inner));
-    } else {
-      FK_TRY(grid_to_modes<float>(p1, grid1, 0, 1, 2 * m, corr1, inv_n, T1 + 2 * static_cast<int64_t>(l) * M2, st, inner));
-      FK_TRY(grid_to_modes<float>(p1, grid1, 1, nt, m, corr1, inv_n, bt, st, inner));
+  // The 1-D transforms run on side stream 2, forked here and joined after the pair
+  // transforms (which they do not touch), so that their short launches (FFT,
+  // extraction, copies) overlap the pairs' long ones.  Every exit after the fork joins
+  // first: the scratch memory they use is released on the caller's stream.
+  cudaStream_t side[NSIDE];
+  FK_TRY(side_streams(side));
+  cudaEvent_t ev_fork = nullptr, ev_1d = nullptr;
+  FK_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+  FK_CUDA(cudaEventCreateWithFlags(&ev_1d, cudaEventDisableTiming));
+  struct EvGuard {
+    cudaEvent_t* e[2];
+    ~EvGuard() {
+      for (cudaEvent_t* p : e) cudaEventDestroy(*p);
     }
-    // rhs[t][l K + k] = bt[t][k]
-    FK_CUDA(cudaMemcpy2DAsync(rhs + 2 * static_cast<int64_t>(l) * K, sizeof(double) * 2 * Dall, bt,
-                              sizeof(double) * 2 * K, sizeof(double) * 2 * K, nt, cudaMemcpyDeviceToDevice, st));
+  } ev_guard{{&ev_fork, &ev_1d}};
+  FK_CUDA(cudaEventRecord(ev_fork, st));
+  FK_CUDA(cudaStreamWaitEvent(side[2], ev_fork, 0));
+  auto run1d = [&](cudaStream_t s1) -> fk_status {
+    for (int l = 0; l < d; ++l) {
+      Scratch inner(s1);  // released (stream-ordered) after each coordinate
+      if (fixed1d)
+        FK_TRY(spread1d_fixed(p1, n, reinterpret_cast<const float*>(x + static_cast<int64_t>(l) * n),
+                              reinterpret_cast<const float*>(y), nt, true, amax, grid1, false, flags, s1, inner,
+                              o.autotune != 0, o.spread != FK_SPREAD_FIXED_SHARED));
+      else if (det)
+        FK_TRY(spread_deterministic<R>(p1, n, x + static_cast<int64_t>(l) * n, y, nt, true, grid1, flags, s1, inner));
+      else
+        FK_TRY(spread_atomic<R>(p1, n, x + static_cast<int64_t>(l) * n, y, nt, true, grid1, flags, s1));
+      if (precision == FK_FP64) {
+        FK_TRY(grid_to_modes<double>(p1, grid1, 0, 1, 2 * m, corr1, inv_n, T1 + 2 * static_cast<int64_t>(l) * M2, s1, inner));
+        FK_TRY(grid_to_modes<double>(p1, grid1, 1, nt, m, corr1, inv_n, bt, s1, inner));
+      } else {
+        FK_TRY(grid_to_modes<float>(p1, grid1, 0, 1, 2 * m, corr1, inv_n, T1 + 2 * static_cast<int64_t>(l) * M2, s1, inner));
+        FK_TRY(grid_to_modes<float>(p1, grid1, 1, nt, m, corr1, inv_n, bt, s1, inner));
+      }
+      // rhs[t][l K + k] = bt[t][k]
+      FK_CUDA(cudaMemcpy2DAsync(rhs + 2 * static_cast<int64_t>(l) * K, sizeof(double) * 2 * Dall, bt,
+                                sizeof(double) * 2 * K, sizeof(double) * 2 * K, nt, cudaMemcpyDeviceToDevice, s1));
+    }
+    return FK_OK;
+  };
+  {
+    const fk_status rc1 = run1d(side[2]);
+    const cudaError_t e1 = cudaEventRecord(ev_1d, side[2]);
+    if (rc1 != FK_OK || e1 != cudaSuccess) {
+      if (e1 == cudaSuccess) cudaStreamWaitEvent(st, ev_1d, 0);
+      else cudaStreamSynchronize(side[2]);
+      if (rc1 != FK_OK) return rc1;
+      FK_CUDA(e1);
+    }
   }
+  // from here every return joins side stream 2 first
+  auto join1d = [&]() { cudaStreamWaitEvent(st, ev_1d, 0); };
+  struct Join {
+    std::function<void()> f;
+    bool done = false;
+    void operator()() {
+      if (!done) f();
+      done = true;
+    }
+    ~Join() { (*this)(); }
+  } join{join1d};
   // 2-D blocks of ones at (X_l1, -X_l2)
   EsPlan p2;
   FK_TRY(make_es_plan(2, m, eps, o.upsampfac, &p2));
@@ -168,39 +212,53 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
     double* pg = nullptr;
     FK_TRY(scr.alloc(&pg, static_cast<size_t>(npairs) * NN));
     FK_TRY(additive_pairs_begin(p2, d, n, reinterpret_cast<const float*>(x), flags, st, scr, &S));
-    cudaStream_t side[2];
-    FK_TRY(side_streams(side));
     cudaEvent_t ev_part = nullptr, ev_done[2] = {};
     FK_CUDA(cudaEventCreateWithFlags(&ev_part, cudaEventDisableTiming));
     FK_CUDA(cudaEventCreateWithFlags(&ev_done[0], cudaEventDisableTiming));
     FK_CUDA(cudaEventCreateWithFlags(&ev_done[1], cudaEventDisableTiming));
     bool used[2] = {false, false};
     fk_status rc = FK_OK;
+    // a failed call inside the fork ends the loop (no early return: the side streams are
+    // joined below first)
+    auto ck = [&](cudaError_t e, const char* what) {
+      if (e != cudaSuccess && rc == FK_OK)
+        rc = set_error(FK_ECUDA, "additive pairs: %s failed: %s", what, cudaGetErrorString(e));
+      return rc == FK_OK;
+    };
     int pair0 = 0;
     for (int l1 = 0; l1 + 1 < d && rc == FK_OK; ++l1) {
       const int s = l1 & 1;
-      if (used[s]) FK_CUDA(cudaStreamWaitEvent(st, ev_done[s], 0));
+      if (used[s] && !ck(cudaStreamWaitEvent(st, ev_done[s], 0), "cudaStreamWaitEvent")) break;
       rc = additive_pairs_part(S, l1, flags, st);
       if (rc != FK_OK) break;
-      FK_CUDA(cudaEventRecord(ev_part, st));
-      FK_CUDA(cudaStreamWaitEvent(side[s], ev_part, 0));
+      if (!ck(cudaEventRecord(ev_part, st), "cudaEventRecord")) break;
+      if (!ck(cudaStreamWaitEvent(side[s], ev_part, 0), "cudaStreamWaitEvent")) break;
       rc = additive_pairs_acc(S, l1, pg + pair0 * NN, flags, side[s]);
-      FK_CUDA(cudaEventRecord(ev_done[s], side[s]));
+      // the pair blocks of l1 from their grids, on the same side stream
+      for (int l2 = l1 + 1; l2 < d && rc == FK_OK; ++l2) {
+        Scratch inner(side[s]);
+        const int pair = pair0 + (l2 - l1 - 1);
+        rc = grid_to_modes<float>(p2, pg + pair * NN, 0, 1, m, corr2, inv_n,
+                                  Bp + 2 * static_cast<int64_t>(pair) * K * K, side[s], inner);
+      }
+      if (cudaEventRecord(ev_done[s], side[s]) != cudaSuccess) {
+        cudaStreamSynchronize(side[s]);  // cannot be joined by an event: wait for it here
+        ck(cudaErrorUnknown, "cudaEventRecord");
+        break;
+      }
       used[s] = true;
       pair0 += d - 1 - l1;
     }
     // join the side streams (also after an error, so that nothing is left forked)
     for (int s = 0; s < 2; ++s)
-      if (used[s]) FK_CUDA(cudaStreamWaitEvent(st, ev_done[s], 0));
+      if (used[s] && cudaStreamWaitEvent(st, ev_done[s], 0) != cudaSuccess) {
+        cudaStreamSynchronize(side[s]);
+        ck(cudaErrorUnknown, "cudaStreamWaitEvent");
+      }
     cudaEventDestroy(ev_part);
     cudaEventDestroy(ev_done[0]);
     cudaEventDestroy(ev_done[1]);
     FK_TRY(rc);
-    for (int pair = 0; pair < npairs; ++pair) {
-      Scratch inner(st);
-      FK_TRY(grid_to_modes<float>(p2, pg + pair * NN, 0, 1, m, corr2, inv_n,
-                                  Bp + 2 * static_cast<int64_t>(pair) * K * K, st, inner));
-    }
   }
   int pair = 0;
   for (int l1 = 0; l1 < d && !rowpairs; ++l1)
@@ -231,6 +289,7 @@ fk_status fit_additive_impl(int d, int64_t n, const R* x, const R* y, int nt, in
         FK_TRY(grid_to_modes<float>(p2, grid2, 0, 1, m, corr2, inv_n, blk, st, inner));
       }
     }
+  join();  // the 1-D transforms
   if (rep) cudaEventRecord(ev[1], st);
   // block Gram + lambda I, dense solve per lambda (or one eigendecomposition for all)
   stage_range.next("fk additive solve");
