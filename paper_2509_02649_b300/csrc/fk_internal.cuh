@@ -221,9 +221,9 @@ fk_status spread_binned_xy(const EsPlan& p, int64_t n, const float* x0, const fl
 // Pair grids of the additive model (Sec. 5): for l1 < d - 1, the N x N grids of ones at
 // (X_l1, -X_l2) for the partners l2 = l1 + 1 .. d - 1, from one partition of the points
 // by the rows of coordinate l1 (mixed path, N <= 256, 4 <= w <= 8).  begin allocates the
-// record streams in scr (two sets) and counts coordinate 0's rows; part(l1) must follow
-// for l1 = 0, 1, .. in order on one stream (each partition counts the next coordinate's
-// rows) and writes record set l1 & 1; acc(l1), on any stream ordered after part(l1),
+// record streams in scr (two sets), counts every coordinate's row owners and computes
+// the partners' code words once; part(l1) must follow for l1 = 0, 1, .. in order on one
+// stream and writes record set l1 & 1; acc(l1), on any stream ordered after part(l1),
 // reads that set and writes the d - 1 - l1 grids [partner][N^2] (zeroed inside).  So
 // part(l1 + 2) must be ordered after acc(l1), and acc(l1) may overlap part(l1 + 1) and
 // acc(l1 + 1).
@@ -235,6 +235,7 @@ struct AddPairState {
   int* cnt = nullptr;           // [d + 1][G]: counts of each coordinate's row owners, then reservations
   unsigned* o1[2] = {};         // per record set: [stride] row words
   unsigned* code[2] = {};       // per record set: [d - 1][stride] code words
+  unsigned* codes = nullptr;    // [d - 1][n] code words of -X_1 .. -X_(d-1), unbucketed
 };
 bool additive_pairs_supported(const EsPlan& p, int d, int64_t n);
 fk_status additive_pairs_begin(const EsPlan& p, int d, int64_t n, const float* x, unsigned* flags, cudaStream_t st,

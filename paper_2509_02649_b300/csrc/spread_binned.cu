@@ -1476,9 +1476,9 @@ fk_status spread_binned_xy(const EsPlan& p, int64_t n, const float* x, const flo
 // point has the same owner for every partner l2: one partition per l1 sorts the points
 // by row owner and writes the row word once plus one code word per partner (RecAdd),
 // and one accumulation launch runs the (owner, partner) CTAs of all partners of l1.
-// Bucket sizes are exact, counted before the partition (coordinate 0 by k_add_count,
-// coordinate l1 + 1 by the partition of l1, which reads it as its first partner), so
-// no bucket overflows; buckets start at multiples of 4 records for the 16-byte copies.
+// Bucket sizes are exact, counted before the partitions for every coordinate by
+// k_add_codes (which also computes each partner coordinate's code words once), so no
+// bucket overflows; buckets start at multiples of 4 records for the 16-byte copies.
 namespace fk {
 namespace {
 
@@ -1490,11 +1490,13 @@ struct AddPartArgs {
   int N, W, G, P;   // grid nodes per dimension (<= 256), width, row owners (N / 2), partners
   int64_t n;
   const float* xl1;  // coordinate l1 (n floats); partner p is the row xl1 + (1 + p) n
+  // precomputed partner code words (k_add_codes): partner p's are the row pre + p n, and
+  // the partition takes them instead of the partners' coordinates (null: computes them)
+  const unsigned* pre;
   int vec_ok;        // 16-byte aligned rows and n % 4 == 0: bulk copies of the tiles
   int64_t range;     // points per CTA (multiple of 4)
   const int* cnt;    // [G] exact bucket sizes of this l1
   int* fill;         // [G] reservation counters (zeroed)
-  int* cnt_next;     // [G] (zeroed) counts of the row owners of coordinate l1 + 1, or null
   unsigned* o1;      // row words, bucketed
   unsigned* code;    // [P][stride] code words, bucketed like o1
   int64_t stride;
@@ -1513,25 +1515,57 @@ __device__ __forceinline__ bool add_window(float x, const AddPartArgs& A, int* n
   return true;
 }
 
-// row owners of coordinate xl1 counted into cnt_next
-__global__ void __launch_bounds__(512) k_add_count(AddPartArgs A) {
-  __shared__ int h[256];
-  for (int o = threadIdx.x; o < A.G; o += blockDim.x) h[o] = 0;
+// Once per fit, for every coordinate l: the row owners' counts of l (l < d - 1) into
+// cnt[l][G], and the code word of -X_l (l >= 1) into codes[l - 1][n], c << 23 | v with
+// the window-start column c and v = (w/2 - f) 2^23, or 0xFFFFFFFF for a point out of
+// range (flagged).  A partition then adds the row bit (r N << 23) to a partner's code
+// word, so each coordinate's window is computed here once instead of once per pair.
+struct AddCodeArgs {
+  int d, N, W, G;
+  int64_t n;
+  const float* x;  // [d][n]
+  int* cnt;        // [d][G]
+  unsigned* codes; // [d - 1][n]
+  unsigned* flags;
+  float c_hi, c_lo;
+};
+constexpr int AC_MAXD = 16;
+__global__ void __launch_bounds__(512) k_add_codes(AddCodeArgs C) {
+  __shared__ int h[AC_MAXD - 1][128];
+  AddPartArgs A{};
+  A.N = C.N;
+  A.W = C.W;
+  A.c_hi = C.c_hi;
+  A.c_lo = C.c_lo;
+  for (int t = threadIdx.x; t < (C.d - 1) * 128; t += blockDim.x) h[t / 128][t % 128] = 0;
   __syncthreads();
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < A.n;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < C.n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    int c;
-    unsigned v;
-    if (add_window(__ldg(A.xl1 + i), A, &c, &v)) atomicAdd(&h[c >> 1], 1);
-    else atomicOr(A.flags, FLAG_RANGE);
+    for (int l = 0; l < C.d; ++l) {
+      const float xv = __ldg(C.x + static_cast<int64_t>(l) * C.n + i);
+      int c;
+      unsigned v;
+      if (l + 1 < C.d) {
+        if (add_window(xv, A, &c, &v)) atomicAdd(&h[l][c >> 1], 1);
+        else atomicOr(C.flags, FLAG_RANGE);
+      }
+      if (l >= 1) {
+        unsigned code = 0xFFFFFFFFu;
+        if (add_window(-xv, A, &c, &v)) code = (static_cast<unsigned>(c) << 23) | v;
+        else atomicOr(C.flags, FLAG_RANGE);
+        C.codes[static_cast<int64_t>(l - 1) * C.n + i] = code;
+      }
+    }
   }
   __syncthreads();
-  for (int o = threadIdx.x; o < A.G; o += blockDim.x)
-    if (h[o]) atomicAdd(A.cnt_next + o, h[o]);
+  for (int t = threadIdx.x; t < (C.d - 1) * C.G; t += blockDim.x) {
+    const int l = t / C.G, o = t - l * C.G;
+    if (h[l][o]) atomicAdd(C.cnt + t, h[l][o]);
+  }
 }
 
 struct ApLayout {
-  size_t stage, srow, scode, gdj, base, tcnt, toff, hnext, gdelta, bar, total;
+  size_t stage, srow, scode, gdj, base, tcnt, toff, gdelta, bar, total;
 };
 __host__ __device__ inline ApLayout ap_layout(int P, int G) {
   ApLayout L;
@@ -1542,8 +1576,7 @@ __host__ __device__ inline ApLayout ap_layout(int P, int G) {
   L.base = L.gdj + sizeof(long long) * AP_TILE;                    // int [G]
   L.tcnt = L.base + sizeof(int) * G;                               // int [G + 1]
   L.toff = L.tcnt + sizeof(int) * (G + 1);                         // int [G + 1]
-  L.hnext = L.toff + sizeof(int) * (G + 1);                        // int [G]
-  L.gdelta = (L.hnext + sizeof(int) * G + 7) & ~static_cast<size_t>(7);  // long long [G]
+  L.gdelta = (L.toff + sizeof(int) * (G + 1) + 7) & ~static_cast<size_t>(7);  // long long [G]
   L.bar = (L.gdelta + sizeof(long long) * G + 15) & ~static_cast<size_t>(15);  // uint64_t [P + 1]
   L.total = L.bar + sizeof(uint64_t) * (P + 1);
   return L;
@@ -1561,7 +1594,6 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
   int* base = reinterpret_cast<int*>(smem + L.base);              // bucket starts
   int* tcnt = reinterpret_cast<int*>(smem + L.tcnt);              // tile counts
   int* toff = reinterpret_cast<int*>(smem + L.toff);              // tile run starts
-  int* hnext = reinterpret_cast<int*>(smem + L.hnext);            // counts for the next l1
   long long* gdelta = reinterpret_cast<long long*>(smem + L.gdelta);  // bucket slot of tile slot 0
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);     // one per staged row
   // bucket starts: exclusive scan of the counts padded to 4 (G <= blockDim)
@@ -1578,10 +1610,7 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
     __syncthreads();
     int pre = 0;
     for (int w = 0; w < warp; ++w) pre += wsum[w];
-    if (tid < G) {
-      base[tid] = pre + incl - v;
-      hnext[tid] = 0;
-    }
+    if (tid < G) base[tid] = pre + incl - v;
   }
   if (tid == 0) {
     for (int q = 0; q <= P; ++q) mbar_init(bar + q);
@@ -1595,11 +1624,16 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
   // bar[q].  Each row of the next tile is requested as soon as every thread has passed
   // the barrier after the row's last read in this tile (row 0 after the row words,
   // row 1 + p after partner p's codes), so the loads overlap this tile's work.
+  // staged row q: coordinate l1 (q = 0), then partner q - 1's coordinate or code words
+  auto row_src = [&](int q) -> const float* {
+    if (q > 0 && A.pre) return reinterpret_cast<const float*>(A.pre + static_cast<int64_t>(q - 1) * A.n);
+    return A.xl1 + q * A.n;
+  };
   auto issue_row = [&](int q, int64_t t) {
     const unsigned bytes = static_cast<unsigned>(min(static_cast<int64_t>(AP_TILE), e0 - t)) * 4u;  // % 16 == 0
     fence_proxy_async();
     mbar_arrive_expect(bar + q, bytes);
-    bulk_g2s(stage + q * AP_TILE, A.xl1 + q * A.n + t, bytes, bar + q);
+    bulk_g2s(stage + q * AP_TILE, row_src(q) + t, bytes, bar + q);
   };
   if (A.vec_ok && tid == 0 && s0 < e0)
     for (int q = 0; q <= P; ++q) issue_row(q, s0);
@@ -1616,13 +1650,13 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
     // the tile counts were zeroed after their last read of the tile before; with bulk
     // copies each thread waits for the staged rows itself, plain loads need a barrier
     if (A.vec_ok) {
-      if (!mbar_wait(bar, phase, A.flags) || !mbar_wait(bar + 1, phase, A.flags)) {
+      if (!mbar_wait(bar, phase, A.flags)) {
         drain(-1, next);
         return;
       }
     } else {
       for (int q = 0; q <= P; ++q)
-        for (int i = tid; i < cnt; i += AP_THREADS) stage[q * AP_TILE + i] = __ldg(A.xl1 + q * A.n + t0 + i);
+        for (int i = tid; i < cnt; i += AP_THREADS) stage[q * AP_TILE + i] = __ldg(row_src(q) + t0 + i);
       __syncthreads();
     }
     // row word and rank of each point inside its owner's run of the tile
@@ -1642,7 +1676,6 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
         } else {
           atomicOr(A.flags, FLAG_RANGE);
         }
-        if (A.cnt_next && add_window(stage[AP_TILE + i], A, &c, &v)) atomicAdd(&hnext[c >> 1], 1);
       }
     }
     __syncthreads();
@@ -1700,7 +1733,7 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
     // every thread has passed the barrier in between)
     for (int p = 0; p < P; ++p) {
       unsigned* sc = scode + (p & 1) * AP_TILE;
-      if (A.vec_ok && p >= 1 && !mbar_wait(bar + 1 + p, phase, A.flags)) {
+      if (A.vec_ok && !mbar_wait(bar + 1 + p, phase, A.flags)) {
         drain(p, next);
         return;
       }
@@ -1710,10 +1743,15 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
         const int i = k * AP_THREADS + tid;
         int c;
         unsigned v, code = 0u;
-        if (add_window(-stage[(1 + p) * AP_TILE + i], A, &c, &v))
+        if (A.pre) {
+          // precomputed c << 23 | v (out-of-range points were flagged there)
+          const unsigned pc = __float_as_uint(stage[(1 + p) * AP_TILE + i]);
+          if (pc != 0xFFFFFFFFu) code = pc + ((((w1[k] >> 24) & 1u) * static_cast<unsigned>(A.N)) << 23);
+        } else if (add_window(-stage[(1 + p) * AP_TILE + i], A, &c, &v)) {
           code = ((((w1[k] >> 24) & 1u) * static_cast<unsigned>(A.N) + static_cast<unsigned>(c)) << 23) | v;
-        else
+        } else {
           atomicOr(A.flags, FLAG_RANGE);
+        }
         sc[toff[w1[k] >> 25] + rk[k]] = code;
       }
       __syncthreads();
@@ -1727,15 +1765,12 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
     __syncthreads();  // the code buffers are free for the next tile
     phase ^= 1u;
   }
-  if (A.cnt_next)
-    for (int o = tid; o < G; o += AP_THREADS)
-      if (hnext[o]) atomicAdd(A.cnt_next + o, hnext[o]);
 }
 
 }  // namespace
 
 bool additive_pairs_supported(const EsPlan& p, int d, int64_t n) {
-  return p.d == 2 && p.N >= 16 && p.N <= 256 && p.w >= 4 && p.w <= 8 && d >= 2 && d <= 16 && n >= 1 &&
+  return p.d == 2 && p.N >= 16 && p.N <= 256 && p.w >= 4 && p.w <= 8 && d >= 2 && d <= AC_MAXD && n >= 1 &&
          n + 4LL * 256 + 16 < (static_cast<int64_t>(1) << 31) && sm_count() > 0;
 }
 
@@ -1755,19 +1790,22 @@ fk_status additive_pairs_begin(const EsPlan& p, int d, int64_t n, const float* x
     FK_TRY(scr.alloc(&S->o1[s], static_cast<size_t>(S->stride)));
     FK_TRY(scr.alloc(&S->code[s], static_cast<size_t>(S->stride) * (d - 1 - s)));
   }
+  FK_TRY(scr.alloc(&S->codes, static_cast<size_t>(n) * (d - 1)));
   FK_CUDA(cudaMemsetAsync(S->cnt, 0, sizeof(int) * (d + 1) * S->G, st));
-  AddPartArgs A{};
+  AddCodeArgs C{};
   const CoordConst cc = coord_const(p.N);
-  A.N = p.N;
-  A.W = p.w;
-  A.G = S->G;
-  A.n = n;
-  A.xl1 = x;
-  A.cnt_next = S->cnt;  // counts of coordinate 0
-  A.flags = flags;
-  A.c_hi = cc.hi;
-  A.c_lo = cc.lo;
-  k_add_count<<<grid_for(n, 512, 4 * sm_count()), 512, 0, st>>>(A); note_launch();
+  C.d = d;
+  C.N = p.N;
+  C.W = p.w;
+  C.G = S->G;
+  C.n = n;
+  C.x = x;
+  C.cnt = S->cnt;
+  C.codes = S->codes;
+  C.flags = flags;
+  C.c_hi = cc.hi;
+  C.c_lo = cc.lo;
+  k_add_codes<<<grid_for(n, 512, 4 * sm_count()), 512, 0, st>>>(C); note_launch();
   FK_CUDA(cudaGetLastError());
   return FK_OK;
 }
@@ -1777,7 +1815,6 @@ fk_status additive_pairs_part(AddPairState& S, int l1, unsigned* flags, cudaStre
   const int G = S.G, P = S.d - 1 - l1, N = p.N;
   if (P < 1) return FK_OK;
   int* cnt = S.cnt + l1 * G;
-  int* cnt_next = S.cnt + (l1 + 1) * G;  // zeroed by begin
   int* fill = S.cnt + S.d * G;
   const int sms = sm_count();
   FK_CUDA(cudaMemsetAsync(fill, 0, sizeof(int) * G, st));
@@ -1794,7 +1831,7 @@ fk_status additive_pairs_part(AddPairState& S, int l1, unsigned* flags, cudaStre
   A.range = ((S.n + nblk - 1) / nblk + 3) & ~static_cast<int64_t>(3);
   A.cnt = cnt;
   A.fill = fill;
-  A.cnt_next = (l1 + 2 <= S.d - 1) ? cnt_next : nullptr;  // rows of l1 + 1 are needed if it has partners
+  A.pre = S.codes + static_cast<int64_t>(l1) * S.n;  // partner p = coordinate l1 + 1 + p
   A.o1 = S.o1[l1 & 1];
   A.code = S.code[l1 & 1];
   A.stride = S.stride;
