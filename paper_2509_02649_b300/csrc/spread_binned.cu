@@ -1530,7 +1530,9 @@ struct AddCodeArgs {
   float c_hi, c_lo;
 };
 constexpr int AC_MAXD = 16;
-__global__ void __launch_bounds__(512) k_add_codes(AddCodeArgs C) {
+// DMAX: coordinates held at once (d <= DMAX); 8 keeps three 512-thread CTAs per SM
+template <int DMAX>
+__global__ void __launch_bounds__(512, DMAX <= 8 ? 3 : 2) k_add_codes(AddCodeArgs C) {
   __shared__ int h[AC_MAXD - 1][128];
   AddPartArgs A{};
   A.N = C.N;
@@ -1539,22 +1541,33 @@ __global__ void __launch_bounds__(512) k_add_codes(AddCodeArgs C) {
   A.c_lo = C.c_lo;
   for (int t = threadIdx.x; t < (C.d - 1) * 128; t += blockDim.x) h[t / 128][t % 128] = 0;
   __syncthreads();
+  // one coordinate value: its row owner counted (l < d - 1), its code word returned (l >= 1)
+  auto one = [&](int l, float xv) -> unsigned {
+    int c;
+    unsigned v, code = 0xFFFFFFFFu;
+    if (l + 1 < C.d) {
+      if (add_window(xv, A, &c, &v)) atomicAdd(&h[l][c >> 1], 1);
+      else atomicOr(C.flags, FLAG_RANGE);
+    }
+    if (l >= 1) {
+      if (add_window(-xv, A, &c, &v)) code = (static_cast<unsigned>(c) << 23) | v;
+      else atomicOr(C.flags, FLAG_RANGE);
+    }
+    return code;
+  };
+  // one point per thread (the window arithmetic is latency bound: many warps per SM),
+  // every coordinate's load in flight before the arithmetic
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < C.n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    for (int l = 0; l < C.d; ++l) {
-      const float xv = __ldg(C.x + static_cast<int64_t>(l) * C.n + i);
-      int c;
-      unsigned v;
-      if (l + 1 < C.d) {
-        if (add_window(xv, A, &c, &v)) atomicAdd(&h[l][c >> 1], 1);
-        else atomicOr(C.flags, FLAG_RANGE);
-      }
-      if (l >= 1) {
-        unsigned code = 0xFFFFFFFFu;
-        if (add_window(-xv, A, &c, &v)) code = (static_cast<unsigned>(c) << 23) | v;
-        else atomicOr(C.flags, FLAG_RANGE);
-        C.codes[static_cast<int64_t>(l - 1) * C.n + i] = code;
-      }
+    float xv[DMAX];
+#pragma unroll
+    for (int l = 0; l < DMAX; ++l)
+      if (l < C.d) xv[l] = __ldg(C.x + static_cast<int64_t>(l) * C.n + i);
+#pragma unroll
+    for (int l = 0; l < DMAX; ++l) {
+      if (l >= C.d) break;
+      const unsigned code = one(l, xv[l]);
+      if (l >= 1) C.codes[static_cast<int64_t>(l - 1) * C.n + i] = code;
     }
   }
   __syncthreads();
@@ -1805,7 +1818,9 @@ fk_status additive_pairs_begin(const EsPlan& p, int d, int64_t n, const float* x
   C.flags = flags;
   C.c_hi = cc.hi;
   C.c_lo = cc.lo;
-  k_add_codes<<<grid_for(n, 512, 4 * sm_count()), 512, 0, st>>>(C); note_launch();
+  if (d <= 8) k_add_codes<8><<<grid_for(n, 512, 6 * sm_count()), 512, 0, st>>>(C);
+  else k_add_codes<AC_MAXD><<<grid_for(n, 512, 4 * sm_count()), 512, 0, st>>>(C);
+  note_launch();
   FK_CUDA(cudaGetLastError());
   return FK_OK;
 }
