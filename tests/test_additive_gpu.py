@@ -72,3 +72,41 @@ def test_additive_rejects_zero_lambda():
     X = torch.zeros((2, 8), dtype=torch.float64, device="cuda")
     with pytest.raises(fk.FkError):
         fk.fk_fit_additive(X, X[0], 3, [0.0], 1e-6, "fp64")
+
+
+def test_additive_fits_from_two_host_threads():
+    # the fit forks its pair and 1-D transforms onto side streams of the calling host
+    # thread (joined before it returns); two threads fitting at once on their own
+    # streams must each get the answer of a fit made alone
+    import threading
+
+    d, m, n = 8, 20, 40_000
+    X, y = S.wl4_additive(n, d=d, dtype=np.float32)
+    lam = 1e-3
+    Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    want = fk.fk_fit_additive(Xd, yd, m, [lam], 1e-6, "mixed").cpu().numpy()[0, 0]
+    tho = O.fit_additive(X.astype(np.float64), y.astype(np.float64), m, lam)
+    assert rel(unique_part(want, d, m), unique_part(tho, d, m)) <= 1e-5
+    out, errs = {}, []
+
+    def worker(k):
+        try:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                res = [fk.fk_fit_additive(Xd, yd, m, [lam], 1e-6, "mixed") for _ in range(3)]
+            s.synchronize()
+            out[k] = [r.cpu().numpy()[0, 0] for r in res]
+        except Exception as e:  # reported below
+            errs.append(e)
+
+    ts = [threading.Thread(target=worker, args=(k,)) for k in range(2)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errs, errs
+    for k in range(2):
+        for th in out[k]:
+            # the 2-D register sums depend on the order in which records reach a cell,
+            # so fits agree to the spreading's rounding, not bit for bit
+            assert rel(unique_part(th, d, m), unique_part(want, d, m)) <= 1e-6
