@@ -1578,15 +1578,14 @@ __global__ void __launch_bounds__(512, DMAX <= 8 ? 3 : 2) k_add_codes(AddCodeArg
 }
 
 struct ApLayout {
-  size_t stage, srow, scode, gdj, base, tcnt, toff, gdelta, bar, total;
+  size_t stage, srow, scode, base, tcnt, toff, gdelta, bar, total;
 };
 __host__ __device__ inline ApLayout ap_layout(int P, int G) {
   ApLayout L;
   L.stage = 0;                                                     // float [P + 1][AP_TILE]
   L.srow = L.stage + sizeof(float) * (P + 1) * AP_TILE;            // unsigned [AP_TILE]
   L.scode = L.srow + sizeof(unsigned) * AP_TILE;                   // unsigned [2][AP_TILE]
-  L.gdj = L.scode + sizeof(unsigned) * 2 * AP_TILE;                // long long [AP_TILE]
-  L.base = L.gdj + sizeof(long long) * AP_TILE;                    // int [G]
+  L.base = L.scode + sizeof(unsigned) * 2 * AP_TILE;               // int [G]
   L.tcnt = L.base + sizeof(int) * G;                               // int [G + 1]
   L.toff = L.tcnt + sizeof(int) * (G + 1);                         // int [G + 1]
   L.gdelta = (L.toff + sizeof(int) * (G + 1) + 7) & ~static_cast<size_t>(7);  // long long [G]
@@ -1603,7 +1602,6 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
   float* stage = reinterpret_cast<float*>(smem + L.stage);
   unsigned* srow = reinterpret_cast<unsigned*>(smem + L.srow);    // row words in owner order
   unsigned* scode = reinterpret_cast<unsigned*>(smem + L.scode);  // two partners' codes in owner order
-  long long* gdj = reinterpret_cast<long long*>(smem + L.gdj);    // bucket slot of tile slot j, or -1
   int* base = reinterpret_cast<int*>(smem + L.base);              // bucket starts
   int* tcnt = reinterpret_cast<int*>(smem + L.tcnt);              // tile counts
   int* toff = reinterpret_cast<int*>(smem + L.toff);              // tile run starts
@@ -1726,20 +1724,31 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
       if (!room) atomicOr(A.flags, FLAG_INTERNAL);
       gdelta[tid] = room ? static_cast<long long>(base[tid]) + my_pos - toff[tid] : NO_ROOM;
     }
+    // each point's slot in the tile's owner order, the same for the row word and every
+    // partner's code word: looked up once
+    int pos[AP_PER];
 #pragma unroll
-    for (int k = 0; k < AP_PER; ++k)
-      if (w1[k] != 0xFFFFFFFFu) srow[toff[w1[k] >> 25] + rk[k]] = w1[k];
+    for (int k = 0; k < AP_PER; ++k) {
+      pos[k] = (w1[k] != 0xFFFFFFFFu) ? toff[w1[k] >> 25] + rk[k] : 0;
+      if (w1[k] != 0xFFFFFFFFu) srow[pos[k]] = w1[k];
+    }
     __syncthreads();
     const int valid = toff[G];
-    for (int j = tid; j < valid; j += AP_THREADS) {
-      const unsigned w = srow[j];
-      const long long gd = gdelta[w >> 25];
-      long long at = -1;
-      if (gd != NO_ROOM && fk_check(gd + j >= 0 && gd + j < A.stride, A.flags)) {
-        at = gd + j;
-        A.o1[at] = w;
+    // bucket index of this thread's tile slots j = k AP_THREADS + tid (or -1), kept in
+    // registers for the partners' copies
+    long long at[AP_PER];
+#pragma unroll
+    for (int k = 0; k < AP_PER; ++k) {
+      const int j = k * AP_THREADS + tid;
+      at[k] = -1;
+      if (j < valid) {
+        const unsigned w = srow[j];
+        const long long gd = gdelta[w >> 25];
+        if (gd != NO_ROOM && fk_check(gd + j >= 0 && gd + j < A.stride, A.flags)) {
+          at[k] = gd + j;
+          A.o1[at[k]] = w;
+        }
       }
-      gdj[j] = at;  // read by this thread only until the partners' barrier below
     }
     // one code stream per partner, in the same order; two code buffers, so that one
     // barrier per partner suffices (a buffer is rewritten two partners later, after
@@ -1765,15 +1774,14 @@ __global__ void __launch_bounds__(AP_THREADS, 2) k_add_part(AddPartArgs A) {
         } else {
           atomicOr(A.flags, FLAG_RANGE);
         }
-        sc[toff[w1[k] >> 25] + rk[k]] = code;
+        sc[pos[k]] = code;
       }
       __syncthreads();
       if (A.vec_ok && tid == 0 && next) issue_row(1 + p, t0 + AP_TILE);
       unsigned* out = A.code + p * A.stride;
-      for (int j = tid; j < valid; j += AP_THREADS) {
-        const long long at = gdj[j];
-        if (at >= 0) out[at] = sc[j];
-      }
+#pragma unroll
+      for (int k = 0; k < AP_PER; ++k)
+        if (at[k] >= 0) out[at[k]] = sc[k * AP_THREADS + tid];
     }
     __syncthreads();  // the code buffers are free for the next tile
     phase ^= 1u;
