@@ -193,7 +193,7 @@ struct Timer {
 };
 
 // Spread (ones channel if with_ones, then n_y strength channels) onto the fine grid.
-static fk_status spread_any(const EsPlan& p, int precision, const fk_opts& o, int64_t n, const void* x,
+fk_status spread_any(const EsPlan& p, int precision, const fk_opts& o, int64_t n, const void* x,
                             const void* y, int n_y, bool with_ones, double* grid, unsigned* flags,
                             cudaStream_t st, Scratch& scr) {
   // deterministic sums: the 1-D fixed-point spreader (order-independent already) where it

@@ -246,6 +246,13 @@ fk_status additive_pairs_acc(AddPairState& S, int l1, double* grids, unsigned* f
 // 1-D fixed-point shared-memory spreading (fp32 inputs, any channel count).  y_absmax:
 // device array of max|y_c| bit patterns for the n_y strength channels, or null to
 // compute it here.  accumulate: add into grid instead of overwriting it.
+// Spread (ones channel if with_ones, then n_y strength channels) onto the fine grid with
+// the spreader the options and the shape select (binned or fixed-point for the mixed path
+// where they apply, fp64 atomics for FK_FP64, deterministic sums when asked), as the
+// fits do.  x, y: device arrays of the precision's type.
+fk_status spread_any(const EsPlan& p, int precision, const fk_opts& o, int64_t n, const void* x, const void* y,
+                     int n_y, bool with_ones, double* grid, unsigned* flags, cudaStream_t st, Scratch& scr);
+
 bool spread1d_fixed_supported(const EsPlan& p, int n_y, bool with_ones);
 fk_status spread1d_fixed(const EsPlan& p, int64_t n, const float* x, const float* y, int n_y, bool with_ones,
                          const unsigned* y_absmax, double* grid, bool accumulate, unsigned* flags, cudaStream_t st,

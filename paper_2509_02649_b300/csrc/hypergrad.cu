@@ -140,8 +140,8 @@ fk_status hypergrad_impl(int d, int64_t n, const R* x, int64_t n_v, const R* xv,
   FK_CUDA(cudaMemsetAsync(sum, 0, sizeof(double), st));
   k_residual<R><<<grid_for(n_v, 256, 148 * 8), 256, 0, st>>>(n_v, f, yv, r, sum); note_launch();
   FK_CUDA(cudaGetLastError());
-  // g = type1(xv, r) / n_v
-  FK_TRY(spread_atomic<R>(p, n_v, xv, r, 1, false, grid, flags, st));
+  // g = type1(xv, r) / n_v, with the fits' spreader (binned for the mixed path in 2-D)
+  FK_TRY(spread_any(p, precision, o, n_v, xv, r, 1, false, grid, flags, st, scr));
   if (precision == FK_FP64)
     FK_TRY(grid_to_modes<double>(p, grid, 0, 1, m, corr, 1.0 / static_cast<double>(n_v), g, st, scr));
   else
@@ -220,7 +220,8 @@ fk_status adjoint_impl(int d, int m, int64_t n_v, const R* xv, const R* r, const
   FK_TRY(scr.alloc(&g, 2 * static_cast<size_t>(D)));
   FK_TRY(scr.alloc(&z, 2 * static_cast<size_t>(D)));
   FK_TRY(scr.alloc(&grid, static_cast<size_t>(G)));
-  FK_TRY(spread_atomic<R>(p, n_v, xv, r, 1, false, grid, flags, st));
+  // g = type1(xv, r) / n_v, with the fits' spreader (binned for the mixed path in 2-D)
+  FK_TRY(spread_any(p, precision, o, n_v, xv, r, 1, false, grid, flags, st, scr));
   if (precision == FK_FP64)
     FK_TRY(grid_to_modes<double>(p, grid, 0, 1, m, corr, 1.0 / static_cast<double>(n_v), g, st, scr));
   else
