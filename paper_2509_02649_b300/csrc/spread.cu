@@ -11,6 +11,7 @@
 // mixed path; the register-accumulating binned spreader lives in spread_binned.cu.
 #include "fk_internal.cuh"
 #include "window.cuh"
+#include "es_poly.cuh"
 
 namespace fk {
 
@@ -378,6 +379,100 @@ __global__ void k_t2_interp(int d, Win<R> win, R beta, int64_t n, const R* __res
   }
 }
 
+// Interpolation in 2-D, fp32, fine grids of at most T2S_MAXN^2 nodes: each CTA stages the
+// real parts of the grid (the only part Re f needs) in shared memory once, rows padded
+// by W - 1 columns that repeat the first ones (so a window's columns are contiguous),
+// and takes the W taps of each coordinate from the tap polynomials.  Row sums in fp32;
+// the W row terms are summed with error-free transformations (two-product, two-sum),
+// so the outer sum is as accurate as a double one without FP64 instructions.
+constexpr int T2S_MAXN = 128;
+template <int W>
+__global__ void __launch_bounds__(256) k_t2_interp2d_smem(Win<float> win, EsPoly poly, int64_t n,
+                                                          const float* __restrict__ x, int n_sets,
+                                                          const cplx<float>* __restrict__ G, double* out,
+                                                          unsigned* flags) {
+  extern __shared__ float gr[];  // [N][N + W - 1]
+  const int N = win.N, ld = N + W - 1;
+  const float gc = 0.5f * static_cast<float>(W - 1);
+  for (int s = 0; s < n_sets; ++s) {
+    const cplx<float>* g = G + static_cast<int64_t>(s) * N * N;
+    __syncthreads();  // the previous set's reads are done
+    for (int t = threadIdx.x; t < N * ld; t += blockDim.x) {
+      const int r = t / ld, c = t - r * ld;
+      gr[t] = g[r * N + (c & (N - 1))].x;
+    }
+    __syncthreads();
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+      int l0, l1;
+      float f0, f1;
+      if (!win(x[i], &l0, &f0) || !win(x[n + i], &l1, &f1)) {
+        if (s == 0) atomicOr(flags, FLAG_RANGE);
+        out[static_cast<int64_t>(s) * n + i] = 0.0;
+        continue;
+      }
+      float k0[W], k1[W];
+      es_taps_poly<W>(f0 - gc, poly, k0);
+      es_taps_poly<W>(f1 - gc, poly, k1);
+      const int r0 = wrap_node(l0, N);
+      const float* col = gr + wrap_node(l1, N);
+      float hi = 0.f, lo = 0.f;  // outer sum as hi + lo
+#pragma unroll
+      for (int a = 0; a < W; ++a) {
+        const float* row = col + ((r0 + a) & (N - 1)) * ld;
+        float rs = 0.f;
+#pragma unroll
+        for (int b = 0; b < W; ++b) rs = fmaf(k1[b], row[b], rs);
+        // two-product: k0 rs = p + e exactly; two-sum: hi + p = u + v exactly (explicitly
+        // rounded operations, so that none is contracted into an FMA)
+        const float pr = __fmul_rn(k0[a], rs);
+        const float e = fmaf(k0[a], rs, -pr);
+        const float u = __fadd_rn(hi, pr);
+        const float bb = __fsub_rn(u, hi);
+        const float v = __fadd_rn(__fsub_rn(hi, __fsub_rn(u, bb)), __fsub_rn(pr, bb));
+        hi = u;
+        lo += e + v;
+      }
+      out[static_cast<int64_t>(s) * n + i] = static_cast<double>(hi) + static_cast<double>(lo);
+    }
+  }
+}
+
+template <int W>
+fk_status launch_t2_smem(const EsPlan& p, int n_sets, int64_t n, const float* x, const cplx<float>* G, double* out,
+                         unsigned* flags, cudaStream_t st) {
+  const size_t sm = sizeof(float) * static_cast<size_t>(p.N) * (p.N + W - 1);
+  FK_CUDA(cudaFuncSetAttribute(k_t2_interp2d_smem<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+  int per_sm = 1;
+  FK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_t2_interp2d_smem<W>, 256, sm));
+  const int blocks = grid_for(n, 256, std::max(1, per_sm) * std::max(1, sm_count()));
+  k_t2_interp2d_smem<W><<<blocks, 256, sm, st>>>(make_win<float>(p.N, p.w), es_poly(p.w, p.beta), n, x, n_sets, G, out,
+                                                 flags);
+  note_launch();
+  FK_CUDA(cudaGetLastError());
+  return FK_OK;
+}
+
+// the shared-memory interpolation where it applies (2-D, fp32, N <= T2S_MAXN, 4 <= w <= 8)
+template <typename R>
+bool t2_smem_launch(const EsPlan&, int, int64_t, const R*, const cplx<R>*, double*, unsigned*, cudaStream_t,
+                    fk_status*) {
+  return false;
+}
+template <>
+bool t2_smem_launch<float>(const EsPlan& p, int n_sets, int64_t n, const float* x, const cplx<float>* G, double* out,
+                           unsigned* flags, cudaStream_t st, fk_status* rc) {
+  if (p.d != 2 || p.N > T2S_MAXN || p.N < 16) return false;
+  switch (p.w) {
+    case 4: *rc = launch_t2_smem<4>(p, n_sets, n, x, G, out, flags, st); return true;
+    case 5: *rc = launch_t2_smem<5>(p, n_sets, n, x, G, out, flags, st); return true;
+    case 6: *rc = launch_t2_smem<6>(p, n_sets, n, x, G, out, flags, st); return true;
+    case 7: *rc = launch_t2_smem<7>(p, n_sets, n, x, G, out, flags, st); return true;
+    case 8: *rc = launch_t2_smem<8>(p, n_sets, n, x, G, out, flags, st); return true;
+    default: return false;
+  }
+}
+
 template <typename R>
 fk_status type2_eval(const EsPlan& p, int kmax_c, const double* coef, int n_sets, int64_t n, const R* x,
                      const double* corr, double* out, unsigned* flags, cudaStream_t st, Scratch& scratch) {
@@ -417,6 +512,8 @@ fk_status type2_eval(const EsPlan& p, int kmax_c, const double* coef, int n_sets
     FK_TRY(fft_lines<R>(G, N, static_cast<int64_t>(n_sets) * N, N, 1, +1, tw, st));
   }
   if (n > 0) {
+    fk_status rc = FK_OK;
+    if (t2_smem_launch<R>(p, n_sets, n, x, G, out, flags, st, &rc)) return rc;
     k_t2_interp<R><<<grid_for(n, 256, 148 * 16), 256, 0, st>>>(p.d, make_win<R>(N, p.w), static_cast<R>(p.beta), n, x, n_sets,
                                                                G, out, flags); note_launch();
     FK_CUDA(cudaGetLastError());

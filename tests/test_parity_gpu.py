@@ -402,3 +402,23 @@ def test_sobolev_pairs_sweep(d, m, solver):
     for i, (s, lam) in enumerate(pairs):
         want = O.fit(x, y, m, O.penalty_sobolev(d, m, lam, s))
         assert rel(th[i, 0], want) < 1e-9, (s, lam)
+
+
+@pytest.mark.parametrize("kmax,eps", [(30, 1e-6), (13, 1e-3)])
+def test_type2_shared_grid_path_matches_direct_sums(kmax, eps):
+    # mixed 2-D type-2 on fine grids of <= 128^2 nodes (here 128^2 at width 7 and 64^2 at
+    # width 4) interpolates from a copy of the grid in shared memory: several coefficient
+    # sets, a ragged n, and points at the ends of [-3 pi, 3 pi) whose windows wrap
+    n = 20_003
+    x = S.uniform_points(n, 2, 24)
+    x[:, :64] = np.float32(-3 * np.pi) + np.float32(1e-6)
+    x[:, 64:128] = np.nextafter(np.float32(3 * np.pi), np.float32(0)) - np.float32(1e-6)
+    x[:, 128:192] = np.float32(np.pi)
+    x = x.astype(np.float32)
+    g = np.random.default_rng(7)
+    D = (2 * kmax + 1) ** 2
+    coef = g.standard_normal((3, D)) + 1j * g.standard_normal((3, D))
+    got = host(fk.fk_type2(torch.from_numpy(coef).cuda(), dev(x, torch.float32), kmax, eps, "mixed"))
+    for s_ in range(3):
+        want = O.type2(coef[s_], x.astype(np.float64), kmax)
+        assert rel(got[s_], want.real) <= 10 * eps * np.linalg.norm(want) / np.linalg.norm(want.real)
