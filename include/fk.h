@@ -207,7 +207,12 @@ FK_API fk_status fk_box_moments(int d, int m, const double* lo, const double* hi
                                 void* stream);
 
 /* Low-bias additive estimator (Prop. 5.1): theta = (Sigma + lambda I)^{-1} (Phi_l^*Y/n)_l.
- *   d in [2, 16] coordinates; theta: device, [n_lambda][n_targets][d][2m+1] complex. */
+ *   d in [2, 16] coordinates; theta: device, [n_lambda][n_targets][d][2m+1] complex.
+ *   The mixed path forks part of its work onto non-blocking streams of its own (one set
+ *   per device and host thread: the pair transforms' accumulations and the 1-D
+ *   transforms), ordered after the work already on `stream` by events and joined back
+ *   into `stream` before the call returns, on error paths too; to the caller the work is
+ *   ordered as if it were all on `stream`, and a capture on `stream` takes it in. */
 FK_API fk_status fk_fit_additive(int d, int64_t n, const void* x, const void* y, int n_targets,
                           int m, const double* lambdas, int n_lambda, double eps,
                           int precision, const fk_opts* opts, double* theta, void* stream,
