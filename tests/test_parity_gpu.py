@@ -404,11 +404,12 @@ def test_sobolev_pairs_sweep(d, m, solver):
         assert rel(th[i, 0], want) < 1e-9, (s, lam)
 
 
-@pytest.mark.parametrize("kmax,eps", [(30, 1e-6), (13, 1e-3)])
+@pytest.mark.parametrize("kmax,eps", [(30, 1e-6), (13, 1e-3), (3, 1e-6)])
 def test_type2_shared_grid_path_matches_direct_sums(kmax, eps):
-    # mixed 2-D type-2 on fine grids of <= 128^2 nodes (here 128^2 at width 7 and 64^2 at
-    # width 4) interpolates from a copy of the grid in shared memory: several coefficient
-    # sets, a ragged n, and points at the ends of [-3 pi, 3 pi) whose windows wrap
+    # mixed 2-D type-2 on fine grids of <= 128^2 nodes (here 128^2 and 16^2 at width 7,
+    # 64^2 at width 4) interpolates from a copy of the grid in shared memory: several
+    # coefficient sets, a ragged n, and points at the ends of [-3 pi, 3 pi) whose windows
+    # wrap (on the 16-node grid a 7-wide window wraps for most points)
     n = 20_003
     x = S.uniform_points(n, 2, 24)
     x[:, :64] = np.float32(-3 * np.pi) + np.float32(1e-6)
